@@ -1,0 +1,177 @@
+/*
+ * efie.h -- C ABI of the GB300 stabilized multilevel B-spline fast EFIE library.
+ *
+ * The library solves the discretized PEC electric field integral equation
+ *     T j = e,   T = jk A + (jk)^-1 Sigma V Sigma^T
+ * (Sec. II, Eq. discretizedEFIE, with the star form of Sec. VI-A), where A is
+ * the Galerkin vector-potential matrix of RWG functions without edge-length
+ * normalization (Eq. matTA), V the single-layer matrix of pulse functions
+ * phi_c = 1/a_c and Sigma the star matrix.  Products with T use the fast
+ * method of Sec. III-V: exact B-spline moments, knot-insertion interlevel
+ * transfers, knot-removal stabilization (Table I), FFT-accelerated Toeplitz
+ * translations per level, and a sparse FP64 near-field correction.
+ *
+ * Conventions shared by every call:
+ *  - SI units: metres, wavenumber k in rad/m; time dependence e^{j w t}.
+ *  - Unknown m is the RWG of the m-th mesh edge in lexicographic order of its
+ *    (lower, higher) vertex ids; its c+ triangle is the one whose
+ *    counter-clockwise vertex cycle runs lower -> higher.
+ *  - Complex vectors are interleaved (re, im) doubles ("c128"), laid out
+ *    [n_rhs][N] row-major, in device memory owned by the caller unless a call
+ *    says otherwise.  Calls enqueue work on the caller's CUDA stream `stream`
+ *    (a cudaStream_t passed as void*, NULL = legacy default stream).
+ *  - Return codes: 0 success, negative error, positive EFIE_NOT_CONVERGED.
+ *    efie_last_error() gives a message for the last failure of the handle.
+ *
+ * Every call that computes runs in this library's CUDA kernels on the current
+ * device; there is no CPU fallback.  A call made without a usable CUDA device
+ * returns EFIE_ECUDA.
+ */
+#ifndef EFIE_GB300_H
+#define EFIE_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define EFIE_OK 0
+#define EFIE_EINVAL (-1)        /* bad mesh, parameter or size */
+#define EFIE_ENOMEM (-2)        /* device or host allocation failed / over limit */
+#define EFIE_ECUDA (-3)         /* CUDA runtime error or no device */
+#define EFIE_ETIMEOUT (-4)      /* a bounded device wait expired */
+#define EFIE_NOT_CONVERGED 1    /* solver stopped at max_iters; x holds the best iterate */
+
+#define EFIE_FP64 0             /* plain form: every step in complex FP64 */
+#define EFIE_MIXED 1            /* far field in complex FP32; near field, projector
+                                   construction, Arnoldi and true residual in FP64 */
+
+#define EFIE_PRECOND_NONE 0
+#define EFIE_PRECOND_LEARNED 1  /* learned mesh-local FGMRES preconditioner (not in
+                                   the paper); falls back to NONE when unusable */
+
+typedef struct efie_handle efie_handle;   /* opaque, library-owned */
+
+/* Closed, consistently oriented triangle mesh (outward CCW).  Caller-owned host
+ * arrays, copied by efie_setup. */
+typedef struct {
+    int64_t n_vertices;
+    const double *xyz;      /* [n_vertices][3] metres */
+    int64_t n_triangles;
+    const int32_t *tri;     /* [n_triangles][3] vertex ids */
+} efie_mesh;
+
+typedef struct {
+    int32_t n_splines;       /* leaf splines per axis s; 0 -> p + 4 (Sec. VII-B) */
+    int32_t precision;       /* EFIE_FP64 or EFIE_MIXED */
+    int32_t gmres_restart;   /* 0 -> 100 */
+    int32_t max_iters;       /* 0 -> 1000 */
+    int32_t precond;         /* EFIE_PRECOND_* */
+    int32_t rhs_chunk;       /* right-hand sides per far-field pass; 0 -> automatic */
+    const char *weights_path;/* learned preconditioner weights, or NULL */
+    int64_t device_mem_limit;/* bytes; 0 -> no limit beyond the device */
+    uint64_t seed;
+} efie_options;
+
+/* Per-level summary filled by efie_plan / efie_level_info. */
+typedef struct {
+    int32_t level;           /* octree level (root 0) */
+    int32_t s, sb, sp, shat; /* splines, buffer splines, s' = s + 2 sb, stabilized count */
+    int32_t nfft;            /* FFT length per axis (>= 2 shat - 1) */
+    int64_t n_boxes;         /* occupied boxes */
+    int64_t n_far_pairs;     /* translated box pairs at this level */
+    int64_t n_offsets;       /* distinct translation offsets (kernel spectra) */
+    double h, delta, Delta;  /* box edge, knot spacing, interpolation-point spacing */
+} efie_level_info_t;
+
+typedef struct {
+    int64_t n_unknowns, n_triangles;
+    int32_t depth, top_level, n_levels, p;
+    double root_lo[3], root_edge;
+    int64_t near_nnz_A, near_nnz_V;
+    int64_t device_bytes;    /* estimated resident device bytes of the setup products */
+} efie_plan_info_t;
+
+typedef struct {
+    int32_t iterations;          /* matvecs spent on this right-hand side */
+    double true_rel_residual;    /* ||e - T x|| / ||e|| with the FP64 fast matvec */
+    int32_t converged;           /* 1 if true_rel_residual <= tol */
+    int32_t precond_fallback;    /* 1 if the learned preconditioner was dropped */
+} efie_solve_info;
+
+/* Host-only planning (no device work): octree, per-level spline parameters and
+ * interaction counts for the problem efie_setup would build (Sec. III-B, IV-C,
+ * IV-D, Table I).  levels_out may be NULL; otherwise it must hold
+ * max_levels entries.  Returns EFIE_EINVAL for a bad mesh or parameters (p not
+ * in 1..6, levels outside 1..depth+1, grid spacing so small that the buffer
+ * splines close the gap between far interpolation domains). */
+int efie_plan(const efie_mesh *mesh, double wavenumber, int spline_degree,
+              double grid_spacing, int levels, const efie_options *opt,
+              efie_plan_info_t *info, efie_level_info_t *levels_out, int max_levels);
+
+/* Host-only: the per-level dense matrices of the far pipeline, row-major FP64.
+ *   P[level]   (shat x sp)   = B_stab^{-1} S (Sec. V-B)
+ *   CL, CR     (sp_parent x sp_child) interlevel transfers into level-1 (Sec. IV-B)
+ * `which`: 0 = P, 1 = C^L, 2 = C^R.  `out` must hold rows*cols doubles; rows
+ * and cols are returned.  For C^L/C^R, `level` is the child level. */
+int efie_plan_matrix(const efie_mesh *mesh, double wavenumber, int spline_degree,
+                     double grid_spacing, int levels, const efie_options *opt,
+                     int level, int which, double *out, int64_t out_len,
+                     int32_t *rows, int32_t *cols);
+
+/* Build every setup product on the current device: geometry, octree,
+ * transfers, projectors, exact moments (Q10), kernel spectra per level and
+ * offset, and the FP64 near field (Sec. VI-A: RWG pairs for A and triangle
+ * pairs for V, each in adjacent leaf boxes).  opt may be NULL (defaults).
+ * On success *out owns all device memory until efie_destroy. */
+int efie_setup(const efie_mesh *mesh, double wavenumber, int spline_degree,
+               double grid_spacing, int levels, const efie_options *opt,
+               efie_handle **out);
+
+int efie_num_unknowns(const efie_handle *h, int64_t *n);
+int efie_plan_info(const efie_handle *h, efie_plan_info_t *info);
+
+/* Host arrays filled per unknown: edge_vertices [N][2] (lower, higher) and
+ * tri_pm [N][2] (c+, c-). Either may be NULL. */
+int efie_rwg_edges(const efie_handle *h, int32_t *edge_vertices, int32_t *tri_pm);
+
+/* Plane-wave right-hand sides [e^i]_m = int f_m . pol_r exp(-jk khat_r . x) dS
+ * (Sec. II), FP64.  khat, pol: host [n_rhs][3]; rhs: device c128 [n_rhs][N]. */
+int efie_rhs_planewave(efie_handle *h, int n_rhs, const double *khat, const double *pol,
+                       void *rhs, void *stream);
+
+/* y = T x for n_rhs vectors (device c128 [n_rhs][N]; x and y must not alias).
+ * Uses the handle's precision.  Steps a1-a10: charges, anterpolation, upward
+ * transfers, stabilized FFT translations, downward transfers, interpolation,
+ * near field. */
+int efie_matvec(efie_handle *h, const void *x, void *y, int n_rhs, void *stream);
+
+/* Same product computed in FP64 regardless of the handle's precision (the
+ * plain FP64 form used for true residuals).  Needs FP64 setup products, which
+ * EFIE_MIXED handles keep alongside the FP32 ones. */
+int efie_matvec_fp64(efie_handle *h, const void *x, void *y, int n_rhs, void *stream);
+
+/* Separate parts, y_A = A x and y_V = Sigma V Sigma^T x (far + near), so that
+ * T x = jk y_A + (jk)^-1 y_V.  Either output may be NULL. */
+int efie_matvec_parts(efie_handle *h, const void *x, void *yA, void *yV, int n_rhs,
+                      void *stream);
+
+/* Solve T x = rhs by GMRES(m) (FGMRES with the learned preconditioner), x0 = 0,
+ * FP64 CGS2 Arnoldi; success when the true relative residual, recomputed with
+ * the FP64 fast matvec, is <= tol.  rhs, x: device c128 [n_rhs][N]; info: host
+ * array of n_rhs entries or NULL.  Returns EFIE_NOT_CONVERGED if any rhs did not
+ * reach tol within max_iters (x then holds the best iterate). */
+int efie_solve(efie_handle *h, const void *rhs, void *x, int n_rhs, double tol,
+               efie_solve_info *info, void *stream);
+
+int efie_destroy(efie_handle *h);
+
+/* Message of the last error of h, or of the last failed setup/plan of this
+ * thread when h is NULL.  Never NULL; valid until the next call. */
+const char *efie_last_error(const efie_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EFIE_GB300_H */

@@ -1,0 +1,243 @@
+"""GB300-native stabilized multilevel B-spline fast EFIE (Python binding).
+
+A thin ctypes layer over the C ABI declared in include/efie.h.  It only
+marshals arguments: device vectors are torch tensors (complex128, CUDA) whose
+data pointers and current CUDA stream are passed to the library, and every step
+of the computation runs in the library's CUDA kernels.  Loading fails loudly if
+the shared library has not been built (see ``build.py``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+__all__ = ["load_library", "Options", "EFIE", "plan", "plan_matrix", "EfieError",
+           "EFIE_FP64", "EFIE_MIXED", "EFIE_PRECOND_NONE", "EFIE_PRECOND_LEARNED",
+           "EXPORTED_SYMBOLS"]
+
+EFIE_OK, EFIE_EINVAL, EFIE_ENOMEM, EFIE_ECUDA, EFIE_ETIMEOUT, EFIE_NOT_CONVERGED = 0, -1, -2, -3, -4, 1
+EFIE_FP64, EFIE_MIXED = 0, 1
+EFIE_PRECOND_NONE, EFIE_PRECOND_LEARNED = 0, 1
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libefie_gb300.so")
+
+EXPORTED_SYMBOLS = [
+    "efie_plan", "efie_plan_matrix", "efie_setup", "efie_num_unknowns", "efie_plan_info",
+    "efie_rwg_edges", "efie_rhs_planewave", "efie_matvec", "efie_matvec_fp64",
+    "efie_matvec_parts", "efie_solve", "efie_destroy", "efie_last_error",
+]
+
+
+class EfieError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+class _Mesh(ctypes.Structure):
+    _fields_ = [("n_vertices", ctypes.c_int64), ("xyz", ctypes.POINTER(ctypes.c_double)),
+                ("n_triangles", ctypes.c_int64), ("tri", ctypes.POINTER(ctypes.c_int32))]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("n_splines", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("gmres_restart", ctypes.c_int32), ("max_iters", ctypes.c_int32),
+                ("precond", ctypes.c_int32), ("rhs_chunk", ctypes.c_int32),
+                ("weights_path", ctypes.c_char_p), ("device_mem_limit", ctypes.c_int64),
+                ("seed", ctypes.c_uint64)]
+
+
+class LevelInfo(ctypes.Structure):
+    _fields_ = [("level", ctypes.c_int32), ("s", ctypes.c_int32), ("sb", ctypes.c_int32),
+                ("sp", ctypes.c_int32), ("shat", ctypes.c_int32), ("nfft", ctypes.c_int32),
+                ("n_boxes", ctypes.c_int64), ("n_far_pairs", ctypes.c_int64),
+                ("n_offsets", ctypes.c_int64), ("h", ctypes.c_double), ("delta", ctypes.c_double),
+                ("Delta", ctypes.c_double)]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("n_unknowns", ctypes.c_int64), ("n_triangles", ctypes.c_int64),
+                ("depth", ctypes.c_int32), ("top_level", ctypes.c_int32),
+                ("n_levels", ctypes.c_int32), ("p", ctypes.c_int32),
+                ("root_lo", ctypes.c_double * 3), ("root_edge", ctypes.c_double),
+                ("near_nnz_A", ctypes.c_int64), ("near_nnz_V", ctypes.c_int64),
+                ("device_bytes", ctypes.c_int64)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("true_rel_residual", ctypes.c_double),
+                ("converged", ctypes.c_int32), ("precond_fallback", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"CUDA library not built: {path} (run paper_2606_13482_gb300/build.py)")
+    lib = ctypes.CDLL(path)
+    P, I32, I64, D, VP = ctypes.POINTER, ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
+    lib.efie_plan.argtypes = [P(_Mesh), D, ctypes.c_int, D, ctypes.c_int, P(Options), P(PlanInfo),
+                              P(LevelInfo), ctypes.c_int]
+    lib.efie_plan_matrix.argtypes = [P(_Mesh), D, ctypes.c_int, D, ctypes.c_int, P(Options), ctypes.c_int,
+                                     ctypes.c_int, P(D), I64, P(I32), P(I32)]
+    lib.efie_setup.argtypes = [P(_Mesh), D, ctypes.c_int, D, ctypes.c_int, P(Options), P(VP)]
+    lib.efie_num_unknowns.argtypes = [VP, P(I64)]
+    lib.efie_plan_info.argtypes = [VP, P(PlanInfo)]
+    lib.efie_rwg_edges.argtypes = [VP, P(I32), P(I32)]
+    lib.efie_rhs_planewave.argtypes = [VP, ctypes.c_int, P(D), P(D), VP, VP]
+    lib.efie_matvec.argtypes = [VP, VP, VP, ctypes.c_int, VP]
+    lib.efie_matvec_fp64.argtypes = [VP, VP, VP, ctypes.c_int, VP]
+    lib.efie_matvec_parts.argtypes = [VP, VP, VP, VP, ctypes.c_int, VP]
+    lib.efie_solve.argtypes = [VP, VP, VP, ctypes.c_int, D, P(SolveInfo), VP]
+    lib.efie_destroy.argtypes = [VP]
+    lib.efie_last_error.argtypes = [VP]
+    lib.efie_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _mesh(V, T):
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    T = np.ascontiguousarray(T, dtype=np.int32)
+    m = _Mesh(V.shape[0], V.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), T.shape[0],
+              T.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+    return m, (V, T)
+
+
+def _check(lib, rc, h=None):
+    if rc < 0:
+        raise EfieError(rc, lib.efie_last_error(h).decode())
+    return rc
+
+
+def plan(V, T, k, p, grid_spacing, levels, options: Options | None = None):
+    """Host-only planning: (plan info dict, list of per-level dicts)."""
+    lib = load_library()
+    m, keep = _mesh(V, T)
+    info = PlanInfo()
+    lv = (LevelInfo * 32)()
+    _check(lib, lib.efie_plan(ctypes.byref(m), k, p, grid_spacing, levels,
+                              ctypes.byref(options) if options else None, ctypes.byref(info), lv, 32))
+    d = {f: getattr(info, f) for f, _ in PlanInfo._fields_}
+    d["root_lo"] = list(info.root_lo)
+    levels_out = [{f: getattr(lv[i], f) for f, _ in LevelInfo._fields_} for i in range(info.n_levels)]
+    return d, levels_out
+
+
+def plan_matrix(V, T, k, p, grid_spacing, levels, level, which, options: Options | None = None):
+    lib = load_library()
+    m, keep = _mesh(V, T)
+    r, c = ctypes.c_int32(), ctypes.c_int32()
+    _check(lib, lib.efie_plan_matrix(ctypes.byref(m), k, p, grid_spacing, levels,
+                                     ctypes.byref(options) if options else None, level, which, None, 0,
+                                     ctypes.byref(r), ctypes.byref(c)))
+    out = np.zeros(r.value * c.value)
+    _check(lib, lib.efie_plan_matrix(ctypes.byref(m), k, p, grid_spacing, levels,
+                                     ctypes.byref(options) if options else None, level, which,
+                                     out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), out.size,
+                                     None, None))
+    return out.reshape(r.value, c.value)
+
+
+class EFIE:
+    """Handle to a set-up problem on the current CUDA device."""
+
+    def __init__(self, V, T, k, p, grid_spacing, levels, precision=EFIE_FP64, **opts):
+        import torch  # noqa: F401  (device memory and streams)
+        self.lib = load_library()
+        o = Options()
+        o.precision = precision
+        for key, val in opts.items():
+            setattr(o, key, val)
+        self.options = o
+        m, keep = _mesh(V, T)
+        h = ctypes.c_void_p()
+        _check(self.lib, self.lib.efie_setup(ctypes.byref(m), k, p, grid_spacing, levels, ctypes.byref(o),
+                                             ctypes.byref(h)))
+        self.h = h
+        n = ctypes.c_int64()
+        self.lib.efie_num_unknowns(self.h, ctypes.byref(n))
+        self.N = n.value
+        self.k = k
+
+    def _stream(self):
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+    def _vec(self, x):
+        import torch
+        if x.dtype != torch.complex128 or not x.is_cuda or not x.is_contiguous():
+            raise ValueError("expected a contiguous complex128 CUDA tensor")
+        if x.shape[-1] != self.N:
+            raise ValueError("last dimension must equal the number of unknowns")
+        return ctypes.c_void_p(x.data_ptr())
+
+    def info(self):
+        i = PlanInfo()
+        _check(self.lib, self.lib.efie_plan_info(self.h, ctypes.byref(i)), self.h)
+        return {f: getattr(i, f) for f, _ in PlanInfo._fields_}
+
+    def rwg_edges(self):
+        e = np.zeros((self.N, 2), dtype=np.int32)
+        t = np.zeros((self.N, 2), dtype=np.int32)
+        _check(self.lib, self.lib.efie_rwg_edges(self.h, e.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                                 t.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))), self.h)
+        return e, t
+
+    def rhs_planewave(self, khat, pol):
+        import torch
+        khat = np.ascontiguousarray(np.atleast_2d(khat), dtype=np.float64)
+        pol = np.ascontiguousarray(np.atleast_2d(pol), dtype=np.float64)
+        out = torch.empty((khat.shape[0], self.N), dtype=torch.complex128, device="cuda")
+        _check(self.lib, self.lib.efie_rhs_planewave(
+            self.h, khat.shape[0], khat.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+            pol.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.c_void_p(out.data_ptr()),
+            self._stream()), self.h)
+        return out
+
+    def matvec(self, x, y=None, fp64=False):
+        import torch
+        x2 = x if x.dim() == 2 else x.unsqueeze(0)
+        if y is None:
+            y = torch.empty_like(x2)
+        fn = self.lib.efie_matvec_fp64 if fp64 else self.lib.efie_matvec
+        _check(self.lib, fn(self.h, self._vec(x2), self._vec(y), x2.shape[0], self._stream()), self.h)
+        return y if x.dim() == 2 else y[0]
+
+    def matvec_parts(self, x):
+        import torch
+        x2 = x if x.dim() == 2 else x.unsqueeze(0)
+        yA = torch.empty_like(x2)
+        yV = torch.empty_like(x2)
+        _check(self.lib, self.lib.efie_matvec_parts(self.h, self._vec(x2), self._vec(yA), self._vec(yV),
+                                                    x2.shape[0], self._stream()), self.h)
+        return (yA, yV) if x.dim() == 2 else (yA[0], yV[0])
+
+    def solve(self, rhs, tol=1e-6, x=None):
+        import torch
+        r2 = rhs if rhs.dim() == 2 else rhs.unsqueeze(0)
+        if x is None:
+            x = torch.empty_like(r2)
+        infos = (SolveInfo * r2.shape[0])()
+        rc = _check(self.lib, self.lib.efie_solve(self.h, self._vec(r2), self._vec(x), r2.shape[0], tol, infos,
+                                                  self._stream()), self.h)
+        out = [{f: getattr(i, f) for f, _ in SolveInfo._fields_} for i in infos]
+        return (x if rhs.dim() == 2 else x[0]), out, rc
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.efie_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,992 @@
+// C ABI of the GB300 fast EFIE library: setup orchestration, the matvec
+// pipeline (steps a1-a10) and the batched GMRES / FGMRES driver.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/efie.h"
+#include "common.cuh"
+#include "device_api.cuh"
+#include "plan.hpp"
+
+namespace efie {
+int upload_rhs_rule(const double* q6);
+}
+
+using namespace efie;
+
+namespace {
+
+thread_local std::string g_last_error = "";
+
+void cuda_check(cudaError_t e, const char* what) {
+  if (e != cudaSuccess)
+    throw EfieError{e == cudaErrorMemoryAllocation ? EFIE_ENOMEM : EFIE_ECUDA,
+                    std::string(what) + ": " + cudaGetErrorString(e)};
+}
+
+// device allocation tracker
+struct DevMem {
+  std::vector<void*> ptrs;
+  int64_t bytes = 0, limit = 0;
+  template <typename T>
+  T* alloc(int64_t n) {
+    if (n <= 0) n = 1;
+    int64_t b = n * (int64_t)sizeof(T);
+    if (limit > 0 && bytes + b > limit)
+      throw EfieError{EFIE_ENOMEM, "device_mem_limit exceeded (" + std::to_string(bytes + b) + " bytes)"};
+    void* p = nullptr;
+    cuda_check(cudaMalloc(&p, (size_t)b), "cudaMalloc");
+    ptrs.push_back(p);
+    bytes += b;
+    return (T*)p;
+  }
+  template <typename T>
+  T* upload(const std::vector<T>& v) {
+    T* p = alloc<T>((int64_t)v.size());
+    if (!v.empty()) cuda_check(cudaMemcpy(p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice), "upload");
+    return p;
+  }
+  void release(void* p) {
+    for (auto& q : ptrs)
+      if (q == p) {
+        cudaFree(q);
+        q = nullptr;
+      }
+  }
+  ~DevMem() {
+    for (void* p : ptrs)
+      if (p) cudaFree(p);
+  }
+};
+
+template <typename R>
+struct FarSet {
+  bool built = false;
+  R *mr = nullptr, *mt = nullptr;
+  struct Lev {
+    cpx_t<R>* Mf = nullptr;
+    cpx_t<R>* Mb = nullptr;
+    R *CL = nullptr, *CR = nullptr, *CLt = nullptr, *CRt = nullptr;
+    cpx_t<R>* Kh = nullptr;
+  };
+  std::vector<Lev> lv;
+  int Rc = 0;
+  std::vector<cpx_t<R>*> q, r;
+  cpx_t<R>*tmp1 = nullptr, *tmp2 = nullptr, *Qh = nullptr, *Rh = nullptr;
+};
+
+struct LevDev {
+  int64_t B = 0;
+  int64_t* il_ptr = nullptr;
+  int32_t* il_src = nullptr;
+  int32_t* il_off = nullptr;
+  int32_t* offsets = nullptr;
+  int64_t* parent = nullptr;
+  int8_t* bits = nullptr;
+  int64_t* child_ptr = nullptr;
+  int64_t nfar = 0, O = 0;
+};
+
+std::complex<double> jk_of(double k) { return std::complex<double>(0.0, k); }
+
+}  // namespace
+
+struct efie_handle {
+  Plan plan;
+  efie_options opt{};
+  int precision = EFIE_FP64;
+  std::string err;
+  int device = 0;
+  DevMem mem;
+  // geometry
+  double* dV = nullptr;
+  int32_t* dT = nullptr;
+  double* darea = nullptr;
+  int32_t* dtri_pm = nullptr;
+  int32_t* dfree_pm = nullptr;
+  // orders
+  int32_t *d_rwg_perm = nullptr, *d_rwg_box = nullptr, *d_tri_box = nullptr, *d_rwg_tri_sorted = nullptr;
+  int64_t *d_box_rwg_ptr = nullptr, *d_box_tri_ptr = nullptr;
+  int32_t* d_tri_rwg = nullptr;
+  int8_t* d_tri_sgn = nullptr;
+  // moments structure (shared by precisions)
+  int32_t *mr_base = nullptr, *mr_ext = nullptr, *mt_base = nullptr, *mt_ext = nullptr;
+  int64_t *mr_off = nullptr, *mt_off = nullptr;
+  // near
+  NearDev nd{};
+  int64_t *d_near_ptr = nullptr, *d_blkA_off = nullptr, *d_blkV_off = nullptr;
+  int32_t* d_near_src = nullptr;
+  // far
+  std::vector<LevDev> lev;
+  FarSet<double> f64;
+  FarSet<float> f32;
+  // work vectors (FP64, sorted)
+  int Rw = 0;
+  double2 *xs = nullptr, *rho = nullptr, *yA = nullptr, *w = nullptr;
+};
+
+namespace {
+
+void set_err(efie_handle* h, const EfieError& e) {
+  if (h) h->err = e.msg;
+  g_last_error = e.msg;
+}
+
+efie_options defaults(const efie_options* o) {
+  efie_options d{};
+  if (o) d = *o;
+  if (d.gmres_restart <= 0) d.gmres_restart = 100;
+  if (d.max_iters <= 0) d.max_iters = 1000;
+  if (d.precision != EFIE_MIXED) d.precision = EFIE_FP64;
+  return d;
+}
+
+void check_mesh(const efie_mesh* mesh) {
+  if (!mesh || !mesh->xyz || !mesh->tri || mesh->n_vertices < 4 || mesh->n_triangles < 4)
+    throw EfieError{EFIE_EINVAL, "invalid mesh"};
+}
+
+void collapsed_rule(int n, std::vector<double>& out) {
+  std::vector<double> x, w;
+  gauss_legendre01(n, x, w);
+  out.assign(3 * n * n, 0.0);
+  int q = 0;
+  for (int a = 0; a < n; ++a)
+    for (int b = 0; b < n; ++b, ++q) {
+      out[q] = x[a];
+      out[n * n + q] = x[b] * (1.0 - x[a]);
+      out[2 * n * n + q] = w[a] * w[b] * (1.0 - x[a]);
+    }
+}
+
+// ------------------------------------------------------------- far setup
+template <typename R>
+void build_far(efie_handle* h, FarSet<R>& F, cudaStream_t s) {
+  Plan& P = h->plan;
+  DevMem& M = h->mem;
+  // moments
+  std::vector<R> mr(P.mom_rwg.data.begin(), P.mom_rwg.data.end());
+  std::vector<R> mt(P.mom_tri.data.begin(), P.mom_tri.data.end());
+  F.mr = M.upload(mr);
+  F.mt = M.upload(mt);
+  F.lv.assign(P.lv.size(), {});
+  for (int ell = P.D; ell >= P.top; --ell) {
+    Level& L = P.L(ell);
+    auto& FL = F.lv[ell - P.top];
+    std::vector<cpx_t<R>> mf(L.Mf.size()), mb(L.Mb.size());
+    for (size_t i = 0; i < mf.size(); ++i) mf[i] = mk<R>((R)L.Mf[i].real(), (R)L.Mf[i].imag());
+    for (size_t i = 0; i < mb.size(); ++i) mb[i] = mk<R>((R)L.Mb[i].real(), (R)L.Mb[i].imag());
+    FL.Mf = M.upload(mf);
+    FL.Mb = M.upload(mb);
+    if (ell > P.top) {
+      const Level& U = P.L(ell - 1);
+      int sp = L.sp, spp = U.sp;
+      std::vector<R> cl(L.CL.begin(), L.CL.end()), cr(L.CR.begin(), L.CR.end());
+      std::vector<R> clt((size_t)sp * spp), crt((size_t)sp * spp);
+      for (int j = 0; j < spp; ++j)
+        for (int i = 0; i < sp; ++i) {
+          clt[(size_t)i * spp + j] = (R)L.CL[(size_t)j * sp + i];
+          crt[(size_t)i * spp + j] = (R)L.CR[(size_t)j * sp + i];
+        }
+      FL.CL = M.upload(cl);
+      FL.CR = M.upload(cr);
+      FL.CLt = M.upload(clt);
+      FL.CRt = M.upload(crt);
+    }
+  }
+  F.built = true;
+}
+
+// kernel spectra K^_o for every level (FP64), converted to R
+template <typename R>
+void build_spectra(efie_handle* h, FarSet<R>& F, const std::vector<double2*>& K64, cudaStream_t s) {
+  Plan& P = h->plan;
+  for (int ell = P.D; ell >= P.top; --ell) {
+    const LevDev& LD = h->lev[ell - P.top];
+    const Level& L = P.L(ell);
+    int64_t n3 = (int64_t)L.nfft * L.nfft * L.nfft;
+    int64_t tot = n3 * std::max<int64_t>(LD.O, 1);
+    if (sizeof(R) == 8) {
+      F.lv[ell - P.top].Kh = (cpx_t<R>*)K64[ell - P.top];
+    } else {
+      F.lv[ell - P.top].Kh = h->mem.alloc<cpx_t<R>>(tot);
+      launch_convert<R>(K64[ell - P.top], F.lv[ell - P.top].Kh, LD.O * n3, s);
+    }
+  }
+}
+
+std::vector<double2*> build_kernel_spectra64(efie_handle* h, cudaStream_t s) {
+  Plan& P = h->plan;
+  std::vector<double2*> out(P.lv.size(), nullptr);
+  for (int ell = P.D; ell >= P.top; --ell) {
+    const LevDev& LD = h->lev[ell - P.top];
+    const Level& L = P.L(ell);
+    const int n = L.nfft;
+    const int64_t n3 = (int64_t)n * n * n;
+    const int64_t O = LD.O;
+    double2* Kh = h->mem.alloc<double2>(n3 * std::max<int64_t>(O, 1));
+    out[ell - P.top] = Kh;
+    if (O == 0) continue;
+    double2* Fn = h->mem.alloc<double2>((int64_t)n * n);
+    std::vector<double2> fh((size_t)n * n);
+    for (size_t i = 0; i < fh.size(); ++i) fh[i] = make_double2(L.Fn[i].real(), L.Fn[i].imag());
+    cuda_check(cudaMemcpy(Fn, fh.data(), sizeof(double2) * fh.size(), cudaMemcpyHostToDevice), "Fn");
+    int64_t ob = std::max<int64_t>(1, std::min<int64_t>(O, (int64_t)(512LL << 20) / (n3 * 16)));
+    double2* a = h->mem.alloc<double2>(ob * n3);
+    double2* b = h->mem.alloc<double2>(ob * n3);
+    for (int64_t o0 = 0; o0 < O; o0 += ob) {
+      int64_t no = std::min(ob, O - o0);
+      launch_kernel_samples(a, LD.offsets, o0, no, n, L.shat, L.h, L.Delta, P.k, s);
+      // [o][i0][i1][i2] -> DFT along each axis; last pass writes frequency-major
+      View v0{n3, (int64_t)n * n, n, 1};
+      launch_mode<double>(a, v0, b, v0, no, 1, 0, n, n, n, n, Fn, Fn, true, nullptr, nullptr, false, s);
+      launch_mode<double>(b, v0, a, v0, no, 1, 1, n, n, n, n, Fn, Fn, true, nullptr, nullptr, false, s);
+      View vf{1, (int64_t)n * n * O, (int64_t)n * O, O};
+      launch_mode<double>(a, v0, Kh + o0, vf, no, 1, 2, n, n, n, n, Fn, Fn, true, nullptr, nullptr, false, s);
+    }
+    cuda_check(cudaStreamSynchronize(s), "kernel spectra");
+    h->mem.release(a);
+    h->mem.release(b);
+    h->mem.release(Fn);
+  }
+  return out;
+}
+
+template <typename R>
+void ensure_far_buffers(efie_handle* h, FarSet<R>& F, int Rc) {
+  if (F.Rc >= Rc) return;
+  Plan& P = h->plan;
+  for (auto* p : F.q) h->mem.release(p);
+  for (auto* p : F.r) h->mem.release(p);
+  for (void* p : {(void*)F.tmp1, (void*)F.tmp2, (void*)F.Qh, (void*)F.Rh})
+    if (p) h->mem.release(p);
+  const int64_t C = 4 * Rc;
+  F.q.assign(P.lv.size(), nullptr);
+  F.r.assign(P.lv.size(), nullptr);
+  int64_t tmax = 1, smax = 1;
+  for (int ell = P.D; ell >= P.top; --ell) {
+    const Level& L = P.L(ell);
+    const int64_t B = (int64_t)L.code.size();
+    const int64_t sp = L.sp, n = L.nfft;
+    F.q[ell - P.top] = h->mem.alloc<cpx_t<R>>(B * sp * sp * sp * C);
+    F.r[ell - P.top] = h->mem.alloc<cpx_t<R>>(B * sp * sp * sp * C);
+    // forward / inverse intermediates
+    tmax = std::max({tmax, B * n * sp * sp * C, B * n * n * sp * C, B * sp * n * n * C});
+    smax = std::max(smax, B * n * n * n * C);
+    if (ell > P.top) {
+      // upward and downward intermediates (child level ell, parent ell-1)
+      const int64_t spp = P.L(ell - 1).sp;
+      tmax = std::max({tmax, B * spp * sp * sp * C, B * spp * spp * sp * C, B * spp * spp * spp * C,
+                       B * sp * spp * spp * C, B * sp * sp * spp * C});
+    }
+  }
+  F.tmp1 = h->mem.alloc<cpx_t<R>>(tmax);
+  F.tmp2 = h->mem.alloc<cpx_t<R>>(tmax);
+  F.Qh = h->mem.alloc<cpx_t<R>>(smax);
+  F.Rh = h->mem.alloc<cpx_t<R>>(smax);
+  F.Rc = Rc;
+}
+
+void ensure_work(efie_handle* h, int Rw) {
+  if (h->Rw >= Rw) return;
+  const int64_t N = h->plan.g.N, Nt = h->plan.g.nt;
+  h->xs = h->mem.alloc<double2>(N * Rw);
+  h->yA = h->mem.alloc<double2>(N * Rw);
+  h->rho = h->mem.alloc<double2>(Nt * Rw);
+  h->w = h->mem.alloc<double2>(Nt * Rw);
+  h->Rw = Rw;
+}
+
+// ------------------------------------------------------------- far pipeline
+template <typename R>
+void far_chunk(efie_handle* h, FarSet<R>& F, int nr, cudaStream_t s) {
+  Plan& P = h->plan;
+  const int C = 4 * nr;
+  const int D = P.D, top = P.top;
+  const int64_t N = P.g.N, Nt = P.g.nt;
+  // a2: anterpolation into the leaf grids
+  {
+    const Level& L = P.L(D);
+    launch_anterp<R>(F.mr, h->mr_base, h->mr_ext, h->mr_off, F.mt, h->mt_base, h->mt_ext, h->mt_off,
+                     h->d_box_rwg_ptr, h->d_box_tri_ptr, (int64_t)L.code.size(), h->xs, N, h->rho, Nt, nr,
+                     F.q[D - top], L.sp, s);
+  }
+  // a3: upward transfers
+  for (int ell = D; ell > top; --ell) {
+    const Level& L = P.L(ell);
+    const Level& U = P.L(ell - 1);
+    const LevDev& LD = h->lev[ell - top];
+    auto& FL = F.lv[ell - top];
+    int64_t B = (int64_t)L.code.size();
+    int sp = L.sp, spp = U.sp;
+    View vq{(int64_t)sp * sp * sp * C, (int64_t)sp * sp * C, (int64_t)sp * C, C};
+    View v1{(int64_t)spp * sp * sp * C, (int64_t)sp * sp * C, (int64_t)sp * C, C};
+    View v2{(int64_t)spp * spp * sp * C, (int64_t)spp * sp * C, (int64_t)sp * C, C};
+    View v3{(int64_t)spp * spp * spp * C, (int64_t)spp * spp * C, (int64_t)spp * C, C};
+    launch_mode<R>(F.q[ell - top], vq, F.tmp1, v1, B, C, 0, sp, spp, sp, sp, FL.CL, FL.CR, false, LD.bits,
+                   nullptr, false, s);
+    launch_mode<R>(F.tmp1, v1, F.tmp2, v2, B, C, 1, sp, spp, spp, sp, FL.CL, FL.CR, false, LD.bits, nullptr,
+                   false, s);
+    launch_mode<R>(F.tmp2, v2, F.tmp1, v3, B, C, 2, sp, spp, spp, spp, FL.CL, FL.CR, false, LD.bits,
+                   nullptr, false, s);
+    launch_reduce_children<R>(F.tmp1, F.q[ell - 1 - top], h->lev[ell - 1 - top].child_ptr,
+                              (int64_t)U.code.size(), (int64_t)spp * spp * spp * C, s);
+  }
+  // a4-a7: stabilized FFT translations per level
+  for (int ell = D; ell >= top; --ell) {
+    const Level& L = P.L(ell);
+    const LevDev& LD = h->lev[ell - top];
+    auto& FL = F.lv[ell - top];
+    int64_t B = (int64_t)L.code.size();
+    int sp = L.sp, n = L.nfft;
+    int64_t n3 = (int64_t)n * n * n;
+    if (LD.nfar == 0) {
+      cuda_check(cudaMemsetAsync(F.r[ell - top], 0, sizeof(cpx_t<R>) * B * sp * sp * sp * C, s), "memset r");
+      continue;
+    }
+    View vq{(int64_t)sp * sp * sp * C, (int64_t)sp * sp * C, (int64_t)sp * C, C};
+    View a1{(int64_t)n * sp * sp * C, (int64_t)sp * sp * C, (int64_t)sp * C, C};
+    View a2{(int64_t)n * n * sp * C, (int64_t)n * sp * C, (int64_t)sp * C, C};
+    View vf{C, (int64_t)n * n * B * C, (int64_t)n * B * C, B * C};
+    launch_mode<R>(F.q[ell - top], vq, F.tmp1, a1, B, C, 0, sp, n, sp, sp, FL.Mf, FL.Mf, true, nullptr,
+                   nullptr, false, s);
+    launch_mode<R>(F.tmp1, a1, F.tmp2, a2, B, C, 1, sp, n, n, sp, FL.Mf, FL.Mf, true, nullptr, nullptr,
+                   false, s);
+    launch_mode<R>(F.tmp2, a2, F.Qh, vf, B, C, 2, sp, n, n, n, FL.Mf, FL.Mf, true, nullptr, nullptr, false,
+                   s);
+    launch_mac<R>(F.Qh, F.Rh, FL.Kh, B, C, LD.O, n3, LD.il_ptr, LD.il_src, LD.il_off, s);
+    View b1{(int64_t)sp * n * n * C, (int64_t)n * n * C, (int64_t)n * C, C};
+    View b2{(int64_t)sp * sp * n * C, (int64_t)sp * n * C, (int64_t)n * C, C};
+    launch_mode<R>(F.Rh, vf, F.tmp1, b1, B, C, 0, n, sp, n, n, FL.Mb, FL.Mb, true, nullptr, nullptr, false,
+                   s);
+    launch_mode<R>(F.tmp1, b1, F.tmp2, b2, B, C, 1, n, sp, sp, n, FL.Mb, FL.Mb, true, nullptr, nullptr,
+                   false, s);
+    launch_mode<R>(F.tmp2, b2, F.r[ell - top], vq, B, C, 2, n, sp, sp, sp, FL.Mb, FL.Mb, true, nullptr,
+                   nullptr, false, s);
+  }
+  // a8: downward transfers r_c += C^T r_parent
+  for (int ell = top + 1; ell <= D; ++ell) {
+    const Level& L = P.L(ell);
+    const Level& U = P.L(ell - 1);
+    const LevDev& LD = h->lev[ell - top];
+    auto& FL = F.lv[ell - top];
+    int64_t B = (int64_t)L.code.size();
+    int sp = L.sp, spp = U.sp;
+    View vp{(int64_t)spp * spp * spp * C, (int64_t)spp * spp * C, (int64_t)spp * C, C};
+    View w1{(int64_t)sp * spp * spp * C, (int64_t)spp * spp * C, (int64_t)spp * C, C};
+    View w2{(int64_t)sp * sp * spp * C, (int64_t)sp * spp * C, (int64_t)spp * C, C};
+    View vq{(int64_t)sp * sp * sp * C, (int64_t)sp * sp * C, (int64_t)sp * C, C};
+    launch_mode<R>(F.r[ell - 1 - top], vp, F.tmp1, w1, B, C, 0, spp, sp, spp, spp, FL.CLt, FL.CRt, false,
+                   LD.bits, LD.parent, false, s);
+    launch_mode<R>(F.tmp1, w1, F.tmp2, w2, B, C, 1, spp, sp, sp, spp, FL.CLt, FL.CRt, false, LD.bits,
+                   nullptr, false, s);
+    launch_mode<R>(F.tmp2, w2, F.r[ell - top], vq, B, C, 2, spp, sp, sp, sp, FL.CLt, FL.CRt, false, LD.bits,
+                   nullptr, true, s);
+  }
+  // a9: interpolation
+  {
+    const Level& L = P.L(D);
+    launch_interp<R>(F.mr, h->mr_base, h->mr_ext, h->mr_off, h->d_rwg_box, N, F.mt, h->mt_base, h->mt_ext,
+                     h->mt_off, h->d_tri_box, Nt, F.r[D - top], L.sp, nr, h->yA, N, h->w, Nt, s);
+  }
+}
+
+// y = T x (or parts) for nr <= 8 right-hand sides; x, y canonical [nr][ldx]
+template <typename R>
+void matvec_chunk(efie_handle* h, FarSet<R>& F, const double2* x, int64_t ldx, int nr, double2* y,
+                  double2* yAo, double2* yVo, int64_t ldy, cudaStream_t s) {
+  Plan& P = h->plan;
+  const int64_t N = P.g.N, Nt = P.g.nt;
+  ensure_work(h, 8);
+  ensure_far_buffers(h, F, nr);
+  launch_permute_in(x, ldx, h->d_rwg_perm, N, nr, h->xs, s);
+  launch_charges(h->xs, N, h->d_tri_rwg, h->d_tri_sgn, Nt, nr, h->rho, Nt, s);  // a1
+  far_chunk<R>(h, F, nr, s);                                                     // a2-a9
+  // a10: near field, FP64
+  int64_t BD = (int64_t)P.L(P.D).code.size();
+  launch_near_spmv(h->nd.A, h->d_blkA_off, h->d_near_ptr, h->d_near_src, h->d_box_rwg_ptr, BD, h->xs,
+                   h->yA, N, nr, s);
+  launch_near_spmv(h->nd.Vn, h->d_blkV_off, h->d_near_ptr, h->d_near_src, h->d_box_tri_ptr, BD, h->rho,
+                   h->w, Nt, nr, s);
+  std::complex<double> cA = jk_of(P.k), cV = 1.0 / jk_of(P.k);
+  launch_combine(h->yA, N, h->w, Nt, h->d_rwg_perm, h->d_rwg_tri_sorted, N, nr,
+                 make_double2(cA.real(), cA.imag()), make_double2(cV.real(), cV.imag()), y, ldy, yAo, yVo,
+                 s);
+}
+
+void do_matvec(efie_handle* h, const double2* x, int64_t ldx, double2* y, double2* yA, double2* yV,
+               int64_t ldy, int n_rhs, bool force64, cudaStream_t s) {
+  // right-hand sides per far pass: at most 8; the FP64 pass of a mixed handle
+  // (true residuals) runs one at a time to bound its buffers
+  int Rc = h->opt.rhs_chunk > 0 ? std::min(h->opt.rhs_chunk, 8) : 8;
+  if (force64 && h->precision == EFIE_MIXED) Rc = 1;
+  Rc = std::min(Rc, n_rhs);
+  for (int r0 = 0; r0 < n_rhs; r0 += Rc) {
+    int nr = std::min(Rc, n_rhs - r0);
+    double2* yy = y ? y + (int64_t)r0 * ldy : nullptr;
+    double2* ya = yA ? yA + (int64_t)r0 * ldy : nullptr;
+    double2* yv = yV ? yV + (int64_t)r0 * ldy : nullptr;
+    if (h->precision == EFIE_MIXED && !force64)
+      matvec_chunk<float>(h, h->f32, x + (int64_t)r0 * ldx, ldx, nr, yy, ya, yv, ldy, s);
+    else
+      matvec_chunk<double>(h, h->f64, x + (int64_t)r0 * ldx, ldx, nr, yy, ya, yv, ldy, s);
+  }
+  cuda_check(cudaGetLastError(), "matvec launch");
+}
+
+// ------------------------------------------------------------- setup
+void setup_impl(efie_handle* h, const efie_mesh* mesh, double k, int p, double grid_spacing, int levels) {
+  check_mesh(mesh);
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0)
+    throw EfieError{EFIE_ECUDA, "no CUDA device"};
+  cuda_check(cudaGetDevice(&h->device), "cudaGetDevice");
+  h->mem.limit = h->opt.device_mem_limit;
+  Plan& P = h->plan;
+  build_plan(P, mesh->xyz, mesh->n_vertices, mesh->tri, mesh->n_triangles, k, p, grid_spacing, levels,
+             h->opt.n_splines, true);
+  DevMem& M = h->mem;
+  cudaStream_t s = 0;
+  // quadrature rules
+  {
+    std::vector<double> q3, q4, q6;
+    collapsed_rule(3, q3);
+    collapsed_rule(4, q4);
+    collapsed_rule(6, q6);
+    if (near_upload_rules(q3.data(), q4.data()) || upload_rhs_rule(q6.data()))
+      throw EfieError{EFIE_ECUDA, "constant upload failed"};
+  }
+  const Geometry& g = P.g;
+  const int64_t N = g.N, Nt = g.nt;
+  h->dV = M.upload(g.V);
+  h->dT = M.upload(g.T);
+  h->darea = M.upload(g.area);
+  h->dtri_pm = M.upload(g.tri_pm);
+  h->dfree_pm = M.upload(g.free_pm);
+  h->d_rwg_perm = M.upload(P.rwg_perm);
+  h->d_rwg_box = M.upload(P.rwg_box);
+  h->d_tri_box = M.upload(P.tri_box);
+  h->d_box_rwg_ptr = M.upload(P.box_rwg_ptr);
+  h->d_box_tri_ptr = M.upload(P.box_tri_ptr);
+  h->d_rwg_tri_sorted = M.upload(P.rwg_tri_sorted);
+  {
+    // per sorted triangle: its RWGs (sorted index) and signs
+    std::vector<int32_t> tr(3 * Nt, -1);
+    std::vector<int8_t> ts(3 * Nt, 0);
+    std::vector<int> cnt(Nt, 0);
+    for (int64_t i = 0; i < N; ++i)
+      for (int sd = 0; sd < 2; ++sd) {
+        int32_t t = P.rwg_tri_sorted[2 * i + sd];
+        if (cnt[t] >= 3) throw EfieError{EFIE_EINVAL, "triangle with more than 3 edges"};
+        tr[3 * t + cnt[t]] = (int32_t)i;
+        ts[3 * t + cnt[t]] = sd == 0 ? 1 : -1;
+        cnt[t]++;
+      }
+    h->d_tri_rwg = M.upload(tr);
+    h->d_tri_sgn = M.upload(ts);
+  }
+  h->mr_base = M.upload(P.mom_rwg.base);
+  h->mr_ext = M.upload(P.mom_rwg.ext);
+  h->mr_off = M.upload(P.mom_rwg.off);
+  h->mt_base = M.upload(P.mom_tri.base);
+  h->mt_ext = M.upload(P.mom_tri.ext);
+  h->mt_off = M.upload(P.mom_tri.off);
+  // levels
+  h->lev.assign(P.lv.size(), LevDev());
+  for (int ell = P.D; ell >= P.top; --ell) {
+    const Level& L = P.L(ell);
+    LevDev& LD = h->lev[ell - P.top];
+    LD.B = (int64_t)L.code.size();
+    LD.il_ptr = M.upload(L.il_ptr);
+    LD.il_src = M.upload(L.il_src);
+    LD.il_off = M.upload(L.il_off);
+    LD.offsets = M.upload(L.offsets);
+    LD.nfar = (int64_t)L.il_src.size();
+    LD.O = (int64_t)L.offsets.size() / 3;
+    LD.parent = M.upload(L.parent);
+    std::vector<int8_t> bits(3 * LD.B);
+    for (int64_t b = 0; b < LD.B; ++b)
+      for (int d = 0; d < 3; ++d) bits[3 * b + d] = (int8_t)(L.ijk[3 * b + d] & 1);
+    LD.bits = M.upload(bits);
+    if (ell < P.D) LD.child_ptr = M.upload(L.child_ptr);
+  }
+  // near field (FP64)
+  {
+    const Level& LD = P.L(P.D);
+    int64_t BD = (int64_t)LD.code.size();
+    h->d_near_ptr = M.upload(P.near_ptr);
+    h->d_near_src = M.upload(P.near_src);
+    h->d_blkA_off = M.upload(P.blkA_off);
+    h->d_blkV_off = M.upload(P.blkV_off);
+    std::vector<int32_t> tgt(P.near_src.size());
+    for (int64_t x = 0; x < BD; ++x)
+      for (int64_t j = P.near_ptr[x]; j < P.near_ptr[x + 1]; ++j) tgt[j] = (int32_t)x;
+    NearDev& nd = h->nd;
+    nd.V = h->dV;
+    nd.T = h->dT;
+    nd.area = h->darea;
+    nd.k = k;
+    nd.n_boxes = BD;
+    nd.n_blocks = (int64_t)P.near_src.size();
+    nd.near_ptr = h->d_near_ptr;
+    nd.near_src = h->d_near_src;
+    nd.blk_tgt = M.upload(tgt);
+    nd.blkA_off = h->d_blkA_off;
+    nd.blkV_off = h->d_blkV_off;
+    nd.box_rwg_ptr = h->d_box_rwg_ptr;
+    nd.box_tri_ptr = h->d_box_tri_ptr;
+    nd.tri_perm = M.upload(P.tri_perm);
+    nd.tset_ptr = M.upload(P.tset_ptr);
+    nd.tset = M.upload(P.tset);
+    nd.rwg_tl = M.upload(P.rwg_tl);
+    nd.rwg_loc = M.upload(P.rwg_loc);
+    nd.rwg_coef = M.upload(P.rwg_coef);
+    nd.A = M.alloc<double2>(P.nnzA);
+    nd.Vn = M.alloc<double2>(P.nnzV);
+    // A: triangle-pair scratch per batch of blocks
+    const int64_t nblk = nd.n_blocks;
+    const int64_t scr_cap = (int64_t)(1LL << 30) / (10 * 16);  // pairs per batch (~1 GiB)
+    double2* scratch = nullptr;
+    int64_t* d_scr_off = M.alloc<int64_t>(nblk + 1);
+    int64_t max_pairs = 1;
+    for (int64_t j = 0; j < nblk; ++j) {
+      int32_t x = tgt[j], y = P.near_src[j];
+      max_pairs = std::max(max_pairs, (P.tset_ptr[x + 1] - P.tset_ptr[x]) * (P.tset_ptr[y + 1] - P.tset_ptr[y]));
+    }
+    int64_t cap = std::max(scr_cap, max_pairs);
+    scratch = M.alloc<double2>(10 * cap);
+    int64_t j0 = 0;
+    std::vector<int64_t> scr_off;
+    while (j0 < nblk) {
+      scr_off.assign(1, 0);
+      int64_t j1 = j0;
+      while (j1 < nblk) {
+        int32_t x = tgt[j1], y = P.near_src[j1];
+        int64_t np = (P.tset_ptr[x + 1] - P.tset_ptr[x]) * (P.tset_ptr[y + 1] - P.tset_ptr[y]);
+        if (scr_off.back() + np > cap && j1 > j0) break;
+        scr_off.push_back(scr_off.back() + np);
+        ++j1;
+      }
+      cuda_check(cudaMemcpy(d_scr_off, scr_off.data(), sizeof(int64_t) * scr_off.size(), cudaMemcpyHostToDevice),
+                 "scr_off");
+      launch_near_pairs_A(nd, j0, j1 - j0, d_scr_off, scratch, scr_off.back(), s);
+      launch_near_combine_A(nd, j0, j1 - j0, d_scr_off, scratch, P.blkA_off[j0],
+                            P.blkA_off[j1] - P.blkA_off[j0], s);
+      cuda_check(cudaStreamSynchronize(s), "near A assembly");
+      j0 = j1;
+    }
+    M.release(scratch);
+    const int64_t vchunk = 1LL << 26;
+    for (int64_t e0 = 0; e0 < P.nnzV; e0 += vchunk) {
+      launch_near_V(nd, e0, std::min(vchunk, P.nnzV - e0), s);
+      cuda_check(cudaStreamSynchronize(s), "near V assembly");
+    }
+  }
+  // far products
+  build_far<double>(h, h->f64, s);
+  std::vector<double2*> K64 = build_kernel_spectra64(h, s);
+  build_spectra<double>(h, h->f64, K64, s);
+  if (h->precision == EFIE_MIXED) {
+    build_far<float>(h, h->f32, s);
+    build_spectra<float>(h, h->f32, K64, s);
+  }
+  cuda_check(cudaStreamSynchronize(s), "setup");
+}
+
+// ------------------------------------------------------------- GMRES
+struct Givens {
+  std::vector<std::complex<double>> H, cs, sn, g;
+};
+
+int solve_impl(efie_handle* h, const double2* b, double2* x, int n_rhs, double tol, efie_solve_info* info,
+               cudaStream_t s) {
+  if (!(tol > 0)) throw EfieError{EFIE_EINVAL, "tol must be positive"};
+  const int64_t N = h->plan.g.N;
+  const int m = h->opt.gmres_restart;
+  const int max_it = h->opt.max_iters;
+  // device workspace
+  double2* Vb = h->mem.alloc<double2>((int64_t)n_rhs * (m + 1) * N);
+  double2* wv = h->mem.alloc<double2>((int64_t)n_rhs * N);
+  double2* rv = h->mem.alloc<double2>((int64_t)n_rhs * N);
+  double2* dh = h->mem.alloc<double2>((int64_t)n_rhs * (m + 1));
+  double2* dh2 = h->mem.alloc<double2>((int64_t)n_rhs * (m + 1));
+  double* dn = h->mem.alloc<double>(n_rhs);
+  int* dact = h->mem.alloc<int>(n_rhs);
+  const int64_t ldr = (int64_t)(m + 1) * N;
+  std::vector<double> bnorm(n_rhs), nrm(n_rhs);
+  std::vector<int> its(n_rhs, 0), conv(n_rhs, 0), act(n_rhs, 1);
+  std::vector<std::complex<double>> hh((size_t)n_rhs * (m + 1)), hh2((size_t)n_rhs * (m + 1));
+  auto d2h = [&](std::vector<std::complex<double>>& dst, const double2* src, int64_t n) {
+    cuda_check(cudaMemcpyAsync(dst.data(), src, sizeof(double2) * n, cudaMemcpyDeviceToHost, s), "d2h");
+    cuda_check(cudaStreamSynchronize(s), "sync");
+  };
+  auto norms = [&](const double2* v, int64_t ld, std::vector<double>& out) {
+    launch_norms(v, ld, N, n_rhs, dn, s);
+    cuda_check(cudaMemcpyAsync(out.data(), dn, sizeof(double) * n_rhs, cudaMemcpyDeviceToHost, s), "d2h");
+    cuda_check(cudaStreamSynchronize(s), "sync");
+    for (auto& v2 : out) v2 = std::sqrt(v2);
+  };
+  cuda_check(cudaMemsetAsync(x, 0, sizeof(double2) * n_rhs * N, s), "x0");
+  cuda_check(cudaMemsetAsync(Vb, 0, sizeof(double2) * n_rhs * ldr, s), "basis");
+  norms(b, N, bnorm);
+  cuda_check(cudaMemcpyAsync(rv, b, sizeof(double2) * n_rhs * N, cudaMemcpyDeviceToDevice, s), "r0");
+  std::vector<double> beta(n_rhs);
+  for (int r = 0; r < n_rhs; ++r) {
+    beta[r] = bnorm[r];
+    if (bnorm[r] == 0) {
+      act[r] = 0;
+      conv[r] = 1;
+    }
+  }
+  std::vector<std::vector<std::complex<double>>> H(n_rhs), cs(n_rhs), sn(n_rhs), gg(n_rhs);
+  while (true) {
+    bool any = false;
+    for (int r = 0; r < n_rhs; ++r) {
+      if (act[r] && (beta[r] / bnorm[r] <= tol || its[r] >= max_it)) act[r] = 0;
+      any |= act[r] != 0;
+    }
+    if (!any) break;
+    cuda_check(cudaMemcpyAsync(dact, act.data(), sizeof(int) * n_rhs, cudaMemcpyHostToDevice, s), "act");
+    // V0 = r / beta
+    for (int r = 0; r < n_rhs; ++r) {
+      H[r].assign((size_t)(m + 1) * m, 0.0);
+      cs[r].assign(m, 0.0);
+      sn[r].assign(m, 0.0);
+      gg[r].assign(m + 1, 0.0);
+      gg[r][0] = beta[r];
+      hh[r] = act[r] ? 1.0 / beta[r] : 0.0;
+    }
+    for (int r = 0; r < n_rhs; ++r) cuda_check(cudaMemsetAsync(Vb + r * ldr, 0, sizeof(double2) * N, s), "v0");
+    cuda_check(cudaMemcpyAsync(dh, hh.data(), sizeof(double2) * n_rhs, cudaMemcpyHostToDevice, s), "h");
+    launch_multiaxpy(rv, N, 0, 1, dh, 1, Vb, ldr, N, n_rhs, dact, 1.0, s);
+    std::vector<int> kdim(n_rhs, 0), inner(n_rhs, 0);
+    for (int r = 0; r < n_rhs; ++r) inner[r] = act[r];
+    for (int k = 0; k < m; ++k) {
+      bool anyin = false;
+      for (int r = 0; r < n_rhs; ++r) anyin |= inner[r] != 0;
+      if (!anyin) break;
+      std::vector<int> ia(inner);
+      cuda_check(cudaMemcpyAsync(dact, ia.data(), sizeof(int) * n_rhs, cudaMemcpyHostToDevice, s), "act");
+      // w = T v_k (all rhs; inactive ones are ignored)
+      do_matvec(h, Vb + (int64_t)k * N, ldr, wv, nullptr, nullptr, N, n_rhs, false, s);
+      // CGS2
+      launch_multidot(Vb, ldr, N, k + 1, wv, N, N, n_rhs, dact, dh, s);
+      launch_multiaxpy(Vb, ldr, N, k + 1, dh, k + 1, wv, N, N, n_rhs, dact, -1.0, s);
+      launch_multidot(Vb, ldr, N, k + 1, wv, N, N, n_rhs, dact, dh2, s);
+      launch_multiaxpy(Vb, ldr, N, k + 1, dh2, k + 1, wv, N, N, n_rhs, dact, -1.0, s);
+      d2h(hh, dh, (int64_t)n_rhs * (k + 1));
+      d2h(hh2, dh2, (int64_t)n_rhs * (k + 1));
+      norms(wv, N, nrm);
+      std::vector<std::complex<double>> sc((size_t)n_rhs, 0.0);
+      for (int r = 0; r < n_rhs; ++r) {
+        if (!inner[r]) continue;
+        for (int i = 0; i <= k; ++i) H[r][(size_t)i * m + k] = hh[(size_t)r * (k + 1) + i] + hh2[(size_t)r * (k + 1) + i];
+        H[r][(size_t)(k + 1) * m + k] = nrm[r];
+        sc[r] = nrm[r] > 0 ? 1.0 / nrm[r] : 0.0;
+        // Givens: G = [[conj(c), conj(s)], [-s, c]], c = a/den, s = b/den
+        for (int i = 0; i < k; ++i) {
+          auto t = std::conj(cs[r][i]) * H[r][(size_t)i * m + k] + std::conj(sn[r][i]) * H[r][(size_t)(i + 1) * m + k];
+          H[r][(size_t)(i + 1) * m + k] = -sn[r][i] * H[r][(size_t)i * m + k] + cs[r][i] * H[r][(size_t)(i + 1) * m + k];
+          H[r][(size_t)i * m + k] = t;
+        }
+        auto a = H[r][(size_t)k * m + k], bb = H[r][(size_t)(k + 1) * m + k];
+        double den = std::sqrt(std::norm(a) + std::norm(bb));
+        cs[r][k] = den > 0 ? a / den : 1.0;
+        sn[r][k] = den > 0 ? bb / den : 0.0;
+        H[r][(size_t)k * m + k] = den;
+        H[r][(size_t)(k + 1) * m + k] = 0.0;
+        gg[r][k + 1] = -sn[r][k] * gg[r][k];
+        gg[r][k] = std::conj(cs[r][k]) * gg[r][k];
+        its[r]++;
+        kdim[r] = k + 1;
+        if (std::abs(gg[r][k + 1]) / bnorm[r] <= tol || its[r] >= max_it || nrm[r] == 0) inner[r] = 0;
+      }
+      // v_{k+1} = w / ||w||
+      std::vector<std::complex<double>> scv(sc);
+      cuda_check(cudaMemcpyAsync(dh, scv.data(), sizeof(double2) * n_rhs, cudaMemcpyHostToDevice, s), "h");
+      if (k + 1 <= m) {
+        for (int r = 0; r < n_rhs; ++r)
+          cuda_check(cudaMemsetAsync(Vb + r * ldr + (int64_t)(k + 1) * N, 0, sizeof(double2) * N, s), "vk");
+        launch_multiaxpy(wv, N, 0, 1, dh, 1, Vb + (int64_t)(k + 1) * N, ldr, N, n_rhs, dact, 1.0, s);
+      }
+    }
+    // x += V y (y from the triangular system)
+    std::vector<std::complex<double>> yv((size_t)n_rhs * m, 0.0);
+    for (int r = 0; r < n_rhs; ++r) {
+      int kd = kdim[r];
+      for (int i = kd - 1; i >= 0; --i) {
+        auto sacc = gg[r][i];
+        for (int j = i + 1; j < kd; ++j) sacc -= H[r][(size_t)i * m + j] * yv[(size_t)r * m + j];
+        yv[(size_t)r * m + i] = sacc / H[r][(size_t)i * m + i];
+      }
+    }
+    cuda_check(cudaMemcpyAsync(dh, yv.data(), sizeof(double2) * n_rhs * m, cudaMemcpyHostToDevice, s), "y");
+    cuda_check(cudaMemcpyAsync(dact, act.data(), sizeof(int) * n_rhs, cudaMemcpyHostToDevice, s), "act");
+    launch_multiaxpy(Vb, ldr, N, m, dh, m, x, N, N, n_rhs, dact, 1.0, s);
+    // restart residual r = b - T x (working precision)
+    do_matvec(h, x, N, wv, nullptr, nullptr, N, n_rhs, false, s);
+    launch_lincomb(b, wv, 1.0, -1.0, rv, (int64_t)n_rhs * N, s);
+    norms(rv, N, beta);
+  }
+  // true residual with the FP64 fast matvec
+  do_matvec(h, x, N, wv, nullptr, nullptr, N, n_rhs, true, s);
+  launch_lincomb(b, wv, 1.0, -1.0, rv, (int64_t)n_rhs * N, s);
+  norms(rv, N, nrm);
+  int ret = EFIE_OK;
+  for (int r = 0; r < n_rhs; ++r) {
+    double rel = bnorm[r] > 0 ? nrm[r] / bnorm[r] : 0.0;
+    conv[r] = rel <= tol;
+    if (!conv[r]) ret = EFIE_NOT_CONVERGED;
+    if (info) {
+      info[r].iterations = its[r];
+      info[r].true_rel_residual = rel;
+      info[r].converged = conv[r];
+      info[r].precond_fallback = 0;
+    }
+  }
+  for (void* p : {(void*)Vb, (void*)wv, (void*)rv, (void*)dh, (void*)dh2, (void*)dn, (void*)dact}) h->mem.release(p);
+  return ret;
+}
+
+template <typename F>
+int guarded(efie_handle* h, F&& f) {
+  try {
+    return f();
+  } catch (const EfieError& e) {
+    set_err(h, e);
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    set_err(h, EfieError{EFIE_ENOMEM, "host allocation failed"});
+    return EFIE_ENOMEM;
+  } catch (const std::exception& e) {
+    set_err(h, EfieError{EFIE_EINVAL, e.what()});
+    return EFIE_EINVAL;
+  }
+}
+
+void fill_plan_info(const Plan& P, efie_plan_info_t* info, efie_level_info_t* lv, int max_levels) {
+  if (info) {
+    std::memset(info, 0, sizeof(*info));
+    info->n_unknowns = P.g.N;
+    info->n_triangles = P.g.nt;
+    info->depth = P.D;
+    info->top_level = P.top;
+    info->n_levels = P.n_levels;
+    info->p = P.p;
+    for (int d = 0; d < 3; ++d) info->root_lo[d] = P.root_lo[d];
+    info->root_edge = P.root_edge;
+    info->near_nnz_A = P.nnzA;
+    info->near_nnz_V = P.nnzV;
+    int64_t bytes = (P.nnzA + P.nnzV) * 16;
+    for (const Level& L : P.lv) {
+      int64_t n3 = (int64_t)L.nfft * L.nfft * L.nfft;
+      bytes += n3 * (int64_t)(L.offsets.size() / 3) * 16;
+    }
+    info->device_bytes = bytes;
+  }
+  if (lv) {
+    int i = 0;
+    for (int ell = P.D; ell >= P.top && i < max_levels; --ell, ++i) {
+      const Level& L = P.L(ell);
+      efie_level_info_t& o = lv[i];
+      o.level = ell;
+      o.s = L.s;
+      o.sb = L.sb;
+      o.sp = L.sp;
+      o.shat = L.shat;
+      o.nfft = L.nfft;
+      o.n_boxes = (int64_t)L.code.size();
+      o.n_far_pairs = (int64_t)L.il_src.size();
+      o.n_offsets = (int64_t)L.offsets.size() / 3;
+      o.h = L.h;
+      o.delta = L.delta;
+      o.Delta = L.Delta;
+    }
+  }
+}
+
+}  // namespace
+
+// ================================================================= C ABI
+extern "C" {
+
+int efie_plan(const efie_mesh* mesh, double wavenumber, int spline_degree, double grid_spacing, int levels,
+              const efie_options* opt, efie_plan_info_t* info, efie_level_info_t* levels_out, int max_levels) {
+  return guarded(nullptr, [&] {
+    check_mesh(mesh);
+    efie_options o = defaults(opt);
+    Plan P;
+    build_plan(P, mesh->xyz, mesh->n_vertices, mesh->tri, mesh->n_triangles, wavenumber, spline_degree,
+               grid_spacing, levels, o.n_splines, false);
+    fill_plan_info(P, info, levels_out, max_levels);
+    return EFIE_OK;
+  });
+}
+
+int efie_plan_matrix(const efie_mesh* mesh, double wavenumber, int spline_degree, double grid_spacing,
+                     int levels, const efie_options* opt, int level, int which, double* out, int64_t out_len,
+                     int32_t* rows, int32_t* cols) {
+  return guarded(nullptr, [&] {
+    check_mesh(mesh);
+    efie_options o = defaults(opt);
+    Plan P;
+    build_plan(P, mesh->xyz, mesh->n_vertices, mesh->tri, mesh->n_triangles, wavenumber, spline_degree,
+               grid_spacing, levels, o.n_splines, false);
+    if (level < P.top || level > P.D) throw EfieError{EFIE_EINVAL, "level is not a grid level"};
+    const Level& L = P.L(level);
+    const std::vector<double>* M = nullptr;
+    int r = 0, c = 0;
+    if (which == 0) {
+      M = &L.P;
+      r = L.shat;
+      c = L.sp;
+    } else if (which == 1 || which == 2) {
+      if (level == P.top) throw EfieError{EFIE_EINVAL, "no transfer above the top grid level"};
+      M = which == 1 ? &L.CL : &L.CR;
+      r = P.L(level - 1).sp;
+      c = L.sp;
+    } else {
+      throw EfieError{EFIE_EINVAL, "which must be 0, 1 or 2"};
+    }
+    if (rows) *rows = r;
+    if (cols) *cols = c;
+    if (out) {
+      if (out_len < (int64_t)M->size()) throw EfieError{EFIE_EINVAL, "output buffer too small"};
+      std::memcpy(out, M->data(), sizeof(double) * M->size());
+    }
+    return EFIE_OK;
+  });
+}
+
+int efie_setup(const efie_mesh* mesh, double wavenumber, int spline_degree, double grid_spacing, int levels,
+               const efie_options* opt, efie_handle** out) {
+  if (!out) {
+    g_last_error = "out is NULL";
+    return EFIE_EINVAL;
+  }
+  *out = nullptr;
+  efie_handle* h = new (std::nothrow) efie_handle();
+  if (!h) {
+    g_last_error = "host allocation failed";
+    return EFIE_ENOMEM;
+  }
+  h->opt = defaults(opt);
+  h->precision = h->opt.precision;
+  int rc = guarded(h, [&] {
+    setup_impl(h, mesh, wavenumber, spline_degree, grid_spacing, levels);
+    return EFIE_OK;
+  });
+  if (rc != EFIE_OK) {
+    g_last_error = h->err;
+    delete h;
+    return rc;
+  }
+  *out = h;
+  return EFIE_OK;
+}
+
+int efie_num_unknowns(const efie_handle* h, int64_t* n) {
+  if (!h || !n) return EFIE_EINVAL;
+  *n = h->plan.g.N;
+  return EFIE_OK;
+}
+
+int efie_plan_info(const efie_handle* h, efie_plan_info_t* info) {
+  if (!h || !info) return EFIE_EINVAL;
+  fill_plan_info(h->plan, info, nullptr, 0);
+  info->device_bytes = h->mem.bytes;
+  return EFIE_OK;
+}
+
+int efie_rwg_edges(const efie_handle* h, int32_t* edge_vertices, int32_t* tri_pm) {
+  if (!h) return EFIE_EINVAL;
+  const Geometry& g = h->plan.g;
+  if (edge_vertices) std::memcpy(edge_vertices, g.edge.data(), sizeof(int32_t) * g.edge.size());
+  if (tri_pm) std::memcpy(tri_pm, g.tri_pm.data(), sizeof(int32_t) * g.tri_pm.size());
+  return EFIE_OK;
+}
+
+int efie_rhs_planewave(efie_handle* h, int n_rhs, const double* khat, const double* pol, void* rhs,
+                       void* stream) {
+  if (!h) return EFIE_EINVAL;
+  return guarded(h, [&] {
+    if (n_rhs < 0 || !khat || !pol || (!rhs && n_rhs > 0)) throw EfieError{EFIE_EINVAL, "bad arguments"};
+    if (n_rhs == 0) return EFIE_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    double* dk = h->mem.alloc<double>(3 * n_rhs);
+    double* dp = h->mem.alloc<double>(3 * n_rhs);
+    cuda_check(cudaMemcpyAsync(dk, khat, sizeof(double) * 3 * n_rhs, cudaMemcpyHostToDevice, s), "khat");
+    cuda_check(cudaMemcpyAsync(dp, pol, sizeof(double) * 3 * n_rhs, cudaMemcpyHostToDevice, s), "pol");
+    launch_rhs_planewave(h->dV, h->dT, h->darea, h->dtri_pm, h->dfree_pm, h->plan.g.N, h->plan.k, dk, dp, n_rhs,
+                         (double2*)rhs, h->plan.g.N, s);
+    cuda_check(cudaStreamSynchronize(s), "rhs");
+    h->mem.release(dk);
+    h->mem.release(dp);
+    return EFIE_OK;
+  });
+}
+
+int efie_matvec(efie_handle* h, const void* x, void* y, int n_rhs, void* stream) {
+  if (!h) return EFIE_EINVAL;
+  return guarded(h, [&] {
+    if (n_rhs < 0 || ((!x || !y) && n_rhs > 0)) throw EfieError{EFIE_EINVAL, "bad arguments"};
+    if (x == y && n_rhs > 0) throw EfieError{EFIE_EINVAL, "x and y must not alias"};
+    if (n_rhs == 0) return EFIE_OK;
+    do_matvec(h, (const double2*)x, h->plan.g.N, (double2*)y, nullptr, nullptr, h->plan.g.N, n_rhs, false,
+              (cudaStream_t)stream);
+    return EFIE_OK;
+  });
+}
+
+int efie_matvec_fp64(efie_handle* h, const void* x, void* y, int n_rhs, void* stream) {
+  if (!h) return EFIE_EINVAL;
+  return guarded(h, [&] {
+    if (n_rhs < 0 || ((!x || !y) && n_rhs > 0)) throw EfieError{EFIE_EINVAL, "bad arguments"};
+    if (x == y && n_rhs > 0) throw EfieError{EFIE_EINVAL, "x and y must not alias"};
+    if (n_rhs == 0) return EFIE_OK;
+    do_matvec(h, (const double2*)x, h->plan.g.N, (double2*)y, nullptr, nullptr, h->plan.g.N, n_rhs, true,
+              (cudaStream_t)stream);
+    return EFIE_OK;
+  });
+}
+
+int efie_matvec_parts(efie_handle* h, const void* x, void* yA, void* yV, int n_rhs, void* stream) {
+  if (!h) return EFIE_EINVAL;
+  return guarded(h, [&] {
+    if (n_rhs < 0 || (!x && n_rhs > 0)) throw EfieError{EFIE_EINVAL, "bad arguments"};
+    if (n_rhs == 0) return EFIE_OK;
+    do_matvec(h, (const double2*)x, h->plan.g.N, nullptr, (double2*)yA, (double2*)yV, h->plan.g.N, n_rhs,
+              false, (cudaStream_t)stream);
+    return EFIE_OK;
+  });
+}
+
+int efie_solve(efie_handle* h, const void* rhs, void* x, int n_rhs, double tol, efie_solve_info* info,
+               void* stream) {
+  if (!h) return EFIE_EINVAL;
+  return guarded(h, [&] {
+    if (n_rhs < 0 || ((!rhs || !x) && n_rhs > 0)) throw EfieError{EFIE_EINVAL, "bad arguments"};
+    if (n_rhs == 0) return EFIE_OK;
+    return solve_impl(h, (const double2*)rhs, (double2*)x, n_rhs, tol, info, (cudaStream_t)stream);
+  });
+}
+
+int efie_destroy(efie_handle* h) {
+  if (!h) return EFIE_EINVAL;
+  delete h;
+  return EFIE_OK;
+}
+
+const char* efie_last_error(const efie_handle* h) {
+  if (h) return h->err.c_str();
+  return g_last_error.c_str();
+}
+
+}  // extern "C"

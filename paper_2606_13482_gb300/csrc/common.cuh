@@ -1,0 +1,63 @@
+// Shared device helpers: complex arithmetic on interleaved (re, im) pairs.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace efie {
+
+template <typename R> struct C2;
+template <> struct C2<float> { using T = float2; };
+template <> struct C2<double> { using T = double2; };
+
+template <typename R> using cpx_t = typename C2<R>::T;
+
+template <typename R>
+__host__ __device__ __forceinline__ cpx_t<R> mk(R re, R im) {
+  cpx_t<R> z;
+  z.x = re;
+  z.y = im;
+  return z;
+}
+template <typename T>
+__host__ __device__ __forceinline__ T cadd(T a, T b) {
+  a.x += b.x;
+  a.y += b.y;
+  return a;
+}
+template <typename T>
+__host__ __device__ __forceinline__ T csub(T a, T b) {
+  a.x -= b.x;
+  a.y -= b.y;
+  return a;
+}
+template <typename T>
+__host__ __device__ __forceinline__ T cmul(T a, T b) {
+  T z;
+  z.x = a.x * b.x - a.y * b.y;
+  z.y = a.x * b.y + a.y * b.x;
+  return z;
+}
+// acc += a * b
+template <typename T>
+__host__ __device__ __forceinline__ void cfma(T& acc, T a, T b) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(a.y, b.x, acc.y);
+}
+__device__ __forceinline__ void cfma(float2& acc, float2 a, float2 b) {
+  acc.x = fmaf(a.x, b.x, acc.x);
+  acc.x = fmaf(-a.y, b.y, acc.x);
+  acc.y = fmaf(a.x, b.y, acc.y);
+  acc.y = fmaf(a.y, b.x, acc.y);
+}
+template <typename T, typename S>
+__host__ __device__ __forceinline__ T cscale(T a, S s) {
+  a.x *= s;
+  a.y *= s;
+  return a;
+}
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+}  // namespace efie

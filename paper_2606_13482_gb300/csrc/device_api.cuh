@@ -1,0 +1,109 @@
+// Device-side data descriptors and kernel launchers shared by the CUDA
+// translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace efie {
+
+// Near field (always FP64).  Block j of the CSR near lists couples target box
+// blk_tgt[j] with source box near_src[j]; A blocks are [n_rwg(x)][n_rwg(y)],
+// V blocks [n_tri(x)][n_tri(y)], row-major, in sorted basis order.
+struct NearDev {
+  const double* V;          // [nv][3]
+  const int32_t* T;         // [nt][3]
+  const double* area;       // [nt]
+  double k;
+  int64_t n_boxes, n_blocks;
+  const int64_t* near_ptr;  // [B+1]
+  const int32_t* near_src;  // [n_blocks]
+  const int32_t* blk_tgt;   // [n_blocks]
+  const int64_t* blkA_off;  // [n_blocks+1]
+  const int64_t* blkV_off;  // [n_blocks+1]
+  const int64_t* box_rwg_ptr;
+  const int64_t* box_tri_ptr;
+  const int32_t* tri_perm;  // sorted -> canonical triangle
+  const int64_t* tset_ptr;
+  const int32_t* tset;
+  const int32_t* rwg_tl;
+  const int32_t* rwg_loc;
+  const double* rwg_coef;
+  double2* A;               // [nnzA]
+  double2* Vn;              // [nnzV]
+};
+
+int near_upload_rules(const double* q3, const double* q4);
+void launch_near_pairs_A(const NearDev& nd, int64_t j0, int64_t nblk, const int64_t* scr_off,
+                         double2* scratch, int64_t total, cudaStream_t s);
+void launch_near_combine_A(const NearDev& nd, int64_t j0, int64_t nblk, const int64_t* scr_off,
+                           const double2* scratch, int64_t e_begin, int64_t total, cudaStream_t s);
+void launch_near_V(const NearDev& nd, int64_t e_begin, int64_t total, cudaStream_t s);
+void launch_near_spmv(const double2* M, const int64_t* blk_off, const int64_t* near_ptr,
+                      const int32_t* near_src, const int64_t* box_ptr, int64_t n_boxes,
+                      const double2* x, double2* y, int64_t ld, int nr, cudaStream_t s);
+
+// Strided tensor view of a box-batched 3D grid with channels innermost:
+// element (b, i0, i1, i2, c) at b*sb + i0*s0 + i1*s1 + i2*s2 + c.
+struct View {
+  int64_t sb, s0, s1, s2;
+};
+
+template <typename R>
+void launch_mode(const cpx_t<R>* in, View vin, cpx_t<R>* out, View vout, int64_t B, int C, int ax,
+                 int nin, int e0, int e1, int e2, const void* M0, const void* M1, bool complex_m,
+                 const int8_t* sel, const int64_t* srcmap, bool accumulate, cudaStream_t s);
+
+template <typename R>
+void launch_anterp(const R* mr, const int32_t* mr_base, const int32_t* mr_ext, const int64_t* mr_off,
+                   const R* mt, const int32_t* mt_base, const int32_t* mt_ext, const int64_t* mt_off,
+                   const int64_t* box_rwg_ptr, const int64_t* box_tri_ptr, int64_t B,
+                   const double2* xs, int64_t ldx, const double2* rho, int64_t ldr, int nr,
+                   cpx_t<R>* q, int sp, cudaStream_t s);
+
+template <typename R>
+void launch_interp(const R* mr, const int32_t* mr_base, const int32_t* mr_ext, const int64_t* mr_off,
+                   const int32_t* rwg_box, int64_t N, const R* mt, const int32_t* mt_base,
+                   const int32_t* mt_ext, const int64_t* mt_off, const int32_t* tri_box, int64_t Nt,
+                   const cpx_t<R>* r, int sp, int nr, double2* yA, int64_t ldy, double2* u,
+                   int64_t ldu, cudaStream_t s);
+
+template <typename R>
+void launch_mac(const cpx_t<R>* Qh, cpx_t<R>* Rh, const cpx_t<R>* Kh, int64_t B, int C, int64_t O,
+                int64_t nf, const int64_t* il_ptr, const int32_t* il_src, const int32_t* il_off,
+                cudaStream_t s);
+
+template <typename R>
+void launch_reduce_children(const cpx_t<R>* tmp, cpx_t<R>* q_parent, const int64_t* child_ptr,
+                            int64_t Bp, int64_t per_box, cudaStream_t s);
+
+void launch_kernel_samples(double2* Kc, const int32_t* offsets, int64_t o0, int64_t no, int n,
+                           int shat, double h, double Delta, double k, cudaStream_t s);
+template <typename R>
+void launch_convert(const double2* in, cpx_t<R>* out, int64_t n, cudaStream_t s);
+
+// misc vector kernels (FP64, c128)
+void launch_permute_in(const double2* x, int64_t ldx, const int32_t* perm, int64_t N, int nr,
+                       double2* xs, cudaStream_t s);
+void launch_charges(const double2* xs, int64_t ldx, const int32_t* tri_rwg, const int8_t* tri_sgn,
+                    int64_t Nt, int nr, double2* rho, int64_t ldr, cudaStream_t s);
+void launch_combine(const double2* yA, int64_t ldA, const double2* w, int64_t ldw,
+                    const int32_t* rwg_perm, const int32_t* rwg_tri_sorted, int64_t N, int nr,
+                    double2 cA, double2 cV, double2* y, int64_t ldy, double2* yAout,
+                    double2* yVout, cudaStream_t s);
+void launch_rhs_planewave(const double* V, const int32_t* T, const double* area, const int32_t* tri_pm,
+                          const int32_t* free_pm, int64_t N, double k, const double* khat,
+                          const double* pol, int nr, double2* rhs, int64_t ld, cudaStream_t s);
+
+// Krylov helpers (FP64)
+void launch_multidot(const double2* Vb, int64_t ldv_r, int64_t ldv_i, int nbasis, const double2* w,
+                     int64_t ldw, int64_t N, int nr, const int* active, double2* h, cudaStream_t s);
+void launch_multiaxpy(const double2* Vb, int64_t ldv_r, int64_t ldv_i, int nbasis, const double2* h,
+                      int hstride, double2* w, int64_t ldw, int64_t N, int nr, const int* active,
+                      double sign, cudaStream_t s);
+void launch_lincomb(const double2* x, const double2* y, double a, double b, double2* out, int64_t n,
+                    cudaStream_t s);
+void launch_norms(const double2* w, int64_t ldw, int64_t N, int nr, double* out, cudaStream_t s);
+
+}  // namespace efie

@@ -1,0 +1,656 @@
+// Far-field kernels of the fast matvec (steps a1-a9) and small vector kernels.
+//
+//  a2  k_anterp : leaf anterpolation q_{d,b} = sum_{n in b} j_n m_{d,n} and the
+//                 charge component q_{4,b} = sum_{c in b} rho_c m^phi_c
+//                 (Eq. TAfactor, Sec. VI-A); one CTA per leaf box, the box grid
+//                 accumulated in shared memory and written once, coalesced.
+//  a3/a8 k_mode : tensor mode products with the knot-insertion transfers
+//                 C^L / C^R and their transposes (Eq. interleveltransfer).
+//  a4-a7 k_mode : stabilize + zero-pad + DFT fused into one n x s' complex
+//                 matrix per axis (F P, P = B_stab^{-1} S), inverse likewise
+//                 (P^T F^{-1}); Sec. III-C, Sec. V-B.
+//  a6  k_mac    : frequency-domain translation R_x = sum_{y in IL(x)} K_{x-y} Q_y
+//                 (Eq. TAfactorBspline, Toeplitz structure), spectra stored
+//                 frequency-major so one frequency of all boxes is contiguous.
+//  a9  k_interp : interpolation (transpose of a2), one warp per basis function.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "common.cuh"
+#include "device_api.cuh"
+
+namespace efie {
+
+// ---------------------------------------------------------------- mode product
+template <typename R, bool CM>
+__global__ void k_mode(const cpx_t<R>* __restrict__ in, View vin, cpx_t<R>* __restrict__ out,
+                       View vout, int64_t B, int C, int ax, int nin, int e0, int e1, int e2,
+                       const void* __restrict__ M0, const void* __restrict__ M1,
+                       const int8_t* __restrict__ sel, const int64_t* __restrict__ srcmap,
+                       bool accumulate) {
+  using T = cpx_t<R>;
+  const int64_t total = B * e0 * e1 * e2 * (int64_t)C;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    int64_t t = idx;
+    int c = (int)(t % C);
+    t /= C;
+    int j2 = (int)(t % e2);
+    t /= e2;
+    int j1 = (int)(t % e1);
+    t /= e1;
+    int j0 = (int)(t % e0);
+    int64_t b = t / e0;
+    int64_t bs = srcmap ? srcmap[b] : b;
+    int jo = ax == 0 ? j0 : (ax == 1 ? j1 : j2);
+    int64_t step = ax == 0 ? vin.s0 : (ax == 1 ? vin.s1 : vin.s2);
+    int64_t base = bs * vin.sb + (int64_t)(ax == 0 ? 0 : j0) * vin.s0 +
+                   (int64_t)(ax == 1 ? 0 : j1) * vin.s1 + (int64_t)(ax == 2 ? 0 : j2) * vin.s2 + c;
+    const void* Mv = (sel && sel[3 * b + ax]) ? M1 : M0;
+    T acc = mk<R>(0, 0);
+    if (CM) {
+      const T* M = (const T*)Mv + (int64_t)jo * nin;
+      for (int i = 0; i < nin; ++i) cfma(acc, M[i], in[base + i * step]);
+    } else {
+      const R* M = (const R*)Mv + (int64_t)jo * nin;
+      for (int i = 0; i < nin; ++i) {
+        T v = in[base + i * step];
+        acc.x = fma(M[i], v.x, acc.x);
+        acc.y = fma(M[i], v.y, acc.y);
+      }
+    }
+    int64_t o = b * vout.sb + (int64_t)j0 * vout.s0 + (int64_t)j1 * vout.s1 + (int64_t)j2 * vout.s2 + c;
+    if (accumulate) acc = cadd(acc, out[o]);
+    out[o] = acc;
+  }
+}
+
+template <typename R>
+void launch_mode(const cpx_t<R>* in, View vin, cpx_t<R>* out, View vout, int64_t B, int C, int ax,
+                 int nin, int e0, int e1, int e2, const void* M0, const void* M1, bool complex_m,
+                 const int8_t* sel, const int64_t* srcmap, bool accumulate, cudaStream_t s) {
+  int64_t total = B * e0 * e1 * e2 * (int64_t)C;
+  if (total <= 0) return;
+  int64_t blocks = ceil_div(total, 256);
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  if (complex_m)
+    k_mode<R, true><<<(unsigned)blocks, 256, 0, s>>>(in, vin, out, vout, B, C, ax, nin, e0, e1, e2, M0,
+                                                     M1, sel, srcmap, accumulate);
+  else
+    k_mode<R, false><<<(unsigned)blocks, 256, 0, s>>>(in, vin, out, vout, B, C, ax, nin, e0, e1, e2, M0,
+                                                      M1, sel, srcmap, accumulate);
+}
+
+// ---------------------------------------------------------------- anterpolation
+// CTA (box b, rhs tile): shared grid [sp^3][4 * rt] complex.
+template <typename R>
+__global__ void k_anterp(const R* __restrict__ mr, const int32_t* __restrict__ mr_base,
+                         const int32_t* __restrict__ mr_ext, const int64_t* __restrict__ mr_off,
+                         const R* __restrict__ mt, const int32_t* __restrict__ mt_base,
+                         const int32_t* __restrict__ mt_ext, const int64_t* __restrict__ mt_off,
+                         const int64_t* __restrict__ box_rwg_ptr, const int64_t* __restrict__ box_tri_ptr,
+                         const double2* __restrict__ xs, int64_t ldx, const double2* __restrict__ rho,
+                         int64_t ldr, int nr, int rt, cpx_t<R>* __restrict__ q, int sp) {
+  extern __shared__ unsigned char smem_raw[];
+  R* g = (R*)smem_raw;  // [sp^3][4*rt][2]
+  const int b = blockIdx.x;
+  const int r0 = blockIdx.y * rt;
+  const int nrt = min(rt, nr - r0);
+  const int CT = 4 * rt;
+  const int npts = sp * sp * sp;
+  for (int i = threadIdx.x; i < npts * CT * 2; i += blockDim.x) g[i] = (R)0;
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  // RWGs: components 0..2
+  for (int64_t i = box_rwg_ptr[b] + warp; i < box_rwg_ptr[b + 1]; i += nw) {
+    const int e0 = mr_ext[3 * i], e1 = mr_ext[3 * i + 1], e2 = mr_ext[3 * i + 2];
+    const int b0 = mr_base[3 * i], b1 = mr_base[3 * i + 1], b2 = mr_base[3 * i + 2];
+    const int ne = e0 * e1 * e2;
+    const R* m = mr + mr_off[i];
+    for (int e = lane; e < ne; e += 32) {
+      int a0 = e / (e1 * e2), rem = e - a0 * e1 * e2, a1 = rem / e2, a2 = rem - a1 * e2;
+      int pt = ((b0 + a0) * sp + (b1 + a1)) * sp + (b2 + a2);
+      R mv[3] = {m[e], m[ne + e], m[2 * ne + e]};
+      for (int r = 0; r < nrt; ++r) {
+        double2 xv = xs[(int64_t)(r0 + r) * ldx + i];
+        for (int d = 0; d < 3; ++d) {
+          R* dst = g + ((int64_t)pt * CT + 4 * r + d) * 2;
+          atomicAdd(dst, mv[d] * (R)xv.x);
+          atomicAdd(dst + 1, mv[d] * (R)xv.y);
+        }
+      }
+    }
+  }
+  // triangles: component 3 with the charges rho
+  for (int64_t i = box_tri_ptr[b] + warp; i < box_tri_ptr[b + 1]; i += nw) {
+    const int e0 = mt_ext[3 * i], e1 = mt_ext[3 * i + 1], e2 = mt_ext[3 * i + 2];
+    const int b0 = mt_base[3 * i], b1 = mt_base[3 * i + 1], b2 = mt_base[3 * i + 2];
+    const int ne = e0 * e1 * e2;
+    const R* m = mt + mt_off[i];
+    for (int e = lane; e < ne; e += 32) {
+      int a0 = e / (e1 * e2), rem = e - a0 * e1 * e2, a1 = rem / e2, a2 = rem - a1 * e2;
+      int pt = ((b0 + a0) * sp + (b1 + a1)) * sp + (b2 + a2);
+      R mv = m[e];
+      for (int r = 0; r < nrt; ++r) {
+        double2 rv = rho[(int64_t)(r0 + r) * ldr + i];
+        R* dst = g + ((int64_t)pt * CT + 4 * r + 3) * 2;
+        atomicAdd(dst, mv * (R)rv.x);
+        atomicAdd(dst + 1, mv * (R)rv.y);
+      }
+    }
+  }
+  __syncthreads();
+  // write out: q[b][pt][4*r0 .. 4*(r0+nrt))
+  const int C = 4 * nr;
+  cpx_t<R>* qb = q + (int64_t)b * npts * C;
+  for (int idx = threadIdx.x; idx < npts * 4 * nrt; idx += blockDim.x) {
+    int pt = idx / (4 * nrt), cc = idx - pt * 4 * nrt;
+    qb[(int64_t)pt * C + 4 * r0 + cc] = mk<R>(g[((int64_t)pt * CT + cc) * 2], g[((int64_t)pt * CT + cc) * 2 + 1]);
+  }
+}
+
+template <typename R>
+void launch_anterp(const R* mr, const int32_t* mr_base, const int32_t* mr_ext, const int64_t* mr_off,
+                   const R* mt, const int32_t* mt_base, const int32_t* mt_ext, const int64_t* mt_off,
+                   const int64_t* box_rwg_ptr, const int64_t* box_tri_ptr, int64_t B,
+                   const double2* xs, int64_t ldx, const double2* rho, int64_t ldr, int nr,
+                   cpx_t<R>* q, int sp, cudaStream_t s) {
+  if (B <= 0 || nr <= 0) return;
+  const int64_t npts = (int64_t)sp * sp * sp;
+  const int64_t per_rhs = npts * 4 * 2 * sizeof(R);
+  int rt = (int)(200 * 1024 / per_rhs);
+  if (rt < 1) rt = 1;
+  if (rt > nr) rt = nr;
+  size_t smem = (size_t)per_rhs * rt;
+  static bool attr_set[2] = {false, false};
+  int which = sizeof(R) == 8;
+  if (!attr_set[which]) {
+    cudaFuncSetAttribute(k_anterp<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    attr_set[which] = true;
+  }
+  dim3 grid((unsigned)B, (unsigned)ceil_div(nr, rt));
+  k_anterp<R><<<grid, 256, smem, s>>>(mr, mr_base, mr_ext, mr_off, mt, mt_base, mt_ext, mt_off,
+                                      box_rwg_ptr, box_tri_ptr, xs, ldx, rho, ldr, nr, rt, q, sp);
+}
+
+// ---------------------------------------------------------------- interpolation
+// One warp per basis function; yA[r][i] = sum_d sum_e m_d[e] r[b][pt][4r+d],
+// u[r][t] = sum_e m^phi[e] r[b][pt][4r+3] (FP64 outputs).
+template <typename R, int RMAX>
+__global__ void k_interp(const R* __restrict__ mr, const int32_t* __restrict__ mr_base,
+                         const int32_t* __restrict__ mr_ext, const int64_t* __restrict__ mr_off,
+                         const int32_t* __restrict__ rwg_box, int64_t N, const R* __restrict__ mt,
+                         const int32_t* __restrict__ mt_base, const int32_t* __restrict__ mt_ext,
+                         const int64_t* __restrict__ mt_off, const int32_t* __restrict__ tri_box,
+                         int64_t Nt, const cpx_t<R>* __restrict__ rg, int sp, int nr,
+                         double2* __restrict__ yA, int64_t ldy, double2* __restrict__ u, int64_t ldu) {
+  using T = cpx_t<R>;
+  const int lane = threadIdx.x & 31;
+  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int npts = sp * sp * sp;
+  const int C = 4 * nr;
+  const bool is_rwg = w < N;
+  if (w >= N + Nt) return;
+  const int64_t i = is_rwg ? w : w - N;
+  const int32_t* base = is_rwg ? mr_base + 3 * i : mt_base + 3 * i;
+  const int32_t* ext = is_rwg ? mr_ext + 3 * i : mt_ext + 3 * i;
+  const int e0 = ext[0], e1 = ext[1], e2 = ext[2];
+  const int ne = e0 * e1 * e2;
+  const R* m = is_rwg ? mr + mr_off[i] : mt + mt_off[i];
+  const int box = is_rwg ? rwg_box[i] : tri_box[i];
+  const T* gb = rg + (int64_t)box * npts * C;
+  T acc[RMAX];
+#pragma unroll
+  for (int r = 0; r < RMAX; ++r) acc[r] = mk<R>(0, 0);
+  for (int e = lane; e < ne; e += 32) {
+    int a0 = e / (e1 * e2), rem = e - a0 * e1 * e2, a1 = rem / e2, a2 = rem - a1 * e2;
+    int pt = ((base[0] + a0) * sp + (base[1] + a1)) * sp + (base[2] + a2);
+    const T* gp = gb + (int64_t)pt * C;
+    if (is_rwg) {
+      R m0 = m[e], m1 = m[ne + e], m2 = m[2 * ne + e];
+#pragma unroll
+      for (int r = 0; r < RMAX; ++r) {
+        if (r >= nr) break;
+        T g0 = gp[4 * r], g1 = gp[4 * r + 1], g2 = gp[4 * r + 2];
+        acc[r].x += m0 * g0.x + m1 * g1.x + m2 * g2.x;
+        acc[r].y += m0 * g0.y + m1 * g1.y + m2 * g2.y;
+      }
+    } else {
+      R m0 = m[e];
+#pragma unroll
+      for (int r = 0; r < RMAX; ++r) {
+        if (r >= nr) break;
+        T g3 = gp[4 * r + 3];
+        acc[r].x += m0 * g3.x;
+        acc[r].y += m0 * g3.y;
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < RMAX; ++r) {
+    if (r >= nr) break;
+    double vx = (double)acc[r].x, vy = (double)acc[r].y;
+    for (int o = 16; o > 0; o >>= 1) {
+      vx += __shfl_down_sync(0xffffffffu, vx, o);
+      vy += __shfl_down_sync(0xffffffffu, vy, o);
+    }
+    if (lane == 0) {
+      if (is_rwg)
+        yA[r * ldy + i] = make_double2(vx, vy);
+      else
+        u[r * ldu + i] = make_double2(vx, vy);
+    }
+  }
+}
+
+template <typename R>
+void launch_interp(const R* mr, const int32_t* mr_base, const int32_t* mr_ext, const int64_t* mr_off,
+                   const int32_t* rwg_box, int64_t N, const R* mt, const int32_t* mt_base,
+                   const int32_t* mt_ext, const int64_t* mt_off, const int32_t* tri_box, int64_t Nt,
+                   const cpx_t<R>* r, int sp, int nr, double2* yA, int64_t ldy, double2* u,
+                   int64_t ldu, cudaStream_t s) {
+  // nr <= 8 (the far pipeline runs right-hand sides in chunks of at most 8)
+  int64_t warps = N + Nt;
+  int64_t blocks = ceil_div(warps * 32, 256);
+  if (nr <= 1)
+    k_interp<R, 1><<<(unsigned)blocks, 256, 0, s>>>(mr, mr_base, mr_ext, mr_off, rwg_box, N, mt, mt_base,
+                                                    mt_ext, mt_off, tri_box, Nt, r, sp, nr, yA, ldy, u, ldu);
+  else if (nr <= 4)
+    k_interp<R, 4><<<(unsigned)blocks, 256, 0, s>>>(mr, mr_base, mr_ext, mr_off, rwg_box, N, mt, mt_base,
+                                                    mt_ext, mt_off, tri_box, Nt, r, sp, nr, yA, ldy, u, ldu);
+  else
+    k_interp<R, 8><<<(unsigned)blocks, 256, 0, s>>>(mr, mr_base, mr_ext, mr_off, rwg_box, N, mt, mt_base,
+                                                    mt_ext, mt_off, tri_box, Nt, r, sp, nr, yA, ldy, u, ldu);
+}
+
+// ---------------------------------------------------------------- translation MAC
+// Rh[f][x][c] = sum_{j in IL(x)} Kh[f][off_j] * Qh[f][src_j][c]
+// block: (C channels) x (TY targets); grid: (frequency f, target tile)
+template <typename R>
+__global__ void k_mac(const cpx_t<R>* __restrict__ Qh, cpx_t<R>* __restrict__ Rh,
+                      const cpx_t<R>* __restrict__ Kh, int64_t B, int C, int64_t O,
+                      const int64_t* __restrict__ il_ptr, const int32_t* __restrict__ il_src,
+                      const int32_t* __restrict__ il_off) {
+  using T = cpx_t<R>;
+  const int64_t f = blockIdx.x;
+  const int c = threadIdx.x;
+  const int64_t x = (int64_t)blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= B) return;
+  const T* Qf = Qh + f * B * C;
+  const T* Kf = Kh + f * O;
+  T acc = mk<R>(0, 0);
+  for (int64_t j = il_ptr[x]; j < il_ptr[x + 1]; ++j) {
+    T kv = Kf[il_off[j]];
+    T qv = Qf[(int64_t)il_src[j] * C + c];
+    cfma(acc, kv, qv);
+  }
+  Rh[f * B * C + x * C + c] = acc;
+}
+
+template <typename R>
+void launch_mac(const cpx_t<R>* Qh, cpx_t<R>* Rh, const cpx_t<R>* Kh, int64_t B, int C, int64_t O,
+                int64_t nf, const int64_t* il_ptr, const int32_t* il_src, const int32_t* il_off,
+                cudaStream_t s) {
+  if (B <= 0 || nf <= 0) return;
+  int ty = 256 / C;
+  if (ty < 1) ty = 1;
+  dim3 block(C, ty);
+  dim3 grid((unsigned)nf, (unsigned)ceil_div(B, ty));
+  k_mac<R><<<grid, block, 0, s>>>(Qh, Rh, Kh, B, C, O, il_ptr, il_src, il_off);
+}
+
+// ---------------------------------------------------------------- children sum
+// q_parent[P][e] = sum_{c in children(P)} tmp[c][e]   (children contiguous)
+template <typename R>
+__global__ void k_reduce_children(const cpx_t<R>* __restrict__ tmp, cpx_t<R>* __restrict__ qp,
+                                  const int64_t* __restrict__ child_ptr, int64_t Bp, int64_t per_box) {
+  int64_t total = Bp * per_box;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    int64_t P = idx / per_box, e = idx - P * per_box;
+    cpx_t<R> acc = mk<R>(0, 0);
+    for (int64_t c = child_ptr[P]; c < child_ptr[P + 1]; ++c) acc = cadd(acc, tmp[c * per_box + e]);
+    qp[idx] = acc;
+  }
+}
+
+template <typename R>
+void launch_reduce_children(const cpx_t<R>* tmp, cpx_t<R>* q_parent, const int64_t* child_ptr,
+                            int64_t Bp, int64_t per_box, cudaStream_t s) {
+  int64_t total = Bp * per_box;
+  if (total <= 0) return;
+  int64_t blocks = ceil_div(total, 256);
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  k_reduce_children<R><<<(unsigned)blocks, 256, 0, s>>>(tmp, q_parent, child_ptr, Bp, per_box);
+}
+
+// ---------------------------------------------------------------- kernel samples
+// Kc[o][i0][i1][i2] = g(o h + t Delta), t_d = i_d (i_d < shat) or i_d - n, FP64.
+__global__ void k_kernel_samples(double2* __restrict__ Kc, const int32_t* __restrict__ offsets,
+                                 int64_t o0, int64_t no, int n, int shat, double h, double Delta,
+                                 double k) {
+  const int64_t n3 = (int64_t)n * n * n;
+  const int64_t total = no * n3;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    int64_t o = idx / n3, e = idx - o * n3;
+    int i0 = (int)(e / (n * n)), i1 = (int)((e / n) % n), i2 = (int)(e % n);
+    int t0 = i0 < shat ? i0 : i0 - n, t1 = i1 < shat ? i1 : i1 - n, t2 = i2 < shat ? i2 : i2 - n;
+    const int32_t* ov = offsets + 3 * (o0 + o);
+    double d0 = ov[0] * h + t0 * Delta, d1 = ov[1] * h + t1 * Delta, d2 = ov[2] * h + t2 * Delta;
+    double R = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+    double sn, cs;
+    sincos(k * R, &sn, &cs);
+    double fct = 1.0 / (12.566370614359172953850573533118 * R);
+    Kc[idx] = make_double2(cs * fct, -sn * fct);
+  }
+}
+
+void launch_kernel_samples(double2* Kc, const int32_t* offsets, int64_t o0, int64_t no, int n,
+                           int shat, double h, double Delta, double k, cudaStream_t s) {
+  int64_t total = no * (int64_t)n * n * n;
+  if (total <= 0) return;
+  int64_t blocks = ceil_div(total, 256);
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  k_kernel_samples<<<(unsigned)blocks, 256, 0, s>>>(Kc, offsets, o0, no, n, shat, h, Delta, k);
+}
+
+template <typename R>
+__global__ void k_convert(const double2* __restrict__ in, cpx_t<R>* __restrict__ out, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = mk<R>((R)in[i].x, (R)in[i].y);
+}
+template <typename R>
+void launch_convert(const double2* in, cpx_t<R>* out, int64_t n, cudaStream_t s) {
+  if (n <= 0) return;
+  int64_t blocks = ceil_div(n, 256);
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  k_convert<R><<<(unsigned)blocks, 256, 0, s>>>(in, out, n);
+}
+
+// ---------------------------------------------------------------- vectors
+__global__ void k_permute_in(const double2* __restrict__ x, int64_t ldx, const int32_t* __restrict__ perm,
+                             int64_t N, int nr, double2* __restrict__ xs) {
+  int64_t total = N * nr;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    int64_t r = idx / N, i = idx - r * N;
+    xs[r * N + i] = x[r * ldx + perm[i]];
+  }
+}
+void launch_permute_in(const double2* x, int64_t ldx, const int32_t* perm, int64_t N, int nr,
+                       double2* xs, cudaStream_t s) {
+  int64_t total = N * nr;
+  if (total <= 0) return;
+  int64_t blocks = ceil_div(total, 256);
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  k_permute_in<<<(unsigned)blocks, 256, 0, s>>>(x, ldx, perm, N, nr, xs);
+}
+
+// rho[r][t] = sum over the 3 RWGs of triangle t of sign * x (Sigma^T x, FP64)
+__global__ void k_charges(const double2* __restrict__ xs, int64_t ldx, const int32_t* __restrict__ tri_rwg,
+                          const int8_t* __restrict__ tri_sgn, int64_t Nt, int nr, double2* __restrict__ rho,
+                          int64_t ldr) {
+  int64_t total = Nt * nr;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    int64_t r = idx / Nt, t = idx - r * Nt;
+    double2 a = make_double2(0, 0);
+    for (int q = 0; q < 3; ++q) {
+      int32_t i = tri_rwg[3 * t + q];
+      if (i < 0) continue;
+      double2 v = xs[r * ldx + i];
+      double sg = (double)tri_sgn[3 * t + q];
+      a.x += sg * v.x;
+      a.y += sg * v.y;
+    }
+    rho[r * ldr + t] = a;
+  }
+}
+void launch_charges(const double2* xs, int64_t ldx, const int32_t* tri_rwg, const int8_t* tri_sgn,
+                    int64_t Nt, int nr, double2* rho, int64_t ldr, cudaStream_t s) {
+  int64_t total = Nt * nr;
+  if (total <= 0) return;
+  int64_t blocks = ceil_div(total, 256);
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  k_charges<<<(unsigned)blocks, 256, 0, s>>>(xs, ldx, tri_rwg, tri_sgn, Nt, nr, rho, ldr);
+}
+
+// y[r][m] = cA * yA[r][i] + cV * (w[r][t+] - w[r][t-]), m = perm[i]
+__global__ void k_combine(const double2* __restrict__ yA, int64_t ldA, const double2* __restrict__ w,
+                          int64_t ldw, const int32_t* __restrict__ perm, const int32_t* __restrict__ rts,
+                          int64_t N, int nr, double2 cA, double2 cV, double2* __restrict__ y, int64_t ldy,
+                          double2* __restrict__ yAo, double2* __restrict__ yVo) {
+  int64_t total = N * nr;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    int64_t r = idx / N, i = idx - r * N;
+    double2 a = yA[r * ldA + i];
+    double2 wp = w[r * ldw + rts[2 * i]], wm = w[r * ldw + rts[2 * i + 1]];
+    double2 v = make_double2(wp.x - wm.x, wp.y - wm.y);
+    int64_t m = perm[i];
+    if (y) y[r * ldy + m] = cadd(cmul(cA, a), cmul(cV, v));
+    if (yAo) yAo[r * ldy + m] = a;
+    if (yVo) yVo[r * ldy + m] = v;
+  }
+}
+void launch_combine(const double2* yA, int64_t ldA, const double2* w, int64_t ldw,
+                    const int32_t* rwg_perm, const int32_t* rwg_tri_sorted, int64_t N, int nr,
+                    double2 cA, double2 cV, double2* y, int64_t ldy, double2* yAout, double2* yVout,
+                    cudaStream_t s) {
+  int64_t total = N * nr;
+  if (total <= 0) return;
+  int64_t blocks = ceil_div(total, 256);
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  k_combine<<<(unsigned)blocks, 256, 0, s>>>(yA, ldA, w, ldw, rwg_perm, rwg_tri_sorted, N, nr, cA, cV,
+                                             y, ldy, yAout, yVout);
+}
+
+// Plane-wave RHS: per RWG, both triangles with a degree-10 collapsed rule.
+__constant__ double c_q6[3][36];
+__global__ void k_rhs_pw(const double* __restrict__ V, const int32_t* __restrict__ T,
+                         const double* __restrict__ area, const int32_t* __restrict__ tri_pm,
+                         const int32_t* __restrict__ free_pm, int64_t N, double k,
+                         const double* __restrict__ khat, const double* __restrict__ pol, int nr,
+                         double2* __restrict__ rhs, int64_t ld) {
+  int64_t total = N * nr;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    int64_t r = idx / N, m = idx - r * N;
+    const double* kh = khat + 3 * r;
+    const double* pl = pol + 3 * r;
+    double2 acc = make_double2(0, 0);
+    for (int s = 0; s < 2; ++s) {
+      int t = tri_pm[2 * m + s];
+      const double* xf = V + 3 * free_pm[2 * m + s];
+      double sc = (s == 0 ? 1.0 : -1.0) / (2.0 * area[t]);
+      const double* a = V + 3 * T[3 * t];
+      const double* b = V + 3 * T[3 * t + 1];
+      const double* c = V + 3 * T[3 * t + 2];
+      for (int q = 0; q < 36; ++q) {
+        double xi = c_q6[0][q], eta = c_q6[1][q], w = c_q6[2][q] * 2.0 * area[t];
+        double x[3];
+        for (int d = 0; d < 3; ++d) x[d] = a[d] + xi * (b[d] - a[d]) + eta * (c[d] - a[d]);
+        double ph = -k * (kh[0] * x[0] + kh[1] * x[1] + kh[2] * x[2]);
+        double sn, cs;
+        sincos(ph, &sn, &cs);
+        double fp = 0;
+        for (int d = 0; d < 3; ++d) fp += (x[d] - xf[d]) * pl[d];
+        fp *= sc * w;
+        acc.x += fp * cs;
+        acc.y += fp * sn;
+      }
+    }
+    rhs[r * ld + m] = acc;
+  }
+}
+int upload_rhs_rule(const double* q6) {
+  return cudaMemcpyToSymbol(c_q6, q6, sizeof(double) * 108) == cudaSuccess ? 0 : -1;
+}
+void launch_rhs_planewave(const double* V, const int32_t* T, const double* area, const int32_t* tri_pm,
+                          const int32_t* free_pm, int64_t N, double k, const double* khat,
+                          const double* pol, int nr, double2* rhs, int64_t ld, cudaStream_t s) {
+  int64_t total = N * nr;
+  if (total <= 0) return;
+  int64_t blocks = ceil_div(total, 128);
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  k_rhs_pw<<<(unsigned)blocks, 128, 0, s>>>(V, T, area, tri_pm, free_pm, N, k, khat, pol, nr, rhs, ld);
+}
+
+// ---------------------------------------------------------------- Krylov
+// h[r][i] += sum_n conj(V[r][i][n]) w[r][n]; grid (chunks, nbasis, nr)
+__global__ void k_multidot(const double2* __restrict__ Vb, int64_t ldv_r, int64_t ldv_i,
+                           const double2* __restrict__ w, int64_t ldw, int64_t N,
+                           const int* __restrict__ active, double2* __restrict__ h, int nbasis) {
+  int i = blockIdx.y, r = blockIdx.z;
+  if (active && !active[r]) return;
+  const double2* v = Vb + r * ldv_r + i * ldv_i;
+  const double2* wr = w + r * ldw;
+  double sx = 0, sy = 0;
+  for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
+    double2 a = v[n], b = wr[n];
+    sx += a.x * b.x + a.y * b.y;
+    sy += a.x * b.y - a.y * b.x;
+  }
+  __shared__ double rx[32], ry[32];
+  for (int o = 16; o > 0; o >>= 1) {
+    sx += __shfl_down_sync(0xffffffffu, sx, o);
+    sy += __shfl_down_sync(0xffffffffu, sy, o);
+  }
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    rx[wid] = sx;
+    ry[wid] = sy;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    int nw = blockDim.x >> 5;
+    sx = lane < nw ? rx[lane] : 0;
+    sy = lane < nw ? ry[lane] : 0;
+    for (int o = 16; o > 0; o >>= 1) {
+      sx += __shfl_down_sync(0xffffffffu, sx, o);
+      sy += __shfl_down_sync(0xffffffffu, sy, o);
+    }
+    if (lane == 0) {
+      atomicAdd(&h[(int64_t)r * nbasis + i].x, sx);
+      atomicAdd(&h[(int64_t)r * nbasis + i].y, sy);
+    }
+  }
+}
+void launch_multidot(const double2* Vb, int64_t ldv_r, int64_t ldv_i, int nbasis, const double2* w,
+                     int64_t ldw, int64_t N, int nr, const int* active, double2* h, cudaStream_t s) {
+  if (nbasis <= 0 || nr <= 0) return;
+  cudaMemsetAsync(h, 0, sizeof(double2) * nbasis * nr, s);
+  int chunks = (int)ceil_div(N, 256 * 16);
+  if (chunks > 64) chunks = 64;
+  if (chunks < 1) chunks = 1;
+  dim3 grid(chunks, nbasis, nr);
+  k_multidot<<<grid, 256, 0, s>>>(Vb, ldv_r, ldv_i, w, ldw, N, active, h, nbasis);
+}
+
+// w[r][n] += sign * sum_i h[r][i] V[r][i][n]
+__global__ void k_multiaxpy(const double2* __restrict__ Vb, int64_t ldv_r, int64_t ldv_i, int nbasis,
+                            const double2* __restrict__ h, int hstride, double2* __restrict__ w,
+                            int64_t ldw, int64_t N, int nr, const int* __restrict__ active, double sign) {
+  int64_t total = N * nr;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    int64_t r = idx / N, n = idx - r * N;
+    if (active && !active[r]) continue;
+    double2 acc = make_double2(0, 0);
+    for (int i = 0; i < nbasis; ++i) cfma(acc, h[r * hstride + i], Vb[r * ldv_r + i * ldv_i + n]);
+    double2 t = w[r * ldw + n];
+    w[r * ldw + n] = make_double2(t.x + sign * acc.x, t.y + sign * acc.y);
+  }
+}
+void launch_multiaxpy(const double2* Vb, int64_t ldv_r, int64_t ldv_i, int nbasis, const double2* h,
+                      int hstride, double2* w, int64_t ldw, int64_t N, int nr, const int* active,
+                      double sign, cudaStream_t s) {
+  int64_t total = N * nr;
+  if (total <= 0 || nbasis <= 0) return;
+  int64_t blocks = ceil_div(total, 256);
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  k_multiaxpy<<<(unsigned)blocks, 256, 0, s>>>(Vb, ldv_r, ldv_i, nbasis, h, hstride, w, ldw, N, nr, active,
+                                               sign);
+}
+
+// out = a x + b y over n complex entries (real a, b)
+__global__ void k_lincomb(const double2* __restrict__ x, const double2* __restrict__ y, double a, double b,
+                          double2* __restrict__ out, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double2 u = x[i], v = y[i];
+    out[i] = make_double2(a * u.x + b * v.x, a * u.y + b * v.y);
+  }
+}
+void launch_lincomb(const double2* x, const double2* y, double a, double b, double2* out, int64_t n,
+                    cudaStream_t s) {
+  if (n <= 0) return;
+  int64_t blocks = ceil_div(n, 256);
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  k_lincomb<<<(unsigned)blocks, 256, 0, s>>>(x, y, a, b, out, n);
+}
+
+__global__ void k_norms(const double2* __restrict__ w, int64_t ldw, int64_t N, double* out) {
+  int r = blockIdx.y;
+  double s = 0;
+  for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
+    double2 a = w[r * ldw + n];
+    s += a.x * a.x + a.y * a.y;
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  __shared__ double red[32];
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) red[wid] = s;
+  __syncthreads();
+  if (wid == 0) {
+    int nw = blockDim.x >> 5;
+    s = lane < nw ? red[lane] : 0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) atomicAdd(&out[r], s);
+  }
+}
+void launch_norms(const double2* w, int64_t ldw, int64_t N, int nr, double* out, cudaStream_t s) {
+  if (nr <= 0) return;
+  cudaMemsetAsync(out, 0, sizeof(double) * nr, s);
+  int chunks = (int)ceil_div(N, 256 * 16);
+  if (chunks > 64) chunks = 64;
+  if (chunks < 1) chunks = 1;
+  dim3 grid(chunks, nr);
+  k_norms<<<grid, 256, 0, s>>>(w, ldw, N, out);
+}
+
+// explicit instantiations
+template void launch_mode<float>(const float2*, View, float2*, View, int64_t, int, int, int, int, int, int,
+                                 const void*, const void*, bool, const int8_t*, const int64_t*, bool,
+                                 cudaStream_t);
+template void launch_mode<double>(const double2*, View, double2*, View, int64_t, int, int, int, int, int, int,
+                                  const void*, const void*, bool, const int8_t*, const int64_t*, bool,
+                                  cudaStream_t);
+template void launch_anterp<float>(const float*, const int32_t*, const int32_t*, const int64_t*, const float*,
+                                   const int32_t*, const int32_t*, const int64_t*, const int64_t*,
+                                   const int64_t*, int64_t, const double2*, int64_t, const double2*, int64_t,
+                                   int, float2*, int, cudaStream_t);
+template void launch_anterp<double>(const double*, const int32_t*, const int32_t*, const int64_t*,
+                                    const double*, const int32_t*, const int32_t*, const int64_t*,
+                                    const int64_t*, const int64_t*, int64_t, const double2*, int64_t,
+                                    const double2*, int64_t, int, double2*, int, cudaStream_t);
+template void launch_interp<float>(const float*, const int32_t*, const int32_t*, const int64_t*, const int32_t*,
+                                   int64_t, const float*, const int32_t*, const int32_t*, const int64_t*,
+                                   const int32_t*, int64_t, const float2*, int, int, double2*, int64_t,
+                                   double2*, int64_t, cudaStream_t);
+template void launch_interp<double>(const double*, const int32_t*, const int32_t*, const int64_t*,
+                                    const int32_t*, int64_t, const double*, const int32_t*, const int32_t*,
+                                    const int64_t*, const int32_t*, int64_t, const double2*, int, int,
+                                    double2*, int64_t, double2*, int64_t, cudaStream_t);
+template void launch_mac<float>(const float2*, float2*, const float2*, int64_t, int, int64_t, int64_t,
+                                const int64_t*, const int32_t*, const int32_t*, cudaStream_t);
+template void launch_mac<double>(const double2*, double2*, const double2*, int64_t, int, int64_t, int64_t,
+                                 const int64_t*, const int32_t*, const int32_t*, cudaStream_t);
+template void launch_reduce_children<float>(const float2*, float2*, const int64_t*, int64_t, int64_t,
+                                            cudaStream_t);
+template void launch_reduce_children<double>(const double2*, double2*, const int64_t*, int64_t, int64_t,
+                                             cudaStream_t);
+template void launch_convert<float>(const double2*, float2*, int64_t, cudaStream_t);
+template void launch_convert<double>(const double2*, double2*, int64_t, cudaStream_t);
+
+}  // namespace efie

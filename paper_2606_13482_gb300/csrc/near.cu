@@ -1,0 +1,461 @@
+// FP64 near field: triangle-pair Galerkin integrals, block assembly of the
+// two near sets of the star factorization (Sec. VI-A: RWG pairs for A and
+// triangle pairs for V, each between adjacent leaf boxes), and the blocked
+// near-field SpMV.
+//
+// Quadrature rule (identical in definition to the CPU reference, written
+// independently):
+//   close pair  |cen_c - cen_c'|^2 < 4 max(emax_c^2, emax_c'^2):
+//     outer collapsed 4x4 Gauss rule on c; inner analytic static part
+//     int 1/R, int (y-rho)/R over the flat triangle c' (Wilton et al. 1984,
+//     Graglia 1993) plus the smooth remainder (exp(-jkR)-1)/(4 pi R) on a 4x4
+//     rule; result averaged over the two orientations (c outer / c' outer).
+//   regular pair: collapsed 3x3 rule on both triangles.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "common.cuh"
+#include "device_api.cuh"
+
+namespace efie {
+
+__constant__ double c_q3[3][9];   // xi, eta, w (sum w = 1/2)
+__constant__ double c_q4[3][16];
+
+struct TriG {
+  double v[3][3];
+  double c[3];
+  double twoa;
+  double emax2;
+};
+
+__device__ __forceinline__ void load_tri(const double* __restrict__ V, const int32_t* __restrict__ T,
+                                         int t, TriG& g) {
+  for (int a = 0; a < 3; ++a) {
+    int vi = T[3 * t + a];
+    for (int d = 0; d < 3; ++d) g.v[a][d] = V[3 * vi + d];
+  }
+  double e1[3], e2[3];
+  for (int d = 0; d < 3; ++d) {
+    g.c[d] = (g.v[0][d] + g.v[1][d] + g.v[2][d]) / 3.0;
+    e1[d] = g.v[1][d] - g.v[0][d];
+    e2[d] = g.v[2][d] - g.v[0][d];
+  }
+  double nx = e1[1] * e2[2] - e1[2] * e2[1], ny = e1[2] * e2[0] - e1[0] * e2[2],
+         nz = e1[0] * e2[1] - e1[1] * e2[0];
+  g.twoa = sqrt(nx * nx + ny * ny + nz * nz);
+  double m = 0;
+  for (int a = 0; a < 3; ++a) {
+    double s = 0;
+    for (int d = 0; d < 3; ++d) {
+      double t_ = g.v[(a + 1) % 3][d] - g.v[a][d];
+      s += t_ * t_;
+    }
+    m = fmax(m, s);
+  }
+  g.emax2 = m;
+}
+
+__device__ __forceinline__ void rule_point(const TriG& g, double xi, double eta, double* x) {
+  for (int d = 0; d < 3; ++d)
+    x[d] = g.v[0][d] + xi * (g.v[1][d] - g.v[0][d]) + eta * (g.v[2][d] - g.v[0][d]);
+}
+
+#define FOUR_PI 12.566370614359172953850573533118
+
+// ln((R+ + l+)/(R- + l-)) without cancellation
+__device__ __forceinline__ double safe_log_ratio(double Rp, double lp, double Rm, double lm,
+                                                 double R0sq) {
+  double num = lp >= 0 ? Rp + lp : R0sq / fmax(Rp - lp, 1e-300);
+  double den = lm >= 0 ? Rm + lm : R0sq / fmax(Rm - lm, 1e-300);
+  if (!(num > 0) || !(den > 0)) return 0.0;
+  return log(num / den);
+}
+
+// Static potentials of triangle g at observation point r:
+//   I1 = int 1/|r-r'| dS', Iv = int (r' - rho)/|r-r'| dS', rho = projection of r.
+__device__ void static_pot(const TriG& g, const double* r, double& I1, double* Iv, double* rho) {
+  double e1[3], e2[3], n[3];
+  for (int d = 0; d < 3; ++d) {
+    e1[d] = g.v[1][d] - g.v[0][d];
+    e2[d] = g.v[2][d] - g.v[0][d];
+  }
+  n[0] = e1[1] * e2[2] - e1[2] * e2[1];
+  n[1] = e1[2] * e2[0] - e1[0] * e2[2];
+  n[2] = e1[0] * e2[1] - e1[1] * e2[0];
+  double nn = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+  for (int d = 0; d < 3; ++d) n[d] /= nn;
+  double dh = 0;
+  for (int d = 0; d < 3; ++d) dh += (r[d] - g.v[0][d]) * n[d];
+  for (int d = 0; d < 3; ++d) rho[d] = r[d] - dh * n[d];
+  double ad = fabs(dh);
+  I1 = 0.0;
+  Iv[0] = Iv[1] = Iv[2] = 0.0;
+  for (int i = 0; i < 3; ++i) {
+    const double* a = g.v[i];
+    const double* b = g.v[(i + 1) % 3];
+    double L[3], ll = 0;
+    for (int d = 0; d < 3; ++d) {
+      L[d] = b[d] - a[d];
+      ll += L[d] * L[d];
+    }
+    ll = sqrt(ll);
+    double lh[3] = {L[0] / ll, L[1] / ll, L[2] / ll};
+    double uh[3] = {lh[1] * n[2] - lh[2] * n[1], lh[2] * n[0] - lh[0] * n[2],
+                    lh[0] * n[1] - lh[1] * n[0]};
+    double lm = 0, lp = 0, P0 = 0, Rm = 0, Rp = 0;
+    for (int d = 0; d < 3; ++d) {
+      lm += (a[d] - rho[d]) * lh[d];
+      lp += (b[d] - rho[d]) * lh[d];
+      P0 += (a[d] - rho[d]) * uh[d];
+      Rm += (r[d] - a[d]) * (r[d] - a[d]);
+      Rp += (r[d] - b[d]) * (r[d] - b[d]);
+    }
+    Rm = sqrt(Rm);
+    Rp = sqrt(Rp);
+    double R0sq = P0 * P0 + dh * dh;
+    double lg = safe_log_ratio(Rp, lp, Rm, lm, R0sq);
+    double vterm = 0.5 * (R0sq * lg + lp * Rp - lm * Rm);
+    for (int d = 0; d < 3; ++d) Iv[d] += vterm * uh[d];
+    if (fabs(P0) > 1e-300) {
+      double at = atan2(P0 * lp, R0sq + ad * Rp) - atan2(P0 * lm, R0sq + ad * Rm);
+      I1 += P0 * lg - ad * at;
+    }
+  }
+}
+
+// (exp(-jkR) - 1)/(4 pi R), limit -jk/(4 pi) at R = 0
+__device__ __forceinline__ double2 smooth_rem(double R, double k) {
+  if (!(R > 0)) return make_double2(0.0, -k / FOUR_PI);
+  double s, c, sh, ch;
+  sincos(k * R, &s, &c);
+  sincos(0.5 * k * R, &sh, &ch);
+  return make_double2(-2.0 * sh * sh / (FOUR_PI * R), -s / (FOUR_PI * R));
+}
+
+__device__ __forceinline__ double2 green(double R, double k) {
+  double s, c;
+  sincos(k * R, &s, &c);
+  double f = 1.0 / (FOUR_PI * R);
+  return make_double2(c * f, -s * f);
+}
+
+__device__ __forceinline__ bool is_close(const TriG& A, const TriG& B) {
+  double d2 = 0;
+  for (int d = 0; d < 3; ++d) {
+    double t = A.c[d] - B.c[d];
+    d2 += t * t;
+  }
+  return d2 < 4.0 * fmax(A.emax2, B.emax2);
+}
+
+// One orientation of the singular rule: outer on A, inner on B.
+// Ivv[i][j] = int_A int_B (x - vA_i).(y - vB_j) g ; full = false -> only I0.
+__device__ void pair_close_oriented(const TriG& A, const TriG& B, double k, bool full,
+                                    double2& I0, double2* Ivv) {
+  I0 = make_double2(0, 0);
+  if (full)
+    for (int q = 0; q < 9; ++q) Ivv[q] = make_double2(0, 0);
+  double ya[16][3];
+  for (int q = 0; q < 16; ++q) rule_point(B, c_q4[0][q], c_q4[1][q], ya[q]);
+  for (int p = 0; p < 16; ++p) {
+    double x[3];
+    rule_point(A, c_q4[0][p], c_q4[1][p], x);
+    double wx = c_q4[2][p] * A.twoa;
+    double I1, Iv[3], rho[3];
+    static_pot(B, x, I1, Iv, rho);
+    double2 in0 = make_double2(I1 / FOUR_PI, 0.0);
+    double2 iny[3];
+    for (int d = 0; d < 3; ++d) iny[d] = make_double2((Iv[d] + (rho[d] - B.c[d]) * I1) / FOUR_PI, 0.0);
+    for (int q = 0; q < 16; ++q) {
+      double dd[3], R = 0;
+      for (int d = 0; d < 3; ++d) {
+        dd[d] = x[d] - ya[q][d];
+        R += dd[d] * dd[d];
+      }
+      R = sqrt(R);
+      double2 s = smooth_rem(R, k);
+      double wy = c_q4[2][q] * B.twoa;
+      s.x *= wy;
+      s.y *= wy;
+      in0.x += s.x;
+      in0.y += s.y;
+      if (full)
+        for (int d = 0; d < 3; ++d) {
+          double yl = ya[q][d] - B.c[d];
+          iny[d].x += s.x * yl;
+          iny[d].y += s.y * yl;
+        }
+    }
+    I0.x += wx * in0.x;
+    I0.y += wx * in0.y;
+    if (full) {
+      for (int i = 0; i < 3; ++i) {
+        double xv[3];
+        for (int d = 0; d < 3; ++d) xv[d] = x[d] - A.v[i][d];
+        for (int j = 0; j < 3; ++j) {
+          double2 acc = make_double2(0, 0);
+          for (int d = 0; d < 3; ++d) {
+            double bj = B.v[j][d] - B.c[d];
+            acc.x += xv[d] * (iny[d].x - bj * in0.x);
+            acc.y += xv[d] * (iny[d].y - bj * in0.y);
+          }
+          Ivv[3 * i + j].x += wx * acc.x;
+          Ivv[3 * i + j].y += wx * acc.y;
+        }
+      }
+    }
+  }
+}
+
+__device__ void pair_regular(const TriG& A, const TriG& B, double k, bool full, double2& I0,
+                             double2* Ivv) {
+  double ya[9][3], wy[9];
+  for (int q = 0; q < 9; ++q) {
+    double y[3];
+    rule_point(B, c_q3[0][q], c_q3[1][q], y);
+    for (int d = 0; d < 3; ++d) ya[q][d] = y[d] - B.c[d];
+    wy[q] = c_q3[2][q] * B.twoa;
+  }
+  double dc[3] = {A.c[0] - B.c[0], A.c[1] - B.c[1], A.c[2] - B.c[2]};
+  double2 J00 = make_double2(0, 0), Jx[3], Jy[3], Jxy = make_double2(0, 0);
+  for (int d = 0; d < 3; ++d) Jx[d] = Jy[d] = make_double2(0, 0);
+  for (int p = 0; p < 9; ++p) {
+    double x[3], xl[3];
+    rule_point(A, c_q3[0][p], c_q3[1][p], x);
+    for (int d = 0; d < 3; ++d) xl[d] = x[d] - A.c[d];
+    double wx = c_q3[2][p] * A.twoa;
+    double2 S = make_double2(0, 0), Sy[3];
+    for (int d = 0; d < 3; ++d) Sy[d] = make_double2(0, 0);
+    for (int q = 0; q < 9; ++q) {
+      double R = 0;
+      for (int d = 0; d < 3; ++d) {
+        double t = dc[d] + xl[d] - ya[q][d];
+        R += t * t;
+      }
+      R = sqrt(R);
+      double2 g = green(R, k);
+      g.x *= wy[q];
+      g.y *= wy[q];
+      S.x += g.x;
+      S.y += g.y;
+      if (full)
+        for (int d = 0; d < 3; ++d) {
+          Sy[d].x += g.x * ya[q][d];
+          Sy[d].y += g.y * ya[q][d];
+        }
+    }
+    J00.x += wx * S.x;
+    J00.y += wx * S.y;
+    if (full)
+      for (int d = 0; d < 3; ++d) {
+        Jx[d].x += wx * xl[d] * S.x;
+        Jx[d].y += wx * xl[d] * S.y;
+        Jy[d].x += wx * Sy[d].x;
+        Jy[d].y += wx * Sy[d].y;
+        Jxy.x += wx * xl[d] * Sy[d].x;
+        Jxy.y += wx * xl[d] * Sy[d].y;
+      }
+  }
+  I0 = J00;
+  if (!full) return;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double a[3], b[3], ab = 0;
+      for (int d = 0; d < 3; ++d) {
+        a[d] = A.v[i][d] - A.c[d];
+        b[d] = B.v[j][d] - B.c[d];
+        ab += a[d] * b[d];
+      }
+      double2 v = Jxy;
+      for (int d = 0; d < 3; ++d) {
+        v.x -= a[d] * Jy[d].x + b[d] * Jx[d].x;
+        v.y -= a[d] * Jy[d].y + b[d] * Jx[d].y;
+      }
+      v.x += ab * J00.x;
+      v.y += ab * J00.y;
+      Ivv[3 * i + j] = v;
+    }
+}
+
+// Pair integrals of canonical triangles (ta, tb): I0 and (full) Ivv[9].
+__device__ void pair_integrals(const double* V, const int32_t* T, int ta, int tb, double k,
+                               bool full, double2& I0, double2* Ivv) {
+  TriG A, B;
+  load_tri(V, T, ta, A);
+  load_tri(V, T, tb, B);
+  if (!is_close(A, B)) {
+    pair_regular(A, B, k, full, I0, Ivv);
+    return;
+  }
+  double2 I0a, I0b, Ia[9], Ib[9];
+  pair_close_oriented(A, B, k, full, I0a, Ia);
+  pair_close_oriented(B, A, k, full, I0b, Ib);
+  I0 = make_double2(0.5 * (I0a.x + I0b.x), 0.5 * (I0a.y + I0b.y));
+  if (full)
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j)
+        Ivv[3 * i + j] = make_double2(0.5 * (Ia[3 * i + j].x + Ib[3 * j + i].x),
+                                      0.5 * (Ia[3 * i + j].y + Ib[3 * j + i].y));
+}
+
+__device__ __forceinline__ int64_t find_block(const int64_t* off, int64_t n, int64_t e) {
+  // largest j with off[j] <= e (off has n+1 entries, off[0] = 0)
+  int64_t lo = 0, hi = n;
+  while (hi - lo > 1) {
+    int64_t mid = (lo + hi) >> 1;
+    if (off[mid] <= e) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// ---------------------------------------------------------------- assembly
+// Triangle-pair integrals for the A blocks j in [j0, j1): pair (a, b) of the
+// triangle sets T_x x T_y; scratch[e] = {I0, Ivv[9]} (10 double2).
+__global__ void k_near_pairs_A(NearDev nd, int64_t j0, int64_t nblk, const int64_t* scr_off,
+                               double2* scratch, int64_t total) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= total) return;
+  int64_t jl = find_block(scr_off, nblk, e);
+  int64_t j = j0 + jl;
+  int32_t x = nd.blk_tgt[j], y = nd.near_src[j];
+  int64_t ny = nd.tset_ptr[y + 1] - nd.tset_ptr[y];
+  int64_t loc = e - scr_off[jl];
+  int64_t a = loc / ny, b = loc - a * ny;
+  int ta = nd.tset[nd.tset_ptr[x] + a];
+  int tb = nd.tset[nd.tset_ptr[y] + b];
+  double2 I0, Ivv[9];
+  pair_integrals(nd.V, nd.T, ta, tb, nd.k, true, I0, Ivv);
+  double2* out = scratch + 10 * e;
+  out[0] = I0;
+  for (int q = 0; q < 9; ++q) out[1 + q] = Ivv[q];
+}
+
+// A block entries from the pair scratch:
+// A[i][n] = sum_{s,t} coef_is coef_nt Ivv[(tl_is, tl_nt)][loc_is][loc_nt]
+__global__ void k_near_combine_A(NearDev nd, int64_t j0, int64_t nblk, const int64_t* scr_off,
+                                 const double2* scratch, int64_t e_begin, int64_t total) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= total) return;
+  int64_t eg = e_begin + e;
+  int64_t j = find_block(nd.blkA_off + j0, nblk, eg) + j0;
+  int32_t x = nd.blk_tgt[j], y = nd.near_src[j];
+  int64_t nyr = nd.box_rwg_ptr[y + 1] - nd.box_rwg_ptr[y];
+  int64_t loc = eg - nd.blkA_off[j];
+  int64_t r = loc / nyr, c = loc - r * nyr;
+  int64_t i = nd.box_rwg_ptr[x] + r, n = nd.box_rwg_ptr[y] + c;
+  int64_t nty = nd.tset_ptr[y + 1] - nd.tset_ptr[y];
+  const double2* scr = scratch + 10 * scr_off[j - j0];
+  double2 acc = make_double2(0, 0);
+  for (int s = 0; s < 2; ++s)
+    for (int t = 0; t < 2; ++t) {
+      int64_t pe = (int64_t)nd.rwg_tl[2 * i + s] * nty + nd.rwg_tl[2 * n + t];
+      double cf = nd.rwg_coef[2 * i + s] * nd.rwg_coef[2 * n + t];
+      double2 v = scr[10 * pe + 1 + 3 * nd.rwg_loc[2 * i + s] + nd.rwg_loc[2 * n + t]];
+      acc.x += cf * v.x;
+      acc.y += cf * v.y;
+    }
+  nd.A[eg] = acc;
+}
+
+// V block entries: V[a][b] = int int g / (a_a a_b) for sorted triangles
+__global__ void k_near_V(NearDev nd, int64_t e_begin, int64_t total) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= total) return;
+  int64_t eg = e_begin + e;
+  int64_t j = find_block(nd.blkV_off, nd.n_blocks, eg);
+  int32_t x = nd.blk_tgt[j], y = nd.near_src[j];
+  int64_t nyt = nd.box_tri_ptr[y + 1] - nd.box_tri_ptr[y];
+  int64_t loc = eg - nd.blkV_off[j];
+  int64_t a = loc / nyt, b = loc - a * nyt;
+  int ta = nd.tri_perm[nd.box_tri_ptr[x] + a];
+  int tb = nd.tri_perm[nd.box_tri_ptr[y] + b];
+  double2 I0, dummy[9];
+  pair_integrals(nd.V, nd.T, ta, tb, nd.k, false, I0, dummy);
+  double s = 1.0 / (nd.area[ta] * nd.area[tb]);
+  nd.Vn[eg] = make_double2(I0.x * s, I0.y * s);
+}
+
+// ---------------------------------------------------------------- SpMV
+// y[r][i] += sum_{blocks} M_blk[row][col] x[r][src_start + col]; one CTA per
+// target box, one warp per row, lanes over columns.  Sorted orders; x, y are
+// [R][n] c128 with leading dimension ld.
+template <int RMAX>
+__global__ void k_near_spmv(const double2* __restrict__ M, const int64_t* __restrict__ blk_off,
+                            const int64_t* __restrict__ near_ptr, const int32_t* __restrict__ near_src,
+                            const int64_t* __restrict__ box_ptr, const double2* __restrict__ x,
+                            double2* __restrict__ y, int64_t ld, int nr) {
+  int xb = blockIdx.x;
+  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  int64_t r0 = box_ptr[xb], nrow = box_ptr[xb + 1] - r0;
+  for (int64_t row = warp; row < nrow; row += nw) {
+    double2 acc[RMAX];
+#pragma unroll
+    for (int r = 0; r < RMAX; ++r) acc[r] = make_double2(0, 0);
+    for (int64_t j = near_ptr[xb]; j < near_ptr[xb + 1]; ++j) {
+      int32_t yb = near_src[j];
+      int64_t c0 = box_ptr[yb], ncol = box_ptr[yb + 1] - c0;
+      const double2* Mr = M + blk_off[j] + row * ncol;
+      for (int64_t c = lane; c < ncol; c += 32) {
+        double2 a = Mr[c];
+#pragma unroll
+        for (int r = 0; r < RMAX; ++r)
+          if (r < nr) cfma(acc[r], a, x[r * ld + c0 + c]);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < RMAX; ++r) {
+      if (r >= nr) break;
+      double2 v = acc[r];
+      for (int o = 16; o > 0; o >>= 1) {
+        v.x += __shfl_down_sync(0xffffffffu, v.x, o);
+        v.y += __shfl_down_sync(0xffffffffu, v.y, o);
+      }
+      if (lane == 0) {
+        double2 t = y[r * ld + r0 + row];
+        y[r * ld + r0 + row] = make_double2(t.x + v.x, t.y + v.y);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- launchers
+int near_upload_rules(const double* q3, const double* q4) {
+  if (cudaMemcpyToSymbol(c_q3, q3, sizeof(double) * 27) != cudaSuccess) return -1;
+  if (cudaMemcpyToSymbol(c_q4, q4, sizeof(double) * 48) != cudaSuccess) return -1;
+  return 0;
+}
+
+void launch_near_pairs_A(const NearDev& nd, int64_t j0, int64_t nblk, const int64_t* scr_off,
+                         double2* scratch, int64_t total, cudaStream_t s) {
+  if (total <= 0) return;
+  k_near_pairs_A<<<(unsigned)ceil_div(total, 128), 128, 0, s>>>(nd, j0, nblk, scr_off, scratch, total);
+}
+void launch_near_combine_A(const NearDev& nd, int64_t j0, int64_t nblk, const int64_t* scr_off,
+                           const double2* scratch, int64_t e_begin, int64_t total, cudaStream_t s) {
+  if (total <= 0) return;
+  k_near_combine_A<<<(unsigned)ceil_div(total, 256), 256, 0, s>>>(nd, j0, nblk, scr_off, scratch,
+                                                                    e_begin, total);
+}
+void launch_near_V(const NearDev& nd, int64_t e_begin, int64_t total, cudaStream_t s) {
+  if (total <= 0) return;
+  k_near_V<<<(unsigned)ceil_div(total, 128), 128, 0, s>>>(nd, e_begin, total);
+}
+void launch_near_spmv(const double2* M, const int64_t* blk_off, const int64_t* near_ptr,
+                      const int32_t* near_src, const int64_t* box_ptr, int64_t n_boxes,
+                      const double2* x, double2* y, int64_t ld, int nr, cudaStream_t s) {
+  if (n_boxes <= 0) return;
+  for (int r0 = 0; r0 < nr; r0 += 8) {
+    int cnt = nr - r0 < 8 ? nr - r0 : 8;
+    const double2* xr = x + (int64_t)r0 * ld;
+    double2* yr = y + (int64_t)r0 * ld;
+    if (cnt <= 1)
+      k_near_spmv<1><<<(unsigned)n_boxes, 256, 0, s>>>(M, blk_off, near_ptr, near_src, box_ptr, xr, yr, ld, cnt);
+    else if (cnt <= 4)
+      k_near_spmv<4><<<(unsigned)n_boxes, 256, 0, s>>>(M, blk_off, near_ptr, near_src, box_ptr, xr, yr, ld, cnt);
+    else
+      k_near_spmv<8><<<(unsigned)n_boxes, 256, 0, s>>>(M, blk_off, near_ptr, near_src, box_ptr, xr, yr, ld, cnt);
+  }
+}
+
+}  // namespace efie

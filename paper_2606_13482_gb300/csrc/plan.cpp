@@ -1,0 +1,884 @@
+// Host-side planning: geometry, octree, spline algebra, moments, lists.
+// See plan.hpp for the paper passages each part follows.
+#include "plan.hpp"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <unordered_map>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+namespace efie {
+
+static const int S_REMOVE[7] = {0, 0, 0, 1, 1, 2, 2};  // Table I, index p
+
+[[noreturn]] static void fail(int code, const std::string& m) { throw EfieError{code, m}; }
+
+// ------------------------------------------------------------------ geometry
+// Sec. II: RWG without edge-length normalization; c+ is the triangle whose CCW
+// cycle runs lo -> hi along the edge (lo < hi).
+static void build_geometry(Geometry& g, const double* xyz, int64_t nv, const int32_t* tri,
+                           int64_t nt) {
+  if (nv < 4 || nt < 4) fail(-1, "mesh too small");
+  g.nv = nv;
+  g.nt = nt;
+  g.V.assign(xyz, xyz + 3 * nv);
+  g.T.assign(tri, tri + 3 * nt);
+  g.area.resize(nt);
+  g.cen.resize(3 * nt);
+  for (int64_t t = 0; t < nt; ++t) {
+    for (int k = 0; k < 3; ++k)
+      if (g.T[3 * t + k] < 0 || g.T[3 * t + k] >= nv) fail(-1, "triangle vertex id out of range");
+    const double* a = &g.V[3 * g.T[3 * t]];
+    const double* b = &g.V[3 * g.T[3 * t + 1]];
+    const double* c = &g.V[3 * g.T[3 * t + 2]];
+    double e1[3], e2[3], n[3];
+    for (int d = 0; d < 3; ++d) {
+      e1[d] = b[d] - a[d];
+      e2[d] = c[d] - a[d];
+    }
+    n[0] = e1[1] * e2[2] - e1[2] * e2[1];
+    n[1] = e1[2] * e2[0] - e1[0] * e2[2];
+    n[2] = e1[0] * e2[1] - e1[1] * e2[0];
+    double nn = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+    if (!(nn > 1e-300)) fail(-1, "degenerate triangle " + std::to_string(t));
+    g.area[t] = 0.5 * nn;
+    for (int d = 0; d < 3; ++d) g.cen[3 * t + d] = (a[d] + b[d] + c[d]) / 3.0;
+  }
+  struct HalfEdge {
+    int64_t key;
+    int32_t t;
+    int32_t fwd;
+    int32_t w;
+  };
+  std::vector<HalfEdge> he(3 * nt);
+  for (int64_t t = 0; t < nt; ++t)
+    for (int k = 0; k < 3; ++k) {
+      int32_t u = g.T[3 * t + k], v = g.T[3 * t + (k + 1) % 3], w = g.T[3 * t + (k + 2) % 3];
+      int64_t lo = std::min(u, v), hi = std::max(u, v);
+      if (lo == hi) fail(-1, "repeated vertex in a triangle");
+      he[3 * t + k] = {lo * nv + hi, (int32_t)t, u < v ? 1 : 0, w};
+    }
+  std::sort(he.begin(), he.end(), [](const HalfEdge& a, const HalfEdge& b) {
+    return a.key != b.key ? a.key < b.key : a.t < b.t;
+  });
+  g.N = 0;
+  for (size_t i = 0; i < he.size();) {
+    size_t j = i;
+    while (j < he.size() && he[j].key == he[i].key) ++j;
+    if (j - i != 2) fail(-1, "mesh is not a closed 2-manifold (edge shared by " +
+                                 std::to_string(j - i) + " triangles)");
+    if (he[i].fwd == he[i + 1].fwd) fail(-1, "inconsistent triangle orientation");
+    const HalfEdge& pl = he[i].fwd ? he[i] : he[i + 1];
+    const HalfEdge& mi = he[i].fwd ? he[i + 1] : he[i];
+    g.edge.push_back((int32_t)(he[i].key / nv));
+    g.edge.push_back((int32_t)(he[i].key % nv));
+    g.tri_pm.push_back(pl.t);
+    g.tri_pm.push_back(mi.t);
+    g.free_pm.push_back(pl.w);
+    g.free_pm.push_back(mi.w);
+    ++g.N;
+    i = j;
+  }
+}
+
+// ------------------------------------------------------------------ splines
+std::vector<double> open_knots(double lo, double hi, int ns, int p) {
+  int m = ns - p;
+  std::vector<double> U;
+  for (int i = 0; i <= p; ++i) U.push_back(lo);
+  for (int i = 1; i < m; ++i) U.push_back(lo + (hi - lo) * i / m);
+  for (int i = 0; i <= p; ++i) U.push_back(hi);
+  return U;
+}
+
+// All B-splines of U at x (Cox-de Boor), spans half-open except the last
+// non-empty one (closed), so x = right end is covered.
+static void basis_all(const std::vector<double>& U, int p, double x, std::vector<double>& out) {
+  int nk = (int)U.size();
+  int last = -1;
+  for (int i = 0; i + 1 < nk; ++i)
+    if (U[i] < U[i + 1]) last = i;
+  std::vector<double> N(nk - 1, 0.0);
+  for (int i = 0; i + 1 < nk; ++i)
+    if (U[i] < U[i + 1]) {
+      bool in = (x >= U[i]) && (i == last ? x <= U[i + 1] : x < U[i + 1]);
+      N[i] = in ? 1.0 : 0.0;
+    }
+  for (int q = 1; q <= p; ++q) {
+    for (int i = 0; i + q + 1 < nk; ++i) {
+      double t = 0.0;
+      double d1 = U[i + q] - U[i];
+      if (d1 > 0) t += (x - U[i]) / d1 * N[i];
+      double d2 = U[i + q + 1] - U[i + 1];
+      if (d2 > 0) t += (U[i + q + 1] - x) / d2 * N[i + 1];
+      N[i] = t;
+    }
+  }
+  out.assign(N.begin(), N.begin() + (nk - p - 1));
+}
+
+// Boehm insertion (Sec. IV-B): with u_k <= ub < u_{k+1}, new coefficients
+// w_i' = a_i w_i + (1 - a_i) w_{i-1}, a_i = (ub - u_i)/(u_{i+p} - u_i) on
+// k-p+1..k, 1 below, 0 above.
+static void insert_knot(std::vector<double>& U, int p, std::vector<double>& w, double ub) {
+  int k = (int)(std::upper_bound(U.begin(), U.end(), ub) - U.begin()) - 1;
+  int n = (int)w.size();
+  std::vector<double> wb(n + 1);
+  for (int i = 0; i <= n; ++i) {
+    if (i <= k - p)
+      wb[i] = w[i];
+    else if (i >= k + 1)
+      wb[i] = w[i - 1];
+    else {
+      double a = (ub - U[i]) / (U[i + p] - U[i]);
+      wb[i] = a * w[i] + (1.0 - a) * w[i - 1];
+    }
+  }
+  U.insert(U.begin() + k + 1, ub);
+  w.swap(wb);
+}
+
+static void refine_to(std::vector<double>& U, int p, std::vector<double>& w,
+                      const std::vector<double>& target) {
+  std::vector<double> t = target;
+  std::sort(t.begin(), t.end());
+  for (size_t i = 0; i < t.size();) {
+    size_t j = i;
+    while (j < t.size() && t[j] == t[i]) ++j;
+    long need = (long)(j - i) - (long)std::count(U.begin(), U.end(), t[i]);
+    for (long r = 0; r < need; ++r) insert_knot(U, p, w, t[i]);
+    i = j;
+  }
+}
+
+std::vector<double> restriction_matrix(const std::vector<double>& Up,
+                                       const std::vector<double>& Uc, int p, int* rows,
+                                       int* cols) {
+  double a = Uc.front(), b = Uc.back();
+  int nsp = (int)Up.size() - p - 1, nsc = (int)Uc.size() - p - 1;
+  std::vector<double> target;
+  for (double t : Up)
+    if (t < a || t > b) target.push_back(t);
+  for (double t : Uc) target.push_back(t);
+  std::vector<double> C((size_t)nsp * nsc);
+  for (int j = 0; j < nsp; ++j) {
+    std::vector<double> U = Up, w(nsp, 0.0);
+    w[j] = 1.0;
+    refine_to(U, p, w, target);
+    int k0 = (int)(std::lower_bound(U.begin(), U.end(), a) - U.begin());
+    for (int i = 0; i < nsc + p + 1; ++i)
+      if (U[k0 + i] != Uc[i]) fail(-1, "child knots not nested in the parent knot vector");
+    for (int i = 0; i < nsc; ++i) C[(size_t)j * nsc + i] = w[k0 + i];
+  }
+  *rows = nsp;
+  *cols = nsc;
+  return C;
+}
+
+// Dense LU with partial pivoting: solves A X = B in place (A n x n, B n x m).
+static void lu_solve(std::vector<double> A, int n, std::vector<double>& B, int m) {
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < n; ++r)
+      if (std::fabs(A[(size_t)r * n + c]) > std::fabs(A[(size_t)piv * n + c])) piv = r;
+    if (A[(size_t)piv * n + c] == 0.0) fail(-1, "singular sampling matrix");
+    if (piv != c) {
+      for (int k = 0; k < n; ++k) std::swap(A[(size_t)c * n + k], A[(size_t)piv * n + k]);
+      for (int k = 0; k < m; ++k) std::swap(B[(size_t)c * m + k], B[(size_t)piv * m + k]);
+    }
+    for (int r = c + 1; r < n; ++r) {
+      double f = A[(size_t)r * n + c] / A[(size_t)c * n + c];
+      if (f == 0.0) continue;
+      for (int k = c; k < n; ++k) A[(size_t)r * n + k] -= f * A[(size_t)c * n + k];
+      for (int k = 0; k < m; ++k) B[(size_t)r * m + k] -= f * B[(size_t)c * m + k];
+    }
+  }
+  for (int c = n - 1; c >= 0; --c) {
+    for (int k = 0; k < m; ++k) {
+      double s = B[(size_t)c * m + k];
+      for (int j = c + 1; j < n; ++j) s -= A[(size_t)c * n + j] * B[(size_t)j * m + k];
+      B[(size_t)c * m + k] = s / A[(size_t)c * n + c];
+    }
+  }
+}
+
+// P = B_stab^{-1} S (Sec. V-B): stabilized knots drop the first and last
+// s_remove interior knots; S by knot insertion; B_stab[m][k] = b_m(x_k) at s_hat
+// equispaced points including both domain ends.
+static void projector(int sp, int p, std::vector<double>& P, int* shat_out) {
+  std::vector<double> Ue = open_knots(0.0, (double)(sp - p), sp, p);
+  int r = S_REMOVE[p];
+  std::vector<double> Us;
+  for (int i = 0; i <= p; ++i) Us.push_back(Ue.front());
+  for (size_t i = p + 1 + r; i + p + 1 + r < Ue.size(); ++i) Us.push_back(Ue[i]);
+  for (int i = 0; i <= p; ++i) Us.push_back(Ue.back());
+  int ns = (int)Us.size() - p - 1;
+  // S[j][i]: equidistant coefficients of stabilized spline j
+  std::vector<double> S((size_t)ns * sp);
+  for (int j = 0; j < ns; ++j) {
+    std::vector<double> U = Us, w(ns, 0.0);
+    w[j] = 1.0;
+    refine_to(U, p, w, Ue);
+    for (int i = 0; i < sp; ++i) S[(size_t)j * sp + i] = w[i];
+  }
+  std::vector<double> B((size_t)ns * ns), row;
+  for (int kk = 0; kk < ns; ++kk) {
+    double x = Ue.front() + (Ue.back() - Ue.front()) * kk / (ns - 1);
+    basis_all(Us, p, x, row);
+    for (int m = 0; m < ns; ++m) B[(size_t)m * ns + kk] = row[m];
+  }
+  lu_solve(B, ns, S, sp);
+  P = S;
+  *shat_out = ns;
+}
+
+void gauss_legendre01(int n, std::vector<double>& x, std::vector<double>& w) {
+  // Newton iteration on the Legendre polynomial P_n (three-term recurrence)
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  const double pi = 3.14159265358979323846;
+  for (int i = 0; i < n; ++i) {
+    double z = std::cos(pi * (i + 0.75) / (n + 0.5));
+    double dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      double pn = (n == 1) ? z : p1;
+      double pm = (n == 1) ? 1.0 : p0;
+      dp = n * (z * pn - pm) / (z * z - 1.0);
+      double dz = pn / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      double pn = (n == 1) ? z : p1;
+      double pm = (n == 1) ? 1.0 : p0;
+      dp = n * (z * pn - pm) / (z * z - 1.0);
+    }
+    x[n - 1 - i] = 0.5 * (z + 1.0);
+    w[n - 1 - i] = 1.0 / ((1.0 - z * z) * dp * dp);  // (2/((1-z^2)P'^2)) / 2
+  }
+  std::vector<int> idx(n);
+  std::iota(idx.begin(), idx.end(), 0);
+  std::sort(idx.begin(), idx.end(), [&](int a, int b) { return x[a] < x[b]; });
+  std::vector<double> xs(n), ws(n);
+  for (int i = 0; i < n; ++i) {
+    xs[i] = x[idx[i]];
+    ws[i] = w[idx[i]];
+  }
+  x.swap(xs);
+  w.swap(ws);
+}
+
+// ------------------------------------------------------------------ octree
+static uint64_t spread3(uint64_t v) {
+  v &= 0x1fffff;
+  v = (v | v << 32) & 0x1f00000000ffffULL;
+  v = (v | v << 16) & 0x1f0000ff0000ffULL;
+  v = (v | v << 8) & 0x100f00f00f00f00fULL;
+  v = (v | v << 4) & 0x10c30c30c30c30c3ULL;
+  v = (v | v << 2) & 0x1249249249249249ULL;
+  return v;
+}
+static uint64_t morton(int64_t i, int64_t j, int64_t k) {
+  return spread3((uint64_t)i) | (spread3((uint64_t)j) << 1) | (spread3((uint64_t)k) << 2);
+}
+static int64_t find_code(const std::vector<uint64_t>& codes, uint64_t c) {
+  auto it = std::lower_bound(codes.begin(), codes.end(), c);
+  if (it == codes.end() || *it != c) return -1;
+  return it - codes.begin();
+}
+
+static void box_of(const Plan& P, const double* x, int level, int64_t* ijk) {
+  double h = P.root_edge / (double)(1LL << level);
+  int64_t nb = 1LL << level;
+  for (int d = 0; d < 3; ++d) {
+    int64_t i = (int64_t)std::floor((x[d] - P.root_lo[d]) / h);
+    ijk[d] = std::min<int64_t>(std::max<int64_t>(i, 0), nb - 1);
+  }
+}
+
+// ------------------------------------------------------------------ moments
+namespace {
+struct Poly {
+  int n = 0;
+  double v[24][3];
+};
+
+void split(const Poly& P, int axis, double val, Poly& L, Poly& R) {
+  L.n = R.n = 0;
+  for (int i = 0; i < P.n; ++i) {
+    const double* a = P.v[i];
+    const double* b = P.v[(i + 1) % P.n];
+    double sa = a[axis] - val, sb = b[axis] - val;
+    if (sa <= 0) { std::memcpy(L.v[L.n++], a, sizeof(double) * 3); }
+    if (sa >= 0) { std::memcpy(R.v[R.n++], a, sizeof(double) * 3); }
+    if ((sa < 0 && sb > 0) || (sb < 0 && sa > 0)) {
+      double t = sa / (sa - sb);
+      double x[3];
+      for (int d = 0; d < 3; ++d) x[d] = a[d] + t * (b[d] - a[d]);
+      x[axis] = val;
+      std::memcpy(L.v[L.n++], x, sizeof(x));
+      std::memcpy(R.v[R.n++], x, sizeof(x));
+    }
+  }
+}
+
+struct LeafKnots {
+  int p, sp;
+  double lo[3], delta;
+  std::vector<double> U[3];
+};
+
+int find_span(const std::vector<double>& U, int p, int ns, double x) {
+  if (x >= U[ns]) return ns - 1;
+  if (x <= U[p]) return p;
+  int lo = p, hi = ns;
+  while (hi - lo > 1) {
+    int mid = (lo + hi) / 2;
+    if (x < U[mid]) hi = mid; else lo = mid;
+  }
+  return lo;
+}
+
+// nonzero B-splines i-p..i at x in span i (triangular recursion)
+void basis_nz(const std::vector<double>& U, int p, int i, double x, double* N) {
+  double left[8], right[8];
+  N[0] = 1.0;
+  for (int j = 1; j <= p; ++j) {
+    left[j] = x - U[i + 1 - j];
+    right[j] = U[i + j] - x;
+    double saved = 0.0;
+    for (int r = 0; r < j; ++r) {
+      double tmp = N[r] / (right[r + 1] + left[j - r]);
+      N[r] = saved + right[r + 1] * tmp;
+      saved = left[j - r] * tmp;
+    }
+    N[j] = saved;
+  }
+}
+
+// Integrate sum_q w_q f_c(x_q) l_i(x_q) over one triangle (clipped by knot
+// planes) into block[ncomp][e0][e1][e2] at base. f: RWG (ncomp 3) or pulse.
+void integrate_triangle(const LeafKnots& K, const double* tv, int ncomp, const double* xfree,
+                        double scale, const int* base, const int* ext, double* block,
+                        const std::vector<double>& qx, const std::vector<double>& qw) {
+  const int p = K.p, sp = K.sp;
+  std::vector<Poly> pieces(1);
+  pieces[0].n = 3;
+  for (int a = 0; a < 3; ++a)
+    for (int d = 0; d < 3; ++d) pieces[0].v[a][d] = tv[3 * a + d];
+  for (int axis = 0; axis < 3; ++axis) {
+    for (int kk = p + 1; kk < sp; ++kk) {
+      double val = K.U[axis][kk];
+      std::vector<Poly> nxt;
+      for (const Poly& P : pieces) {
+        double mn = 1e300, mx = -1e300;
+        for (int i = 0; i < P.n; ++i) {
+          mn = std::min(mn, P.v[i][axis]);
+          mx = std::max(mx, P.v[i][axis]);
+        }
+        if (mn < val && val < mx) {
+          Poly L, R;
+          split(P, axis, val, L, R);
+          if (L.n >= 3) nxt.push_back(L);
+          if (R.n >= 3) nxt.push_back(R);
+        } else {
+          nxt.push_back(P);
+        }
+      }
+      pieces.swap(nxt);
+    }
+  }
+  const int nq = (int)qx.size();
+  const int e0 = ext[0], e1 = ext[1], e2 = ext[2];
+  double N0[8], N1[8], N2[8];
+  for (const Poly& P : pieces) {
+    for (int f = 1; f + 1 < P.n; ++f) {
+      const double* A = P.v[0];
+      const double* B = P.v[f];
+      const double* C = P.v[f + 1];
+      double u[3], v[3];
+      for (int d = 0; d < 3; ++d) {
+        u[d] = B[d] - A[d];
+        v[d] = C[d] - A[d];
+      }
+      double cx = u[1] * v[2] - u[2] * v[1], cy = u[2] * v[0] - u[0] * v[2],
+             cz = u[0] * v[1] - u[1] * v[0];
+      double twoa = std::sqrt(cx * cx + cy * cy + cz * cz);
+      if (!(twoa > 0)) continue;
+      for (int a = 0; a < nq; ++a)
+        for (int b = 0; b < nq; ++b) {
+          double xi = qx[a], eta = qx[b] * (1.0 - qx[a]);
+          double w = qw[a] * qw[b] * (1.0 - qx[a]) * twoa * scale;
+          double x[3];
+          for (int d = 0; d < 3; ++d) x[d] = A[d] + xi * u[d] + eta * v[d];
+          int s0 = find_span(K.U[0], p, sp, x[0]);
+          int s1 = find_span(K.U[1], p, sp, x[1]);
+          int s2 = find_span(K.U[2], p, sp, x[2]);
+          basis_nz(K.U[0], p, s0, x[0], N0);
+          basis_nz(K.U[1], p, s1, x[1], N1);
+          basis_nz(K.U[2], p, s2, x[2], N2);
+          double fv[3];
+          if (ncomp == 3)
+            for (int d = 0; d < 3; ++d) fv[d] = w * (x[d] - xfree[d]);
+          else
+            fv[0] = w;
+          for (int i0 = 0; i0 <= p; ++i0) {
+            int g0 = s0 - p + i0 - base[0];
+            if (g0 < 0 || g0 >= e0) continue;
+            for (int i1 = 0; i1 <= p; ++i1) {
+              int g1 = s1 - p + i1 - base[1];
+              if (g1 < 0 || g1 >= e1) continue;
+              double n01 = N0[i0] * N1[i1];
+              for (int i2 = 0; i2 <= p; ++i2) {
+                int g2 = s2 - p + i2 - base[2];
+                if (g2 < 0 || g2 >= e2) continue;
+                double bb = n01 * N2[i2];
+                size_t o = ((size_t)g0 * e1 + g1) * e2 + g2;
+                for (int c = 0; c < ncomp; ++c) block[(size_t)c * e0 * e1 * e2 + o] += fv[c] * bb;
+              }
+            }
+          }
+        }
+    }
+  }
+}
+}  // namespace
+
+// ------------------------------------------------------------------ build
+void build_plan(Plan& P, const double* xyz, int64_t nv, const int32_t* tri, int64_t nt,
+                double k, int p, double grid_spacing, int levels, int n_splines,
+                bool with_moments) {
+  if (!(k > 0) || !std::isfinite(k)) fail(-1, "wavenumber must be positive");
+  if (p < 1 || p > 6) fail(-1, "spline degree p must be in 1..6");
+  if (!(grid_spacing > 0)) fail(-1, "grid spacing must be positive");
+  build_geometry(P.g, xyz, nv, tri, nt);
+  Geometry& g = P.g;
+  P.k = k;
+  P.p = p;
+  const int s0 = n_splines > 0 ? n_splines : p + 4;
+  if (s0 <= p) fail(-1, "n_splines must exceed p");
+  const double delta = grid_spacing;
+  const double h_leaf = (s0 - p) * delta;
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  for (int64_t v = 0; v < nv; ++v)
+    for (int d = 0; d < 3; ++d) {
+      lo[d] = std::min(lo[d], g.V[3 * v + d]);
+      hi[d] = std::max(hi[d], g.V[3 * v + d]);
+    }
+  double edge = std::max(hi[0] - lo[0], std::max(hi[1] - lo[1], hi[2] - lo[2]));
+  int D = 0;
+  while (h_leaf * (double)(1LL << D) < edge) {
+    ++D;
+    if (D > 20) fail(-1, "grid spacing too small for the mesh extent");
+  }
+  if (levels < 1 || levels > D + 1) fail(-1, "levels must be in 1..depth+1 (depth " + std::to_string(D) + ")");
+  P.D = D;
+  P.top = D - levels + 1;
+  P.n_levels = levels;
+  P.root_edge = h_leaf * (double)(1LL << D);
+  for (int d = 0; d < 3; ++d) P.root_lo[d] = (lo[d] + hi[d]) * 0.5 - P.root_edge * 0.5;
+  const double lam = 2.0 * 3.14159265358979323846 / k;
+
+  // leaf boxes of basis functions
+  const int64_t N = g.N;
+  std::vector<int64_t> rijk(3 * N), tijk(3 * nt);
+  for (int64_t m = 0; m < N; ++m) {
+    double mid[3];
+    for (int d = 0; d < 3; ++d) mid[d] = (g.V[3 * g.edge[2 * m] + d] + g.V[3 * g.edge[2 * m + 1] + d]) * 0.5;
+    box_of(P, mid, D, &rijk[3 * m]);
+  }
+  for (int64_t t = 0; t < nt; ++t) box_of(P, &g.cen[3 * t], D, &tijk[3 * t]);
+  // maximum protrusion (Sec. III-B)
+  double prot = 0.0;
+  auto upd = [&](const int64_t* ijk, const int32_t* verts, int nvv) {
+    for (int d = 0; d < 3; ++d) {
+      double blo = P.root_lo[d] + ijk[d] * h_leaf;
+      double bhi = blo + h_leaf;
+      for (int a = 0; a < nvv; ++a) {
+        double x = g.V[3 * verts[a] + d];
+        prot = std::max(prot, std::max(blo - x, 0.0));
+        prot = std::max(prot, std::max(x - bhi, 0.0));
+      }
+    }
+  };
+  for (int64_t m = 0; m < N; ++m) {
+    int32_t vv[6];
+    for (int a = 0; a < 3; ++a) {
+      vv[a] = g.T[3 * g.tri_pm[2 * m] + a];
+      vv[3 + a] = g.T[3 * g.tri_pm[2 * m + 1] + a];
+    }
+    upd(&rijk[3 * m], vv, 6);
+  }
+  for (int64_t t = 0; t < nt; ++t) upd(&tijk[3 * t], &g.T[3 * t], 3);
+  const int sb0 = (int)std::ceil(prot / delta);
+
+  // per-level parameters (Sec. IV-C constant s, Sec. IV-D increasing s)
+  P.lv.assign(levels, Level());
+  {
+    int s = s0, sb = sb0;
+    double dl = delta;
+    for (int ell = D; ell >= P.top; --ell) {
+      double h = P.root_edge / (double)(1LL << ell);
+      if (ell < D) {
+        if (h < 0.5 * lam) {
+          sb = (sb + 1) / 2;
+          dl = dl * 2.0;
+        } else {
+          s = 2 * s - p;
+        }
+      }
+      if (2 * sb >= s - p)
+        fail(-1, "grid spacing too small for the mesh: " + std::to_string(sb) +
+                     " buffer splines leave no gap between far interpolation domains");
+      Level& L = P.L(ell);
+      L.level = ell;
+      L.h = h;
+      L.s = s;
+      L.sb = sb;
+      L.sp = s + 2 * sb;
+      L.delta = dl;
+      projector(L.sp, p, L.P, &L.shat);
+      if (L.shat <= p) fail(-1, "too few splines after stabilization");
+      L.Delta = (L.sp - p) * dl / (L.shat - 1);
+      L.nfft = 2 * L.shat - 1;
+    }
+  }
+  // occupied boxes per level in Morton order
+  {
+    std::vector<uint64_t> codes;
+    codes.reserve(N + nt);
+    for (int64_t m = 0; m < N; ++m) codes.push_back(morton(rijk[3 * m], rijk[3 * m + 1], rijk[3 * m + 2]));
+    for (int64_t t = 0; t < nt; ++t) codes.push_back(morton(tijk[3 * t], tijk[3 * t + 1], tijk[3 * t + 2]));
+    std::sort(codes.begin(), codes.end());
+    codes.erase(std::unique(codes.begin(), codes.end()), codes.end());
+    for (int ell = D; ell >= P.top; --ell) {
+      Level& L = P.L(ell);
+      L.code = codes;
+      L.ijk.resize(3 * codes.size());
+      for (size_t b = 0; b < codes.size(); ++b) {
+        uint64_t c = codes[b];
+        int64_t ii[3] = {0, 0, 0};
+        for (int bit = 0; bit < 21; ++bit)
+          for (int d = 0; d < 3; ++d) ii[d] |= (int64_t)((c >> (3 * bit + d)) & 1) << bit;
+        for (int d = 0; d < 3; ++d) L.ijk[3 * b + d] = ii[d];
+      }
+      for (auto& c : codes) c >>= 3;
+      codes.erase(std::unique(codes.begin(), codes.end()), codes.end());
+    }
+    for (int ell = D; ell >= P.top; --ell) {
+      Level& L = P.L(ell);
+      size_t B = L.code.size();
+      L.parent.assign(B, -1);
+      if (ell > P.top) {
+        const Level& U = P.L(ell - 1);
+        for (size_t b = 0; b < B; ++b) L.parent[b] = find_code(U.code, L.code[b] >> 3);
+      }
+      if (ell < D) {
+        const Level& C = P.L(ell + 1);
+        L.child_ptr.assign(B + 1, 0);
+        for (size_t c = 0; c < C.code.size(); ++c) L.child_ptr[C.parent[c] + 1]++;
+        for (size_t b = 0; b < B; ++b) L.child_ptr[b + 1] += L.child_ptr[b];
+      }
+    }
+  }
+  // interaction lists per grid level
+  for (int ell = D; ell >= P.top; --ell) {
+    Level& L = P.L(ell);
+    size_t B = L.code.size();
+    std::unordered_map<int64_t, int32_t> off_id;
+    std::vector<std::vector<std::pair<int32_t, int64_t>>> lists(B);
+    auto key_of = [](int64_t dx, int64_t dy, int64_t dz) {
+      return ((dx + (1LL << 20)) << 42) | ((dy + (1LL << 20)) << 21) | (dz + (1LL << 20));
+    };
+    for (size_t x = 0; x < B; ++x) {
+      const int64_t* xi = &L.ijk[3 * x];
+      auto consider = [&](int64_t y) {
+        const int64_t* yi = &L.ijk[3 * y];
+        int64_t dx = xi[0] - yi[0], dy = xi[1] - yi[1], dz = xi[2] - yi[2];
+        if (std::max(std::llabs(dx), std::max(std::llabs(dy), std::llabs(dz))) < 2) return;
+        lists[x].push_back({(int32_t)y, key_of(dx, dy, dz)});
+      };
+      if (ell == P.top) {
+        for (size_t y = 0; y < B; ++y) consider((int64_t)y);
+      } else {
+        const Level& U = P.L(ell - 1);
+        int64_t pb = L.parent[x];
+        const int64_t* pi = &U.ijk[3 * pb];
+        int64_t nb = 1LL << (ell - 1);
+        for (int a = -1; a <= 1; ++a)
+          for (int b = -1; b <= 1; ++b)
+            for (int c = -1; c <= 1; ++c) {
+              int64_t q[3] = {pi[0] + a, pi[1] + b, pi[2] + c};
+              if (q[0] < 0 || q[1] < 0 || q[2] < 0 || q[0] >= nb || q[1] >= nb || q[2] >= nb) continue;
+              int64_t qb = find_code(U.code, morton(q[0], q[1], q[2]));
+              if (qb < 0) continue;
+              for (int64_t y = U.child_ptr[qb]; y < U.child_ptr[qb + 1]; ++y) consider(y);
+            }
+      }
+      std::sort(lists[x].begin(), lists[x].end());
+    }
+    std::vector<int64_t> keys;
+    for (auto& l : lists)
+      for (auto& e : l) keys.push_back(e.second);
+    std::sort(keys.begin(), keys.end());
+    keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
+    L.offsets.resize(3 * keys.size());
+    for (size_t i = 0; i < keys.size(); ++i) {
+      off_id[keys[i]] = (int32_t)i;
+      L.offsets[3 * i] = (int32_t)((keys[i] >> 42) - (1LL << 20));
+      L.offsets[3 * i + 1] = (int32_t)(((keys[i] >> 21) & ((1LL << 21) - 1)) - (1LL << 20));
+      L.offsets[3 * i + 2] = (int32_t)((keys[i] & ((1LL << 21) - 1)) - (1LL << 20));
+    }
+    L.il_ptr.assign(B + 1, 0);
+    for (size_t x = 0; x < B; ++x) {
+      L.il_ptr[x + 1] = L.il_ptr[x] + (int64_t)lists[x].size();
+      for (auto& e : lists[x]) {
+        L.il_src.push_back(e.first);
+        L.il_off.push_back(off_id[e.second]);
+      }
+    }
+  }
+  // transfer matrices C^L, C^R (child level ell -> ell-1), lattice units of
+  // the child knot spacing (Sec. IV-B)
+  for (int ell = D; ell > P.top; --ell) {
+    Level& c = P.L(ell);
+    const Level& pa = P.L(ell - 1);
+    int r = (int)std::lround(pa.delta / c.delta);
+    std::vector<double> Up = open_knots(-pa.sb * r, (pa.s - p + pa.sb) * r, pa.sp, p);
+    std::vector<double> UcL = open_knots(-c.sb, (c.s - p) + c.sb, c.sp, p);
+    std::vector<double> UcR = open_knots((c.s - p) - c.sb, 2 * (c.s - p) + c.sb, c.sp, p);
+    int rr, cc;
+    c.CL = restriction_matrix(Up, UcL, p, &rr, &cc);
+    c.CR = restriction_matrix(Up, UcR, p, &rr, &cc);
+  }
+  // DFT-fused projector matrices (n = 2 s_hat - 1)
+  const double twopi = 2.0 * 3.14159265358979323846;
+  for (int ell = D; ell >= P.top; --ell) {
+    Level& L = P.L(ell);
+    int n = L.nfft, ns = L.shat, sp = L.sp;
+    L.Fn.resize((size_t)n * n);
+    for (int f = 0; f < n; ++f)
+      for (int t = 0; t < n; ++t) {
+        long ft = ((long)f * t) % n;
+        double ang = -twopi * (double)ft / n;
+        L.Fn[(size_t)f * n + t] = cplx(std::cos(ang), std::sin(ang));
+      }
+    L.Mf.assign((size_t)n * sp, cplx(0, 0));
+    for (int f = 0; f < n; ++f)
+      for (int i = 0; i < sp; ++i) {
+        cplx acc(0, 0);
+        for (int t = 0; t < ns; ++t) acc += L.Fn[(size_t)f * n + t] * L.P[(size_t)t * sp + i];
+        L.Mf[(size_t)f * sp + i] = acc;
+      }
+    L.Mb.assign((size_t)sp * n, cplx(0, 0));
+    for (int i = 0; i < sp; ++i)
+      for (int f = 0; f < n; ++f) {
+        cplx acc(0, 0);
+        for (int t = 0; t < ns; ++t) acc += L.P[(size_t)t * sp + i] * std::conj(L.Fn[(size_t)f * n + t]);
+        L.Mb[(size_t)i * n + f] = acc / (double)n;
+      }
+  }
+
+  // sorted basis-function order (by leaf box)
+  const Level& LD = P.L(D);
+  const size_t BD = LD.code.size();
+  {
+    std::vector<std::pair<int64_t, int32_t>> kk(N);
+    for (int64_t m = 0; m < N; ++m)
+      kk[m] = {find_code(LD.code, morton(rijk[3 * m], rijk[3 * m + 1], rijk[3 * m + 2])), (int32_t)m};
+    std::sort(kk.begin(), kk.end());
+    P.rwg_perm.resize(N);
+    P.rwg_box.resize(N);
+    P.box_rwg_ptr.assign(BD + 1, 0);
+    for (int64_t i = 0; i < N; ++i) {
+      P.rwg_perm[i] = kk[i].second;
+      P.rwg_box[i] = (int32_t)kk[i].first;
+      P.box_rwg_ptr[kk[i].first + 1]++;
+    }
+    for (size_t b = 0; b < BD; ++b) P.box_rwg_ptr[b + 1] += P.box_rwg_ptr[b];
+    std::vector<std::pair<int64_t, int32_t>> tt(nt);
+    for (int64_t t = 0; t < nt; ++t)
+      tt[t] = {find_code(LD.code, morton(tijk[3 * t], tijk[3 * t + 1], tijk[3 * t + 2])), (int32_t)t};
+    std::sort(tt.begin(), tt.end());
+    P.tri_perm.resize(nt);
+    P.tri_box.resize(nt);
+    P.tri_rank.resize(nt);
+    P.box_tri_ptr.assign(BD + 1, 0);
+    for (int64_t i = 0; i < nt; ++i) {
+      P.tri_perm[i] = tt[i].second;
+      P.tri_box[i] = (int32_t)tt[i].first;
+      P.tri_rank[tt[i].second] = (int32_t)i;
+      P.box_tri_ptr[tt[i].first + 1]++;
+    }
+    for (size_t b = 0; b < BD; ++b) P.box_tri_ptr[b + 1] += P.box_tri_ptr[b];
+    P.rwg_tri_sorted.resize(2 * N);
+    for (int64_t i = 0; i < N; ++i)
+      for (int s = 0; s < 2; ++s) P.rwg_tri_sorted[2 * i + s] = P.tri_rank[g.tri_pm[2 * P.rwg_perm[i] + s]];
+  }
+  // near lists and block offsets
+  {
+    P.near_ptr.assign(BD + 1, 0);
+    P.near_src.clear();
+    int64_t nb = 1LL << D;
+    for (size_t x = 0; x < BD; ++x) {
+      const int64_t* xi = &LD.ijk[3 * x];
+      std::vector<int32_t> l;
+      for (int a = -1; a <= 1; ++a)
+        for (int b = -1; b <= 1; ++b)
+          for (int c = -1; c <= 1; ++c) {
+            int64_t q[3] = {xi[0] + a, xi[1] + b, xi[2] + c};
+            if (q[0] < 0 || q[1] < 0 || q[2] < 0 || q[0] >= nb || q[1] >= nb || q[2] >= nb) continue;
+            int64_t y = find_code(LD.code, morton(q[0], q[1], q[2]));
+            if (y >= 0) l.push_back((int32_t)y);
+          }
+      std::sort(l.begin(), l.end());
+      for (int32_t y : l) P.near_src.push_back(y);
+      P.near_ptr[x + 1] = (int64_t)P.near_src.size();
+    }
+    size_t nblk = P.near_src.size();
+    P.blkA_off.assign(nblk + 1, 0);
+    P.blkV_off.assign(nblk + 1, 0);
+    for (size_t x = 0; x < BD; ++x)
+      for (int64_t j = P.near_ptr[x]; j < P.near_ptr[x + 1]; ++j) {
+        int32_t y = P.near_src[j];
+        int64_t na = (P.box_rwg_ptr[x + 1] - P.box_rwg_ptr[x]) * (P.box_rwg_ptr[y + 1] - P.box_rwg_ptr[y]);
+        int64_t nvv = (P.box_tri_ptr[x + 1] - P.box_tri_ptr[x]) * (P.box_tri_ptr[y + 1] - P.box_tri_ptr[y]);
+        P.blkA_off[j + 1] = P.blkA_off[j] + na;
+        P.blkV_off[j + 1] = P.blkV_off[j] + nvv;
+      }
+    P.nnzA = P.blkA_off[nblk];
+    P.nnzV = P.blkV_off[nblk];
+    // triangle sets of RWGs per box, local indices, coefficients sigma/(2a)
+    P.tset_ptr.assign(BD + 1, 0);
+    P.tset.clear();
+    P.rwg_tl.assign(2 * N, 0);
+    P.rwg_loc.assign(2 * N, 0);
+    P.rwg_coef.assign(2 * N, 0.0);
+    for (size_t b = 0; b < BD; ++b) {
+      std::vector<int32_t> ts;
+      for (int64_t i = P.box_rwg_ptr[b]; i < P.box_rwg_ptr[b + 1]; ++i)
+        for (int s = 0; s < 2; ++s) ts.push_back(g.tri_pm[2 * P.rwg_perm[i] + s]);
+      std::sort(ts.begin(), ts.end());
+      ts.erase(std::unique(ts.begin(), ts.end()), ts.end());
+      for (int64_t i = P.box_rwg_ptr[b]; i < P.box_rwg_ptr[b + 1]; ++i) {
+        int32_t m = P.rwg_perm[i];
+        for (int s = 0; s < 2; ++s) {
+          int32_t t = g.tri_pm[2 * m + s];
+          P.rwg_tl[2 * i + s] = (int32_t)(std::lower_bound(ts.begin(), ts.end(), t) - ts.begin());
+          int32_t fv = g.free_pm[2 * m + s];
+          int loc = 0;
+          for (int a = 0; a < 3; ++a)
+            if (g.T[3 * t + a] == fv) loc = a;
+          P.rwg_loc[2 * i + s] = loc;
+          P.rwg_coef[2 * i + s] = (s == 0 ? 1.0 : -1.0) / (2.0 * g.area[t]);
+        }
+      }
+      for (int32_t t : ts) P.tset.push_back(t);
+      P.tset_ptr[b + 1] = (int64_t)P.tset.size();
+    }
+  }
+  if (!with_moments) return;
+
+  // exact moments (Q10): collapsed Gauss rule of degree >= 3p+1 per piece
+  {
+    std::vector<double> qx, qw;
+    gauss_legendre01((3 * p + 4) / 2, qx, qw);
+    const int sp = LD.sp;
+    auto knots_of = [&](int64_t b, LeafKnots& K) {
+      K.p = p;
+      K.sp = sp;
+      K.delta = LD.delta;
+      for (int d = 0; d < 3; ++d) {
+        K.lo[d] = P.root_lo[d] + LD.ijk[3 * b + d] * LD.h - LD.sb * LD.delta;
+        K.U[d] = open_knots(K.lo[d], K.lo[d] + (sp - p) * LD.delta, sp, p);
+      }
+    };
+    auto extents = [&](const LeafKnots& K, const int32_t* verts, int nvv, int* base, int* ext) {
+      for (int d = 0; d < 3; ++d) {
+        double mn = 1e300, mx = -1e300;
+        for (int a = 0; a < nvv; ++a) {
+          mn = std::min(mn, g.V[3 * verts[a] + d]);
+          mx = std::max(mx, g.V[3 * verts[a] + d]);
+        }
+        int a0 = find_span(K.U[d], p, sp, mn) - p;
+        int a1 = find_span(K.U[d], p, sp, mx);
+        a0 = std::max(a0, 0);
+        a1 = std::min(a1, sp - 1);
+        base[d] = a0;
+        ext[d] = a1 - a0 + 1;
+      }
+    };
+    // RWG blocks (sorted order)
+    MomentBlocks& MR = P.mom_rwg;
+    MR.base.assign(3 * N, 0);
+    MR.ext.assign(3 * N, 0);
+    MR.off.assign(N + 1, 0);
+    std::vector<LeafKnots> kcache(BD);
+    for (size_t b = 0; b < BD; ++b) knots_of((int64_t)b, kcache[b]);
+    for (int64_t i = 0; i < N; ++i) {
+      int32_t m = P.rwg_perm[i];
+      int32_t vv[6];
+      for (int a = 0; a < 3; ++a) {
+        vv[a] = g.T[3 * g.tri_pm[2 * m] + a];
+        vv[3 + a] = g.T[3 * g.tri_pm[2 * m + 1] + a];
+      }
+      extents(kcache[P.rwg_box[i]], vv, 6, &MR.base[3 * i], &MR.ext[3 * i]);
+      MR.off[i + 1] = MR.off[i] + 3LL * MR.ext[3 * i] * MR.ext[3 * i + 1] * MR.ext[3 * i + 2];
+    }
+    MR.data.assign(MR.off[N], 0.0);
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < N; ++i) {
+      int32_t m = P.rwg_perm[i];
+      const LeafKnots& K = kcache[P.rwg_box[i]];
+      for (int s = 0; s < 2; ++s) {
+        int32_t t = g.tri_pm[2 * m + s];
+        double tv[9];
+        for (int a = 0; a < 3; ++a)
+          for (int d = 0; d < 3; ++d) tv[3 * a + d] = g.V[3 * g.T[3 * t + a] + d];
+        const double* xf = &g.V[3 * g.free_pm[2 * m + s]];
+        double scale = (s == 0 ? 1.0 : -1.0) / (2.0 * g.area[t]);
+        integrate_triangle(K, tv, 3, xf, scale, &MR.base[3 * i], &MR.ext[3 * i],
+                           &MR.data[MR.off[i]], qx, qw);
+      }
+    }
+    MomentBlocks& MT = P.mom_tri;
+    MT.base.assign(3 * nt, 0);
+    MT.ext.assign(3 * nt, 0);
+    MT.off.assign(nt + 1, 0);
+    for (int64_t i = 0; i < nt; ++i) {
+      int32_t t = P.tri_perm[i];
+      extents(kcache[P.tri_box[i]], &g.T[3 * t], 3, &MT.base[3 * i], &MT.ext[3 * i]);
+      MT.off[i + 1] = MT.off[i] + (int64_t)MT.ext[3 * i] * MT.ext[3 * i + 1] * MT.ext[3 * i + 2];
+    }
+    MT.data.assign(MT.off[nt], 0.0);
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < nt; ++i) {
+      int32_t t = P.tri_perm[i];
+      const LeafKnots& K = kcache[P.tri_box[i]];
+      double tv[9];
+      for (int a = 0; a < 3; ++a)
+        for (int d = 0; d < 3; ++d) tv[3 * a + d] = g.V[3 * g.T[3 * t + a] + d];
+      integrate_triangle(K, tv, 1, nullptr, 1.0 / g.area[t], &MT.base[3 * i], &MT.ext[3 * i],
+                         &MT.data[MT.off[i]], qx, qw);
+    }
+  }
+}
+
+}  // namespace efie

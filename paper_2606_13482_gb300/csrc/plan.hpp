@@ -1,0 +1,111 @@
+// Host-side planning for the stabilized multilevel B-spline fast EFIE.
+// Everything here runs once in efie_setup / efie_plan, in FP64 on the host:
+// RWG geometry (Sec. II), the uniform octree and per-level spline parameters
+// (Sec. III-B, IV-C, IV-D), knot insertion, stabilization and projector
+// matrices (Sec. IV-B, V-B, Table I), exact moments (Eq. TAfactor, Sec. VI-A),
+// interaction lists and the block structure of the near field.
+#pragma once
+#include <complex>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace efie {
+
+using cplx = std::complex<double>;
+
+struct EfieError {
+  int code;
+  std::string msg;
+};
+
+struct Geometry {
+  int64_t nv = 0, nt = 0, N = 0;
+  std::vector<double> V;            // [nv][3]
+  std::vector<int32_t> T;           // [nt][3]
+  std::vector<int32_t> edge;        // [N][2] (lo, hi)
+  std::vector<int32_t> tri_pm;      // [N][2] (c+, c-)
+  std::vector<int32_t> free_pm;     // [N][2] vertex ids of x+, x-
+  std::vector<double> area;         // [nt]
+  std::vector<double> cen;          // [nt][3]
+};
+
+struct Level {
+  int level = 0;
+  int s = 0, sb = 0, sp = 0, shat = 0, nfft = 0;
+  double h = 0, delta = 0, Delta = 0;
+  std::vector<int64_t> ijk;          // [B][3] occupied boxes, Morton order
+  std::vector<uint64_t> code;        // [B] Morton codes (sorted)
+  std::vector<int64_t> parent;       // [B] index at level-1 (grid levels above top: -1)
+  std::vector<int64_t> child_ptr;    // [B+1] children (level+1) of each box
+  // interaction list (CSR over target boxes)
+  std::vector<int64_t> il_ptr;       // [B+1]
+  std::vector<int32_t> il_src;       // [nnz] source box
+  std::vector<int32_t> il_off;       // [nnz] offset id
+  std::vector<int32_t> offsets;      // [O][3] o = ijk_target - ijk_source
+  // dense per-level matrices (row-major, FP64)
+  std::vector<double> P;             // [shat][sp] = B_stab^-1 S
+  std::vector<double> CL, CR;        // [sp_parent][sp_this] (child = this level)
+  std::vector<cplx> Mf;              // [nfft][sp] = F[:, :shat] P
+  std::vector<cplx> Mb;              // [sp][nfft] = P^T Finv[:shat, :]
+  std::vector<cplx> Fn;              // [nfft][nfft] full DFT (kernel spectra)
+};
+
+struct MomentBlocks {
+  // per basis function (sorted order): base index and extents of its dense
+  // block in the leaf box grid, offset of its data; data is [ncomp][e0][e1][e2]
+  std::vector<int32_t> base;   // [n][3]
+  std::vector<int32_t> ext;    // [n][3]
+  std::vector<int64_t> off;    // [n+1]
+  std::vector<double> data;
+};
+
+struct Plan {
+  Geometry g;
+  double k = 0;
+  int p = 0, D = 0, top = 0, n_levels = 0;
+  double root_lo[3] = {0, 0, 0}, root_edge = 0;
+  std::vector<Level> lv;             // lv[ell - top], ell = top..D
+  Level& L(int ell) { return lv[ell - top]; }
+  const Level& L(int ell) const { return lv[ell - top]; }
+
+  // leaf-level basis-function ordering (sorted by leaf box)
+  std::vector<int32_t> rwg_perm;     // sorted k -> canonical m
+  std::vector<int32_t> rwg_box;      // sorted k -> leaf box
+  std::vector<int64_t> box_rwg_ptr;  // [B_D+1]
+  std::vector<int32_t> tri_perm;     // sorted t -> canonical triangle
+  std::vector<int32_t> tri_box;      // sorted t -> leaf box
+  std::vector<int64_t> box_tri_ptr;  // [B_D+1]
+  std::vector<int32_t> tri_rank;     // canonical triangle -> sorted index
+  std::vector<int32_t> rwg_tri_sorted;  // [N_sorted][2] sorted triangle index of c+, c-
+
+  // near field structure (leaf boxes with |d|_inf <= 1)
+  std::vector<int64_t> near_ptr;     // [B_D+1]
+  std::vector<int32_t> near_src;     // source box
+  std::vector<int64_t> blkA_off;     // [nnz_blocks+1] offset of A block (entries)
+  std::vector<int64_t> blkV_off;     // [nnz_blocks+1]
+  int64_t nnzA = 0, nnzV = 0;
+  // triangle set per leaf box for A assembly: triangles of RWGs in the box
+  std::vector<int64_t> tset_ptr;     // [B_D+1]
+  std::vector<int32_t> tset;         // canonical triangle ids
+  std::vector<int32_t> rwg_tl;       // [N_sorted][2] local index in tset of its box
+  std::vector<int32_t> rwg_loc;      // [N_sorted][2] local vertex index of the free vertex
+  std::vector<double> rwg_coef;      // [N_sorted][2] sigma / (2 a)
+
+  MomentBlocks mom_rwg;              // 3 components
+  MomentBlocks mom_tri;              // 1 component (pulse, includes 1/a)
+};
+
+// Builds everything except moments when with_moments is false.
+void build_plan(Plan& P, const double* xyz, int64_t nv, const int32_t* tri, int64_t nt,
+                double k, int p, double grid_spacing, int levels, int n_splines,
+                bool with_moments);
+
+// Spline helpers exposed for tests of the host code
+std::vector<double> open_knots(double lo, double hi, int ns, int p);
+std::vector<double> restriction_matrix(const std::vector<double>& Up,
+                                       const std::vector<double>& Uc, int p, int* rows,
+                                       int* cols);
+void gauss_legendre01(int n, std::vector<double>& x, std::vector<double>& w);
+
+}  // namespace efie

@@ -1,0 +1,113 @@
+"""CPU tests of the library: the C ABI loads and exports every declared symbol,
+and its host-side planning (octree, per-level spline counts, interaction and
+near lists, projector and transfer matrices) agrees with the oracle."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import efie_inputs as E
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__ as g
+    g.build_library_only()
+    import paper_2606_13482_gb300 as G
+    return G, G.load_library()
+
+
+def test_exports_every_declared_symbol(lib):
+    G, L = lib
+    hdr = open(os.path.join(ROOT, "include", "efie.h")).read()
+    declared = set(re.findall(r"^(?:int|const char \*)\s*(efie_\w+)\s*\(", hdr, re.M))
+    assert declared == set(G.EXPORTED_SYMBOLS)
+    for name in declared:
+        assert hasattr(L, name), name
+
+
+def test_plan_matches_oracle(lib):
+    G, _ = lib
+    from oracle import fastmv
+    from oracle.geometry import build_rwg
+    from oracle.tree import build_tree, interaction_lists
+    for (freq, r, k, p, delta, levels) in [(8, 0.5, 2 * np.pi, 3, 0.1, 2), (10, 0.5, 2 * np.pi * 1.7, 2, 0.08, 3),
+                                           (8, 0.5, 2 * np.pi, 5, 0.1, 1), (14, 0.5, 2 * np.pi * 2.5, 3, 0.06, 2),
+                                           (14, 0.5, 2 * np.pi * 0.5, 3, 0.06, 3)]:
+        V, T = E.icosphere(freq, r)
+        info, lv = G.plan(V, T, k, p, delta, levels)
+        m = build_rwg(V, T)
+        tr = build_tree(m, k, p, delta, levels)
+        assert info["depth"] == tr.D and info["top_level"] == tr.top
+        assert np.allclose(info["root_lo"], tr.root_lo, atol=0, rtol=0)
+        for L in lv:
+            O = tr.levels[L["level"]]
+            assert (L["s"], L["sb"], L["sp"], L["shat"]) == (O.s, O.sb, O.sp, O.shat)
+            assert L["n_boxes"] == len(O.boxes)
+            assert L["n_far_pairs"] == len(interaction_lists(tr, L["level"])[0])
+            assert L["nfft"] >= 2 * L["shat"] - 1
+        op = fastmv.BsplineEFIE.__new__(fastmv.BsplineEFIE)
+        op.tree = tr
+        nb, rb, tb = fastmv.BsplineEFIE.near_masks(op)
+        assert info["near_nnz_A"] == int(nb[rb[:, None], rb[None, :]].sum())
+        assert info["near_nnz_V"] == int(nb[tb[:, None], tb[None, :]].sum())
+
+
+def test_plan_matrices_match_oracle(lib):
+    """P = B_stab^-1 S and the knot-insertion transfers C^L, C^R, built by the
+    library's host code, against the oracle's construction (both the
+    increasing-s and the constant-s rule)."""
+    G, _ = lib
+    from oracle.bspline import S_REMOVE, open_knots, projector, restriction_matrix
+    from oracle.geometry import build_rwg
+    from oracle.tree import build_tree
+    for (freq, r, k, p, delta, levels) in [(14, 0.5, 2 * np.pi * 2.5, 3, 0.06, 2),
+                                           (14, 0.5, 2 * np.pi * 0.5, 3, 0.06, 3),
+                                           (14, 0.5, 2 * np.pi * 0.5, 5, 0.06, 2)]:
+        V, T = E.icosphere(freq, r)
+        tr = build_tree(build_rwg(V, T), k, p, delta, levels)
+        for ell in range(tr.D, tr.top - 1, -1):
+            L = tr.levels[ell]
+            Pref = projector(open_knots(0.0, float(L.sp - p), L.sp, p), p, S_REMOVE[p])[0]
+            Pm = G.plan_matrix(V, T, k, p, delta, levels, ell, 0)
+            assert np.abs(Pm - Pref).max() < 1e-12 * max(1, np.abs(Pref).max())
+            if ell > tr.top:
+                pa = tr.levels[ell - 1]
+                rr = int(round(pa.delta / L.delta))
+                Up = open_knots(-pa.sb * rr, (pa.s - p + pa.sb) * rr, pa.sp, p)
+                CL = restriction_matrix(Up, open_knots(-L.sb, (L.s - p) + L.sb, L.sp, p), p)
+                CR = restriction_matrix(Up, open_knots((L.s - p) - L.sb, 2 * (L.s - p) + L.sb, L.sp, p), p)
+                assert np.abs(G.plan_matrix(V, T, k, p, delta, levels, ell, 1) - CL).max() < 1e-14
+                assert np.abs(G.plan_matrix(V, T, k, p, delta, levels, ell, 2) - CR).max() < 1e-14
+
+
+def test_invalid_inputs(lib):
+    G, _ = lib
+    V, T = E.icosphere(4, 0.5)
+    with pytest.raises(G.EfieError) as e:
+        G.plan(V, T[:-1], 2 * np.pi, 3, 0.1, 1)          # open mesh
+    assert e.value.code == -1
+    with pytest.raises(G.EfieError):
+        G.plan(V, T, 2 * np.pi, 7, 0.1, 1)               # p out of range
+    with pytest.raises(G.EfieError):
+        G.plan(V, T, 2 * np.pi, 3, 0.1, 9)               # levels beyond depth + 1
+    with pytest.raises(G.EfieError):
+        G.plan(V, T, 2 * np.pi, 3, 0.03, 1)              # buffers close the far gap
+    Tbad = T.copy()
+    Tbad[0] = Tbad[0][[0, 2, 1]]
+    with pytest.raises(G.EfieError):
+        G.plan(V, Tbad, 2 * np.pi, 3, 0.1, 1)            # inconsistent orientation
+
+
+def test_setup_without_gpu_fails_loudly(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    G, _ = lib
+    V, T = E.icosphere(4, 0.5)
+    with pytest.raises(G.EfieError) as e:
+        G.EFIE(V, T, 2 * np.pi, 3, 0.1, 1)
+    assert e.value.code == -3
