@@ -165,6 +165,22 @@ int efie_matvec_parts(efie_handle *h, const void *x, void *yA, void *yV, int n_r
 int efie_solve(efie_handle *h, const void *rhs, void *x, int n_rhs, double tol,
                efie_solve_info *info, void *stream);
 
+/* Kernel-class timing for measurement.  efie_profile(h, 1) clears and starts
+ * recording: every later call that launches kernels records a CUDA event pair
+ * on the caller's stream around each class of kernels (anterpolation,
+ * transfers, transforms, translation, interpolation, near field, vectors, ...);
+ * efie_profile(h, 0) stops.  efie_profile_read synchronizes the recorded
+ * events and returns, for class index idx (0-based, EFIE_EINVAL past the last),
+ * its name (NUL-terminated, truncated to name_len), total milliseconds and
+ * number of kernel launches.  Either output pointer may be NULL. */
+int efie_profile(efie_handle *h, int enable);
+int efie_profile_read(efie_handle *h, int idx, char *name, int name_len, double *ms,
+                      int64_t *launches);
+
+/* Number of this library's kernel launches issued through h since setup
+ * (setup kernels excluded). */
+int efie_launch_count(const efie_handle *h, int64_t *n);
+
 int efie_destroy(efie_handle *h);
 
 /* Message of the last error of h, or of the last failed setup/plan of this

@@ -93,14 +93,16 @@ def quad_order(p):
     return int(math.ceil((3 * p + 3) / 2.0))
 
 
-def rwg_moments(mesh: RWGMesh, tree):
-    """[N, 3, s', s', s'] RWG moments in each RWG's leaf box."""
+def rwg_moments(mesh: RWGMesh, tree, subset=None):
+    """[N, 3, s', s', s'] RWG moments in each RWG's leaf box (or only for the
+    RWGs listed in subset, in that order)."""
     L = tree.levels[tree.D]
     p = tree.p
     n = quad_order(p)
-    out = np.zeros((mesh.N, 3, L.sp, L.sp, L.sp))
+    ids = np.arange(mesh.N) if subset is None else np.asarray(subset)
+    out = np.zeros((len(ids), 3, L.sp, L.sp, L.sp))
     cache = {}
-    for m in range(mesh.N):
+    for oi, m in enumerate(ids):
         b = tree.rwg_box[m]
         if b not in cache:
             cache[b] = LeafSplines(L.box_ext_lo(tree.root_lo, L.ijk[b]), L.sp, p, L.delta)
@@ -114,18 +116,20 @@ def rwg_moments(mesh: RWGMesh, tree):
             X = X.reshape(-1, 3)
             w = w.reshape(-1)
             f = sgn * (X - xv) / (2.0 * mesh.area[c])
-            out[m] += spl.tensor(X, w, f)
+            out[oi] += spl.tensor(X, w, f)
     return out
 
 
-def pulse_moments(mesh: RWGMesh, tree):
-    """[Nt, s', s', s'] pulse moments in each triangle's leaf box."""
+def pulse_moments(mesh: RWGMesh, tree, subset=None):
+    """[Nt, s', s', s'] pulse moments in each triangle's leaf box (or only for
+    the triangles listed in subset)."""
     L = tree.levels[tree.D]
     p = tree.p
     n = quad_order(p)
-    out = np.zeros((mesh.Nt, L.sp, L.sp, L.sp))
+    ids = np.arange(mesh.Nt) if subset is None else np.asarray(subset)
+    out = np.zeros((len(ids), L.sp, L.sp, L.sp))
     cache = {}
-    for c in range(mesh.Nt):
+    for oi, c in enumerate(ids):
         b = tree.tri_box[c]
         if b not in cache:
             cache[b] = LeafSplines(L.box_ext_lo(tree.root_lo, L.ijk[b]), L.sp, p, L.delta)
@@ -134,5 +138,5 @@ def pulse_moments(mesh: RWGMesh, tree):
         X, w = map_rule(pieces, n)
         X = X.reshape(-1, 3)
         w = w.reshape(-1)
-        out[c] = spl.tensor(X, w, np.full(len(w), 1.0 / mesh.area[c]))
+        out[oi] = spl.tensor(X, w, np.full(len(w), 1.0 / mesh.area[c]))
     return out

@@ -27,7 +27,8 @@ LIB_PATH = os.path.join(HERE, "libefie_gb300.so")
 EXPORTED_SYMBOLS = [
     "efie_plan", "efie_plan_matrix", "efie_setup", "efie_num_unknowns", "efie_plan_info",
     "efie_rwg_edges", "efie_rhs_planewave", "efie_matvec", "efie_matvec_fp64",
-    "efie_matvec_parts", "efie_solve", "efie_destroy", "efie_last_error",
+    "efie_matvec_parts", "efie_solve", "efie_profile", "efie_profile_read", "efie_launch_count",
+    "efie_destroy", "efie_last_error",
 ]
 
 
@@ -96,6 +97,9 @@ def load_library(path: str = LIB_PATH):
     lib.efie_matvec_fp64.argtypes = [VP, VP, VP, ctypes.c_int, VP]
     lib.efie_matvec_parts.argtypes = [VP, VP, VP, VP, ctypes.c_int, VP]
     lib.efie_solve.argtypes = [VP, VP, VP, ctypes.c_int, D, P(SolveInfo), VP]
+    lib.efie_profile.argtypes = [VP, ctypes.c_int]
+    lib.efie_profile_read.argtypes = [VP, ctypes.c_int, ctypes.c_char_p, ctypes.c_int, P(D), P(I64)]
+    lib.efie_launch_count.argtypes = [VP, P(I64)]
     lib.efie_destroy.argtypes = [VP]
     lib.efie_last_error.argtypes = [VP]
     lib.efie_last_error.restype = ctypes.c_char_p
@@ -230,6 +234,30 @@ class EFIE:
                                                   self._stream()), self.h)
         out = [{f: getattr(i, f) for f, _ in SolveInfo._fields_} for i in infos]
         return (x if rhs.dim() == 2 else x[0]), out, rc
+
+    def profile(self, enable: bool):
+        _check(self.lib, self.lib.efie_profile(self.h, 1 if enable else 0), self.h)
+
+    def profile_read(self):
+        """{class name: (total ms, launches)} of the recorded kernel classes."""
+        out = {}
+        i = 0
+        while True:
+            name = ctypes.create_string_buffer(64)
+            ms = ctypes.c_double()
+            nl = ctypes.c_int64()
+            rc = self.lib.efie_profile_read(self.h, i, name, 64, ctypes.byref(ms), ctypes.byref(nl))
+            if rc == EFIE_EINVAL:
+                break
+            _check(self.lib, rc, self.h)
+            out[name.value.decode()] = (ms.value, nl.value)
+            i += 1
+        return out
+
+    def launch_count(self):
+        n = ctypes.c_int64()
+        _check(self.lib, self.lib.efie_launch_count(self.h, ctypes.byref(n)), self.h)
+        return n.value
 
     def close(self):
         if getattr(self, "h", None):

@@ -98,7 +98,30 @@ std::complex<double> jk_of(double k) { return std::complex<double>(0.0, k); }
 
 }  // namespace
 
+namespace {
+// kernel classes for the profiling facility
+enum KClass { K_VEC = 0, K_ANTERP, K_UP, K_FWD, K_MAC, K_INV, K_DOWN, K_INTERP, K_NEAR_A, K_NEAR_V, K_KRYLOV, K_NCLASS };
+const char* kclass_name[K_NCLASS] = {"vector",  "anterpolation", "upward",  "forward_fft", "translation_mac", "inverse_fft",
+                                     "downward", "interpolation", "near_A", "near_V",      "krylov"};
+struct Prof {
+  bool on = false;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev;
+  int64_t launches[K_NCLASS] = {0};
+  void clear() {
+    for (auto& e : ev) {
+      cudaEventDestroy(e.second.first);
+      cudaEventDestroy(e.second.second);
+    }
+    ev.clear();
+    for (auto& l : launches) l = 0;
+  }
+  ~Prof() { clear(); }
+};
+}  // namespace
+
 struct efie_handle {
+  Prof prof;
+  int64_t n_launches = 0;
   Plan plan;
   efie_options opt{};
   int precision = EFIE_FP64;
@@ -133,6 +156,30 @@ struct efie_handle {
 };
 
 namespace {
+
+// RAII scope around the launches of one kernel class: counts launches and,
+// while profiling is on, records an event pair on the launching stream.
+struct KScope {
+  efie_handle* h;
+  int cls;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr, b = nullptr;
+  KScope(efie_handle* h_, int cls_, cudaStream_t s_, int nlaunch) : h(h_), cls(cls_), s(s_) {
+    h->n_launches += nlaunch;
+    if (h->prof.on) {
+      h->prof.launches[cls] += nlaunch;
+      cudaEventCreate(&a);
+      cudaEventCreate(&b);
+      cudaEventRecord(a, s);
+    }
+  }
+  ~KScope() {
+    if (a) {
+      cudaEventRecord(b, s);
+      h->prof.ev.push_back({cls, {a, b}});
+    }
+  }
+};
 
 void set_err(efie_handle* h, const EfieError& e) {
   if (h) h->err = e.msg;
@@ -313,6 +360,7 @@ void far_chunk(efie_handle* h, FarSet<R>& F, int nr, cudaStream_t s) {
   const int64_t N = P.g.N, Nt = P.g.nt;
   // a2: anterpolation into the leaf grids
   {
+    KScope ks(h, K_ANTERP, s, 1);
     const Level& L = P.L(D);
     launch_anterp<R>(F.mr, h->mr_base, h->mr_ext, h->mr_off, F.mt, h->mt_base, h->mt_ext, h->mt_off,
                      h->d_box_rwg_ptr, h->d_box_tri_ptr, (int64_t)L.code.size(), h->xs, N, h->rho, Nt, nr,
@@ -320,6 +368,7 @@ void far_chunk(efie_handle* h, FarSet<R>& F, int nr, cudaStream_t s) {
   }
   // a3: upward transfers
   for (int ell = D; ell > top; --ell) {
+    KScope ks(h, K_UP, s, 4);
     const Level& L = P.L(ell);
     const Level& U = P.L(ell - 1);
     const LevDev& LD = h->lev[ell - top];
@@ -355,13 +404,20 @@ void far_chunk(efie_handle* h, FarSet<R>& F, int nr, cudaStream_t s) {
     View a1{(int64_t)n * sp * sp * C, (int64_t)sp * sp * C, (int64_t)sp * C, C};
     View a2{(int64_t)n * n * sp * C, (int64_t)n * sp * C, (int64_t)sp * C, C};
     View vf{C, (int64_t)n * n * B * C, (int64_t)n * B * C, B * C};
-    launch_mode<R>(F.q[ell - top], vq, F.tmp1, a1, B, C, 0, sp, n, sp, sp, FL.Mf, FL.Mf, true, nullptr,
-                   nullptr, false, s);
-    launch_mode<R>(F.tmp1, a1, F.tmp2, a2, B, C, 1, sp, n, n, sp, FL.Mf, FL.Mf, true, nullptr, nullptr,
-                   false, s);
-    launch_mode<R>(F.tmp2, a2, F.Qh, vf, B, C, 2, sp, n, n, n, FL.Mf, FL.Mf, true, nullptr, nullptr, false,
-                   s);
-    launch_mac<R>(F.Qh, F.Rh, FL.Kh, B, C, LD.O, n3, LD.il_ptr, LD.il_src, LD.il_off, s);
+    {
+      KScope ks(h, K_FWD, s, 3);
+      launch_mode<R>(F.q[ell - top], vq, F.tmp1, a1, B, C, 0, sp, n, sp, sp, FL.Mf, FL.Mf, true, nullptr,
+                     nullptr, false, s);
+      launch_mode<R>(F.tmp1, a1, F.tmp2, a2, B, C, 1, sp, n, n, sp, FL.Mf, FL.Mf, true, nullptr, nullptr,
+                     false, s);
+      launch_mode<R>(F.tmp2, a2, F.Qh, vf, B, C, 2, sp, n, n, n, FL.Mf, FL.Mf, true, nullptr, nullptr, false,
+                     s);
+    }
+    {
+      KScope ks(h, K_MAC, s, 1);
+      launch_mac<R>(F.Qh, F.Rh, FL.Kh, B, C, LD.O, n3, LD.il_ptr, LD.il_src, LD.il_off, s);
+    }
+    KScope ks(h, K_INV, s, 3);
     View b1{(int64_t)sp * n * n * C, (int64_t)n * n * C, (int64_t)n * C, C};
     View b2{(int64_t)sp * sp * n * C, (int64_t)sp * n * C, (int64_t)n * C, C};
     launch_mode<R>(F.Rh, vf, F.tmp1, b1, B, C, 0, n, sp, n, n, FL.Mb, FL.Mb, true, nullptr, nullptr, false,
@@ -373,6 +429,7 @@ void far_chunk(efie_handle* h, FarSet<R>& F, int nr, cudaStream_t s) {
   }
   // a8: downward transfers r_c += C^T r_parent
   for (int ell = top + 1; ell <= D; ++ell) {
+    KScope ks(h, K_DOWN, s, 3);
     const Level& L = P.L(ell);
     const Level& U = P.L(ell - 1);
     const LevDev& LD = h->lev[ell - top];
@@ -392,6 +449,7 @@ void far_chunk(efie_handle* h, FarSet<R>& F, int nr, cudaStream_t s) {
   }
   // a9: interpolation
   {
+    KScope ks(h, K_INTERP, s, 1);
     const Level& L = P.L(D);
     launch_interp<R>(F.mr, h->mr_base, h->mr_ext, h->mr_off, h->d_rwg_box, N, F.mt, h->mt_base, h->mt_ext,
                      h->mt_off, h->d_tri_box, Nt, F.r[D - top], L.sp, nr, h->yA, N, h->w, Nt, s);
@@ -406,16 +464,26 @@ void matvec_chunk(efie_handle* h, FarSet<R>& F, const double2* x, int64_t ldx, i
   const int64_t N = P.g.N, Nt = P.g.nt;
   ensure_work(h, 8);
   ensure_far_buffers(h, F, nr);
-  launch_permute_in(x, ldx, h->d_rwg_perm, N, nr, h->xs, s);
-  launch_charges(h->xs, N, h->d_tri_rwg, h->d_tri_sgn, Nt, nr, h->rho, Nt, s);  // a1
-  far_chunk<R>(h, F, nr, s);                                                     // a2-a9
+  {
+    KScope ks(h, K_VEC, s, 2);
+    launch_permute_in(x, ldx, h->d_rwg_perm, N, nr, h->xs, s);
+    launch_charges(h->xs, N, h->d_tri_rwg, h->d_tri_sgn, Nt, nr, h->rho, Nt, s);  // a1
+  }
+  far_chunk<R>(h, F, nr, s);                                                       // a2-a9
   // a10: near field, FP64
   int64_t BD = (int64_t)P.L(P.D).code.size();
-  launch_near_spmv(h->nd.A, h->d_blkA_off, h->d_near_ptr, h->d_near_src, h->d_box_rwg_ptr, BD, h->xs,
-                   h->yA, N, nr, s);
-  launch_near_spmv(h->nd.Vn, h->d_blkV_off, h->d_near_ptr, h->d_near_src, h->d_box_tri_ptr, BD, h->rho,
-                   h->w, Nt, nr, s);
+  {
+    KScope ks(h, K_NEAR_A, s, 1);
+    launch_near_spmv(h->nd.A, h->d_blkA_off, h->d_near_ptr, h->d_near_src, h->d_box_rwg_ptr, BD, h->xs,
+                     h->yA, N, nr, s);
+  }
+  {
+    KScope ks(h, K_NEAR_V, s, 1);
+    launch_near_spmv(h->nd.Vn, h->d_blkV_off, h->d_near_ptr, h->d_near_src, h->d_box_tri_ptr, BD, h->rho,
+                     h->w, Nt, nr, s);
+  }
   std::complex<double> cA = jk_of(P.k), cV = 1.0 / jk_of(P.k);
+  KScope ks(h, K_VEC, s, 1);
   launch_combine(h->yA, N, h->w, Nt, h->d_rwg_perm, h->d_rwg_tri_sorted, N, nr,
                  make_double2(cA.real(), cA.imag()), make_double2(cV.real(), cV.imag()), y, ldy, yAo, yVo,
                  s);
@@ -677,6 +745,7 @@ int solve_impl(efie_handle* h, const double2* b, double2* x, int n_rhs, double t
       // w = T v_k (all rhs; inactive ones are ignored)
       do_matvec(h, Vb + (int64_t)k * N, ldr, wv, nullptr, nullptr, N, n_rhs, false, s);
       // CGS2
+      KScope ks(h, K_KRYLOV, s, 5);
       launch_multidot(Vb, ldr, N, k + 1, wv, N, N, n_rhs, dact, dh, s);
       launch_multiaxpy(Vb, ldr, N, k + 1, dh, k + 1, wv, N, N, n_rhs, dact, -1.0, s);
       launch_multidot(Vb, ldr, N, k + 1, wv, N, N, n_rhs, dact, dh2, s);
@@ -976,6 +1045,38 @@ int efie_solve(efie_handle* h, const void* rhs, void* x, int n_rhs, double tol, 
     if (n_rhs == 0) return EFIE_OK;
     return solve_impl(h, (const double2*)rhs, (double2*)x, n_rhs, tol, info, (cudaStream_t)stream);
   });
+}
+
+int efie_profile(efie_handle* h, int enable) {
+  if (!h) return EFIE_EINVAL;
+  if (enable) h->prof.clear();
+  h->prof.on = enable != 0;
+  return EFIE_OK;
+}
+
+int efie_profile_read(efie_handle* h, int idx, char* name, int name_len, double* ms, int64_t* launches) {
+  if (!h || idx < 0 || idx >= K_NCLASS) return EFIE_EINVAL;
+  if (name && name_len > 0) {
+    std::strncpy(name, kclass_name[idx], (size_t)name_len - 1);
+    name[name_len - 1] = 0;
+  }
+  double tot = 0;
+  for (auto& e : h->prof.ev) {
+    if (e.first != idx) continue;
+    if (cudaEventSynchronize(e.second.second) != cudaSuccess) return EFIE_ECUDA;
+    float t = 0;
+    cudaEventElapsedTime(&t, e.second.first, e.second.second);
+    tot += t;
+  }
+  if (ms) *ms = tot;
+  if (launches) *launches = h->prof.launches[idx];
+  return EFIE_OK;
+}
+
+int efie_launch_count(const efie_handle* h, int64_t* n) {
+  if (!h || !n) return EFIE_EINVAL;
+  *n = h->n_launches;
+  return EFIE_OK;
 }
 
 int efie_destroy(efie_handle* h) {
