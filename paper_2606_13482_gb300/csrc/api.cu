@@ -92,6 +92,11 @@ struct LevDev {
   int8_t* bits = nullptr;
   int64_t* child_ptr = nullptr;
   int64_t nfar = 0, O = 0;
+  // translation tiles
+  int64_t ntiles = 0;
+  int max_tile = 0;
+  int64_t *tile_tgt_ptr = nullptr, *tile_src_ptr = nullptr, *tile_kidx_off = nullptr;
+  int32_t *tile_tgt = nullptr, *tile_src = nullptr, *tile_kidx = nullptr;
 };
 
 std::complex<double> jk_of(double k) { return std::complex<double>(0.0, k); }
@@ -150,9 +155,11 @@ struct efie_handle {
   std::vector<LevDev> lev;
   FarSet<double> f64;
   FarSet<float> f32;
-  // work vectors (FP64, sorted)
+  // work vectors (FP64, sorted) and their double-float splits
   int Rw = 0;
   double2 *xs = nullptr, *rho = nullptr, *yA = nullptr, *w = nullptr;
+  float4 *xs4 = nullptr, *rho4 = nullptr;
+  bool near_df = false;   // near matrices stored as double-float pairs
 };
 
 namespace {
@@ -348,6 +355,10 @@ void ensure_work(efie_handle* h, int Rw) {
   h->yA = h->mem.alloc<double2>(N * Rw);
   h->rho = h->mem.alloc<double2>(Nt * Rw);
   h->w = h->mem.alloc<double2>(Nt * Rw);
+  if (h->near_df) {
+    h->xs4 = h->mem.alloc<float4>(N * Rw);
+    h->rho4 = h->mem.alloc<float4>(Nt * Rw);
+  }
   h->Rw = Rw;
 }
 
@@ -415,7 +426,8 @@ void far_chunk(efie_handle* h, FarSet<R>& F, int nr, cudaStream_t s) {
     }
     {
       KScope ks(h, K_MAC, s, 1);
-      launch_mac<R>(F.Qh, F.Rh, FL.Kh, B, C, LD.O, n3, LD.il_ptr, LD.il_src, LD.il_off, s);
+      launch_mac<R>(F.Qh, F.Rh, FL.Kh, B, C, LD.O, n3, LD.ntiles, LD.max_tile, LD.tile_tgt_ptr, LD.tile_tgt,
+                    LD.tile_src_ptr, LD.tile_src, LD.tile_kidx_off, LD.tile_kidx, s);
     }
     KScope ks(h, K_INV, s, 3);
     View b1{(int64_t)sp * n * n * C, (int64_t)n * n * C, (int64_t)n * C, C};
@@ -472,15 +484,30 @@ void matvec_chunk(efie_handle* h, FarSet<R>& F, const double2* x, int64_t ldx, i
   far_chunk<R>(h, F, nr, s);                                                       // a2-a9
   // a10: near field, FP64
   int64_t BD = (int64_t)P.L(P.D).code.size();
-  {
-    KScope ks(h, K_NEAR_A, s, 1);
-    launch_near_spmv(h->nd.A, h->d_blkA_off, h->d_near_ptr, h->d_near_src, h->d_box_rwg_ptr, BD, h->xs,
-                     h->yA, N, nr, s);
-  }
-  {
-    KScope ks(h, K_NEAR_V, s, 1);
-    launch_near_spmv(h->nd.Vn, h->d_blkV_off, h->d_near_ptr, h->d_near_src, h->d_box_tri_ptr, BD, h->rho,
-                     h->w, Nt, nr, s);
+  if (h->near_df) {
+    {
+      KScope ks(h, K_NEAR_A, s, 2);
+      launch_split_vec(h->xs, h->xs4, N * nr, s);
+      launch_near_spmv_df((const float4*)h->nd.A, h->d_blkA_off, h->d_near_ptr, h->d_near_src, h->d_box_rwg_ptr,
+                          BD, h->xs4, h->yA, N, nr, s);
+    }
+    {
+      KScope ks(h, K_NEAR_V, s, 2);
+      launch_split_vec(h->rho, h->rho4, Nt * nr, s);
+      launch_near_spmv_df((const float4*)h->nd.Vn, h->d_blkV_off, h->d_near_ptr, h->d_near_src,
+                          h->d_box_tri_ptr, BD, h->rho4, h->w, Nt, nr, s);
+    }
+  } else {
+    {
+      KScope ks(h, K_NEAR_A, s, 1);
+      launch_near_spmv(h->nd.A, h->d_blkA_off, h->d_near_ptr, h->d_near_src, h->d_box_rwg_ptr, BD, h->xs,
+                       h->yA, N, nr, s);
+    }
+    {
+      KScope ks(h, K_NEAR_V, s, 1);
+      launch_near_spmv(h->nd.Vn, h->d_blkV_off, h->d_near_ptr, h->d_near_src, h->d_box_tri_ptr, BD, h->rho,
+                       h->w, Nt, nr, s);
+    }
   }
   std::complex<double> cA = jk_of(P.k), cV = 1.0 / jk_of(P.k);
   KScope ks(h, K_VEC, s, 1);
@@ -584,6 +611,15 @@ void setup_impl(efie_handle* h, const efie_mesh* mesh, double k, int p, double g
       for (int d = 0; d < 3; ++d) bits[3 * b + d] = (int8_t)(L.ijk[3 * b + d] & 1);
     LD.bits = M.upload(bits);
     if (ell < P.D) LD.child_ptr = M.upload(L.child_ptr);
+    LD.ntiles = (int64_t)L.tile_tgt_ptr.size() - 1;
+    for (int64_t t = 0; t < LD.ntiles; ++t)
+      LD.max_tile = std::max<int>(LD.max_tile, (int)(L.tile_tgt_ptr[t + 1] - L.tile_tgt_ptr[t]));
+    LD.tile_tgt_ptr = M.upload(L.tile_tgt_ptr);
+    LD.tile_src_ptr = M.upload(L.tile_src_ptr);
+    LD.tile_kidx_off = M.upload(L.tile_kidx_off);
+    LD.tile_tgt = M.upload(L.tile_tgt);
+    LD.tile_src = M.upload(L.tile_src);
+    LD.tile_kidx = M.upload(L.tile_kidx);
   }
   // near field (FP64)
   {
@@ -655,6 +691,13 @@ void setup_impl(efie_handle* h, const efie_mesh* mesh, double k, int p, double g
     for (int64_t e0 = 0; e0 < P.nnzV; e0 += vchunk) {
       launch_near_V(nd, e0, std::min(vchunk, P.nnzV - e0), s);
       cuda_check(cudaStreamSynchronize(s), "near V assembly");
+    }
+    if (h->precision == EFIE_MIXED) {
+      // keep the FP64-assembled values as double-float pairs (in place)
+      launch_split_df(nd.A, P.nnzA, s);
+      launch_split_df(nd.Vn, P.nnzV, s);
+      cuda_check(cudaStreamSynchronize(s), "near split");
+      h->near_df = true;
     }
   }
   // far products

@@ -44,6 +44,12 @@ void launch_near_spmv(const double2* M, const int64_t* blk_off, const int64_t* n
                       const int32_t* near_src, const int64_t* box_ptr, int64_t n_boxes,
                       const double2* x, double2* y, int64_t ld, int nr, cudaStream_t s);
 
+void launch_split_df(double2* a, int64_t n, cudaStream_t s);
+void launch_split_vec(const double2* x, float4* y, int64_t n, cudaStream_t s);
+void launch_near_spmv_df(const float4* M, const int64_t* blk_off, const int64_t* near_ptr,
+                         const int32_t* near_src, const int64_t* box_ptr, int64_t n_boxes, const float4* x,
+                         double2* y, int64_t ld, int nr, cudaStream_t s);
+
 // Strided tensor view of a box-batched 3D grid with channels innermost:
 // element (b, i0, i1, i2, c) at b*sb + i0*s0 + i1*s1 + i2*s2 + c.
 struct View {
@@ -71,7 +77,8 @@ void launch_interp(const R* mr, const int32_t* mr_base, const int32_t* mr_ext, c
 
 template <typename R>
 void launch_mac(const cpx_t<R>* Qh, cpx_t<R>* Rh, const cpx_t<R>* Kh, int64_t B, int C, int64_t O,
-                int64_t nf, const int64_t* il_ptr, const int32_t* il_src, const int32_t* il_off,
+                int64_t nf, int64_t ntiles, int max_tile_targets, const int64_t* tgt_ptr, const int32_t* tgt,
+                const int64_t* src_ptr, const int32_t* src, const int64_t* kidx_off, const int32_t* kidx,
                 cudaStream_t s);
 
 template <typename R>

@@ -16,6 +16,8 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "device_api.cuh"
 
@@ -65,12 +67,103 @@ __global__ void k_mode(const cpx_t<R>* __restrict__ in, View vin, cpx_t<R>* __re
   }
 }
 
+// Line form: one thread owns one line (box, the two other indices, channel),
+// loads its nin inputs into registers once and writes all nout outputs; the
+// one or two matrices of the pass sit in shared memory.
+template <typename R, bool CM, int NMAX>
+__global__ void k_mode_line(const cpx_t<R>* __restrict__ in, View vin, cpx_t<R>* __restrict__ out,
+                            View vout, int64_t B, int C, int ax, int nin, int e0, int e1, int e2,
+                            const void* __restrict__ M0, const void* __restrict__ M1,
+                            const int8_t* __restrict__ sel, const int64_t* __restrict__ srcmap,
+                            bool accumulate) {
+  using T = cpx_t<R>;
+  extern __shared__ unsigned char smem_raw[];
+  const int nout = ax == 0 ? e0 : (ax == 1 ? e1 : e2);
+  const int msz = nout * nin;
+  const int esz = CM ? (int)sizeof(T) : (int)sizeof(R);
+  const int nmat = M1 && M1 != M0 ? 2 : 1;
+  for (int i = threadIdx.x; i < msz * esz / 4; i += blockDim.x) {
+    ((int*)smem_raw)[i] = ((const int*)M0)[i];
+    if (nmat == 2) ((int*)smem_raw)[msz * esz / 4 + i] = ((const int*)M1)[i];
+  }
+  __syncthreads();
+  // the two axes other than ax
+  const int ea = ax == 0 ? e1 : e0, eb = ax == 2 ? e1 : e2;
+  const int64_t sa_in = ax == 0 ? vin.s1 : vin.s0, sb_in = ax == 2 ? vin.s1 : vin.s2;
+  const int64_t sa_out = ax == 0 ? vout.s1 : vout.s0, sb_out = ax == 2 ? vout.s1 : vout.s2;
+  const int64_t step_in = ax == 0 ? vin.s0 : (ax == 1 ? vin.s1 : vin.s2);
+  const int64_t step_out = ax == 0 ? vout.s0 : (ax == 1 ? vout.s1 : vout.s2);
+  const int64_t lines = B * ea * eb * (int64_t)C;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < lines;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    int64_t t = idx;
+    const int c = (int)(t % C);
+    t /= C;
+    const int ib = (int)(t % eb);
+    t /= eb;
+    const int ia = (int)(t % ea);
+    const int64_t b = t / ea;
+    const int64_t bs = srcmap ? srcmap[b] : b;
+    const T* ip = in + bs * vin.sb + ia * sa_in + ib * sb_in + c;
+    T v[NMAX];
+#pragma unroll
+    for (int i = 0; i < NMAX; ++i)
+      if (i < nin) v[i] = ip[i * step_in];
+    const unsigned char* Ms = smem_raw + ((nmat == 2 && sel && sel[3 * b + ax]) ? (size_t)msz * esz : 0);
+    T* op = out + b * vout.sb + ia * sa_out + ib * sb_out + c;
+    for (int j = 0; j < nout; ++j) {
+      T acc = mk<R>(0, 0);
+      if (CM) {
+        const T* M = (const T*)Ms + j * nin;
+#pragma unroll
+        for (int i = 0; i < NMAX; ++i)
+          if (i < nin) cfma(acc, M[i], v[i]);
+      } else {
+        const R* M = (const R*)Ms + j * nin;
+#pragma unroll
+        for (int i = 0; i < NMAX; ++i)
+          if (i < nin) {
+            acc.x = fma(M[i], v[i].x, acc.x);
+            acc.y = fma(M[i], v[i].y, acc.y);
+          }
+      }
+      if (accumulate) acc = cadd(acc, op[j * step_out]);
+      op[j * step_out] = acc;
+    }
+  }
+}
+
 template <typename R>
 void launch_mode(const cpx_t<R>* in, View vin, cpx_t<R>* out, View vout, int64_t B, int C, int ax,
                  int nin, int e0, int e1, int e2, const void* M0, const void* M1, bool complex_m,
                  const int8_t* sel, const int64_t* srcmap, bool accumulate, cudaStream_t s) {
   int64_t total = B * e0 * e1 * e2 * (int64_t)C;
   if (total <= 0) return;
+  const int nout = ax == 0 ? e0 : (ax == 1 ? e1 : e2);
+  const size_t esz = complex_m ? sizeof(cpx_t<R>) : sizeof(R);
+  const size_t smem = (size_t)nout * nin * esz * ((M1 && M1 != M0) ? 2 : 1);
+  if (nin <= 40 && smem <= 96 * 1024) {
+    const int ea = ax == 0 ? e1 : e0, eb = ax == 2 ? e1 : e2;
+    int64_t lines = B * ea * eb * (int64_t)C;
+    int64_t blocks = ceil_div(lines, 128);
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    static bool attr[4] = {false, false, false, false};
+    int ai = (sizeof(R) == 8 ? 2 : 0) + (complex_m ? 1 : 0);
+    if (!attr[ai]) {
+      if (complex_m)
+        cudaFuncSetAttribute(k_mode_line<R, true, 40>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+      else
+        cudaFuncSetAttribute(k_mode_line<R, false, 40>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+      attr[ai] = true;
+    }
+    if (complex_m)
+      k_mode_line<R, true, 40><<<(unsigned)blocks, 128, smem, s>>>(in, vin, out, vout, B, C, ax, nin, e0, e1, e2,
+                                                                   M0, M1, sel, srcmap, accumulate);
+    else
+      k_mode_line<R, false, 40><<<(unsigned)blocks, 128, smem, s>>>(in, vin, out, vout, B, C, ax, nin, e0, e1,
+                                                                    e2, M0, M1, sel, srcmap, accumulate);
+    return;
+  }
   int64_t blocks = ceil_div(total, 256);
   if (blocks > 152 * 64) blocks = 152 * 64;
   if (complex_m)
@@ -92,13 +185,14 @@ __global__ void k_anterp(const R* __restrict__ mr, const int32_t* __restrict__ m
                          const double2* __restrict__ xs, int64_t ldx, const double2* __restrict__ rho,
                          int64_t ldr, int nr, int rt, cpx_t<R>* __restrict__ q, int sp) {
   extern __shared__ unsigned char smem_raw[];
-  R* g = (R*)smem_raw;  // [sp^3][4*rt][2]
+  R* g = (R*)smem_raw;  // [sp^3][4*rt complex], point stride PS = 8 rt + 1 (odd: no bank conflicts)
   const int b = blockIdx.x;
   const int r0 = blockIdx.y * rt;
   const int nrt = min(rt, nr - r0);
   const int CT = 4 * rt;
+  const int PS = 2 * CT + 1;
   const int npts = sp * sp * sp;
-  for (int i = threadIdx.x; i < npts * CT * 2; i += blockDim.x) g[i] = (R)0;
+  for (int i = threadIdx.x; i < npts * PS; i += blockDim.x) g[i] = (R)0;
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   // RWGs: components 0..2
@@ -114,7 +208,7 @@ __global__ void k_anterp(const R* __restrict__ mr, const int32_t* __restrict__ m
       for (int r = 0; r < nrt; ++r) {
         double2 xv = xs[(int64_t)(r0 + r) * ldx + i];
         for (int d = 0; d < 3; ++d) {
-          R* dst = g + ((int64_t)pt * CT + 4 * r + d) * 2;
+          R* dst = g + (int64_t)pt * PS + (4 * r + d) * 2;
           atomicAdd(dst, mv[d] * (R)xv.x);
           atomicAdd(dst + 1, mv[d] * (R)xv.y);
         }
@@ -133,7 +227,7 @@ __global__ void k_anterp(const R* __restrict__ mr, const int32_t* __restrict__ m
       R mv = m[e];
       for (int r = 0; r < nrt; ++r) {
         double2 rv = rho[(int64_t)(r0 + r) * ldr + i];
-        R* dst = g + ((int64_t)pt * CT + 4 * r + 3) * 2;
+        R* dst = g + (int64_t)pt * PS + (4 * r + 3) * 2;
         atomicAdd(dst, mv * (R)rv.x);
         atomicAdd(dst + 1, mv * (R)rv.y);
       }
@@ -145,7 +239,7 @@ __global__ void k_anterp(const R* __restrict__ mr, const int32_t* __restrict__ m
   cpx_t<R>* qb = q + (int64_t)b * npts * C;
   for (int idx = threadIdx.x; idx < npts * 4 * nrt; idx += blockDim.x) {
     int pt = idx / (4 * nrt), cc = idx - pt * 4 * nrt;
-    qb[(int64_t)pt * C + 4 * r0 + cc] = mk<R>(g[((int64_t)pt * CT + cc) * 2], g[((int64_t)pt * CT + cc) * 2 + 1]);
+    qb[(int64_t)pt * C + 4 * r0 + cc] = mk<R>(g[(int64_t)pt * PS + cc * 2], g[(int64_t)pt * PS + cc * 2 + 1]);
   }
 }
 
@@ -158,10 +252,10 @@ void launch_anterp(const R* mr, const int32_t* mr_base, const int32_t* mr_ext, c
   if (B <= 0 || nr <= 0) return;
   const int64_t npts = (int64_t)sp * sp * sp;
   const int64_t per_rhs = npts * 4 * 2 * sizeof(R);
-  int rt = (int)(200 * 1024 / per_rhs);
+  int rt = (int)(200 * 1024 / (per_rhs + npts * sizeof(R)));
   if (rt < 1) rt = 1;
   if (rt > nr) rt = nr;
-  size_t smem = (size_t)per_rhs * rt;
+  size_t smem = (size_t)npts * (8 * rt + 1) * sizeof(R);
   static bool attr_set[2] = {false, false};
   int which = sizeof(R) == 8;
   if (!attr_set[which]) {
@@ -264,39 +358,169 @@ void launch_interp(const R* mr, const int32_t* mr_base, const int32_t* mr_ext, c
 }
 
 // ---------------------------------------------------------------- translation MAC
-// Rh[f][x][c] = sum_{j in IL(x)} Kh[f][off_j] * Qh[f][src_j][c]
-// block: (C channels) x (TY targets); grid: (frequency f, target tile)
-template <typename R>
-__global__ void k_mac(const cpx_t<R>* __restrict__ Qh, cpx_t<R>* __restrict__ Rh,
-                      const cpx_t<R>* __restrict__ Kh, int64_t B, int C, int64_t O,
-                      const int64_t* __restrict__ il_ptr, const int32_t* __restrict__ il_src,
-                      const int32_t* __restrict__ il_off) {
+// Rh[f][x][c] = sum_{y in IL(x)} Kh[f][off(x - y)] * Qh[f][y][c].
+// Tiles group targets that share one source list (the children of a parent
+// box on interaction-list levels, chunks of boxes on the top grid level);
+// kidx[tile][j][a] holds the offset id of (target a, source j) or -1.  Each
+// thread keeps XR targets x CR channels of one frequency in registers, so every
+// loaded spectrum value feeds XR complex MACs and every kernel value CR.
+// grid: (tile, frequency chunk); block: fpb frequencies x ntx target groups x
+// C/CR channel groups.
+template <typename R, int XR, int CR>
+__global__ void k_mac_tiled(const cpx_t<R>* __restrict__ Qh, cpx_t<R>* __restrict__ Rh,
+                            const cpx_t<R>* __restrict__ Kh, int64_t B, int C, int64_t O, int64_t nf,
+                            const int64_t* __restrict__ tgt_ptr, const int32_t* __restrict__ tgt,
+                            const int64_t* __restrict__ src_ptr, const int32_t* __restrict__ src,
+                            const int64_t* __restrict__ kidx_off, const int32_t* __restrict__ kidx,
+                            int fpb, int ntx, int64_t f0) {
   using T = cpx_t<R>;
-  const int64_t f = blockIdx.x;
-  const int c = threadIdx.x;
-  const int64_t x = (int64_t)blockIdx.y * blockDim.y + threadIdx.y;
-  if (x >= B) return;
-  const T* Qf = Qh + f * B * C;
+  const int tile = blockIdx.x;
+  const int ncg = C / CR;
+  const int per_f = ntx * ncg;
+  const int fl = threadIdx.x / per_f;
+  const int rem = threadIdx.x - fl * per_f;
+  const int tg = rem / ncg, cg = rem - (rem / ncg) * ncg;
+  const int64_t f = f0 + (int64_t)blockIdx.y * fpb + fl;
+  if (fl >= fpb || f >= nf) return;
+  const int64_t t0 = tgt_ptr[tile], nt = tgt_ptr[tile + 1] - t0;
+  const int64_t s0 = src_ptr[tile], ns = src_ptr[tile + 1] - s0;
+  const int xb = tg * XR;
+  if (xb >= nt) return;
+  const int tpad = (int)(((nt + XR - 1) / XR) * XR);
+  const int32_t* kb = kidx + kidx_off[tile] + xb;
+  const T* Qf = Qh + f * B * C + cg * CR;
   const T* Kf = Kh + f * O;
-  T acc = mk<R>(0, 0);
-  for (int64_t j = il_ptr[x]; j < il_ptr[x + 1]; ++j) {
-    T kv = Kf[il_off[j]];
-    T qv = Qf[(int64_t)il_src[j] * C + c];
-    cfma(acc, kv, qv);
+  T acc[XR][CR];
+#pragma unroll
+  for (int a = 0; a < XR; ++a)
+#pragma unroll
+    for (int c = 0; c < CR; ++c) acc[a][c] = mk<R>(0, 0);
+#pragma unroll 2
+  for (int64_t j = 0; j < ns; ++j) {
+    const int32_t y = __ldg(src + s0 + j);
+    T q[CR];
+#pragma unroll
+    for (int c = 0; c < CR; ++c) q[c] = Qf[(int64_t)y * C + c];
+    const int32_t* kr = kb + j * tpad;
+#pragma unroll
+    for (int a = 0; a < XR; ++a) {
+      const int32_t id = __ldg(kr + a);
+      if (id < 0) continue;
+      const T kv = Kf[id];
+#pragma unroll
+      for (int c = 0; c < CR; ++c) cfma(acc[a][c], kv, q[c]);
+    }
   }
-  Rh[f * B * C + x * C + c] = acc;
+#pragma unroll
+  for (int a = 0; a < XR; ++a) {
+    if (xb + a >= nt) break;
+    T* out = Rh + f * B * C + (int64_t)tgt[t0 + xb + a] * C + cg * CR;
+#pragma unroll
+    for (int c = 0; c < CR; ++c) out[c] = acc[a][c];
+  }
+}
+
+// Top grid level, 32 channels (8 right-hand sides), FP32: every block owns one
+// tile of <= 128 targets and one frequency; chunks of YS sources are staged in
+// shared memory (kernel values gathered cooperatively through the index tile,
+// spectra loaded coalesced), then each thread runs 8 targets x 4 channels out
+// of shared memory.
+template <int YS>
+__global__ void __launch_bounds__(128) k_mac_top32(const float2* __restrict__ Qh, float2* __restrict__ Rh,
+                                                   const float2* __restrict__ Kh, int64_t B, int64_t O,
+                                                   int64_t nf, const int64_t* __restrict__ tgt_ptr,
+                                                   const int32_t* __restrict__ tgt,
+                                                   const int64_t* __restrict__ src_ptr,
+                                                   const int32_t* __restrict__ src,
+                                                   const int64_t* __restrict__ kidx_off,
+                                                   const int32_t* __restrict__ kidx, int64_t f0) {
+  __shared__ __align__(16) float2 Ks[YS][128];
+  __shared__ __align__(16) float2 Qs[YS][32];
+  const int tile = blockIdx.x;
+  const int64_t f = f0 + blockIdx.y;
+  if (f >= nf) return;
+  const int64_t t0 = tgt_ptr[tile], nt = tgt_ptr[tile + 1] - t0;
+  const int64_t s0 = src_ptr[tile], ns = src_ptr[tile + 1] - s0;
+  const int tpad = (int)(((nt + 7) / 8) * 8);
+  const int32_t* kb = kidx + kidx_off[tile];
+  const float2* Qf = Qh + f * B * 32;
+  const float2* Kf = Kh + f * O;
+  const int tg = threadIdx.x >> 3, cg = threadIdx.x & 7;
+  float2 acc[8][4];
+#pragma unroll
+  for (int a = 0; a < 8; ++a)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[a][c] = make_float2(0.f, 0.f);
+  for (int64_t j0 = 0; j0 < ns; j0 += YS) {
+    const int jn = (int)min((int64_t)YS, ns - j0);
+    for (int e = threadIdx.x; e < YS * 128; e += 128) {
+      const int j = e >> 7, a = e & 127;
+      float2 v = make_float2(0.f, 0.f);
+      if (j < jn && a < tpad) {
+        const int32_t id = __ldg(kb + (j0 + j) * tpad + a);
+        if (id >= 0) v = __ldg(Kf + id);
+      }
+      Ks[j][a] = v;
+    }
+    for (int e = threadIdx.x; e < YS * 32; e += 128) {
+      const int j = e >> 5, c = e & 31;
+      Qs[j][c] = j < jn ? __ldg(Qf + (int64_t)__ldg(src + s0 + j0 + j) * 32 + c) : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    if (tg * 8 < nt) {
+      for (int j = 0; j < jn; ++j) {
+        const float4 qa = *reinterpret_cast<const float4*>(&Qs[j][cg * 4]);
+        const float4 qb = *reinterpret_cast<const float4*>(&Qs[j][cg * 4 + 2]);
+        const float2 q[4] = {make_float2(qa.x, qa.y), make_float2(qa.z, qa.w), make_float2(qb.x, qb.y),
+                             make_float2(qb.z, qb.w)};
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+          const float2 kv = Ks[j][tg * 8 + a];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) cfma(acc[a][c], kv, q[c]);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (tg * 8 >= nt) return;
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    if (tg * 8 + a >= nt) break;
+    float2* out = Rh + f * B * 32 + (int64_t)tgt[t0 + tg * 8 + a] * 32 + cg * 4;
+    *reinterpret_cast<float4*>(out) = make_float4(acc[a][0].x, acc[a][0].y, acc[a][1].x, acc[a][1].y);
+    *reinterpret_cast<float4*>(out + 2) = make_float4(acc[a][2].x, acc[a][2].y, acc[a][3].x, acc[a][3].y);
+  }
 }
 
 template <typename R>
 void launch_mac(const cpx_t<R>* Qh, cpx_t<R>* Rh, const cpx_t<R>* Kh, int64_t B, int C, int64_t O,
-                int64_t nf, const int64_t* il_ptr, const int32_t* il_src, const int32_t* il_off,
+                int64_t nf, int64_t ntiles, int max_tile_targets, const int64_t* tgt_ptr, const int32_t* tgt,
+                const int64_t* src_ptr, const int32_t* src, const int64_t* kidx_off, const int32_t* kidx,
                 cudaStream_t s) {
-  if (B <= 0 || nf <= 0) return;
-  int ty = 256 / C;
-  if (ty < 1) ty = 1;
-  dim3 block(C, ty);
-  dim3 grid((unsigned)nf, (unsigned)ceil_div(B, ty));
-  k_mac<R><<<grid, block, 0, s>>>(Qh, Rh, Kh, B, C, O, il_ptr, il_src, il_off);
+  if (B <= 0 || nf <= 0 || ntiles <= 0) return;
+  if (sizeof(R) == 4 && C == 32 && max_tile_targets > 8 && max_tile_targets <= 128) {
+    for (int64_t f0 = 0; f0 < nf; f0 += 65535) {
+      int64_t nfc = std::min<int64_t>(65535, nf - f0);
+      dim3 grid((unsigned)ntiles, (unsigned)nfc);
+      k_mac_top32<32><<<grid, 128, 0, s>>>((const float2*)Qh, (float2*)Rh, (const float2*)Kh, B, O, nf, tgt_ptr,
+                                           tgt, src_ptr, src, kidx_off, kidx, f0);
+    }
+    return;
+  }
+  constexpr int XR = 8, CR = 4;
+  const int ncg = C / CR;
+  const int ntx = (max_tile_targets + XR - 1) / XR;
+  const int per_f = ntx * ncg;
+  int fpb = per_f >= 128 ? 1 : 128 / per_f;
+  const int threads = fpb * per_f;
+  const int64_t fchunk = (int64_t)65535 * fpb;
+  for (int64_t f0 = 0; f0 < nf; f0 += fchunk) {
+    int64_t nfc = std::min<int64_t>(fchunk, nf - f0);
+    dim3 grid((unsigned)ntiles, (unsigned)ceil_div(nfc, fpb));
+    k_mac_tiled<R, XR, CR><<<grid, threads, 0, s>>>(Qh, Rh, Kh, B, C, O, nf, tgt_ptr, tgt, src_ptr, src, kidx_off,
+                                                    kidx, fpb, ntx, f0);
+  }
 }
 
 // ---------------------------------------------------------------- children sum
@@ -642,10 +866,12 @@ template void launch_interp<double>(const double*, const int32_t*, const int32_t
                                     const int32_t*, int64_t, const double*, const int32_t*, const int32_t*,
                                     const int64_t*, const int32_t*, int64_t, const double2*, int, int,
                                     double2*, int64_t, double2*, int64_t, cudaStream_t);
-template void launch_mac<float>(const float2*, float2*, const float2*, int64_t, int, int64_t, int64_t,
-                                const int64_t*, const int32_t*, const int32_t*, cudaStream_t);
+template void launch_mac<float>(const float2*, float2*, const float2*, int64_t, int, int64_t, int64_t, int64_t,
+                                int, const int64_t*, const int32_t*, const int64_t*, const int32_t*,
+                                const int64_t*, const int32_t*, cudaStream_t);
 template void launch_mac<double>(const double2*, double2*, const double2*, int64_t, int, int64_t, int64_t,
-                                 const int64_t*, const int32_t*, const int32_t*, cudaStream_t);
+                                 int64_t, int, const int64_t*, const int32_t*, const int64_t*, const int32_t*,
+                                 const int64_t*, const int32_t*, cudaStream_t);
 template void launch_reduce_children<float>(const float2*, float2*, const int64_t*, int64_t, int64_t,
                                             cudaStream_t);
 template void launch_reduce_children<double>(const double2*, double2*, const int64_t*, int64_t, int64_t,

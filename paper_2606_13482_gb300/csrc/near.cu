@@ -419,6 +419,128 @@ __global__ void k_near_spmv(const double2* __restrict__ M, const int64_t* __rest
   }
 }
 
+// ---------------------------------------------------------------- double-float SpMV
+// Mixed form: every FP64 entry a is kept as a pair of floats (a_hi, a_lo) with
+// a_hi = fl32(a), a_lo = fl32(a - a_hi) (48-bit significand, same 16 bytes per
+// complex entry), and the product runs on the FP32 pipes: a_hi x_hi is formed
+// exactly as p + e with one FMA, the cross terms a_hi x_lo + a_lo x_hi are
+// added in FP32, and sums use the error-free two-sum, so each row is accurate
+// to ~1e-14 relative -- FP64-class results at FP32 instruction rates.
+
+// in place: double2 (re, im) -> float4 (re_hi, re_lo, im_hi, im_lo)
+__global__ void k_split_df(double2* __restrict__ a, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double2 v = a[i];
+    float rh = (float)v.x, ih = (float)v.y;
+    float rl = (float)(v.x - (double)rh), il = (float)(v.y - (double)ih);
+    ((float4*)a)[i] = make_float4(rh, rl, ih, il);
+  }
+}
+
+// out-of-place split of [nr][n] vectors
+__global__ void k_split_vec(const double2* __restrict__ x, float4* __restrict__ y, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double2 v = x[i];
+    float rh = (float)v.x, ih = (float)v.y;
+    y[i] = make_float4(rh, (float)(v.x - (double)rh), ih, (float)(v.y - (double)ih));
+  }
+}
+
+struct DF {
+  float hi, lo;
+};
+// S += p (error-free two-sum, error folded into lo)
+// (the _rn intrinsics are never contracted into FMAs, which would break the
+// error-free transformations)
+__device__ __forceinline__ void df_add(DF& S, float p) {
+  float s = __fadd_rn(S.hi, p);
+  float bb = __fsub_rn(s, S.hi);
+  float err = __fadd_rn(__fsub_rn(S.hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  S.hi = s;
+  S.lo = __fadd_rn(S.lo, err);
+}
+
+template <int RMAX>
+__global__ void k_near_spmv_df(const float4* __restrict__ M, const int64_t* __restrict__ blk_off,
+                               const int64_t* __restrict__ near_ptr, const int32_t* __restrict__ near_src,
+                               const int64_t* __restrict__ box_ptr, const float4* __restrict__ x,
+                               double2* __restrict__ y, int64_t ld, int nr) {
+  int xb = blockIdx.x;
+  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  int64_t r0 = box_ptr[xb], nrow = box_ptr[xb + 1] - r0;
+  for (int64_t row = warp; row < nrow; row += nw) {
+    DF re[RMAX], im[RMAX];
+#pragma unroll
+    for (int r = 0; r < RMAX; ++r) re[r] = im[r] = DF{0.f, 0.f};
+    for (int64_t j = near_ptr[xb]; j < near_ptr[xb + 1]; ++j) {
+      int32_t yb = near_src[j];
+      int64_t c0 = box_ptr[yb], ncol = box_ptr[yb + 1] - c0;
+      const float4* Mr = M + blk_off[j] + row * ncol;
+      for (int64_t c = lane; c < ncol; c += 32) {
+        float4 a = Mr[c];
+#pragma unroll
+        for (int r = 0; r < RMAX; ++r) {
+          if (r >= nr) break;
+          float4 v = x[r * ld + c0 + c];
+          // re += a_r x_r - a_i x_i ; im += a_r x_i + a_i x_r
+          float p1 = __fmul_rn(a.x, v.x), e1 = fmaf(a.x, v.x, -p1), c1 = fmaf(a.x, v.y, a.y * v.x);
+          float p2 = __fmul_rn(a.z, v.z), e2 = fmaf(a.z, v.z, -p2), c2 = fmaf(a.z, v.w, a.w * v.z);
+          df_add(re[r], p1);
+          df_add(re[r], -p2);
+          re[r].lo += (e1 - e2) + (c1 - c2);
+          float p3 = __fmul_rn(a.x, v.z), e3 = fmaf(a.x, v.z, -p3), c3 = fmaf(a.x, v.w, a.y * v.z);
+          float p4 = __fmul_rn(a.z, v.x), e4 = fmaf(a.z, v.x, -p4), c4 = fmaf(a.z, v.y, a.w * v.x);
+          df_add(im[r], p3);
+          df_add(im[r], p4);
+          im[r].lo += (e3 + e4) + (c3 + c4);
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < RMAX; ++r) {
+      if (r >= nr) break;
+      double vx = (double)re[r].hi + (double)re[r].lo, vy = (double)im[r].hi + (double)im[r].lo;
+      for (int o = 16; o > 0; o >>= 1) {
+        vx += __shfl_down_sync(0xffffffffu, vx, o);
+        vy += __shfl_down_sync(0xffffffffu, vy, o);
+      }
+      if (lane == 0) {
+        double2 t = y[r * ld + r0 + row];
+        y[r * ld + r0 + row] = make_double2(t.x + vx, t.y + vy);
+      }
+    }
+  }
+}
+
+void launch_split_df(double2* a, int64_t n, cudaStream_t s) {
+  if (n <= 0) return;
+  int64_t blocks = ceil_div(n, 256);
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  k_split_df<<<(unsigned)blocks, 256, 0, s>>>(a, n);
+}
+void launch_split_vec(const double2* x, float4* y, int64_t n, cudaStream_t s) {
+  if (n <= 0) return;
+  int64_t blocks = ceil_div(n, 256);
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  k_split_vec<<<(unsigned)blocks, 256, 0, s>>>(x, y, n);
+}
+void launch_near_spmv_df(const float4* M, const int64_t* blk_off, const int64_t* near_ptr,
+                         const int32_t* near_src, const int64_t* box_ptr, int64_t n_boxes, const float4* x,
+                         double2* y, int64_t ld, int nr, cudaStream_t s) {
+  if (n_boxes <= 0) return;
+  for (int r0 = 0; r0 < nr; r0 += 8) {
+    int cnt = nr - r0 < 8 ? nr - r0 : 8;
+    const float4* xr = x + (int64_t)r0 * ld;
+    double2* yr = y + (int64_t)r0 * ld;
+    if (cnt <= 1)
+      k_near_spmv_df<1><<<(unsigned)n_boxes, 256, 0, s>>>(M, blk_off, near_ptr, near_src, box_ptr, xr, yr, ld, cnt);
+    else if (cnt <= 4)
+      k_near_spmv_df<4><<<(unsigned)n_boxes, 256, 0, s>>>(M, blk_off, near_ptr, near_src, box_ptr, xr, yr, ld, cnt);
+    else
+      k_near_spmv_df<8><<<(unsigned)n_boxes, 256, 0, s>>>(M, blk_off, near_ptr, near_src, box_ptr, xr, yr, ld, cnt);
+  }
+}
+
 // ---------------------------------------------------------------- launchers
 int near_upload_rules(const double* q3, const double* q4) {
   if (cudaMemcpyToSymbol(c_q3, q3, sizeof(double) * 27) != cudaSuccess) return -1;

@@ -655,6 +655,76 @@ void build_plan(Plan& P, const double* xyz, int64_t nv, const int32_t* tri, int6
       }
     }
   }
+  // translation tiles.  Top grid level: chunks of TILE_TOP consecutive boxes,
+  // every box a source.  Lower levels: the children of one parent, whose
+  // interaction lists all lie in the children of the parent's neighbours.
+  for (int ell = D; ell >= P.top; --ell) {
+    Level& L = P.L(ell);
+    const int64_t B = (int64_t)L.code.size();
+    std::unordered_map<int64_t, int32_t> off_id;
+    for (size_t i = 0; i < L.offsets.size() / 3; ++i) {
+      int64_t key = (((int64_t)L.offsets[3 * i] + (1LL << 20)) << 42) |
+                    (((int64_t)L.offsets[3 * i + 1] + (1LL << 20)) << 21) | ((int64_t)L.offsets[3 * i + 2] + (1LL << 20));
+      off_id[key] = (int32_t)i;
+    }
+    auto add_tile = [&](const std::vector<int32_t>& tg, const std::vector<int32_t>& sr, int tpad) {
+      L.tile_tgt_ptr.push_back((int64_t)L.tile_tgt.size());
+      L.tile_src_ptr.push_back((int64_t)L.tile_src.size());
+      L.tile_kidx_off.push_back((int64_t)L.tile_kidx.size());
+      for (int32_t x : tg) L.tile_tgt.push_back(x);
+      for (int32_t y : sr) L.tile_src.push_back(y);
+      for (int32_t y : sr)
+        for (int a = 0; a < tpad; ++a) {
+          int32_t id = -1;
+          if (a < (int)tg.size()) {
+            const int64_t* xi = &L.ijk[3 * tg[a]];
+            const int64_t* yi = &L.ijk[3 * y];
+            int64_t dx = xi[0] - yi[0], dy = xi[1] - yi[1], dz = xi[2] - yi[2];
+            if (std::max(std::llabs(dx), std::max(std::llabs(dy), std::llabs(dz))) >= 2) {
+              int64_t key = ((dx + (1LL << 20)) << 42) | ((dy + (1LL << 20)) << 21) | (dz + (1LL << 20));
+              auto it = off_id.find(key);
+              if (it == off_id.end()) fail(-1, "internal: offset missing from the translation table");
+              id = it->second;
+            }
+          }
+          L.tile_kidx.push_back(id);
+        }
+    };
+    if (L.il_src.empty()) {
+      // no far pairs on this level
+    } else if (ell == P.top) {
+      std::vector<int32_t> all(B);
+      std::iota(all.begin(), all.end(), 0);
+      for (int64_t x0 = 0; x0 < B; x0 += TILE_TOP) {
+        std::vector<int32_t> tg;
+        for (int64_t x = x0; x < std::min<int64_t>(B, x0 + TILE_TOP); ++x) tg.push_back((int32_t)x);
+        int tpad = (int)((tg.size() + TILE_X - 1) / TILE_X) * TILE_X;
+        add_tile(tg, all, tpad);
+      }
+    } else {
+      const Level& U = P.L(ell - 1);
+      const int64_t nbp = 1LL << (ell - 1);
+      for (size_t pb = 0; pb < U.code.size(); ++pb) {
+        std::vector<int32_t> tg, sr;
+        for (int64_t c = U.child_ptr[pb]; c < U.child_ptr[pb + 1]; ++c) tg.push_back((int32_t)c);
+        const int64_t* pi = &U.ijk[3 * pb];
+        for (int a = -1; a <= 1; ++a)
+          for (int b = -1; b <= 1; ++b)
+            for (int c = -1; c <= 1; ++c) {
+              int64_t q[3] = {pi[0] + a, pi[1] + b, pi[2] + c};
+              if (q[0] < 0 || q[1] < 0 || q[2] < 0 || q[0] >= nbp || q[1] >= nbp || q[2] >= nbp) continue;
+              int64_t qb = find_code(U.code, morton(q[0], q[1], q[2]));
+              if (qb < 0) continue;
+              for (int64_t y = U.child_ptr[qb]; y < U.child_ptr[qb + 1]; ++y) sr.push_back((int32_t)y);
+            }
+        std::sort(sr.begin(), sr.end());
+        add_tile(tg, sr, TILE_X);
+      }
+    }
+    L.tile_tgt_ptr.push_back((int64_t)L.tile_tgt.size());
+    L.tile_src_ptr.push_back((int64_t)L.tile_src.size());
+    L.tile_kidx_off.push_back((int64_t)L.tile_kidx.size());
+  }
   // transfer matrices C^L, C^R (child level ell -> ell-1), lattice units of
   // the child knot spacing (Sec. IV-B)
   for (int ell = D; ell > P.top; --ell) {

@@ -43,6 +43,10 @@ struct Level {
   std::vector<int32_t> il_src;       // [nnz] source box
   std::vector<int32_t> il_off;       // [nnz] offset id
   std::vector<int32_t> offsets;      // [O][3] o = ijk_target - ijk_source
+  // translation tiles: groups of <= TILE_T targets sharing one source list;
+  // kidx[tile] is [n_src][TILE_T] offset ids (-1: pair not translated here)
+  std::vector<int64_t> tile_tgt_ptr, tile_src_ptr, tile_kidx_off;
+  std::vector<int32_t> tile_tgt, tile_src, tile_kidx;
   // dense per-level matrices (row-major, FP64)
   std::vector<double> P;             // [shat][sp] = B_stab^-1 S
   std::vector<double> CL, CR;        // [sp_parent][sp_this] (child = this level)
@@ -59,6 +63,9 @@ struct MomentBlocks {
   std::vector<int64_t> off;    // [n+1]
   std::vector<double> data;
 };
+
+constexpr int TILE_X = 8;      // targets per thread in the translation MAC
+constexpr int TILE_TOP = 128;  // targets per tile on the top grid level
 
 struct Plan {
   Geometry g;

@@ -82,9 +82,10 @@ def test_matvec_mixed_vs_oracle(G, c1_gpu, c1_oracle):
     x = E.complex_gaussian(h32.N, 2)
     y = h32.matvec(torch.from_numpy(x).cuda()).cpu().numpy()
     assert _rel(y, c1_oracle.matvec(x)) < TOL32
-    # the FP64 entry point of a mixed handle is the plain form
+    # the FP64 entry point of a mixed handle: FP64 far field and the near field
+    # kept as double-float pairs (48-bit significand), so ~1e-13 from the oracle
     y64 = h32.matvec(torch.from_numpy(x).cuda(), fp64=True).cpu().numpy()
-    assert _rel(y64, c1_oracle.matvec(x)) < TOL64
+    assert _rel(y64, c1_oracle.matvec(x)) < 1e-10
 
 
 def test_batched_rhs_ragged_chunks(G, c1_gpu, c1_oracle):
@@ -151,19 +152,42 @@ def test_empty_batch(G, c1_gpu):
     assert y.shape == (0, h64.N)
 
 
-def test_two_level_increasing_s(G):
+TWO_LEVEL = (11, 0.5, 2 * np.pi * 2.2, 3, 0.06, 2)
+
+
+@pytest.fixture(scope="module")
+def two_level_oracle():
+    from oracle import fastmv
+    from oracle.geometry import build_rwg
+    freq, r, k, p, delta, levels = TWO_LEVEL
+    V, T = E.icosphere(freq, r)
+    return V, T, fastmv.BsplineEFIE(build_rwg(V, T), k, p, delta, levels)
+
+
+def test_two_level_increasing_s(G, two_level_oracle):
     """Two grid levels with far pairs on both and s -> 2s - p at the parent
     (boxes >= lambda/2): upward / downward transfers on the GPU."""
     torch = _torch()
-    from oracle import fastmv
-    from oracle.geometry import build_rwg
-    V, T = E.icosphere(11, 0.5)
-    k, p, delta, levels = 2 * np.pi * 2.2, 3, 0.06, 2
+    V, T, ref_op = two_level_oracle
+    _, _, k, p, delta, levels = TWO_LEVEL
     info, lv = G.plan(V, T, k, p, delta, levels)
     assert lv[1]["s"] == 2 * lv[0]["s"] - p and lv[0]["n_far_pairs"] > 0 and lv[1]["n_far_pairs"] > 0
     h = G.EFIE(V, T, k, p, delta, levels, precision=G.EFIE_FP64)
     x = E.complex_gaussian(h.N, 5)
     y = h.matvec(torch.from_numpy(x).cuda()).cpu().numpy()
     h.close()
-    ref = fastmv.BsplineEFIE(build_rwg(V, T), k, p, delta, levels).matvec(x)
-    assert _rel(y, ref) < TOL64
+    assert _rel(y, ref_op.matvec(x)) < TOL64
+
+
+def test_top_level_mixed_batched(G, two_level_oracle):
+    """Mixed form with 8- and 3-vector chunks on a tree whose top grid level has
+    far pairs (the shared-memory top-level translation path)."""
+    torch = _torch()
+    V, T, ref_op = two_level_oracle
+    _, _, k, p, delta, levels = TWO_LEVEL
+    h = G.EFIE(V, T, k, p, delta, levels, precision=G.EFIE_MIXED)
+    X = E.complex_gaussian((11, h.N), 6)
+    Y = h.matvec(torch.from_numpy(X).cuda()).cpu().numpy()
+    h.close()
+    for r in (0, 5, 9):
+        assert _rel(Y[r], ref_op.matvec(X[r])) < TOL32
