@@ -105,9 +105,13 @@ std::complex<double> jk_of(double k) { return std::complex<double>(0.0, k); }
 
 namespace {
 // kernel classes for the profiling facility
-enum KClass { K_VEC = 0, K_ANTERP, K_UP, K_FWD, K_MAC, K_INV, K_DOWN, K_INTERP, K_NEAR_A, K_NEAR_V, K_KRYLOV, K_NCLASS };
-const char* kclass_name[K_NCLASS] = {"vector",  "anterpolation", "upward",  "forward_fft", "translation_mac", "inverse_fft",
-                                     "downward", "interpolation", "near_A", "near_V",      "krylov"};
+enum KClass {
+  K_VEC = 0, K_ANTERP, K_UP, K_FWD, K_MAC, K_INV, K_DOWN, K_INTERP, K_NEAR_A, K_NEAR_V, K_KRYLOV, K_MAC_TOP,
+  K_PRECOND, K_NCLASS
+};
+const char* kclass_name[K_NCLASS] = {"vector",   "anterpolation", "upward",  "forward_fft", "translation_mac",
+                                     "inverse_fft", "downward",   "interpolation", "near_A", "near_V", "krylov",
+                                     "translation_mac_top", "precond"};
 struct Prof {
   bool on = false;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev;
@@ -159,6 +163,7 @@ struct efie_handle {
   int Rw = 0;
   double2 *xs = nullptr, *rho = nullptr, *yA = nullptr, *w = nullptr;
   float4 *xs4 = nullptr, *rho4 = nullptr;
+  float2 *xsf = nullptr, *rhof = nullptr;   // FP32 copies for the far field
   bool near_df = false;   // near matrices stored as double-float pairs
 };
 
@@ -359,6 +364,10 @@ void ensure_work(efie_handle* h, int Rw) {
     h->xs4 = h->mem.alloc<float4>(N * Rw);
     h->rho4 = h->mem.alloc<float4>(Nt * Rw);
   }
+  if (h->precision == EFIE_MIXED) {
+    h->xsf = h->mem.alloc<float2>(N * Rw);
+    h->rhof = h->mem.alloc<float2>(Nt * Rw);
+  }
   h->Rw = Rw;
 }
 
@@ -371,10 +380,18 @@ void far_chunk(efie_handle* h, FarSet<R>& F, int nr, cudaStream_t s) {
   const int64_t N = P.g.N, Nt = P.g.nt;
   // a2: anterpolation into the leaf grids
   {
-    KScope ks(h, K_ANTERP, s, 1);
     const Level& L = P.L(D);
+    const cpx_t<R>* xin = (const cpx_t<R>*)h->xs;
+    const cpx_t<R>* rin = (const cpx_t<R>*)h->rho;
+    KScope ks(h, K_ANTERP, s, sizeof(R) == 4 ? 3 : 1);
+    if (sizeof(R) == 4) {
+      launch_convert<R>(h->xs, (cpx_t<R>*)h->xsf, N * nr, s);
+      launch_convert<R>(h->rho, (cpx_t<R>*)h->rhof, Nt * nr, s);
+      xin = (const cpx_t<R>*)h->xsf;
+      rin = (const cpx_t<R>*)h->rhof;
+    }
     launch_anterp<R>(F.mr, h->mr_base, h->mr_ext, h->mr_off, F.mt, h->mt_base, h->mt_ext, h->mt_off,
-                     h->d_box_rwg_ptr, h->d_box_tri_ptr, (int64_t)L.code.size(), h->xs, N, h->rho, Nt, nr,
+                     h->d_box_rwg_ptr, h->d_box_tri_ptr, (int64_t)L.code.size(), xin, N, rin, Nt, nr,
                      F.q[D - top], L.sp, s);
   }
   // a3: upward transfers
@@ -425,7 +442,7 @@ void far_chunk(efie_handle* h, FarSet<R>& F, int nr, cudaStream_t s) {
                      s);
     }
     {
-      KScope ks(h, K_MAC, s, 1);
+      KScope ks(h, ell == top ? K_MAC_TOP : K_MAC, s, 1);
       launch_mac<R>(F.Qh, F.Rh, FL.Kh, B, C, LD.O, n3, LD.ntiles, LD.max_tile, LD.tile_tgt_ptr, LD.tile_tgt,
                     LD.tile_src_ptr, LD.tile_src, LD.tile_kidx_off, LD.tile_kidx, s);
     }
@@ -925,6 +942,25 @@ void fill_plan_info(const Plan& P, efie_plan_info_t* info, efie_level_info_t* lv
 }
 
 }  // namespace
+
+namespace efie {
+int handle_rhs_args(const efie_handle* h, const double** V, const int32_t** T, const double** area,
+                    const int32_t** tri_pm, const int32_t** free_pm, int64_t* N, double* k) {
+  if (!h) return EFIE_EINVAL;
+  *V = h->dV;
+  *T = h->dT;
+  *area = h->darea;
+  *tri_pm = h->dtri_pm;
+  *free_pm = h->dfree_pm;
+  *N = h->plan.g.N;
+  *k = h->plan.k;
+  return EFIE_OK;
+}
+void handle_set_error(efie_handle* h, const char* msg) {
+  if (h) h->err = msg;
+  g_last_error = msg;
+}
+}  // namespace efie
 
 // ================================================================= C ABI
 extern "C" {

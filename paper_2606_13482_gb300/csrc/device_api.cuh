@@ -65,7 +65,7 @@ template <typename R>
 void launch_anterp(const R* mr, const int32_t* mr_base, const int32_t* mr_ext, const int64_t* mr_off,
                    const R* mt, const int32_t* mt_base, const int32_t* mt_ext, const int64_t* mt_off,
                    const int64_t* box_rwg_ptr, const int64_t* box_tri_ptr, int64_t B,
-                   const double2* xs, int64_t ldx, const double2* rho, int64_t ldr, int nr,
+                   const cpx_t<R>* xs, int64_t ldx, const cpx_t<R>* rho, int64_t ldr, int nr,
                    cpx_t<R>* q, int sp, cudaStream_t s);
 
 template <typename R>

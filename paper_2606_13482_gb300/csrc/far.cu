@@ -67,10 +67,11 @@ __global__ void k_mode(const cpx_t<R>* __restrict__ in, View vin, cpx_t<R>* __re
   }
 }
 
-// Line form: one thread owns one line (box, the two other indices, channel),
-// loads its nin inputs into registers once and writes all nout outputs; the
-// one or two matrices of the pass sit in shared memory.
-template <typename R, bool CM, int NMAX>
+// Line form: one thread owns LPT lines (box, the two other indices, LPT
+// consecutive channels), loads their nin inputs into registers once and writes
+// all nout outputs; the one or two matrices of the pass sit in shared memory,
+// so each matrix value read feeds LPT complex MACs.
+template <typename R, bool CM, int NMAX, int LPT>
 __global__ void k_mode_line(const cpx_t<R>* __restrict__ in, View vin, cpx_t<R>* __restrict__ out,
                             View vout, int64_t B, int C, int ax, int nin, int e0, int e1, int e2,
                             const void* __restrict__ M0, const void* __restrict__ M1,
@@ -87,50 +88,110 @@ __global__ void k_mode_line(const cpx_t<R>* __restrict__ in, View vin, cpx_t<R>*
     if (nmat == 2) ((int*)smem_raw)[msz * esz / 4 + i] = ((const int*)M1)[i];
   }
   __syncthreads();
-  // the two axes other than ax
   const int ea = ax == 0 ? e1 : e0, eb = ax == 2 ? e1 : e2;
   const int64_t sa_in = ax == 0 ? vin.s1 : vin.s0, sb_in = ax == 2 ? vin.s1 : vin.s2;
   const int64_t sa_out = ax == 0 ? vout.s1 : vout.s0, sb_out = ax == 2 ? vout.s1 : vout.s2;
   const int64_t step_in = ax == 0 ? vin.s0 : (ax == 1 ? vin.s1 : vin.s2);
   const int64_t step_out = ax == 0 ? vout.s0 : (ax == 1 ? vout.s1 : vout.s2);
-  const int64_t lines = B * ea * eb * (int64_t)C;
+  const int CL = C / LPT;  // channel groups
+  const int64_t lines = B * ea * eb * (int64_t)CL;
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < lines;
        idx += (int64_t)gridDim.x * blockDim.x) {
     int64_t t = idx;
-    const int c = (int)(t % C);
-    t /= C;
+    const int c = (int)(t % CL) * LPT;
+    t /= CL;
     const int ib = (int)(t % eb);
     t /= eb;
     const int ia = (int)(t % ea);
     const int64_t b = t / ea;
     const int64_t bs = srcmap ? srcmap[b] : b;
     const T* ip = in + bs * vin.sb + ia * sa_in + ib * sb_in + c;
-    T v[NMAX];
+    T v[NMAX][LPT];
 #pragma unroll
     for (int i = 0; i < NMAX; ++i)
-      if (i < nin) v[i] = ip[i * step_in];
+      if (i < nin)
+#pragma unroll
+        for (int l = 0; l < LPT; ++l) v[i][l] = ip[i * step_in + l];
     const unsigned char* Ms = smem_raw + ((nmat == 2 && sel && sel[3 * b + ax]) ? (size_t)msz * esz : 0);
     T* op = out + b * vout.sb + ia * sa_out + ib * sb_out + c;
     for (int j = 0; j < nout; ++j) {
-      T acc = mk<R>(0, 0);
+      T acc[LPT];
+#pragma unroll
+      for (int l = 0; l < LPT; ++l) acc[l] = mk<R>(0, 0);
       if (CM) {
         const T* M = (const T*)Ms + j * nin;
 #pragma unroll
         for (int i = 0; i < NMAX; ++i)
-          if (i < nin) cfma(acc, M[i], v[i]);
+          if (i < nin) {
+            const T m = M[i];
+#pragma unroll
+            for (int l = 0; l < LPT; ++l) cfma(acc[l], m, v[i][l]);
+          }
       } else {
         const R* M = (const R*)Ms + j * nin;
 #pragma unroll
         for (int i = 0; i < NMAX; ++i)
           if (i < nin) {
-            acc.x = fma(M[i], v[i].x, acc.x);
-            acc.y = fma(M[i], v[i].y, acc.y);
+            const R m = M[i];
+#pragma unroll
+            for (int l = 0; l < LPT; ++l) {
+              acc[l].x = fma(m, v[i][l].x, acc[l].x);
+              acc[l].y = fma(m, v[i][l].y, acc[l].y);
+            }
           }
       }
-      if (accumulate) acc = cadd(acc, op[j * step_out]);
-      op[j * step_out] = acc;
+#pragma unroll
+      for (int l = 0; l < LPT; ++l) {
+        T r = acc[l];
+        if (accumulate) r = cadd(r, op[j * step_out + l]);
+        op[j * step_out + l] = r;
+      }
     }
   }
+}
+
+template <typename R, bool CM, int NMAX, int LPT>
+static void run_mode_line(const cpx_t<R>* in, View vin, cpx_t<R>* out, View vout, int64_t B, int C, int ax,
+                          int nin, int e0, int e1, int e2, const void* M0, const void* M1, const int8_t* sel,
+                          const int64_t* srcmap, bool accumulate, size_t smem, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_mode_line<R, CM, NMAX, LPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    attr = true;
+  }
+  const int ea = ax == 0 ? e1 : e0, eb = ax == 2 ? e1 : e2;
+  int64_t lines = B * ea * eb * (int64_t)(C / LPT);
+  int64_t blocks = ceil_div(lines, 128);
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  k_mode_line<R, CM, NMAX, LPT><<<(unsigned)blocks, 128, smem, s>>>(in, vin, out, vout, B, C, ax, nin, e0, e1, e2,
+                                                                     M0, M1, sel, srcmap, accumulate);
+}
+
+template <typename R, bool CM>
+static bool dispatch_mode_line(const cpx_t<R>* in, View vin, cpx_t<R>* out, View vout, int64_t B, int C, int ax,
+                               int nin, int e0, int e1, int e2, const void* M0, const void* M1,
+                               const int8_t* sel, const int64_t* srcmap, bool accumulate, size_t smem,
+                               cudaStream_t s) {
+  const bool two = (C % 2) == 0 && sizeof(R) == 4;
+#define EFIE_ML(NM)                                                                                          \
+  if (nin <= NM) {                                                                                           \
+    if constexpr (sizeof(R) == 4 && NM <= 21) {                                                              \
+      if (two) {                                                                                             \
+        run_mode_line<R, CM, NM, 2>(in, vin, out, vout, B, C, ax, nin, e0, e1, e2, M0, M1, sel, srcmap,     \
+                                    accumulate, smem, s);                                                    \
+        return true;                                                                                         \
+      }                                                                                                      \
+    }                                                                                                        \
+    run_mode_line<R, CM, NM, 1>(in, vin, out, vout, B, C, ax, nin, e0, e1, e2, M0, M1, sel, srcmap,         \
+                                accumulate, smem, s);                                                        \
+    return true;                                                                                             \
+  }
+  EFIE_ML(9)
+  EFIE_ML(13)
+  EFIE_ML(21)
+  EFIE_ML(40)
+#undef EFIE_ML
+  return false;
 }
 
 template <typename R>
@@ -142,27 +203,12 @@ void launch_mode(const cpx_t<R>* in, View vin, cpx_t<R>* out, View vout, int64_t
   const int nout = ax == 0 ? e0 : (ax == 1 ? e1 : e2);
   const size_t esz = complex_m ? sizeof(cpx_t<R>) : sizeof(R);
   const size_t smem = (size_t)nout * nin * esz * ((M1 && M1 != M0) ? 2 : 1);
-  if (nin <= 40 && smem <= 96 * 1024) {
-    const int ea = ax == 0 ? e1 : e0, eb = ax == 2 ? e1 : e2;
-    int64_t lines = B * ea * eb * (int64_t)C;
-    int64_t blocks = ceil_div(lines, 128);
-    if (blocks > 152 * 32) blocks = 152 * 32;
-    static bool attr[4] = {false, false, false, false};
-    int ai = (sizeof(R) == 8 ? 2 : 0) + (complex_m ? 1 : 0);
-    if (!attr[ai]) {
-      if (complex_m)
-        cudaFuncSetAttribute(k_mode_line<R, true, 40>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-      else
-        cudaFuncSetAttribute(k_mode_line<R, false, 40>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-      attr[ai] = true;
-    }
-    if (complex_m)
-      k_mode_line<R, true, 40><<<(unsigned)blocks, 128, smem, s>>>(in, vin, out, vout, B, C, ax, nin, e0, e1, e2,
-                                                                   M0, M1, sel, srcmap, accumulate);
-    else
-      k_mode_line<R, false, 40><<<(unsigned)blocks, 128, smem, s>>>(in, vin, out, vout, B, C, ax, nin, e0, e1,
-                                                                    e2, M0, M1, sel, srcmap, accumulate);
-    return;
+  if (smem <= 96 * 1024) {
+    bool done = complex_m ? dispatch_mode_line<R, true>(in, vin, out, vout, B, C, ax, nin, e0, e1, e2, M0, M1, sel,
+                                                        srcmap, accumulate, smem, s)
+                          : dispatch_mode_line<R, false>(in, vin, out, vout, B, C, ax, nin, e0, e1, e2, M0, M1,
+                                                         sel, srcmap, accumulate, smem, s);
+    if (done) return;
   }
   int64_t blocks = ceil_div(total, 256);
   if (blocks > 152 * 64) blocks = 152 * 64;
@@ -182,7 +228,7 @@ __global__ void k_anterp(const R* __restrict__ mr, const int32_t* __restrict__ m
                          const R* __restrict__ mt, const int32_t* __restrict__ mt_base,
                          const int32_t* __restrict__ mt_ext, const int64_t* __restrict__ mt_off,
                          const int64_t* __restrict__ box_rwg_ptr, const int64_t* __restrict__ box_tri_ptr,
-                         const double2* __restrict__ xs, int64_t ldx, const double2* __restrict__ rho,
+                         const cpx_t<R>* __restrict__ xs, int64_t ldx, const cpx_t<R>* __restrict__ rho,
                          int64_t ldr, int nr, int rt, cpx_t<R>* __restrict__ q, int sp) {
   extern __shared__ unsigned char smem_raw[];
   R* g = (R*)smem_raw;  // [sp^3][4*rt complex], point stride PS = 8 rt + 1 (odd: no bank conflicts)
@@ -206,11 +252,11 @@ __global__ void k_anterp(const R* __restrict__ mr, const int32_t* __restrict__ m
       int pt = ((b0 + a0) * sp + (b1 + a1)) * sp + (b2 + a2);
       R mv[3] = {m[e], m[ne + e], m[2 * ne + e]};
       for (int r = 0; r < nrt; ++r) {
-        double2 xv = xs[(int64_t)(r0 + r) * ldx + i];
+        const cpx_t<R> xv = xs[(int64_t)(r0 + r) * ldx + i];
         for (int d = 0; d < 3; ++d) {
           R* dst = g + (int64_t)pt * PS + (4 * r + d) * 2;
-          atomicAdd(dst, mv[d] * (R)xv.x);
-          atomicAdd(dst + 1, mv[d] * (R)xv.y);
+          atomicAdd(dst, mv[d] * xv.x);
+          atomicAdd(dst + 1, mv[d] * xv.y);
         }
       }
     }
@@ -226,10 +272,10 @@ __global__ void k_anterp(const R* __restrict__ mr, const int32_t* __restrict__ m
       int pt = ((b0 + a0) * sp + (b1 + a1)) * sp + (b2 + a2);
       R mv = m[e];
       for (int r = 0; r < nrt; ++r) {
-        double2 rv = rho[(int64_t)(r0 + r) * ldr + i];
+        const cpx_t<R> rv = rho[(int64_t)(r0 + r) * ldr + i];
         R* dst = g + (int64_t)pt * PS + (4 * r + 3) * 2;
-        atomicAdd(dst, mv * (R)rv.x);
-        atomicAdd(dst + 1, mv * (R)rv.y);
+        atomicAdd(dst, mv * rv.x);
+        atomicAdd(dst + 1, mv * rv.y);
       }
     }
   }
@@ -247,7 +293,7 @@ template <typename R>
 void launch_anterp(const R* mr, const int32_t* mr_base, const int32_t* mr_ext, const int64_t* mr_off,
                    const R* mt, const int32_t* mt_base, const int32_t* mt_ext, const int64_t* mt_off,
                    const int64_t* box_rwg_ptr, const int64_t* box_tri_ptr, int64_t B,
-                   const double2* xs, int64_t ldx, const double2* rho, int64_t ldr, int nr,
+                   const cpx_t<R>* xs, int64_t ldx, const cpx_t<R>* rho, int64_t ldr, int nr,
                    cpx_t<R>* q, int sp, cudaStream_t s) {
   if (B <= 0 || nr <= 0) return;
   const int64_t npts = (int64_t)sp * sp * sp;
@@ -852,7 +898,7 @@ template void launch_mode<double>(const double2*, View, double2*, View, int64_t,
                                   cudaStream_t);
 template void launch_anterp<float>(const float*, const int32_t*, const int32_t*, const int64_t*, const float*,
                                    const int32_t*, const int32_t*, const int64_t*, const int64_t*,
-                                   const int64_t*, int64_t, const double2*, int64_t, const double2*, int64_t,
+                                   const int64_t*, int64_t, const float2*, int64_t, const float2*, int64_t,
                                    int, float2*, int, cudaStream_t);
 template void launch_anterp<double>(const double*, const int32_t*, const int32_t*, const int64_t*,
                                     const double*, const int32_t*, const int32_t*, const int64_t*,
