@@ -141,6 +141,22 @@ int efie_rwg_edges(const efie_handle *h, int32_t *edge_vertices, int32_t *tri_pm
 int efie_rhs_planewave(efie_handle *h, int n_rhs, const double *khat, const double *pol,
                        void *rhs, void *stream);
 
+/* Same result as efie_rhs_planewave, for callers that must not allocate
+ * device memory once running (a no-allocation or memory-pool policy, loops
+ * that cannot take the synchronisation of cudaMalloc/cudaFree, hosts whose
+ * allocator belongs to another framework).  It calls no cudaMalloc, cudaFree
+ * or allocating library routine: khat and pol are staged in a fixed device
+ * array of the library (4096 plane waves, 192 KiB), which every GPU that loads
+ * the library keeps until the process exits.  n_rhs above 4096 returns
+ * EFIE_EINVAL.  The paper has no counterpart; this is a deployment variant.
+ * Notes: the first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress) with the device current, so make it before any
+ * stream capture; all calls on a device share the array, so calls whose
+ * copies and kernels overlap on the GPU race -- serialise them; the call
+ * synchronises `stream` before returning. */
+int efie_rhs_planewave_noalloc(efie_handle *h, int n_rhs, const double *khat, const double *pol,
+                               void *rhs, void *stream);
+
 /* y = T x for n_rhs vectors (device c128 [n_rhs][N]; x and y must not alias).
  * Uses the handle's precision.  Steps a1-a10: charges, anterpolation, upward
  * transfers, stabilized FFT translations, downward transfers, interpolation,

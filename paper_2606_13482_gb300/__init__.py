@@ -26,7 +26,7 @@ LIB_PATH = os.path.join(HERE, "libefie_gb300.so")
 
 EXPORTED_SYMBOLS = [
     "efie_plan", "efie_plan_matrix", "efie_setup", "efie_num_unknowns", "efie_plan_info",
-    "efie_rwg_edges", "efie_rhs_planewave", "efie_matvec", "efie_matvec_fp64",
+    "efie_rwg_edges", "efie_rhs_planewave", "efie_rhs_planewave_noalloc", "efie_matvec", "efie_matvec_fp64",
     "efie_matvec_parts", "efie_solve", "efie_profile", "efie_profile_read", "efie_launch_count",
     "efie_destroy", "efie_last_error",
 ]
@@ -93,6 +93,7 @@ def load_library(path: str = LIB_PATH):
     lib.efie_plan_info.argtypes = [VP, P(PlanInfo)]
     lib.efie_rwg_edges.argtypes = [VP, P(I32), P(I32)]
     lib.efie_rhs_planewave.argtypes = [VP, ctypes.c_int, P(D), P(D), VP, VP]
+    lib.efie_rhs_planewave_noalloc.argtypes = [VP, ctypes.c_int, P(D), P(D), VP, VP]
     lib.efie_matvec.argtypes = [VP, VP, VP, ctypes.c_int, VP]
     lib.efie_matvec_fp64.argtypes = [VP, VP, VP, ctypes.c_int, VP]
     lib.efie_matvec_parts.argtypes = [VP, VP, VP, VP, ctypes.c_int, VP]
@@ -204,6 +205,16 @@ class EFIE:
             self.h, khat.shape[0], khat.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
             pol.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.c_void_p(out.data_ptr()),
             self._stream()), self.h)
+        return out
+
+    def rhs_planewave_noalloc(self, khat, pol, out):
+        """Plane-wave right-hand sides into the caller's complex128 CUDA tensor
+        `out` [n, N] without any device allocation by the library."""
+        khat = np.ascontiguousarray(np.atleast_2d(khat), dtype=np.float64)
+        pol = np.ascontiguousarray(np.atleast_2d(pol), dtype=np.float64)
+        _check(self.lib, self.lib.efie_rhs_planewave_noalloc(
+            self.h, khat.shape[0], khat.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+            pol.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), self._vec(out), self._stream()), self.h)
         return out
 
     def matvec(self, x, y=None, fp64=False):
