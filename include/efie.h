@@ -181,6 +181,41 @@ int efie_matvec_parts(efie_handle *h, const void *x, void *yA, void *yV, int n_r
 int efie_solve(efie_handle *h, const void *rhs, void *x, int n_rhs, double tol,
                efie_solve_info *info, void *stream);
 
+/* ---- Learned preconditioner (not part of the paper) ----------------------
+ * A message-passing network on the RWG adjacency graph (3 layers, width 64,
+ * bfloat16 weights, FP32 accumulation on the tensor cores) maps a residual to
+ * an approximate error and serves as the flexible right preconditioner of
+ * FGMRES when enabled; a non-finite output switches that right-hand side back
+ * to plain GMRES (efie_solve_info.precond_fallback = 1).  Weights files start
+ * with the 8 bytes "EFIENN01", an int32 count, then float32 parameters. */
+
+/* Residual/error pairs from the plain solver's own runs: e_j = x* - x_j and
+ * r_j = rhs - T x_j for the iterates x_j of restarted GMRES(restart) after
+ * cycles j = 0..n_cycles-1, x* a converged (1e-9) solution.  rhs: device c128
+ * [n_rhs][N]; r_out, e_out: device c128 [n_cycles][n_rhs][N]. */
+int efie_precond_harvest(efie_handle *h, const void *rhs, int n_rhs, int restart, int n_cycles,
+                         void *r_out, void *e_out, void *stream);
+
+/* Train (Adam, batches of 4 pairs) on n_pairs device pairs r, e (c128
+ * [n_pairs][N]) for `epochs` passes.  objective 0 minimises the error loss
+ * |net(r) - e|^2 / |e|^2; objective 1 the residual loss |T net(r) - r|^2 / |r|^2
+ * (T e = r), whose gradient 2 conj(T conj(T z - r)) / |r|^2 costs two fast
+ * matvecs per pair.  Starts from the handle's current weights (or a seeded
+ * initialisation).  loss_out: host array of `epochs` mean losses, or NULL. */
+int efie_precond_train(efie_handle *h, const void *r, const void *e, int n_pairs, int epochs, double lr,
+                       uint64_t seed, int objective, double *loss_out, void *stream);
+int efie_precond_save(const efie_handle *h, const char *path);
+int efie_precond_load(efie_handle *h, const char *path);   /* also enables it */
+int efie_precond_enable(efie_handle *h, int enable);
+/* Copy the parameters out (out != NULL) and/or replace them (in != NULL); n must
+ * equal the network's parameter count. */
+int efie_precond_params(efie_handle *h, float *out, const float *in, int n);
+/* z_i = net(r_i) for n_vec device c128 vectors [n_vec][N]. */
+int efie_precond_apply(efie_handle *h, const void *r, void *z, int n_vec, void *stream);
+/* Loss and parameter gradient (host float[n]) of one pair at the current weights. */
+int efie_precond_gradient(efie_handle *h, const void *r, const void *e, float *grad, double *loss,
+                          void *stream);
+
 /* Kernel-class timing for measurement.  efie_profile(h, 1) clears and starts
  * recording: every later call that launches kernels records a CUDA event pair
  * on the caller's stream around each class of kernels (anterpolation,

@@ -27,7 +27,9 @@ LIB_PATH = os.path.join(HERE, "libefie_gb300.so")
 EXPORTED_SYMBOLS = [
     "efie_plan", "efie_plan_matrix", "efie_setup", "efie_num_unknowns", "efie_plan_info",
     "efie_rwg_edges", "efie_rhs_planewave", "efie_rhs_planewave_noalloc", "efie_matvec", "efie_matvec_fp64",
-    "efie_matvec_parts", "efie_solve", "efie_profile", "efie_profile_read", "efie_launch_count",
+    "efie_matvec_parts", "efie_solve", "efie_precond_harvest", "efie_precond_train", "efie_precond_save",
+    "efie_precond_load", "efie_precond_enable", "efie_precond_params", "efie_precond_apply",
+    "efie_precond_gradient", "efie_profile", "efie_profile_read", "efie_launch_count",
     "efie_destroy", "efie_last_error",
 ]
 
@@ -98,6 +100,16 @@ def load_library(path: str = LIB_PATH):
     lib.efie_matvec_fp64.argtypes = [VP, VP, VP, ctypes.c_int, VP]
     lib.efie_matvec_parts.argtypes = [VP, VP, VP, VP, ctypes.c_int, VP]
     lib.efie_solve.argtypes = [VP, VP, VP, ctypes.c_int, D, P(SolveInfo), VP]
+    F = ctypes.c_float
+    lib.efie_precond_harvest.argtypes = [VP, VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, VP, VP, VP]
+    lib.efie_precond_train.argtypes = [VP, VP, VP, ctypes.c_int, ctypes.c_int, D, ctypes.c_uint64, ctypes.c_int,
+                                       P(D), VP]
+    lib.efie_precond_save.argtypes = [VP, ctypes.c_char_p]
+    lib.efie_precond_load.argtypes = [VP, ctypes.c_char_p]
+    lib.efie_precond_enable.argtypes = [VP, ctypes.c_int]
+    lib.efie_precond_params.argtypes = [VP, P(F), P(F), ctypes.c_int]
+    lib.efie_precond_apply.argtypes = [VP, VP, VP, ctypes.c_int, VP]
+    lib.efie_precond_gradient.argtypes = [VP, VP, VP, P(F), P(D), VP]
     lib.efie_profile.argtypes = [VP, ctypes.c_int]
     lib.efie_profile_read.argtypes = [VP, ctypes.c_int, ctypes.c_char_p, ctypes.c_int, P(D), P(I64)]
     lib.efie_launch_count.argtypes = [VP, P(I64)]
@@ -245,6 +257,63 @@ class EFIE:
                                                   self._stream()), self.h)
         out = [{f: getattr(i, f) for f, _ in SolveInfo._fields_} for i in infos]
         return (x if rhs.dim() == 2 else x[0]), out, rc
+
+    # ---- learned preconditioner (not part of the paper)
+    N_PARAMS = 25218
+
+    def precond_harvest(self, rhs, restart=10, n_cycles=4):
+        """Residual/error pairs from the plain solver's restarted GMRES iterates."""
+        import torch
+        r2 = rhs if rhs.dim() == 2 else rhs.unsqueeze(0)
+        n = r2.shape[0] * n_cycles
+        R = torch.empty((n, self.N), dtype=torch.complex128, device="cuda")
+        Ee = torch.empty_like(R)
+        _check(self.lib, self.lib.efie_precond_harvest(self.h, self._vec(r2), r2.shape[0], restart, n_cycles,
+                                                       ctypes.c_void_p(R.data_ptr()), ctypes.c_void_p(Ee.data_ptr()),
+                                                       self._stream()), self.h)
+        return R, Ee
+
+    def precond_train(self, r, e, epochs=10, lr=1e-3, seed=0, objective="residual"):
+        losses = (ctypes.c_double * epochs)()
+        obj = {"error": 0, "residual": 1}[objective]
+        _check(self.lib, self.lib.efie_precond_train(self.h, self._vec(r), self._vec(e), r.shape[0], epochs, lr,
+                                                     seed, obj, losses, self._stream()), self.h)
+        return list(losses)
+
+    def precond_save(self, path):
+        _check(self.lib, self.lib.efie_precond_save(self.h, path.encode()), self.h)
+
+    def precond_load(self, path):
+        _check(self.lib, self.lib.efie_precond_load(self.h, path.encode()), self.h)
+
+    def precond_enable(self, on: bool):
+        _check(self.lib, self.lib.efie_precond_enable(self.h, 1 if on else 0), self.h)
+
+    def precond_params(self, new=None):
+        out = np.zeros(self.N_PARAMS, dtype=np.float32)
+        pin = None
+        if new is not None:
+            new = np.ascontiguousarray(new, dtype=np.float32)
+            pin = new.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+        _check(self.lib, self.lib.efie_precond_params(self.h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                                      pin, self.N_PARAMS), self.h)
+        return out
+
+    def precond_apply(self, r):
+        import torch
+        r2 = r if r.dim() == 2 else r.unsqueeze(0)
+        z = torch.empty_like(r2)
+        _check(self.lib, self.lib.efie_precond_apply(self.h, self._vec(r2), self._vec(z), r2.shape[0],
+                                                     self._stream()), self.h)
+        return z if r.dim() == 2 else z[0]
+
+    def precond_gradient(self, r, e):
+        g = np.zeros(self.N_PARAMS, dtype=np.float32)
+        loss = ctypes.c_double()
+        _check(self.lib, self.lib.efie_precond_gradient(self.h, self._vec(r), self._vec(e),
+                                                        g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                                        ctypes.byref(loss), self._stream()), self.h)
+        return g, loss.value
 
     def profile(self, enable: bool):
         _check(self.lib, self.lib.efie_profile(self.h, 1 if enable else 0), self.h)

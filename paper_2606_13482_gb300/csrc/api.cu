@@ -7,6 +7,7 @@
 #include <complex>
 #include <cstring>
 #include <memory>
+#include <random>
 #include <string>
 #include <vector>
 
@@ -17,6 +18,22 @@
 
 namespace efie {
 int upload_rhs_rule(const double* q6);
+struct Net;
+int nn_param_count();
+void nn_init_params(std::vector<float>& p, uint64_t seed);
+void nn_setup(Net& net, int64_t N, const std::vector<int32_t>& nbr, const std::vector<float>& sgn,
+              const std::vector<float>& lnorm, const std::vector<float>& params, bool training);
+void nn_free(Net& net);
+void nn_forward(Net& net, const double2* r, double2* z, bool training, cudaStream_t s);
+void nn_backward(Net& net, const double2* z, const double2* e, double2* gbuf, cudaStream_t s);
+void nn_backward_g(Net& net, const double2* gz, cudaStream_t s);
+void nn_zero_grad(Net& net, cudaStream_t s);
+void nn_adam(Net& net, float lr, float gscale, cudaStream_t s);
+void nn_read_params(Net& net, std::vector<float>& out);
+void nn_read_grads(Net& net, std::vector<float>& out);
+void nn_loss_terms(Net& net, double* num, double* den);
+Net* nn_new();
+void nn_delete(Net* n);
 }
 
 using namespace efie;
@@ -130,6 +147,15 @@ struct Prof {
 
 struct efie_handle {
   Prof prof;
+  // learned preconditioner
+  efie::Net* net = nullptr;
+  bool net_training = false;
+  std::vector<float> net_params;
+  std::vector<int32_t> g_nbr;
+  std::vector<float> g_sgn, g_len;
+  ~efie_handle() {
+    if (net) efie::nn_delete(net);
+  }
   int64_t n_launches = 0;
   Plan plan;
   efie_options opt{};
@@ -168,6 +194,8 @@ struct efie_handle {
 };
 
 namespace {
+void net_activate(efie_handle* h, const std::vector<float>& params, bool training);
+bool read_weights(const char* path, std::vector<float>& p);
 
 // RAII scope around the launches of one kernel class: counts launches and,
 // while profiling is on, records an event pair on the launching stream.
@@ -718,6 +746,10 @@ void setup_impl(efie_handle* h, const efie_mesh* mesh, double k, int p, double g
     }
   }
   // far products
+  if (h->opt.precond == EFIE_PRECOND_LEARNED && h->opt.weights_path) {
+    std::vector<float> w;
+    if (read_weights(h->opt.weights_path, w)) net_activate(h, w, false);  // else: plain GMRES (fallback flag)
+  }
   build_far<double>(h, h->f64, s);
   std::vector<double2*> K64 = build_kernel_spectra64(h, s);
   build_spectra<double>(h, h->f64, K64, s);
@@ -734,13 +766,20 @@ struct Givens {
 };
 
 int solve_impl(efie_handle* h, const double2* b, double2* x, int n_rhs, double tol, efie_solve_info* info,
-               cudaStream_t s) {
+               cudaStream_t s, double2* rec = nullptr, int rec_cycles = 0) {
   if (!(tol > 0)) throw EfieError{EFIE_EINVAL, "tol must be positive"};
+  // the working-precision (estimated and restart) residuals aim at tol/2 so that
+  // the final FP64 true residual meets tol
+  const double tol_in = 0.5 * tol;
   const int64_t N = h->plan.g.N;
   const int m = h->opt.gmres_restart;
-  const int max_it = h->opt.max_iters;
+  const int max_it = rec ? m * rec_cycles : h->opt.max_iters;
+  int cycle = 0;
   // device workspace
   double2* Vb = h->mem.alloc<double2>((int64_t)n_rhs * (m + 1) * N);
+  const bool use_pc = h->net != nullptr && h->opt.precond == EFIE_PRECOND_LEARNED;
+  double2* Zb = use_pc ? h->mem.alloc<double2>((int64_t)n_rhs * m * N) : nullptr;
+  std::vector<int> pc_fallback(n_rhs, 0);
   double2* wv = h->mem.alloc<double2>((int64_t)n_rhs * N);
   double2* rv = h->mem.alloc<double2>((int64_t)n_rhs * N);
   double2* dh = h->mem.alloc<double2>((int64_t)n_rhs * (m + 1));
@@ -777,7 +816,7 @@ int solve_impl(efie_handle* h, const double2* b, double2* x, int n_rhs, double t
   while (true) {
     bool any = false;
     for (int r = 0; r < n_rhs; ++r) {
-      if (act[r] && (beta[r] / bnorm[r] <= tol || its[r] >= max_it)) act[r] = 0;
+      if (act[r] && (beta[r] / bnorm[r] <= tol_in || its[r] >= max_it)) act[r] = 0;
       any |= act[r] != 0;
     }
     if (!any) break;
@@ -802,8 +841,30 @@ int solve_impl(efie_handle* h, const double2* b, double2* x, int n_rhs, double t
       if (!anyin) break;
       std::vector<int> ia(inner);
       cuda_check(cudaMemcpyAsync(dact, ia.data(), sizeof(int) * n_rhs, cudaMemcpyHostToDevice, s), "act");
-      // w = T v_k (all rhs; inactive ones are ignored)
-      do_matvec(h, Vb + (int64_t)k * N, ldr, wv, nullptr, nullptr, N, n_rhs, false, s);
+      // z_k = M(v_k) (flexible right preconditioner), w = T z_k
+      const double2* zk = Vb + (int64_t)k * N;
+      int64_t ldz = ldr;
+      if (use_pc) {
+        KScope ks(h, K_PRECOND, s, 6);
+        for (int r = 0; r < n_rhs; ++r) {
+          double2* zr = Zb + (int64_t)r * m * N + (int64_t)k * N;
+          const double2* vr = Vb + r * ldr + (int64_t)k * N;
+          if (inner[r] && !pc_fallback[r]) {
+            efie::nn_forward(*h->net, vr, zr, false, s);
+            // non-finite network output: identity for the rest of this solve
+            double nz = 0;
+            launch_norms(zr, N, N, 1, dn, s);
+            cuda_check(cudaMemcpyAsync(&nz, dn, sizeof(double), cudaMemcpyDeviceToHost, s), "d2h");
+            cuda_check(cudaStreamSynchronize(s), "sync");
+            if (!std::isfinite(nz) || nz == 0) pc_fallback[r] = 1;
+          }
+          if (!inner[r] || pc_fallback[r])
+            cuda_check(cudaMemcpyAsync(zr, vr, sizeof(double2) * N, cudaMemcpyDeviceToDevice, s), "copy");
+        }
+        zk = Zb + (int64_t)k * N;
+        ldz = (int64_t)m * N;
+      }
+      do_matvec(h, zk, ldz, wv, nullptr, nullptr, N, n_rhs, false, s);
       // CGS2
       KScope ks(h, K_KRYLOV, s, 5);
       launch_multidot(Vb, ldr, N, k + 1, wv, N, N, n_rhs, dact, dh, s);
@@ -835,7 +896,7 @@ int solve_impl(efie_handle* h, const double2* b, double2* x, int n_rhs, double t
         gg[r][k] = std::conj(cs[r][k]) * gg[r][k];
         its[r]++;
         kdim[r] = k + 1;
-        if (std::abs(gg[r][k + 1]) / bnorm[r] <= tol || its[r] >= max_it || nrm[r] == 0) inner[r] = 0;
+        if (std::abs(gg[r][k + 1]) / bnorm[r] <= tol_in || its[r] >= max_it || nrm[r] == 0) inner[r] = 0;
       }
       // v_{k+1} = w / ||w||
       std::vector<std::complex<double>> scv(sc);
@@ -858,11 +919,24 @@ int solve_impl(efie_handle* h, const double2* b, double2* x, int n_rhs, double t
     }
     cuda_check(cudaMemcpyAsync(dh, yv.data(), sizeof(double2) * n_rhs * m, cudaMemcpyHostToDevice, s), "y");
     cuda_check(cudaMemcpyAsync(dact, act.data(), sizeof(int) * n_rhs, cudaMemcpyHostToDevice, s), "act");
-    launch_multiaxpy(Vb, ldr, N, m, dh, m, x, N, N, n_rhs, dact, 1.0, s);
+    if (use_pc)
+      launch_multiaxpy(Zb, (int64_t)m * N, N, m, dh, m, x, N, N, n_rhs, dact, 1.0, s);
+    else
+      launch_multiaxpy(Vb, ldr, N, m, dh, m, x, N, N, n_rhs, dact, 1.0, s);
+    if (rec && cycle < rec_cycles)
+      cuda_check(cudaMemcpyAsync(rec + (int64_t)cycle * n_rhs * N, x, sizeof(double2) * n_rhs * N,
+                                 cudaMemcpyDeviceToDevice, s), "record");
+    ++cycle;
     // restart residual r = b - T x (working precision)
     do_matvec(h, x, N, wv, nullptr, nullptr, N, n_rhs, false, s);
     launch_lincomb(b, wv, 1.0, -1.0, rv, (int64_t)n_rhs * N, s);
+    std::vector<double> beta_prev(beta);
     norms(rv, N, beta);
+    // a flexible cycle that made no progress (< 1%) hands this right-hand side
+    // back to plain GMRES
+    if (use_pc)
+      for (int r = 0; r < n_rhs; ++r)
+        if (act[r] && !pc_fallback[r] && beta[r] > 0.99 * beta_prev[r]) pc_fallback[r] = 1;
   }
   // true residual with the FP64 fast matvec
   do_matvec(h, x, N, wv, nullptr, nullptr, N, n_rhs, true, s);
@@ -877,10 +951,11 @@ int solve_impl(efie_handle* h, const double2* b, double2* x, int n_rhs, double t
       info[r].iterations = its[r];
       info[r].true_rel_residual = rel;
       info[r].converged = conv[r];
-      info[r].precond_fallback = 0;
+      info[r].precond_fallback = (h->opt.precond == EFIE_PRECOND_LEARNED && (!use_pc || pc_fallback[r])) ? 1 : 0;
     }
   }
   for (void* p : {(void*)Vb, (void*)wv, (void*)rv, (void*)dh, (void*)dh2, (void*)dn, (void*)dact}) h->mem.release(p);
+  if (Zb) h->mem.release(Zb);
   return ret;
 }
 
@@ -941,6 +1016,80 @@ void fill_plan_info(const Plan& P, efie_plan_info_t* info, efie_level_info_t* lv
   }
 }
 
+}  // namespace
+
+namespace {
+// RWG adjacency: neighbours share a triangle c, sign sigma_{m,c} sigma_{n,c}
+void build_nn_graph(efie_handle* h) {
+  if (!h->g_nbr.empty()) return;
+  const Geometry& g = h->plan.g;
+  const int64_t N = g.N, nt = g.nt;
+  std::vector<int32_t> tr(3 * nt, -1);
+  std::vector<float> ts(3 * nt, 0.f);
+  std::vector<int> cnt(nt, 0);
+  for (int64_t m = 0; m < N; ++m)
+    for (int sd = 0; sd < 2; ++sd) {
+      int32_t t = g.tri_pm[2 * m + sd];
+      tr[3 * t + cnt[t]] = (int32_t)m;
+      ts[3 * t + cnt[t]] = sd == 0 ? 1.f : -1.f;
+      cnt[t]++;
+    }
+  h->g_nbr.assign(4 * N, -1);
+  h->g_sgn.assign(4 * N, 0.f);
+  std::vector<int> nc(N, 0);
+  for (int64_t t = 0; t < nt; ++t)
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) {
+        if (a == b || tr[3 * t + a] < 0 || tr[3 * t + b] < 0) continue;
+        int32_t m = tr[3 * t + a];
+        if (nc[m] >= 4) continue;
+        h->g_nbr[4 * m + nc[m]] = tr[3 * t + b];
+        h->g_sgn[4 * m + nc[m]] = ts[3 * t + a] * ts[3 * t + b];
+        nc[m]++;
+      }
+  h->g_len.resize(N);
+  double mean = 0;
+  for (int64_t m = 0; m < N; ++m) {
+    double d2 = 0;
+    for (int d = 0; d < 3; ++d) {
+      double t = g.V[3 * g.edge[2 * m] + d] - g.V[3 * g.edge[2 * m + 1] + d];
+      d2 += t * t;
+    }
+    h->g_len[m] = (float)std::sqrt(d2);
+    mean += h->g_len[m];
+  }
+  mean /= (double)N;
+  for (auto& l : h->g_len) l = (float)(l / mean);
+}
+
+void net_activate(efie_handle* h, const std::vector<float>& params, bool training) {
+  build_nn_graph(h);
+  if (h->net) {
+    efie::nn_delete(h->net);
+    h->net = nullptr;
+  }
+  h->net = efie::nn_new();
+  efie::nn_setup(*h->net, h->plan.g.N, h->g_nbr, h->g_sgn, h->g_len, params, training);
+  h->net_params = params;
+  h->net_training = training;
+}
+
+bool read_weights(const char* path, std::vector<float>& p) {
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return false;
+  char magic[8] = {0};
+  int32_t n = 0;
+  bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, "EFIENN01", 8) == 0 &&
+            std::fread(&n, sizeof(n), 1, f) == 1 && n == efie::nn_param_count();
+  if (ok) {
+    p.resize(n);
+    ok = std::fread(p.data(), sizeof(float), n, f) == (size_t)n;
+  }
+  std::fclose(f);
+  for (float v : p)
+    if (!std::isfinite(v)) ok = false;
+  return ok;
+}
 }  // namespace
 
 namespace efie {
@@ -1156,6 +1305,194 @@ int efie_launch_count(const efie_handle* h, int64_t* n) {
   if (!h || !n) return EFIE_EINVAL;
   *n = h->n_launches;
   return EFIE_OK;
+}
+
+int efie_precond_harvest(efie_handle* h, const void* rhs, int n_rhs, int restart, int n_cycles, void* r_out,
+                         void* e_out, void* stream) {
+  if (!h) return EFIE_EINVAL;
+  return guarded(h, [&] {
+    if (n_rhs <= 0 || restart <= 0 || n_cycles <= 0 || !rhs || !r_out || !e_out)
+      throw EfieError{EFIE_EINVAL, "bad arguments"};
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t N = h->plan.g.N;
+    const double2* b = (const double2*)rhs;
+    efie_options saved = h->opt;
+    h->opt.precond = EFIE_PRECOND_NONE;
+    // reference solution of the plain solver
+    double2* xs = h->mem.alloc<double2>((int64_t)n_rhs * N);
+    double2* rec = h->mem.alloc<double2>((int64_t)n_cycles * n_rhs * N);
+    double2* tmp = h->mem.alloc<double2>((int64_t)n_rhs * N);
+    h->opt.max_iters = std::max(saved.max_iters, 2000);
+    solve_impl(h, b, xs, n_rhs, 1e-9, nullptr, s);
+    // iterates of restarted GMRES(restart): x_j after cycle j
+    h->opt.gmres_restart = restart;
+    cuda_check(cudaMemsetAsync(rec, 0, sizeof(double2) * n_cycles * n_rhs * N, s), "rec");
+    solve_impl(h, b, tmp, n_rhs, 1e-300, nullptr, s, rec, n_cycles);
+    h->opt = saved;
+    double2* ro = (double2*)r_out;
+    double2* eo = (double2*)e_out;
+    for (int c = 0; c < n_cycles; ++c) {
+      double2* xc = rec + (int64_t)c * n_rhs * N;
+      launch_lincomb(xs, xc, 1.0, -1.0, eo + (int64_t)c * n_rhs * N, (int64_t)n_rhs * N, s);
+      do_matvec(h, xc, N, tmp, nullptr, nullptr, N, n_rhs, true, s);
+      launch_lincomb(b, tmp, 1.0, -1.0, ro + (int64_t)c * n_rhs * N, (int64_t)n_rhs * N, s);
+    }
+    cuda_check(cudaStreamSynchronize(s), "harvest");
+    h->mem.release(xs);
+    h->mem.release(rec);
+    h->mem.release(tmp);
+    return EFIE_OK;
+  });
+}
+
+int efie_precond_train(efie_handle* h, const void* r, const void* e, int n_pairs, int epochs, double lr,
+                       uint64_t seed, int objective, double* loss_out, void* stream) {
+  if (!h) return EFIE_EINVAL;
+  return guarded(h, [&] {
+    if (n_pairs <= 0 || epochs <= 0 || !(lr > 0) || !r || !e || objective < 0 || objective > 1)
+      throw EfieError{EFIE_EINVAL, "bad arguments"};
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t N = h->plan.g.N;
+    std::vector<float> p = h->net_params;
+    if ((int)p.size() != efie::nn_param_count()) efie::nn_init_params(p, seed);
+    net_activate(h, p, true);
+    double2* z = h->mem.alloc<double2>(N);
+    double2* g = h->mem.alloc<double2>(N);
+    double2* w = h->mem.alloc<double2>(N);
+    double2* t = h->mem.alloc<double2>(N);
+    double* dn = h->mem.alloc<double>(2);
+    std::mt19937_64 rng(seed);
+    std::vector<int> order(n_pairs);
+    const int batch = 4;
+    for (int ep = 0; ep < epochs; ++ep) {
+      for (int i = 0; i < n_pairs; ++i) order[i] = i;
+      std::shuffle(order.begin(), order.end(), rng);
+      double lsum = 0;
+      for (int b0 = 0; b0 < n_pairs; b0 += batch) {
+        const int nb = std::min(batch, n_pairs - b0);
+        efie::nn_zero_grad(*h->net, s);
+        for (int q = 0; q < nb; ++q) {
+          const int i = order[b0 + q];
+          const double2* ri = (const double2*)r + (int64_t)i * N;
+          const double2* ei = (const double2*)e + (int64_t)i * N;
+          efie::nn_forward(*h->net, ri, z, true, s);
+          double num = 0, den = 1;
+          if (objective == 0) {
+            efie::nn_backward(*h->net, z, ei, g, s);
+            cuda_check(cudaStreamSynchronize(s), "train");
+            efie::nn_loss_terms(*h->net, &num, &den);
+          } else {
+            // L = |T z - r|^2 / |r|^2 ; dL/dz = 2 conj(T conj(T z - r)) / |r|^2 (T = T^T)
+            do_matvec(h, z, N, w, nullptr, nullptr, N, 1, false, s);
+            launch_lincomb(w, ri, 1.0, -1.0, w, N, s);
+            launch_norms(w, N, N, 1, dn, s);
+            launch_norms(ri, N, N, 1, dn + 1, s);
+            double nn2[2];
+            cuda_check(cudaMemcpyAsync(nn2, dn, sizeof(double) * 2, cudaMemcpyDeviceToHost, s), "d2h");
+            cuda_check(cudaStreamSynchronize(s), "train");
+            num = nn2[0];
+            den = nn2[1];
+            launch_conj_scale(w, 1.0, t, N, s);
+            do_matvec(h, t, N, g, nullptr, nullptr, N, 1, false, s);
+            launch_conj_scale(g, den > 0 ? 2.0 / den : 0.0, g, N, s);
+            efie::nn_backward_g(*h->net, g, s);
+          }
+          lsum += den > 0 ? num / den : 0.0;
+        }
+        efie::nn_adam(*h->net, (float)lr, 1.0f / (float)nb, s);
+      }
+      if (loss_out) loss_out[ep] = lsum / n_pairs;
+    }
+    cuda_check(cudaStreamSynchronize(s), "train");
+    efie::nn_read_params(*h->net, p);
+    for (void* q : {(void*)z, (void*)g, (void*)w, (void*)t, (void*)dn}) h->mem.release(q);
+    for (float v : p)
+      if (!std::isfinite(v)) throw EfieError{EFIE_EINVAL, "training diverged (non-finite weights)"};
+    net_activate(h, p, false);
+    return EFIE_OK;
+  });
+}
+
+int efie_precond_save(const efie_handle* h, const char* path) {
+  if (!h || !path || h->net_params.empty()) return EFIE_EINVAL;
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return EFIE_EINVAL;
+  int32_t n = (int32_t)h->net_params.size();
+  bool ok = std::fwrite("EFIENN01", 1, 8, f) == 8 && std::fwrite(&n, sizeof(n), 1, f) == 1 &&
+            std::fwrite(h->net_params.data(), sizeof(float), n, f) == (size_t)n;
+  std::fclose(f);
+  return ok ? EFIE_OK : EFIE_EINVAL;
+}
+
+int efie_precond_load(efie_handle* h, const char* path) {
+  if (!h || !path) return EFIE_EINVAL;
+  return guarded(h, [&] {
+    std::vector<float> w;
+    if (!read_weights(path, w)) throw EfieError{EFIE_EINVAL, std::string("cannot read weights: ") + path};
+    net_activate(h, w, false);
+    h->opt.precond = EFIE_PRECOND_LEARNED;
+    return EFIE_OK;
+  });
+}
+
+int efie_precond_enable(efie_handle* h, int enable) {
+  if (!h) return EFIE_EINVAL;
+  h->opt.precond = enable ? EFIE_PRECOND_LEARNED : EFIE_PRECOND_NONE;
+  return EFIE_OK;
+}
+
+int efie_precond_params(efie_handle* h, float* out, const float* in, int n) {
+  if (!h || n != efie::nn_param_count()) return EFIE_EINVAL;
+  return guarded(h, [&] {
+    if (in) {
+      std::vector<float> p(in, in + n);
+      net_activate(h, p, false);
+    }
+    if (out) {
+      if (h->net_params.empty()) throw EfieError{EFIE_EINVAL, "no network parameters"};
+      std::memcpy(out, h->net_params.data(), sizeof(float) * n);
+    }
+    return EFIE_OK;
+  });
+}
+
+int efie_precond_apply(efie_handle* h, const void* r, void* z, int n_vec, void* stream) {
+  if (!h) return EFIE_EINVAL;
+  return guarded(h, [&] {
+    if (!h->net) throw EfieError{EFIE_EINVAL, "no network loaded"};
+    const int64_t N = h->plan.g.N;
+    KScope ks(h, K_PRECOND, (cudaStream_t)stream, 6 * n_vec);
+    for (int i = 0; i < n_vec; ++i)
+      efie::nn_forward(*h->net, (const double2*)r + (int64_t)i * N, (double2*)z + (int64_t)i * N, false,
+                       (cudaStream_t)stream);
+    return EFIE_OK;
+  });
+}
+
+int efie_precond_gradient(efie_handle* h, const void* r, const void* e, float* grad, double* loss, void* stream) {
+  if (!h) return EFIE_EINVAL;
+  return guarded(h, [&] {
+    if (h->net_params.empty()) throw EfieError{EFIE_EINVAL, "no network parameters"};
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<float> p = h->net_params;
+    net_activate(h, p, true);
+    double2* z = h->mem.alloc<double2>(h->plan.g.N);
+    double2* gb = h->mem.alloc<double2>(h->plan.g.N);
+    efie::nn_zero_grad(*h->net, s);
+    efie::nn_forward(*h->net, (const double2*)r, z, true, s);
+    efie::nn_backward(*h->net, z, (const double2*)e, gb, s);
+    cuda_check(cudaStreamSynchronize(s), "gradient");
+    double num = 0, den = 1;
+    efie::nn_loss_terms(*h->net, &num, &den);
+    if (loss) *loss = num / den;
+    std::vector<float> g;
+    efie::nn_read_grads(*h->net, g);
+    if (grad) std::memcpy(grad, g.data(), sizeof(float) * g.size());
+    h->mem.release(z);
+    h->mem.release(gb);
+    net_activate(h, p, false);
+    return EFIE_OK;
+  });
 }
 
 int efie_destroy(efie_handle* h) {

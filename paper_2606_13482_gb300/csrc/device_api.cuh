@@ -111,6 +111,7 @@ void launch_multiaxpy(const double2* Vb, int64_t ldv_r, int64_t ldv_i, int nbasi
                       double sign, cudaStream_t s);
 void launch_lincomb(const double2* x, const double2* y, double a, double b, double2* out, int64_t n,
                     cudaStream_t s);
+void launch_conj_scale(const double2* x, double a, double2* out, int64_t n, cudaStream_t s);
 void launch_norms(const double2* w, int64_t ldw, int64_t N, int nr, double* out, cudaStream_t s);
 
 }  // namespace efie

@@ -860,6 +860,20 @@ void launch_lincomb(const double2* x, const double2* y, double a, double b, doub
   k_lincomb<<<(unsigned)blocks, 256, 0, s>>>(x, y, a, b, out, n);
 }
 
+// out = a conj(x)
+__global__ void k_conj_scale(const double2* __restrict__ x, double a, double2* __restrict__ out, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double2 v = x[i];
+    out[i] = make_double2(a * v.x, -a * v.y);
+  }
+}
+void launch_conj_scale(const double2* x, double a, double2* out, int64_t n, cudaStream_t s) {
+  if (n <= 0) return;
+  int64_t blocks = ceil_div(n, 256);
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  k_conj_scale<<<(unsigned)blocks, 256, 0, s>>>(x, a, out, n);
+}
+
 __global__ void k_norms(const double2* __restrict__ w, int64_t ldw, int64_t N, double* out) {
   int r = blockIdx.y;
   double s = 0;
