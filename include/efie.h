@@ -216,6 +216,25 @@ int efie_precond_apply(efie_handle *h, const void *r, void *z, int n_vec, void *
 int efie_precond_gradient(efie_handle *h, const void *r, const void *e, float *grad, double *loss,
                           void *stream);
 
+/* ---- Batching over right-hand sides and meshes ----------------------------
+ * efie_autotune times one product of n_rhs vectors for each candidate
+ * right-hand-side chunk (8, 4, 2, 1 vectors per far-field pass) and each
+ * top-level translation kernel (shared-memory staged, register tiles) and keeps
+ * the fastest in the handle; the choices are returned if the pointers are set. */
+int efie_autotune(efie_handle *h, int n_rhs, void *stream, int *best_chunk, int *best_mac);
+
+/* A batch groups set-up handles (meshes of any size, same device).  Each
+ * efie_batch_matvec runs y[i] = T_i x[i] (n_rhs[i] vectors, device c128) for
+ * every member as ONE CUDA graph launch on `stream` (any stream, the legacy
+ * default one included: capture uses an internal stream), each member on its
+ * own branch of the graph.  The graph is captured on the first call and re-captured
+ * whenever the pointers or counts change (that call also runs the products
+ * once uncaptured to allocate the members' work buffers). */
+typedef struct efie_batch efie_batch;
+int efie_batch_create(efie_handle *const *hs, int n, efie_batch **out);
+int efie_batch_matvec(efie_batch *b, const void *const *x, void *const *y, const int *n_rhs, void *stream);
+int efie_batch_destroy(efie_batch *b);
+
 /* Kernel-class timing for measurement.  efie_profile(h, 1) clears and starts
  * recording: every later call that launches kernels records a CUDA event pair
  * on the caller's stream around each class of kernels (anterpolation,

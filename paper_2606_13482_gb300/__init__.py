@@ -13,7 +13,7 @@ import os
 
 import numpy as np
 
-__all__ = ["load_library", "Options", "EFIE", "plan", "plan_matrix", "EfieError",
+__all__ = ["load_library", "Options", "EFIE", "Batch", "plan", "plan_matrix", "EfieError",
            "EFIE_FP64", "EFIE_MIXED", "EFIE_PRECOND_NONE", "EFIE_PRECOND_LEARNED",
            "EXPORTED_SYMBOLS"]
 
@@ -29,7 +29,8 @@ EXPORTED_SYMBOLS = [
     "efie_rwg_edges", "efie_rhs_planewave", "efie_rhs_planewave_noalloc", "efie_matvec", "efie_matvec_fp64",
     "efie_matvec_parts", "efie_solve", "efie_precond_harvest", "efie_precond_train", "efie_precond_save",
     "efie_precond_load", "efie_precond_enable", "efie_precond_params", "efie_precond_apply",
-    "efie_precond_gradient", "efie_profile", "efie_profile_read", "efie_launch_count",
+    "efie_precond_gradient", "efie_autotune", "efie_batch_create", "efie_batch_matvec", "efie_batch_destroy",
+    "efie_profile", "efie_profile_read", "efie_launch_count",
     "efie_destroy", "efie_last_error",
 ]
 
@@ -110,6 +111,10 @@ def load_library(path: str = LIB_PATH):
     lib.efie_precond_params.argtypes = [VP, P(F), P(F), ctypes.c_int]
     lib.efie_precond_apply.argtypes = [VP, VP, VP, ctypes.c_int, VP]
     lib.efie_precond_gradient.argtypes = [VP, VP, VP, P(F), P(D), VP]
+    lib.efie_autotune.argtypes = [VP, ctypes.c_int, VP, P(ctypes.c_int), P(ctypes.c_int)]
+    lib.efie_batch_create.argtypes = [P(VP), ctypes.c_int, P(VP)]
+    lib.efie_batch_matvec.argtypes = [VP, P(VP), P(VP), P(ctypes.c_int), VP]
+    lib.efie_batch_destroy.argtypes = [VP]
     lib.efie_profile.argtypes = [VP, ctypes.c_int]
     lib.efie_profile_read.argtypes = [VP, ctypes.c_int, ctypes.c_char_p, ctypes.c_int, P(D), P(I64)]
     lib.efie_launch_count.argtypes = [VP, P(I64)]
@@ -132,6 +137,39 @@ def _check(lib, rc, h=None):
     if rc < 0:
         raise EfieError(rc, lib.efie_last_error(h).decode())
     return rc
+
+
+class Batch:
+    """Set-up handles whose products run as one CUDA graph launch."""
+
+    def __init__(self, handles):
+        self.lib = load_library()
+        self.handles = list(handles)
+        arr = (ctypes.c_void_p * len(self.handles))(*[h.h.value for h in self.handles])
+        b = ctypes.c_void_p()
+        _check(self.lib, self.lib.efie_batch_create(arr, len(self.handles), ctypes.byref(b)))
+        self.b = b
+
+    def matvec(self, xs, ys):
+        import torch
+        n = len(self.handles)
+        X = (ctypes.c_void_p * n)(*[x.data_ptr() for x in xs])
+        Y = (ctypes.c_void_p * n)(*[y.data_ptr() for y in ys])
+        R = (ctypes.c_int * n)(*[x.shape[0] for x in xs])
+        _check(self.lib, self.lib.efie_batch_matvec(self.b, X, Y, R,
+                                                    ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)))
+        return ys
+
+    def close(self):
+        if getattr(self, "b", None):
+            self.lib.efie_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def plan(V, T, k, p, grid_spacing, levels, options: Options | None = None):
@@ -314,6 +352,12 @@ class EFIE:
                                                         g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
                                                         ctypes.byref(loss), self._stream()), self.h)
         return g, loss.value
+
+    def autotune(self, n_rhs):
+        c, m = ctypes.c_int(), ctypes.c_int()
+        _check(self.lib, self.lib.efie_autotune(self.h, n_rhs, self._stream(), ctypes.byref(c), ctypes.byref(m)),
+               self.h)
+        return c.value, m.value
 
     def profile(self, enable: bool):
         _check(self.lib, self.lib.efie_profile(self.h, 1 if enable else 0), self.h)

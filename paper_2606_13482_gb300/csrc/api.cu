@@ -185,6 +185,7 @@ struct efie_handle {
   std::vector<LevDev> lev;
   FarSet<double> f64;
   FarSet<float> f32;
+  int mac_variant = 0;   // 0 auto, 1 register tiles only (autotuner knob)
   // work vectors (FP64, sorted) and their double-float splits
   int Rw = 0;
   double2 *xs = nullptr, *rho = nullptr, *yA = nullptr, *w = nullptr;
@@ -471,8 +472,8 @@ void far_chunk(efie_handle* h, FarSet<R>& F, int nr, cudaStream_t s) {
     }
     {
       KScope ks(h, ell == top ? K_MAC_TOP : K_MAC, s, 1);
-      launch_mac<R>(F.Qh, F.Rh, FL.Kh, B, C, LD.O, n3, LD.ntiles, LD.max_tile, LD.tile_tgt_ptr, LD.tile_tgt,
-                    LD.tile_src_ptr, LD.tile_src, LD.tile_kidx_off, LD.tile_kidx, s);
+      launch_mac<R>(F.Qh, F.Rh, FL.Kh, B, C, LD.O, n3, LD.ntiles, h->mac_variant == 1 ? -LD.max_tile : LD.max_tile,
+                    LD.tile_tgt_ptr, LD.tile_tgt, LD.tile_src_ptr, LD.tile_src, LD.tile_kidx_off, LD.tile_kidx, s);
     }
     KScope ks(h, K_INV, s, 3);
     View b1{(int64_t)sp * n * n * C, (int64_t)n * n * C, (int64_t)n * C, C};
@@ -1495,9 +1496,184 @@ int efie_precond_gradient(efie_handle* h, const void* r, const void* e, float* g
   });
 }
 
+int efie_autotune(efie_handle* h, int n_rhs, void* stream, int* best_chunk, int* best_mac) {
+  if (!h) return EFIE_EINVAL;
+  return guarded(h, [&] {
+    if (n_rhs <= 0) throw EfieError{EFIE_EINVAL, "n_rhs must be positive"};
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t N = h->plan.g.N;
+    double2* x = h->mem.alloc<double2>((int64_t)n_rhs * N);
+    double2* y = h->mem.alloc<double2>((int64_t)n_rhs * N);
+    cuda_check(cudaMemsetAsync(x, 0, sizeof(double2) * n_rhs * N, s), "x");
+    const bool prof = h->prof.on;
+    h->prof.on = false;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    int bc = 8, bm = 0;
+    for (int chunk : {8, 4, 2, 1}) {
+      if (chunk > n_rhs && chunk != 1) continue;
+      for (int mv : {0, 1}) {
+        h->opt.rhs_chunk = chunk;
+        h->mac_variant = mv;
+        do_matvec(h, x, N, y, nullptr, nullptr, N, n_rhs, false, s);  // warm-up / allocation
+        cudaEventRecord(e0, s);
+        do_matvec(h, x, N, y, nullptr, nullptr, N, n_rhs, false, s);
+        cudaEventRecord(e1, s);
+        cuda_check(cudaEventSynchronize(e1), "autotune");
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+          best = ms;
+          bc = chunk;
+          bm = mv;
+        }
+      }
+    }
+    h->opt.rhs_chunk = bc;
+    h->mac_variant = bm;
+    h->prof.on = prof;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->mem.release(x);
+    h->mem.release(y);
+    if (best_chunk) *best_chunk = bc;
+    if (best_mac) *best_mac = bm;
+    return EFIE_OK;
+  });
+}
+
 int efie_destroy(efie_handle* h) {
   if (!h) return EFIE_EINVAL;
   delete h;
+  return EFIE_OK;
+}
+
+}  // extern "C"
+
+// ----------------------------------------------------------------- batches
+struct efie_batch {
+  std::vector<efie_handle*> hs;
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> events;
+  cudaEvent_t fork = nullptr;
+  cudaStream_t cap = nullptr;   // capture stream (the caller's may be the legacy default stream)
+  cudaGraphExec_t exec = nullptr;
+  cudaGraph_t graph = nullptr;
+  std::vector<const void*> key_x;
+  std::vector<void*> key_y;
+  std::vector<int> key_n;
+  int64_t launches = 0;
+  std::string err;
+  ~efie_batch() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    for (auto st : streams) cudaStreamDestroy(st);
+    for (auto ev : events) cudaEventDestroy(ev);
+    if (fork) cudaEventDestroy(fork);
+    if (cap) cudaStreamDestroy(cap);
+  }
+};
+
+extern "C" {
+
+int efie_batch_create(efie_handle* const* hs, int n, efie_batch** out) {
+  if (!hs || n <= 0 || !out) return EFIE_EINVAL;
+  efie_batch* b = new (std::nothrow) efie_batch();
+  if (!b) return EFIE_ENOMEM;
+  for (int i = 0; i < n; ++i) {
+    if (!hs[i]) {
+      delete b;
+      return EFIE_EINVAL;
+    }
+    b->hs.push_back(hs[i]);
+    cudaStream_t st;
+    cudaEvent_t ev;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+      delete b;
+      return EFIE_ECUDA;
+    }
+    b->streams.push_back(st);
+    b->events.push_back(ev);
+  }
+  if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) {
+    delete b;
+    return EFIE_ECUDA;
+  }
+  *out = b;
+  return EFIE_OK;
+}
+
+// One CUDA-graph launch for the products of every member: member i computes
+// y[i] = T_i x[i] for n_rhs[i] vectors, on its own branch of the graph.
+int efie_batch_matvec(efie_batch* b, const void* const* x, void* const* y, const int* n_rhs, void* stream) {
+  if (!b || !x || !y || !n_rhs) return EFIE_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t n = b->hs.size();
+  std::vector<const void*> kx(x, x + n);
+  std::vector<void*> ky(y, y + n);
+  std::vector<int> kn(n_rhs, n_rhs + n);
+  try {
+    if (!b->exec || kx != b->key_x || ky != b->key_y || kn != b->key_n) {
+      // allocate every member's buffers outside the capture
+      for (size_t i = 0; i < n; ++i) {
+        efie_handle* h = b->hs[i];
+        if (kn[i] < 0 || (kn[i] > 0 && (!x[i] || !y[i]))) throw EfieError{EFIE_EINVAL, "bad batch arguments"};
+        if (kn[i] > 0)
+          do_matvec(h, (const double2*)x[i], h->plan.g.N, (double2*)y[i], nullptr, nullptr, h->plan.g.N, kn[i],
+                    false, s);
+      }
+      cuda_check(cudaStreamSynchronize(s), "batch warm-up");
+      if (b->exec) cudaGraphExecDestroy(b->exec);
+      if (b->graph) cudaGraphDestroy(b->graph);
+      b->exec = nullptr;
+      b->graph = nullptr;
+      std::vector<bool> prof(n);
+      for (size_t i = 0; i < n; ++i) {
+        prof[i] = b->hs[i]->prof.on;
+        b->hs[i]->prof.on = false;
+      }
+      cudaStream_t c = b->cap;
+      cuda_check(cudaStreamBeginCapture(c, cudaStreamCaptureModeThreadLocal), "capture");
+      cuda_check(cudaEventRecord(b->fork, c), "fork");
+      for (size_t i = 0; i < n; ++i) {
+        efie_handle* h = b->hs[i];
+        cuda_check(cudaStreamWaitEvent(b->streams[i], b->fork, 0), "fork wait");
+        if (kn[i] > 0)
+          do_matvec(h, (const double2*)x[i], h->plan.g.N, (double2*)y[i], nullptr, nullptr, h->plan.g.N, kn[i],
+                    false, b->streams[i]);
+        cuda_check(cudaEventRecord(b->events[i], b->streams[i]), "join");
+        cuda_check(cudaStreamWaitEvent(c, b->events[i], 0), "join wait");
+      }
+      cuda_check(cudaStreamEndCapture(c, &b->graph), "end capture");
+      for (size_t i = 0; i < n; ++i) b->hs[i]->prof.on = prof[i];
+      cuda_check(cudaGraphInstantiate(&b->exec, b->graph, 0), "instantiate");
+      b->key_x = kx;
+      b->key_y = ky;
+      b->key_n = kn;
+    }
+    cuda_check(cudaGraphLaunch(b->exec, s), "graph launch");
+    b->launches++;
+    return EFIE_OK;
+  } catch (const EfieError& e) {
+    cudaGraph_t g = nullptr;
+    cudaStreamCaptureStatus st;
+    if (cudaStreamIsCapturing(b->cap, &st) == cudaSuccess && st != cudaStreamCaptureStatusNone) {
+      cudaStreamEndCapture(b->cap, &g);
+      if (g) cudaGraphDestroy(g);
+    }
+    b->err = e.msg;
+    g_last_error = e.msg;
+    return e.code;
+  }
+}
+
+int efie_batch_destroy(efie_batch* b) {
+  if (!b) return EFIE_EINVAL;
+  delete b;
   return EFIE_OK;
 }
 

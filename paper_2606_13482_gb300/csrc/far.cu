@@ -545,7 +545,10 @@ void launch_mac(const cpx_t<R>* Qh, cpx_t<R>* Rh, const cpx_t<R>* Kh, int64_t B,
                 const int64_t* src_ptr, const int32_t* src, const int64_t* kidx_off, const int32_t* kidx,
                 cudaStream_t s) {
   if (B <= 0 || nf <= 0 || ntiles <= 0) return;
-  if (sizeof(R) == 4 && C == 32 && max_tile_targets > 8 && max_tile_targets <= 128) {
+  // a negative tile size asks for the register-tile kernel (autotuner choice)
+  const bool force_reg = max_tile_targets < 0;
+  if (force_reg) max_tile_targets = -max_tile_targets;
+  if (!force_reg && sizeof(R) == 4 && C == 32 && max_tile_targets > 8 && max_tile_targets <= 128) {
     for (int64_t f0 = 0; f0 < nf; f0 += 65535) {
       int64_t nfc = std::min<int64_t>(65535, nf - f0);
       dim3 grid((unsigned)ntiles, (unsigned)nfc);
