@@ -468,9 +468,24 @@ __global__ void k_mac_tiled(const cpx_t<R>* __restrict__ Qh, cpx_t<R>* __restric
 
 // Top grid level, 32 channels (8 right-hand sides), FP32: every block owns one
 // tile of <= 128 targets and one frequency; chunks of YS sources are staged in
-// shared memory (kernel values gathered cooperatively through the index tile,
-// spectra loaded coalesced), then each thread runs 8 targets x 4 channels out
-// of shared memory.
+// shared memory by cp.async (kernel values gathered through the index tile,
+// zero-filled for excluded pairs; spectra copied 16 bytes at a time), double
+// buffered so the next chunk's gathers run while the current chunk is
+// multiplied; each thread runs 8 targets x 4 channels out of shared memory.
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem, bool valid) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  const int sz = valid ? 8 : 0;
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(sa), "l"(gmem), "r"(sz));
+}
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool valid) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  const int sz = valid ? 16 : 0;
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(sz));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
 template <int YS>
 __global__ void __launch_bounds__(128) k_mac_top32(const float2* __restrict__ Qh, float2* __restrict__ Rh,
                                                    const float2* __restrict__ Kh, int64_t B, int64_t O,
@@ -480,8 +495,9 @@ __global__ void __launch_bounds__(128) k_mac_top32(const float2* __restrict__ Qh
                                                    const int32_t* __restrict__ src,
                                                    const int64_t* __restrict__ kidx_off,
                                                    const int32_t* __restrict__ kidx, int64_t f0) {
-  __shared__ __align__(16) float2 Ks[YS][128];
-  __shared__ __align__(16) float2 Qs[YS][32];
+  extern __shared__ __align__(16) unsigned char mac_smem[];
+  float2(*Ks)[YS][128] = reinterpret_cast<float2(*)[YS][128]>(mac_smem);
+  float2(*Qs)[YS][32] = reinterpret_cast<float2(*)[YS][32]>(mac_smem + 2 * sizeof(float2) * YS * 128);
   const int tile = blockIdx.x;
   const int64_t f = f0 + blockIdx.y;
   if (f >= nf) return;
@@ -492,36 +508,49 @@ __global__ void __launch_bounds__(128) k_mac_top32(const float2* __restrict__ Qh
   const float2* Qf = Qh + f * B * 32;
   const float2* Kf = Kh + f * O;
   const int tg = threadIdx.x >> 3, cg = threadIdx.x & 7;
+  const float2 zero = make_float2(0.f, 0.f);
+  auto stage = [&](int buf, int64_t j0) {
+    const int jn = (int)min((int64_t)YS, ns - j0);
+    for (int e = threadIdx.x; e < YS * 128; e += 128) {
+      const int j = e >> 7, a = e & 127;
+      int32_t id = -1;
+      if (j < jn && a < tpad) id = __ldg(kb + (j0 + j) * tpad + a);
+      cp_async8(&Ks[buf][j][a], id >= 0 ? (const void*)(Kf + id) : (const void*)Kf, id >= 0);
+    }
+    for (int e = threadIdx.x; e < YS * 16; e += 128) {
+      const int j = e >> 4, c2 = (e & 15) * 2;
+      const bool ok = j < jn;
+      const int32_t y = ok ? __ldg(src + s0 + j0 + j) : 0;
+      cp_async16(&Qs[buf][j][c2], Qf + (int64_t)y * 32 + c2, ok);
+    }
+    cp_async_commit();
+  };
   float2 acc[8][4];
 #pragma unroll
   for (int a = 0; a < 8; ++a)
 #pragma unroll
-    for (int c = 0; c < 4; ++c) acc[a][c] = make_float2(0.f, 0.f);
-  for (int64_t j0 = 0; j0 < ns; j0 += YS) {
-    const int jn = (int)min((int64_t)YS, ns - j0);
-    for (int e = threadIdx.x; e < YS * 128; e += 128) {
-      const int j = e >> 7, a = e & 127;
-      float2 v = make_float2(0.f, 0.f);
-      if (j < jn && a < tpad) {
-        const int32_t id = __ldg(kb + (j0 + j) * tpad + a);
-        if (id >= 0) v = __ldg(Kf + id);
-      }
-      Ks[j][a] = v;
-    }
-    for (int e = threadIdx.x; e < YS * 32; e += 128) {
-      const int j = e >> 5, c = e & 31;
-      Qs[j][c] = j < jn ? __ldg(Qf + (int64_t)__ldg(src + s0 + j0 + j) * 32 + c) : make_float2(0.f, 0.f);
+    for (int c = 0; c < 4; ++c) acc[a][c] = zero;
+  const int nchunks = (int)((ns + YS - 1) / YS);
+  if (nchunks > 0) stage(0, 0);
+  for (int ch = 0; ch < nchunks; ++ch) {
+    const int buf = ch & 1;
+    if (ch + 1 < nchunks) {
+      stage(buf ^ 1, (int64_t)(ch + 1) * YS);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
     }
     __syncthreads();
+    const int jn = (int)min((int64_t)YS, ns - (int64_t)ch * YS);
     if (tg * 8 < nt) {
       for (int j = 0; j < jn; ++j) {
-        const float4 qa = *reinterpret_cast<const float4*>(&Qs[j][cg * 4]);
-        const float4 qb = *reinterpret_cast<const float4*>(&Qs[j][cg * 4 + 2]);
+        const float4 qa = *reinterpret_cast<const float4*>(&Qs[buf][j][cg * 4]);
+        const float4 qb = *reinterpret_cast<const float4*>(&Qs[buf][j][cg * 4 + 2]);
         const float2 q[4] = {make_float2(qa.x, qa.y), make_float2(qa.z, qa.w), make_float2(qb.x, qb.y),
                              make_float2(qb.z, qb.w)};
 #pragma unroll
         for (int a = 0; a < 8; ++a) {
-          const float2 kv = Ks[j][tg * 8 + a];
+          const float2 kv = Ks[buf][j][tg * 8 + a];
 #pragma unroll
           for (int c = 0; c < 4; ++c) cfma(acc[a][c], kv, q[c]);
         }
@@ -539,6 +568,69 @@ __global__ void __launch_bounds__(128) k_mac_top32(const float2* __restrict__ Qh
   }
 }
 
+// Interaction-list levels, FP32: the kernel values of one frequency are at most
+// O (<= 316 on these levels) complex numbers; every block stages the rows of its
+// fpb frequencies in shared memory, so the per-pair kernel lookups hit shared
+// memory and only the spectra come from L1/L2.
+template <int XR, int CR>
+__global__ void __launch_bounds__(128) k_mac_il32(const float2* __restrict__ Qh, float2* __restrict__ Rh,
+                                                  const float2* __restrict__ Kh, int64_t B, int C, int64_t O,
+                                                  int64_t nf, const int64_t* __restrict__ tgt_ptr,
+                                                  const int32_t* __restrict__ tgt,
+                                                  const int64_t* __restrict__ src_ptr,
+                                                  const int32_t* __restrict__ src,
+                                                  const int64_t* __restrict__ kidx_off,
+                                                  const int32_t* __restrict__ kidx, int fpb, int64_t f0) {
+  extern __shared__ __align__(16) unsigned char mac_smem[];
+  float2* Kr = reinterpret_cast<float2*>(mac_smem);   // [fpb][O]
+  const int tile = blockIdx.x;
+  const int64_t fb = f0 + (int64_t)blockIdx.y * fpb;
+  for (int e = threadIdx.x; e < fpb * O; e += blockDim.x) {
+    const int fl = e / (int)O;
+    const int64_t f = fb + fl;
+    Kr[e] = f < nf ? __ldg(Kh + f * O + (e - fl * O)) : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  const int ncg = C / CR;
+  const int fl = threadIdx.x / ncg, cg = threadIdx.x - fl * ncg;
+  const int64_t f = fb + fl;
+  if (fl >= fpb || f >= nf) return;
+  const int64_t t0 = tgt_ptr[tile], nt = tgt_ptr[tile + 1] - t0;
+  const int64_t s0 = src_ptr[tile], ns = src_ptr[tile + 1] - s0;
+  const int32_t* kb = kidx + kidx_off[tile];
+  const float2* Qf = Qh + f * B * C + cg * CR;
+  const float2* Kf = Kr + fl * O;
+  float2 acc[XR][CR];
+#pragma unroll
+  for (int a = 0; a < XR; ++a)
+#pragma unroll
+    for (int c = 0; c < CR; ++c) acc[a][c] = make_float2(0.f, 0.f);
+  for (int64_t j = 0; j < ns; ++j) {
+    const int32_t y = __ldg(src + s0 + j);
+    const float4 qa = __ldg(reinterpret_cast<const float4*>(Qf + (int64_t)y * C));
+    const float4 qb = __ldg(reinterpret_cast<const float4*>(Qf + (int64_t)y * C + 2));
+    const float2 q[4] = {make_float2(qa.x, qa.y), make_float2(qa.z, qa.w), make_float2(qb.x, qb.y),
+                         make_float2(qb.z, qb.w)};
+    const int4 ia = __ldg(reinterpret_cast<const int4*>(kb + j * XR));
+    const int4 ib = __ldg(reinterpret_cast<const int4*>(kb + j * XR + 4));
+    const int ids[8] = {ia.x, ia.y, ia.z, ia.w, ib.x, ib.y, ib.z, ib.w};
+#pragma unroll
+    for (int a = 0; a < XR; ++a) {
+      if (ids[a] < 0) continue;
+      const float2 kv = Kf[ids[a]];
+#pragma unroll
+      for (int c = 0; c < CR; ++c) cfma(acc[a][c], kv, q[c]);
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < XR; ++a) {
+    if (a >= nt) break;
+    float2* out = Rh + f * B * C + (int64_t)tgt[t0 + a] * C + cg * CR;
+    *reinterpret_cast<float4*>(out) = make_float4(acc[a][0].x, acc[a][0].y, acc[a][1].x, acc[a][1].y);
+    *reinterpret_cast<float4*>(out + 2) = make_float4(acc[a][2].x, acc[a][2].y, acc[a][3].x, acc[a][3].y);
+  }
+}
+
 template <typename R>
 void launch_mac(const cpx_t<R>* Qh, cpx_t<R>* Rh, const cpx_t<R>* Kh, int64_t B, int C, int64_t O,
                 int64_t nf, int64_t ntiles, int max_tile_targets, const int64_t* tgt_ptr, const int32_t* tgt,
@@ -549,11 +641,39 @@ void launch_mac(const cpx_t<R>* Qh, cpx_t<R>* Rh, const cpx_t<R>* Kh, int64_t B,
   const bool force_reg = max_tile_targets < 0;
   if (force_reg) max_tile_targets = -max_tile_targets;
   if (!force_reg && sizeof(R) == 4 && C == 32 && max_tile_targets > 8 && max_tile_targets <= 128) {
+    constexpr int YS = 16;
+    const size_t smem = 2 * sizeof(float2) * YS * (128 + 32);
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_mac_top32<YS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      attr = true;
+    }
     for (int64_t f0 = 0; f0 < nf; f0 += 65535) {
       int64_t nfc = std::min<int64_t>(65535, nf - f0);
       dim3 grid((unsigned)ntiles, (unsigned)nfc);
-      k_mac_top32<32><<<grid, 128, 0, s>>>((const float2*)Qh, (float2*)Rh, (const float2*)Kh, B, O, nf, tgt_ptr,
-                                           tgt, src_ptr, src, kidx_off, kidx, f0);
+      k_mac_top32<YS><<<grid, 128, smem, s>>>((const float2*)Qh, (float2*)Rh, (const float2*)Kh, B, O, nf, tgt_ptr,
+                                              tgt, src_ptr, src, kidx_off, kidx, f0);
+    }
+    return;
+  }
+  if (!force_reg && sizeof(R) == 4 && (C % 4) == 0 && C >= 16 && max_tile_targets <= 8 && O <= 2048) {
+    // interaction-list tiles (<= 8 targets): kernel rows of fpb frequencies in shared memory
+    const int ncg = C / 4;
+    int fpb = 128 / ncg;
+    if (fpb < 1) fpb = 1;
+    while (fpb > 1 && (size_t)fpb * O * sizeof(float2) > 64 * 1024) fpb >>= 1;
+    const size_t smem = (size_t)fpb * O * sizeof(float2);
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_mac_il32<8, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+      attr = true;
+    }
+    const int64_t fchunk = (int64_t)65535 * fpb;
+    for (int64_t f0 = 0; f0 < nf; f0 += fchunk) {
+      int64_t nfc = std::min<int64_t>(fchunk, nf - f0);
+      dim3 grid((unsigned)ntiles, (unsigned)ceil_div(nfc, fpb));
+      k_mac_il32<8, 4><<<grid, fpb * ncg, smem, s>>>((const float2*)Qh, (float2*)Rh, (const float2*)Kh, B, C, O, nf,
+                                                     tgt_ptr, tgt, src_ptr, src, kidx_off, kidx, fpb, f0);
     }
     return;
   }
