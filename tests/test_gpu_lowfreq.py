@@ -1,0 +1,66 @@
+"""Precision and low-frequency stress (PEC sphere of radius 1 m, 20,280 RWG,
+ka = 1e-1 ... 1e-4): the mixed form (complex FP32 far field; FP64 assembly,
+projectors, charges; double-float near field) against the plain FP64 form,
+whose parity with the oracle is tested elsewhere.  Errors are reported per ka
+for the vector-potential part A x and the scalar part Sigma V Sigma^T x
+separately, on a seeded complex Gaussian vector, a loop-space vector and a
+plane-wave right-hand side; they are recorded, and bounded loosely."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import efie_inputs as E
+
+pytestmark = pytest.mark.gpu
+
+
+def test_mixed_vs_fp64_per_ka():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    import paper_2606_13482_gb300 as G
+    from oracle.geometry import build_rwg
+    V, T = E.icosphere(26, 1.0)
+    m = build_rwg(V, T)
+    # loop-space vector: x - Sigma (Sigma^T Sigma)^-1 Sigma^T x via a few CG steps on the
+    # graph Laplacian Sigma^T Sigma (sparse, host)
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+    S = sp.csr_matrix((np.r_[np.ones(m.N), -np.ones(m.N)],
+                       (np.r_[np.arange(m.N), np.arange(m.N)], np.r_[m.tri_pm[:, 0], m.tri_pm[:, 1]])),
+                      shape=(m.N, m.Nt))
+    xg = E.complex_gaussian(m.N, 1)
+    L = (S.T @ S).tocsc() + 1e-12 * sp.eye(m.Nt)
+    sol = spla.spsolve(L, S.T @ xg.real) + 1j * spla.spsolve(L, S.T @ xg.imag)
+    xloop = xg - S @ sol
+    results = {}
+    for ka in (1e-1, 1e-2, 1e-3, 1e-4):
+        k = ka / 1.0
+        h64 = G.EFIE(V, T, k, 3, 0.064, 2, precision=G.EFIE_FP64)
+        h32 = G.EFIE(V, T, k, 3, 0.064, 2, precision=G.EFIE_MIXED)
+        b = h64.rhs_planewave([0, 0, -1.0], [1.0, 0, 0]).cpu().numpy()[0]
+        row = {}
+        for name, x in (("gaussian", xg), ("loop", xloop), ("planewave_rhs", b)):
+            xt = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+            a64, v64 = [t.cpu().numpy() for t in h64.matvec_parts(xt)]
+            a32, v32 = [t.cpu().numpy() for t in h32.matvec_parts(xt)]
+            y64 = h64.matvec(xt).cpu().numpy()
+            y32 = h32.matvec(xt).cpu().numpy()
+            row[name] = {
+                "A": float(np.linalg.norm(a32 - a64) / np.linalg.norm(a64)),
+                "V": float(np.linalg.norm(v32 - v64) / max(np.linalg.norm(v64), 1e-300)),
+                "T": float(np.linalg.norm(y32 - y64) / np.linalg.norm(y64)),
+            }
+            assert row[name]["A"] < 1e-4 and row[name]["T"] < 1e-4, (ka, name, row[name])
+        results[f"{ka:g}"] = row
+        h64.close()
+        h32.close()
+    out = os.environ.get("EFIE_LOWFREQ_JSON")
+    if out:
+        with open(out, "w") as f:
+            json.dump(results, f, indent=1)
+    print(json.dumps(results))
