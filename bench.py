@@ -124,6 +124,35 @@ def algorithmic(w, info, levels, nrhs):
             "near_V": ("flops", near_V_flops), "near_A_bytes": near_A_bytes, "near_V_bytes": near_V_bytes}
 
 
+def grid_bytes(info, levels, nrhs, vb):
+    """Algorithmic HBM bytes per batched matvec of the grid kernels: every
+    setup product read once per right-hand-side chunk of <= 8, every grid and
+    spectrum written once and read once.  vb = bytes per complex far-field
+    value (8 for complex FP32), moments are real with vb/2 bytes.
+      anterpolation: moments + leaf grids written + currents and charges read
+      interpolation: moments + leaf grids read + FP64 outputs written
+      forward_fft / inverse_fft: grids and spectra of every level, once each
+      upward: child grids read, parent grids written
+      downward: parent grids read, child grids read and written (accumulated)"""
+    ch = 4 * nrhs
+    chunks = -(-nrhs // 8)
+    by = {L["level"]: L for L in levels}
+    top, leaf = min(by), max(by)
+    grid = lambda L: L["n_boxes"] * L["sp"] ** 3 * ch * vb
+    spec = lambda L: L["n_boxes"] * L["nfft"] ** 3 * ch * vb
+    mom = chunks * (3 * info["moment_entries_rwg"] + info["moment_entries_tri"]) * (vb // 2)
+    nb = info["n_unknowns"] + info["n_triangles"]
+    out = {
+        "anterpolation": mom + grid(by[leaf]) + nb * nrhs * vb,
+        "interpolation": mom + grid(by[leaf]) + nb * nrhs * 16,
+        "forward_fft": sum(grid(L) + spec(L) for L in levels),
+        "inverse_fft": sum(grid(L) + spec(L) for L in levels),
+        "upward": sum(grid(by[l]) + grid(by[l - 1]) for l in by if l > top),
+        "downward": sum(grid(by[l - 1]) + 2 * grid(by[l]) for l in by if l > top),
+    }
+    return out
+
+
 def run_ours(args, w, rank, world, local_rank):
     import torch
     import __graft_entry__ as g
@@ -140,6 +169,8 @@ def run_ours(args, w, rank, world, local_rank):
     h = G.EFIE(V, T, w["k"], w["p"], w["delta"], w["levels"], precision=prec)
     t_setup = time.time() - t0
     info, levels = G.plan(V, T, w["k"], w["p"], w["delta"], w["levels"])
+    hi = h.info()
+    info["moment_entries_rwg"], info["moment_entries_tri"] = hi["moment_entries_rwg"], hi["moment_entries_tri"]
     N = h.N
     R = args.nrhs or w["nrhs"]
     gen = torch.Generator().manual_seed(1234 + rank)
@@ -219,6 +250,20 @@ def run_ours(args, w, rank, world, local_rank):
         roof["hbm_achieved_gbs"] = nb
         roof["hbm_frac"] = nb / peaks["hbm_gbs"]
         roof["hbm_peak_source"] = psrc
+    vb = 8 if w["precision"] == "mixed" else 16
+    gb = grid_bytes(info, levels, R, vb)
+    kernel_rooflines = {}
+    for name, b in gb.items():
+        if name in prof and prof[name][0] > 0:
+            gbs = b * args.steps / (prof[name][0] / 1000.0) / 1e9
+            kernel_rooflines[name] = {"bound": "hbm", "bytes_per_step": b, "achieved": gbs, "unit": "GB/s",
+                                      "peak": peaks["hbm_gbs"], "frac": gbs / peaks["hbm_gbs"]}
+    for name in ("near_A", "near_V", "translation_mac", "translation_mac_top"):
+        if name in prof and prof[name][0] > 0:
+            fl = alg[name][1] * args.steps / (prof[name][0] / 1000.0) / 1e12
+            pk = FP32_TFLOPS if w["precision"] == "mixed" else FP64_TFLOPS
+            kernel_rooflines[name] = {"bound": "alu", "flops_per_step": alg[name][1], "achieved": fl,
+                                      "unit": "TFLOP/s", "peak": pk, "frac": fl / pk}
     line = {
         "metric": METRIC, "value": value, "unit": "matvecs/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_s * 1000.0 / args.steps, "higher_is_better": True,
@@ -235,6 +280,7 @@ def run_ours(args, w, rank, world, local_rank):
         "clocks": clocks.summary(local_rank),
         "e2e": e2e, "gpu_launches": int(n_launch), "roofline": roof,
         "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+        "kernel_rooflines": kernel_rooflines,
     }
     if rank == 0 and not args.no_solve:
         line["time_to_solve"] = time_to_solve(G, torch)

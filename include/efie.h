@@ -91,6 +91,8 @@ typedef struct {
     double root_lo[3], root_edge;
     int64_t near_nnz_A, near_nnz_V;
     int64_t device_bytes;    /* estimated resident device bytes of the setup products */
+    int64_t moment_entries_rwg;  /* leaf moment entries of all RWGs, per vector component */
+    int64_t moment_entries_tri;  /* leaf moment entries of all triangles (charge part) */
 } efie_plan_info_t;
 
 typedef struct {

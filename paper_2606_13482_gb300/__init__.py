@@ -68,7 +68,8 @@ class PlanInfo(ctypes.Structure):
                 ("n_levels", ctypes.c_int32), ("p", ctypes.c_int32),
                 ("root_lo", ctypes.c_double * 3), ("root_edge", ctypes.c_double),
                 ("near_nnz_A", ctypes.c_int64), ("near_nnz_V", ctypes.c_int64),
-                ("device_bytes", ctypes.c_int64)]
+                ("device_bytes", ctypes.c_int64), ("moment_entries_rwg", ctypes.c_int64),
+                ("moment_entries_tri", ctypes.c_int64)]
 
 
 class SolveInfo(ctypes.Structure):

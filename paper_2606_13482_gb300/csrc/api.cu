@@ -86,7 +86,8 @@ struct DevMem {
 template <typename R>
 struct FarSet {
   bool built = false;
-  R *mr = nullptr, *mt = nullptr;
+  R *mr = nullptr, *mt = nullptr;  // moments by basis function (interpolation)
+  R *gr = nullptr, *gt = nullptr;  // the same moments by grid point (anterpolation)
   struct Lev {
     cpx_t<R>* Mf = nullptr;
     cpx_t<R>* Mb = nullptr;
@@ -177,6 +178,7 @@ struct efie_handle {
   // moments structure (shared by precisions)
   int32_t *mr_base = nullptr, *mr_ext = nullptr, *mt_base = nullptr, *mt_ext = nullptr;
   int64_t *mr_off = nullptr, *mt_off = nullptr;
+  int32_t *gptr_r = nullptr, *gptr_t = nullptr;  // gather-list offsets per leaf box and grid point
   // near
   NearDev nd{};
   int64_t *d_near_ptr = nullptr, *d_blkA_off = nullptr, *d_blkV_off = nullptr;
@@ -264,6 +266,19 @@ void build_far(efie_handle* h, FarSet<R>& F, cudaStream_t s) {
   std::vector<R> mt(P.mom_tri.data.begin(), P.mom_tri.data.end());
   F.mr = M.upload(mr);
   F.mt = M.upload(mt);
+  {
+    const Level& L = P.L(P.D);
+    const int64_t B = (int64_t)L.code.size(), npts = (int64_t)L.sp * L.sp * L.sp;
+    if (!h->gptr_r) {
+      h->gptr_r = M.alloc<int32_t>(B * (npts + 1));
+      h->gptr_t = M.alloc<int32_t>(B * (npts + 1));
+    }
+    F.gr = M.alloc<R>((int64_t)mr.size() / 3 * 4);
+    F.gt = M.alloc<R>((int64_t)mt.size() * 2);
+    launch_gather_build<R>(F.mr, h->mr_base, h->mr_ext, h->mr_off, F.mt, h->mt_base, h->mt_ext, h->mt_off,
+                           h->d_box_rwg_ptr, h->d_box_tri_ptr, B, L.sp, h->gptr_r, h->gptr_t, F.gr, F.gt, s);
+    cuda_check(cudaGetLastError(), "gather lists");
+  }
   F.lv.assign(P.lv.size(), {});
   for (int ell = P.D; ell >= P.top; --ell) {
     Level& L = P.L(ell);
@@ -419,9 +434,8 @@ void far_chunk(efie_handle* h, FarSet<R>& F, int nr, cudaStream_t s) {
       xin = (const cpx_t<R>*)h->xsf;
       rin = (const cpx_t<R>*)h->rhof;
     }
-    launch_anterp<R>(F.mr, h->mr_base, h->mr_ext, h->mr_off, F.mt, h->mt_base, h->mt_ext, h->mt_off,
-                     h->d_box_rwg_ptr, h->d_box_tri_ptr, (int64_t)L.code.size(), xin, N, rin, Nt, nr,
-                     F.q[D - top], L.sp, s);
+    launch_anterp<R>(F.gr, F.gt, h->gptr_r, h->gptr_t, h->mr_off, h->mt_off, h->d_box_rwg_ptr,
+                     h->d_box_tri_ptr, (int64_t)L.code.size(), xin, N, rin, Nt, nr, F.q[D - top], L.sp, s);
   }
   // a3: upward transfers
   for (int ell = D; ell > top; --ell) {
@@ -814,6 +828,7 @@ int solve_impl(efie_handle* h, const double2* b, double2* x, int n_rhs, double t
     }
   }
   std::vector<std::vector<std::complex<double>>> H(n_rhs), cs(n_rhs), sn(n_rhs), gg(n_rhs);
+  std::vector<int> floor_hits(n_rhs, 0);
   while (true) {
     bool any = false;
     for (int r = 0; r < n_rhs; ++r) {
@@ -834,7 +849,7 @@ int solve_impl(efie_handle* h, const double2* b, double2* x, int n_rhs, double t
     for (int r = 0; r < n_rhs; ++r) cuda_check(cudaMemsetAsync(Vb + r * ldr, 0, sizeof(double2) * N, s), "v0");
     cuda_check(cudaMemcpyAsync(dh, hh.data(), sizeof(double2) * n_rhs, cudaMemcpyHostToDevice, s), "h");
     launch_multiaxpy(rv, N, 0, 1, dh, 1, Vb, ldr, N, n_rhs, dact, 1.0, s);
-    std::vector<int> kdim(n_rhs, 0), inner(n_rhs, 0);
+    std::vector<int> kdim(n_rhs, 0), inner(n_rhs, 0), est_conv(n_rhs, 0);
     for (int r = 0; r < n_rhs; ++r) inner[r] = act[r];
     for (int k = 0; k < m; ++k) {
       bool anyin = false;
@@ -897,7 +912,8 @@ int solve_impl(efie_handle* h, const double2* b, double2* x, int n_rhs, double t
         gg[r][k] = std::conj(cs[r][k]) * gg[r][k];
         its[r]++;
         kdim[r] = k + 1;
-        if (std::abs(gg[r][k + 1]) / bnorm[r] <= tol_in || its[r] >= max_it || nrm[r] == 0) inner[r] = 0;
+        if (std::abs(gg[r][k + 1]) / bnorm[r] <= tol_in) est_conv[r] = 1;
+        if (est_conv[r] || its[r] >= max_it || nrm[r] == 0) inner[r] = 0;
       }
       // v_{k+1} = w / ||w||
       std::vector<std::complex<double>> scv(sc);
@@ -938,6 +954,18 @@ int solve_impl(efie_handle* h, const double2* b, double2* x, int n_rhs, double t
     if (use_pc)
       for (int r = 0; r < n_rhs; ++r)
         if (act[r] && !pc_fallback[r] && beta[r] > 0.99 * beta_prev[r]) pc_fallback[r] = 1;
+    // accuracy floor of the working precision: the cycle met the tolerance in
+    // its own arithmetic but the recomputed residual did not, twice in a row;
+    // further cycles cannot lower it, so stop and let the FP64 true residual
+    // below decide convergence
+    for (int r = 0; r < n_rhs; ++r) {
+      if (!act[r]) continue;
+      if (est_conv[r] && beta[r] / bnorm[r] > tol_in) {
+        if (++floor_hits[r] >= 2) act[r] = 0;
+      } else {
+        floor_hits[r] = 0;
+      }
+    }
   }
   // true residual with the FP64 fast matvec
   do_matvec(h, x, N, wv, nullptr, nullptr, N, n_rhs, true, s);
@@ -995,6 +1023,8 @@ void fill_plan_info(const Plan& P, efie_plan_info_t* info, efie_level_info_t* lv
       bytes += n3 * (int64_t)(L.offsets.size() / 3) * 16;
     }
     info->device_bytes = bytes;
+    info->moment_entries_rwg = P.mom_rwg.off.empty() ? 0 : P.mom_rwg.off.back() / 3;
+    info->moment_entries_tri = P.mom_tri.off.empty() ? 0 : P.mom_tri.off.back();
   }
   if (lv) {
     int i = 0;

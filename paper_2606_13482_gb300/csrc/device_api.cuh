@@ -10,7 +10,8 @@ namespace efie {
 
 // Near field (always FP64).  Block j of the CSR near lists couples target box
 // blk_tgt[j] with source box near_src[j]; A blocks are [n_rwg(x)][n_rwg(y)],
-// V blocks [n_tri(x)][n_tri(y)], row-major, in sorted basis order.
+// V blocks [n_tri(x)][n_tri(y)], column-major ([col][row]), in sorted basis
+// order.
 struct NearDev {
   const double* V;          // [nv][3]
   const int32_t* T;         // [nt][3]
@@ -62,11 +63,16 @@ void launch_mode(const cpx_t<R>* in, View vin, cpx_t<R>* out, View vout, int64_t
                  const int8_t* sel, const int64_t* srcmap, bool accumulate, cudaStream_t s);
 
 template <typename R>
-void launch_anterp(const R* mr, const int32_t* mr_base, const int32_t* mr_ext, const int64_t* mr_off,
-                   const R* mt, const int32_t* mt_base, const int32_t* mt_ext, const int64_t* mt_off,
-                   const int64_t* box_rwg_ptr, const int64_t* box_tri_ptr, int64_t B,
-                   const cpx_t<R>* xs, int64_t ldx, const cpx_t<R>* rho, int64_t ldr, int nr,
-                   cpx_t<R>* q, int sp, cudaStream_t s);
+void launch_gather_build(const R* mr, const int32_t* mr_base, const int32_t* mr_ext, const int64_t* mr_off,
+                         const R* mt, const int32_t* mt_base, const int32_t* mt_ext, const int64_t* mt_off,
+                         const int64_t* box_rwg_ptr, const int64_t* box_tri_ptr, int64_t B, int sp,
+                         int32_t* gptr_r, int32_t* gptr_t, R* gr, R* gt, cudaStream_t s);
+
+template <typename R>
+void launch_anterp(const R* gr, const R* gt, const int32_t* gptr_r, const int32_t* gptr_t, const int64_t* mr_off,
+                   const int64_t* mt_off, const int64_t* box_rwg_ptr, const int64_t* box_tri_ptr, int64_t B,
+                   const cpx_t<R>* xs, int64_t ldx, const cpx_t<R>* rho, int64_t ldr, int nr, cpx_t<R>* q,
+                   int sp, cudaStream_t s);
 
 template <typename R>
 void launch_interp(const R* mr, const int32_t* mr_base, const int32_t* mr_ext, const int64_t* mr_off,

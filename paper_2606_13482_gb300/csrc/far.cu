@@ -2,8 +2,8 @@
 //
 //  a2  k_anterp : leaf anterpolation q_{d,b} = sum_{n in b} j_n m_{d,n} and the
 //                 charge component q_{4,b} = sum_{c in b} rho_c m^phi_c
-//                 (Eq. TAfactor, Sec. VI-A); one CTA per leaf box, the box grid
-//                 accumulated in shared memory and written once, coalesced.
+//                 (Eq. TAfactor, Sec. VI-A); one CTA per leaf box, one thread
+//                 per grid point gathering over the moments that cover it.
 //  a3/a8 k_mode : tensor mode products with the knot-insertion transfers
 //                 C^L / C^R and their transposes (Eq. interleveltransfer).
 //  a4-a7 k_mode : stabilize + zero-pad + DFT fused into one n x s' complex
@@ -12,7 +12,8 @@
 //  a6  k_mac    : frequency-domain translation R_x = sum_{y in IL(x)} K_{x-y} Q_y
 //                 (Eq. TAfactorBspline, Toeplitz structure), spectra stored
 //                 frequency-major so one frequency of all boxes is contiguous.
-//  a9  k_interp : interpolation (transpose of a2), one warp per basis function.
+//  a9  k_interp : interpolation (transpose of a2), one warp per basis function,
+//                 lanes over channels.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -220,166 +221,328 @@ void launch_mode(const cpx_t<R>* in, View vin, cpx_t<R>* out, View vout, int64_t
                                                       M1, sel, srcmap, accumulate);
 }
 
-// ---------------------------------------------------------------- anterpolation
-// CTA (box b, rhs tile): shared grid [sp^3][4 * rt] complex.
+// ---------------------------------------------------------------- leaf grids
+// Channel order inside a grid point: c = d * nr + r (component d = 0..2 the
+// vector part, 3 the charge part; r the right-hand side), so the vector part
+// of one point is 3 nr contiguous values and the charge part nr more.
+
+// Gather lists (setup): the moments re-indexed by grid point.  For leaf box b
+// and point pt of its sp^3 grid, entries [ptr[pt], ptr[pt+1]) (offsets within
+// the box) hold (k, m_0, m_1, m_2) for every RWG k of the box (local index)
+// whose moment block covers pt, in increasing k; triangles likewise hold
+// (t, m^phi).  A box's entries start where its RWGs' moment data starts
+// (mr_off / 3, mt_off), since both orderings hold the same entries.  One CTA
+// per box, one thread per point; the covering test reads each basis
+// function's base and extents, so the lists are deterministic.
 template <typename R>
-__global__ void k_anterp(const R* __restrict__ mr, const int32_t* __restrict__ mr_base,
-                         const int32_t* __restrict__ mr_ext, const int64_t* __restrict__ mr_off,
-                         const R* __restrict__ mt, const int32_t* __restrict__ mt_base,
-                         const int32_t* __restrict__ mt_ext, const int64_t* __restrict__ mt_off,
-                         const int64_t* __restrict__ box_rwg_ptr, const int64_t* __restrict__ box_tri_ptr,
-                         const cpx_t<R>* __restrict__ xs, int64_t ldx, const cpx_t<R>* __restrict__ rho,
-                         int64_t ldr, int nr, int rt, cpx_t<R>* __restrict__ q, int sp) {
-  extern __shared__ unsigned char smem_raw[];
-  R* g = (R*)smem_raw;  // [sp^3][4*rt complex], point stride PS = 8 rt + 1 (odd: no bank conflicts)
-  const int b = blockIdx.x;
-  const int r0 = blockIdx.y * rt;
-  const int nrt = min(rt, nr - r0);
-  const int CT = 4 * rt;
-  const int PS = 2 * CT + 1;
-  const int npts = sp * sp * sp;
-  for (int i = threadIdx.x; i < npts * PS; i += blockDim.x) g[i] = (R)0;
+__global__ void k_gather_build(const R* __restrict__ mr, const int32_t* __restrict__ mr_base,
+                               const int32_t* __restrict__ mr_ext, const int64_t* __restrict__ mr_off,
+                               const R* __restrict__ mt, const int32_t* __restrict__ mt_base,
+                               const int32_t* __restrict__ mt_ext, const int64_t* __restrict__ mt_off,
+                               const int64_t* __restrict__ box_rwg_ptr, const int64_t* __restrict__ box_tri_ptr,
+                               int sp, int32_t* __restrict__ gptr_r, int32_t* __restrict__ gptr_t,
+                               R* __restrict__ gr, R* __restrict__ gt) {
+  extern __shared__ int32_t gcnt[];  // [2][npts]
+  const int b = blockIdx.x, npts = sp * sp * sp;
+  const int64_t k0 = box_rwg_ptr[b], k1 = box_rwg_ptr[b + 1];
+  const int64_t t0 = box_tri_ptr[b], t1 = box_tri_ptr[b + 1];
+  auto covers = [&](const int32_t* base, const int32_t* ext, int64_t i, int p0, int p1, int p2, int& e) {
+    const int a0 = p0 - base[3 * i], a1 = p1 - base[3 * i + 1], a2 = p2 - base[3 * i + 2];
+    const int e0 = ext[3 * i], e1 = ext[3 * i + 1], e2 = ext[3 * i + 2];
+    if ((unsigned)a0 >= (unsigned)e0 || (unsigned)a1 >= (unsigned)e1 || (unsigned)a2 >= (unsigned)e2) return false;
+    e = (a0 * e1 + a1) * e2 + a2;
+    return true;
+  };
+  for (int pt = threadIdx.x; pt < npts; pt += blockDim.x) {
+    const int p0 = pt / (sp * sp), p1 = (pt / sp) % sp, p2 = pt % sp;
+    int cr = 0, ct = 0, e;
+    for (int64_t i = k0; i < k1; ++i) cr += covers(mr_base, mr_ext, i, p0, p1, p2, e);
+    for (int64_t i = t0; i < t1; ++i) ct += covers(mt_base, mt_ext, i, p0, p1, p2, e);
+    gcnt[pt] = cr;
+    gcnt[npts + pt] = ct;
+  }
   __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  // RWGs: components 0..2
-  for (int64_t i = box_rwg_ptr[b] + warp; i < box_rwg_ptr[b + 1]; i += nw) {
-    const int e0 = mr_ext[3 * i], e1 = mr_ext[3 * i + 1], e2 = mr_ext[3 * i + 2];
-    const int b0 = mr_base[3 * i], b1 = mr_base[3 * i + 1], b2 = mr_base[3 * i + 2];
-    const int ne = e0 * e1 * e2;
-    const R* m = mr + mr_off[i];
-    for (int e = lane; e < ne; e += 32) {
-      int a0 = e / (e1 * e2), rem = e - a0 * e1 * e2, a1 = rem / e2, a2 = rem - a1 * e2;
-      int pt = ((b0 + a0) * sp + (b1 + a1)) * sp + (b2 + a2);
-      R mv[3] = {m[e], m[ne + e], m[2 * ne + e]};
-      for (int r = 0; r < nrt; ++r) {
-        const cpx_t<R> xv = xs[(int64_t)(r0 + r) * ldx + i];
-        for (int d = 0; d < 3; ++d) {
-          R* dst = g + (int64_t)pt * PS + (4 * r + d) * 2;
-          atomicAdd(dst, mv[d] * xv.x);
-          atomicAdd(dst + 1, mv[d] * xv.y);
+  if (threadIdx.x == 0) {
+    int32_t* pr = gptr_r + (int64_t)b * (npts + 1);
+    int32_t* pt_ = gptr_t + (int64_t)b * (npts + 1);
+    int32_t rr = 0, rt = 0;
+    for (int pt = 0; pt < npts; ++pt) {
+      const int32_t vr = gcnt[pt], vt = gcnt[npts + pt];
+      gcnt[pt] = rr;
+      gcnt[npts + pt] = rt;
+      pr[pt] = rr;
+      pt_[pt] = rt;
+      rr += vr;
+      rt += vt;
+    }
+    pr[npts] = rr;
+    pt_[npts] = rt;
+  }
+  __syncthreads();
+  R* outr = gr + 4 * (k0 < k1 ? mr_off[k0] / 3 : 0);
+  R* outt = gt + 2 * (t0 < t1 ? mt_off[t0] : 0);
+  for (int pt = threadIdx.x; pt < npts; pt += blockDim.x) {
+    const int p0 = pt / (sp * sp), p1 = (pt / sp) % sp, p2 = pt % sp;
+    int64_t pos = gcnt[pt];
+    int e;
+    for (int64_t i = k0; i < k1; ++i)
+      if (covers(mr_base, mr_ext, i, p0, p1, p2, e)) {
+        const int ne = mr_ext[3 * i] * mr_ext[3 * i + 1] * mr_ext[3 * i + 2];
+        const R* m = mr + mr_off[i];
+        R* o = outr + 4 * pos++;
+        o[0] = (R)(i - k0);
+        o[1] = m[e];
+        o[2] = m[ne + e];
+        o[3] = m[2 * ne + e];
+      }
+    pos = gcnt[npts + pt];
+    for (int64_t i = t0; i < t1; ++i)
+      if (covers(mt_base, mt_ext, i, p0, p1, p2, e)) {
+        R* o = outt + 2 * pos++;
+        o[0] = (R)(i - t0);
+        o[1] = mt[mt_off[i] + e];
+      }
+  }
+}
+
+// ---------------------------------------------------------------- anterpolation
+// q[b][pt][d nr + r] = sum over the gather list of pt: m_d x_r[k] (d < 3) and
+// sum of m^phi rho_r[t] (d = 3).  One CTA per leaf box; the box's currents and
+// charges are staged in shared memory (AK basis functions at a time; boxes
+// with more take several passes over their sorted lists), then each thread
+// owns one grid point and RPU right-hand sides and keeps all 4 components in
+// registers: no atomics, each moment entry read once per launch, each output
+// value written once.
+template <typename R>
+struct AnterpCfg;
+template <>
+struct AnterpCfg<float> {
+  static constexpr int AK = 256, XS = 10, RPU = 8;  // 80-byte rows: conflict-light broadcasts
+};
+template <>
+struct AnterpCfg<double> {
+  static constexpr int AK = 128, XS = 9, RPU = 4;
+};
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_anterp(const R* __restrict__ gr, const R* __restrict__ gt,
+                                                const int32_t* __restrict__ gptr_r,
+                                                const int32_t* __restrict__ gptr_t,
+                                                const int64_t* __restrict__ mr_off,
+                                                const int64_t* __restrict__ mt_off,
+                                                const int64_t* __restrict__ box_rwg_ptr,
+                                                const int64_t* __restrict__ box_tri_ptr,
+                                                const cpx_t<R>* __restrict__ xs, int64_t ldx,
+                                                const cpx_t<R>* __restrict__ rho, int64_t ldr, int nr,
+                                                cpx_t<R>* __restrict__ q, int sp) {
+  using T = cpx_t<R>;
+  constexpr int AK = AnterpCfg<R>::AK, XS = AnterpCfg<R>::XS, RPU = AnterpCfg<R>::RPU;
+  __shared__ __align__(16) T xsm[AK][XS];
+  __shared__ __align__(16) T rsm[AK][XS];
+  const int b = blockIdx.x, tid = threadIdx.x;
+  const int npts = sp * sp * sp;
+  const int64_t k0 = box_rwg_ptr[b], t0 = box_tri_ptr[b];
+  const int nk = (int)(box_rwg_ptr[b + 1] - k0), nt = (int)(box_tri_ptr[b + 1] - t0);
+  const R* ger = gr + 4 * (nk > 0 ? mr_off[k0] / 3 : 0);
+  const R* get = gt + 2 * (nt > 0 ? mt_off[t0] : 0);
+  const int32_t* pr = gptr_r + (int64_t)b * (npts + 1);
+  const int32_t* pq = gptr_t + (int64_t)b * (npts + 1);
+  const int ngrp = (nr + RPU - 1) / RPU, nunits = npts * ngrp;
+  const int nchunk = max((nk + AK - 1) / AK, (nt + AK - 1) / AK);
+  auto stage = [&](int c) {
+    for (int i = tid; i < AK * nr; i += blockDim.x) {
+      const int r = i / AK, kk = i - r * AK, k = c * AK + kk;
+      if (k < nk) xsm[kk][r] = xs[r * ldx + k0 + k];
+      if (k < nt) rsm[kk][r] = rho[r * ldr + t0 + k];
+    }
+  };
+  if (nchunk == 1) {
+    stage(0);
+    __syncthreads();
+  }
+  const int C = 4 * nr;
+  for (int ub = 0; ub < nunits; ub += blockDim.x) {
+    const int u = ub + tid;
+    const bool ok = u < nunits;
+    const int g = ok ? u / npts : 0, p = ok ? u - g * npts : 0;
+    const int rb = g * RPU;
+    T acc[RPU][4];
+#pragma unroll
+    for (int r = 0; r < RPU; ++r)
+#pragma unroll
+      for (int d = 0; d < 4; ++d) acc[r][d] = mk<R>(0, 0);
+    int er = ok ? pr[p] : 0, er1 = ok ? pr[p + 1] : 0;
+    int et = ok ? pq[p] : 0, et1 = ok ? pq[p + 1] : 0;
+    for (int c = 0; c < nchunk; ++c) {
+      if (nchunk > 1) {
+        __syncthreads();
+        stage(c);
+        __syncthreads();
+      }
+      const R kc0 = (R)(c * AK), kc1 = (R)((c + 1) * AK);
+      for (; er < er1; ++er) {
+        const R* e = ger + 4 * (int64_t)er;
+        R ek, m0, m1, m2;
+        if constexpr (sizeof(R) == 4) {
+          const float4 v = *reinterpret_cast<const float4*>(e);
+          ek = v.x, m0 = v.y, m1 = v.z, m2 = v.w;
+        } else {
+          const double2 v0 = *reinterpret_cast<const double2*>(e), v1 = *reinterpret_cast<const double2*>(e + 2);
+          ek = v0.x, m0 = v0.y, m1 = v1.x, m2 = v1.y;
+        }
+        if (ek >= kc1) break;
+        const T* xr = xsm[(int)(ek - kc0)] + rb;
+#pragma unroll
+        for (int r = 0; r < RPU; ++r) {
+          if (rb + r >= nr) break;
+          const T xv = xr[r];
+          acc[r][0].x = fma(m0, xv.x, acc[r][0].x);
+          acc[r][0].y = fma(m0, xv.y, acc[r][0].y);
+          acc[r][1].x = fma(m1, xv.x, acc[r][1].x);
+          acc[r][1].y = fma(m1, xv.y, acc[r][1].y);
+          acc[r][2].x = fma(m2, xv.x, acc[r][2].x);
+          acc[r][2].y = fma(m2, xv.y, acc[r][2].y);
+        }
+      }
+      for (; et < et1; ++et) {
+        const R* e = get + 2 * (int64_t)et;
+        R ek, m;
+        if constexpr (sizeof(R) == 4) {
+          const float2 v = *reinterpret_cast<const float2*>(e);
+          ek = v.x, m = v.y;
+        } else {
+          const double2 v = *reinterpret_cast<const double2*>(e);
+          ek = v.x, m = v.y;
+        }
+        if (ek >= kc1) break;
+        const T* rr = rsm[(int)(ek - kc0)] + rb;
+#pragma unroll
+        for (int r = 0; r < RPU; ++r) {
+          if (rb + r >= nr) break;
+          const T v = rr[r];
+          acc[r][3].x = fma(m, v.x, acc[r][3].x);
+          acc[r][3].y = fma(m, v.y, acc[r][3].y);
         }
       }
     }
-  }
-  // triangles: component 3 with the charges rho
-  for (int64_t i = box_tri_ptr[b] + warp; i < box_tri_ptr[b + 1]; i += nw) {
-    const int e0 = mt_ext[3 * i], e1 = mt_ext[3 * i + 1], e2 = mt_ext[3 * i + 2];
-    const int b0 = mt_base[3 * i], b1 = mt_base[3 * i + 1], b2 = mt_base[3 * i + 2];
-    const int ne = e0 * e1 * e2;
-    const R* m = mt + mt_off[i];
-    for (int e = lane; e < ne; e += 32) {
-      int a0 = e / (e1 * e2), rem = e - a0 * e1 * e2, a1 = rem / e2, a2 = rem - a1 * e2;
-      int pt = ((b0 + a0) * sp + (b1 + a1)) * sp + (b2 + a2);
-      R mv = m[e];
-      for (int r = 0; r < nrt; ++r) {
-        const cpx_t<R> rv = rho[(int64_t)(r0 + r) * ldr + i];
-        R* dst = g + (int64_t)pt * PS + (4 * r + 3) * 2;
-        atomicAdd(dst, mv * rv.x);
-        atomicAdd(dst + 1, mv * rv.y);
-      }
+    if (ok) {
+      T* qp = q + ((int64_t)b * npts + p) * C + rb;
+#pragma unroll
+      for (int d = 0; d < 4; ++d)
+#pragma unroll
+        for (int r = 0; r < RPU; ++r)
+          if (rb + r < nr) qp[d * nr + r] = acc[r][d];
     }
-  }
-  __syncthreads();
-  // write out: q[b][pt][4*r0 .. 4*(r0+nrt))
-  const int C = 4 * nr;
-  cpx_t<R>* qb = q + (int64_t)b * npts * C;
-  for (int idx = threadIdx.x; idx < npts * 4 * nrt; idx += blockDim.x) {
-    int pt = idx / (4 * nrt), cc = idx - pt * 4 * nrt;
-    qb[(int64_t)pt * C + 4 * r0 + cc] = mk<R>(g[(int64_t)pt * PS + cc * 2], g[(int64_t)pt * PS + cc * 2 + 1]);
   }
 }
 
 template <typename R>
-void launch_anterp(const R* mr, const int32_t* mr_base, const int32_t* mr_ext, const int64_t* mr_off,
-                   const R* mt, const int32_t* mt_base, const int32_t* mt_ext, const int64_t* mt_off,
-                   const int64_t* box_rwg_ptr, const int64_t* box_tri_ptr, int64_t B,
-                   const cpx_t<R>* xs, int64_t ldx, const cpx_t<R>* rho, int64_t ldr, int nr,
-                   cpx_t<R>* q, int sp, cudaStream_t s) {
+void launch_gather_build(const R* mr, const int32_t* mr_base, const int32_t* mr_ext, const int64_t* mr_off,
+                         const R* mt, const int32_t* mt_base, const int32_t* mt_ext, const int64_t* mt_off,
+                         const int64_t* box_rwg_ptr, const int64_t* box_tri_ptr, int64_t B, int sp,
+                         int32_t* gptr_r, int32_t* gptr_t, R* gr, R* gt, cudaStream_t s) {
+  if (B <= 0) return;
+  const size_t smem = sizeof(int32_t) * 2 * (size_t)sp * sp * sp;
+  if (smem > 48 * 1024) cudaFuncSetAttribute(k_gather_build<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_gather_build<R><<<(unsigned)B, 256, smem, s>>>(mr, mr_base, mr_ext, mr_off, mt, mt_base, mt_ext, mt_off,
+                                                   box_rwg_ptr, box_tri_ptr, sp, gptr_r, gptr_t, gr, gt);
+}
+
+template <typename R>
+void launch_anterp(const R* gr, const R* gt, const int32_t* gptr_r, const int32_t* gptr_t, const int64_t* mr_off,
+                   const int64_t* mt_off, const int64_t* box_rwg_ptr, const int64_t* box_tri_ptr, int64_t B,
+                   const cpx_t<R>* xs, int64_t ldx, const cpx_t<R>* rho, int64_t ldr, int nr, cpx_t<R>* q,
+                   int sp, cudaStream_t s) {
   if (B <= 0 || nr <= 0) return;
-  const int64_t npts = (int64_t)sp * sp * sp;
-  const int64_t per_rhs = npts * 4 * 2 * sizeof(R);
-  int rt = (int)(200 * 1024 / (per_rhs + npts * sizeof(R)));
-  if (rt < 1) rt = 1;
-  if (rt > nr) rt = nr;
-  size_t smem = (size_t)npts * (8 * rt + 1) * sizeof(R);
-  static bool attr_set[2] = {false, false};
-  int which = sizeof(R) == 8;
-  if (!attr_set[which]) {
-    cudaFuncSetAttribute(k_anterp<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    attr_set[which] = true;
-  }
-  dim3 grid((unsigned)B, (unsigned)ceil_div(nr, rt));
-  k_anterp<R><<<grid, 256, smem, s>>>(mr, mr_base, mr_ext, mr_off, mt, mt_base, mt_ext, mt_off,
-                                      box_rwg_ptr, box_tri_ptr, xs, ldx, rho, ldr, nr, rt, q, sp);
+  k_anterp<R><<<(unsigned)B, 256, 0, s>>>(gr, gt, gptr_r, gptr_t, mr_off, mt_off, box_rwg_ptr, box_tri_ptr, xs,
+                                          ldx, rho, ldr, nr, q, sp);
 }
 
 // ---------------------------------------------------------------- interpolation
-// One warp per basis function; yA[r][i] = sum_d sum_e m_d[e] r[b][pt][4r+d],
-// u[r][t] = sum_e m^phi[e] r[b][pt][4r+3] (FP64 outputs).
-template <typename R, int RMAX>
-__global__ void k_interp(const R* __restrict__ mr, const int32_t* __restrict__ mr_base,
-                         const int32_t* __restrict__ mr_ext, const int64_t* __restrict__ mr_off,
-                         const int32_t* __restrict__ rwg_box, int64_t N, const R* __restrict__ mt,
-                         const int32_t* __restrict__ mt_base, const int32_t* __restrict__ mt_ext,
-                         const int64_t* __restrict__ mt_off, const int32_t* __restrict__ tri_box,
-                         int64_t Nt, const cpx_t<R>* __restrict__ rg, int sp, int nr,
-                         double2* __restrict__ yA, int64_t ldy, double2* __restrict__ u, int64_t ldu) {
+// yA[r][i] = sum_e sum_d m_d[e] r[b][pt(e)][d nr + r] for RWG i, and
+// u[r][t] = sum_e m^phi[e] r[b][pt(e)][3 nr + r] for triangle t (FP64
+// outputs).  One warp per basis function.  RWG: lane = channel d nr + r of
+// the vector part (3 nr <= 24 lanes), so every grid point is one coalesced
+// read; the three components are summed by shuffles at the end.  Triangle:
+// the charge part is nr values per point, so the warp takes 32/nr entries at
+// a time, lane = (entry slot, r).
+template <typename R>
+__global__ void __launch_bounds__(256) k_interp(const R* __restrict__ mr, const int32_t* __restrict__ mr_base,
+                                                const int32_t* __restrict__ mr_ext,
+                                                const int64_t* __restrict__ mr_off,
+                                                const int32_t* __restrict__ rwg_box, int64_t N,
+                                                const R* __restrict__ mt, const int32_t* __restrict__ mt_base,
+                                                const int32_t* __restrict__ mt_ext,
+                                                const int64_t* __restrict__ mt_off,
+                                                const int32_t* __restrict__ tri_box, int64_t Nt,
+                                                const cpx_t<R>* __restrict__ rg, int sp, int nr,
+                                                double2* __restrict__ yA, int64_t ldy, double2* __restrict__ u,
+                                                int64_t ldu) {
   using T = cpx_t<R>;
   const int lane = threadIdx.x & 31;
   const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int npts = sp * sp * sp;
-  const int C = 4 * nr;
-  const bool is_rwg = w < N;
   if (w >= N + Nt) return;
-  const int64_t i = is_rwg ? w : w - N;
-  const int32_t* base = is_rwg ? mr_base + 3 * i : mt_base + 3 * i;
-  const int32_t* ext = is_rwg ? mr_ext + 3 * i : mt_ext + 3 * i;
-  const int e0 = ext[0], e1 = ext[1], e2 = ext[2];
-  const int ne = e0 * e1 * e2;
-  const R* m = is_rwg ? mr + mr_off[i] : mt + mt_off[i];
-  const int box = is_rwg ? rwg_box[i] : tri_box[i];
-  const T* gb = rg + (int64_t)box * npts * C;
-  T acc[RMAX];
-#pragma unroll
-  for (int r = 0; r < RMAX; ++r) acc[r] = mk<R>(0, 0);
-  for (int e = lane; e < ne; e += 32) {
-    int a0 = e / (e1 * e2), rem = e - a0 * e1 * e2, a1 = rem / e2, a2 = rem - a1 * e2;
-    int pt = ((base[0] + a0) * sp + (base[1] + a1)) * sp + (base[2] + a2);
-    const T* gp = gb + (int64_t)pt * C;
-    if (is_rwg) {
-      R m0 = m[e], m1 = m[ne + e], m2 = m[2 * ne + e];
-#pragma unroll
-      for (int r = 0; r < RMAX; ++r) {
-        if (r >= nr) break;
-        T g0 = gp[4 * r], g1 = gp[4 * r + 1], g2 = gp[4 * r + 2];
-        acc[r].x += m0 * g0.x + m1 * g1.x + m2 * g2.x;
-        acc[r].y += m0 * g0.y + m1 * g1.y + m2 * g2.y;
+  const int npts = sp * sp * sp, C = 4 * nr;
+  T acc = mk<R>(0, 0);
+  if (w < N) {
+    const int64_t i = w;
+    const int b0 = mr_base[3 * i], b1 = mr_base[3 * i + 1], b2 = mr_base[3 * i + 2];
+    const int e0 = mr_ext[3 * i], e1 = mr_ext[3 * i + 1], e2 = mr_ext[3 * i + 2];
+    const int ne = e0 * e1 * e2;
+    const bool act = lane < 3 * nr;
+    const int d = act ? lane / nr : 0;
+    const R* m = mr + mr_off[i] + (int64_t)d * ne;
+    const T* gp = rg + (int64_t)rwg_box[i] * npts * C + lane;
+    if (act) {
+      int e = 0;
+      for (int a0 = 0; a0 < e0; ++a0)
+        for (int a1 = 0; a1 < e1; ++a1) {
+          const T* gl = gp + (int64_t)(((b0 + a0) * sp + b1 + a1) * sp + b2) * C;
+#pragma unroll 4
+          for (int a2 = 0; a2 < e2; ++a2, ++e) {
+            const R mv = m[e];
+            const T gv = gl[a2 * C];
+            acc.x = fma(mv, gv.x, acc.x);
+            acc.y = fma(mv, gv.y, acc.y);
+          }
+        }
+    }
+    R sx = acc.x + __shfl_down_sync(0xffffffffu, acc.x, nr) + __shfl_down_sync(0xffffffffu, acc.x, 2 * nr);
+    R sy = acc.y + __shfl_down_sync(0xffffffffu, acc.y, nr) + __shfl_down_sync(0xffffffffu, acc.y, 2 * nr);
+    if (lane < nr) yA[lane * ldy + i] = make_double2((double)sx, (double)sy);
+  } else {
+    const int64_t i = w - N;
+    const int b0 = mt_base[3 * i], b1 = mt_base[3 * i + 1], b2 = mt_base[3 * i + 2];
+    const int e0 = mt_ext[3 * i], e1 = mt_ext[3 * i + 1], e2 = mt_ext[3 * i + 2];
+    const int ne = e0 * e1 * e2;
+    const int Q = 32 / nr;
+    const int slot = lane / nr, r = lane - slot * nr;
+    const R* m = mt + mt_off[i];
+    const T* gp = rg + (int64_t)tri_box[i] * npts * C + 3 * nr + r;
+    if (slot < Q && ne > 0) {
+      int e = slot;
+      int a0 = e / (e1 * e2), a1 = (e / e2) % e1, a2 = e % e2;
+      for (; e < ne; e += Q) {
+        const T gv = gp[(int64_t)(((b0 + a0) * sp + b1 + a1) * sp + b2 + a2) * C];
+        const R mv = m[e];
+        acc.x = fma(mv, gv.x, acc.x);
+        acc.y = fma(mv, gv.y, acc.y);
+        a2 += Q;
+        while (a2 >= e2) {
+          a2 -= e2;
+          if (++a1 == e1) {
+            a1 = 0;
+            ++a0;
+          }
+        }
       }
-    } else {
-      R m0 = m[e];
-#pragma unroll
-      for (int r = 0; r < RMAX; ++r) {
-        if (r >= nr) break;
-        T g3 = gp[4 * r + 3];
-        acc[r].x += m0 * g3.x;
-        acc[r].y += m0 * g3.y;
-      }
     }
-  }
-#pragma unroll
-  for (int r = 0; r < RMAX; ++r) {
-    if (r >= nr) break;
-    double vx = (double)acc[r].x, vy = (double)acc[r].y;
-    for (int o = 16; o > 0; o >>= 1) {
-      vx += __shfl_down_sync(0xffffffffu, vx, o);
-      vy += __shfl_down_sync(0xffffffffu, vy, o);
+    R sx = acc.x, sy = acc.y;
+    for (int o = 1; o < Q; ++o) {
+      sx += __shfl_down_sync(0xffffffffu, acc.x, o * nr);
+      sy += __shfl_down_sync(0xffffffffu, acc.y, o * nr);
     }
-    if (lane == 0) {
-      if (is_rwg)
-        yA[r * ldy + i] = make_double2(vx, vy);
-      else
-        u[r * ldu + i] = make_double2(vx, vy);
-    }
+    if (lane < nr) u[lane * ldu + i] = make_double2((double)sx, (double)sy);
   }
 }
 
@@ -392,15 +555,8 @@ void launch_interp(const R* mr, const int32_t* mr_base, const int32_t* mr_ext, c
   // nr <= 8 (the far pipeline runs right-hand sides in chunks of at most 8)
   int64_t warps = N + Nt;
   int64_t blocks = ceil_div(warps * 32, 256);
-  if (nr <= 1)
-    k_interp<R, 1><<<(unsigned)blocks, 256, 0, s>>>(mr, mr_base, mr_ext, mr_off, rwg_box, N, mt, mt_base,
-                                                    mt_ext, mt_off, tri_box, Nt, r, sp, nr, yA, ldy, u, ldu);
-  else if (nr <= 4)
-    k_interp<R, 4><<<(unsigned)blocks, 256, 0, s>>>(mr, mr_base, mr_ext, mr_off, rwg_box, N, mt, mt_base,
-                                                    mt_ext, mt_off, tri_box, Nt, r, sp, nr, yA, ldy, u, ldu);
-  else
-    k_interp<R, 8><<<(unsigned)blocks, 256, 0, s>>>(mr, mr_base, mr_ext, mr_off, rwg_box, N, mt, mt_base,
-                                                    mt_ext, mt_off, tri_box, Nt, r, sp, nr, yA, ldy, u, ldu);
+  k_interp<R><<<(unsigned)blocks, 256, 0, s>>>(mr, mr_base, mr_ext, mr_off, rwg_box, N, mt, mt_base, mt_ext,
+                                               mt_off, tri_box, Nt, r, sp, nr, yA, ldy, u, ldu);
 }
 
 // ---------------------------------------------------------------- translation MAC
@@ -1033,14 +1189,20 @@ template void launch_mode<float>(const float2*, View, float2*, View, int64_t, in
 template void launch_mode<double>(const double2*, View, double2*, View, int64_t, int, int, int, int, int, int,
                                   const void*, const void*, bool, const int8_t*, const int64_t*, bool,
                                   cudaStream_t);
-template void launch_anterp<float>(const float*, const int32_t*, const int32_t*, const int64_t*, const float*,
-                                   const int32_t*, const int32_t*, const int64_t*, const int64_t*,
-                                   const int64_t*, int64_t, const float2*, int64_t, const float2*, int64_t,
-                                   int, float2*, int, cudaStream_t);
-template void launch_anterp<double>(const double*, const int32_t*, const int32_t*, const int64_t*,
-                                    const double*, const int32_t*, const int32_t*, const int64_t*,
-                                    const int64_t*, const int64_t*, int64_t, const double2*, int64_t,
-                                    const double2*, int64_t, int, double2*, int, cudaStream_t);
+template void launch_gather_build<float>(const float*, const int32_t*, const int32_t*, const int64_t*,
+                                         const float*, const int32_t*, const int32_t*, const int64_t*,
+                                         const int64_t*, const int64_t*, int64_t, int, int32_t*, int32_t*, float*,
+                                         float*, cudaStream_t);
+template void launch_gather_build<double>(const double*, const int32_t*, const int32_t*, const int64_t*,
+                                          const double*, const int32_t*, const int32_t*, const int64_t*,
+                                          const int64_t*, const int64_t*, int64_t, int, int32_t*, int32_t*,
+                                          double*, double*, cudaStream_t);
+template void launch_anterp<float>(const float*, const float*, const int32_t*, const int32_t*, const int64_t*,
+                                   const int64_t*, const int64_t*, const int64_t*, int64_t, const float2*, int64_t,
+                                   const float2*, int64_t, int, float2*, int, cudaStream_t);
+template void launch_anterp<double>(const double*, const double*, const int32_t*, const int32_t*, const int64_t*,
+                                    const int64_t*, const int64_t*, const int64_t*, int64_t, const double2*,
+                                    int64_t, const double2*, int64_t, int, double2*, int, cudaStream_t);
 template void launch_interp<float>(const float*, const int32_t*, const int32_t*, const int64_t*, const int32_t*,
                                    int64_t, const float*, const int32_t*, const int32_t*, const int64_t*,
                                    const int32_t*, int64_t, const float2*, int, int, double2*, int64_t,

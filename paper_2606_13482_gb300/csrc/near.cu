@@ -340,9 +340,9 @@ __global__ void k_near_combine_A(NearDev nd, int64_t j0, int64_t nblk, const int
   int64_t eg = e_begin + e;
   int64_t j = find_block(nd.blkA_off + j0, nblk, eg) + j0;
   int32_t x = nd.blk_tgt[j], y = nd.near_src[j];
-  int64_t nyr = nd.box_rwg_ptr[y + 1] - nd.box_rwg_ptr[y];
+  int64_t nxr = nd.box_rwg_ptr[x + 1] - nd.box_rwg_ptr[x];
   int64_t loc = eg - nd.blkA_off[j];
-  int64_t r = loc / nyr, c = loc - r * nyr;
+  int64_t c = loc / nxr, r = loc - c * nxr;  // column-major block
   int64_t i = nd.box_rwg_ptr[x] + r, n = nd.box_rwg_ptr[y] + c;
   int64_t nty = nd.tset_ptr[y + 1] - nd.tset_ptr[y];
   const double2* scr = scratch + 10 * scr_off[j - j0];
@@ -365,9 +365,9 @@ __global__ void k_near_V(NearDev nd, int64_t e_begin, int64_t total) {
   int64_t eg = e_begin + e;
   int64_t j = find_block(nd.blkV_off, nd.n_blocks, eg);
   int32_t x = nd.blk_tgt[j], y = nd.near_src[j];
-  int64_t nyt = nd.box_tri_ptr[y + 1] - nd.box_tri_ptr[y];
+  int64_t nxt = nd.box_tri_ptr[x + 1] - nd.box_tri_ptr[x];
   int64_t loc = eg - nd.blkV_off[j];
-  int64_t a = loc / nyt, b = loc - a * nyt;
+  int64_t b = loc / nxt, a = loc - b * nxt;  // column-major block
   int ta = nd.tri_perm[nd.box_tri_ptr[x] + a];
   int tb = nd.tri_perm[nd.box_tri_ptr[y] + b];
   double2 I0, dummy[9];
@@ -377,43 +377,78 @@ __global__ void k_near_V(NearDev nd, int64_t e_begin, int64_t total) {
 }
 
 // ---------------------------------------------------------------- SpMV
-// y[r][i] += sum_{blocks} M_blk[row][col] x[r][src_start + col]; one CTA per
-// target box, one warp per row, lanes over columns.  Sorted orders; x, y are
-// [R][n] c128 with leading dimension ld.
-template <int RMAX>
-__global__ void k_near_spmv(const double2* __restrict__ M, const int64_t* __restrict__ blk_off,
-                            const int64_t* __restrict__ near_ptr, const int32_t* __restrict__ near_src,
-                            const int64_t* __restrict__ box_ptr, const double2* __restrict__ x,
-                            double2* __restrict__ y, int64_t ld, int nr) {
-  int xb = blockIdx.x;
-  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  int64_t r0 = box_ptr[xb], nrow = box_ptr[xb + 1] - r0;
-  for (int64_t row = warp; row < nrow; row += nw) {
-    double2 acc[RMAX];
+// y[r][i] += sum_{blocks} M_blk[row][col] x[r][src_start + col] over the near
+// blocks of the target box.  Blocks are column-major ([col][row]), so threads
+// that own consecutive rows read one column of a block as one coalesced
+// stream; the source box's x values are staged in shared memory, NEAR_CH
+// columns at a time, and read as broadcasts.  One CTA per target box; a
+// thread owns up to UPT "units" = (row, group of RPT right-hand sides), and
+// keeps their sums in registers across all source boxes, so no reduction is
+// needed.  Sorted orders; x, y are [nr][n] with leading dimension ld, nr <= 8.
+constexpr int NEAR_CH = 64;
+constexpr int NEAR_THREADS = 128;
+
+template <int RPT, int UPT>
+__global__ void __launch_bounds__(NEAR_THREADS)
+k_near_rows(const double2* __restrict__ M, const int64_t* __restrict__ blk_off,
+            const int64_t* __restrict__ near_ptr, const int32_t* __restrict__ near_src,
+            const int64_t* __restrict__ box_ptr, const double2* __restrict__ x,
+            double2* __restrict__ y, int64_t ld, int nr) {
+  __shared__ double2 xs[8][NEAR_CH];
+  const int xb = blockIdx.x, tid = threadIdx.x;
+  const int64_t r0 = box_ptr[xb];
+  const int nrow = (int)(box_ptr[xb + 1] - r0);
+  const int ngrp = (nr + RPT - 1) / RPT, nunits = nrow * ngrp;
+  const int64_t j0 = near_ptr[xb], j1 = near_ptr[xb + 1];
+  for (int ubase = 0; ubase < nunits; ubase += UPT * NEAR_THREADS) {
+    int row[UPT], grp[UPT];
+    bool ok[UPT];
+    double2 acc[UPT][RPT];
 #pragma unroll
-    for (int r = 0; r < RMAX; ++r) acc[r] = make_double2(0, 0);
-    for (int64_t j = near_ptr[xb]; j < near_ptr[xb + 1]; ++j) {
-      int32_t yb = near_src[j];
-      int64_t c0 = box_ptr[yb], ncol = box_ptr[yb + 1] - c0;
-      const double2* Mr = M + blk_off[j] + row * ncol;
-      for (int64_t c = lane; c < ncol; c += 32) {
-        double2 a = Mr[c];
+    for (int k = 0; k < UPT; ++k) {
+      int u = ubase + k * NEAR_THREADS + tid;
+      ok[k] = u < nunits;
+      grp[k] = ok[k] ? u / nrow : 0;
+      row[k] = ok[k] ? u - grp[k] * nrow : 0;
 #pragma unroll
-        for (int r = 0; r < RMAX; ++r)
-          if (r < nr) cfma(acc[r], a, x[r * ld + c0 + c]);
+      for (int q = 0; q < RPT; ++q) acc[k][q] = make_double2(0, 0);
+    }
+    for (int64_t j = j0; j < j1; ++j) {
+      const int32_t yb = near_src[j];
+      const int64_t c0 = box_ptr[yb];
+      const int ncol = (int)(box_ptr[yb + 1] - c0);
+      const double2* Mb = M + blk_off[j];
+      for (int cb = 0; cb < ncol; cb += NEAR_CH) {
+        const int ncc = min(NEAR_CH, ncol - cb);
+        __syncthreads();
+        for (int i = tid; i < nr * NEAR_CH; i += NEAR_THREADS) {
+          int r = i / NEAR_CH, cc = i - r * NEAR_CH;
+          if (cc < ncc) xs[r][cc] = x[r * ld + c0 + cb + cc];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < UPT; ++k) {
+          if (!ok[k]) continue;
+          const double2* Mc = Mb + (int64_t)cb * nrow + row[k];
+          for (int cc = 0; cc < ncc; ++cc) {
+            double2 a = Mc[(int64_t)cc * nrow];
+#pragma unroll
+            for (int q = 0; q < RPT; ++q)
+              if (grp[k] * RPT + q < nr) cfma(acc[k][q], a, xs[grp[k] * RPT + q][cc]);
+          }
+        }
       }
     }
 #pragma unroll
-    for (int r = 0; r < RMAX; ++r) {
-      if (r >= nr) break;
-      double2 v = acc[r];
-      for (int o = 16; o > 0; o >>= 1) {
-        v.x += __shfl_down_sync(0xffffffffu, v.x, o);
-        v.y += __shfl_down_sync(0xffffffffu, v.y, o);
-      }
-      if (lane == 0) {
-        double2 t = y[r * ld + r0 + row];
-        y[r * ld + r0 + row] = make_double2(t.x + v.x, t.y + v.y);
+    for (int k = 0; k < UPT; ++k) {
+      if (!ok[k]) continue;
+#pragma unroll
+      for (int q = 0; q < RPT; ++q) {
+        int r = grp[k] * RPT + q;
+        if (r >= nr) break;
+        double2* yp = y + r * ld + r0 + row[k];
+        double2 t = *yp;
+        *yp = make_double2(t.x + acc[k][q].x, t.y + acc[k][q].y);
       }
     }
   }
@@ -460,53 +495,107 @@ __device__ __forceinline__ void df_add(DF& S, float p) {
   S.lo = __fadd_rn(S.lo, err);
 }
 
-template <int RMAX>
-__global__ void k_near_spmv_df(const float4* __restrict__ M, const int64_t* __restrict__ blk_off,
-                               const int64_t* __restrict__ near_ptr, const int32_t* __restrict__ near_src,
-                               const int64_t* __restrict__ box_ptr, const float4* __restrict__ x,
-                               double2* __restrict__ y, int64_t ld, int nr) {
-  int xb = blockIdx.x;
-  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  int64_t r0 = box_ptr[xb], nrow = box_ptr[xb + 1] - r0;
-  for (int64_t row = warp; row < nrow; row += nw) {
-    DF re[RMAX], im[RMAX];
+// re/im += a * v for one complex entry a = (re_hi, re_lo, im_hi, im_lo) and
+// one complex x value v in the same form.  Each hi x hi product is split into
+// p + e exactly by one FMA; e and the hi x lo cross terms go straight into the
+// low word, p into the high word by the two-sum.  48 FP32 operations.
+__device__ __forceinline__ void df_cmac(DF& re, DF& im, const float4 a, const float4 v) {
+  float p1 = __fmul_rn(a.x, v.x), e1 = __fmaf_rn(a.x, v.x, -p1);  // ar xr
+  float p2 = __fmul_rn(a.z, v.z), e2 = __fmaf_rn(a.z, v.z, -p2);  // ai xi
+  float lr = __fmaf_rn(a.x, v.y, re.lo);
+  lr = __fmaf_rn(a.y, v.x, lr);
+  lr = __fmaf_rn(-a.z, v.w, lr);
+  lr = __fmaf_rn(-a.w, v.z, lr);
+  re.lo = __fadd_rn(lr, __fsub_rn(e1, e2));
+  df_add(re, p1);
+  df_add(re, -p2);
+  float p3 = __fmul_rn(a.x, v.z), e3 = __fmaf_rn(a.x, v.z, -p3);  // ar xi
+  float p4 = __fmul_rn(a.z, v.x), e4 = __fmaf_rn(a.z, v.x, -p4);  // ai xr
+  float li = __fmaf_rn(a.x, v.w, im.lo);
+  li = __fmaf_rn(a.y, v.z, li);
+  li = __fmaf_rn(a.z, v.y, li);
+  li = __fmaf_rn(a.w, v.x, li);
+  im.lo = __fadd_rn(li, __fadd_rn(e3, e4));
+  df_add(im, p3);
+  df_add(im, p4);
+}
+
+// Same structure as k_near_rows (column-major blocks, x staged in shared
+// memory, sums in registers), in double-float arithmetic.  The next column's
+// matrix entry is loaded before the current one is used.
+template <int RPT, int UPT>
+__global__ void __launch_bounds__(NEAR_THREADS)
+k_near_rows_df(const float4* __restrict__ M, const int64_t* __restrict__ blk_off,
+               const int64_t* __restrict__ near_ptr, const int32_t* __restrict__ near_src,
+               const int64_t* __restrict__ box_ptr, const float4* __restrict__ x,
+               double2* __restrict__ y, int64_t ld, int nr) {
+  __shared__ float4 xs[8][NEAR_CH];
+  const int xb = blockIdx.x, tid = threadIdx.x;
+  const int64_t r0 = box_ptr[xb];
+  const int nrow = (int)(box_ptr[xb + 1] - r0);
+  const int ngrp = (nr + RPT - 1) / RPT, nunits = nrow * ngrp;
+  const int64_t j0 = near_ptr[xb], j1 = near_ptr[xb + 1];
+  for (int ubase = 0; ubase < nunits; ubase += UPT * NEAR_THREADS) {
+    int row[UPT], grp[UPT];
+    bool ok[UPT];
+    DF re[UPT][RPT], im[UPT][RPT];
 #pragma unroll
-    for (int r = 0; r < RMAX; ++r) re[r] = im[r] = DF{0.f, 0.f};
-    for (int64_t j = near_ptr[xb]; j < near_ptr[xb + 1]; ++j) {
-      int32_t yb = near_src[j];
-      int64_t c0 = box_ptr[yb], ncol = box_ptr[yb + 1] - c0;
-      const float4* Mr = M + blk_off[j] + row * ncol;
-      for (int64_t c = lane; c < ncol; c += 32) {
-        float4 a = Mr[c];
+    for (int k = 0; k < UPT; ++k) {
+      int u = ubase + k * NEAR_THREADS + tid;
+      ok[k] = u < nunits;
+      grp[k] = ok[k] ? u / nrow : 0;
+      row[k] = ok[k] ? u - grp[k] * nrow : 0;
 #pragma unroll
-        for (int r = 0; r < RMAX; ++r) {
-          if (r >= nr) break;
-          float4 v = x[r * ld + c0 + c];
-          // re += a_r x_r - a_i x_i ; im += a_r x_i + a_i x_r
-          float p1 = __fmul_rn(a.x, v.x), e1 = fmaf(a.x, v.x, -p1), c1 = fmaf(a.x, v.y, a.y * v.x);
-          float p2 = __fmul_rn(a.z, v.z), e2 = fmaf(a.z, v.z, -p2), c2 = fmaf(a.z, v.w, a.w * v.z);
-          df_add(re[r], p1);
-          df_add(re[r], -p2);
-          re[r].lo += (e1 - e2) + (c1 - c2);
-          float p3 = __fmul_rn(a.x, v.z), e3 = fmaf(a.x, v.z, -p3), c3 = fmaf(a.x, v.w, a.y * v.z);
-          float p4 = __fmul_rn(a.z, v.x), e4 = fmaf(a.z, v.x, -p4), c4 = fmaf(a.z, v.y, a.w * v.x);
-          df_add(im[r], p3);
-          df_add(im[r], p4);
-          im[r].lo += (e3 + e4) + (c3 + c4);
+      for (int q = 0; q < RPT; ++q) re[k][q] = im[k][q] = DF{0.f, 0.f};
+    }
+    for (int64_t j = j0; j < j1; ++j) {
+      const int32_t yb = near_src[j];
+      const int64_t c0 = box_ptr[yb];
+      const int ncol = (int)(box_ptr[yb + 1] - c0);
+      const float4* Mb = M + blk_off[j];
+      for (int cb = 0; cb < ncol; cb += NEAR_CH) {
+        const int ncc = min(NEAR_CH, ncol - cb);
+        __syncthreads();
+        for (int i = tid; i < nr * NEAR_CH; i += NEAR_THREADS) {
+          int r = i / NEAR_CH, cc = i - r * NEAR_CH;
+          if (cc < ncc) xs[r][cc] = x[r * ld + c0 + cb + cc];
+        }
+        __syncthreads();
+        const float4* Mc[UPT];
+        float4 a[UPT];
+#pragma unroll
+        for (int k = 0; k < UPT; ++k) {
+          Mc[k] = Mb + (int64_t)cb * nrow + row[k];
+          a[k] = ok[k] ? Mc[k][0] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        for (int cc = 0; cc < ncc; ++cc) {
+          const int cn = cc + 1 < ncc ? cc + 1 : cc;
+          float4 an[UPT];
+#pragma unroll
+          for (int k = 0; k < UPT; ++k) an[k] = ok[k] ? Mc[k][(int64_t)cn * nrow] : a[k];
+#pragma unroll
+          for (int k = 0; k < UPT; ++k) {
+            if (!ok[k]) continue;
+#pragma unroll
+            for (int q = 0; q < RPT; ++q)
+              if (grp[k] * RPT + q < nr) df_cmac(re[k][q], im[k][q], a[k], xs[grp[k] * RPT + q][cc]);
+          }
+#pragma unroll
+          for (int k = 0; k < UPT; ++k) a[k] = an[k];
         }
       }
     }
 #pragma unroll
-    for (int r = 0; r < RMAX; ++r) {
-      if (r >= nr) break;
-      double vx = (double)re[r].hi + (double)re[r].lo, vy = (double)im[r].hi + (double)im[r].lo;
-      for (int o = 16; o > 0; o >>= 1) {
-        vx += __shfl_down_sync(0xffffffffu, vx, o);
-        vy += __shfl_down_sync(0xffffffffu, vy, o);
-      }
-      if (lane == 0) {
-        double2 t = y[r * ld + r0 + row];
-        y[r * ld + r0 + row] = make_double2(t.x + vx, t.y + vy);
+    for (int k = 0; k < UPT; ++k) {
+      if (!ok[k]) continue;
+#pragma unroll
+      for (int q = 0; q < RPT; ++q) {
+        int r = grp[k] * RPT + q;
+        if (r >= nr) break;
+        double2* yp = y + r * ld + r0 + row[k];
+        double2 t = *yp;
+        *yp = make_double2(t.x + ((double)re[k][q].hi + (double)re[k][q].lo),
+                           t.y + ((double)im[k][q].hi + (double)im[k][q].lo));
       }
     }
   }
@@ -524,6 +613,8 @@ void launch_split_vec(const double2* x, float4* y, int64_t n, cudaStream_t s) {
   if (blocks > 152 * 64) blocks = 152 * 64;
   k_split_vec<<<(unsigned)blocks, 256, 0, s>>>(x, y, n);
 }
+// right-hand sides per unit: all of a 1-, 2- or 4-wide chunk; 4 for wider
+// chunks (two units per row)
 void launch_near_spmv_df(const float4* M, const int64_t* blk_off, const int64_t* near_ptr,
                          const int32_t* near_src, const int64_t* box_ptr, int64_t n_boxes, const float4* x,
                          double2* y, int64_t ld, int nr, cudaStream_t s) {
@@ -532,12 +623,15 @@ void launch_near_spmv_df(const float4* M, const int64_t* blk_off, const int64_t*
     int cnt = nr - r0 < 8 ? nr - r0 : 8;
     const float4* xr = x + (int64_t)r0 * ld;
     double2* yr = y + (int64_t)r0 * ld;
-    if (cnt <= 1)
-      k_near_spmv_df<1><<<(unsigned)n_boxes, 256, 0, s>>>(M, blk_off, near_ptr, near_src, box_ptr, xr, yr, ld, cnt);
-    else if (cnt <= 4)
-      k_near_spmv_df<4><<<(unsigned)n_boxes, 256, 0, s>>>(M, blk_off, near_ptr, near_src, box_ptr, xr, yr, ld, cnt);
+    if (cnt == 1)
+      k_near_rows_df<1, 1><<<(unsigned)n_boxes, NEAR_THREADS, 0, s>>>(M, blk_off, near_ptr, near_src, box_ptr,
+                                                                       xr, yr, ld, cnt);
+    else if (cnt == 2)
+      k_near_rows_df<2, 1><<<(unsigned)n_boxes, NEAR_THREADS, 0, s>>>(M, blk_off, near_ptr, near_src, box_ptr,
+                                                                       xr, yr, ld, cnt);
     else
-      k_near_spmv_df<8><<<(unsigned)n_boxes, 256, 0, s>>>(M, blk_off, near_ptr, near_src, box_ptr, xr, yr, ld, cnt);
+      k_near_rows_df<4, 2><<<(unsigned)n_boxes, NEAR_THREADS, 0, s>>>(M, blk_off, near_ptr, near_src, box_ptr,
+                                                                       xr, yr, ld, cnt);
   }
 }
 
@@ -571,12 +665,15 @@ void launch_near_spmv(const double2* M, const int64_t* blk_off, const int64_t* n
     int cnt = nr - r0 < 8 ? nr - r0 : 8;
     const double2* xr = x + (int64_t)r0 * ld;
     double2* yr = y + (int64_t)r0 * ld;
-    if (cnt <= 1)
-      k_near_spmv<1><<<(unsigned)n_boxes, 256, 0, s>>>(M, blk_off, near_ptr, near_src, box_ptr, xr, yr, ld, cnt);
-    else if (cnt <= 4)
-      k_near_spmv<4><<<(unsigned)n_boxes, 256, 0, s>>>(M, blk_off, near_ptr, near_src, box_ptr, xr, yr, ld, cnt);
+    if (cnt == 1)
+      k_near_rows<1, 1><<<(unsigned)n_boxes, NEAR_THREADS, 0, s>>>(M, blk_off, near_ptr, near_src, box_ptr, xr,
+                                                                    yr, ld, cnt);
+    else if (cnt == 2)
+      k_near_rows<2, 1><<<(unsigned)n_boxes, NEAR_THREADS, 0, s>>>(M, blk_off, near_ptr, near_src, box_ptr, xr,
+                                                                    yr, ld, cnt);
     else
-      k_near_spmv<8><<<(unsigned)n_boxes, 256, 0, s>>>(M, blk_off, near_ptr, near_src, box_ptr, xr, yr, ld, cnt);
+      k_near_rows<4, 2><<<(unsigned)n_boxes, NEAR_THREADS, 0, s>>>(M, blk_off, near_ptr, near_src, box_ptr, xr,
+                                                                    yr, ld, cnt);
   }
 }
 
