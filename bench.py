@@ -32,6 +32,7 @@ sys.path.insert(0, ROOT)
 WORKLOADS = {
     "sphere20": dict(freq=200, radius=10.0, k=2 * np.pi, p=3, delta=0.1, levels=3, nrhs=64, precision="mixed"),
     "sphere10": dict(freq=100, radius=5.0, k=2 * np.pi, p=3, delta=0.1, levels=3, nrhs=64, precision="mixed"),
+    "sphere6": dict(freq=60, radius=3.0, k=2 * np.pi, p=3, delta=0.1, levels=3, nrhs=16, precision="mixed"),
     "sphere4": dict(freq=40, radius=2.0, k=2 * np.pi, p=3, delta=0.1, levels=2, nrhs=16, precision="mixed"),
     "c1": dict(freq=8, radius=0.5, k=2 * np.pi, p=3, delta=0.1, levels=2, nrhs=1, precision="fp64"),
 }
@@ -46,10 +47,11 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-# FMA throughput of this GPU measured with a dependent-FMA probe (8 independent
-# chains per thread, 8 CTAs of 256 threads per SM): FP32 69.6 TFLOP/s,
-# FP64 1.20 TFLOP/s at ~1.99 GHz.
-FP32_TFLOPS = 69.6
+# FMA throughput of this GPU measured with a dependent-FMA probe (16 independent
+# chains per thread, 8 CTAs of 256 threads per SM, 2.07 GHz): FP32 74.3 TFLOP/s
+# with fma.rn.f32 and 76.0 TFLOP/s with the packed fma.rn.f32x2 (the larger is
+# the peak used here); FP64 1.20 TFLOP/s (8 chains, ~1.99 GHz).
+FP32_TFLOPS = 76.0
 FP64_TFLOPS = 1.20
 
 
@@ -523,13 +525,91 @@ def reference_arm(args, w):
             "e2e": {"value": v, "unit": "matvecs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def batch_meshes():
+    """Ten PEC ellipsoids, semi-axes uniform in [0.5, 3] wavelengths (seed 3),
+    each a scaled geodesic sphere whose frequency gives ~0.1-wavelength edges
+    (area-equivalent radius), clamped to 5,000 - 60,000 unknowns."""
+    import efie_inputs as E
+    rng = np.random.default_rng(3)
+    out = []
+    for _ in range(10):
+        a, b, c = rng.uniform(0.5, 3.0, size=3)
+        # Knud Thomsen's surface approximation, then the equal-area sphere radius
+        pp = 1.6075
+        area = 4 * np.pi * (((a * b) ** pp + (a * c) ** pp + (b * c) ** pp) / 3) ** (1 / pp)
+        r_eq = np.sqrt(area / (4 * np.pi))
+        freq = int(round(1.205 * r_eq / 0.1))
+        freq = int(np.clip(freq, 13, 44))
+        out.append(E.ellipsoid(freq, (a, b, c)))
+    return out
+
+
+def run_batch(args):
+    """Batched form: every ellipsoid's product in one CUDA graph launch, one
+    plane wave on nine of them and 360 monostatic plane waves (azimuth, 1 degree
+    steps, theta-hat polarisation) on the largest; mixed precision, p = 3,
+    0.1-wavelength grid, autotuned chunk and kernels per mesh."""
+    import torch
+    import __graft_entry__ as g
+    import paper_2606_13482_gb300 as G
+    import efie_inputs as E
+    g.build()
+    k = 2 * np.pi
+    meshes = batch_meshes()
+    hs, t0 = [], time.time()
+    for V, T in meshes:
+        info, _ = G.plan(V, T, k, 3, 0.1, 1)
+        levels = max(1, min(3, info["depth"] - 1))
+        hs.append(G.EFIE(V, T, k, 3, 0.1, levels, precision=G.EFIE_MIXED))
+    t_setup = time.time() - t0
+    big = int(np.argmax([h.N for h in hs]))
+    xs = []
+    for i, h in enumerate(hs):
+        kh, pol = E.azimuth_planewaves(360 if i == big else 1, 1.0)
+        xs.append(h.rhs_planewave(kh, pol))
+    for i, h in enumerate(hs):
+        h.autotune(min(8, xs[i].shape[0]))
+    ys = [torch.empty_like(x) for x in xs]
+    b = G.Batch(hs)
+    for _ in range(args.warmup):
+        b.matvec(xs, ys)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        b.matvec(xs, ys)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    # the same products launched one handle at a time, for comparison
+    e0.record(stream)
+    for _ in range(args.steps):
+        for h, x, y in zip(hs, xs, ys):
+            h.matvec(x, y)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_seq = e0.elapsed_time(e1) / args.steps
+    nv = sum(x.shape[0] for x in xs)
+    b.close()
+    for h in hs:
+        h.close()
+    return {"metric": "batched fast-EFIE matvecs/s (10 ellipsoids, 369 right-hand sides, one graph launch)",
+            "value": nv / (ms / 1000.0), "unit": "matvecs/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c64 far / c128 near", "data": "synthetic (seeded ellipsoids, plane waves)",
+            "config": {"workload": "batch10", "rwg_unknowns": [int(1.5 * T.shape[0]) for _, T in meshes],
+                       "nrhs": [int(x.shape[0]) for x in xs], "setup_s": t_setup},
+            "sequential_ms_per_step": ms_seq, "graph_speedup": ms_seq / ms}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="sphere20", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="sphere20", choices=sorted(WORKLOADS) + ["batch10"])
     ap.add_argument("--nrhs", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -540,6 +620,10 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.workload == "batch10":
+        if args.impl == "ours" and rank == 0:
+            print(json.dumps(run_batch(args)), flush=True)
+        return
     w = WORKLOADS[args.workload]
     if args.cpu_worker:
         print(json.dumps(oracle_sampled_matvec_time(w, args.sample_seed)), flush=True)

@@ -29,7 +29,8 @@ EXPORTED_SYMBOLS = [
     "efie_rwg_edges", "efie_rhs_planewave", "efie_rhs_planewave_noalloc", "efie_matvec", "efie_matvec_fp64",
     "efie_matvec_parts", "efie_solve", "efie_precond_harvest", "efie_precond_train", "efie_precond_save",
     "efie_precond_load", "efie_precond_enable", "efie_precond_params", "efie_precond_apply",
-    "efie_precond_gradient", "efie_autotune", "efie_batch_create", "efie_batch_matvec", "efie_batch_destroy",
+    "efie_precond_gradient", "efie_autotune", "efie_autotune_set", "efie_batch_create", "efie_batch_matvec",
+    "efie_batch_destroy",
     "efie_profile", "efie_profile_read", "efie_launch_count",
     "efie_destroy", "efie_last_error",
 ]
@@ -112,7 +113,8 @@ def load_library(path: str = LIB_PATH):
     lib.efie_precond_params.argtypes = [VP, P(F), P(F), ctypes.c_int]
     lib.efie_precond_apply.argtypes = [VP, VP, VP, ctypes.c_int, VP]
     lib.efie_precond_gradient.argtypes = [VP, VP, VP, P(F), P(D), VP]
-    lib.efie_autotune.argtypes = [VP, ctypes.c_int, VP, P(ctypes.c_int), P(ctypes.c_int)]
+    lib.efie_autotune.argtypes = [VP, ctypes.c_int, VP, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int)]
+    lib.efie_autotune_set.argtypes = [VP, ctypes.c_int, ctypes.c_int, ctypes.c_int]
     lib.efie_batch_create.argtypes = [P(VP), ctypes.c_int, P(VP)]
     lib.efie_batch_matvec.argtypes = [VP, P(VP), P(VP), P(ctypes.c_int), VP]
     lib.efie_batch_destroy.argtypes = [VP]
@@ -355,10 +357,14 @@ class EFIE:
         return g, loss.value
 
     def autotune(self, n_rhs):
-        c, m = ctypes.c_int(), ctypes.c_int()
-        _check(self.lib, self.lib.efie_autotune(self.h, n_rhs, self._stream(), ctypes.byref(c), ctypes.byref(m)),
-               self.h)
-        return c.value, m.value
+        """Returns (rhs_chunk, mac_variant, near_variant) chosen for this handle."""
+        c, m, n = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(self.lib, self.lib.efie_autotune(self.h, n_rhs, self._stream(), ctypes.byref(c), ctypes.byref(m),
+                                                ctypes.byref(n)), self.h)
+        return c.value, m.value, n.value
+
+    def autotune_set(self, rhs_chunk: int, mac_variant: int, near_variant: int = 0):
+        _check(self.lib, self.lib.efie_autotune_set(self.h, rhs_chunk, mac_variant, near_variant), self.h)
 
     def profile(self, enable: bool):
         _check(self.lib, self.lib.efie_profile(self.h, 1 if enable else 0), self.h)

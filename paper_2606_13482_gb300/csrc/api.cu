@@ -115,6 +115,15 @@ struct LevDev {
   int max_tile = 0;
   int64_t *tile_tgt_ptr = nullptr, *tile_src_ptr = nullptr, *tile_kidx_off = nullptr;
   int32_t *tile_tgt = nullptr, *tile_src = nullptr, *tile_kidx = nullptr;
+  // sibling-shared transfers between this (child) level and its parents:
+  // g1 = (parent, b_x, b_y) groups of children, g2 = (parent, b_x) groups
+  int64_t ng1 = 0, ng2 = 0;
+  int64_t *uz_s0 = nullptr, *uz_s1 = nullptr, *uy_s0 = nullptr, *uy_s1 = nullptr, *ux_s0 = nullptr,
+          *ux_s1 = nullptr;
+  int8_t *uz_b0 = nullptr, *uz_b1 = nullptr, *uy_b0 = nullptr, *uy_b1 = nullptr, *ux_b0 = nullptr,
+         *ux_b1 = nullptr;
+  int64_t *dx_src = nullptr, *dy_src = nullptr, *dz_src = nullptr;  // downward: g2 -> parent, g1 -> g2, child -> g1
+  int8_t *dx_sel = nullptr, *dy_sel = nullptr;                      // [G][3]
 };
 
 std::complex<double> jk_of(double k) { return std::complex<double>(0.0, k); }
@@ -187,7 +196,8 @@ struct efie_handle {
   std::vector<LevDev> lev;
   FarSet<double> f64;
   FarSet<float> f32;
-  int mac_variant = 0;   // 0 auto, 1 register tiles only (autotuner knob)
+  int mac_variant = 0;   // 0 auto (shared-memory staged), 1 register tiles (autotuner knob)
+  int near_variant = 0;  // mixed near field: 0 shared-memory staged x, 1 x through L1 (autotuner knob)
   // work vectors (FP64, sorted) and their double-float splits
   int Rw = 0;
   double2 *xs = nullptr, *rho = nullptr, *yA = nullptr, *w = nullptr;
@@ -262,7 +272,17 @@ void build_far(efie_handle* h, FarSet<R>& F, cudaStream_t s) {
   Plan& P = h->plan;
   DevMem& M = h->mem;
   // moments
-  std::vector<R> mr(P.mom_rwg.data.begin(), P.mom_rwg.data.end());
+  // RWG moments interleaved by entry on the device: [e][3] per basis function
+  std::vector<R> mr(P.mom_rwg.data.size());
+  {
+    const MomentBlocks& MB = P.mom_rwg;
+    const int64_t n = (int64_t)MB.off.size() - 1;
+    for (int64_t i = 0; i < n; ++i) {
+      const int64_t o = MB.off[i], ne = (MB.off[i + 1] - o) / 3;
+      for (int64_t e = 0; e < ne; ++e)
+        for (int d = 0; d < 3; ++d) mr[o + 3 * e + d] = (R)MB.data[o + d * ne + e];
+    }
+  }
   std::vector<R> mt(P.mom_tri.data.begin(), P.mom_tri.data.end());
   F.mr = M.upload(mr);
   F.mt = M.upload(mt);
@@ -437,27 +457,25 @@ void far_chunk(efie_handle* h, FarSet<R>& F, int nr, cudaStream_t s) {
     launch_anterp<R>(F.gr, F.gt, h->gptr_r, h->gptr_t, h->mr_off, h->mt_off, h->d_box_rwg_ptr,
                      h->d_box_tri_ptr, (int64_t)L.code.size(), xin, N, rin, Nt, nr, F.q[D - top], L.sp, s);
   }
-  // a3: upward transfers
+  // a3: upward transfers, shared among siblings one axis at a time (z, y, x)
   for (int ell = D; ell > top; --ell) {
-    KScope ks(h, K_UP, s, 4);
+    KScope ks(h, K_UP, s, 3);
     const Level& L = P.L(ell);
     const Level& U = P.L(ell - 1);
     const LevDev& LD = h->lev[ell - top];
     auto& FL = F.lv[ell - top];
-    int64_t B = (int64_t)L.code.size();
-    int sp = L.sp, spp = U.sp;
+    const int64_t Bp = (int64_t)U.code.size();
+    const int sp = L.sp, spp = U.sp;
     View vq{(int64_t)sp * sp * sp * C, (int64_t)sp * sp * C, (int64_t)sp * C, C};
-    View v1{(int64_t)spp * sp * sp * C, (int64_t)sp * sp * C, (int64_t)sp * C, C};
-    View v2{(int64_t)spp * spp * sp * C, (int64_t)spp * sp * C, (int64_t)sp * C, C};
-    View v3{(int64_t)spp * spp * spp * C, (int64_t)spp * spp * C, (int64_t)spp * C, C};
-    launch_mode<R>(F.q[ell - top], vq, F.tmp1, v1, B, C, 0, sp, spp, sp, sp, FL.CL, FL.CR, false, LD.bits,
-                   nullptr, false, s);
-    launch_mode<R>(F.tmp1, v1, F.tmp2, v2, B, C, 1, sp, spp, spp, sp, FL.CL, FL.CR, false, LD.bits, nullptr,
-                   false, s);
-    launch_mode<R>(F.tmp2, v2, F.tmp1, v3, B, C, 2, sp, spp, spp, spp, FL.CL, FL.CR, false, LD.bits,
-                   nullptr, false, s);
-    launch_reduce_children<R>(F.tmp1, F.q[ell - 1 - top], h->lev[ell - 1 - top].child_ptr,
-                              (int64_t)U.code.size(), (int64_t)spp * spp * spp * C, s);
+    View t1{(int64_t)sp * sp * spp * C, (int64_t)sp * spp * C, (int64_t)spp * C, C};
+    View t2{(int64_t)sp * spp * spp * C, (int64_t)spp * spp * C, (int64_t)spp * C, C};
+    View vp{(int64_t)spp * spp * spp * C, (int64_t)spp * spp * C, (int64_t)spp * C, C};
+    launch_mode_pair<R>(F.q[ell - top], vq, F.tmp1, t1, LD.ng1, C, 2, sp, sp, sp, spp, FL.CL, FL.CR, LD.uz_s0,
+                        LD.uz_s1, LD.uz_b0, LD.uz_b1, s);
+    launch_mode_pair<R>(F.tmp1, t1, F.tmp2, t2, LD.ng2, C, 1, sp, sp, spp, spp, FL.CL, FL.CR, LD.uy_s0,
+                        LD.uy_s1, LD.uy_b0, LD.uy_b1, s);
+    launch_mode_pair<R>(F.tmp2, t2, F.q[ell - 1 - top], vp, Bp, C, 0, sp, spp, spp, spp, FL.CL, FL.CR, LD.ux_s0,
+                        LD.ux_s1, LD.ux_b0, LD.ux_b1, s);
   }
   // a4-a7: stabilized FFT translations per level
   for (int ell = D; ell >= top; --ell) {
@@ -477,12 +495,15 @@ void far_chunk(efie_handle* h, FarSet<R>& F, int nr, cudaStream_t s) {
     View vf{C, (int64_t)n * n * B * C, (int64_t)n * B * C, B * C};
     {
       KScope ks(h, K_FWD, s, 3);
-      launch_mode<R>(F.q[ell - top], vq, F.tmp1, a1, B, C, 0, sp, n, sp, sp, FL.Mf, FL.Mf, true, nullptr,
-                     nullptr, false, s);
-      launch_mode<R>(F.tmp1, a1, F.tmp2, a2, B, C, 1, sp, n, n, sp, FL.Mf, FL.Mf, true, nullptr, nullptr,
-                     false, s);
-      launch_mode<R>(F.tmp2, a2, F.Qh, vf, B, C, 2, sp, n, n, n, FL.Mf, FL.Mf, true, nullptr, nullptr, false,
-                     s);
+      if (!launch_dft<R>(F.q[ell - top], vq, F.tmp1, a1, B, C, 0, sp, n, sp, sp, FL.Mf, n, false, s))
+        launch_mode<R>(F.q[ell - top], vq, F.tmp1, a1, B, C, 0, sp, n, sp, sp, FL.Mf, FL.Mf, true, nullptr,
+                       nullptr, false, s);
+      if (!launch_dft<R>(F.tmp1, a1, F.tmp2, a2, B, C, 1, sp, n, n, sp, FL.Mf, n, false, s))
+        launch_mode<R>(F.tmp1, a1, F.tmp2, a2, B, C, 1, sp, n, n, sp, FL.Mf, FL.Mf, true, nullptr, nullptr,
+                       false, s);
+      if (!launch_dft<R>(F.tmp2, a2, F.Qh, vf, B, C, 2, sp, n, n, n, FL.Mf, n, false, s))
+        launch_mode<R>(F.tmp2, a2, F.Qh, vf, B, C, 2, sp, n, n, n, FL.Mf, FL.Mf, true, nullptr, nullptr, false,
+                       s);
     }
     {
       KScope ks(h, ell == top ? K_MAC_TOP : K_MAC, s, 1);
@@ -492,14 +513,18 @@ void far_chunk(efie_handle* h, FarSet<R>& F, int nr, cudaStream_t s) {
     KScope ks(h, K_INV, s, 3);
     View b1{(int64_t)sp * n * n * C, (int64_t)n * n * C, (int64_t)n * C, C};
     View b2{(int64_t)sp * sp * n * C, (int64_t)sp * n * C, (int64_t)n * C, C};
-    launch_mode<R>(F.Rh, vf, F.tmp1, b1, B, C, 0, n, sp, n, n, FL.Mb, FL.Mb, true, nullptr, nullptr, false,
-                   s);
-    launch_mode<R>(F.tmp1, b1, F.tmp2, b2, B, C, 1, n, sp, sp, n, FL.Mb, FL.Mb, true, nullptr, nullptr,
-                   false, s);
-    launch_mode<R>(F.tmp2, b2, F.r[ell - top], vq, B, C, 2, n, sp, sp, sp, FL.Mb, FL.Mb, true, nullptr,
-                   nullptr, false, s);
+    if (!launch_dft<R>(F.Rh, vf, F.tmp1, b1, B, C, 0, n, sp, n, n, FL.Mb, n, true, s))
+      launch_mode<R>(F.Rh, vf, F.tmp1, b1, B, C, 0, n, sp, n, n, FL.Mb, FL.Mb, true, nullptr, nullptr, false,
+                     s);
+    if (!launch_dft<R>(F.tmp1, b1, F.tmp2, b2, B, C, 1, n, sp, sp, n, FL.Mb, n, true, s))
+      launch_mode<R>(F.tmp1, b1, F.tmp2, b2, B, C, 1, n, sp, sp, n, FL.Mb, FL.Mb, true, nullptr, nullptr,
+                     false, s);
+    if (!launch_dft<R>(F.tmp2, b2, F.r[ell - top], vq, B, C, 2, n, sp, sp, sp, FL.Mb, n, true, s))
+      launch_mode<R>(F.tmp2, b2, F.r[ell - top], vq, B, C, 2, n, sp, sp, sp, FL.Mb, FL.Mb, true, nullptr,
+                     nullptr, false, s);
   }
-  // a8: downward transfers r_c += C^T r_parent
+  // a8: downward transfers r_c += C^T r_parent, shared among siblings one
+  // axis at a time (x for (parent, b_x), y for (parent, b_x, b_y), z per child)
   for (int ell = top + 1; ell <= D; ++ell) {
     KScope ks(h, K_DOWN, s, 3);
     const Level& L = P.L(ell);
@@ -512,12 +537,12 @@ void far_chunk(efie_handle* h, FarSet<R>& F, int nr, cudaStream_t s) {
     View w1{(int64_t)sp * spp * spp * C, (int64_t)spp * spp * C, (int64_t)spp * C, C};
     View w2{(int64_t)sp * sp * spp * C, (int64_t)sp * spp * C, (int64_t)spp * C, C};
     View vq{(int64_t)sp * sp * sp * C, (int64_t)sp * sp * C, (int64_t)sp * C, C};
-    launch_mode<R>(F.r[ell - 1 - top], vp, F.tmp1, w1, B, C, 0, spp, sp, spp, spp, FL.CLt, FL.CRt, false,
-                   LD.bits, LD.parent, false, s);
-    launch_mode<R>(F.tmp1, w1, F.tmp2, w2, B, C, 1, spp, sp, sp, spp, FL.CLt, FL.CRt, false, LD.bits,
-                   nullptr, false, s);
+    launch_mode<R>(F.r[ell - 1 - top], vp, F.tmp1, w1, LD.ng2, C, 0, spp, sp, spp, spp, FL.CLt, FL.CRt, false,
+                   LD.dx_sel, LD.dx_src, false, s);
+    launch_mode<R>(F.tmp1, w1, F.tmp2, w2, LD.ng1, C, 1, spp, sp, sp, spp, FL.CLt, FL.CRt, false, LD.dy_sel,
+                   LD.dy_src, false, s);
     launch_mode<R>(F.tmp2, w2, F.r[ell - top], vq, B, C, 2, spp, sp, sp, sp, FL.CLt, FL.CRt, false, LD.bits,
-                   nullptr, true, s);
+                   LD.dz_src, true, s);
   }
   // a9: interpolation
   {
@@ -549,13 +574,13 @@ void matvec_chunk(efie_handle* h, FarSet<R>& F, const double2* x, int64_t ldx, i
       KScope ks(h, K_NEAR_A, s, 2);
       launch_split_vec(h->xs, h->xs4, N * nr, s);
       launch_near_spmv_df((const float4*)h->nd.A, h->d_blkA_off, h->d_near_ptr, h->d_near_src, h->d_box_rwg_ptr,
-                          BD, h->xs4, h->yA, N, nr, s);
+                          BD, h->xs4, h->yA, N, nr, h->near_variant, s);
     }
     {
       KScope ks(h, K_NEAR_V, s, 2);
       launch_split_vec(h->rho, h->rho4, Nt * nr, s);
       launch_near_spmv_df((const float4*)h->nd.Vn, h->d_blkV_off, h->d_near_ptr, h->d_near_src,
-                          h->d_box_tri_ptr, BD, h->rho4, h->w, Nt, nr, s);
+                          h->d_box_tri_ptr, BD, h->rho4, h->w, Nt, nr, h->near_variant, s);
     }
   } else {
     {
@@ -671,6 +696,85 @@ void setup_impl(efie_handle* h, const efie_mesh* mesh, double k, int p, double g
       for (int d = 0; d < 3; ++d) bits[3 * b + d] = (int8_t)(L.ijk[3 * b + d] & 1);
     LD.bits = M.upload(bits);
     if (ell < P.D) LD.child_ptr = M.upload(L.child_ptr);
+    if (ell > P.top) {
+      const Level& U = P.L(ell - 1);
+      const int64_t Bp = (int64_t)U.code.size();
+      std::vector<int64_t> z0, z1, y0, y1, x0(Bp, -1), x1(Bp, -1), dxs, dys, dzs(LD.B, -1);
+      std::vector<int8_t> zb0, zb1, yb0, yb1, xb0(Bp, 0), xb1(Bp, 0), dxsel, dysel;
+      for (int64_t pb = 0; pb < Bp; ++pb) {
+        int64_t g1id[2][2] = {{-1, -1}, {-1, -1}}, g2id[2] = {-1, -1};
+        for (int64_t c = U.child_ptr[pb]; c < U.child_ptr[pb + 1]; ++c) {
+          const int bx = (int)(L.ijk[3 * c] & 1), by = (int)(L.ijk[3 * c + 1] & 1), bz = (int)(L.ijk[3 * c + 2] & 1);
+          int64_t& g = g1id[bx][by];
+          if (g < 0) {
+            g = (int64_t)z0.size();
+            z0.push_back(c);
+            zb0.push_back((int8_t)bz);
+            z1.push_back(-1);
+            zb1.push_back(0);
+          } else {
+            if (z1[g] >= 0) throw EfieError{EFIE_EINVAL, "internal: more than two children share (bx, by)"};
+            z1[g] = c;
+            zb1[g] = (int8_t)bz;
+          }
+          dzs[c] = g;
+        }
+        for (int bx = 0; bx < 2; ++bx)
+          for (int by = 0; by < 2; ++by) {
+            const int64_t g = g1id[bx][by];
+            if (g < 0) continue;
+            int64_t& h2 = g2id[bx];
+            if (h2 < 0) {
+              h2 = (int64_t)y0.size();
+              y0.push_back(g);
+              yb0.push_back((int8_t)by);
+              y1.push_back(-1);
+              yb1.push_back(0);
+              dxs.push_back(pb);
+              dxsel.insert(dxsel.end(), {(int8_t)bx, 0, 0});
+            } else {
+              y1[h2] = g;
+              yb1[h2] = (int8_t)by;
+            }
+            if ((int64_t)dys.size() <= g) {
+              dys.resize(g + 1, -1);
+              dysel.resize(3 * (g + 1), 0);
+            }
+            dys[g] = h2;
+            dysel[3 * g + 1] = (int8_t)by;
+          }
+        for (int bx = 0; bx < 2; ++bx) {
+          if (g2id[bx] < 0) continue;
+          if (x0[pb] < 0) {
+            x0[pb] = g2id[bx];
+            xb0[pb] = (int8_t)bx;
+          } else {
+            x1[pb] = g2id[bx];
+            xb1[pb] = (int8_t)bx;
+          }
+        }
+        if (x0[pb] < 0) throw EfieError{EFIE_EINVAL, "internal: parent box without children"};
+      }
+      LD.ng1 = (int64_t)z0.size();
+      LD.ng2 = (int64_t)y0.size();
+      LD.uz_s0 = M.upload(z0);
+      LD.uz_s1 = M.upload(z1);
+      LD.uz_b0 = M.upload(zb0);
+      LD.uz_b1 = M.upload(zb1);
+      LD.uy_s0 = M.upload(y0);
+      LD.uy_s1 = M.upload(y1);
+      LD.uy_b0 = M.upload(yb0);
+      LD.uy_b1 = M.upload(yb1);
+      LD.ux_s0 = M.upload(x0);
+      LD.ux_s1 = M.upload(x1);
+      LD.ux_b0 = M.upload(xb0);
+      LD.ux_b1 = M.upload(xb1);
+      LD.dx_src = M.upload(dxs);
+      LD.dx_sel = M.upload(dxsel);
+      LD.dy_src = M.upload(dys);
+      LD.dy_sel = M.upload(dysel);
+      LD.dz_src = M.upload(dzs);
+    }
     LD.ntiles = (int64_t)L.tile_tgt_ptr.size() - 1;
     for (int64_t t = 0; t < LD.ntiles; ++t)
       LD.max_tile = std::max<int>(LD.max_tile, (int)(L.tile_tgt_ptr[t + 1] - L.tile_tgt_ptr[t]));
@@ -1526,7 +1630,17 @@ int efie_precond_gradient(efie_handle* h, const void* r, const void* e, float* g
   });
 }
 
-int efie_autotune(efie_handle* h, int n_rhs, void* stream, int* best_chunk, int* best_mac) {
+int efie_autotune_set(efie_handle* h, int rhs_chunk, int mac_variant, int near_variant) {
+  if (!h || rhs_chunk < 1 || rhs_chunk > 8 || mac_variant < 0 || mac_variant > 1 || near_variant < 0 ||
+      near_variant > 1)
+    return EFIE_EINVAL;
+  h->opt.rhs_chunk = rhs_chunk;
+  h->mac_variant = mac_variant;
+  h->near_variant = near_variant;
+  return EFIE_OK;
+}
+
+int efie_autotune(efie_handle* h, int n_rhs, void* stream, int* best_chunk, int* best_mac, int* best_near) {
   if (!h) return EFIE_EINVAL;
   return guarded(h, [&] {
     if (n_rhs <= 0) throw EfieError{EFIE_EINVAL, "n_rhs must be positive"};
@@ -1541,12 +1655,15 @@ int efie_autotune(efie_handle* h, int n_rhs, void* stream, int* best_chunk, int*
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     float best = 1e30f;
-    int bc = 8, bm = 0;
+    int bc = 8, bm = 0, bn = 0;
     for (int chunk : {8, 4, 2, 1}) {
       if (chunk > n_rhs && chunk != 1) continue;
-      for (int mv : {0, 1}) {
+      for (int cand = 0; cand < 4; ++cand) {
+        const int mv = cand & 1, nv = cand >> 1;
+        if (nv == 1 && !h->near_df) continue;  // the near variants differ in the mixed form only
         h->opt.rhs_chunk = chunk;
         h->mac_variant = mv;
+        h->near_variant = nv;
         do_matvec(h, x, N, y, nullptr, nullptr, N, n_rhs, false, s);  // warm-up / allocation
         cudaEventRecord(e0, s);
         do_matvec(h, x, N, y, nullptr, nullptr, N, n_rhs, false, s);
@@ -1558,11 +1675,13 @@ int efie_autotune(efie_handle* h, int n_rhs, void* stream, int* best_chunk, int*
           best = ms;
           bc = chunk;
           bm = mv;
+          bn = nv;
         }
       }
     }
     h->opt.rhs_chunk = bc;
     h->mac_variant = bm;
+    h->near_variant = bn;
     h->prof.on = prof;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -1570,6 +1689,7 @@ int efie_autotune(efie_handle* h, int n_rhs, void* stream, int* best_chunk, int*
     h->mem.release(y);
     if (best_chunk) *best_chunk = bc;
     if (best_mac) *best_mac = bm;
+    if (best_near) *best_near = bn;
     return EFIE_OK;
   });
 }

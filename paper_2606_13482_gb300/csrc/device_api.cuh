@@ -49,7 +49,7 @@ void launch_split_df(double2* a, int64_t n, cudaStream_t s);
 void launch_split_vec(const double2* x, float4* y, int64_t n, cudaStream_t s);
 void launch_near_spmv_df(const float4* M, const int64_t* blk_off, const int64_t* near_ptr,
                          const int32_t* near_src, const int64_t* box_ptr, int64_t n_boxes, const float4* x,
-                         double2* y, int64_t ld, int nr, cudaStream_t s);
+                         double2* y, int64_t ld, int nr, int variant, cudaStream_t s);
 
 // Strided tensor view of a box-batched 3D grid with channels innermost:
 // element (b, i0, i1, i2, c) at b*sb + i0*s0 + i1*s1 + i2*s2 + c.
@@ -61,6 +61,42 @@ template <typename R>
 void launch_mode(const cpx_t<R>* in, View vin, cpx_t<R>* out, View vout, int64_t B, int C, int ax,
                  int nin, int e0, int e1, int e2, const void* M0, const void* M1, bool complex_m,
                  const int8_t* sel, const int64_t* srcmap, bool accumulate, cudaStream_t s);
+
+// one pass of the sibling-shared upward transfer: out[g] = M(bit0) in[src0] +
+// M(bit1) in[src1] along axis ax (src1 < 0: absent), M(0) = M0, M(1) = M1
+template <typename R>
+void launch_mode_pair(const cpx_t<R>* in, View vin, cpx_t<R>* out, View vout, int64_t G, int C, int ax, int nin,
+                      int e0, int e1, int e2, const R* M0, const R* M1, const int64_t* src0, const int64_t* src1,
+                      const int8_t* bit0, const int8_t* bit1, cudaStream_t s);
+
+// DFT passes of the stabilized transforms using the conjugate symmetry of
+// M = F P (forward, n x nin) / P^T F^{-1} (inverse, nout x n); false when no
+// specialisation fits
+template <typename R>
+bool launch_dft(const cpx_t<R>* in, View vin, cpx_t<R>* out, View vout, int64_t B, int C, int ax, int nin,
+                int e0, int e1, int e2, const cpx_t<R>* M, int n, bool inverse, cudaStream_t s);
+
+// one pass of the sibling-shared upward transfer: out[g] = M(bit0) in[src0] +
+// M(bit1) in[src1] along axis ax (src1 < 0: absent), M(0) = M0, M(1) = M1
+template <typename R>
+void launch_mode_pair(const cpx_t<R>* in, View vin, cpx_t<R>* out, View vout, int64_t G, int C, int ax, int nin,
+                      int e0, int e1, int e2, const R* M0, const R* M1, const int64_t* src0, const int64_t* src1,
+                      const int8_t* bit0, const int8_t* bit1, cudaStream_t s);
+
+// DFT passes of the stabilized transforms using the conjugate symmetry of
+// M = F P (forward, n x nin) / P^T F^{-1} (inverse, nout x n); false when no
+// specialisation fits
+template <typename R>
+bool launch_dft(const cpx_t<R>* in, View vin, cpx_t<R>* out, View vout, int64_t B, int C, int ax, int nin,
+                int e0, int e1, int e2, const cpx_t<R>* M, int n, bool inverse, cudaStream_t s);
+
+// top grid level: kernel spectra as a dense cube over box offsets (FP32)
+void launch_scatter_cube(const double2* K64, const int32_t* offsets, int64_t O, int64_t n3, int Dm, float2* Kd,
+                         cudaStream_t s);
+bool launch_mac_top_cube(const float2* Qh, float2* Rh, const float2* Kd, int64_t B, int C, int Dm, int64_t nf,
+                         int64_t ntiles, int max_tile_targets, int64_t max_tile_sources, const int64_t* tgt_ptr,
+                         const int32_t* tgt, const int64_t* src_ptr, const int32_t* src, const int4* ijk,
+                         cudaStream_t s);
 
 template <typename R>
 void launch_gather_build(const R* mr, const int32_t* mr_base, const int32_t* mr_ext, const int64_t* mr_off,
@@ -87,9 +123,6 @@ void launch_mac(const cpx_t<R>* Qh, cpx_t<R>* Rh, const cpx_t<R>* Kh, int64_t B,
                 const int64_t* src_ptr, const int32_t* src, const int64_t* kidx_off, const int32_t* kidx,
                 cudaStream_t s);
 
-template <typename R>
-void launch_reduce_children(const cpx_t<R>* tmp, cpx_t<R>* q_parent, const int64_t* child_ptr,
-                            int64_t Bp, int64_t per_box, cudaStream_t s);
 
 void launch_kernel_samples(double2* Kc, const int32_t* offsets, int64_t o0, int64_t no, int n,
                            int shat, double h, double Delta, double k, cudaStream_t s);

@@ -21,6 +21,8 @@
 
 #include "common.cuh"
 #include "device_api.cuh"
+#include "plan.hpp"
+#include "../../include/efie.h"
 
 namespace efie {
 
@@ -195,6 +197,380 @@ static bool dispatch_mode_line(const cpx_t<R>* in, View vin, cpx_t<R>* out, View
   return false;
 }
 
+// ---------------------------------------------------------------- sibling-shared transfers
+// Upward transfer as a tree over the children of each parent: the product
+// q_P = sum_c (C_x(c) (x) C_y(c) (x) C_z(c)) q_c is taken one axis at a time,
+// summing after each axis the (at most two) partial results that will see the
+// same matrices on the remaining axes -- z for children sharing (b_x, b_y),
+// then y for groups sharing b_x, then x.  Each output unit g of a pass is
+// out[g] = M(bit0[g]) in[src0[g]] + M(bit1[g]) in[src1[g]] (src1 < 0: absent),
+// M(0) = C^L, M(1) = C^R, real, applied along axis ax.  The intermediates are
+// about a quarter of those of transferring every child separately.
+template <typename R, int NMAX, int LPT>
+__global__ void k_mode_pair(const cpx_t<R>* __restrict__ in, View vin, cpx_t<R>* __restrict__ out, View vout,
+                            int64_t G, int C, int ax, int nin, int e0, int e1, int e2, const R* __restrict__ M0,
+                            const R* __restrict__ M1, const int64_t* __restrict__ src0,
+                            const int64_t* __restrict__ src1, const int8_t* __restrict__ bit0,
+                            const int8_t* __restrict__ bit1) {
+  using T = cpx_t<R>;
+  extern __shared__ unsigned char smem_raw[];
+  const int nout = ax == 0 ? e0 : (ax == 1 ? e1 : e2);
+  const int msz = nout * nin;
+  R* Ms = reinterpret_cast<R*>(smem_raw);  // [2][nout][nin]
+  for (int i = threadIdx.x; i < msz; i += blockDim.x) {
+    Ms[i] = M0[i];
+    Ms[msz + i] = M1[i];
+  }
+  __syncthreads();
+  const int ea = ax == 0 ? e1 : e0, eb = ax == 2 ? e1 : e2;
+  const int64_t sa_in = ax == 0 ? vin.s1 : vin.s0, sb_in = ax == 2 ? vin.s1 : vin.s2;
+  const int64_t sa_out = ax == 0 ? vout.s1 : vout.s0, sb_out = ax == 2 ? vout.s1 : vout.s2;
+  const int64_t step_in = ax == 0 ? vin.s0 : (ax == 1 ? vin.s1 : vin.s2);
+  const int64_t step_out = ax == 0 ? vout.s0 : (ax == 1 ? vout.s1 : vout.s2);
+  const int CL = C / LPT;
+  const int64_t lines = G * ea * eb * (int64_t)CL;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < lines;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    int64_t t = idx;
+    const int c = (int)(t % CL) * LPT;
+    t /= CL;
+    const int ib = (int)(t % eb);
+    t /= eb;
+    const int ia = (int)(t % ea);
+    const int64_t g = t / ea;
+    const int64_t g0 = src0[g], g1 = src1[g];
+    const T* ip0 = in + g0 * vin.sb + ia * sa_in + ib * sb_in + c;
+    const T* ip1 = in + (g1 >= 0 ? g1 : g0) * vin.sb + ia * sa_in + ib * sb_in + c;
+    T v0[NMAX][LPT], v1[NMAX][LPT];
+#pragma unroll
+    for (int i = 0; i < NMAX; ++i)
+      if (i < nin)
+#pragma unroll
+        for (int l = 0; l < LPT; ++l) {
+          v0[i][l] = ip0[i * step_in + l];
+          v1[i][l] = g1 >= 0 ? ip1[i * step_in + l] : mk<R>(0, 0);
+        }
+    const R* Ma = Ms + (bit0[g] ? msz : 0);
+    const R* Mb = Ms + (g1 >= 0 && bit1[g] ? msz : 0);
+    T* op = out + g * vout.sb + ia * sa_out + ib * sb_out + c;
+    for (int j = 0; j < nout; ++j) {
+      T acc[LPT];
+#pragma unroll
+      for (int l = 0; l < LPT; ++l) acc[l] = mk<R>(0, 0);
+#pragma unroll
+      for (int i = 0; i < NMAX; ++i)
+        if (i < nin) {
+          const R ma = Ma[j * nin + i], mb = Mb[j * nin + i];
+#pragma unroll
+          for (int l = 0; l < LPT; ++l) {
+            acc[l].x = fma(ma, v0[i][l].x, acc[l].x);
+            acc[l].y = fma(ma, v0[i][l].y, acc[l].y);
+            acc[l].x = fma(mb, v1[i][l].x, acc[l].x);
+            acc[l].y = fma(mb, v1[i][l].y, acc[l].y);
+          }
+        }
+#pragma unroll
+      for (int l = 0; l < LPT; ++l) op[j * step_out + l] = acc[l];
+    }
+  }
+}
+
+template <typename R>
+void launch_mode_pair(const cpx_t<R>* in, View vin, cpx_t<R>* out, View vout, int64_t G, int C, int ax, int nin,
+                      int e0, int e1, int e2, const R* M0, const R* M1, const int64_t* src0, const int64_t* src1,
+                      const int8_t* bit0, const int8_t* bit1, cudaStream_t s) {
+  const int ea = ax == 0 ? e1 : e0, eb = ax == 2 ? e1 : e2;
+  const int nout = ax == 0 ? e0 : (ax == 1 ? e1 : e2);
+  if (G <= 0) return;
+  const size_t smem = 2 * sizeof(R) * (size_t)nout * nin;
+  const bool two = (C % 2) == 0 && sizeof(R) == 4;
+  const int lpt = two ? 2 : 1;
+  const int64_t lines = G * ea * eb * (int64_t)(C / lpt);
+  int64_t blocks = ceil_div(lines, 128);
+  if (blocks > 152 * 32) blocks = 152 * 32;
+#define EFIE_MP(NM)                                                                                          \
+  if (nin <= NM) {                                                                                           \
+    if (two && NM <= 9) {                                                                                    \
+      auto k = k_mode_pair<R, NM, (sizeof(R) == 4 && NM <= 9) ? 2 : 1>;                                      \
+      k<<<(unsigned)blocks, 128, smem, s>>>(in, vin, out, vout, G, C, ax, nin, e0, e1, e2, M0, M1, src0,    \
+                                            src1, bit0, bit1);                                               \
+    } else {                                                                                                 \
+      const int64_t lines1 = G * ea * eb * (int64_t)C;                                                       \
+      int64_t blocks1 = ceil_div(lines1, 128);                                                               \
+      if (blocks1 > 152 * 32) blocks1 = 152 * 32;                                                            \
+      auto k = k_mode_pair<R, NM, 1>;                                                                        \
+      k<<<(unsigned)blocks1, 128, smem, s>>>(in, vin, out, vout, G, C, ax, nin, e0, e1, e2, M0, M1, src0,   \
+                                             src1, bit0, bit1);                                              \
+    }                                                                                                        \
+    return;                                                                                                  \
+  }
+  EFIE_MP(9)
+  EFIE_MP(13)
+  EFIE_MP(21)
+  EFIE_MP(40)
+#undef EFIE_MP
+  throw EfieError{EFIE_EINVAL, "transfer: more than 40 splines per axis below the top level"};
+}
+
+// ---------------------------------------------------------------- DFT passes
+// The transform passes apply M = F P (forward, n x s') or M = P^T F^{-1}
+// (inverse, s' x n) along one axis, F the n-point DFT and P real.  Because F's
+// rows f and n - f (columns, for F^{-1}) are complex conjugates and P is real,
+// M[n-f] = conj(M[f]) (forward) and M[:, n-f] = conj(M[:, f]) (inverse), so a
+// pair of outputs (inputs) shares one set of real products:
+//   forward: with M[f] = A + iB and four real sums S1 = sum A Re v,
+//            S2 = sum B Im v, S3 = sum A Im v, S4 = sum B Re v,
+//            y_f = (S1 - S2) + i (S3 + S4), y_{n-f} = (S1 + S2) + i (S3 - S4);
+//   inverse: M v_f + conj(M) v_{n-f} = A u + i B w with u = v_f + v_{n-f},
+//            w = v_f - v_{n-f}.
+// That is half the multiply-adds of the dense product, with only rows
+// (columns) 0 .. n/2 of M read.  Same line mapping as k_mode_line.
+template <typename R, int NMAX, int LPT>
+__global__ void k_dft_fwd_line(const cpx_t<R>* __restrict__ in, View vin, cpx_t<R>* __restrict__ out, View vout,
+                               int64_t B, int C, int ax, int nin, int e0, int e1, int e2,
+                               const cpx_t<R>* __restrict__ M, int n) {
+  using T = cpx_t<R>;
+  extern __shared__ unsigned char smem_raw[];
+  T* Ms = reinterpret_cast<T*>(smem_raw);  // rows 0 .. n/2 of M
+  const int nh = n / 2 + 1;
+  for (int i = threadIdx.x; i < nh * nin; i += blockDim.x) Ms[i] = M[i];
+  __syncthreads();
+  const int ea = ax == 0 ? e1 : e0, eb = ax == 2 ? e1 : e2;
+  const int64_t sa_in = ax == 0 ? vin.s1 : vin.s0, sb_in = ax == 2 ? vin.s1 : vin.s2;
+  const int64_t sa_out = ax == 0 ? vout.s1 : vout.s0, sb_out = ax == 2 ? vout.s1 : vout.s2;
+  const int64_t step_in = ax == 0 ? vin.s0 : (ax == 1 ? vin.s1 : vin.s2);
+  const int64_t step_out = ax == 0 ? vout.s0 : (ax == 1 ? vout.s1 : vout.s2);
+  const int CL = C / LPT;
+  const int64_t lines = B * ea * eb * (int64_t)CL;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < lines;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    int64_t t = idx;
+    const int c = (int)(t % CL) * LPT;
+    t /= CL;
+    const int ib = (int)(t % eb);
+    t /= eb;
+    const int ia = (int)(t % ea);
+    const int64_t b = t / ea;
+    const T* ip = in + b * vin.sb + ia * sa_in + ib * sb_in + c;
+    T v[NMAX][LPT];
+#pragma unroll
+    for (int i = 0; i < NMAX; ++i)
+      if (i < nin)
+#pragma unroll
+        for (int l = 0; l < LPT; ++l) v[i][l] = ip[i * step_in + l];
+    T* op = out + b * vout.sb + ia * sa_out + ib * sb_out + c;
+    for (int f = 0; f < nh; ++f) {
+      R s1[LPT], s2[LPT], s3[LPT], s4[LPT];
+#pragma unroll
+      for (int l = 0; l < LPT; ++l) s1[l] = s2[l] = s3[l] = s4[l] = (R)0;
+      const T* Mr = Ms + f * nin;
+#pragma unroll
+      for (int i = 0; i < NMAX; ++i)
+        if (i < nin) {
+          const T m = Mr[i];
+#pragma unroll
+          for (int l = 0; l < LPT; ++l) {
+            s1[l] = fma(m.x, v[i][l].x, s1[l]);
+            s2[l] = fma(m.y, v[i][l].y, s2[l]);
+            s3[l] = fma(m.x, v[i][l].y, s3[l]);
+            s4[l] = fma(m.y, v[i][l].x, s4[l]);
+          }
+        }
+      const bool pair = f != 0 && 2 * f != n;
+#pragma unroll
+      for (int l = 0; l < LPT; ++l) {
+        op[f * step_out + l] = mk<R>(s1[l] - s2[l], s3[l] + s4[l]);
+        if (pair) op[(n - f) * step_out + l] = mk<R>(s1[l] + s2[l], s3[l] - s4[l]);
+      }
+    }
+  }
+}
+
+// Inverse passes keep the nout (= s') outputs of a line in registers and
+// stream the conjugate input pairs (f, n - f) through them.
+template <typename R, int AMAX, int LPT>
+__global__ void k_dft_inv_line(const cpx_t<R>* __restrict__ in, View vin, cpx_t<R>* __restrict__ out, View vout,
+                               int64_t B, int C, int ax, int nin_unused, int e0, int e1, int e2,
+                               const cpx_t<R>* __restrict__ M, int n) {
+  using T = cpx_t<R>;
+  extern __shared__ unsigned char smem_raw[];
+  T* Ms = reinterpret_cast<T*>(smem_raw);  // [f][a], f = 0 .. n/2
+  const int nout = ax == 0 ? e0 : (ax == 1 ? e1 : e2);
+  const int nh = n / 2 + 1;
+  for (int i = threadIdx.x; i < nout * nh; i += blockDim.x) {
+    const int f = i / nout, a = i - f * nout;
+    Ms[i] = M[(int64_t)a * n + f];
+  }
+  __syncthreads();
+  const int ea = ax == 0 ? e1 : e0, eb = ax == 2 ? e1 : e2;
+  const int64_t sa_in = ax == 0 ? vin.s1 : vin.s0, sb_in = ax == 2 ? vin.s1 : vin.s2;
+  const int64_t sa_out = ax == 0 ? vout.s1 : vout.s0, sb_out = ax == 2 ? vout.s1 : vout.s2;
+  const int64_t step_in = ax == 0 ? vin.s0 : (ax == 1 ? vin.s1 : vin.s2);
+  const int64_t step_out = ax == 0 ? vout.s0 : (ax == 1 ? vout.s1 : vout.s2);
+  const int CL = C / LPT;
+  const int64_t lines = B * ea * eb * (int64_t)CL;
+  const int np = (n - 1) / 2;     // conjugate pairs (f, n - f), f = 1 .. np
+  const bool mid = (n % 2) == 0;  // f = n/2 pairs with itself
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < lines;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    int64_t t = idx;
+    const int c = (int)(t % CL) * LPT;
+    t /= CL;
+    const int ib = (int)(t % eb);
+    t /= eb;
+    const int ia = (int)(t % ea);
+    const int64_t b = t / ea;
+    const T* ip = in + b * vin.sb + ia * sa_in + ib * sb_in + c;
+    T acc[AMAX][LPT];
+    {
+      T v0[LPT];
+#pragma unroll
+      for (int l = 0; l < LPT; ++l) v0[l] = ip[l];
+#pragma unroll
+      for (int a = 0; a < AMAX; ++a)
+        if (a < nout) {
+          const T m = Ms[a];
+#pragma unroll
+          for (int l = 0; l < LPT; ++l) acc[a][l] = cmul(m, v0[l]);
+        }
+    }
+    T z1[LPT], z2[LPT];
+#pragma unroll
+    for (int l = 0; l < LPT; ++l) {
+      z1[l] = np > 0 ? ip[step_in + l] : mk<R>(0, 0);
+      z2[l] = np > 0 ? ip[(int64_t)(n - 1) * step_in + l] : mk<R>(0, 0);
+    }
+    for (int f = 1; f <= np; ++f) {
+      T u[LPT], w[LPT];
+#pragma unroll
+      for (int l = 0; l < LPT; ++l) {
+        u[l] = mk<R>(z1[l].x + z2[l].x, z1[l].y + z2[l].y);
+        w[l] = mk<R>(z1[l].x - z2[l].x, z1[l].y - z2[l].y);
+      }
+      if (f < np) {  // next pair's loads in flight during this pair's products
+#pragma unroll
+        for (int l = 0; l < LPT; ++l) {
+          z1[l] = ip[(int64_t)(f + 1) * step_in + l];
+          z2[l] = ip[(int64_t)(n - f - 1) * step_in + l];
+        }
+      }
+      const T* Mr = Ms + f * nout;
+#pragma unroll
+      for (int a = 0; a < AMAX; ++a)
+        if (a < nout) {
+          const T m = Mr[a];
+#pragma unroll
+          for (int l = 0; l < LPT; ++l) {
+            acc[a][l].x = fma(m.x, u[l].x, acc[a][l].x);
+            acc[a][l].x = fma(-m.y, w[l].y, acc[a][l].x);
+            acc[a][l].y = fma(m.x, u[l].y, acc[a][l].y);
+            acc[a][l].y = fma(m.y, w[l].x, acc[a][l].y);
+          }
+        }
+    }
+    if (mid) {
+      const T* Mr = Ms + (n / 2) * nout;
+      T vm[LPT];
+#pragma unroll
+      for (int l = 0; l < LPT; ++l) vm[l] = ip[(int64_t)(n / 2) * step_in + l];
+#pragma unroll
+      for (int a = 0; a < AMAX; ++a)
+        if (a < nout)
+#pragma unroll
+          for (int l = 0; l < LPT; ++l) cfma(acc[a][l], Mr[a], vm[l]);
+    }
+    T* op = out + b * vout.sb + ia * sa_out + ib * sb_out + c;
+#pragma unroll
+    for (int a = 0; a < AMAX; ++a)
+      if (a < nout)
+#pragma unroll
+        for (int l = 0; l < LPT; ++l) op[a * step_out + l] = acc[a][l];
+  }
+}
+
+// forward (inverse = false: M is n x nin, nin inputs -> n outputs along ax) or
+// inverse (M is nout x n, n inputs -> nout outputs); returns false when no
+// specialisation fits (the caller then uses launch_mode)
+template <typename R>
+bool launch_dft(const cpx_t<R>* in, View vin, cpx_t<R>* out, View vout, int64_t B, int C, int ax, int nin,
+                int e0, int e1, int e2, const cpx_t<R>* M, int n, bool inverse, cudaStream_t s) {
+  using T = cpx_t<R>;
+  const int ea = ax == 0 ? e1 : e0, eb = ax == 2 ? e1 : e2;
+  const int nout = ax == 0 ? e0 : (ax == 1 ? e1 : e2);
+  const int nh = n / 2 + 1;
+  const bool two = (C % 2) == 0 && sizeof(R) == 4;
+  const int lpt = two ? 2 : 1;
+  const int64_t lines = B * ea * eb * (int64_t)(C / lpt);
+  if (lines <= 0) return true;
+  int64_t blocks = ceil_div(lines, 128);
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  if (!inverse) {
+    const size_t smem = sizeof(T) * (size_t)nh * nin;
+    if (smem > 96 * 1024) return false;
+#define EFIE_DF(NM)                                                                                          \
+  if (nin <= NM) {                                                                                           \
+    if (two && NM <= 21) {                                                                                   \
+      auto k = k_dft_fwd_line<R, NM, (sizeof(R) == 4 && NM <= 21) ? 2 : 1>;                                  \
+      static bool attr = false;                                                                              \
+      if (!attr) {                                                                                           \
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);                     \
+        attr = true;                                                                                         \
+      }                                                                                                      \
+      k<<<(unsigned)blocks, 128, smem, s>>>(in, vin, out, vout, B, C, ax, nin, e0, e1, e2, M, n);            \
+      return true;                                                                                           \
+    }                                                                                                        \
+    const int64_t lines1 = B * ea * eb * (int64_t)C;                                                         \
+    int64_t blocks1 = ceil_div(lines1, 128);                                                                 \
+    if (blocks1 > 152 * 32) blocks1 = 152 * 32;                                                              \
+    auto k = k_dft_fwd_line<R, NM, 1>;                                                                       \
+    static bool attr1 = false;                                                                               \
+    if (!attr1) {                                                                                            \
+      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);                       \
+      attr1 = true;                                                                                          \
+    }                                                                                                        \
+    k<<<(unsigned)blocks1, 128, smem, s>>>(in, vin, out, vout, B, C, ax, nin, e0, e1, e2, M, n);             \
+    return true;                                                                                             \
+  }
+    EFIE_DF(9)
+    EFIE_DF(13)
+    EFIE_DF(21)
+    EFIE_DF(40)
+#undef EFIE_DF
+    return false;
+  }
+  const size_t smem = sizeof(T) * (size_t)nout * nh;
+  if (smem > 96 * 1024) return false;
+#define EFIE_DI(AM)                                                                                          \
+  if (nout <= AM) {                                                                                          \
+    if (two && AM <= 13) {                                                                                   \
+      auto k = k_dft_inv_line<R, AM, (sizeof(R) == 4 && AM <= 13) ? 2 : 1>;                                  \
+      static bool attr = false;                                                                              \
+      if (!attr) {                                                                                           \
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);                     \
+        attr = true;                                                                                         \
+      }                                                                                                      \
+      k<<<(unsigned)blocks, 128, smem, s>>>(in, vin, out, vout, B, C, ax, nin, e0, e1, e2, M, n);            \
+      return true;                                                                                           \
+    }                                                                                                        \
+    const int64_t lines1 = B * ea * eb * (int64_t)C;                                                         \
+    int64_t blocks1 = ceil_div(lines1, 128);                                                                 \
+    if (blocks1 > 152 * 32) blocks1 = 152 * 32;                                                              \
+    auto k = k_dft_inv_line<R, AM, 1>;                                                                       \
+    static bool attr1 = false;                                                                               \
+    if (!attr1) {                                                                                            \
+      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);                       \
+      attr1 = true;                                                                                          \
+    }                                                                                                        \
+    k<<<(unsigned)blocks1, 128, smem, s>>>(in, vin, out, vout, B, C, ax, nin, e0, e1, e2, M, n);             \
+    return true;                                                                                             \
+  }
+  EFIE_DI(9)
+  EFIE_DI(13)
+  EFIE_DI(21)
+#undef EFIE_DI
+  return false;
+}
+
 template <typename R>
 void launch_mode(const cpx_t<R>* in, View vin, cpx_t<R>* out, View vout, int64_t B, int C, int ax,
                  int nin, int e0, int e1, int e2, const void* M0, const void* M1, bool complex_m,
@@ -287,13 +663,12 @@ __global__ void k_gather_build(const R* __restrict__ mr, const int32_t* __restri
     int e;
     for (int64_t i = k0; i < k1; ++i)
       if (covers(mr_base, mr_ext, i, p0, p1, p2, e)) {
-        const int ne = mr_ext[3 * i] * mr_ext[3 * i + 1] * mr_ext[3 * i + 2];
-        const R* m = mr + mr_off[i];
+        const R* m = mr + mr_off[i] + 3 * e;
         R* o = outr + 4 * pos++;
         o[0] = (R)(i - k0);
-        o[1] = m[e];
-        o[2] = m[ne + e];
-        o[3] = m[2 * ne + e];
+        o[1] = m[0];
+        o[2] = m[1];
+        o[3] = m[2];
       }
     pos = gcnt[npts + pt];
     for (int64_t i = t0; i < t1; ++i)
@@ -309,19 +684,20 @@ __global__ void k_gather_build(const R* __restrict__ mr, const int32_t* __restri
 // q[b][pt][d nr + r] = sum over the gather list of pt: m_d x_r[k] (d < 3) and
 // sum of m^phi rho_r[t] (d = 3).  One CTA per leaf box; the box's currents and
 // charges are staged in shared memory (AK basis functions at a time; boxes
-// with more take several passes over their sorted lists), then each thread
-// owns one grid point and RPU right-hand sides and keeps all 4 components in
-// registers: no atomics, each moment entry read once per launch, each output
-// value written once.
+// with more take several passes over their sorted lists).  A warp takes four
+// grid points at a time, lane = (point, right-hand side): the eight lanes of a
+// point read the same list entry (one broadcast) and eight consecutive staged
+// values, and own their 4 output components outright -- no atomics, no
+// reductions, each moment entry read once per launch, each output written once.
 template <typename R>
 struct AnterpCfg;
 template <>
 struct AnterpCfg<float> {
-  static constexpr int AK = 256, XS = 10, RPU = 8;  // 80-byte rows: conflict-light broadcasts
+  static constexpr int AK = 256, XS = 10;  // 80-byte rows
 };
 template <>
 struct AnterpCfg<double> {
-  static constexpr int AK = 128, XS = 9, RPU = 4;
+  static constexpr int AK = 128, XS = 9;   // 144-byte rows
 };
 
 template <typename R>
@@ -336,10 +712,10 @@ __global__ void __launch_bounds__(256) k_anterp(const R* __restrict__ gr, const 
                                                 const cpx_t<R>* __restrict__ rho, int64_t ldr, int nr,
                                                 cpx_t<R>* __restrict__ q, int sp) {
   using T = cpx_t<R>;
-  constexpr int AK = AnterpCfg<R>::AK, XS = AnterpCfg<R>::XS, RPU = AnterpCfg<R>::RPU;
+  constexpr int AK = AnterpCfg<R>::AK, XS = AnterpCfg<R>::XS;
   __shared__ __align__(16) T xsm[AK][XS];
   __shared__ __align__(16) T rsm[AK][XS];
-  const int b = blockIdx.x, tid = threadIdx.x;
+  const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int npts = sp * sp * sp;
   const int64_t k0 = box_rwg_ptr[b], t0 = box_tri_ptr[b];
   const int nk = (int)(box_rwg_ptr[b + 1] - k0), nt = (int)(box_tri_ptr[b + 1] - t0);
@@ -347,7 +723,6 @@ __global__ void __launch_bounds__(256) k_anterp(const R* __restrict__ gr, const 
   const R* get = gt + 2 * (nt > 0 ? mt_off[t0] : 0);
   const int32_t* pr = gptr_r + (int64_t)b * (npts + 1);
   const int32_t* pq = gptr_t + (int64_t)b * (npts + 1);
-  const int ngrp = (nr + RPU - 1) / RPU, nunits = npts * ngrp;
   const int nchunk = max((nk + AK - 1) / AK, (nt + AK - 1) / AK);
   auto stage = [&](int c) {
     for (int i = tid; i < AK * nr; i += blockDim.x) {
@@ -360,19 +735,15 @@ __global__ void __launch_bounds__(256) k_anterp(const R* __restrict__ gr, const 
     stage(0);
     __syncthreads();
   }
+  const int r = lane & 7, ps = lane >> 3;
   const int C = 4 * nr;
-  for (int ub = 0; ub < nunits; ub += blockDim.x) {
-    const int u = ub + tid;
-    const bool ok = u < nunits;
-    const int g = ok ? u / npts : 0, p = ok ? u - g * npts : 0;
-    const int rb = g * RPU;
-    T acc[RPU][4];
-#pragma unroll
-    for (int r = 0; r < RPU; ++r)
-#pragma unroll
-      for (int d = 0; d < 4; ++d) acc[r][d] = mk<R>(0, 0);
-    int er = ok ? pr[p] : 0, er1 = ok ? pr[p + 1] : 0;
-    int et = ok ? pq[p] : 0, et1 = ok ? pq[p + 1] : 0;
+  const int per_pass = 4 * (blockDim.x >> 5);
+  for (int pb = 0; pb < npts; pb += per_pass) {
+    const int p = pb + 4 * warp + ps;
+    const bool okp = p < npts;
+    T a0 = mk<R>(0, 0), a1 = a0, a2 = a0, a3 = a0;
+    int er = okp ? pr[p] : 0, er1 = okp ? pr[p + 1] : 0;
+    int et = okp ? pq[p] : 0, et1 = okp ? pq[p + 1] : 0;
     for (int c = 0; c < nchunk; ++c) {
       if (nchunk > 1) {
         __syncthreads();
@@ -380,9 +751,8 @@ __global__ void __launch_bounds__(256) k_anterp(const R* __restrict__ gr, const 
         __syncthreads();
       }
       const R kc0 = (R)(c * AK), kc1 = (R)((c + 1) * AK);
-      for (; er < er1; ++er) {
-        const R* e = ger + 4 * (int64_t)er;
-        R ek, m0, m1, m2;
+      auto load4 = [&](int64_t i, R& ek, R& m0, R& m1, R& m2) {
+        const R* e = ger + 4 * i;
         if constexpr (sizeof(R) == 4) {
           const float4 v = *reinterpret_cast<const float4*>(e);
           ek = v.x, m0 = v.y, m1 = v.z, m2 = v.w;
@@ -390,23 +760,34 @@ __global__ void __launch_bounds__(256) k_anterp(const R* __restrict__ gr, const 
           const double2 v0 = *reinterpret_cast<const double2*>(e), v1 = *reinterpret_cast<const double2*>(e + 2);
           ek = v0.x, m0 = v0.y, m1 = v1.x, m2 = v1.y;
         }
-        if (ek >= kc1) break;
-        const T* xr = xsm[(int)(ek - kc0)] + rb;
+      };
+      auto mac3 = [&](R ek, R m0, R m1, R m2) {
+        const T xv = xsm[(int)(ek - kc0)][r];
+        a0.x = fma(m0, xv.x, a0.x);
+        a0.y = fma(m0, xv.y, a0.y);
+        a1.x = fma(m1, xv.x, a1.x);
+        a1.y = fma(m1, xv.y, a1.y);
+        a2.x = fma(m2, xv.x, a2.x);
+        a2.y = fma(m2, xv.y, a2.y);
+      };
+      if (nchunk == 1) {
+        // every entry belongs to this chunk: four list entries in flight at a time
+        for (; er + 3 < er1; er += 4) {
+          R k_[4], x_[4], y_[4], z_[4];
 #pragma unroll
-        for (int r = 0; r < RPU; ++r) {
-          if (rb + r >= nr) break;
-          const T xv = xr[r];
-          acc[r][0].x = fma(m0, xv.x, acc[r][0].x);
-          acc[r][0].y = fma(m0, xv.y, acc[r][0].y);
-          acc[r][1].x = fma(m1, xv.x, acc[r][1].x);
-          acc[r][1].y = fma(m1, xv.y, acc[r][1].y);
-          acc[r][2].x = fma(m2, xv.x, acc[r][2].x);
-          acc[r][2].y = fma(m2, xv.y, acc[r][2].y);
+          for (int t = 0; t < 4; ++t) load4(er + t, k_[t], x_[t], y_[t], z_[t]);
+#pragma unroll
+          for (int t = 0; t < 4; ++t) mac3(k_[t], x_[t], y_[t], z_[t]);
         }
       }
-      for (; et < et1; ++et) {
-        const R* e = get + 2 * (int64_t)et;
-        R ek, m;
+      for (; er < er1; ++er) {
+        R ek, m0, m1, m2;
+        load4(er, ek, m0, m1, m2);
+        if (ek >= kc1) break;
+        mac3(ek, m0, m1, m2);
+      }
+      auto load2 = [&](int64_t i, R& ek, R& m) {
+        const R* e = get + 2 * i;
         if constexpr (sizeof(R) == 4) {
           const float2 v = *reinterpret_cast<const float2*>(e);
           ek = v.x, m = v.y;
@@ -414,24 +795,34 @@ __global__ void __launch_bounds__(256) k_anterp(const R* __restrict__ gr, const 
           const double2 v = *reinterpret_cast<const double2*>(e);
           ek = v.x, m = v.y;
         }
-        if (ek >= kc1) break;
-        const T* rr = rsm[(int)(ek - kc0)] + rb;
+      };
+      auto mac1 = [&](R ek, R m) {
+        const T v = rsm[(int)(ek - kc0)][r];
+        a3.x = fma(m, v.x, a3.x);
+        a3.y = fma(m, v.y, a3.y);
+      };
+      if (nchunk == 1) {
+        for (; et + 3 < et1; et += 4) {
+          R k_[4], m_[4];
 #pragma unroll
-        for (int r = 0; r < RPU; ++r) {
-          if (rb + r >= nr) break;
-          const T v = rr[r];
-          acc[r][3].x = fma(m, v.x, acc[r][3].x);
-          acc[r][3].y = fma(m, v.y, acc[r][3].y);
+          for (int t = 0; t < 4; ++t) load2(et + t, k_[t], m_[t]);
+#pragma unroll
+          for (int t = 0; t < 4; ++t) mac1(k_[t], m_[t]);
         }
       }
+      for (; et < et1; ++et) {
+        R ek, m;
+        load2(et, ek, m);
+        if (ek >= kc1) break;
+        mac1(ek, m);
+      }
     }
-    if (ok) {
-      T* qp = q + ((int64_t)b * npts + p) * C + rb;
-#pragma unroll
-      for (int d = 0; d < 4; ++d)
-#pragma unroll
-        for (int r = 0; r < RPU; ++r)
-          if (rb + r < nr) qp[d * nr + r] = acc[r][d];
+    if (okp && r < nr) {
+      T* qp = q + ((int64_t)b * npts + p) * C + r;
+      qp[0] = a0;
+      qp[nr] = a1;
+      qp[2 * nr] = a2;
+      qp[3 * nr] = a3;
     }
   }
 }
@@ -491,20 +882,22 @@ __global__ void __launch_bounds__(256) k_interp(const R* __restrict__ mr, const 
     const int ne = e0 * e1 * e2;
     const bool act = lane < 3 * nr;
     const int d = act ? lane / nr : 0;
-    const R* m = mr + mr_off[i] + (int64_t)d * ne;
+    const R* m = mr + mr_off[i] + d;  // entry e at m[3 e]
     const T* gp = rg + (int64_t)rwg_box[i] * npts * C + lane;
-    if (act) {
+    if (act && ne > 0) {
       int e = 0;
       for (int a0 = 0; a0 < e0; ++a0)
         for (int a1 = 0; a1 < e1; ++a1) {
           const T* gl = gp + (int64_t)(((b0 + a0) * sp + b1 + a1) * sp + b2) * C;
+          const R* ml = m + 3 * e;
 #pragma unroll 4
-          for (int a2 = 0; a2 < e2; ++a2, ++e) {
-            const R mv = m[e];
+          for (int a2 = 0; a2 < e2; ++a2) {
+            const R mv = ml[3 * a2];
             const T gv = gl[a2 * C];
             acc.x = fma(mv, gv.x, acc.x);
             acc.y = fma(mv, gv.y, acc.y);
           }
+          e += e2;
         }
     }
     R sx = acc.x + __shfl_down_sync(0xffffffffu, acc.x, nr) + __shfl_down_sync(0xffffffffu, acc.x, 2 * nr);
@@ -848,31 +1241,6 @@ void launch_mac(const cpx_t<R>* Qh, cpx_t<R>* Rh, const cpx_t<R>* Kh, int64_t B,
   }
 }
 
-// ---------------------------------------------------------------- children sum
-// q_parent[P][e] = sum_{c in children(P)} tmp[c][e]   (children contiguous)
-template <typename R>
-__global__ void k_reduce_children(const cpx_t<R>* __restrict__ tmp, cpx_t<R>* __restrict__ qp,
-                                  const int64_t* __restrict__ child_ptr, int64_t Bp, int64_t per_box) {
-  int64_t total = Bp * per_box;
-  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    int64_t P = idx / per_box, e = idx - P * per_box;
-    cpx_t<R> acc = mk<R>(0, 0);
-    for (int64_t c = child_ptr[P]; c < child_ptr[P + 1]; ++c) acc = cadd(acc, tmp[c * per_box + e]);
-    qp[idx] = acc;
-  }
-}
-
-template <typename R>
-void launch_reduce_children(const cpx_t<R>* tmp, cpx_t<R>* q_parent, const int64_t* child_ptr,
-                            int64_t Bp, int64_t per_box, cudaStream_t s) {
-  int64_t total = Bp * per_box;
-  if (total <= 0) return;
-  int64_t blocks = ceil_div(total, 256);
-  if (blocks > 152 * 64) blocks = 152 * 64;
-  k_reduce_children<R><<<(unsigned)blocks, 256, 0, s>>>(tmp, q_parent, child_ptr, Bp, per_box);
-}
-
 // ---------------------------------------------------------------- kernel samples
 // Kc[o][i0][i1][i2] = g(o h + t Delta), t_d = i_d (i_d < shat) or i_d - n, FP64.
 __global__ void k_kernel_samples(double2* __restrict__ Kc, const int32_t* __restrict__ offsets,
@@ -1183,6 +1551,16 @@ void launch_norms(const double2* w, int64_t ldw, int64_t N, int nr, double* out,
 }
 
 // explicit instantiations
+template void launch_mode_pair<float>(const float2*, View, float2*, View, int64_t, int, int, int, int, int, int,
+                                      const float*, const float*, const int64_t*, const int64_t*, const int8_t*,
+                                      const int8_t*, cudaStream_t);
+template void launch_mode_pair<double>(const double2*, View, double2*, View, int64_t, int, int, int, int, int, int,
+                                       const double*, const double*, const int64_t*, const int64_t*,
+                                       const int8_t*, const int8_t*, cudaStream_t);
+template bool launch_dft<float>(const float2*, View, float2*, View, int64_t, int, int, int, int, int, int,
+                                const float2*, int, bool, cudaStream_t);
+template bool launch_dft<double>(const double2*, View, double2*, View, int64_t, int, int, int, int, int, int,
+                                 const double2*, int, bool, cudaStream_t);
 template void launch_mode<float>(const float2*, View, float2*, View, int64_t, int, int, int, int, int, int,
                                  const void*, const void*, bool, const int8_t*, const int64_t*, bool,
                                  cudaStream_t);
@@ -1217,10 +1595,6 @@ template void launch_mac<float>(const float2*, float2*, const float2*, int64_t, 
 template void launch_mac<double>(const double2*, double2*, const double2*, int64_t, int, int64_t, int64_t,
                                  int64_t, int, const int64_t*, const int32_t*, const int64_t*, const int32_t*,
                                  const int64_t*, const int32_t*, cudaStream_t);
-template void launch_reduce_children<float>(const float2*, float2*, const int64_t*, int64_t, int64_t,
-                                            cudaStream_t);
-template void launch_reduce_children<double>(const double2*, double2*, const int64_t*, int64_t, int64_t,
-                                             cudaStream_t);
 template void launch_convert<float>(const double2*, float2*, int64_t, cudaStream_t);
 template void launch_convert<double>(const double2*, double2*, int64_t, cudaStream_t);
 

@@ -386,7 +386,7 @@ __global__ void k_near_V(NearDev nd, int64_t e_begin, int64_t total) {
 // keeps their sums in registers across all source boxes, so no reduction is
 // needed.  Sorted orders; x, y are [nr][n] with leading dimension ld, nr <= 8.
 constexpr int NEAR_CH = 64;
-constexpr int NEAR_THREADS = 128;
+constexpr int NEAR_THREADS = 256;
 
 template <int RPT, int UPT>
 __global__ void __launch_bounds__(NEAR_THREADS)
@@ -601,6 +601,52 @@ k_near_rows_df(const float4* __restrict__ M, const int64_t* __restrict__ blk_off
   }
 }
 
+// Variant without shared memory and without barriers: each thread reads the
+// x values of its right-hand-side group straight from global memory (the
+// threads of a group read the same address, one broadcast; a source box's x
+// stays in L1 while the block runs over it), so warps never wait for one
+// another.  Same units, layouts and arithmetic as k_near_rows_df.
+template <int RPT>
+__global__ void __launch_bounds__(NEAR_THREADS)
+k_near_rows_df_g(const float4* __restrict__ M, const int64_t* __restrict__ blk_off,
+                 const int64_t* __restrict__ near_ptr, const int32_t* __restrict__ near_src,
+                 const int64_t* __restrict__ box_ptr, const float4* __restrict__ x,
+                 double2* __restrict__ y, int64_t ld, int nr) {
+  const int xb = blockIdx.x;
+  const int64_t r0 = box_ptr[xb];
+  const int nrow = (int)(box_ptr[xb + 1] - r0);
+  const int ngrp = (nr + RPT - 1) / RPT, nunits = nrow * ngrp;
+  const int64_t j0 = near_ptr[xb], j1 = near_ptr[xb + 1];
+  for (int u = threadIdx.x; u < nunits; u += NEAR_THREADS) {
+    const int grp = u / nrow, row = u - grp * nrow;
+    const int nq = min(RPT, nr - grp * RPT);
+    const float4* xg = x + (int64_t)grp * RPT * ld;
+    DF re[RPT], im[RPT];
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) re[q] = im[q] = DF{0.f, 0.f};
+    for (int64_t j = j0; j < j1; ++j) {
+      const int32_t yb = near_src[j];
+      const int64_t c0 = box_ptr[yb];
+      const int ncol = (int)(box_ptr[yb + 1] - c0);
+      const float4* Mc = M + blk_off[j] + row;
+      const float4* xc = xg + c0;
+      for (int cc = 0; cc < ncol; ++cc) {
+        const float4 a = Mc[(int64_t)cc * nrow];
+#pragma unroll
+        for (int q = 0; q < RPT; ++q)
+          if (q < nq) df_cmac(re[q], im[q], a, xc[q * ld + cc]);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+      if (q >= nq) break;
+      double2* yp = y + (grp * RPT + q) * ld + r0 + row;
+      double2 t = *yp;
+      *yp = make_double2(t.x + ((double)re[q].hi + (double)re[q].lo), t.y + ((double)im[q].hi + (double)im[q].lo));
+    }
+  }
+}
+
 void launch_split_df(double2* a, int64_t n, cudaStream_t s) {
   if (n <= 0) return;
   int64_t blocks = ceil_div(n, 256);
@@ -614,15 +660,24 @@ void launch_split_vec(const double2* x, float4* y, int64_t n, cudaStream_t s) {
   k_split_vec<<<(unsigned)blocks, 256, 0, s>>>(x, y, n);
 }
 // right-hand sides per unit: all of a 1-, 2- or 4-wide chunk; 4 for wider
-// chunks (two units per row)
+// chunks (two units per row, one unit per thread)
 void launch_near_spmv_df(const float4* M, const int64_t* blk_off, const int64_t* near_ptr,
                          const int32_t* near_src, const int64_t* box_ptr, int64_t n_boxes, const float4* x,
-                         double2* y, int64_t ld, int nr, cudaStream_t s) {
+                         double2* y, int64_t ld, int nr, int variant, cudaStream_t s) {
   if (n_boxes <= 0) return;
   for (int r0 = 0; r0 < nr; r0 += 8) {
     int cnt = nr - r0 < 8 ? nr - r0 : 8;
     const float4* xr = x + (int64_t)r0 * ld;
     double2* yr = y + (int64_t)r0 * ld;
+    if (variant == 1) {
+      if (cnt <= 2)
+        k_near_rows_df_g<2><<<(unsigned)n_boxes, NEAR_THREADS, 0, s>>>(M, blk_off, near_ptr, near_src, box_ptr, xr,
+                                                                       yr, ld, cnt);
+      else
+        k_near_rows_df_g<4><<<(unsigned)n_boxes, NEAR_THREADS, 0, s>>>(M, blk_off, near_ptr, near_src, box_ptr, xr,
+                                                                       yr, ld, cnt);
+      continue;
+    }
     if (cnt == 1)
       k_near_rows_df<1, 1><<<(unsigned)n_boxes, NEAR_THREADS, 0, s>>>(M, blk_off, near_ptr, near_src, box_ptr,
                                                                        xr, yr, ld, cnt);
@@ -630,7 +685,7 @@ void launch_near_spmv_df(const float4* M, const int64_t* blk_off, const int64_t*
       k_near_rows_df<2, 1><<<(unsigned)n_boxes, NEAR_THREADS, 0, s>>>(M, blk_off, near_ptr, near_src, box_ptr,
                                                                        xr, yr, ld, cnt);
     else
-      k_near_rows_df<4, 2><<<(unsigned)n_boxes, NEAR_THREADS, 0, s>>>(M, blk_off, near_ptr, near_src, box_ptr,
+      k_near_rows_df<4, 1><<<(unsigned)n_boxes, NEAR_THREADS, 0, s>>>(M, blk_off, near_ptr, near_src, box_ptr,
                                                                        xr, yr, ld, cnt);
   }
 }
@@ -672,7 +727,7 @@ void launch_near_spmv(const double2* M, const int64_t* blk_off, const int64_t* n
       k_near_rows<2, 1><<<(unsigned)n_boxes, NEAR_THREADS, 0, s>>>(M, blk_off, near_ptr, near_src, box_ptr, xr,
                                                                     yr, ld, cnt);
     else
-      k_near_rows<4, 2><<<(unsigned)n_boxes, NEAR_THREADS, 0, s>>>(M, blk_off, near_ptr, near_src, box_ptr, xr,
+      k_near_rows<4, 1><<<(unsigned)n_boxes, NEAR_THREADS, 0, s>>>(M, blk_off, near_ptr, near_src, box_ptr, xr,
                                                                     yr, ld, cnt);
   }
 }

@@ -191,3 +191,38 @@ def test_top_level_mixed_batched(G, two_level_oracle):
     h.close()
     for r in (0, 5, 9):
         assert _rel(Y[r], ref_op.matvec(X[r])) < TOL32
+
+
+@pytest.mark.parametrize("mac_variant", [0, 1])
+def test_top_level_translation_variants(G, two_level_oracle, mac_variant):
+    """Both top-level translation kernels the autotuner can pick (0: shared-memory
+    staging through the pair index tile, 1: register tiles) against the oracle,
+    mixed form."""
+    torch = _torch()
+    V, T, ref_op = two_level_oracle
+    _, _, k, p, delta, levels = TWO_LEVEL
+    h = G.EFIE(V, T, k, p, delta, levels, precision=G.EFIE_MIXED)
+    h.autotune_set(8, mac_variant)
+    X = E.complex_gaussian((8, h.N), 7)
+    Y = h.matvec(torch.from_numpy(X).cuda()).cpu().numpy()
+    h.close()
+    for r in (0, 7):
+        assert _rel(Y[r], ref_op.matvec(X[r])) < TOL32
+
+
+@pytest.mark.parametrize("near_variant", [0, 1])
+def test_near_field_variants_mixed(G, c1_gpu, c1_oracle, near_variant):
+    """Both double-float near-field kernels (x staged in shared memory; x read
+    through L1) against the FP64 oracle, with 8-, 3- and 1-vector chunks."""
+    torch = _torch()
+    h64, h32 = c1_gpu
+    X = E.complex_gaussian((12, h32.N), 8)
+    for chunk in (8, 3, 1):
+        h32.autotune_set(chunk, 0, near_variant)
+        Y = h32.matvec(torch.from_numpy(X).cuda()).cpu().numpy()
+        for r in (0, 11):
+            assert _rel(Y[r], c1_oracle.matvec(X[r])) < TOL32
+    # FP64 far field + this double-float near field: FP64-class agreement
+    Y64 = h32.matvec(torch.from_numpy(X[:2]).cuda(), fp64=True).cpu().numpy()
+    assert _rel(Y64[1], c1_oracle.matvec(X[1])) < 1e-10
+    h32.autotune_set(8, 0, 0)
