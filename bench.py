@@ -32,6 +32,7 @@ sys.path.insert(0, ROOT)
 WORKLOADS = {
     "sphere20": dict(freq=200, radius=10.0, k=2 * np.pi, p=3, delta=0.1, levels=3, nrhs=64, precision="mixed"),
     "sphere10": dict(freq=100, radius=5.0, k=2 * np.pi, p=3, delta=0.1, levels=3, nrhs=64, precision="mixed"),
+    "mlf": dict(freq=200, radius=0.1, k=2 * np.pi, p=3, delta=0.0008, levels=5, nrhs=64, precision="mixed"),
     "sphere6": dict(freq=60, radius=3.0, k=2 * np.pi, p=3, delta=0.1, levels=3, nrhs=16, precision="mixed"),
     "sphere4": dict(freq=40, radius=2.0, k=2 * np.pi, p=3, delta=0.1, levels=2, nrhs=16, precision="mixed"),
     "c1": dict(freq=8, radius=0.5, k=2 * np.pi, p=3, delta=0.1, levels=2, nrhs=1, precision="fp64"),
@@ -527,20 +528,16 @@ def reference_arm(args, w):
 
 def batch_meshes():
     """Ten PEC ellipsoids, semi-axes uniform in [0.5, 3] wavelengths (seed 3),
-    each a scaled geodesic sphere whose frequency gives ~0.1-wavelength edges
-    (area-equivalent radius), clamped to 5,000 - 60,000 unknowns."""
+    each a scaled geodesic sphere whose frequency keeps the edges along the
+    longest axis near 0.1 wavelength, clamped to 5,000 - 60,000 unknowns."""
     import efie_inputs as E
     rng = np.random.default_rng(3)
     out = []
     for _ in range(10):
-        a, b, c = rng.uniform(0.5, 3.0, size=3)
-        # Knud Thomsen's surface approximation, then the equal-area sphere radius
-        pp = 1.6075
-        area = 4 * np.pi * (((a * b) ** pp + (a * c) ** pp + (b * c) ** pp) / 3) ** (1 / pp)
-        r_eq = np.sqrt(area / (4 * np.pi))
-        freq = int(round(1.205 * r_eq / 0.1))
+        axes = rng.uniform(0.5, 3.0, size=3)
+        freq = int(np.ceil(1.205 * axes.max() / 0.1))
         freq = int(np.clip(freq, 13, 44))
-        out.append(E.ellipsoid(freq, (a, b, c)))
+        out.append(E.ellipsoid(freq, tuple(axes)))
     return out
 
 
