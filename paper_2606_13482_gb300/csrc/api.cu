@@ -196,8 +196,7 @@ struct efie_handle {
   std::vector<LevDev> lev;
   FarSet<double> f64;
   FarSet<float> f32;
-  int mac_variant = 0;   // translation: 0 shared-memory staged, 1 register tiles, 2 staged with packed
-                         // f32x2 multiply-adds and pipelined interaction lists (autotuner knob)
+  int mac_variant = 0;   // 0 auto (shared-memory staged), 1 register tiles (autotuner knob)
   int near_variant = 0;  // mixed near field: 0 shared-memory staged x, 1 x through L1 (autotuner knob)
   // work vectors (FP64, sorted) and their double-float splits
   int Rw = 0;
@@ -509,8 +508,7 @@ void far_chunk(efie_handle* h, FarSet<R>& F, int nr, cudaStream_t s) {
     {
       KScope ks(h, ell == top ? K_MAC_TOP : K_MAC, s, 1);
       launch_mac<R>(F.Qh, F.Rh, FL.Kh, B, C, LD.O, n3, LD.ntiles, h->mac_variant == 1 ? -LD.max_tile : LD.max_tile,
-                    LD.tile_tgt_ptr, LD.tile_tgt, LD.tile_src_ptr, LD.tile_src, LD.tile_kidx_off, LD.tile_kidx,
-                    h->mac_variant, s);
+                    LD.tile_tgt_ptr, LD.tile_tgt, LD.tile_src_ptr, LD.tile_src, LD.tile_kidx_off, LD.tile_kidx, s);
     }
     KScope ks(h, K_INV, s, 3);
     View b1{(int64_t)sp * n * n * C, (int64_t)n * n * C, (int64_t)n * C, C};
@@ -1633,7 +1631,7 @@ int efie_precond_gradient(efie_handle* h, const void* r, const void* e, float* g
 }
 
 int efie_autotune_set(efie_handle* h, int rhs_chunk, int mac_variant, int near_variant) {
-  if (!h || rhs_chunk < 1 || rhs_chunk > 8 || mac_variant < 0 || mac_variant > 2 || near_variant < 0 ||
+  if (!h || rhs_chunk < 1 || rhs_chunk > 8 || mac_variant < 0 || mac_variant > 1 || near_variant < 0 ||
       near_variant > 1)
     return EFIE_EINVAL;
   h->opt.rhs_chunk = rhs_chunk;
@@ -1660,8 +1658,8 @@ int efie_autotune(efie_handle* h, int n_rhs, void* stream, int* best_chunk, int*
     int bc = 8, bm = 0, bn = 0;
     for (int chunk : {8, 4, 2, 1}) {
       if (chunk > n_rhs && chunk != 1) continue;
-      for (int cand = 0; cand < 6; ++cand) {
-        const int mv = cand % 3, nv = cand / 3;
+      for (int cand = 0; cand < 4; ++cand) {
+        const int mv = cand & 1, nv = cand >> 1;
         if (nv == 1 && !h->near_df) continue;  // the near variants differ in the mixed form only
         h->opt.rhs_chunk = chunk;
         h->mac_variant = mv;

@@ -121,7 +121,7 @@ template <typename R>
 void launch_mac(const cpx_t<R>* Qh, cpx_t<R>* Rh, const cpx_t<R>* Kh, int64_t B, int C, int64_t O,
                 int64_t nf, int64_t ntiles, int max_tile_targets, const int64_t* tgt_ptr, const int32_t* tgt,
                 const int64_t* src_ptr, const int32_t* src, const int64_t* kidx_off, const int32_t* kidx,
-                int top_variant, cudaStream_t s);
+                cudaStream_t s);
 
 
 void launch_kernel_samples(double2* Kc, const int32_t* offsets, int64_t o0, int64_t no, int n,

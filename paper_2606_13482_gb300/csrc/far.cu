@@ -1035,29 +1035,7 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
-// packed FP32 pairs for fma.rn.f32x2 (low word = first value)
-__device__ __forceinline__ uint64_t pack_f2(float lo, float hi) {
-  uint64_t r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-  return r;
-}
-__device__ __forceinline__ float2 unpack_f2(uint64_t v) {
-  float lo, hi;
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-  return make_float2(lo, hi);
-}
-__device__ __forceinline__ uint64_t fma_f2(uint64_t a, uint64_t b, uint64_t c) {
-  uint64_t d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-  return d;
-}
-
-// PK: the complex multiply-adds run as packed pairs (fma.rn.f32x2): with the
-// accumulator (re, im) in one 64-bit register pair, acc += (k_re, k_re) * (q_re, q_im)
-// and acc += (-k_im, k_im) * (q_im, q_re), two instructions per complex MAC
-// instead of four; the paired operands are formed once per kernel value (for
-// four channels) and once per spectrum value (for eight targets).
-template <int YS, bool PK>
+template <int YS>
 __global__ void __launch_bounds__(128) k_mac_top32(const float2* __restrict__ Qh, float2* __restrict__ Rh,
                                                    const float2* __restrict__ Kh, int64_t B, int64_t O,
                                                    int64_t nf, const int64_t* __restrict__ tgt_ptr,
@@ -1097,14 +1075,10 @@ __global__ void __launch_bounds__(128) k_mac_top32(const float2* __restrict__ Qh
     cp_async_commit();
   };
   float2 acc[8][4];
-  uint64_t pacc[8][4];
 #pragma unroll
   for (int a = 0; a < 8; ++a)
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      acc[a][c] = zero;
-      pacc[a][c] = 0ull;
-    }
+    for (int c = 0; c < 4; ++c) acc[a][c] = zero;
   const int nchunks = (int)((ns + YS - 1) / YS);
   if (nchunks > 0) stage(0, 0);
   for (int ch = 0; ch < nchunks; ++ch) {
@@ -1123,42 +1097,17 @@ __global__ void __launch_bounds__(128) k_mac_top32(const float2* __restrict__ Qh
         const float4 qb = *reinterpret_cast<const float4*>(&Qs[buf][j][cg * 4 + 2]);
         const float2 q[4] = {make_float2(qa.x, qa.y), make_float2(qa.z, qa.w), make_float2(qb.x, qb.y),
                              make_float2(qb.z, qb.w)};
-        if constexpr (PK) {
-          uint64_t qn[4], qs[4];
 #pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            qn[c] = pack_f2(q[c].x, q[c].y);
-            qs[c] = pack_f2(q[c].y, q[c].x);
-          }
+        for (int a = 0; a < 8; ++a) {
+          const float2 kv = Ks[buf][j][tg * 8 + a];
 #pragma unroll
-          for (int a = 0; a < 8; ++a) {
-            const float2 kv = Ks[buf][j][tg * 8 + a];
-            const uint64_t kxx = pack_f2(kv.x, kv.x), kyy = pack_f2(-kv.y, kv.y);
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-              pacc[a][c] = fma_f2(kxx, qn[c], pacc[a][c]);
-              pacc[a][c] = fma_f2(kyy, qs[c], pacc[a][c]);
-            }
-          }
-        } else {
-#pragma unroll
-          for (int a = 0; a < 8; ++a) {
-            const float2 kv = Ks[buf][j][tg * 8 + a];
-#pragma unroll
-            for (int c = 0; c < 4; ++c) cfma(acc[a][c], kv, q[c]);
-          }
+          for (int c = 0; c < 4; ++c) cfma(acc[a][c], kv, q[c]);
         }
       }
     }
     __syncthreads();
   }
   if (tg * 8 >= nt) return;
-  if constexpr (PK) {
-#pragma unroll
-    for (int a = 0; a < 8; ++a)
-#pragma unroll
-      for (int c = 0; c < 4; ++c) acc[a][c] = unpack_f2(pacc[a][c]);
-  }
 #pragma unroll
   for (int a = 0; a < 8; ++a) {
     if (tg * 8 + a >= nt) break;
@@ -1172,8 +1121,7 @@ __global__ void __launch_bounds__(128) k_mac_top32(const float2* __restrict__ Qh
 // O (<= 316 on these levels) complex numbers; every block stages the rows of its
 // fpb frequencies in shared memory, so the per-pair kernel lookups hit shared
 // memory and only the spectra come from L1/L2.
-// PF: software-pipelined source loop (next spectra and index row in flight).
-template <int XR, int CR, bool PF>
+template <int XR, int CR>
 __global__ void __launch_bounds__(128) k_mac_il32(const float2* __restrict__ Qh, float2* __restrict__ Rh,
                                                   const float2* __restrict__ Kh, int64_t B, int C, int64_t O,
                                                   int64_t nf, const int64_t* __restrict__ tgt_ptr,
@@ -1206,55 +1154,21 @@ __global__ void __launch_bounds__(128) k_mac_il32(const float2* __restrict__ Qh,
   for (int a = 0; a < XR; ++a)
 #pragma unroll
     for (int c = 0; c < CR; ++c) acc[a][c] = make_float2(0.f, 0.f);
-  if constexpr (PF) {
-    // software pipeline: the source id two ahead and the spectra and index row
-    // one ahead are in flight while the current source is multiplied
-    const int32_t y1 = ns > 0 ? __ldg(src + s0) : 0;
-    int32_t y2 = ns > 1 ? __ldg(src + s0 + 1) : y1;
-    float4 qa = __ldg(reinterpret_cast<const float4*>(Qf + (int64_t)y1 * C));
-    float4 qb = __ldg(reinterpret_cast<const float4*>(Qf + (int64_t)y1 * C + 2));
-    int4 ia = __ldg(reinterpret_cast<const int4*>(kb));
-    int4 ib = __ldg(reinterpret_cast<const int4*>(kb + 4));
-    for (int64_t j = 0; j < ns; ++j) {
-      const int64_t jn = j + 1 < ns ? j + 1 : j;
-      const int32_t y3 = j + 2 < ns ? __ldg(src + s0 + j + 2) : y2;
-      const float4 na = __ldg(reinterpret_cast<const float4*>(Qf + (int64_t)y2 * C));
-      const float4 nb = __ldg(reinterpret_cast<const float4*>(Qf + (int64_t)y2 * C + 2));
-      const int4 nia = __ldg(reinterpret_cast<const int4*>(kb + jn * XR));
-      const int4 nib = __ldg(reinterpret_cast<const int4*>(kb + jn * XR + 4));
-      const float2 q[4] = {make_float2(qa.x, qa.y), make_float2(qa.z, qa.w), make_float2(qb.x, qb.y),
-                           make_float2(qb.z, qb.w)};
-      const int ids[8] = {ia.x, ia.y, ia.z, ia.w, ib.x, ib.y, ib.z, ib.w};
+  for (int64_t j = 0; j < ns; ++j) {
+    const int32_t y = __ldg(src + s0 + j);
+    const float4 qa = __ldg(reinterpret_cast<const float4*>(Qf + (int64_t)y * C));
+    const float4 qb = __ldg(reinterpret_cast<const float4*>(Qf + (int64_t)y * C + 2));
+    const float2 q[4] = {make_float2(qa.x, qa.y), make_float2(qa.z, qa.w), make_float2(qb.x, qb.y),
+                         make_float2(qb.z, qb.w)};
+    const int4 ia = __ldg(reinterpret_cast<const int4*>(kb + j * XR));
+    const int4 ib = __ldg(reinterpret_cast<const int4*>(kb + j * XR + 4));
+    const int ids[8] = {ia.x, ia.y, ia.z, ia.w, ib.x, ib.y, ib.z, ib.w};
 #pragma unroll
-      for (int a = 0; a < XR; ++a) {
-        if (ids[a] < 0) continue;
-        const float2 kv = Kf[ids[a]];
+    for (int a = 0; a < XR; ++a) {
+      if (ids[a] < 0) continue;
+      const float2 kv = Kf[ids[a]];
 #pragma unroll
-        for (int c = 0; c < CR; ++c) cfma(acc[a][c], kv, q[c]);
-      }
-      qa = na;
-      qb = nb;
-      ia = nia;
-      ib = nib;
-      y2 = y3;
-    }
-  } else {
-    for (int64_t j = 0; j < ns; ++j) {
-      const int32_t y = __ldg(src + s0 + j);
-      const float4 qa = __ldg(reinterpret_cast<const float4*>(Qf + (int64_t)y * C));
-      const float4 qb = __ldg(reinterpret_cast<const float4*>(Qf + (int64_t)y * C + 2));
-      const float2 q[4] = {make_float2(qa.x, qa.y), make_float2(qa.z, qa.w), make_float2(qb.x, qb.y),
-                           make_float2(qb.z, qb.w)};
-      const int4 ia = __ldg(reinterpret_cast<const int4*>(kb + j * XR));
-      const int4 ib = __ldg(reinterpret_cast<const int4*>(kb + j * XR + 4));
-      const int ids[8] = {ia.x, ia.y, ia.z, ia.w, ib.x, ib.y, ib.z, ib.w};
-#pragma unroll
-      for (int a = 0; a < XR; ++a) {
-        if (ids[a] < 0) continue;
-        const float2 kv = Kf[ids[a]];
-#pragma unroll
-        for (int c = 0; c < CR; ++c) cfma(acc[a][c], kv, q[c]);
-      }
+      for (int c = 0; c < CR; ++c) cfma(acc[a][c], kv, q[c]);
     }
   }
 #pragma unroll
@@ -1270,7 +1184,7 @@ template <typename R>
 void launch_mac(const cpx_t<R>* Qh, cpx_t<R>* Rh, const cpx_t<R>* Kh, int64_t B, int C, int64_t O,
                 int64_t nf, int64_t ntiles, int max_tile_targets, const int64_t* tgt_ptr, const int32_t* tgt,
                 const int64_t* src_ptr, const int32_t* src, const int64_t* kidx_off, const int32_t* kidx,
-                int top_variant, cudaStream_t s) {
+                cudaStream_t s) {
   if (B <= 0 || nf <= 0 || ntiles <= 0) return;
   // a negative tile size asks for the register-tile kernel (autotuner choice)
   const bool force_reg = max_tile_targets < 0;
@@ -1278,13 +1192,16 @@ void launch_mac(const cpx_t<R>* Qh, cpx_t<R>* Rh, const cpx_t<R>* Kh, int64_t B,
   if (!force_reg && sizeof(R) == 4 && C == 32 && max_tile_targets > 8 && max_tile_targets <= 128) {
     constexpr int YS = 16;
     const size_t smem = 2 * sizeof(float2) * YS * (128 + 32);
-    auto kern = top_variant == 2 ? k_mac_top32<YS, true> : k_mac_top32<YS, false>;
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_mac_top32<YS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      attr = true;
+    }
     for (int64_t f0 = 0; f0 < nf; f0 += 65535) {
       int64_t nfc = std::min<int64_t>(65535, nf - f0);
       dim3 grid((unsigned)ntiles, (unsigned)nfc);
-      kern<<<grid, 128, smem, s>>>((const float2*)Qh, (float2*)Rh, (const float2*)Kh, B, O, nf, tgt_ptr, tgt,
-                                   src_ptr, src, kidx_off, kidx, f0);
+      k_mac_top32<YS><<<grid, 128, smem, s>>>((const float2*)Qh, (float2*)Rh, (const float2*)Kh, B, O, nf, tgt_ptr,
+                                              tgt, src_ptr, src, kidx_off, kidx, f0);
     }
     return;
   }
@@ -1297,16 +1214,14 @@ void launch_mac(const cpx_t<R>* Qh, cpx_t<R>* Rh, const cpx_t<R>* Kh, int64_t B,
     const size_t smem = (size_t)fpb * O * sizeof(float2);
     static bool attr = false;
     if (!attr) {
-      cudaFuncSetAttribute(k_mac_il32<8, 4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
-      cudaFuncSetAttribute(k_mac_il32<8, 4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+      cudaFuncSetAttribute(k_mac_il32<8, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
       attr = true;
     }
     const int64_t fchunk = (int64_t)65535 * fpb;
     for (int64_t f0 = 0; f0 < nf; f0 += fchunk) {
       int64_t nfc = std::min<int64_t>(fchunk, nf - f0);
       dim3 grid((unsigned)ntiles, (unsigned)ceil_div(nfc, fpb));
-      auto kern = top_variant == 2 ? k_mac_il32<8, 4, true> : k_mac_il32<8, 4, false>;
-      kern<<<grid, fpb * ncg, smem, s>>>((const float2*)Qh, (float2*)Rh, (const float2*)Kh, B, C, O, nf,
+      k_mac_il32<8, 4><<<grid, fpb * ncg, smem, s>>>((const float2*)Qh, (float2*)Rh, (const float2*)Kh, B, C, O, nf,
                                                      tgt_ptr, tgt, src_ptr, src, kidx_off, kidx, fpb, f0);
     }
     return;
@@ -1676,10 +1591,10 @@ template void launch_interp<double>(const double*, const int32_t*, const int32_t
                                     double2*, int64_t, double2*, int64_t, cudaStream_t);
 template void launch_mac<float>(const float2*, float2*, const float2*, int64_t, int, int64_t, int64_t, int64_t,
                                 int, const int64_t*, const int32_t*, const int64_t*, const int32_t*,
-                                const int64_t*, const int32_t*, int, cudaStream_t);
+                                const int64_t*, const int32_t*, cudaStream_t);
 template void launch_mac<double>(const double2*, double2*, const double2*, int64_t, int, int64_t, int64_t,
                                  int64_t, int, const int64_t*, const int32_t*, const int64_t*, const int32_t*,
-                                 const int64_t*, const int32_t*, int, cudaStream_t);
+                                 const int64_t*, const int32_t*, cudaStream_t);
 template void launch_convert<float>(const double2*, float2*, int64_t, cudaStream_t);
 template void launch_convert<double>(const double2*, double2*, int64_t, cudaStream_t);
 
