@@ -55,6 +55,12 @@ def measured_peaks():
 FP32_TFLOPS = 76.0
 FP64_TFLOPS = 1.20
 
+# DRAM bytes per launch of the dominant kernel, from a one-pass ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum) of the full-size bench run of
+# the 20-wavelength sphere; valid while k_mac_top32 and the workload are
+# unchanged (profiles/launches_sphere20_bench.md).
+NCU_DRAM_BYTES_PER_LAUNCH = {("sphere20", "translation_mac_top"): 23.16e9}
+
 
 class ClockSampler:
     def __init__(self, path):
@@ -244,7 +250,7 @@ def run_ours(args, w, rank, world, local_rank):
             # pipes in the mixed form (8 flops counted per complex MAC)
             peak = FP64_TFLOPS if w["precision"] != "mixed" else FP32_TFLOPS
         roof = {"kernel": dom_name, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": NCU_DRAM_BYTES_PER_LAUNCH.get((args.workload, dom_name)),
                 "peak_source": "FMA probe on this GB300 (non-tensor FP32/FP64)",
                 "launches_per_step": dom_launches / max(1, args.steps)}
     peaks, psrc = measured_peaks()
@@ -626,7 +632,7 @@ def run_precond(args):
     """Learned preconditioner against plain GMRES: the network is trained on
     residual/error pairs harvested from the plain solver's own GMRES runs on
     four training scatterers, then two held-out scatterers are solved to a
-    1e-6 FP64 true residual with FGMRES + network and with plain GMRES(30),
+    1e-6 FP64 true residual with FGMRES + network and with plain GMRES(100),
     four plane waves each, mixed precision."""
     import tempfile
     import torch
@@ -634,7 +640,7 @@ def run_precond(args):
     import paper_2606_13482_gb300 as G
     g.build()
     k = 2 * np.pi
-    kw = dict(precision=G.EFIE_MIXED, gmres_restart=30, max_iters=6000)
+    kw = dict(precision=G.EFIE_MIXED, gmres_restart=100, max_iters=4000)
 
     def planewaves(n, seed):
         r = np.random.default_rng(seed)
@@ -683,7 +689,7 @@ def run_precond(args):
     return {"metric": "learned preconditioner: held-out iterations and seconds to a 1e-6 true residual",
             "train_rwg_unknowns": [int(1.5 * T.shape[0]) for _, T in train], "train_seconds": t_train,
             "train_loss_first_last": [[round(l[0], 4), round(l[-1], 4)] for l in losses], "held_out": rows,
-            "gmres_restart": 30, "precision": "mixed", "data": "synthetic (seeded ellipsoids and plate unions)"}
+            "gmres_restart": 100, "precision": "mixed", "data": "synthetic (seeded ellipsoids and plate unions)"}
 
 
 def main():
