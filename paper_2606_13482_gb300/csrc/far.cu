@@ -542,8 +542,8 @@ bool launch_dft(const cpx_t<R>* in, View vin, cpx_t<R>* out, View vout, int64_t 
   if (smem > 96 * 1024) return false;
 #define EFIE_DI(AM)                                                                                          \
   if (nout <= AM) {                                                                                          \
-    if (two && AM <= 13) {                                                                                   \
-      auto k = k_dft_inv_line<R, AM, (sizeof(R) == 4 && AM <= 13) ? 2 : 1>;                                  \
+    if (two && AM <= 21) {                                                                                   \
+      auto k = k_dft_inv_line<R, AM, (sizeof(R) == 4 && AM <= 21) ? 2 : 1>;                                  \
       static bool attr = false;                                                                              \
       if (!attr) {                                                                                           \
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);                     \
