@@ -1156,10 +1156,13 @@ __global__ void __launch_bounds__(128) k_mac_il32(const float2* __restrict__ Qh,
     for (int c = 0; c < CR; ++c) acc[a][c] = make_float2(0.f, 0.f);
   for (int64_t j = 0; j < ns; ++j) {
     const int32_t y = __ldg(src + s0 + j);
-    const float4 qa = __ldg(reinterpret_cast<const float4*>(Qf + (int64_t)y * C));
-    const float4 qb = __ldg(reinterpret_cast<const float4*>(Qf + (int64_t)y * C + 2));
-    const float2 q[4] = {make_float2(qa.x, qa.y), make_float2(qa.z, qa.w), make_float2(qb.x, qb.y),
-                         make_float2(qb.z, qb.w)};
+    float2 q[CR];
+#pragma unroll
+    for (int c2 = 0; c2 < CR; c2 += 2) {
+      const float4 qa = __ldg(reinterpret_cast<const float4*>(Qf + (int64_t)y * C + c2));
+      q[c2] = make_float2(qa.x, qa.y);
+      q[c2 + 1] = make_float2(qa.z, qa.w);
+    }
     const int4 ia = __ldg(reinterpret_cast<const int4*>(kb + j * XR));
     const int4 ib = __ldg(reinterpret_cast<const int4*>(kb + j * XR + 4));
     const int ids[8] = {ia.x, ia.y, ia.z, ia.w, ib.x, ib.y, ib.z, ib.w};
@@ -1175,8 +1178,10 @@ __global__ void __launch_bounds__(128) k_mac_il32(const float2* __restrict__ Qh,
   for (int a = 0; a < XR; ++a) {
     if (a >= nt) break;
     float2* out = Rh + f * B * C + (int64_t)tgt[t0 + a] * C + cg * CR;
-    *reinterpret_cast<float4*>(out) = make_float4(acc[a][0].x, acc[a][0].y, acc[a][1].x, acc[a][1].y);
-    *reinterpret_cast<float4*>(out + 2) = make_float4(acc[a][2].x, acc[a][2].y, acc[a][3].x, acc[a][3].y);
+#pragma unroll
+    for (int c2 = 0; c2 < CR; c2 += 2)
+      *reinterpret_cast<float4*>(out + c2) =
+          make_float4(acc[a][c2].x, acc[a][c2].y, acc[a][c2 + 1].x, acc[a][c2 + 1].y);
   }
 }
 
@@ -1205,24 +1210,27 @@ void launch_mac(const cpx_t<R>* Qh, cpx_t<R>* Rh, const cpx_t<R>* Kh, int64_t B,
     }
     return;
   }
-  if (!force_reg && sizeof(R) == 4 && (C % 4) == 0 && C >= 16 && max_tile_targets <= 8 && O <= 2048) {
-    // interaction-list tiles (<= 8 targets): kernel rows of fpb frequencies in shared memory
-    const int ncg = C / 4;
+  if (!force_reg && sizeof(R) == 4 && (C % 2) == 0 && C >= 16 && max_tile_targets <= 8 && O <= 2048) {
+    // interaction-list tiles (<= 8 targets): kernel rows of fpb frequencies in
+    // shared memory; CRI channels per thread (2: fewer registers, more warps
+    // in flight for this latency-bound loop)
+    constexpr int CRI = 2;
+    const int ncg = C / CRI;
     int fpb = 128 / ncg;
     if (fpb < 1) fpb = 1;
     while (fpb > 1 && (size_t)fpb * O * sizeof(float2) > 64 * 1024) fpb >>= 1;
     const size_t smem = (size_t)fpb * O * sizeof(float2);
     static bool attr = false;
     if (!attr) {
-      cudaFuncSetAttribute(k_mac_il32<8, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+      cudaFuncSetAttribute(k_mac_il32<8, CRI>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
       attr = true;
     }
     const int64_t fchunk = (int64_t)65535 * fpb;
     for (int64_t f0 = 0; f0 < nf; f0 += fchunk) {
       int64_t nfc = std::min<int64_t>(fchunk, nf - f0);
       dim3 grid((unsigned)ntiles, (unsigned)ceil_div(nfc, fpb));
-      k_mac_il32<8, 4><<<grid, fpb * ncg, smem, s>>>((const float2*)Qh, (float2*)Rh, (const float2*)Kh, B, C, O, nf,
-                                                     tgt_ptr, tgt, src_ptr, src, kidx_off, kidx, fpb, f0);
+      k_mac_il32<8, CRI><<<grid, fpb * ncg, smem, s>>>((const float2*)Qh, (float2*)Rh, (const float2*)Kh, B, C, O,
+                                                       nf, tgt_ptr, tgt, src_ptr, src, kidx_off, kidx, fpb, f0);
     }
     return;
   }

@@ -385,7 +385,7 @@ __global__ void k_near_V(NearDev nd, int64_t e_begin, int64_t total) {
 // thread owns up to UPT "units" = (row, group of RPT right-hand sides), and
 // keeps their sums in registers across all source boxes, so no reduction is
 // needed.  Sorted orders; x, y are [nr][n] with leading dimension ld, nr <= 8.
-constexpr int NEAR_CH = 64;
+constexpr int NEAR_CH = 128;
 constexpr int NEAR_THREADS = 256;
 
 template <int RPT, int UPT>
