@@ -939,6 +939,113 @@ __global__ void __launch_bounds__(256) k_interp(const R* __restrict__ mr, const 
   }
 }
 
+// Eight right-hand sides in FP32 (32 channels): a half-warp per basis
+// function, two per warp, each lane holding two adjacent channels (one 16-byte
+// load per grid point).  RWG: lanes 0..11 cover the 24 vector channels;
+// triangle: four entries at a time, four lanes each over the 8 charge channels.
+// Entries run in one flat loop with the grid offset advanced incrementally, so
+// the two halves stay in step and each has its own loads in flight.
+__global__ void __launch_bounds__(256) k_interp8(const float* __restrict__ mr, const int32_t* __restrict__ mr_base,
+                                                 const int32_t* __restrict__ mr_ext,
+                                                 const int64_t* __restrict__ mr_off,
+                                                 const int32_t* __restrict__ rwg_box, int64_t N,
+                                                 const float* __restrict__ mt, const int32_t* __restrict__ mt_base,
+                                                 const int32_t* __restrict__ mt_ext,
+                                                 const int64_t* __restrict__ mt_off,
+                                                 const int32_t* __restrict__ tri_box, int64_t Nt,
+                                                 const float2* __restrict__ rg, int sp,
+                                                 double2* __restrict__ yA, int64_t ldy, double2* __restrict__ u,
+                                                 int64_t ldu) {
+  constexpr int C = 32;
+  const int lane = threadIdx.x & 31, hl = lane & 15;
+  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 4;  // one basis function per half-warp
+  const bool valid = w < N + Nt;
+  const int npts = sp * sp * sp;
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  const bool is_rwg = valid && w < N;
+  const int64_t i = is_rwg ? w : w - N;
+  const int32_t* base = is_rwg ? mr_base : mt_base;
+  const int32_t* ext = is_rwg ? mr_ext : mt_ext;
+  int b0 = 0, b1 = 0, b2 = 0, e0 = 0, e1 = 0, e2 = 0;
+  if (valid) {
+    b0 = base[3 * i], b1 = base[3 * i + 1], b2 = base[3 * i + 2];
+    e0 = ext[3 * i], e1 = ext[3 * i + 1], e2 = ext[3 * i + 2];
+  }
+  const int ne = e0 * e1 * e2;
+  if (is_rwg) {
+    const bool act = hl < 12;
+    const int d = hl >> 2;
+    const float* m = mr + mr_off[i] + d;
+    const float2* gp = rg + (int64_t)rwg_box[i] * npts * C + 2 * (act ? hl : 0);
+    int64_t off = (int64_t)((b0 * sp + b1) * sp + b2) * C;
+    int a1 = 0, a2 = 0;
+    for (int e = 0; e < ne; ++e) {
+      if (act) {
+        const float mv = m[3 * e];
+        const float4 g = *reinterpret_cast<const float4*>(gp + off);
+        acc.x = fmaf(mv, g.x, acc.x);
+        acc.y = fmaf(mv, g.y, acc.y);
+        acc.z = fmaf(mv, g.z, acc.z);
+        acc.w = fmaf(mv, g.w, acc.w);
+      }
+      off += C;
+      if (++a2 == e2) {
+        a2 = 0;
+        off += (int64_t)(sp - e2) * C;
+        if (++a1 == e1) {
+          a1 = 0;
+          off += (int64_t)(sp - e1) * sp * C;
+        }
+      }
+    }
+  } else if (valid) {
+    const int slot = hl >> 2, pr = hl & 3;
+    const float* m = mt + mt_off[i];
+    const float2* gp = rg + (int64_t)tri_box[i] * npts * C + 24 + 2 * pr;
+    if (ne > 0) {
+      int e = slot;
+      int a0 = e / (e1 * e2), a1 = (e / e2) % e1, a2 = e % e2;
+      for (; e < ne; e += 4) {
+        const float4 g =
+            *reinterpret_cast<const float4*>(gp + (int64_t)(((b0 + a0) * sp + b1 + a1) * sp + b2 + a2) * C);
+        const float mv = m[e];
+        acc.x = fmaf(mv, g.x, acc.x);
+        acc.y = fmaf(mv, g.y, acc.y);
+        acc.z = fmaf(mv, g.z, acc.z);
+        acc.w = fmaf(mv, g.w, acc.w);
+        a2 += 4;
+        while (a2 >= e2) {
+          a2 -= e2;
+          if (++a1 == e1) {
+            a1 = 0;
+            ++a0;
+          }
+        }
+      }
+    }
+  }
+  // lanes hl < 4 sum lanes hl, hl+4, hl+8, hl+12 of their half-warp: the
+  // three components of an RWG (lanes 12..15 hold zeros) or the four entry
+  // slots of a triangle
+  float4 t;
+  t.x = __shfl_down_sync(0xffffffffu, acc.x, 4, 16);
+  t.y = __shfl_down_sync(0xffffffffu, acc.y, 4, 16);
+  t.z = __shfl_down_sync(0xffffffffu, acc.z, 4, 16);
+  t.w = __shfl_down_sync(0xffffffffu, acc.w, 4, 16);
+  float4 v = make_float4(acc.x + t.x, acc.y + t.y, acc.z + t.z, acc.w + t.w);
+  t.x = __shfl_down_sync(0xffffffffu, v.x, 8, 16);
+  t.y = __shfl_down_sync(0xffffffffu, v.y, 8, 16);
+  t.z = __shfl_down_sync(0xffffffffu, v.z, 8, 16);
+  t.w = __shfl_down_sync(0xffffffffu, v.w, 8, 16);
+  v = make_float4(v.x + t.x, v.y + t.y, v.z + t.z, v.w + t.w);
+  if (valid && hl < 4) {
+    double2* out = is_rwg ? yA : u;
+    const int64_t ld = is_rwg ? ldy : ldu;
+    out[(int64_t)(2 * hl) * ld + i] = make_double2((double)v.x, (double)v.y);
+    out[(int64_t)(2 * hl + 1) * ld + i] = make_double2((double)v.z, (double)v.w);
+  }
+}
+
 template <typename R>
 void launch_interp(const R* mr, const int32_t* mr_base, const int32_t* mr_ext, const int64_t* mr_off,
                    const int32_t* rwg_box, int64_t N, const R* mt, const int32_t* mt_base,
@@ -946,6 +1053,15 @@ void launch_interp(const R* mr, const int32_t* mr_base, const int32_t* mr_ext, c
                    const cpx_t<R>* r, int sp, int nr, double2* yA, int64_t ldy, double2* u,
                    int64_t ldu, cudaStream_t s) {
   // nr <= 8 (the far pipeline runs right-hand sides in chunks of at most 8)
+  if constexpr (sizeof(R) == 4) {
+    if (nr == 8) {
+      const int64_t halves = N + Nt;
+      k_interp8<<<(unsigned)ceil_div(halves * 16, 256), 256, 0, s>>>(
+          (const float*)mr, mr_base, mr_ext, mr_off, rwg_box, N, (const float*)mt, mt_base, mt_ext, mt_off, tri_box,
+          Nt, (const float2*)r, sp, yA, ldy, u, ldu);
+      return;
+    }
+  }
   int64_t warps = N + Nt;
   int64_t blocks = ceil_div(warps * 32, 256);
   k_interp<R><<<(unsigned)blocks, 256, 0, s>>>(mr, mr_base, mr_ext, mr_off, rwg_box, N, mt, mt_base, mt_ext,
