@@ -22,6 +22,7 @@ import json
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -197,8 +198,7 @@ def run_ours(args, w, rank, world, local_rank):
     torch.cuda.synchronize()
     n_launch0 = h.launch_count()
     h.profile(True)
-    clocks = ClockSampler(os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
-                                       f"clocks_rank{rank}.csv"))
+    clocks = ClockSampler(os.path.join(args.clocks_dir, f"clocks_rank{rank}.csv"))
     with clocks:
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -282,7 +282,7 @@ def run_ours(args, w, rank, world, local_rank):
                    "diameter_wavelengths": 2 * w["radius"] * w["k"] / (2 * np.pi), "p": w["p"],
                    "grid_spacing_wavelengths": w["delta"] * w["k"] / (2 * np.pi), "grid_levels": w["levels"],
                    "nrhs_per_step": R, "precision": w["precision"], "parallelism": f"replicas{world}",
-                   "l2": "working set >> L2 (no flush)", "setup_s": t_setup,
+                   "l2": "working set >> L2 (no flush)", "setup_s": t_setup, "setup_phases_s": h.setup_times(),
                    "levels": [{k: L[k] for k in ("level", "s", "sb", "shat", "nfft", "n_boxes", "n_far_pairs",
                                                   "n_offsets")} for L in levels],
                    "near_nnz_A": info["near_nnz_A"], "near_nnz_V": info["near_nnz_V"]},
@@ -703,6 +703,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solve", action="store_true")
+    ap.add_argument("--clocks-dir", default=tempfile.gettempdir(),
+                    help="folder for the raw nvidia-smi clock samples of the timed region")
     ap.add_argument("--cpu-worker", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--sample-seed", type=int, default=0, help=argparse.SUPPRESS)
     args = ap.parse_args()

@@ -122,6 +122,21 @@ int efie_plan_matrix(const efie_mesh *mesh, double wavenumber, int spline_degree
                      int level, int which, double *out, int64_t out_len,
                      int32_t *rows, int32_t *cols);
 
+/* Host-only: the exact moments (Q10) of the leaf splines (Eq. TAfactor,
+ * Sec. VI-A) that efie_setup uploads, for a list of basis functions.
+ *   kind 0: RWG edges (canonical edge index, the order of efie_rwg_edges),
+ *           out[i][d][a][b][c] = integral over the RWG support of f_m,d N_abc;
+ *   kind 1: triangles (canonical index), pulse 1/area:
+ *           out[i][a][b][c] = integral over the triangle of N_abc / area.
+ * a, b, c run over the sp splines per axis of the basis function's leaf box
+ * (sp = s + 2 s_b); entries outside the function's support are 0.  out must
+ * hold n_ids * (3 or 1) * sp^3 doubles (out_len); *sp_out returns sp.
+ * EFIE_EINVAL for a bad mesh, parameters, kind or index, or a short buffer. */
+int efie_plan_moments(const efie_mesh *mesh, double wavenumber, int spline_degree,
+                      double grid_spacing, int levels, const efie_options *opt,
+                      int kind, const int32_t *ids, int64_t n_ids, double *out,
+                      int64_t out_len, int32_t *sp_out);
+
 /* Build every setup product on the current device: geometry, octree,
  * transfers, projectors, exact moments (Q10), kernel spectra per level and
  * offset, and the FP64 near field (Sec. VI-A: RWG pairs for A and triangle
@@ -258,6 +273,15 @@ int efie_profile_read(efie_handle *h, int idx, char *name, int name_len, double 
 /* Number of this library's kernel launches issued through h since setup
  * (setup kernels excluded). */
 int efie_launch_count(const efie_handle *h, int64_t *n);
+
+/* Wall-clock seconds of the phases of efie_setup for h, in this order:
+ * 0 host plan (geometry, octree, transfers, projectors, exact moments),
+ * 1 device tables (uploads, transfer groups, translation tiles),
+ * 2 near field (FP64 assembly of A and V, and the double-float split),
+ * 3 far field (gather lists, kernel spectra, per-precision products).
+ * Writes min(n, 4) values to seconds and the phase count to *n_phases (either
+ * pointer may be NULL).  Host memory only; no device work. */
+int efie_setup_times(const efie_handle *h, double *seconds, int n, int *n_phases);
 
 int efie_destroy(efie_handle *h);
 

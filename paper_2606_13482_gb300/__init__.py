@@ -25,13 +25,13 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libefie_gb300.so")
 
 EXPORTED_SYMBOLS = [
-    "efie_plan", "efie_plan_matrix", "efie_setup", "efie_num_unknowns", "efie_plan_info",
+    "efie_plan", "efie_plan_matrix", "efie_plan_moments", "efie_setup", "efie_num_unknowns", "efie_plan_info",
     "efie_rwg_edges", "efie_rhs_planewave", "efie_rhs_planewave_noalloc", "efie_matvec", "efie_matvec_fp64",
     "efie_matvec_parts", "efie_solve", "efie_precond_harvest", "efie_precond_train", "efie_precond_save",
     "efie_precond_load", "efie_precond_enable", "efie_precond_params", "efie_precond_apply",
     "efie_precond_gradient", "efie_autotune", "efie_autotune_set", "efie_batch_create", "efie_batch_matvec",
     "efie_batch_destroy",
-    "efie_profile", "efie_profile_read", "efie_launch_count",
+    "efie_profile", "efie_profile_read", "efie_launch_count", "efie_setup_times",
     "efie_destroy", "efie_last_error",
 ]
 
@@ -93,6 +93,8 @@ def load_library(path: str = LIB_PATH):
                               P(LevelInfo), ctypes.c_int]
     lib.efie_plan_matrix.argtypes = [P(_Mesh), D, ctypes.c_int, D, ctypes.c_int, P(Options), ctypes.c_int,
                                      ctypes.c_int, P(D), I64, P(I32), P(I32)]
+    lib.efie_plan_moments.argtypes = [P(_Mesh), D, ctypes.c_int, D, ctypes.c_int, P(Options), ctypes.c_int,
+                                      P(I32), I64, P(D), I64, P(I32)]
     lib.efie_setup.argtypes = [P(_Mesh), D, ctypes.c_int, D, ctypes.c_int, P(Options), P(VP)]
     lib.efie_num_unknowns.argtypes = [VP, P(I64)]
     lib.efie_plan_info.argtypes = [VP, P(PlanInfo)]
@@ -121,6 +123,7 @@ def load_library(path: str = LIB_PATH):
     lib.efie_profile.argtypes = [VP, ctypes.c_int]
     lib.efie_profile_read.argtypes = [VP, ctypes.c_int, ctypes.c_char_p, ctypes.c_int, P(D), P(I64)]
     lib.efie_launch_count.argtypes = [VP, P(I64)]
+    lib.efie_setup_times.argtypes = [VP, P(D), ctypes.c_int, P(ctypes.c_int)]
     lib.efie_destroy.argtypes = [VP]
     lib.efie_last_error.argtypes = [VP]
     lib.efie_last_error.restype = ctypes.c_char_p
@@ -202,6 +205,27 @@ def plan_matrix(V, T, k, p, grid_spacing, levels, level, which, options: Options
                                      out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), out.size,
                                      None, None))
     return out.reshape(r.value, c.value)
+
+
+def plan_moments(V, T, k, p, grid_spacing, levels, kind, ids, options: Options | None = None):
+    """Host-only exact moments of the leaf splines (efie_plan_moments):
+    kind 0 -> [n, 3, sp, sp, sp] for canonical RWG ids, kind 1 -> [n, sp, sp, sp]
+    for triangle ids, each in the function's leaf box."""
+    lib = load_library()
+    m, keep = _mesh(V, T)
+    ids = np.ascontiguousarray(ids, dtype=np.int32)
+    sp = ctypes.c_int32()
+    opt = ctypes.byref(options) if options else None
+    _check(lib, lib.efie_plan_moments(ctypes.byref(m), k, p, grid_spacing, levels, opt, kind,
+                                      ids.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), ids.size, None, 0,
+                                      ctypes.byref(sp)))
+    s = sp.value
+    ncomp = 3 if kind == 0 else 1
+    out = np.zeros(ids.size * ncomp * s ** 3)
+    _check(lib, lib.efie_plan_moments(ctypes.byref(m), k, p, grid_spacing, levels, opt, kind,
+                                      ids.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), ids.size,
+                                      out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), out.size, None))
+    return out.reshape((ids.size, 3, s, s, s) if kind == 0 else (ids.size, s, s, s))
 
 
 class EFIE:
@@ -389,6 +413,16 @@ class EFIE:
         n = ctypes.c_int64()
         _check(self.lib, self.lib.efie_launch_count(self.h, ctypes.byref(n)), self.h)
         return n.value
+
+    SETUP_PHASES = ("plan", "tables", "near", "far")
+
+    def setup_times(self):
+        """Wall seconds of the setup phases: host plan (with exact moments),
+        device tables, FP64 near-field assembly, far-field products."""
+        t = (ctypes.c_double * 4)()
+        n = ctypes.c_int()
+        _check(self.lib, self.lib.efie_setup_times(self.h, t, 4, ctypes.byref(n)), self.h)
+        return {k: float(t[i]) for i, k in enumerate(self.SETUP_PHASES[:n.value])}
 
     def close(self):
         if getattr(self, "h", None):

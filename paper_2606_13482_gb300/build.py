@@ -59,7 +59,7 @@ def build(verbose: bool = False, ptxas_info: bool = False) -> str:
         obj = os.path.join(BUILD, f + ".o")
         objs.append(obj)
         if _stale(obj, [src] + headers):
-            jobs.append([CXX, "-O2", "-fPIC", "-fopenmp", "-std=c++17", "-c", src, "-o", obj])
+            jobs.append([CXX, "-O3", "-fPIC", "-fopenmp", "-std=c++17", "-c", src, "-o", obj])
     with ThreadPoolExecutor(max_workers=max(1, min(len(jobs), os.cpu_count() or 4))) as ex:
         outs = list(ex.map(_run, jobs))
     if verbose:

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <complex>
 #include <cstring>
@@ -167,6 +168,7 @@ struct efie_handle {
     if (net) efie::nn_delete(net);
   }
   int64_t n_launches = 0;
+  double setup_s[4] = {0, 0, 0, 0};  // efie_setup phases (efie_setup_times)
   Plan plan;
   efie_options opt{};
   int precision = EFIE_FP64;
@@ -630,8 +632,16 @@ void setup_impl(efie_handle* h, const efie_mesh* mesh, double k, int p, double g
   cuda_check(cudaGetDevice(&h->device), "cudaGetDevice");
   h->mem.limit = h->opt.device_mem_limit;
   Plan& P = h->plan;
+  using clk = std::chrono::steady_clock;
+  auto t_mark = clk::now();
+  auto phase_done = [&](int i) {
+    const auto now = clk::now();
+    h->setup_s[i] = std::chrono::duration<double>(now - t_mark).count();
+    t_mark = now;
+  };
   build_plan(P, mesh->xyz, mesh->n_vertices, mesh->tri, mesh->n_triangles, k, p, grid_spacing, levels,
              h->opt.n_splines, true);
+  phase_done(0);
   DevMem& M = h->mem;
   cudaStream_t s = 0;
   // quadrature rules
@@ -785,6 +795,8 @@ void setup_impl(efie_handle* h, const efie_mesh* mesh, double k, int p, double g
     LD.tile_src = M.upload(L.tile_src);
     LD.tile_kidx = M.upload(L.tile_kidx);
   }
+  cuda_check(cudaStreamSynchronize(s), "setup tables");
+  phase_done(1);
   // near field (FP64)
   {
     const Level& LD = P.L(P.D);
@@ -864,6 +876,8 @@ void setup_impl(efie_handle* h, const efie_mesh* mesh, double k, int p, double g
       h->near_df = true;
     }
   }
+  cuda_check(cudaStreamSynchronize(s), "near setup");
+  phase_done(2);
   // far products
   if (h->opt.precond == EFIE_PRECOND_LEARNED && h->opt.weights_path) {
     std::vector<float> w;
@@ -877,6 +891,7 @@ void setup_impl(efie_handle* h, const efie_mesh* mesh, double k, int p, double g
     build_spectra<float>(h, h->f32, K64, s);
   }
   cuda_check(cudaStreamSynchronize(s), "setup");
+  phase_done(3);
 }
 
 // ------------------------------------------------------------- GMRES
@@ -1297,6 +1312,46 @@ int efie_plan_matrix(const efie_mesh* mesh, double wavenumber, int spline_degree
   });
 }
 
+int efie_plan_moments(const efie_mesh* mesh, double wavenumber, int spline_degree, double grid_spacing,
+                      int levels, const efie_options* opt, int kind, const int32_t* ids, int64_t n_ids,
+                      double* out, int64_t out_len, int32_t* sp_out) {
+  return guarded(nullptr, [&] {
+    check_mesh(mesh);
+    if (kind != 0 && kind != 1) throw EfieError{EFIE_EINVAL, "kind must be 0 (RWG) or 1 (triangle)"};
+    if (n_ids < 0 || (n_ids > 0 && !ids)) throw EfieError{EFIE_EINVAL, "ids is NULL"};
+    efie_options o = defaults(opt);
+    Plan P;
+    build_plan(P, mesh->xyz, mesh->n_vertices, mesh->tri, mesh->n_triangles, wavenumber, spline_degree,
+               grid_spacing, levels, o.n_splines, true);
+    const int sp = P.L(P.D).sp;
+    const int ncomp = kind == 0 ? 3 : 1;
+    if (sp_out) *sp_out = sp;
+    if (!out) return EFIE_OK;
+    const int64_t per = (int64_t)ncomp * sp * sp * sp;
+    if (out_len < n_ids * per) throw EfieError{EFIE_EINVAL, "output buffer too small"};
+    const std::vector<int32_t>& perm = kind == 0 ? P.rwg_perm : P.tri_perm;
+    const MomentBlocks& MB = kind == 0 ? P.mom_rwg : P.mom_tri;
+    std::vector<int64_t> rank(perm.size(), -1);
+    for (size_t i = 0; i < perm.size(); ++i) rank[perm[i]] = (int64_t)i;
+    std::fill(out, out + n_ids * per, 0.0);
+    for (int64_t j = 0; j < n_ids; ++j) {
+      if (ids[j] < 0 || ids[j] >= (int64_t)rank.size()) throw EfieError{EFIE_EINVAL, "index out of range"};
+      const int64_t i = rank[ids[j]];
+      const int* b = &MB.base[3 * i];
+      const int* e = &MB.ext[3 * i];
+      const double* src = &MB.data[MB.off[i]];
+      double* dst = out + j * per;
+      for (int c = 0; c < ncomp; ++c)
+        for (int a0 = 0; a0 < e[0]; ++a0)
+          for (int a1 = 0; a1 < e[1]; ++a1)
+            for (int a2 = 0; a2 < e[2]; ++a2)
+              dst[(((int64_t)c * sp + b[0] + a0) * sp + b[1] + a1) * sp + b[2] + a2] =
+                  src[(((int64_t)c * e[0] + a0) * e[1] + a1) * e[2] + a2];
+    }
+    return EFIE_OK;
+  });
+}
+
 int efie_setup(const efie_mesh* mesh, double wavenumber, int spline_degree, double grid_spacing, int levels,
                const efie_options* opt, efie_handle** out) {
   if (!out) {
@@ -1439,6 +1494,14 @@ int efie_profile_read(efie_handle* h, int idx, char* name, int name_len, double*
 int efie_launch_count(const efie_handle* h, int64_t* n) {
   if (!h || !n) return EFIE_EINVAL;
   *n = h->n_launches;
+  return EFIE_OK;
+}
+
+int efie_setup_times(const efie_handle* h, double* seconds, int n, int* n_phases) {
+  if (!h || n < 0) return EFIE_EINVAL;
+  for (int i = 0; i < std::min(n, 4); ++i)
+    if (seconds) seconds[i] = h->setup_s[i];
+  if (n_phases) *n_phases = 4;
   return EFIE_OK;
 }
 

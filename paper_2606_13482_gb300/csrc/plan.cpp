@@ -356,16 +356,29 @@ int find_span(const std::vector<double>& U, int p, int ns, double x) {
   return lo;
 }
 
-// nonzero B-splines i-p..i at x in span i (triangular recursion)
-void basis_nz(const std::vector<double>& U, int p, int i, double x, double* N) {
+// The nonzero B-splines N_{i-p..i}(x) in span i come from the triangular
+// recursion (Cox-de Boor).  Its denominators
+// (x - U[i+1-j+r]) + (U[i+r+1] - x) = U[i+r+1] - U[i+1-j+r] do not depend on
+// x and are positive for a nonempty span, so their reciprocals are taken once
+// per span.
+static void span_recip(const std::vector<double>& U, int p, int i, double* inv) {
+  int k = 0;
+  for (int j = 1; j <= p; ++j)
+    for (int r = 0; r < j; ++r) inv[k++] = 1.0 / (U[i + r + 1] - U[i + 1 - j + r]);
+}
+
+// N[0..p] = N_{i-p..i}(x), with the reciprocals of span_recip
+static inline void basis_nz_r(const std::vector<double>& U, int p, int i, const double* inv, double x,
+                              double* N) {
   double left[8], right[8];
   N[0] = 1.0;
+  int k = 0;
   for (int j = 1; j <= p; ++j) {
     left[j] = x - U[i + 1 - j];
     right[j] = U[i + j] - x;
     double saved = 0.0;
     for (int r = 0; r < j; ++r) {
-      double tmp = N[r] / (right[r + 1] + left[j - r]);
+      double tmp = N[r] * inv[k++];
       N[r] = saved + right[r + 1] * tmp;
       saved = left[j - r] * tmp;
     }
@@ -373,42 +386,106 @@ void basis_nz(const std::vector<double>& U, int p, int i, double x, double* N) {
   }
 }
 
-// Integrate sum_q w_q f_c(x_q) l_i(x_q) over one triangle (clipped by knot
-// planes) into block[ncomp][e0][e1][e2] at base. f: RWG (ncomp 3) or pulse.
-void integrate_triangle(const LeafKnots& K, const double* tv, int ncomp, const double* xfree,
-                        double scale, const int* base, const int* ext, double* block,
-                        const std::vector<double>& qx, const std::vector<double>& qw) {
-  const int p = K.p, sp = K.sp;
-  std::vector<Poly> pieces(1);
+// T[i0][i1][c][i2] = sum_q NN[i0 p1 + i1][q] F[q][c][i2]: the sum over a
+// piece's quadrature points of the rank-one products N_i0 N_i1 (f_c N_i2),
+// one output row at a time so that the row stays in registers.
+template <int P1>
+static void contract_rows(const double* __restrict NN, const double* __restrict F, int Q, int ld,
+                          double* __restrict T) {
+  constexpr int W = 4 * P1;
+  for (int ii = 0; ii < P1 * P1; ++ii) {
+    double row[W];
+    for (int j = 0; j < W; ++j) row[j] = 0.0;
+    const double* nn = NN + (size_t)ii * ld;
+    for (int q = 0; q < Q; ++q) {
+      const double a = nn[q];
+      const double* f = F + (size_t)q * W;
+      for (int j = 0; j < W; ++j) row[j] += a * f[j];
+    }
+    for (int j = 0; j < W; ++j) T[ii * W + j] = row[j];
+  }
+}
+using contract_fn = void (*)(const double*, const double*, int, int, double*);
+static contract_fn contract_for(int p1) {
+  switch (p1) {
+    case 2: return contract_rows<2>;
+    case 3: return contract_rows<3>;
+    case 4: return contract_rows<4>;
+    case 5: return contract_rows<5>;
+    case 6: return contract_rows<6>;
+    default: return contract_rows<7>;
+  }
+}
+
+// Moments of one triangle against the splines of one leaf box.  The triangle
+// is clipped by every interior knot plane, so each piece lies in one knot
+// cell per axis and meets (p+1)^3 splines; its spans are found once, at the
+// piece's vertex mean.  Each piece's fan triangles take the collapsed Gauss
+// rule, and the piece keeps the tile
+//   T[i0][i1][c][i2] = sum_q w_q f_c(x_q) N_i0(x_q) N_i1(y_q) N_i2(z_q),
+// f_0 = 1 and f_{1+d} = x_d - o_d (o: the triangle's vertex mean), from which
+// every RWG and pulse moment of the triangle is a linear combination.
+struct PieceTile {
+  int span[3];
+  double t[8 * 8 * 4 * 8];
+};
+
+void triangle_tiles(const LeafKnots& K, const double* tv, const double* o,
+                    const std::vector<double>& qx, const std::vector<double>& qw,
+                    std::vector<PieceTile>& out) {
+  const int p = K.p, sp = K.sp, p1 = p + 1;
+  thread_local std::vector<Poly> pieces;
+  pieces.resize(1);
   pieces[0].n = 3;
   for (int a = 0; a < 3; ++a)
     for (int d = 0; d < 3; ++d) pieces[0].v[a][d] = tv[3 * a + d];
+  Poly L, R;
   for (int axis = 0; axis < 3; ++axis) {
     for (int kk = p + 1; kk < sp; ++kk) {
-      double val = K.U[axis][kk];
-      std::vector<Poly> nxt;
-      for (const Poly& P : pieces) {
+      const double val = K.U[axis][kk];
+      const size_t n0 = pieces.size();
+      for (size_t i = 0; i < n0; ++i) {
+        const Poly& P = pieces[i];
         double mn = 1e300, mx = -1e300;
-        for (int i = 0; i < P.n; ++i) {
-          mn = std::min(mn, P.v[i][axis]);
-          mx = std::max(mx, P.v[i][axis]);
+        for (int j = 0; j < P.n; ++j) {
+          mn = std::min(mn, P.v[j][axis]);
+          mx = std::max(mx, P.v[j][axis]);
         }
-        if (mn < val && val < mx) {
-          Poly L, R;
-          split(P, axis, val, L, R);
-          if (L.n >= 3) nxt.push_back(L);
-          if (R.n >= 3) nxt.push_back(R);
+        if (!(mn < val && val < mx)) continue;
+        split(P, axis, val, L, R);
+        if (L.n >= 3) {
+          pieces[i] = L;
+          if (R.n >= 3) pieces.push_back(R);
+        } else if (R.n >= 3) {
+          pieces[i] = R;
         } else {
-          nxt.push_back(P);
+          pieces[i].n = 0;  // nothing left of this piece
         }
       }
-      pieces.swap(nxt);
     }
   }
   const int nq = (int)qx.size();
-  const int e0 = ext[0], e1 = ext[1], e2 = ext[2];
+  const contract_fn contract = contract_for(p1);
+  const int W = 4 * p1;
+  thread_local std::vector<double> NN, F;
   double N0[8], N1[8], N2[8];
+  out.clear();
   for (const Poly& P : pieces) {
+    if (P.n < 3) continue;
+    double cen[3] = {0, 0, 0};
+    for (int i = 0; i < P.n; ++i)
+      for (int d = 0; d < 3; ++d) cen[d] += P.v[i][d];
+    for (int d = 0; d < 3; ++d) cen[d] /= P.n;
+    int span[3];
+    for (int d = 0; d < 3; ++d) span[d] = find_span(K.U[d], p, sp, cen[d]);
+    double r0[28], r1[28], r2[28];
+    span_recip(K.U[0], p, span[0], r0);
+    span_recip(K.U[1], p, span[1], r1);
+    span_recip(K.U[2], p, span[2], r2);
+    const int ld = (P.n - 2) * nq * nq;
+    if ((int)NN.size() < p1 * p1 * ld) NN.resize((size_t)p1 * p1 * ld);
+    if ((int)F.size() < W * ld) F.resize((size_t)W * ld);
+    int Q = 0;
     for (int f = 1; f + 1 < P.n; ++f) {
       const double* A = P.v[0];
       const double* B = P.v[f];
@@ -423,39 +500,59 @@ void integrate_triangle(const LeafKnots& K, const double* tv, int ncomp, const d
       double twoa = std::sqrt(cx * cx + cy * cy + cz * cz);
       if (!(twoa > 0)) continue;
       for (int a = 0; a < nq; ++a)
-        for (int b = 0; b < nq; ++b) {
+        for (int b = 0; b < nq; ++b, ++Q) {
           double xi = qx[a], eta = qx[b] * (1.0 - qx[a]);
-          double w = qw[a] * qw[b] * (1.0 - qx[a]) * twoa * scale;
+          double w = qw[a] * qw[b] * (1.0 - qx[a]) * twoa;
           double x[3];
           for (int d = 0; d < 3; ++d) x[d] = A[d] + xi * u[d] + eta * v[d];
-          int s0 = find_span(K.U[0], p, sp, x[0]);
-          int s1 = find_span(K.U[1], p, sp, x[1]);
-          int s2 = find_span(K.U[2], p, sp, x[2]);
-          basis_nz(K.U[0], p, s0, x[0], N0);
-          basis_nz(K.U[1], p, s1, x[1], N1);
-          basis_nz(K.U[2], p, s2, x[2], N2);
-          double fv[3];
-          if (ncomp == 3)
-            for (int d = 0; d < 3; ++d) fv[d] = w * (x[d] - xfree[d]);
-          else
-            fv[0] = w;
-          for (int i0 = 0; i0 <= p; ++i0) {
-            int g0 = s0 - p + i0 - base[0];
-            if (g0 < 0 || g0 >= e0) continue;
-            for (int i1 = 0; i1 <= p; ++i1) {
-              int g1 = s1 - p + i1 - base[1];
-              if (g1 < 0 || g1 >= e1) continue;
-              double n01 = N0[i0] * N1[i1];
-              for (int i2 = 0; i2 <= p; ++i2) {
-                int g2 = s2 - p + i2 - base[2];
-                if (g2 < 0 || g2 >= e2) continue;
-                double bb = n01 * N2[i2];
-                size_t o = ((size_t)g0 * e1 + g1) * e2 + g2;
-                for (int c = 0; c < ncomp; ++c) block[(size_t)c * e0 * e1 * e2 + o] += fv[c] * bb;
-              }
-            }
+          basis_nz_r(K.U[0], p, span[0], r0, x[0], N0);
+          basis_nz_r(K.U[1], p, span[1], r1, x[1], N1);
+          basis_nz_r(K.U[2], p, span[2], r2, x[2], N2);
+          for (int i0 = 0; i0 < p1; ++i0)
+            for (int i1 = 0; i1 < p1; ++i1) NN[(size_t)(i0 * p1 + i1) * ld + Q] = N0[i0] * N1[i1];
+          double* fq = &F[(size_t)Q * W];
+          for (int i2 = 0; i2 < p1; ++i2) fq[i2] = w * N2[i2];
+          for (int d = 0; d < 3; ++d) {
+            const double xd = x[d] - o[d];
+            for (int i2 = 0; i2 < p1; ++i2) fq[(1 + d) * p1 + i2] = xd * fq[i2];
           }
         }
+    }
+    if (Q == 0) continue;
+    out.emplace_back();
+    PieceTile& T = out.back();
+    for (int d = 0; d < 3; ++d) T.span[d] = span[d];
+    contract(NN.data(), F.data(), Q, ld, T.t);
+  }
+}
+
+// block[c][g] += sum_k coef[c][k] T[..][k][..] over the tiles of one triangle
+// for a basis function with block origin base and extents ext; ncomp rows of
+// coef, each over the 4 tile components.
+void scatter_tiles(const std::vector<PieceTile>& tiles, int p, int ncomp, const double* coef,
+                   const int* base, const int* ext, double* block) {
+  const int p1 = p + 1;
+  const int e0 = ext[0], e1 = ext[1], e2 = ext[2];
+  const size_t cstride = (size_t)e0 * e1 * e2;
+  for (const PieceTile& T : tiles) {
+    for (int i0 = 0; i0 < p1; ++i0) {
+      const int g0 = T.span[0] - p + i0 - base[0];
+      if (g0 < 0 || g0 >= e0) continue;
+      for (int i1 = 0; i1 < p1; ++i1) {
+        const int g1 = T.span[1] - p + i1 - base[1];
+        if (g1 < 0 || g1 >= e1) continue;
+        const double* t = T.t + (i0 * p1 + i1) * 4 * p1;
+        for (int i2 = 0; i2 < p1; ++i2) {
+          const int g2 = T.span[2] - p + i2 - base[2];
+          if (g2 < 0 || g2 >= e2) continue;
+          const size_t o = ((size_t)g0 * e1 + g1) * e2 + g2;
+          for (int c = 0; c < ncomp; ++c) {
+            const double* cc = coef + 4 * c;
+            block[c * cstride + o] += cc[0] * t[i2] + cc[1] * t[p1 + i2] + cc[2] * t[2 * p1 + i2] +
+                                      cc[3] * t[3 * p1 + i2];
+          }
+        }
+      }
     }
   }
 }
@@ -913,21 +1010,6 @@ void build_plan(Plan& P, const double* xyz, int64_t nv, const int32_t* tri, int6
       MR.off[i + 1] = MR.off[i] + 3LL * MR.ext[3 * i] * MR.ext[3 * i + 1] * MR.ext[3 * i + 2];
     }
     MR.data.assign(MR.off[N], 0.0);
-#pragma omp parallel for schedule(dynamic, 64)
-    for (int64_t i = 0; i < N; ++i) {
-      int32_t m = P.rwg_perm[i];
-      const LeafKnots& K = kcache[P.rwg_box[i]];
-      for (int s = 0; s < 2; ++s) {
-        int32_t t = g.tri_pm[2 * m + s];
-        double tv[9];
-        for (int a = 0; a < 3; ++a)
-          for (int d = 0; d < 3; ++d) tv[3 * a + d] = g.V[3 * g.T[3 * t + a] + d];
-        const double* xf = &g.V[3 * g.free_pm[2 * m + s]];
-        double scale = (s == 0 ? 1.0 : -1.0) / (2.0 * g.area[t]);
-        integrate_triangle(K, tv, 3, xf, scale, &MR.base[3 * i], &MR.ext[3 * i],
-                           &MR.data[MR.off[i]], qx, qw);
-      }
-    }
     MomentBlocks& MT = P.mom_tri;
     MT.base.assign(3 * nt, 0);
     MT.ext.assign(3 * nt, 0);
@@ -938,15 +1020,53 @@ void build_plan(Plan& P, const double* xyz, int64_t nv, const int32_t* tri, int6
       MT.off[i + 1] = MT.off[i] + (int64_t)MT.ext[3 * i] * MT.ext[3 * i + 1] * MT.ext[3 * i + 2];
     }
     MT.data.assign(MT.off[nt], 0.0);
-#pragma omp parallel for schedule(dynamic, 64)
-    for (int64_t i = 0; i < nt; ++i) {
-      int32_t t = P.tri_perm[i];
-      const LeafKnots& K = kcache[P.tri_box[i]];
-      double tv[9];
-      for (int a = 0; a < 3; ++a)
-        for (int d = 0; d < 3; ++d) tv[3 * a + d] = g.V[3 * g.T[3 * t + a] + d];
-      integrate_triangle(K, tv, 1, nullptr, 1.0 / g.area[t], &MT.base[3 * i], &MT.ext[3 * i],
-                         &MT.data[MT.off[i]], qx, qw);
+    // One leaf box at a time: every triangle used by the box's RWGs or pulses
+    // is integrated once against the box's splines, and the tiles are
+    // combined into each user's block.  Only the box's own blocks are written.
+#pragma omp parallel
+    {
+      std::vector<PieceTile> tiles;
+      std::vector<int32_t> tris;
+#pragma omp for schedule(dynamic, 4)
+      for (int64_t b = 0; b < (int64_t)BD; ++b) {
+        const LeafKnots& K = kcache[b];
+        tris.clear();
+        for (int64_t i = P.box_rwg_ptr[b]; i < P.box_rwg_ptr[b + 1]; ++i)
+          for (int s = 0; s < 2; ++s) tris.push_back(g.tri_pm[2 * P.rwg_perm[i] + s]);
+        for (int64_t i = P.box_tri_ptr[b]; i < P.box_tri_ptr[b + 1]; ++i) tris.push_back(P.tri_perm[i]);
+        std::sort(tris.begin(), tris.end());
+        tris.erase(std::unique(tris.begin(), tris.end()), tris.end());
+        for (int32_t t : tris) {
+          double tv[9], o[3] = {0, 0, 0};
+          for (int a = 0; a < 3; ++a)
+            for (int d = 0; d < 3; ++d) {
+              tv[3 * a + d] = g.V[3 * g.T[3 * t + a] + d];
+              o[d] += tv[3 * a + d] / 3.0;
+            }
+          triangle_tiles(K, tv, o, qx, qw, tiles);
+          // RWGs of the box on this triangle: sigma / (2a) (x - x_free)
+          for (int64_t i = P.box_rwg_ptr[b]; i < P.box_rwg_ptr[b + 1]; ++i) {
+            const int32_t m = P.rwg_perm[i];
+            for (int s = 0; s < 2; ++s) {
+              if (g.tri_pm[2 * m + s] != t) continue;
+              const double* xf = &g.V[3 * g.free_pm[2 * m + s]];
+              const double sc = (s == 0 ? 1.0 : -1.0) / (2.0 * g.area[t]);
+              double coef[12] = {0};
+              for (int d = 0; d < 3; ++d) {
+                coef[4 * d] = sc * (o[d] - xf[d]);
+                coef[4 * d + 1 + d] = sc;
+              }
+              scatter_tiles(tiles, p, 3, coef, &MR.base[3 * i], &MR.ext[3 * i], &MR.data[MR.off[i]]);
+            }
+          }
+          // the pulse of this triangle, if it belongs to the box: 1 / a
+          const int64_t ti = P.tri_rank[t];
+          if (P.tri_box[ti] == (int32_t)b) {
+            const double coef[4] = {1.0 / g.area[t], 0, 0, 0};
+            scatter_tiles(tiles, p, 1, coef, &MT.base[3 * ti], &MT.ext[3 * ti], &MT.data[MT.off[ti]]);
+          }
+        }
+      }
     }
   }
 }

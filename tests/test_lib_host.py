@@ -84,6 +84,38 @@ def test_plan_matrices_match_oracle(lib):
                 assert np.abs(G.plan_matrix(V, T, k, p, delta, levels, ell, 2) - CR).max() < 1e-14
 
 
+def test_plan_moments_match_oracle(lib):
+    """Exact leaf-spline moments (Q10) built by the library's host planner
+    (each triangle clipped and integrated once per leaf box, its tiles shared
+    by its RWGs and its pulse) against the oracle's per-function clipping and
+    collapsed Gauss rule, for p = 2, 3, 5."""
+    G, _ = lib
+    from oracle.geometry import build_rwg
+    from oracle.moments import pulse_moments, rwg_moments
+    from oracle.tree import build_tree
+    rng = np.random.default_rng(11)
+    for (freq, r, k, p, delta, levels) in [(8, 0.5, 2 * np.pi, 3, 0.1, 2), (10, 0.5, 2 * np.pi * 1.7, 2, 0.08, 3),
+                                           (8, 0.5, 2 * np.pi, 5, 0.1, 1)]:
+        V, T = E.icosphere(freq, r)
+        m = build_rwg(V, T)
+        keys = m.edges[:, 0].astype(np.int64) * len(V) + m.edges[:, 1]
+        assert np.all(np.diff(keys) > 0)  # canonical order: edges sorted by (lo, hi)
+        tr = build_tree(m, k, p, delta, levels)
+        ids = rng.choice(m.N, 48, replace=False).astype(np.int32)
+        ref = rwg_moments(m, tr, ids)
+        got = G.plan_moments(V, T, k, p, delta, levels, 0, ids)
+        assert got.shape == ref.shape
+        assert np.abs(got - ref).max() < 1e-13 * np.abs(ref).max()
+        tids = rng.choice(m.Nt, 48, replace=False).astype(np.int32)
+        ref = pulse_moments(m, tr, tids)
+        got = G.plan_moments(V, T, k, p, delta, levels, 1, tids)
+        assert np.abs(got - ref).max() < 1e-13 * np.abs(ref).max()
+    with pytest.raises(G.EfieError):
+        G.plan_moments(V, T, k, p, delta, levels, 2, ids)
+    with pytest.raises(G.EfieError):
+        G.plan_moments(V, T, k, p, delta, levels, 1, np.array([m.Nt], np.int32))
+
+
 def test_invalid_inputs(lib):
     G, _ = lib
     V, T = E.icosphere(4, 0.5)
