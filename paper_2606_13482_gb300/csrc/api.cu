@@ -835,11 +835,26 @@ void setup_impl(efie_handle* h, const efie_mesh* mesh, double k, int p, double g
     const int64_t scr_cap = (int64_t)(1LL << 30) / (10 * 16);  // pairs per batch (~1 GiB)
     double2* scratch = nullptr;
     int64_t* d_scr_off = M.alloc<int64_t>(nblk + 1);
-    int64_t max_pairs = 1;
+    // T is symmetric: blocks (x, y) with x > y are copied as transposes of
+    // (y, x) instead of being integrated.
+    std::vector<int64_t> mir_blk, mir_src;
     for (int64_t j = 0; j < nblk; ++j) {
-      int32_t x = tgt[j], y = P.near_src[j];
-      max_pairs = std::max(max_pairs, (P.tset_ptr[x + 1] - P.tset_ptr[x]) * (P.tset_ptr[y + 1] - P.tset_ptr[y]));
+      const int32_t x = tgt[j], y = P.near_src[j];
+      if (x <= y) continue;
+      int64_t jm = -1;
+      for (int64_t q = P.near_ptr[y]; q < P.near_ptr[y + 1]; ++q)
+        if (P.near_src[q] == x) jm = q;
+      if (jm < 0) throw EfieError{EFIE_EINVAL, "internal: near list is not symmetric"};
+      mir_blk.push_back(j);
+      mir_src.push_back(jm);
     }
+    int64_t max_pairs = 1;
+    auto n_pairs = [&](int64_t j) -> int64_t {
+      const int32_t x = tgt[j], y = P.near_src[j];
+      if (x > y) return 0;
+      return (P.tset_ptr[x + 1] - P.tset_ptr[x]) * (P.tset_ptr[y + 1] - P.tset_ptr[y]);
+    };
+    for (int64_t j = 0; j < nblk; ++j) max_pairs = std::max(max_pairs, n_pairs(j));
     int64_t cap = std::max(scr_cap, max_pairs);
     scratch = M.alloc<double2>(10 * cap);
     int64_t j0 = 0;
@@ -848,8 +863,7 @@ void setup_impl(efie_handle* h, const efie_mesh* mesh, double k, int p, double g
       scr_off.assign(1, 0);
       int64_t j1 = j0;
       while (j1 < nblk) {
-        int32_t x = tgt[j1], y = P.near_src[j1];
-        int64_t np = (P.tset_ptr[x + 1] - P.tset_ptr[x]) * (P.tset_ptr[y + 1] - P.tset_ptr[y]);
+        const int64_t np = n_pairs(j1);
         if (scr_off.back() + np > cap && j1 > j0) break;
         scr_off.push_back(scr_off.back() + np);
         ++j1;
@@ -867,6 +881,19 @@ void setup_impl(efie_handle* h, const efie_mesh* mesh, double k, int p, double g
     for (int64_t e0 = 0; e0 < P.nnzV; e0 += vchunk) {
       launch_near_V(nd, e0, std::min(vchunk, P.nnzV - e0), s);
       cuda_check(cudaStreamSynchronize(s), "near V assembly");
+    }
+    {
+      const int64_t nm = (int64_t)mir_blk.size();
+      int64_t* d_mir = M.alloc<int64_t>(2 * std::max<int64_t>(nm, 1));
+      if (nm) {
+        cuda_check(cudaMemcpy(d_mir, mir_blk.data(), sizeof(int64_t) * nm, cudaMemcpyHostToDevice), "mirror list");
+        cuda_check(cudaMemcpy(d_mir + nm, mir_src.data(), sizeof(int64_t) * nm, cudaMemcpyHostToDevice),
+                   "mirror list");
+      }
+      launch_near_mirror(nd.A, nd.blkA_off, nd.box_rwg_ptr, nd.blk_tgt, nd.near_src, d_mir, d_mir + nm, nm, s);
+      launch_near_mirror(nd.Vn, nd.blkV_off, nd.box_tri_ptr, nd.blk_tgt, nd.near_src, d_mir, d_mir + nm, nm, s);
+      cuda_check(cudaStreamSynchronize(s), "near mirror");
+      M.release(d_mir);
     }
     if (h->precision == EFIE_MIXED) {
       // keep the FP64-assembled values as double-float pairs (in place)

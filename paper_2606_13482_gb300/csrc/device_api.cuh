@@ -34,6 +34,8 @@ struct NearDev {
   double2* A;               // [nnzA]
   double2* Vn;              // [nnzV]
 };
+// Blocks (x, y) with x > y are not integrated: T is symmetric, so they are the
+// transposes of the (y, x) blocks, copied by launch_near_mirror.
 
 int near_upload_rules(const double* q3, const double* q4);
 void launch_near_pairs_A(const NearDev& nd, int64_t j0, int64_t nblk, const int64_t* scr_off,
@@ -41,6 +43,11 @@ void launch_near_pairs_A(const NearDev& nd, int64_t j0, int64_t nblk, const int6
 void launch_near_combine_A(const NearDev& nd, int64_t j0, int64_t nblk, const int64_t* scr_off,
                            const double2* scratch, int64_t e_begin, int64_t total, cudaStream_t s);
 void launch_near_V(const NearDev& nd, int64_t e_begin, int64_t total, cudaStream_t s);
+// M[blk] = M[mirror]^T for the n listed blocks (column-major blocks; box_ptr:
+// the per-box function ranges that size them).
+void launch_near_mirror(double2* M, const int64_t* blk_off, const int64_t* box_ptr, const int32_t* blk_tgt,
+                        const int32_t* near_src, const int64_t* mir_blk, const int64_t* mir_src, int64_t n,
+                        cudaStream_t s);
 void launch_near_spmv(const double2* M, const int64_t* blk_off, const int64_t* near_ptr,
                       const int32_t* near_src, const int64_t* box_ptr, int64_t n_boxes,
                       const double2* x, double2* y, int64_t ld, int nr, cudaStream_t s);

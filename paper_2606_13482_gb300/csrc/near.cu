@@ -340,6 +340,7 @@ __global__ void k_near_combine_A(NearDev nd, int64_t j0, int64_t nblk, const int
   int64_t eg = e_begin + e;
   int64_t j = find_block(nd.blkA_off + j0, nblk, eg) + j0;
   int32_t x = nd.blk_tgt[j], y = nd.near_src[j];
+  if (x > y) return;  // transpose of block (y, x): k_near_mirror
   int64_t nxr = nd.box_rwg_ptr[x + 1] - nd.box_rwg_ptr[x];
   int64_t loc = eg - nd.blkA_off[j];
   int64_t c = loc / nxr, r = loc - c * nxr;  // column-major block
@@ -365,6 +366,7 @@ __global__ void k_near_V(NearDev nd, int64_t e_begin, int64_t total) {
   int64_t eg = e_begin + e;
   int64_t j = find_block(nd.blkV_off, nd.n_blocks, eg);
   int32_t x = nd.blk_tgt[j], y = nd.near_src[j];
+  if (x > y) return;  // transpose of block (y, x): k_near_mirror
   int64_t nxt = nd.box_tri_ptr[x + 1] - nd.box_tri_ptr[x];
   int64_t loc = eg - nd.blkV_off[j];
   int64_t b = loc / nxt, a = loc - b * nxt;  // column-major block
@@ -374,6 +376,39 @@ __global__ void k_near_V(NearDev nd, int64_t e_begin, int64_t total) {
   pair_integrals(nd.V, nd.T, ta, tb, nd.k, false, I0, dummy);
   double s = 1.0 / (nd.area[ta] * nd.area[tb]);
   nd.Vn[eg] = make_double2(I0.x * s, I0.y * s);
+}
+
+// Block (x, y) = transpose of block (y, x).  Block j is column-major
+// [ny][nx] (entry (r, c) at c nx + r, r over the functions of x, c over those
+// of y); its mirror is [nx][ny], entry (c, r) at r ny + c.  One CTA per listed
+// block, 32 x 32 tiles through shared memory so that both the reads and the
+// writes are coalesced.
+__global__ void __launch_bounds__(256)
+k_near_mirror(double2* __restrict__ M, const int64_t* __restrict__ blk_off, const int64_t* __restrict__ box_ptr,
+              const int32_t* __restrict__ blk_tgt, const int32_t* __restrict__ near_src,
+              const int64_t* __restrict__ mir_blk, const int64_t* __restrict__ mir_src) {
+  __shared__ double2 tile[32][33];
+  const int64_t j = mir_blk[blockIdx.x], jm = mir_src[blockIdx.x];
+  const int32_t x = blk_tgt[j], y = near_src[j];
+  const int nx = (int)(box_ptr[x + 1] - box_ptr[x]), ny = (int)(box_ptr[y + 1] - box_ptr[y]);
+  double2* dst = M + blk_off[j];
+  const double2* src = M + blk_off[jm];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int c0 = 0; c0 < ny; c0 += 32)
+    for (int r0 = 0; r0 < nx; r0 += 32) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int r = r0 + ty + 8 * k, c = c0 + tx;
+        if (r < nx && c < ny) tile[ty + 8 * k][tx] = src[(int64_t)r * ny + c];
+      }
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int c = c0 + ty + 8 * k, r = r0 + tx;
+        if (r < nx && c < ny) dst[(int64_t)c * nx + r] = tile[tx][ty + 8 * k];
+      }
+      __syncthreads();
+    }
 }
 
 // ---------------------------------------------------------------- SpMV
@@ -711,6 +746,12 @@ void launch_near_combine_A(const NearDev& nd, int64_t j0, int64_t nblk, const in
 void launch_near_V(const NearDev& nd, int64_t e_begin, int64_t total, cudaStream_t s) {
   if (total <= 0) return;
   k_near_V<<<(unsigned)ceil_div(total, 128), 128, 0, s>>>(nd, e_begin, total);
+}
+void launch_near_mirror(double2* M, const int64_t* blk_off, const int64_t* box_ptr, const int32_t* blk_tgt,
+                        const int32_t* near_src, const int64_t* mir_blk, const int64_t* mir_src, int64_t n,
+                        cudaStream_t s) {
+  if (n <= 0) return;
+  k_near_mirror<<<(unsigned)n, 256, 0, s>>>(M, blk_off, box_ptr, blk_tgt, near_src, mir_blk, mir_src);
 }
 void launch_near_spmv(const double2* M, const int64_t* blk_off, const int64_t* near_ptr,
                       const int32_t* near_src, const int64_t* box_ptr, int64_t n_boxes,
