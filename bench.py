@@ -163,6 +163,20 @@ def grid_bytes(info, levels, nrhs, vb):
     return out
 
 
+def job_rate(local_s, units_per_rank, world, dist, device):
+    """Whole-job throughput of `world` replicas that each processed
+    units_per_rank units in local_s seconds: the slowest rank's time (MAX over
+    ranks after a barrier) divides the units of all ranks.  Returns
+    (units per second, max seconds)."""
+    import torch
+    t = torch.tensor([float(local_s)], dtype=torch.float64, device=device)
+    if dist:
+        dist.barrier()
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_s = float(t.item())
+    return units_per_rank * world / total_s, total_s
+
+
 def run_ours(args, w, rank, world, local_rank):
     import torch
     import __graft_entry__ as g
@@ -211,12 +225,7 @@ def run_ours(args, w, rank, world, local_rank):
     n_launch = h.launch_count() - n_launch0
     prof = h.profile_read()
     ms = e0.elapsed_time(e1)
-    t_dev = torch.tensor([ms / 1000.0], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.barrier()
-        dist.all_reduce(t_dev, op=dist.ReduceOp.MAX)
-    total_s = float(t_dev.item())
-    value = R * world * args.steps / total_s
+    value, total_s = job_rate(ms / 1000.0, R * args.steps, world, dist, "cuda")
     # end-to-end through the C ABI with host buffers (pinned H2D, matvec, D2H)
     e2e = None
     if not args.no_e2e:
@@ -229,10 +238,8 @@ def run_ours(args, w, rank, world, local_rank):
             h.matvec(x, y)
             yh.copy_(y, non_blocking=True)
         torch.cuda.synchronize()
-        te = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device="cuda")
-        if dist:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
-        e2e = {"value": R * world * max(1, args.steps) / float(te.item()), "unit": "matvecs/s",
+        e2e_rate, _ = job_rate(time.perf_counter() - t0, R * max(1, args.steps), world, dist, "cuda")
+        e2e = {"value": e2e_rate, "unit": "matvecs/s",
                "h2d_bytes_per_step": int(xh.numel() * 16), "d2h_bytes_per_step": int(yh.numel() * 16)}
     # roofline of the dominant kernel class
     alg = algorithmic(w, info, levels, R)
