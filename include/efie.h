@@ -180,6 +180,18 @@ int efie_rhs_planewave_noalloc(efie_handle *h, int n_rhs, const double *khat, co
  * near field. */
 int efie_matvec(efie_handle *h, const void *x, void *y, int n_rhs, void *stream);
 
+/* y = T x with x and y in HOST memory (c128 [n_rhs][N]), the same product as
+ * efie_matvec.  The right-hand sides go through the device in chunks of the
+ * handle's chunk size, double-buffered: the copy-in of one chunk and the
+ * copy-out of the previous one overlap the product of the current one, on two
+ * copy streams of the handle, ordered after the caller's earlier work on
+ * `stream`.  The call returns once the work is queued; y is complete when
+ * `stream` has been synchronized.  x and y should be page-locked (pinned) for
+ * the copies to overlap; pageable memory gives the same result without
+ * overlap.  The handle keeps 2 x 2 staging buffers of chunk x N entries from
+ * the first call until efie_destroy.  Calls on one handle must not overlap. */
+int efie_matvec_host(efie_handle *h, const void *x_host, void *y_host, int n_rhs, void *stream);
+
 /* Same product computed in FP64 regardless of the handle's precision (the
  * plain FP64 form used for true residuals).  Needs FP64 setup products, which
  * EFIE_MIXED handles keep alongside the FP32 ones. */

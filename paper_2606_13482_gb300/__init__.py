@@ -26,7 +26,8 @@ LIB_PATH = os.path.join(HERE, "libefie_gb300.so")
 
 EXPORTED_SYMBOLS = [
     "efie_plan", "efie_plan_matrix", "efie_plan_moments", "efie_setup", "efie_num_unknowns", "efie_plan_info",
-    "efie_rwg_edges", "efie_rhs_planewave", "efie_rhs_planewave_noalloc", "efie_matvec", "efie_matvec_fp64",
+    "efie_rwg_edges", "efie_rhs_planewave", "efie_rhs_planewave_noalloc", "efie_matvec", "efie_matvec_host",
+    "efie_matvec_fp64",
     "efie_matvec_parts", "efie_solve", "efie_precond_harvest", "efie_precond_train", "efie_precond_save",
     "efie_precond_load", "efie_precond_enable", "efie_precond_params", "efie_precond_apply",
     "efie_precond_gradient", "efie_autotune", "efie_autotune_set", "efie_batch_create", "efie_batch_matvec",
@@ -102,6 +103,7 @@ def load_library(path: str = LIB_PATH):
     lib.efie_rhs_planewave.argtypes = [VP, ctypes.c_int, P(D), P(D), VP, VP]
     lib.efie_rhs_planewave_noalloc.argtypes = [VP, ctypes.c_int, P(D), P(D), VP, VP]
     lib.efie_matvec.argtypes = [VP, VP, VP, ctypes.c_int, VP]
+    lib.efie_matvec_host.argtypes = [VP, VP, VP, ctypes.c_int, VP]
     lib.efie_matvec_fp64.argtypes = [VP, VP, VP, ctypes.c_int, VP]
     lib.efie_matvec_parts.argtypes = [VP, VP, VP, VP, ctypes.c_int, VP]
     lib.efie_solve.argtypes = [VP, VP, VP, ctypes.c_int, D, P(SolveInfo), VP]
@@ -302,6 +304,26 @@ class EFIE:
         fn = self.lib.efie_matvec_fp64 if fp64 else self.lib.efie_matvec
         _check(self.lib, fn(self.h, self._vec(x2), self._vec(y), x2.shape[0], self._stream()), self.h)
         return y if x.dim() == 2 else y[0]
+
+    def matvec_host(self, x, y=None):
+        """y = T x with x, y complex128 CPU tensors [n_rhs, N] (pin them for the
+        copies to overlap the products).  Ordered on the current CUDA stream;
+        synchronize it before reading y."""
+        import torch
+        x2 = x if x.dim() == 2 else x.unsqueeze(0)
+        if x2.device.type != "cpu" or x2.dtype != torch.complex128 or not x2.is_contiguous():
+            raise ValueError("x must be a contiguous complex128 CPU tensor")
+        if x2.shape[-1] != self.N:
+            raise ValueError("last dimension must equal the number of unknowns")
+        if y is None:
+            y = torch.empty_like(x2, pin_memory=x2.is_pinned())
+        y2 = y if y.dim() == 2 else y.unsqueeze(0)
+        if y2.shape != x2.shape or y2.dtype != torch.complex128 or not y2.is_contiguous():
+            raise ValueError("y must be a contiguous complex128 CPU tensor shaped like x")
+        _check(self.lib, self.lib.efie_matvec_host(self.h, ctypes.c_void_p(x2.data_ptr()),
+                                                   ctypes.c_void_p(y2.data_ptr()), x2.shape[0],
+                                                   self._stream()), self.h)
+        return y
 
     def matvec_parts(self, x):
         import torch

@@ -156,8 +156,31 @@ struct Prof {
 };
 }  // namespace
 
+// Copy streams, events and double-buffered device staging for
+// efie_matvec_host (created on first use).
+struct HostPipe {
+  bool ready = false;
+  int rc = 0;                        // right-hand sides per staging slot
+  cudaStream_t s_in = nullptr, s_out = nullptr;
+  cudaEvent_t ev_start = nullptr, ev_end = nullptr;
+  cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_comp[2] = {nullptr, nullptr}, ev_out[2] = {nullptr, nullptr};
+  double2 *xs[2] = {nullptr, nullptr}, *ys[2] = {nullptr, nullptr};
+  ~HostPipe() {
+    for (int b = 0; b < 2; ++b) {
+      if (ev_in[b]) cudaEventDestroy(ev_in[b]);
+      if (ev_comp[b]) cudaEventDestroy(ev_comp[b]);
+      if (ev_out[b]) cudaEventDestroy(ev_out[b]);
+    }
+    if (ev_start) cudaEventDestroy(ev_start);
+    if (ev_end) cudaEventDestroy(ev_end);
+    if (s_in) cudaStreamDestroy(s_in);
+    if (s_out) cudaStreamDestroy(s_out);
+  }
+};
+
 struct efie_handle {
   Prof prof;
+  HostPipe pipe;
   // learned preconditioner
   efie::Net* net = nullptr;
   bool net_training = false;
@@ -1455,6 +1478,70 @@ int efie_matvec(efie_handle* h, const void* x, void* y, int n_rhs, void* stream)
     if (n_rhs == 0) return EFIE_OK;
     do_matvec(h, (const double2*)x, h->plan.g.N, (double2*)y, nullptr, nullptr, h->plan.g.N, n_rhs, false,
               (cudaStream_t)stream);
+    return EFIE_OK;
+  });
+}
+
+int efie_matvec_host(efie_handle* h, const void* x_host, void* y_host, int n_rhs, void* stream) {
+  if (!h) return EFIE_EINVAL;
+  return guarded(h, [&] {
+    if (n_rhs < 0 || ((!x_host || !y_host) && n_rhs > 0)) throw EfieError{EFIE_EINVAL, "bad arguments"};
+    if (n_rhs == 0) return EFIE_OK;
+    const int64_t N = h->plan.g.N;
+    const int Rc = h->opt.rhs_chunk > 0 ? std::min(h->opt.rhs_chunk, 8) : 8;
+    HostPipe& hp = h->pipe;
+    if (!hp.ready) {
+      cuda_check(cudaStreamCreateWithFlags(&hp.s_in, cudaStreamNonBlocking), "host pipe stream");
+      cuda_check(cudaStreamCreateWithFlags(&hp.s_out, cudaStreamNonBlocking), "host pipe stream");
+      cuda_check(cudaEventCreateWithFlags(&hp.ev_start, cudaEventDisableTiming), "host pipe event");
+      cuda_check(cudaEventCreateWithFlags(&hp.ev_end, cudaEventDisableTiming), "host pipe event");
+      for (int b = 0; b < 2; ++b) {
+        cuda_check(cudaEventCreateWithFlags(&hp.ev_in[b], cudaEventDisableTiming), "host pipe event");
+        cuda_check(cudaEventCreateWithFlags(&hp.ev_comp[b], cudaEventDisableTiming), "host pipe event");
+        cuda_check(cudaEventCreateWithFlags(&hp.ev_out[b], cudaEventDisableTiming), "host pipe event");
+      }
+      hp.ready = true;
+    }
+    if (hp.rc < Rc) {
+      // the previous slots may still be in use by earlier calls
+      cuda_check(cudaStreamSynchronize(hp.s_in), "host pipe");
+      cuda_check(cudaStreamSynchronize(hp.s_out), "host pipe");
+      for (int b = 0; b < 2; ++b) {
+        if (hp.xs[b]) cuda_check(cudaEventSynchronize(hp.ev_comp[b]), "host pipe");
+        h->mem.release(hp.xs[b]);
+        h->mem.release(hp.ys[b]);
+        hp.xs[b] = h->mem.alloc<double2>((int64_t)Rc * N);
+        hp.ys[b] = h->mem.alloc<double2>((int64_t)Rc * N);
+      }
+      hp.rc = Rc;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const double2* xh = (const double2*)x_host;
+    double2* yh = (double2*)y_host;
+    // the copies start after the caller's earlier work on its stream
+    cuda_check(cudaEventRecord(hp.ev_start, s), "host pipe");
+    cuda_check(cudaStreamWaitEvent(hp.s_in, hp.ev_start, 0), "host pipe");
+    cuda_check(cudaStreamWaitEvent(hp.s_out, hp.ev_start, 0), "host pipe");
+    for (int i = 0, r0 = 0; r0 < n_rhs; ++i, r0 += Rc) {
+      const int b = i & 1, nr = std::min(Rc, n_rhs - r0);
+      const size_t bytes = sizeof(double2) * (size_t)nr * (size_t)N;
+      // slot b's x is free once the product of two chunks back has run
+      cuda_check(cudaStreamWaitEvent(hp.s_in, hp.ev_comp[b], 0), "host pipe");
+      cuda_check(cudaMemcpyAsync(hp.xs[b], xh + (int64_t)r0 * N, bytes, cudaMemcpyHostToDevice, hp.s_in),
+                 "host pipe H2D");
+      cuda_check(cudaEventRecord(hp.ev_in[b], hp.s_in), "host pipe");
+      // slot b's y is free once its copy-out of two chunks back has run
+      cuda_check(cudaStreamWaitEvent(s, hp.ev_in[b], 0), "host pipe");
+      cuda_check(cudaStreamWaitEvent(s, hp.ev_out[b], 0), "host pipe");
+      do_matvec(h, hp.xs[b], N, hp.ys[b], nullptr, nullptr, N, nr, false, s);
+      cuda_check(cudaEventRecord(hp.ev_comp[b], s), "host pipe");
+      cuda_check(cudaStreamWaitEvent(hp.s_out, hp.ev_comp[b], 0), "host pipe");
+      cuda_check(cudaMemcpyAsync(yh + (int64_t)r0 * N, hp.ys[b], bytes, cudaMemcpyDeviceToHost, hp.s_out),
+                 "host pipe D2H");
+      cuda_check(cudaEventRecord(hp.ev_out[b], hp.s_out), "host pipe");
+    }
+    cuda_check(cudaEventRecord(hp.ev_end, hp.s_out), "host pipe");
+    cuda_check(cudaStreamWaitEvent(s, hp.ev_end, 0), "host pipe");
     return EFIE_OK;
   });
 }

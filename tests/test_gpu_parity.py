@@ -100,6 +100,27 @@ def test_batched_rhs_ragged_chunks(G, c1_gpu, c1_oracle):
     assert _rel(Y32, Y) < TOL32
 
 
+def test_matvec_host_buffers(G, c1_gpu, c1_oracle):
+    """efie_matvec_host: 11 right-hand sides in pinned and in pageable host
+    memory (chunks of 8 and 3 through the double-buffered staging) give the
+    device-buffer product; a second call reuses the staging."""
+    torch = _torch()
+    for h, tol in zip(c1_gpu, (1e-12, 1e-6)):
+        X = torch.from_numpy(E.complex_gaussian((11, h.N), 21))
+        ref = h.matvec(X.cuda()).cpu().numpy()
+        for pinned in (True, False):
+            Xh = X.pin_memory() if pinned else X.clone()
+            for _ in range(2):
+                Yh = h.matvec_host(Xh)
+                torch.cuda.synchronize()
+                err = _rel(Yh.numpy(), ref)
+                print(f"host-buffer matvec (pinned={pinned}): {err:.3e}")
+                assert err < tol
+        assert _rel(ref[3], c1_oracle.matvec(X[3].numpy())) < (TOL64 if tol < 1e-9 else TOL32)
+        empty = torch.zeros((0, h.N), dtype=torch.complex128)
+        assert h.matvec_host(empty).shape == (0, h.N)
+
+
 def test_star_null_space_gpu(G, c1_gpu, c1_mesh):
     """Sec. VI-A: the scalar part vanishes on loop currents (to roundoff)."""
     torch = _torch()
