@@ -851,6 +851,17 @@ void setup_impl(efie_handle* h, const efie_mesh* mesh, double k, int p, double g
     nd.rwg_tl = M.upload(P.rwg_tl);
     nd.rwg_loc = M.upload(P.rwg_loc);
     nd.rwg_coef = M.upload(P.rwg_coef);
+    {
+      // position of each sorted triangle in the A triangle set of its own box
+      std::vector<int32_t> tl(P.tri_perm.size(), -1);
+      for (int64_t b = 0; b < BD; ++b)
+        for (int64_t i = P.box_tri_ptr[b]; i < P.box_tri_ptr[b + 1]; ++i) {
+          const auto first = P.tset.begin() + P.tset_ptr[b], last = P.tset.begin() + P.tset_ptr[b + 1];
+          const auto it = std::lower_bound(first, last, P.tri_perm[i]);
+          if (it != last && *it == P.tri_perm[i]) tl[i] = (int32_t)(it - first);
+        }
+      nd.tri_tl = M.upload(tl);
+    }
     nd.A = M.alloc<double2>(P.nnzA);
     nd.Vn = M.alloc<double2>(P.nnzV);
     // A: triangle-pair scratch per batch of blocks
@@ -896,15 +907,11 @@ void setup_impl(efie_handle* h, const efie_mesh* mesh, double k, int p, double g
       launch_near_pairs_A(nd, j0, j1 - j0, d_scr_off, scratch, scr_off.back(), s);
       launch_near_combine_A(nd, j0, j1 - j0, d_scr_off, scratch, P.blkA_off[j0],
                             P.blkA_off[j1] - P.blkA_off[j0], s);
-      cuda_check(cudaStreamSynchronize(s), "near A assembly");
+      launch_near_V_pairs(nd, j0, j1 - j0, d_scr_off, scratch, P.blkV_off[j0], P.blkV_off[j1] - P.blkV_off[j0], s);
+      cuda_check(cudaStreamSynchronize(s), "near assembly");
       j0 = j1;
     }
     M.release(scratch);
-    const int64_t vchunk = 1LL << 26;
-    for (int64_t e0 = 0; e0 < P.nnzV; e0 += vchunk) {
-      launch_near_V(nd, e0, std::min(vchunk, P.nnzV - e0), s);
-      cuda_check(cudaStreamSynchronize(s), "near V assembly");
-    }
     {
       const int64_t nm = (int64_t)mir_blk.size();
       int64_t* d_mir = M.alloc<int64_t>(2 * std::max<int64_t>(nm, 1));

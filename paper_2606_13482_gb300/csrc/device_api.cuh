@@ -33,6 +33,7 @@ struct NearDev {
   const double* rwg_coef;
   double2* A;               // [nnzA]
   double2* Vn;              // [nnzV]
+  const int32_t* tri_tl;    // [nt sorted] index of the triangle in the tset of its own box, -1 if absent
 };
 // Blocks (x, y) with x > y are not integrated: T is symmetric, so they are the
 // transposes of the (y, x) blocks, copied by launch_near_mirror.
@@ -42,7 +43,11 @@ void launch_near_pairs_A(const NearDev& nd, int64_t j0, int64_t nblk, const int6
                          double2* scratch, int64_t total, cudaStream_t s);
 void launch_near_combine_A(const NearDev& nd, int64_t j0, int64_t nblk, const int64_t* scr_off,
                            const double2* scratch, int64_t e_begin, int64_t total, cudaStream_t s);
-void launch_near_V(const NearDev& nd, int64_t e_begin, int64_t total, cudaStream_t s);
+// V entries of the blocks j in [j0, j0 + nblk) (entries [e_begin, e_begin + total)),
+// reading I0 from the A pass's pair scratch of the same blocks where both
+// triangles are in the A triangle sets, computing it otherwise.
+void launch_near_V_pairs(const NearDev& nd, int64_t j0, int64_t nblk, const int64_t* scr_off,
+                         const double2* scratch, int64_t e_begin, int64_t total, cudaStream_t s);
 // M[blk] = M[mirror]^T for the n listed blocks (column-major blocks; box_ptr:
 // the per-box function ranges that size them).
 void launch_near_mirror(double2* M, const int64_t* blk_off, const int64_t* box_ptr, const int32_t* blk_tgt,

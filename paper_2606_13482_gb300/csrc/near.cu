@@ -359,25 +359,6 @@ __global__ void k_near_combine_A(NearDev nd, int64_t j0, int64_t nblk, const int
   nd.A[eg] = acc;
 }
 
-// V block entries: V[a][b] = int int g / (a_a a_b) for sorted triangles
-__global__ void k_near_V(NearDev nd, int64_t e_begin, int64_t total) {
-  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= total) return;
-  int64_t eg = e_begin + e;
-  int64_t j = find_block(nd.blkV_off, nd.n_blocks, eg);
-  int32_t x = nd.blk_tgt[j], y = nd.near_src[j];
-  if (x > y) return;  // transpose of block (y, x): k_near_mirror
-  int64_t nxt = nd.box_tri_ptr[x + 1] - nd.box_tri_ptr[x];
-  int64_t loc = eg - nd.blkV_off[j];
-  int64_t b = loc / nxt, a = loc - b * nxt;  // column-major block
-  int ta = nd.tri_perm[nd.box_tri_ptr[x] + a];
-  int tb = nd.tri_perm[nd.box_tri_ptr[y] + b];
-  double2 I0, dummy[9];
-  pair_integrals(nd.V, nd.T, ta, tb, nd.k, false, I0, dummy);
-  double s = 1.0 / (nd.area[ta] * nd.area[tb]);
-  nd.Vn[eg] = make_double2(I0.x * s, I0.y * s);
-}
-
 // Block (x, y) = transpose of block (y, x).  Block j is column-major
 // [ny][nx] (entry (r, c) at c nx + r, r over the functions of x, c over those
 // of y); its mirror is [nx][ny], entry (c, r) at r ny + c.  One CTA per listed
@@ -409,6 +390,36 @@ k_near_mirror(double2* __restrict__ M, const int64_t* __restrict__ blk_off, cons
       }
       __syncthreads();
     }
+}
+
+// V entries of a batch of blocks from the A pass's triangle-pair scratch:
+// scratch[10 (scr_off[j - j0] + a tl_y + b)] holds I0 of the a-th triangle of
+// T_x and the b-th of T_y.  A triangle whose centroid box is x is almost
+// always in T_x (it has an RWG in x); where it is not, I0 is computed here.
+__global__ void k_near_V_pairs(NearDev nd, int64_t j0, int64_t nblk, const int64_t* scr_off,
+                               const double2* scratch, int64_t e_begin, int64_t total) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= total) return;
+  int64_t eg = e_begin + e;
+  int64_t j = find_block(nd.blkV_off + j0, nblk, eg) + j0;
+  int32_t x = nd.blk_tgt[j], y = nd.near_src[j];
+  if (x > y) return;  // transpose of block (y, x): k_near_mirror
+  int64_t nxt = nd.box_tri_ptr[x + 1] - nd.box_tri_ptr[x];
+  int64_t loc = eg - nd.blkV_off[j];
+  int64_t b = loc / nxt, a = loc - b * nxt;  // column-major block
+  const int64_t ia = nd.box_tri_ptr[x] + a, ib = nd.box_tri_ptr[y] + b;
+  const int ta = nd.tri_perm[ia], tb = nd.tri_perm[ib];
+  const int32_t la = nd.tri_tl[ia], lb = nd.tri_tl[ib];
+  double2 I0;
+  if (la >= 0 && lb >= 0) {
+    const int64_t nty = nd.tset_ptr[y + 1] - nd.tset_ptr[y];
+    I0 = scratch[10 * (scr_off[j - j0] + (int64_t)la * nty + lb)];
+  } else {
+    double2 dummy[9];
+    pair_integrals(nd.V, nd.T, ta, tb, nd.k, false, I0, dummy);
+  }
+  double sc = 1.0 / (nd.area[ta] * nd.area[tb]);
+  nd.Vn[eg] = make_double2(I0.x * sc, I0.y * sc);
 }
 
 // ---------------------------------------------------------------- SpMV
@@ -743,9 +754,10 @@ void launch_near_combine_A(const NearDev& nd, int64_t j0, int64_t nblk, const in
   k_near_combine_A<<<(unsigned)ceil_div(total, 256), 256, 0, s>>>(nd, j0, nblk, scr_off, scratch,
                                                                     e_begin, total);
 }
-void launch_near_V(const NearDev& nd, int64_t e_begin, int64_t total, cudaStream_t s) {
+void launch_near_V_pairs(const NearDev& nd, int64_t j0, int64_t nblk, const int64_t* scr_off,
+                         const double2* scratch, int64_t e_begin, int64_t total, cudaStream_t s) {
   if (total <= 0) return;
-  k_near_V<<<(unsigned)ceil_div(total, 128), 128, 0, s>>>(nd, e_begin, total);
+  k_near_V_pairs<<<(unsigned)ceil_div(total, 128), 128, 0, s>>>(nd, j0, nblk, scr_off, scratch, e_begin, total);
 }
 void launch_near_mirror(double2* M, const int64_t* blk_off, const int64_t* box_ptr, const int32_t* blk_tgt,
                         const int32_t* near_src, const int64_t* mir_blk, const int64_t* mir_src, int64_t n,
