@@ -29,6 +29,9 @@ Contents (all FP64 unless a function says otherwise):
                    TAfactor, Sec. VI-A).
 * ``fastmv``     - the straightforward multilevel B-spline fast matvec (Eq.
                    TAfactorBspline, Eq. interleveltransfer, Sec. V-B).
+* ``nonuniform`` - the same fast matvec on a nonuniform octree (Sec. VII tree
+                   rule, Sec. IV-C/D buffer rule for leaves on the parent
+                   level, level-consistent near blocks).
 * ``krylov``     - plain GMRES / FGMRES.
 * ``mpnn``       - FP64 NumPy forward/backward of the learned preconditioner
                    network (not part of the paper).
