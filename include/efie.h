@@ -112,6 +112,45 @@ int efie_plan(const efie_mesh *mesh, double wavenumber, int spline_degree,
               double grid_spacing, int levels, const efie_options *opt,
               efie_plan_info_t *info, efie_level_info_t *levels_out, int max_levels);
 
+/* Nonuniform octree (Sec. VII): a box is subdivided while it holds more than
+ * max_elems triangles (by centroid), unless a basis function would then
+ * protrude from its child box by more than max_prot of the child's edge. */
+typedef struct {
+    int32_t max_elems;       /* the paper uses 200 */
+    double max_prot;         /* the paper uses 0.25 */
+    int32_t top;             /* top grid level (root 0), >= 1; leaves above it are rejected */
+    int32_t n_splines;       /* s on the deepest level; 0 -> p + 4 */
+    int32_t max_depth;       /* 0 -> 30 */
+} efie_tree_options;
+
+/* Per-level summary of a nonuniform tree (efie_plan_adaptive). */
+typedef struct {
+    int32_t level;           /* octree level (root 0) */
+    int32_t s, sb, sp, shat; /* splines, buffer splines, s' = s + 2 sb, stabilized count */
+    int64_t n_boxes;         /* boxes on the level (leaves and parents) */
+    int64_t n_leaves;
+    int64_t n_far_pairs;     /* translated box pairs on this level */
+    int64_t n_leaf_rwg, n_leaf_tri;  /* functions whose leaf is on this level */
+    double h, delta;         /* box edge, knot spacing */
+} efie_adaptive_level_t;
+
+/* Host-only planning of a nonuniform octree (Sec. VII tree rule; per-level s
+ * and s_b by Sec. IV-C/D, with the buffer rule for leaves on the parent
+ * level).  Every basis function belongs to the leaf holding its point (edge
+ * midpoint, centroid); level l translates the non-adjacent box pairs with
+ * adjacent parents (every non-adjacent pair on the top level); two leaves are
+ * near when, on the coarser of their levels, their ancestors are adjacent or
+ * equal.  levels_out (may be NULL) receives min(max_levels, n_levels) levels
+ * from the top level down; *n_levels the level count; *near_pairs_rwg and
+ * *near_pairs_tri the ordered pairs of RWGs / triangles in near leaves (self
+ * pairs included).  Any output pointer may be NULL.  topt NULL -> the paper's
+ * values (200, 0.25, top 2).  EFIE_EINVAL for a bad mesh or parameters, a
+ * leaf above the top level, or buffer splines that close the gap between far
+ * interpolation domains.  The device path does not take nonuniform trees yet. */
+int efie_plan_adaptive(const efie_mesh *mesh, double wavenumber, int spline_degree,
+                       const efie_tree_options *topt, efie_adaptive_level_t *levels_out, int max_levels,
+                       int32_t *n_levels, int64_t *near_pairs_rwg, int64_t *near_pairs_tri);
+
 /* Host-only: the per-level dense matrices of the far pipeline, row-major FP64.
  *   P[level]   (shat x sp)   = B_stab^{-1} S (Sec. V-B)
  *   CL, CR     (sp_parent x sp_child) interlevel transfers into level-1 (Sec. IV-B)

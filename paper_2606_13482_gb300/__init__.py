@@ -25,7 +25,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libefie_gb300.so")
 
 EXPORTED_SYMBOLS = [
-    "efie_plan", "efie_plan_matrix", "efie_plan_moments", "efie_setup", "efie_num_unknowns", "efie_plan_info",
+    "efie_plan", "efie_plan_adaptive", "efie_plan_matrix", "efie_plan_moments", "efie_setup", "efie_num_unknowns", "efie_plan_info",
     "efie_rwg_edges", "efie_rhs_planewave", "efie_rhs_planewave_noalloc", "efie_matvec", "efie_matvec_host",
     "efie_matvec_fp64",
     "efie_matvec_parts", "efie_solve", "efie_precond_harvest", "efie_precond_train", "efie_precond_save",
@@ -74,6 +74,19 @@ class PlanInfo(ctypes.Structure):
                 ("moment_entries_tri", ctypes.c_int64)]
 
 
+class TreeOptions(ctypes.Structure):
+    _fields_ = [("max_elems", ctypes.c_int32), ("max_prot", ctypes.c_double), ("top", ctypes.c_int32),
+                ("n_splines", ctypes.c_int32), ("max_depth", ctypes.c_int32)]
+
+
+class AdaptiveLevelInfo(ctypes.Structure):
+    _fields_ = [("level", ctypes.c_int32), ("s", ctypes.c_int32), ("sb", ctypes.c_int32),
+                ("sp", ctypes.c_int32), ("shat", ctypes.c_int32), ("n_boxes", ctypes.c_int64),
+                ("n_leaves", ctypes.c_int64), ("n_far_pairs", ctypes.c_int64),
+                ("n_leaf_rwg", ctypes.c_int64), ("n_leaf_tri", ctypes.c_int64),
+                ("h", ctypes.c_double), ("delta", ctypes.c_double)]
+
+
 class SolveInfo(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int32), ("true_rel_residual", ctypes.c_double),
                 ("converged", ctypes.c_int32), ("precond_fallback", ctypes.c_int32)]
@@ -94,6 +107,8 @@ def load_library(path: str = LIB_PATH):
                               P(LevelInfo), ctypes.c_int]
     lib.efie_plan_matrix.argtypes = [P(_Mesh), D, ctypes.c_int, D, ctypes.c_int, P(Options), ctypes.c_int,
                                      ctypes.c_int, P(D), I64, P(I32), P(I32)]
+    lib.efie_plan_adaptive.argtypes = [P(_Mesh), D, ctypes.c_int, P(TreeOptions), P(AdaptiveLevelInfo),
+                                       ctypes.c_int, P(I32), P(I64), P(I64)]
     lib.efie_plan_moments.argtypes = [P(_Mesh), D, ctypes.c_int, D, ctypes.c_int, P(Options), ctypes.c_int,
                                       P(I32), I64, P(D), I64, P(I32)]
     lib.efie_setup.argtypes = [P(_Mesh), D, ctypes.c_int, D, ctypes.c_int, P(Options), P(VP)]
@@ -192,6 +207,20 @@ def plan(V, T, k, p, grid_spacing, levels, options: Options | None = None):
     d["root_lo"] = list(info.root_lo)
     levels_out = [{f: getattr(lv[i], f) for f, _ in LevelInfo._fields_} for i in range(info.n_levels)]
     return d, levels_out
+
+
+def plan_adaptive(V, T, k, p, max_elems=200, max_prot=0.25, top=2, n_splines=0, max_depth=0):
+    """Host-only planning of a nonuniform octree (efie_plan_adaptive):
+    (per-level dicts from the top level down, near RWG pairs, near triangle pairs)."""
+    lib = load_library()
+    m, keep = _mesh(V, T)
+    o = TreeOptions(max_elems, max_prot, top, n_splines, max_depth)
+    lv = (AdaptiveLevelInfo * 64)()
+    n, nr, nt = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int64()
+    _check(lib, lib.efie_plan_adaptive(ctypes.byref(m), k, p, ctypes.byref(o), lv, 64, ctypes.byref(n),
+                                       ctypes.byref(nr), ctypes.byref(nt)))
+    levels = [{f: getattr(lv[i], f) for f, _ in AdaptiveLevelInfo._fields_} for i in range(n.value)]
+    return levels, nr.value, nt.value
 
 
 def plan_matrix(V, T, k, p, grid_spacing, levels, level, which, options: Options | None = None):

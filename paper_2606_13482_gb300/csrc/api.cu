@@ -1334,6 +1334,49 @@ int efie_plan(const efie_mesh* mesh, double wavenumber, int spline_degree, doubl
   });
 }
 
+int efie_plan_adaptive(const efie_mesh* mesh, double wavenumber, int spline_degree, const efie_tree_options* topt,
+                       efie_adaptive_level_t* levels_out, int max_levels, int32_t* n_levels, int64_t* near_pairs_rwg,
+                       int64_t* near_pairs_tri) {
+  return guarded(nullptr, [&] {
+    check_mesh(mesh);
+    if (max_levels < 0) throw EfieError{EFIE_EINVAL, "max_levels < 0"};
+    AdaptiveOptions o;
+    if (topt) {
+      o.max_elems = topt->max_elems;
+      o.max_prot = topt->max_prot;
+      o.top = topt->top;
+      o.n_splines = topt->n_splines;
+      o.max_depth = topt->max_depth > 0 ? topt->max_depth : 30;
+      if (!(o.max_prot >= 0)) throw EfieError{EFIE_EINVAL, "max_prot must be >= 0"};
+    }
+    AdaptivePlan A;
+    build_adaptive_plan(A, mesh->xyz, mesh->n_vertices, mesh->tri, mesh->n_triangles, wavenumber, spline_degree, o);
+    const int nl = (int)A.lv.size();
+    if (n_levels) *n_levels = nl;
+    if (near_pairs_rwg) *near_pairs_rwg = A.near_pairs_rwg;
+    if (near_pairs_tri) *near_pairs_tri = A.near_pairs_tri;
+    if (levels_out)
+      for (int i = 0; i < std::min(nl, max_levels); ++i) {
+        const AdaptiveLevel& L = A.lv[i];
+        efie_adaptive_level_t& out = levels_out[i];
+        out.level = L.level;
+        out.s = L.s;
+        out.sb = L.sb;
+        out.sp = L.sp;
+        out.shat = L.shat;
+        out.n_boxes = (int64_t)L.key.size();
+        out.n_leaves = 0;
+        for (uint8_t f : L.leaf) out.n_leaves += f;
+        out.n_far_pairs = L.n_far_pairs;
+        out.n_leaf_rwg = L.n_leaf_rwg;
+        out.n_leaf_tri = L.n_leaf_tri;
+        out.h = L.h;
+        out.delta = L.delta;
+      }
+    return EFIE_OK;
+  });
+}
+
 int efie_plan_matrix(const efie_mesh* mesh, double wavenumber, int spline_degree, double grid_spacing,
                      int levels, const efie_options* opt, int level, int which, double* out, int64_t out_len,
                      int32_t* rows, int32_t* cols) {

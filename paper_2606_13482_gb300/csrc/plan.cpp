@@ -1071,4 +1071,289 @@ void build_plan(Plan& P, const double* xyz, int64_t nv, const int32_t* tri, int6
   }
 }
 
+// ------------------------------------------------------------ nonuniform tree
+namespace {
+using Key = std::array<int64_t, 3>;
+struct KeyHash {
+  size_t operator()(const Key& k) const {
+    return (size_t)((uint64_t)k[0] * 0x9E3779B97F4A7C15ull ^ (uint64_t)k[1] * 0xC2B2AE3D27D4EB4Full ^
+                    (uint64_t)k[2] * 0x165667B19E3779F9ull);
+  }
+};
+
+// box of a point on a level: floor((x - root_lo) / h), clamped
+Key box_key(const double* x, const double* root_lo, double root_edge, int level) {
+  const double h = root_edge / (double)(1LL << level);
+  const int64_t nmax = (1LL << level) - 1;
+  Key k;
+  for (int d = 0; d < 3; ++d) {
+    int64_t i = (int64_t)std::floor((x[d] - root_lo[d]) / h);
+    k[d] = std::min<int64_t>(std::max<int64_t>(i, 0), nmax);
+  }
+  return k;
+}
+
+// largest distance by which the supports [smin, smax] of the listed functions
+// leave the boxes of their points on the given level
+double protrusion(const std::vector<int32_t>& ids, const std::vector<double>& pt, const std::vector<double>& smin,
+                  const std::vector<double>& smax, const double* root_lo, double root_edge, int level) {
+  const double h = root_edge / (double)(1LL << level);
+  double prot = 0.0;
+  for (int32_t i : ids) {
+    const Key k = box_key(&pt[3 * i], root_lo, root_edge, level);
+    for (int d = 0; d < 3; ++d) {
+      const double blo = root_lo[d] + (double)k[d] * h;
+      prot = std::max(prot, std::max(blo - smin[3 * i + d], 0.0));
+      prot = std::max(prot, std::max(smax[3 * i + d] - (blo + h), 0.0));
+    }
+  }
+  return prot;
+}
+}  // namespace
+
+void build_adaptive_plan(AdaptivePlan& A, const double* xyz, int64_t nv, const int32_t* tri, int64_t nt,
+                         double k, int p, const AdaptiveOptions& o) {
+  if (p < 1 || p > 6) fail(-1, "spline degree p must be in 1..6");
+  if (!(k > 0)) fail(-1, "wavenumber must be positive");
+  if (o.top < 1) fail(-1, "top grid level must be >= 1");
+  Geometry& g = A.g;
+  build_geometry(g, xyz, nv, tri, nt);
+  A.p = p;
+  const int64_t N = g.N;
+  // points and support bounds: RWG (edge midpoint, both triangles), triangle (centroid)
+  std::vector<double> rpt(3 * N), rmin(3 * N, 1e300), rmax(3 * N, -1e300), tmin(3 * nt, 1e300),
+      tmax(3 * nt, -1e300);
+  for (int64_t t = 0; t < nt; ++t)
+    for (int a = 0; a < 3; ++a)
+      for (int d = 0; d < 3; ++d) {
+        const double v = g.V[3 * g.T[3 * t + a] + d];
+        tmin[3 * t + d] = std::min(tmin[3 * t + d], v);
+        tmax[3 * t + d] = std::max(tmax[3 * t + d], v);
+      }
+  for (int64_t m = 0; m < N; ++m)
+    for (int d = 0; d < 3; ++d) {
+      rpt[3 * m + d] = (g.V[3 * g.edge[2 * m] + d] + g.V[3 * g.edge[2 * m + 1] + d]) * 0.5;
+      for (int s = 0; s < 2; ++s) {
+        const int32_t t = g.tri_pm[2 * m + s];
+        rmin[3 * m + d] = std::min(rmin[3 * m + d], tmin[3 * t + d]);
+        rmax[3 * m + d] = std::max(rmax[3 * m + d], tmax[3 * t + d]);
+      }
+    }
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  for (int64_t v = 0; v < nv; ++v)
+    for (int d = 0; d < 3; ++d) {
+      lo[d] = std::min(lo[d], g.V[3 * v + d]);
+      hi[d] = std::max(hi[d], g.V[3 * v + d]);
+    }
+  A.root_edge = std::max(hi[0] - lo[0], std::max(hi[1] - lo[1], hi[2] - lo[2]));
+  for (int d = 0; d < 3; ++d) A.root_lo[d] = (lo[d] + hi[d]) * 0.5 - A.root_edge * 0.5;
+  const double* rl = A.root_lo;
+  const double re = A.root_edge;
+
+  // subdivision, level by level
+  struct Members {
+    std::vector<int32_t> rwg, tri;
+  };
+  std::vector<std::unordered_map<Key, Members, KeyHash>> boxes(1);
+  std::vector<std::vector<Key>> leaves;
+  {
+    Members all;
+    all.rwg.resize(N);
+    all.tri.resize(nt);
+    std::iota(all.rwg.begin(), all.rwg.end(), 0);
+    std::iota(all.tri.begin(), all.tri.end(), 0);
+    boxes[0][Key{0, 0, 0}] = std::move(all);
+  }
+  for (int level = 0; !boxes[level].empty(); ++level) {
+    if (level > 60) fail(-1, "tree too deep");
+    leaves.emplace_back();
+    std::unordered_map<Key, Members, KeyHash> nxt;
+    for (auto& kv : boxes[level]) {
+      const Members& mb = kv.second;
+      bool split = (int64_t)mb.tri.size() > o.max_elems && level < o.max_depth;
+      if (split) {
+        const double prot = std::max(protrusion(mb.rwg, rpt, rmin, rmax, rl, re, level + 1),
+                                     protrusion(mb.tri, g.cen, tmin, tmax, rl, re, level + 1));
+        split = prot <= o.max_prot * re / (double)(1LL << (level + 1));
+      }
+      if (!split) {
+        leaves[level].push_back(kv.first);
+        continue;
+      }
+      for (int32_t i : mb.rwg) nxt[box_key(&rpt[3 * i], rl, re, level + 1)].rwg.push_back(i);
+      for (int32_t i : mb.tri) nxt[box_key(&g.cen[3 * i], rl, re, level + 1)].tri.push_back(i);
+    }
+    boxes.push_back(std::move(nxt));
+  }
+  int D = -1;
+  for (int ell = 0; ell < (int)leaves.size(); ++ell)
+    if (!leaves[ell].empty()) D = ell;
+  for (int ell = 0; ell < std::min(o.top, (int)leaves.size()); ++ell)
+    if (!leaves[ell].empty()) fail(-1, "a leaf lies above the top grid level");
+  if (o.top > D) fail(-1, "top grid level below the deepest leaf");
+  A.D = D;
+  A.top = o.top;
+
+  // per-level parameters, deepest level first
+  const double lam = 2.0 * M_PI / k;
+  const int s_leaf = o.n_splines > 0 ? o.n_splines : p + 4;
+  A.lv.assign(D - o.top + 1, AdaptiveLevel());
+  A.rwg_level.assign(N, -1);
+  A.rwg_box.assign(N, -1);
+  A.tri_level.assign(nt, -1);
+  A.tri_box.assign(nt, -1);
+  int cur_s = s_leaf, cur_sb = 0;
+  for (int ell = D; ell >= o.top; --ell) {
+    AdaptiveLevel& L = A.lv[ell - o.top];
+    L.level = ell;
+    L.h = re / (double)(1LL << ell);
+    if (ell < D && L.h >= 0.5 * lam) cur_s = 2 * cur_s - p;
+    L.delta = L.h / (double)(cur_s - p);
+    for (auto& kv : boxes[ell]) L.key.push_back(kv.first);
+    std::sort(L.key.begin(), L.key.end());
+    const std::vector<Key>& lk = leaves[ell];
+    std::unordered_map<Key, int64_t, KeyHash> index;
+    for (size_t b = 0; b < L.key.size(); ++b) index[L.key[b]] = (int64_t)b;
+    L.leaf.assign(L.key.size(), 0);
+    L.n_rwg.assign(L.key.size(), 0);
+    L.n_tri.assign(L.key.size(), 0);
+    double prot = 0.0;
+    for (const Key& key : lk) {
+      const Members& mb = boxes[ell].at(key);
+      const int64_t b = index.at(key);
+      L.leaf[b] = 1;
+      L.n_rwg[b] = (int32_t)mb.rwg.size();
+      L.n_tri[b] = (int32_t)mb.tri.size();
+      L.n_leaf_rwg += (int64_t)mb.rwg.size();
+      L.n_leaf_tri += (int64_t)mb.tri.size();
+      for (int32_t i : mb.rwg) {
+        A.rwg_level[i] = ell;
+        A.rwg_box[i] = (int32_t)b;
+      }
+      for (int32_t i : mb.tri) {
+        A.tri_level[i] = ell;
+        A.tri_box[i] = (int32_t)b;
+      }
+      prot = std::max(prot, std::max(protrusion(mb.rwg, rpt, rmin, rmax, rl, re, ell),
+                                     protrusion(mb.tri, g.cen, tmin, tmax, rl, re, ell)));
+    }
+    const int sb_leaves = (int)std::ceil(prot / L.delta);
+    if (ell == D)
+      cur_sb = sb_leaves;
+    else
+      cur_sb = std::max(cur_s == A.lv[ell + 1 - o.top].s ? (cur_sb + 1) / 2 : cur_sb, sb_leaves);
+    if (2 * cur_sb >= cur_s - p)
+      fail(-1, "buffer splines leave no gap between far interpolation domains on level " + std::to_string(ell));
+    L.s = cur_s;
+    L.sb = cur_sb;
+    L.sp = cur_s + 2 * cur_sb;
+    L.shat = L.sp - 2 * S_REMOVE[p];
+    if (L.shat <= p) fail(-1, "too few splines after stabilization");
+  }
+  // parents and children
+  auto find = [&](int ell, const Key& key) -> int64_t {
+    const auto& kk = A.lv[ell - o.top].key;
+    auto it = std::lower_bound(kk.begin(), kk.end(), key);
+    return (it != kk.end() && *it == key) ? (int64_t)(it - kk.begin()) : -1;
+  };
+  for (int ell = o.top; ell <= D; ++ell) {
+    AdaptiveLevel& L = A.lv[ell - o.top];
+    L.parent.assign(L.key.size(), -1);
+    if (ell > o.top)
+      for (size_t b = 0; b < L.key.size(); ++b)
+        L.parent[b] = find(ell - 1, Key{L.key[b][0] >> 1, L.key[b][1] >> 1, L.key[b][2] >> 1});
+  }
+  for (int ell = o.top; ell <= D; ++ell) {
+    AdaptiveLevel& L = A.lv[ell - o.top];
+    L.child_ptr.assign(L.key.size() + 1, 0);
+    if (ell == D) continue;
+    const AdaptiveLevel& C = A.lv[ell + 1 - o.top];
+    for (int64_t pb : C.parent) L.child_ptr[pb + 1]++;
+    for (size_t b = 0; b < L.key.size(); ++b) L.child_ptr[b + 1] += L.child_ptr[b];
+    L.child.resize(C.key.size());
+    std::vector<int64_t> fill(L.child_ptr.begin(), L.child_ptr.end() - 1);
+    for (size_t c = 0; c < C.key.size(); ++c) L.child[fill[C.parent[c]]++] = (int64_t)c;
+  }
+  auto adjacent = [](const Key& a, const Key& b) {
+    return std::max(std::llabs(a[0] - b[0]), std::max(std::llabs(a[1] - b[1]), std::llabs(a[2] - b[2]))) <= 1;
+  };
+  // translated pairs: non-adjacent boxes with adjacent parents; every
+  // non-adjacent pair on the top level
+  for (int ell = o.top; ell <= D; ++ell) {
+    AdaptiveLevel& L = A.lv[ell - o.top];
+    int64_t n = 0;
+    if (ell == o.top) {
+      for (size_t x = 0; x < L.key.size(); ++x)
+        for (size_t y = 0; y < L.key.size(); ++y)
+          if (!adjacent(L.key[x], L.key[y])) ++n;
+    } else {
+      const AdaptiveLevel& U = A.lv[ell - 1 - o.top];
+      for (size_t x = 0; x < L.key.size(); ++x) {
+        const Key& pk = U.key[L.parent[x]];
+        for (int a = -1; a <= 1; ++a)
+          for (int b = -1; b <= 1; ++b)
+            for (int c = -1; c <= 1; ++c) {
+              const int64_t q = find(ell - 1, Key{pk[0] + a, pk[1] + b, pk[2] + c});
+              if (q < 0) continue;
+              for (int64_t j = U.child_ptr[q]; j < U.child_ptr[q + 1]; ++j)
+                if (!adjacent(L.key[x], L.key[U.child[j]])) ++n;
+            }
+      }
+    }
+    L.n_far_pairs = n;
+  }
+  // near pairs: leaves x (level lx) and y (level ly) are near when, on the
+  // coarser of the two levels, the ancestors are adjacent or equal
+  A.near_pairs_rwg = A.near_pairs_tri = 0;
+  std::vector<int64_t> stack;
+  for (int lx = o.top; lx <= D; ++lx) {
+    const AdaptiveLevel& LX = A.lv[lx - o.top];
+    for (size_t x = 0; x < LX.key.size(); ++x) {
+      if (!LX.leaf[x]) continue;
+      const int64_t nrx = LX.n_rwg[x], ntx = LX.n_tri[x];
+      // leaves on levels ly <= lx next to (or equal to) x's ancestor
+      for (int ly = o.top; ly <= lx; ++ly) {
+        const int sh = lx - ly;
+        const Key anc{LX.key[x][0] >> sh, LX.key[x][1] >> sh, LX.key[x][2] >> sh};
+        const AdaptiveLevel& LY = A.lv[ly - o.top];
+        for (int a = -1; a <= 1; ++a)
+          for (int b = -1; b <= 1; ++b)
+            for (int c = -1; c <= 1; ++c) {
+              const int64_t y = find(ly, Key{anc[0] + a, anc[1] + b, anc[2] + c});
+              if (y < 0 || !LY.leaf[y]) continue;
+              A.near_pairs_rwg += nrx * LY.n_rwg[y];
+              A.near_pairs_tri += ntx * LY.n_tri[y];
+            }
+      }
+      // leaves on deeper levels under a box of level lx next to x
+      if (lx == D) continue;
+      for (int a = -1; a <= 1; ++a)
+        for (int b = -1; b <= 1; ++b)
+          for (int c = -1; c <= 1; ++c) {
+            const int64_t z = find(lx, Key{LX.key[x][0] + a, LX.key[x][1] + b, LX.key[x][2] + c});
+            if (z < 0 || LX.leaf[z]) continue;
+            // depth-first over the descendants of z: (level, box) packed
+            stack.assign(1, ((int64_t)lx << 40) | z);
+            while (!stack.empty()) {
+              const int64_t e = stack.back();
+              stack.pop_back();
+              const int le = (int)(e >> 40);
+              const int64_t bz = e & ((1LL << 40) - 1);
+              const AdaptiveLevel& LE = A.lv[le - o.top];
+              for (int64_t j = LE.child_ptr[bz]; j < LE.child_ptr[bz + 1]; ++j) {
+                const int64_t cy = LE.child[j];
+                const AdaptiveLevel& LC = A.lv[le + 1 - o.top];
+                if (LC.leaf[cy]) {
+                  A.near_pairs_rwg += nrx * LC.n_rwg[cy];
+                  A.near_pairs_tri += ntx * LC.n_tri[cy];
+                } else {
+                  stack.push_back(((int64_t)(le + 1) << 40) | cy);
+                }
+              }
+            }
+          }
+    }
+  }
+}
+
 }  // namespace efie

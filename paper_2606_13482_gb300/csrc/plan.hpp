@@ -5,6 +5,7 @@
 // matrices (Sec. IV-B, V-B, Table I), exact moments (Eq. TAfactor, Sec. VI-A),
 // interaction lists and the block structure of the near field.
 #pragma once
+#include <array>
 #include <complex>
 #include <cstdint>
 #include <string>
@@ -107,6 +108,44 @@ struct Plan {
 void build_plan(Plan& P, const double* xyz, int64_t nv, const int32_t* tri, int64_t nt,
                 double k, int p, double grid_spacing, int levels, int n_splines,
                 bool with_moments);
+
+// ------------------------------------------------------------ nonuniform tree
+// Sec. VII: a box is subdivided while it holds more than max_elems triangles
+// (by centroid), unless a basis function would then protrude from its child
+// box by more than max_prot of the child's edge.  Per-level s and s_b follow
+// Sec. IV-C/D with the buffer rule for leaves on the parent level.
+struct AdaptiveOptions {
+  int max_elems = 200;
+  double max_prot = 0.25;
+  int top = 2;          // top grid level; leaves above it are rejected
+  int n_splines = 0;    // s on the deepest level; 0 -> p + 4
+  int max_depth = 30;
+};
+
+struct AdaptiveLevel {
+  int level = 0, s = 0, sb = 0, sp = 0, shat = 0;
+  double h = 0, delta = 0;
+  std::vector<std::array<int64_t, 3>> key;  // boxes, sorted
+  std::vector<uint8_t> leaf;                // per box
+  std::vector<int32_t> n_rwg, n_tri;        // functions whose leaf is the box
+  std::vector<int64_t> parent;              // index on level - 1 (-1 on the top level)
+  std::vector<int64_t> child_ptr, child;    // children on level + 1 (CSR)
+  int64_t n_far_pairs = 0;                  // translated box pairs on this level
+  int64_t n_leaf_rwg = 0, n_leaf_tri = 0;
+};
+
+struct AdaptivePlan {
+  Geometry g;
+  double root_lo[3] = {0, 0, 0}, root_edge = 0;
+  int D = 0, top = 0, p = 0;
+  std::vector<AdaptiveLevel> lv;            // lv[ell - top]
+  std::vector<int32_t> rwg_level, rwg_box, tri_level, tri_box;
+  // ordered pairs of functions whose leaves are near (self pairs included)
+  int64_t near_pairs_rwg = 0, near_pairs_tri = 0;
+};
+
+void build_adaptive_plan(AdaptivePlan& A, const double* xyz, int64_t nv, const int32_t* tri, int64_t nt,
+                         double k, int p, const AdaptiveOptions& o);
 
 // Spline helpers exposed for tests of the host code
 std::vector<double> open_knots(double lo, double hi, int ns, int p);

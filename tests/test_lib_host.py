@@ -116,6 +116,37 @@ def test_plan_moments_match_oracle(lib):
         G.plan_moments(V, T, k, p, delta, levels, 1, np.array([m.Nt], np.int32))
 
 
+def test_plan_adaptive_matches_oracle(lib):
+    """Nonuniform octree planned by the library's host code against the
+    oracle's (`oracle.nonuniform`): per-level boxes, leaves, spline counts,
+    translated pairs, leaf functions, and the near RWG / triangle pairs."""
+    G, _ = lib
+    from oracle import nonuniform as NU
+    from oracle.geometry import build_rwg
+    from oracle.tree import interaction_lists
+    for (freq, r, k, me, top) in [(14, 0.5, 2 * np.pi, 60, 2), (14, 0.5, 2 * np.pi * 2.5, 60, 2),
+                                  (12, 0.5, 2 * np.pi, 40, 2)]:
+        V, T = E.icosphere(freq, r)
+        m = build_rwg(V, T)
+        tr = NU.build_adaptive_tree(m, k, 3, max_elems=me, top=top)
+        lv, nr, nt = G.plan_adaptive(V, T, k, 3, max_elems=me, top=top)
+        assert [L["level"] for L in lv] == list(range(tr.top, tr.D + 1))
+        for L in lv:
+            O = tr.levels[L["level"]]
+            assert (L["s"], L["sb"], L["sp"], L["shat"]) == (O.s, O.sb, O.sp, O.shat)
+            assert L["n_boxes"] == len(O.boxes) and L["n_leaves"] == int(tr.is_leaf[L["level"]].sum())
+            assert L["n_far_pairs"] == len(interaction_lists(tr, L["level"])[0])
+            assert L["n_leaf_rwg"] == int((tr.rwg_level == L["level"]).sum())
+            assert L["n_leaf_tri"] == int((tr.tri_level == L["level"]).sum())
+            assert L["h"] == pytest.approx(O.h, rel=1e-15) and L["delta"] == pytest.approx(O.delta, rel=1e-15)
+        nb = NU.near_leaf_pairs(tr)
+        _, _, rl, tl = NU.leaf_index(tr)
+        assert nr == int(nb[rl[:, None], rl[None, :]].sum())
+        assert nt == int(nb[tl[:, None], tl[None, :]].sum())
+    with pytest.raises(G.EfieError):
+        G.plan_adaptive(*E.icosphere(14, 0.5), 2 * np.pi, 3, max_elems=60, top=4)
+
+
 def test_invalid_inputs(lib):
     G, _ = lib
     V, T = E.icosphere(4, 0.5)
