@@ -32,6 +32,8 @@ Contents (all FP64 unless a function says otherwise):
 * ``nonuniform`` - the same fast matvec on a nonuniform octree (Sec. VII tree
                    rule, Sec. IV-C/D buffer rule for leaves on the parent
                    level, level-consistent near blocks).
+* ``factorizations`` - the direct (RWG + divergence moments) and dyadic
+                   (3 x 3 Hessian translations) factorizations (Sec. VI).
 * ``krylov``     - plain GMRES / FGMRES.
 * ``mpnn``       - FP64 NumPy forward/backward of the learned preconditioner
                    network (not part of the paper).

@@ -1,0 +1,90 @@
+"""Pins of the oracle's direct and dyadic factorizations
+(`oracle.factorizations`, Sec. VI): polynomial-kernel exactness of the far
+part against the dense far product with the same kernel (for the dyadic form
+this checks the Hessian translation against the divergence form, since
+int int f_m . grad grad kappa . f_n = -Phi_mn), for constant s and for
+s -> 2s - p; accuracy against the dense Helmholtz product; symmetry; and
+agreement with the star-based factorization of `oracle.fastmv`."""
+import numpy as np
+import pytest
+
+import efie_inputs as E
+from oracle import dense
+from oracle import factorizations as F
+from oracle.geometry import build_rwg
+
+P = 3
+A_VEC = np.array([1.0, 2.0, -1.0])
+
+
+def _kern(D):
+    return (D[..., 0] + 2.0 * D[..., 1] - D[..., 2] + 0.3) ** P + 0j
+
+
+def _hess(D):
+    u = D[..., 0] + 2.0 * D[..., 1] - D[..., 2] + 0.3
+    return (P * (P - 1) * u ** (P - 2))[..., None, None] * np.outer(A_VEC, A_VEC) + 0j
+
+
+@pytest.mark.parametrize("k", [2 * np.pi, 2 * np.pi * 2.5])
+def test_polynomial_kernel_exact(k):
+    V, T = E.icosphere(3, 0.5)
+    m = build_rwg(V, T)
+    A, Vm = dense.assemble_dense(m, k, kernel=_kern, n_reg=(P + 4) // 2)
+    S = m.sigma_dense()
+    Phi = S @ Vm @ S.T
+    x = E.complex_gaussian(m.N, 2)
+    for cls, extra in ((F.DirectBsplineEFIE, {}), (F.DyadicBsplineEFIE, {"kernel_hessian": _hess})):
+        op = cls(m, k, P, 0.06, 2, kernel=_kern, near=None, allow_overlap=True, **extra)
+        if k > 2 * np.pi:
+            assert op.tree.levels[op.tree.D - 1].s == 2 * op.tree.levels[op.tree.D].s - P
+        assert len(op.IL[op.tree.D][0]) > 0
+        nb, rb, _ = op.near_masks()
+        mask = nb[rb[:, None], rb[None, :]]
+        yA, yV = op.far_parts(x)
+        rA, rV = np.where(mask, 0, A) @ x, np.where(mask, 0, Phi) @ x
+        assert np.linalg.norm(yA - rA) / np.linalg.norm(rA) < 1e-12, cls.__name__
+        assert np.linalg.norm(yV - rV) / np.linalg.norm(rV) < 1e-12, cls.__name__
+
+
+def test_green_hessian_finite_difference():
+    k = 2 * np.pi
+    rng = np.random.default_rng(1)
+    D = rng.normal(size=(5, 3)) + np.array([1.0, 0.0, 0.0])
+    H = F.green_hessian(D, k)
+    h = 1e-4
+    g = lambda X: dense.green(np.sqrt(np.sum(X * X, axis=-1)), k)
+    for i in range(3):
+        for j in range(3):
+            ei, ej = np.eye(3)[i] * h, np.eye(3)[j] * h
+            fd = (g(D + ei + ej) - g(D + ei - ej) - g(D - ei + ej) + g(D - ei - ej)) / (4 * h * h)
+            assert np.max(np.abs(fd - H[:, i, j])) < 1e-5 * np.max(np.abs(H))
+
+
+@pytest.fixture(scope="module")
+def c1_forms(c1_mesh, c1_dense):
+    _, _, m = c1_mesh
+    k = 2 * np.pi
+    return (F.DirectBsplineEFIE(m, k, P, 0.1, 2, dense_AV=c1_dense),
+            F.DyadicBsplineEFIE(m, k, P, 0.1, 2, dense_AV=c1_dense))
+
+
+def test_fast_vs_dense_c1(c1_mesh, c1_dense, c1_oracle, c1_forms):
+    _, _, m = c1_mesh
+    k = 2 * np.pi
+    T = dense.efie_matrix(m, k, *c1_dense)
+    x = E.complex_gaussian(m.N, 11)
+    yd = T @ x
+    ys = c1_oracle.matvec(x)
+    for op in c1_forms:
+        y = op.matvec(x)
+        assert np.linalg.norm(y - yd) / np.linalg.norm(yd) < 1e-3, type(op).__name__
+        assert np.linalg.norm(y - ys) / np.linalg.norm(ys) < 1e-3, type(op).__name__
+
+
+def test_symmetric(c1_mesh, c1_forms):
+    _, _, m = c1_mesh
+    x1, x2 = E.complex_gaussian(m.N, 12), E.complex_gaussian(m.N, 13)
+    for op in c1_forms:
+        a, b = x2 @ op.matvec(x1), x1 @ op.matvec(x2)
+        assert abs(a - b) / abs(a) < 1e-12, type(op).__name__
