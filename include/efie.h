@@ -166,10 +166,14 @@ int efie_plan_matrix(const efie_mesh *mesh, double wavenumber, int spline_degree
  *   kind 0: RWG edges (canonical edge index, the order of efie_rwg_edges),
  *           out[i][d][a][b][c] = integral over the RWG support of f_m,d N_abc;
  *   kind 1: triangles (canonical index), pulse 1/area:
- *           out[i][a][b][c] = integral over the triangle of N_abc / area.
+ *           out[i][a][b][c] = integral over the triangle of N_abc / area;
+ *   kind 2: RWG edges, divergence moments of the direct factorization
+ *           (Sec. VI-B) in the RWG's leaf box:
+ *           out[i][a][b][c] = integral over the RWG support of (div f_m) N_abc,
+ *           div f_m = +-1/area on c+-.
  * a, b, c run over the sp splines per axis of the basis function's leaf box
  * (sp = s + 2 s_b); entries outside the function's support are 0.  out must
- * hold n_ids * (3 or 1) * sp^3 doubles (out_len); *sp_out returns sp.
+ * hold n_ids * (3 for kind 0, else 1) * sp^3 doubles (out_len); *sp_out returns sp.
  * EFIE_EINVAL for a bad mesh, parameters, kind or index, or a short buffer. */
 int efie_plan_moments(const efie_mesh *mesh, double wavenumber, int spline_degree,
                       double grid_spacing, int levels, const efie_options *opt,

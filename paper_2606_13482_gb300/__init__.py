@@ -241,7 +241,8 @@ def plan_matrix(V, T, k, p, grid_spacing, levels, level, which, options: Options
 def plan_moments(V, T, k, p, grid_spacing, levels, kind, ids, options: Options | None = None):
     """Host-only exact moments of the leaf splines (efie_plan_moments):
     kind 0 -> [n, 3, sp, sp, sp] for canonical RWG ids, kind 1 -> [n, sp, sp, sp]
-    for triangle ids, each in the function's leaf box."""
+    for triangle ids, kind 2 -> [n, sp, sp, sp] RWG divergence moments (direct
+    factorization), each in the function's leaf box."""
     lib = load_library()
     m, keep = _mesh(V, T)
     ids = np.ascontiguousarray(ids, dtype=np.int32)

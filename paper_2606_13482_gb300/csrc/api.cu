@@ -1417,20 +1417,20 @@ int efie_plan_moments(const efie_mesh* mesh, double wavenumber, int spline_degre
                       double* out, int64_t out_len, int32_t* sp_out) {
   return guarded(nullptr, [&] {
     check_mesh(mesh);
-    if (kind != 0 && kind != 1) throw EfieError{EFIE_EINVAL, "kind must be 0 (RWG) or 1 (triangle)"};
+    if (kind < 0 || kind > 2) throw EfieError{EFIE_EINVAL, "kind must be 0 (RWG), 1 (triangle) or 2 (divergence)"};
     if (n_ids < 0 || (n_ids > 0 && !ids)) throw EfieError{EFIE_EINVAL, "ids is NULL"};
     efie_options o = defaults(opt);
     Plan P;
     build_plan(P, mesh->xyz, mesh->n_vertices, mesh->tri, mesh->n_triangles, wavenumber, spline_degree,
-               grid_spacing, levels, o.n_splines, true);
+               grid_spacing, levels, o.n_splines, true, kind == 2);
     const int sp = P.L(P.D).sp;
     const int ncomp = kind == 0 ? 3 : 1;
     if (sp_out) *sp_out = sp;
     if (!out) return EFIE_OK;
     const int64_t per = (int64_t)ncomp * sp * sp * sp;
     if (out_len < n_ids * per) throw EfieError{EFIE_EINVAL, "output buffer too small"};
-    const std::vector<int32_t>& perm = kind == 0 ? P.rwg_perm : P.tri_perm;
-    const MomentBlocks& MB = kind == 0 ? P.mom_rwg : P.mom_tri;
+    const std::vector<int32_t>& perm = kind == 1 ? P.tri_perm : P.rwg_perm;
+    const MomentBlocks& MB = kind == 0 ? P.mom_rwg : kind == 1 ? P.mom_tri : P.mom_div;
     std::vector<int64_t> rank(perm.size(), -1);
     for (size_t i = 0; i < perm.size(); ++i) rank[perm[i]] = (int64_t)i;
     std::fill(out, out + n_ids * per, 0.0);

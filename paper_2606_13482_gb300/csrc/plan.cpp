@@ -561,7 +561,7 @@ void scatter_tiles(const std::vector<PieceTile>& tiles, int p, int ncomp, const 
 // ------------------------------------------------------------------ build
 void build_plan(Plan& P, const double* xyz, int64_t nv, const int32_t* tri, int64_t nt,
                 double k, int p, double grid_spacing, int levels, int n_splines,
-                bool with_moments) {
+                bool with_moments, bool with_div) {
   if (!(k > 0) || !std::isfinite(k)) fail(-1, "wavenumber must be positive");
   if (p < 1 || p > 6) fail(-1, "spline degree p must be in 1..6");
   if (!(grid_spacing > 0)) fail(-1, "grid spacing must be positive");
@@ -1020,6 +1020,14 @@ void build_plan(Plan& P, const double* xyz, int64_t nv, const int32_t* tri, int6
       MT.off[i + 1] = MT.off[i] + (int64_t)MT.ext[3 * i] * MT.ext[3 * i + 1] * MT.ext[3 * i + 2];
     }
     MT.data.assign(MT.off[nt], 0.0);
+    MomentBlocks& MD = P.mom_div;
+    if (with_div) {
+      MD.base = MR.base;
+      MD.ext = MR.ext;
+      MD.off.assign(N + 1, 0);
+      for (int64_t i = 0; i < N; ++i) MD.off[i + 1] = MD.off[i] + (MR.off[i + 1] - MR.off[i]) / 3;
+      MD.data.assign(MD.off[N], 0.0);
+    }
     // One leaf box at a time: every triangle used by the box's RWGs or pulses
     // is integrated once against the box's splines, and the tiles are
     // combined into each user's block.  Only the box's own blocks are written.
@@ -1057,6 +1065,11 @@ void build_plan(Plan& P, const double* xyz, int64_t nv, const int32_t* tri, int6
                 coef[4 * d + 1 + d] = sc;
               }
               scatter_tiles(tiles, p, 3, coef, &MR.base[3 * i], &MR.ext[3 * i], &MR.data[MR.off[i]]);
+              if (with_div) {
+                // div f = +-1 / a on c+- (the same sigma / (2a) times 2)
+                const double cd[4] = {2.0 * sc, 0, 0, 0};
+                scatter_tiles(tiles, p, 1, cd, &MD.base[3 * i], &MD.ext[3 * i], &MD.data[MD.off[i]]);
+              }
             }
           }
           // the pulse of this triangle, if it belongs to the box: 1 / a

@@ -102,12 +102,15 @@ struct Plan {
 
   MomentBlocks mom_rwg;              // 3 components
   MomentBlocks mom_tri;              // 1 component (pulse, includes 1/a)
+  MomentBlocks mom_div;              // 1 component, RWG divergence (+-1/a on c+-), RWG blocks; only
+                                     // when built with_div (direct factorization, Sec. VI-B)
 };
 
-// Builds everything except moments when with_moments is false.
+// Builds everything except moments when with_moments is false; with_div adds
+// the RWG divergence moments of the direct factorization.
 void build_plan(Plan& P, const double* xyz, int64_t nv, const int32_t* tri, int64_t nt,
                 double k, int p, double grid_spacing, int levels, int n_splines,
-                bool with_moments);
+                bool with_moments, bool with_div = false);
 
 // ------------------------------------------------------------ nonuniform tree
 // Sec. VII: a box is subdivided while it holds more than max_elems triangles

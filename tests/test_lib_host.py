@@ -88,7 +88,8 @@ def test_plan_moments_match_oracle(lib):
     """Exact leaf-spline moments (Q10) built by the library's host planner
     (each triangle clipped and integrated once per leaf box, its tiles shared
     by its RWGs and its pulse) against the oracle's per-function clipping and
-    collapsed Gauss rule, for p = 2, 3, 5."""
+    collapsed Gauss rule, for p = 2, 3, 5; and the divergence moments of the
+    direct factorization."""
     G, _ = lib
     from oracle.geometry import build_rwg
     from oracle.moments import pulse_moments, rwg_moments
@@ -110,8 +111,13 @@ def test_plan_moments_match_oracle(lib):
         ref = pulse_moments(m, tr, tids)
         got = G.plan_moments(V, T, k, p, delta, levels, 1, tids)
         assert np.abs(got - ref).max() < 1e-13 * np.abs(ref).max()
+    # divergence moments of the direct factorization, in the RWG's box
+    from oracle.factorizations import divergence_moments
+    ref = divergence_moments(m, tr, ids)
+    got = G.plan_moments(V, T, k, p, delta, levels, 2, ids)
+    assert np.abs(got - ref).max() < 1e-13 * np.abs(ref).max()
     with pytest.raises(G.EfieError):
-        G.plan_moments(V, T, k, p, delta, levels, 2, ids)
+        G.plan_moments(V, T, k, p, delta, levels, 3, ids)
     with pytest.raises(G.EfieError):
         G.plan_moments(V, T, k, p, delta, levels, 1, np.array([m.Nt], np.int32))
 
