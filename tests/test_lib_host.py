@@ -169,6 +169,17 @@ def test_invalid_inputs(lib):
     Tbad[0] = Tbad[0][[0, 2, 1]]
     with pytest.raises(G.EfieError):
         G.plan(V, Tbad, 2 * np.pi, 3, 0.1, 1)            # inconsistent orientation
+    with pytest.raises(G.EfieError):
+        G.plan_adaptive(V, T[:-1], 2 * np.pi, 3)          # open mesh
+    with pytest.raises(G.EfieError):
+        G.plan_adaptive(V, T, 2 * np.pi, 3, max_elems=-1, max_prot=np.inf, top=1, max_depth=5)  # buffers
+    # entry points that take a handle reject a NULL one without touching a device
+    import ctypes
+    _, L = lib
+    x = (ctypes.c_double * 4)()
+    assert L.efie_matvec_host(None, x, x, 1, None) == G.EFIE_EINVAL
+    assert L.efie_setup_times(None, x, 4, None) == G.EFIE_EINVAL
+    assert L.efie_launch_count(None, None) == G.EFIE_EINVAL
 
 
 def test_setup_without_gpu_fails_loudly(lib):
