@@ -151,6 +151,32 @@ int efie_plan_adaptive(const efie_mesh *mesh, double wavenumber, int spline_degr
                        const efie_tree_options *topt, efie_adaptive_level_t *levels_out, int max_levels,
                        int32_t *n_levels, int64_t *near_pairs_rwg, int64_t *near_pairs_tri);
 
+/* Host-only: the leaves and near-leaf lists of the nonuniform tree of
+ * efie_plan_adaptive.  Leaves are numbered level by level from the top level,
+ * boxes in (i, j, k) order: leaf_level [n_leaves], leaf_ijk [n_leaves][3];
+ * near_ptr [n_leaves + 1] and near_src [nnz] (CSR, sources ascending) list,
+ * for each leaf, the leaves whose ancestors on the coarser of the two levels
+ * are adjacent or equal.  Call with the arrays NULL to get *n_leaves and
+ * *nnz; each array must then hold that many entries (leaf_cap >= n_leaves,
+ * near_cap >= nnz, else EFIE_EINVAL).  Other errors as efie_plan_adaptive. */
+int efie_plan_adaptive_near(const efie_mesh *mesh, double wavenumber, int spline_degree,
+                            const efie_tree_options *topt, int64_t *n_leaves, int64_t *nnz,
+                            int32_t *leaf_level, int64_t *leaf_ijk, int64_t leaf_cap,
+                            int64_t *near_ptr, int32_t *near_src, int64_t near_cap);
+
+/* Host-only: exact moments (Q10) of the nonuniform tree, each function in its
+ * own leaf's splines (that level's s', knots and buffers).  kind 0: RWGs
+ * (canonical edge ids), [3][sp][sp][sp] per id; kind 1: triangles, pulse
+ * 1/area, [sp][sp][sp] per id.  The blocks are packed one after the other in
+ * out (out_len entries), each with its own sp; level_out and sp_out (n_ids
+ * entries each, may be NULL) return the leaf level and sp of every id.  Call
+ * with out NULL to get the needed length in *out_needed.  EFIE_EINVAL for a
+ * bad kind or id or a short buffer; other errors as efie_plan_adaptive. */
+int efie_plan_adaptive_moments(const efie_mesh *mesh, double wavenumber, int spline_degree,
+                               const efie_tree_options *topt, int kind, const int32_t *ids, int64_t n_ids,
+                               double *out, int64_t out_len, int64_t *out_needed, int32_t *level_out,
+                               int32_t *sp_out);
+
 /* Host-only: the per-level dense matrices of the far pipeline, row-major FP64.
  *   P[level]   (shat x sp)   = B_stab^{-1} S (Sec. V-B)
  *   CL, CR     (sp_parent x sp_child) interlevel transfers into level-1 (Sec. IV-B)

@@ -25,7 +25,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libefie_gb300.so")
 
 EXPORTED_SYMBOLS = [
-    "efie_plan", "efie_plan_adaptive", "efie_plan_matrix", "efie_plan_moments", "efie_setup", "efie_num_unknowns", "efie_plan_info",
+    "efie_plan", "efie_plan_adaptive", "efie_plan_adaptive_near", "efie_plan_adaptive_moments", "efie_plan_matrix", "efie_plan_moments", "efie_setup", "efie_num_unknowns", "efie_plan_info",
     "efie_rwg_edges", "efie_rhs_planewave", "efie_rhs_planewave_noalloc", "efie_matvec", "efie_matvec_host",
     "efie_matvec_fp64",
     "efie_matvec_parts", "efie_solve", "efie_precond_harvest", "efie_precond_train", "efie_precond_save",
@@ -109,6 +109,10 @@ def load_library(path: str = LIB_PATH):
                                      ctypes.c_int, P(D), I64, P(I32), P(I32)]
     lib.efie_plan_adaptive.argtypes = [P(_Mesh), D, ctypes.c_int, P(TreeOptions), P(AdaptiveLevelInfo),
                                        ctypes.c_int, P(I32), P(I64), P(I64)]
+    lib.efie_plan_adaptive_near.argtypes = [P(_Mesh), D, ctypes.c_int, P(TreeOptions), P(I64), P(I64), P(I32),
+                                            P(I64), I64, P(I64), P(I32), I64]
+    lib.efie_plan_adaptive_moments.argtypes = [P(_Mesh), D, ctypes.c_int, P(TreeOptions), ctypes.c_int, P(I32),
+                                               I64, P(D), I64, P(I64), P(I32), P(I32)]
     lib.efie_plan_moments.argtypes = [P(_Mesh), D, ctypes.c_int, D, ctypes.c_int, P(Options), ctypes.c_int,
                                       P(I32), I64, P(D), I64, P(I32)]
     lib.efie_setup.argtypes = [P(_Mesh), D, ctypes.c_int, D, ctypes.c_int, P(Options), P(VP)]
@@ -221,6 +225,55 @@ def plan_adaptive(V, T, k, p, max_elems=200, max_prot=0.25, top=2, n_splines=0, 
                                        ctypes.byref(nr), ctypes.byref(nt)))
     levels = [{f: getattr(lv[i], f) for f, _ in AdaptiveLevelInfo._fields_} for i in range(n.value)]
     return levels, nr.value, nt.value
+
+
+def plan_adaptive_near(V, T, k, p, max_elems=200, max_prot=0.25, top=2, n_splines=0, max_depth=0):
+    """Leaves of the nonuniform tree and their near-leaf lists
+    (efie_plan_adaptive_near): (leaf_level [L], leaf_ijk [L,3], near_ptr [L+1], near_src)."""
+    lib = load_library()
+    m, keep = _mesh(V, T)
+    o = TreeOptions(max_elems, max_prot, top, n_splines, max_depth)
+    nl, nz = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib, lib.efie_plan_adaptive_near(ctypes.byref(m), k, p, ctypes.byref(o), ctypes.byref(nl),
+                                            ctypes.byref(nz), None, None, 0, None, None, 0))
+    lvl = np.zeros(nl.value, np.int32)
+    ijk = np.zeros((nl.value, 3), np.int64)
+    ptr = np.zeros(nl.value + 1, np.int64)
+    src = np.zeros(max(nz.value, 1), np.int32)
+    ip = lambda a, t: a.ctypes.data_as(ctypes.POINTER(t))
+    _check(lib, lib.efie_plan_adaptive_near(ctypes.byref(m), k, p, ctypes.byref(o), None, None,
+                                            ip(lvl, ctypes.c_int32), ip(ijk, ctypes.c_int64), nl.value,
+                                            ip(ptr, ctypes.c_int64), ip(src, ctypes.c_int32), src.size))
+    return lvl, ijk, ptr, src[:nz.value]
+
+
+def plan_adaptive_moments(V, T, k, p, kind, ids, max_elems=200, max_prot=0.25, top=2, n_splines=0, max_depth=0):
+    """Exact moments of the nonuniform tree, each function in its own leaf
+    (efie_plan_adaptive_moments): a list of arrays, [3,sp,sp,sp] (kind 0) or
+    [sp,sp,sp] (kind 1) with each leaf level's sp, and the leaf levels."""
+    lib = load_library()
+    m, keep = _mesh(V, T)
+    o = TreeOptions(max_elems, max_prot, top, n_splines, max_depth)
+    ids = np.ascontiguousarray(ids, dtype=np.int32)
+    ip = lambda a, t: a.ctypes.data_as(ctypes.POINTER(t))
+    need = ctypes.c_int64()
+    lvl = np.zeros(ids.size, np.int32)
+    sps = np.zeros(ids.size, np.int32)
+    _check(lib, lib.efie_plan_adaptive_moments(ctypes.byref(m), k, p, ctypes.byref(o), kind,
+                                               ip(ids, ctypes.c_int32), ids.size, None, 0, ctypes.byref(need),
+                                               ip(lvl, ctypes.c_int32), ip(sps, ctypes.c_int32)))
+    out = np.zeros(max(need.value, 1))
+    _check(lib, lib.efie_plan_adaptive_moments(ctypes.byref(m), k, p, ctypes.byref(o), kind,
+                                               ip(ids, ctypes.c_int32), ids.size, ip(out, ctypes.c_double),
+                                               out.size, None, None, None))
+    blocks, pos = [], 0
+    nc = 3 if kind == 0 else 1
+    for s in sps:
+        n = nc * int(s) ** 3
+        blk = out[pos:pos + n]
+        blocks.append(blk.reshape((3, s, s, s) if kind == 0 else (s, s, s)))
+        pos += n
+    return blocks, lvl
 
 
 def plan_matrix(V, T, k, p, grid_spacing, levels, level, which, options: Options | None = None):

@@ -1319,6 +1319,22 @@ void handle_set_error(efie_handle* h, const char* msg) {
 }  // namespace efie
 
 // ================================================================= C ABI
+namespace {
+AdaptiveOptions adaptive_options(const efie_tree_options* topt) {
+  AdaptiveOptions o;
+  if (topt) {
+    o.max_elems = topt->max_elems;
+    o.max_prot = topt->max_prot;
+    o.top = topt->top;
+    o.n_splines = topt->n_splines;
+    o.max_depth = topt->max_depth > 0 ? topt->max_depth : 30;
+    if (!(o.max_prot >= 0)) throw EfieError{EFIE_EINVAL, "max_prot must be >= 0"};
+  }
+  return o;
+}
+
+}  // namespace
+
 extern "C" {
 
 int efie_plan(const efie_mesh* mesh, double wavenumber, int spline_degree, double grid_spacing, int levels,
@@ -1340,17 +1356,9 @@ int efie_plan_adaptive(const efie_mesh* mesh, double wavenumber, int spline_degr
   return guarded(nullptr, [&] {
     check_mesh(mesh);
     if (max_levels < 0) throw EfieError{EFIE_EINVAL, "max_levels < 0"};
-    AdaptiveOptions o;
-    if (topt) {
-      o.max_elems = topt->max_elems;
-      o.max_prot = topt->max_prot;
-      o.top = topt->top;
-      o.n_splines = topt->n_splines;
-      o.max_depth = topt->max_depth > 0 ? topt->max_depth : 30;
-      if (!(o.max_prot >= 0)) throw EfieError{EFIE_EINVAL, "max_prot must be >= 0"};
-    }
     AdaptivePlan A;
-    build_adaptive_plan(A, mesh->xyz, mesh->n_vertices, mesh->tri, mesh->n_triangles, wavenumber, spline_degree, o);
+    build_adaptive_plan(A, mesh->xyz, mesh->n_vertices, mesh->tri, mesh->n_triangles, wavenumber, spline_degree,
+                        adaptive_options(topt));
     const int nl = (int)A.lv.size();
     if (n_levels) *n_levels = nl;
     if (near_pairs_rwg) *near_pairs_rwg = A.near_pairs_rwg;
@@ -1373,6 +1381,82 @@ int efie_plan_adaptive(const efie_mesh* mesh, double wavenumber, int spline_degr
         out.h = L.h;
         out.delta = L.delta;
       }
+    return EFIE_OK;
+  });
+}
+
+int efie_plan_adaptive_near(const efie_mesh* mesh, double wavenumber, int spline_degree,
+                            const efie_tree_options* topt, int64_t* n_leaves, int64_t* nnz, int32_t* leaf_level,
+                            int64_t* leaf_ijk, int64_t leaf_cap, int64_t* near_ptr, int32_t* near_src,
+                            int64_t near_cap) {
+  return guarded(nullptr, [&] {
+    check_mesh(mesh);
+    AdaptivePlan A;
+    build_adaptive_plan(A, mesh->xyz, mesh->n_vertices, mesh->tri, mesh->n_triangles, wavenumber, spline_degree,
+                        adaptive_options(topt));
+    const int64_t NL = (int64_t)A.leaf_level.size(), nz = (int64_t)A.near_src.size();
+    if (n_leaves) *n_leaves = NL;
+    if (nnz) *nnz = nz;
+    if ((leaf_level || leaf_ijk || near_ptr) && leaf_cap < NL) throw EfieError{EFIE_EINVAL, "leaf_cap too small"};
+    if (near_src && near_cap < nz) throw EfieError{EFIE_EINVAL, "near_cap too small"};
+    for (int64_t x = 0; x < NL; ++x) {
+      if (leaf_level) leaf_level[x] = A.leaf_level[x];
+      if (leaf_ijk)
+        for (int d = 0; d < 3; ++d) leaf_ijk[3 * x + d] = A.lv[A.leaf_level[x] - A.top].key[A.leaf_box[x]][d];
+    }
+    if (near_ptr) std::memcpy(near_ptr, A.near_ptr.data(), sizeof(int64_t) * (NL + 1));
+    if (near_src) std::memcpy(near_src, A.near_src.data(), sizeof(int32_t) * nz);
+    return EFIE_OK;
+  });
+}
+
+int efie_plan_adaptive_moments(const efie_mesh* mesh, double wavenumber, int spline_degree,
+                               const efie_tree_options* topt, int kind, const int32_t* ids, int64_t n_ids,
+                               double* out, int64_t out_len, int64_t* out_needed, int32_t* level_out,
+                               int32_t* sp_out) {
+  return guarded(nullptr, [&] {
+    check_mesh(mesh);
+    if (kind != 0 && kind != 1) throw EfieError{EFIE_EINVAL, "kind must be 0 (RWG) or 1 (triangle)"};
+    if (n_ids < 0 || (n_ids > 0 && !ids)) throw EfieError{EFIE_EINVAL, "ids is NULL"};
+    AdaptivePlan A;
+    build_adaptive_plan(A, mesh->xyz, mesh->n_vertices, mesh->tri, mesh->n_triangles, wavenumber, spline_degree,
+                        adaptive_options(topt), true);
+    const int ncomp = kind == 0 ? 3 : 1;
+    const std::vector<int32_t>& perm = kind == 0 ? A.rwg_perm : A.tri_perm;
+    const std::vector<int32_t>& leaf = kind == 0 ? A.rwg_leaf : A.tri_leaf;
+    const MomentBlocks& MB = kind == 0 ? A.mom_rwg : A.mom_tri;
+    std::vector<int64_t> rank(perm.size(), -1);
+    for (size_t i = 0; i < perm.size(); ++i) rank[perm[i]] = (int64_t)i;
+    int64_t need = 0;
+    for (int64_t j = 0; j < n_ids; ++j) {
+      if (ids[j] < 0 || ids[j] >= (int64_t)rank.size()) throw EfieError{EFIE_EINVAL, "index out of range"};
+      const AdaptiveLevel& L = A.lv[A.leaf_level[leaf[rank[ids[j]]]] - A.top];
+      need += (int64_t)ncomp * L.sp * L.sp * L.sp;
+    }
+    if (out_needed) *out_needed = need;
+    if (out && out_len < need) throw EfieError{EFIE_EINVAL, "output buffer too small"};
+    int64_t pos = 0;
+    for (int64_t j = 0; j < n_ids; ++j) {
+      const int64_t i = rank[ids[j]];
+      const int lvl = A.leaf_level[leaf[i]];
+      const int sp = A.lv[lvl - A.top].sp;
+      if (level_out) level_out[j] = lvl;
+      if (sp_out) sp_out[j] = sp;
+      if (out) {
+        double* dst = out + pos;
+        std::fill(dst, dst + (int64_t)ncomp * sp * sp * sp, 0.0);
+        const int* b = &MB.base[3 * i];
+        const int* e = &MB.ext[3 * i];
+        const double* src = &MB.data[MB.off[i]];
+        for (int c = 0; c < ncomp; ++c)
+          for (int a0 = 0; a0 < e[0]; ++a0)
+            for (int a1 = 0; a1 < e[1]; ++a1)
+              for (int a2 = 0; a2 < e[2]; ++a2)
+                dst[(((int64_t)c * sp + b[0] + a0) * sp + b[1] + a1) * sp + b[2] + a2] =
+                    src[(((int64_t)c * e[0] + a0) * e[1] + a1) * e[2] + a2];
+      }
+      pos += (int64_t)ncomp * sp * sp * sp;
+    }
     return EFIE_OK;
   });
 }

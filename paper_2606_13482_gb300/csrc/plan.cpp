@@ -556,6 +556,127 @@ void scatter_tiles(const std::vector<PieceTile>& tiles, int p, int ncomp, const 
     }
   }
 }
+
+// Functions sorted by leaf box: sorted RWG i is canonical rwg_perm[i] in leaf
+// rwg_box[i] (box_rwg_ptr: CSR over leaves); the same for triangles, with
+// tri_rank the inverse of tri_perm.
+struct LeafOrder {
+  const int32_t *rwg_perm, *rwg_box;
+  const int64_t* box_rwg_ptr;
+  const int32_t *tri_perm, *tri_box;
+  const int64_t* box_tri_ptr;
+  const int32_t* tri_rank;
+};
+
+// Exact moments (Q10) of every RWG and pulse in its leaf box's splines
+// (knots kcache[leaf], whose s' may differ from leaf to leaf), in sorted
+// order: dense blocks over each function's B-spline extents.  One leaf at a
+// time: every triangle used by the leaf's RWGs or pulses is integrated once
+// against the leaf's splines, and the tiles are combined into each user's
+// block; only the leaf's own blocks are written.  with_div adds the RWG
+// divergence moments of the direct factorization.
+void leaf_moments(const Geometry& g, int p, const std::vector<LeafKnots>& kcache, const LeafOrder& o, bool with_div,
+                  MomentBlocks& MR, MomentBlocks& MT, MomentBlocks& MD) {
+  const int64_t N = g.N, nt = g.nt;
+  const int64_t BD = (int64_t)kcache.size();
+  std::vector<double> qx, qw;
+  gauss_legendre01((3 * p + 4) / 2, qx, qw);
+  auto extents = [&](const LeafKnots& K, const int32_t* verts, int nvv, int* base, int* ext) {
+    for (int d = 0; d < 3; ++d) {
+      double mn = 1e300, mx = -1e300;
+      for (int a = 0; a < nvv; ++a) {
+        mn = std::min(mn, g.V[3 * verts[a] + d]);
+        mx = std::max(mx, g.V[3 * verts[a] + d]);
+      }
+      int a0 = find_span(K.U[d], p, K.sp, mn) - p;
+      int a1 = find_span(K.U[d], p, K.sp, mx);
+      a0 = std::max(a0, 0);
+      a1 = std::min(a1, K.sp - 1);
+      base[d] = a0;
+      ext[d] = a1 - a0 + 1;
+    }
+  };
+  MR.base.assign(3 * N, 0);
+  MR.ext.assign(3 * N, 0);
+  MR.off.assign(N + 1, 0);
+  for (int64_t i = 0; i < N; ++i) {
+    int32_t m = o.rwg_perm[i];
+    int32_t vv[6];
+    for (int a = 0; a < 3; ++a) {
+      vv[a] = g.T[3 * g.tri_pm[2 * m] + a];
+      vv[3 + a] = g.T[3 * g.tri_pm[2 * m + 1] + a];
+    }
+    extents(kcache[o.rwg_box[i]], vv, 6, &MR.base[3 * i], &MR.ext[3 * i]);
+    MR.off[i + 1] = MR.off[i] + 3LL * MR.ext[3 * i] * MR.ext[3 * i + 1] * MR.ext[3 * i + 2];
+  }
+  MR.data.assign(MR.off[N], 0.0);
+  MT.base.assign(3 * nt, 0);
+  MT.ext.assign(3 * nt, 0);
+  MT.off.assign(nt + 1, 0);
+  for (int64_t i = 0; i < nt; ++i) {
+    int32_t t = o.tri_perm[i];
+    extents(kcache[o.tri_box[i]], &g.T[3 * t], 3, &MT.base[3 * i], &MT.ext[3 * i]);
+    MT.off[i + 1] = MT.off[i] + (int64_t)MT.ext[3 * i] * MT.ext[3 * i + 1] * MT.ext[3 * i + 2];
+  }
+  MT.data.assign(MT.off[nt], 0.0);
+  if (with_div) {
+    MD.base = MR.base;
+    MD.ext = MR.ext;
+    MD.off.assign(N + 1, 0);
+    for (int64_t i = 0; i < N; ++i) MD.off[i + 1] = MD.off[i] + (MR.off[i + 1] - MR.off[i]) / 3;
+    MD.data.assign(MD.off[N], 0.0);
+  }
+#pragma omp parallel
+  {
+    std::vector<PieceTile> tiles;
+    std::vector<int32_t> tris;
+#pragma omp for schedule(dynamic, 4)
+    for (int64_t b = 0; b < BD; ++b) {
+      const LeafKnots& K = kcache[b];
+      tris.clear();
+      for (int64_t i = o.box_rwg_ptr[b]; i < o.box_rwg_ptr[b + 1]; ++i)
+        for (int s = 0; s < 2; ++s) tris.push_back(g.tri_pm[2 * o.rwg_perm[i] + s]);
+      for (int64_t i = o.box_tri_ptr[b]; i < o.box_tri_ptr[b + 1]; ++i) tris.push_back(o.tri_perm[i]);
+      std::sort(tris.begin(), tris.end());
+      tris.erase(std::unique(tris.begin(), tris.end()), tris.end());
+      for (int32_t t : tris) {
+        double tv[9], oc[3] = {0, 0, 0};
+        for (int a = 0; a < 3; ++a)
+          for (int d = 0; d < 3; ++d) {
+            tv[3 * a + d] = g.V[3 * g.T[3 * t + a] + d];
+            oc[d] += tv[3 * a + d] / 3.0;
+          }
+        triangle_tiles(K, tv, oc, qx, qw, tiles);
+        // RWGs of the leaf on this triangle: sigma / (2a) (x - x_free)
+        for (int64_t i = o.box_rwg_ptr[b]; i < o.box_rwg_ptr[b + 1]; ++i) {
+          const int32_t m = o.rwg_perm[i];
+          for (int s = 0; s < 2; ++s) {
+            if (g.tri_pm[2 * m + s] != t) continue;
+            const double* xf = &g.V[3 * g.free_pm[2 * m + s]];
+            const double sc = (s == 0 ? 1.0 : -1.0) / (2.0 * g.area[t]);
+            double coef[12] = {0};
+            for (int d = 0; d < 3; ++d) {
+              coef[4 * d] = sc * (oc[d] - xf[d]);
+              coef[4 * d + 1 + d] = sc;
+            }
+            scatter_tiles(tiles, p, 3, coef, &MR.base[3 * i], &MR.ext[3 * i], &MR.data[MR.off[i]]);
+            if (with_div) {
+              // div f = +-1 / a on c+- (the same sigma / (2a) times 2)
+              const double cd[4] = {2.0 * sc, 0, 0, 0};
+              scatter_tiles(tiles, p, 1, cd, &MD.base[3 * i], &MD.ext[3 * i], &MD.data[MD.off[i]]);
+            }
+          }
+        }
+        // the pulse of this triangle, if it belongs to the leaf: 1 / a
+        const int64_t ti = o.tri_rank[t];
+        if (o.tri_box[ti] == (int32_t)b) {
+          const double coef[4] = {1.0 / g.area[t], 0, 0, 0};
+          scatter_tiles(tiles, p, 1, coef, &MT.base[3 * ti], &MT.ext[3 * ti], &MT.data[MT.off[ti]]);
+        }
+      }
+    }
+  }
+}
 }  // namespace
 
 // ------------------------------------------------------------------ build
@@ -964,124 +1085,20 @@ void build_plan(Plan& P, const double* xyz, int64_t nv, const int32_t* tri, int6
   if (!with_moments) return;
 
   // exact moments (Q10): collapsed Gauss rule of degree >= 3p+1 per piece
-  {
-    std::vector<double> qx, qw;
-    gauss_legendre01((3 * p + 4) / 2, qx, qw);
-    const int sp = LD.sp;
-    auto knots_of = [&](int64_t b, LeafKnots& K) {
-      K.p = p;
-      K.sp = sp;
-      K.delta = LD.delta;
-      for (int d = 0; d < 3; ++d) {
-        K.lo[d] = P.root_lo[d] + LD.ijk[3 * b + d] * LD.h - LD.sb * LD.delta;
-        K.U[d] = open_knots(K.lo[d], K.lo[d] + (sp - p) * LD.delta, sp, p);
-      }
-    };
-    auto extents = [&](const LeafKnots& K, const int32_t* verts, int nvv, int* base, int* ext) {
-      for (int d = 0; d < 3; ++d) {
-        double mn = 1e300, mx = -1e300;
-        for (int a = 0; a < nvv; ++a) {
-          mn = std::min(mn, g.V[3 * verts[a] + d]);
-          mx = std::max(mx, g.V[3 * verts[a] + d]);
-        }
-        int a0 = find_span(K.U[d], p, sp, mn) - p;
-        int a1 = find_span(K.U[d], p, sp, mx);
-        a0 = std::max(a0, 0);
-        a1 = std::min(a1, sp - 1);
-        base[d] = a0;
-        ext[d] = a1 - a0 + 1;
-      }
-    };
-    // RWG blocks (sorted order)
-    MomentBlocks& MR = P.mom_rwg;
-    MR.base.assign(3 * N, 0);
-    MR.ext.assign(3 * N, 0);
-    MR.off.assign(N + 1, 0);
-    std::vector<LeafKnots> kcache(BD);
-    for (size_t b = 0; b < BD; ++b) knots_of((int64_t)b, kcache[b]);
-    for (int64_t i = 0; i < N; ++i) {
-      int32_t m = P.rwg_perm[i];
-      int32_t vv[6];
-      for (int a = 0; a < 3; ++a) {
-        vv[a] = g.T[3 * g.tri_pm[2 * m] + a];
-        vv[3 + a] = g.T[3 * g.tri_pm[2 * m + 1] + a];
-      }
-      extents(kcache[P.rwg_box[i]], vv, 6, &MR.base[3 * i], &MR.ext[3 * i]);
-      MR.off[i + 1] = MR.off[i] + 3LL * MR.ext[3 * i] * MR.ext[3 * i + 1] * MR.ext[3 * i + 2];
-    }
-    MR.data.assign(MR.off[N], 0.0);
-    MomentBlocks& MT = P.mom_tri;
-    MT.base.assign(3 * nt, 0);
-    MT.ext.assign(3 * nt, 0);
-    MT.off.assign(nt + 1, 0);
-    for (int64_t i = 0; i < nt; ++i) {
-      int32_t t = P.tri_perm[i];
-      extents(kcache[P.tri_box[i]], &g.T[3 * t], 3, &MT.base[3 * i], &MT.ext[3 * i]);
-      MT.off[i + 1] = MT.off[i] + (int64_t)MT.ext[3 * i] * MT.ext[3 * i + 1] * MT.ext[3 * i + 2];
-    }
-    MT.data.assign(MT.off[nt], 0.0);
-    MomentBlocks& MD = P.mom_div;
-    if (with_div) {
-      MD.base = MR.base;
-      MD.ext = MR.ext;
-      MD.off.assign(N + 1, 0);
-      for (int64_t i = 0; i < N; ++i) MD.off[i + 1] = MD.off[i] + (MR.off[i + 1] - MR.off[i]) / 3;
-      MD.data.assign(MD.off[N], 0.0);
-    }
-    // One leaf box at a time: every triangle used by the box's RWGs or pulses
-    // is integrated once against the box's splines, and the tiles are
-    // combined into each user's block.  Only the box's own blocks are written.
-#pragma omp parallel
-    {
-      std::vector<PieceTile> tiles;
-      std::vector<int32_t> tris;
-#pragma omp for schedule(dynamic, 4)
-      for (int64_t b = 0; b < (int64_t)BD; ++b) {
-        const LeafKnots& K = kcache[b];
-        tris.clear();
-        for (int64_t i = P.box_rwg_ptr[b]; i < P.box_rwg_ptr[b + 1]; ++i)
-          for (int s = 0; s < 2; ++s) tris.push_back(g.tri_pm[2 * P.rwg_perm[i] + s]);
-        for (int64_t i = P.box_tri_ptr[b]; i < P.box_tri_ptr[b + 1]; ++i) tris.push_back(P.tri_perm[i]);
-        std::sort(tris.begin(), tris.end());
-        tris.erase(std::unique(tris.begin(), tris.end()), tris.end());
-        for (int32_t t : tris) {
-          double tv[9], o[3] = {0, 0, 0};
-          for (int a = 0; a < 3; ++a)
-            for (int d = 0; d < 3; ++d) {
-              tv[3 * a + d] = g.V[3 * g.T[3 * t + a] + d];
-              o[d] += tv[3 * a + d] / 3.0;
-            }
-          triangle_tiles(K, tv, o, qx, qw, tiles);
-          // RWGs of the box on this triangle: sigma / (2a) (x - x_free)
-          for (int64_t i = P.box_rwg_ptr[b]; i < P.box_rwg_ptr[b + 1]; ++i) {
-            const int32_t m = P.rwg_perm[i];
-            for (int s = 0; s < 2; ++s) {
-              if (g.tri_pm[2 * m + s] != t) continue;
-              const double* xf = &g.V[3 * g.free_pm[2 * m + s]];
-              const double sc = (s == 0 ? 1.0 : -1.0) / (2.0 * g.area[t]);
-              double coef[12] = {0};
-              for (int d = 0; d < 3; ++d) {
-                coef[4 * d] = sc * (o[d] - xf[d]);
-                coef[4 * d + 1 + d] = sc;
-              }
-              scatter_tiles(tiles, p, 3, coef, &MR.base[3 * i], &MR.ext[3 * i], &MR.data[MR.off[i]]);
-              if (with_div) {
-                // div f = +-1 / a on c+- (the same sigma / (2a) times 2)
-                const double cd[4] = {2.0 * sc, 0, 0, 0};
-                scatter_tiles(tiles, p, 1, cd, &MD.base[3 * i], &MD.ext[3 * i], &MD.data[MD.off[i]]);
-              }
-            }
-          }
-          // the pulse of this triangle, if it belongs to the box: 1 / a
-          const int64_t ti = P.tri_rank[t];
-          if (P.tri_box[ti] == (int32_t)b) {
-            const double coef[4] = {1.0 / g.area[t], 0, 0, 0};
-            scatter_tiles(tiles, p, 1, coef, &MT.base[3 * ti], &MT.ext[3 * ti], &MT.data[MT.off[ti]]);
-          }
-        }
-      }
+  std::vector<LeafKnots> kcache(BD);
+  for (size_t b = 0; b < BD; ++b) {
+    LeafKnots& K = kcache[b];
+    K.p = p;
+    K.sp = LD.sp;
+    K.delta = LD.delta;
+    for (int d = 0; d < 3; ++d) {
+      K.lo[d] = P.root_lo[d] + LD.ijk[3 * b + d] * LD.h - LD.sb * LD.delta;
+      K.U[d] = open_knots(K.lo[d], K.lo[d] + (LD.sp - p) * LD.delta, LD.sp, p);
     }
   }
+  LeafOrder ord{P.rwg_perm.data(), P.rwg_box.data(), P.box_rwg_ptr.data(), P.tri_perm.data(), P.tri_box.data(),
+                P.box_tri_ptr.data(), P.tri_rank.data()};
+  leaf_moments(g, p, kcache, ord, with_div, P.mom_rwg, P.mom_tri, P.mom_div);
 }
 
 // ------------------------------------------------------------ nonuniform tree
@@ -1125,7 +1142,7 @@ double protrusion(const std::vector<int32_t>& ids, const std::vector<double>& pt
 }  // namespace
 
 void build_adaptive_plan(AdaptivePlan& A, const double* xyz, int64_t nv, const int32_t* tri, int64_t nt,
-                         double k, int p, const AdaptiveOptions& o) {
+                         double k, int p, const AdaptiveOptions& o, bool with_moments) {
   if (p < 1 || p > 6) fail(-1, "spline degree p must be in 1..6");
   if (!(k > 0)) fail(-1, "wavenumber must be positive");
   if (o.top < 1) fail(-1, "top grid level must be >= 1");
@@ -1315,35 +1332,69 @@ void build_adaptive_plan(AdaptivePlan& A, const double* xyz, int64_t nv, const i
     }
     L.n_far_pairs = n;
   }
-  // near pairs: leaves x (level lx) and y (level ly) are near when, on the
-  // coarser of the two levels, the ancestors are adjacent or equal
-  A.near_pairs_rwg = A.near_pairs_tri = 0;
-  std::vector<int64_t> stack;
-  for (int lx = o.top; lx <= D; ++lx) {
-    const AdaptiveLevel& LX = A.lv[lx - o.top];
-    for (size_t x = 0; x < LX.key.size(); ++x) {
-      if (!LX.leaf[x]) continue;
-      const int64_t nrx = LX.n_rwg[x], ntx = LX.n_tri[x];
-      // leaves on levels ly <= lx next to (or equal to) x's ancestor
-      for (int ly = o.top; ly <= lx; ++ly) {
-        const int sh = lx - ly;
-        const Key anc{LX.key[x][0] >> sh, LX.key[x][1] >> sh, LX.key[x][2] >> sh};
-        const AdaptiveLevel& LY = A.lv[ly - o.top];
-        for (int a = -1; a <= 1; ++a)
-          for (int b = -1; b <= 1; ++b)
-            for (int c = -1; c <= 1; ++c) {
-              const int64_t y = find(ly, Key{anc[0] + a, anc[1] + b, anc[2] + c});
-              if (y < 0 || !LY.leaf[y]) continue;
-              A.near_pairs_rwg += nrx * LY.n_rwg[y];
-              A.near_pairs_tri += ntx * LY.n_tri[y];
-            }
+  // leaves of all levels, level by level from the top
+  std::vector<std::vector<int64_t>> leaf_of(A.lv.size());
+  A.leaf_level.clear();
+  A.leaf_box.clear();
+  for (int ell = o.top; ell <= D; ++ell) {
+    const AdaptiveLevel& L = A.lv[ell - o.top];
+    leaf_of[ell - o.top].assign(L.key.size(), -1);
+    for (size_t b = 0; b < L.key.size(); ++b)
+      if (L.leaf[b]) {
+        leaf_of[ell - o.top][b] = (int64_t)A.leaf_level.size();
+        A.leaf_level.push_back(ell);
+        A.leaf_box.push_back((int64_t)b);
       }
-      // leaves on deeper levels under a box of level lx next to x
-      if (lx == D) continue;
+  }
+  const int64_t NL = (int64_t)A.leaf_level.size();
+  // functions sorted by leaf, then canonical id
+  auto sort_by_leaf = [&](const std::vector<int32_t>& lvl, const std::vector<int32_t>& box, int64_t n,
+                          std::vector<int32_t>& perm, std::vector<int32_t>& leaf, std::vector<int64_t>& ptr) {
+    std::vector<std::pair<int64_t, int32_t>> kk(n);
+    for (int64_t i = 0; i < n; ++i) kk[i] = {leaf_of[lvl[i] - o.top][box[i]], (int32_t)i};
+    std::sort(kk.begin(), kk.end());
+    perm.resize(n);
+    leaf.resize(n);
+    ptr.assign(NL + 1, 0);
+    for (int64_t i = 0; i < n; ++i) {
+      perm[i] = kk[i].second;
+      leaf[i] = (int32_t)kk[i].first;
+      ptr[kk[i].first + 1]++;
+    }
+    for (int64_t x = 0; x < NL; ++x) ptr[x + 1] += ptr[x];
+  };
+  sort_by_leaf(A.rwg_level, A.rwg_box, N, A.rwg_perm, A.rwg_leaf, A.leaf_rwg_ptr);
+  sort_by_leaf(A.tri_level, A.tri_box, nt, A.tri_perm, A.tri_leaf, A.leaf_tri_ptr);
+  A.tri_rank.assign(nt, 0);
+  for (int64_t i = 0; i < nt; ++i) A.tri_rank[A.tri_perm[i]] = (int32_t)i;
+  // near leaves: x (level lx) and y (level ly) are near when, on the coarser
+  // of the two levels, the ancestors are adjacent or equal
+  A.near_ptr.assign(NL + 1, 0);
+  A.near_src.clear();
+  A.near_pairs_rwg = A.near_pairs_tri = 0;
+  std::vector<int64_t> stack, ys;
+  for (int64_t xl = 0; xl < NL; ++xl) {
+    const int lx = A.leaf_level[xl];
+    const AdaptiveLevel& LX = A.lv[lx - o.top];
+    const Key& kx = LX.key[A.leaf_box[xl]];
+    ys.clear();
+    // leaves on levels ly <= lx next to (or equal to) x's ancestor
+    for (int ly = o.top; ly <= lx; ++ly) {
+      const int sh = lx - ly;
+      const Key anc{kx[0] >> sh, kx[1] >> sh, kx[2] >> sh};
       for (int a = -1; a <= 1; ++a)
         for (int b = -1; b <= 1; ++b)
           for (int c = -1; c <= 1; ++c) {
-            const int64_t z = find(lx, Key{LX.key[x][0] + a, LX.key[x][1] + b, LX.key[x][2] + c});
+            const int64_t y = find(ly, Key{anc[0] + a, anc[1] + b, anc[2] + c});
+            if (y >= 0 && leaf_of[ly - o.top][y] >= 0) ys.push_back(leaf_of[ly - o.top][y]);
+          }
+    }
+    // leaves on deeper levels under a box of level lx next to x
+    if (lx < D)
+      for (int a = -1; a <= 1; ++a)
+        for (int b = -1; b <= 1; ++b)
+          for (int c = -1; c <= 1; ++c) {
+            const int64_t z = find(lx, Key{kx[0] + a, kx[1] + b, kx[2] + c});
             if (z < 0 || LX.leaf[z]) continue;
             // depth-first over the descendants of z: (level, box) packed
             stack.assign(1, ((int64_t)lx << 40) | z);
@@ -1355,18 +1406,40 @@ void build_adaptive_plan(AdaptivePlan& A, const double* xyz, int64_t nv, const i
               const AdaptiveLevel& LE = A.lv[le - o.top];
               for (int64_t j = LE.child_ptr[bz]; j < LE.child_ptr[bz + 1]; ++j) {
                 const int64_t cy = LE.child[j];
-                const AdaptiveLevel& LC = A.lv[le + 1 - o.top];
-                if (LC.leaf[cy]) {
-                  A.near_pairs_rwg += nrx * LC.n_rwg[cy];
-                  A.near_pairs_tri += ntx * LC.n_tri[cy];
-                } else {
+                const int64_t lid = leaf_of[le + 1 - o.top][cy];
+                if (lid >= 0)
+                  ys.push_back(lid);
+                else
                   stack.push_back(((int64_t)(le + 1) << 40) | cy);
-                }
               }
             }
           }
+    std::sort(ys.begin(), ys.end());
+    for (int64_t y : ys) {
+      A.near_src.push_back((int32_t)y);
+      A.near_pairs_rwg += (A.leaf_rwg_ptr[xl + 1] - A.leaf_rwg_ptr[xl]) * (A.leaf_rwg_ptr[y + 1] - A.leaf_rwg_ptr[y]);
+      A.near_pairs_tri += (A.leaf_tri_ptr[xl + 1] - A.leaf_tri_ptr[xl]) * (A.leaf_tri_ptr[y + 1] - A.leaf_tri_ptr[y]);
+    }
+    A.near_ptr[xl + 1] = (int64_t)A.near_src.size();
+  }
+  if (!with_moments) return;
+  // exact moments in each function's own leaf, with that level's splines
+  std::vector<LeafKnots> kcache(NL);
+  for (int64_t x = 0; x < NL; ++x) {
+    const AdaptiveLevel& L = A.lv[A.leaf_level[x] - o.top];
+    const Key& kx = L.key[A.leaf_box[x]];
+    LeafKnots& K = kcache[x];
+    K.p = p;
+    K.sp = L.sp;
+    K.delta = L.delta;
+    for (int d = 0; d < 3; ++d) {
+      K.lo[d] = A.root_lo[d] + (double)kx[d] * L.h - L.sb * L.delta;
+      K.U[d] = open_knots(K.lo[d], K.lo[d] + (L.sp - p) * L.delta, L.sp, p);
     }
   }
+  LeafOrder ord{A.rwg_perm.data(), A.rwg_leaf.data(), A.leaf_rwg_ptr.data(), A.tri_perm.data(),
+                A.tri_leaf.data(), A.leaf_tri_ptr.data(), A.tri_rank.data()};
+  MomentBlocks unused;
+  leaf_moments(g, p, kcache, ord, false, A.mom_rwg, A.mom_tri, unused);
 }
-
 }  // namespace efie

@@ -142,13 +142,25 @@ struct AdaptivePlan {
   double root_lo[3] = {0, 0, 0}, root_edge = 0;
   int D = 0, top = 0, p = 0;
   std::vector<AdaptiveLevel> lv;            // lv[ell - top]
-  std::vector<int32_t> rwg_level, rwg_box, tri_level, tri_box;
+  std::vector<int32_t> rwg_level, rwg_box, tri_level, tri_box;   // canonical function -> its leaf
+  // leaves of all levels, numbered level by level from the top, boxes in key order
+  std::vector<int32_t> leaf_level;
+  std::vector<int64_t> leaf_box;            // index of the leaf on its level
+  // functions sorted by leaf (then canonical id): sorted -> canonical, sorted -> leaf
+  std::vector<int32_t> rwg_perm, rwg_leaf, tri_perm, tri_leaf, tri_rank;
+  std::vector<int64_t> leaf_rwg_ptr, leaf_tri_ptr;
+  // near leaves (CSR over leaves, sources ascending): leaves whose ancestors on
+  // the coarser of their two levels are adjacent or equal
+  std::vector<int64_t> near_ptr;
+  std::vector<int32_t> near_src;
   // ordered pairs of functions whose leaves are near (self pairs included)
   int64_t near_pairs_rwg = 0, near_pairs_tri = 0;
+  // exact moments in each function's leaf (with_moments), sorted order
+  MomentBlocks mom_rwg, mom_tri;
 };
 
 void build_adaptive_plan(AdaptivePlan& A, const double* xyz, int64_t nv, const int32_t* tri, int64_t nt,
-                         double k, int p, const AdaptiveOptions& o);
+                         double k, int p, const AdaptiveOptions& o, bool with_moments = false);
 
 // Spline helpers exposed for tests of the host code
 std::vector<double> open_knots(double lo, double hi, int ns, int p);

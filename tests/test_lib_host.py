@@ -153,6 +153,41 @@ def test_plan_adaptive_matches_oracle(lib):
         G.plan_adaptive(*E.icosphere(14, 0.5), 2 * np.pi, 3, max_elems=60, top=4)
 
 
+def test_plan_adaptive_near_and_moments_match_oracle(lib):
+    """Leaves, near-leaf lists and per-leaf exact moments of the nonuniform
+    tree, built by the library's host code, against `oracle.nonuniform`
+    (moments of every function in its own leaf's splines, sampled ids)."""
+    G, _ = lib
+    from oracle import nonuniform as NU
+    from oracle.geometry import build_rwg
+    from oracle.moments import pulse_moments, rwg_moments
+    V, T = E.icosphere(14, 0.5)
+    m = build_rwg(V, T)
+    k = 2 * np.pi
+    tr = NU.build_adaptive_tree(m, k, 3, max_elems=60, top=2)
+    lvl, ijk, ptr, src = G.plan_adaptive_near(V, T, k, 3, max_elems=60, top=2)
+    olvl, oijk, _, _ = NU.leaf_index(tr)
+    assert np.array_equal(lvl, olvl) and np.array_equal(ijk, oijk)
+    nb = np.zeros((len(lvl), len(lvl)), dtype=bool)
+    for x in range(len(lvl)):
+        nb[x, src[ptr[x]:ptr[x + 1]]] = True
+        assert np.all(np.diff(src[ptr[x]:ptr[x + 1]]) > 0)
+    assert np.array_equal(nb, NU.near_leaf_pairs(tr))
+    rng = np.random.default_rng(4)
+    for kind, n in ((0, m.N), (1, m.Nt)):
+        ids = rng.choice(n, 40, replace=False).astype(np.int32)
+        blocks, levels = G.plan_adaptive_moments(V, T, k, 3, kind, ids, max_elems=60, top=2)
+        flv = tr.rwg_level if kind == 0 else tr.tri_level
+        assert np.array_equal(levels, flv[ids]) and len(set(levels)) == 2
+        for ell in set(levels.tolist()):
+            sel = np.nonzero(levels == ell)[0]
+            view = NU._LevelView(tr, ell)
+            ref = (rwg_moments if kind == 0 else pulse_moments)(m, view, ids[sel])
+            got = np.stack([blocks[i] for i in sel])
+            assert got.shape == ref.shape
+            assert np.abs(got - ref).max() < 1e-13 * np.abs(ref).max()
+
+
 def test_invalid_inputs(lib):
     G, _ = lib
     V, T = E.icosphere(4, 0.5)
