@@ -157,14 +157,15 @@ int efie_plan_adaptive(const efie_mesh *mesh, double wavenumber, int spline_degr
  * near_ptr [n_leaves + 1] and near_src [nnz] (CSR, sources ascending) list,
  * for each leaf, the leaves whose ancestors on the coarser of the two levels
  * are adjacent or equal.  Call with the arrays NULL to get *n_leaves and
- * *nnz; each array must then hold that many entries (leaf_cap >= n_leaves,
- * near_cap >= nnz, else EFIE_EINVAL).  Other errors as efie_plan_adaptive. */
+ * *nnz; each array must then hold that many entries: leaf_cap >= n_leaves
+ * for leaf_level and leaf_ijk, leaf_cap >= n_leaves + 1 when near_ptr is
+ * given (it is sized by leaf_cap too), near_cap >= nnz; else EFIE_EINVAL.  Other errors as efie_plan_adaptive. */
 int efie_plan_adaptive_near(const efie_mesh *mesh, double wavenumber, int spline_degree,
                             const efie_tree_options *topt, int64_t *n_leaves, int64_t *nnz,
                             int32_t *leaf_level, int64_t *leaf_ijk, int64_t leaf_cap,
                             int64_t *near_ptr, int32_t *near_src, int64_t near_cap);
 
-/* Host-only: exact moments (Q10) of the nonuniform tree, each function in its
+/* Host-only: exact moments of the nonuniform tree, each function in its
  * own leaf's splines (that level's s', knots and buffers).  kind 0: RWGs
  * (canonical edge ids), [3][sp][sp][sp] per id; kind 1: triangles, pulse
  * 1/area, [sp][sp][sp] per id.  The blocks are packed one after the other in
@@ -187,7 +188,7 @@ int efie_plan_matrix(const efie_mesh *mesh, double wavenumber, int spline_degree
                      int level, int which, double *out, int64_t out_len,
                      int32_t *rows, int32_t *cols);
 
-/* Host-only: the exact moments (Q10) of the leaf splines (Eq. TAfactor,
+/* Host-only: the exact moments of the leaf splines (Eq. TAfactor,
  * Sec. VI-A) that efie_setup uploads, for a list of basis functions.
  *   kind 0: RWG edges (canonical edge index, the order of efie_rwg_edges),
  *           out[i][d][a][b][c] = integral over the RWG support of f_m,d N_abc;
@@ -207,7 +208,7 @@ int efie_plan_moments(const efie_mesh *mesh, double wavenumber, int spline_degre
                       int64_t out_len, int32_t *sp_out);
 
 /* Build every setup product on the current device: geometry, octree,
- * transfers, projectors, exact moments (Q10), kernel spectra per level and
+ * transfers, projectors, exact moments, kernel spectra per level and
  * offset, and the FP64 near field (Sec. VI-A: RWG pairs for A and triangle
  * pairs for V, each in adjacent leaf boxes).  opt may be NULL (defaults).
  * On success *out owns all device memory until efie_destroy. */
@@ -235,16 +236,18 @@ int efie_rhs_planewave(efie_handle *h, int n_rhs, const double *khat, const doub
  * array of the library (4096 plane waves, 192 KiB), which every GPU that loads
  * the library keeps until the process exits.  n_rhs above 4096 returns
  * EFIE_EINVAL.  The paper has no counterpart; this is a deployment variant.
- * Notes: the first call on a device looks up that array's device address
+ * Notes: the handle's device must be current (else EFIE_EINVAL); the first
+ * call on a device looks up that array's device address
  * (cudaGetSymbolAddress) with the device current, so make it before any
- * stream capture; all calls on a device share the array, so calls whose
+ * stream capture, and the address it keeps is valid until that device is
+ * reset; all calls on a device share the array, so calls whose
  * copies and kernels overlap on the GPU race -- serialise them; the call
  * synchronises `stream` before returning. */
 int efie_rhs_planewave_noalloc(efie_handle *h, int n_rhs, const double *khat, const double *pol,
                                void *rhs, void *stream);
 
 /* y = T x for n_rhs vectors (device c128 [n_rhs][N]; x and y must not alias).
- * Uses the handle's precision.  Steps a1-a10: charges, anterpolation, upward
+ * Uses the handle's precision.  Charges, anterpolation, upward
  * transfers, stabilized FFT translations, downward transfers, interpolation,
  * near field. */
 int efie_matvec(efie_handle *h, const void *x, void *y, int n_rhs, void *stream);

@@ -8,10 +8,10 @@
   child basis, of parent spline j restricted to the child's extended domain,
   obtained by inserting knots into the unit curve e_j.
 * Knot-removal stabilization (Sec. V-B, Table I): the first and the last
-  s_remove interior knots are removed (reading Q2/Q3: s_remove per side);
+  s_remove interior knots are removed (Table I's count read as per side);
   S maps equidistant to stabilized splines by knot insertion; interpolation
   points are s_hat equispaced points including both ends of the extended
-  domain (reading Q4); P = B_stab^{-1} S, W_stab = P^T G P.
+  domain (equispaced, both ends included); P = B_stab^{-1} S, W_stab = P^T G P.
 
 Knot positions are handled in integer lattice units (the finest spacing of the
 pair of levels involved), so equality tests between knots are exact.
@@ -156,7 +156,7 @@ def stabilization_matrix(eq_knots, stab_knots, p):
 
 
 def interpolation_points(lo, hi, n_points):
-    """n_points equispaced points including both ends (reading Q4)."""
+    """n_points equispaced points including both ends (Eq. avgknots for p = 3)."""
     return lo + (hi - lo) * np.arange(n_points) / (n_points - 1)
 
 

@@ -5,7 +5,7 @@ Sec. VI-A.  With div f_m = sum_c Sigma[m,c] phi_c and phi_c = 1/a_c:
 
     A[m,n] = int int f_m(x) . f_n(y) g(x,y)
     V[c,c'] = int int phi_c(x) g(x,y) phi_c'(y) = (1/(a_c a_c')) int_c int_c' g
-    T = jk A + (jk)^-1 Sigma V Sigma^T                       (reading of Q1)
+    T = jk A + (jk)^-1 Sigma V Sigma^T                       (sign fixed by the Mie series; Eq. matTPhi's minus is absorbed)
 
 e^{j w t} convention, g = exp(-jkR)/(4 pi R).  The paper writes the scalar part
 as -(jk)^-1 T_Phi with a leading minus inside Eq. matTPhi and later
@@ -191,7 +191,7 @@ def assemble_dense(mesh: RWGMesh, k, kernel=None, **quad):
 
 
 def efie_matrix(mesh: RWGMesh, k, A=None, V=None, **quad):
-    """T = jk A + (jk)^-1 Sigma V Sigma^T (reading Q1)."""
+    """T = jk A + (jk)^-1 Sigma V Sigma^T (the physical sign, pinned by the Mie series)."""
     if A is None or V is None:
         A, V = assemble_dense(mesh, k, **quad)
     S = mesh.sigma_dense()

@@ -2,7 +2,7 @@
 infrastructure only).  FP64 throughout; translations either by the plain
 Toeplitz definition (dense G per box pair) or by NumPy FFTs of size
 n = 2 s_hat - 1 (any n >= 2 s_hat - 1 gives the same result up to rounding,
-reading Q9).
+the paper does not fix n).
 
 Steps, in the paper's order:
   a1  rho = Sigma^T j                                        (Sec. VI-A)

@@ -1,6 +1,6 @@
 """Plain restarted GMRES / flexible GMRES in FP64 complex (oracle; test
 infrastructure only).  The paper states only that an iterative solver is used
-(Sec. II); reading Q12: GMRES(m), x0 = 0, success when the true relative
+(Sec. II); the paper names GMRES without its details; here GMRES(m), x0 = 0, success when the true relative
 residual ||b - T x|| / ||b|| <= tol.  Arnoldi with classical Gram-Schmidt
 applied twice (CGS2), Givens rotations for the least-squares problem.
 """

@@ -5,7 +5,7 @@ Eq. TAfactor and Sec. VI-A: for a basis function associated with leaf box b,
     m^phi_c[i] = int_c (1/a_c) l_{i,b}(x) dS     (pulse)
 with l_{i,b} the tensor-product B-splines of the box's extended equidistant
 knot vector (Sec. III-B).  The paper says only "numerical quadrature"; we
-integrate exactly (reading Q10): each triangle is split by every interior knot
+integrate exactly (the paper only says numerical quadrature): each triangle is split by every interior knot
 plane into convex pieces on which the integrand is a polynomial of degree
 <= 3p+1, each piece is fanned into triangles and integrated with a collapsed
 Gauss rule of that degree.

@@ -11,7 +11,7 @@ Spline parameters per level ell (box edge h_ell), from the deepest level D up
 to the top grid level:
   * s_D = n_splines (default p + 4, Sec. VII-B); going up, s stays while the
     box edge is below lambda/2 and becomes 2s - p otherwise (Sec. IV-C, IV-D;
-    reading Q8, the level's own box edge decides); delta_ell = h_ell/(s_ell - p).
+    the level's own box edge decides); delta_ell = h_ell/(s_ell - p).
   * buffer splines (Sec. IV-C, IV-D, including the rule for leaves on the
     parent level):  s_b = max(ceil(s_b,child / 2), s_b,leaves) for constant s,
     s_b = max(s_b,child, s_b,leaves) for s -> 2s - p, where
@@ -19,11 +19,11 @@ to the top grid level:
     beyond their boxes / delta_ell).
 
 Every basis function sits in the leaf holding its point (edge midpoint for an
-RWG, centroid for a triangle; reading Q6) and is anterpolated and interpolated
+RWG, centroid for a triangle) and is anterpolated and interpolated
 there with that box's splines.  The grids of every box go up by knot
 insertion and come down by the transpose; level ell translates the pairs of
 non-adjacent boxes with adjacent parents, and every non-adjacent pair on the
-top grid level (reading Q7).  Two leaves x, y on levels lx <= ly are near
+top grid level (standard H2 admissibility).  Two leaves x, y on levels lx <= ly are near
 when x and the ancestor of y on level lx are adjacent or equal: the
 inadmissible leaf blocks of the level-consistent block tree.  Every pair of
 leaves is thus either near or translated on exactly one level.

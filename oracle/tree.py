@@ -5,18 +5,18 @@ infrastructure only).
   on the bounding-box centre with edge h_leaf 2^D, D the smallest depth with
   h_leaf 2^D >= bounding-box edge.  Box index floor((x - root_lo)/h_l), clamped;
   an RWG sits in the box of its edge midpoint, a triangle in the box of its
-  centroid (reading Q6).
+  centroid (the paper does not say; ties go to the box below by the floor).
 * Leaf level: s = p + 4 splines by default (Sec. VII-B), knot spacing
   delta = grid_spacing, box edge h = (s - p) delta, buffer splines
   s_b = ceil(max protrusion / delta) (Sec. III-B).  We require 2 s_b < s - p at
   every level, so the extended interpolation domains of boxes two apart stay
   disjoint (Sec. VII-B: one buffer spline at s = p + 4 leaves half a box).
-* Going to the parent level (Sec. IV-C, IV-D; reading Q8: the parent's box
-  edge decides): if h_parent < lambda/2, s stays and s_b = ceil(s_b/2); else
-  s = 2s - p and s_b stays.  s' = s + 2 s_b, s_hat = s' - 2 s_remove(p).
-* `levels` levels, counted up from the leaf, carry grids (reading Q5); the
+* Going to the parent level (Sec. IV-C, IV-D; the parent's box edge, without
+  buffers, is the edge length compared with lambda/2): if h_parent < lambda/2,
+  s stays and s_b = ceil(s_b/2); else s = 2s - p and s_b stays.  s' = s + 2 s_b, s_hat = s' - 2 s_remove(p).
+* `levels` levels, counted up from the leaf, carry grids (a parameter of this library, not the paper's); the
   top grid level translates every non-adjacent pair, lower levels the standard
-  interaction list (non-adjacent boxes with adjacent parents, reading Q7).
+  interaction list (non-adjacent boxes with adjacent parents: the standard H2 rule, which the paper does not spell out).
   Near field: leaf boxes with |dx|_inf <= 1.
 """
 from __future__ import annotations

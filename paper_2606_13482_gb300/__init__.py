@@ -160,6 +160,19 @@ def _mesh(V, T):
     return m, (V, T)
 
 
+def planewave_args(khat, pol, out_shape=None, n_unknowns=None):
+    """Directions and polarisations as contiguous float64 [n, 3] arrays of the
+    same n; with out_shape, also checks that the output is [n, n_unknowns].
+    The C ABI takes no sizes for these arrays, so this is their only guard."""
+    khat = np.ascontiguousarray(np.atleast_2d(khat), dtype=np.float64)
+    pol = np.ascontiguousarray(np.atleast_2d(pol), dtype=np.float64)
+    if khat.ndim != 2 or khat.shape[1] != 3 or pol.shape != khat.shape:
+        raise ValueError(f"khat and pol must both be [n, 3] (got {khat.shape} and {pol.shape})")
+    if out_shape is not None and tuple(out_shape) != (khat.shape[0], n_unknowns):
+        raise ValueError(f"out must be [{khat.shape[0]}, {n_unknowns}] (got {list(out_shape)})")
+    return khat, pol
+
+
 def _check(lib, rc, h=None):
     if rc < 0:
         raise EfieError(rc, lib.efie_last_error(h).decode())
@@ -236,15 +249,16 @@ def plan_adaptive_near(V, T, k, p, max_elems=200, max_prot=0.25, top=2, n_spline
     nl, nz = ctypes.c_int64(), ctypes.c_int64()
     _check(lib, lib.efie_plan_adaptive_near(ctypes.byref(m), k, p, ctypes.byref(o), ctypes.byref(nl),
                                             ctypes.byref(nz), None, None, 0, None, None, 0))
-    lvl = np.zeros(nl.value, np.int32)
-    ijk = np.zeros((nl.value, 3), np.int64)
-    ptr = np.zeros(nl.value + 1, np.int64)
+    cap = nl.value + 1                      # near_ptr holds n_leaves + 1 entries
+    lvl = np.zeros(cap, np.int32)
+    ijk = np.zeros((cap, 3), np.int64)
+    ptr = np.zeros(cap, np.int64)
     src = np.zeros(max(nz.value, 1), np.int32)
     ip = lambda a, t: a.ctypes.data_as(ctypes.POINTER(t))
     _check(lib, lib.efie_plan_adaptive_near(ctypes.byref(m), k, p, ctypes.byref(o), None, None,
-                                            ip(lvl, ctypes.c_int32), ip(ijk, ctypes.c_int64), nl.value,
+                                            ip(lvl, ctypes.c_int32), ip(ijk, ctypes.c_int64), cap,
                                             ip(ptr, ctypes.c_int64), ip(src, ctypes.c_int32), src.size))
-    return lvl, ijk, ptr, src[:nz.value]
+    return lvl[:nl.value], ijk[:nl.value], ptr, src[:nz.value]
 
 
 def plan_adaptive_moments(V, T, k, p, kind, ids, max_elems=200, max_prot=0.25, top=2, n_splines=0, max_depth=0):
@@ -360,8 +374,7 @@ class EFIE:
 
     def rhs_planewave(self, khat, pol):
         import torch
-        khat = np.ascontiguousarray(np.atleast_2d(khat), dtype=np.float64)
-        pol = np.ascontiguousarray(np.atleast_2d(pol), dtype=np.float64)
+        khat, pol = planewave_args(khat, pol)
         out = torch.empty((khat.shape[0], self.N), dtype=torch.complex128, device="cuda")
         _check(self.lib, self.lib.efie_rhs_planewave(
             self.h, khat.shape[0], khat.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
@@ -372,8 +385,7 @@ class EFIE:
     def rhs_planewave_noalloc(self, khat, pol, out):
         """Plane-wave right-hand sides into the caller's complex128 CUDA tensor
         `out` [n, N] without any device allocation by the library."""
-        khat = np.ascontiguousarray(np.atleast_2d(khat), dtype=np.float64)
-        pol = np.ascontiguousarray(np.atleast_2d(pol), dtype=np.float64)
+        khat, pol = planewave_args(khat, pol, tuple(out.shape), self.N)
         _check(self.lib, self.lib.efie_rhs_planewave_noalloc(
             self.h, khat.shape[0], khat.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
             pol.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), self._vec(out), self._stream()), self.h)

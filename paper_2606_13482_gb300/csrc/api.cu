@@ -1,5 +1,5 @@
 // C ABI of the GB300 fast EFIE library: setup orchestration, the matvec
-// pipeline (steps a1-a10) and the batched GMRES / FGMRES driver.
+// pipeline (charges, anterpolation, transfers, translations, interpolation, near field) and the batched GMRES / FGMRES driver.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -49,9 +49,10 @@ void cuda_check(cudaError_t e, const char* what) {
                     std::string(what) + ": " + cudaGetErrorString(e)};
 }
 
-// device allocation tracker
+// device allocation tracker: every allocation of a handle, with its size, so
+// that released buffers leave the device_mem_limit budget
 struct DevMem {
-  std::vector<void*> ptrs;
+  std::vector<std::pair<void*, int64_t>> ptrs;
   int64_t bytes = 0, limit = 0;
   template <typename T>
   T* alloc(int64_t n) {
@@ -61,7 +62,7 @@ struct DevMem {
       throw EfieError{EFIE_ENOMEM, "device_mem_limit exceeded (" + std::to_string(bytes + b) + " bytes)"};
     void* p = nullptr;
     cuda_check(cudaMalloc(&p, (size_t)b), "cudaMalloc");
-    ptrs.push_back(p);
+    ptrs.push_back({p, b});
     bytes += b;
     return (T*)p;
   }
@@ -72,15 +73,17 @@ struct DevMem {
     return p;
   }
   void release(void* p) {
-    for (auto& q : ptrs)
-      if (q == p) {
-        cudaFree(q);
-        q = nullptr;
+    if (!p) return;
+    for (size_t i = 0; i < ptrs.size(); ++i)
+      if (ptrs[i].first == p) {
+        cudaFree(p);
+        bytes -= ptrs[i].second;
+        ptrs.erase(ptrs.begin() + (int64_t)i);
+        return;
       }
   }
   ~DevMem() {
-    for (void* p : ptrs)
-      if (p) cudaFree(p);
+    for (auto& q : ptrs) cudaFree(q.first);
   }
 };
 
@@ -952,6 +955,22 @@ void setup_impl(efie_handle* h, const efie_mesh* mesh, double k, int p, double g
 }
 
 // ------------------------------------------------------------- GMRES
+// Device buffers of one call, released on every exit (also when an
+// allocation or a launch throws).
+struct Workspace {
+  DevMem& M;
+  std::vector<void*> p;
+  template <typename T>
+  T* take(int64_t n) {
+    T* q = M.alloc<T>(n);
+    p.push_back(q);
+    return q;
+  }
+  ~Workspace() {
+    for (void* q : p) M.release(q);
+  }
+};
+
 struct Givens {
   std::vector<std::complex<double>> H, cs, sn, g;
 };
@@ -966,17 +985,17 @@ int solve_impl(efie_handle* h, const double2* b, double2* x, int n_rhs, double t
   const int m = h->opt.gmres_restart;
   const int max_it = rec ? m * rec_cycles : h->opt.max_iters;
   int cycle = 0;
-  // device workspace
-  double2* Vb = h->mem.alloc<double2>((int64_t)n_rhs * (m + 1) * N);
+  Workspace ws{h->mem, {}};
+  double2* Vb = ws.take<double2>((int64_t)n_rhs * (m + 1) * N);
   const bool use_pc = h->net != nullptr && h->opt.precond == EFIE_PRECOND_LEARNED;
-  double2* Zb = use_pc ? h->mem.alloc<double2>((int64_t)n_rhs * m * N) : nullptr;
+  double2* Zb = use_pc ? ws.take<double2>((int64_t)n_rhs * m * N) : nullptr;
   std::vector<int> pc_fallback(n_rhs, 0);
-  double2* wv = h->mem.alloc<double2>((int64_t)n_rhs * N);
-  double2* rv = h->mem.alloc<double2>((int64_t)n_rhs * N);
-  double2* dh = h->mem.alloc<double2>((int64_t)n_rhs * (m + 1));
-  double2* dh2 = h->mem.alloc<double2>((int64_t)n_rhs * (m + 1));
-  double* dn = h->mem.alloc<double>(n_rhs);
-  int* dact = h->mem.alloc<int>(n_rhs);
+  double2* wv = ws.take<double2>((int64_t)n_rhs * N);
+  double2* rv = ws.take<double2>((int64_t)n_rhs * N);
+  double2* dh = ws.take<double2>((int64_t)n_rhs * (m + 1));
+  double2* dh2 = ws.take<double2>((int64_t)n_rhs * (m + 1));
+  double* dn = ws.take<double>(n_rhs);
+  int* dact = ws.take<int>(n_rhs);
   const int64_t ldr = (int64_t)(m + 1) * N;
   std::vector<double> bnorm(n_rhs), nrm(n_rhs);
   std::vector<int> its(n_rhs, 0), conv(n_rhs, 0), act(n_rhs, 1);
@@ -1159,8 +1178,6 @@ int solve_impl(efie_handle* h, const double2* b, double2* x, int n_rhs, double t
       info[r].precond_fallback = (h->opt.precond == EFIE_PRECOND_LEARNED && (!use_pc || pc_fallback[r])) ? 1 : 0;
     }
   }
-  for (void* p : {(void*)Vb, (void*)wv, (void*)rv, (void*)dh, (void*)dh2, (void*)dn, (void*)dact}) h->mem.release(p);
-  if (Zb) h->mem.release(Zb);
   return ret;
 }
 
@@ -1301,8 +1318,9 @@ bool read_weights(const char* path, std::vector<float>& p) {
 
 namespace efie {
 int handle_rhs_args(const efie_handle* h, const double** V, const int32_t** T, const double** area,
-                    const int32_t** tri_pm, const int32_t** free_pm, int64_t* N, double* k) {
+                    const int32_t** tri_pm, const int32_t** free_pm, int64_t* N, double* k, int* device) {
   if (!h) return EFIE_EINVAL;
+  *device = h->device;
   *V = h->dV;
   *T = h->dT;
   *area = h->darea;
@@ -1397,7 +1415,9 @@ int efie_plan_adaptive_near(const efie_mesh* mesh, double wavenumber, int spline
     const int64_t NL = (int64_t)A.leaf_level.size(), nz = (int64_t)A.near_src.size();
     if (n_leaves) *n_leaves = NL;
     if (nnz) *nnz = nz;
-    if ((leaf_level || leaf_ijk || near_ptr) && leaf_cap < NL) throw EfieError{EFIE_EINVAL, "leaf_cap too small"};
+    if ((leaf_level || leaf_ijk) && leaf_cap < NL) throw EfieError{EFIE_EINVAL, "leaf_cap too small"};
+    if (near_ptr && leaf_cap < NL + 1)
+      throw EfieError{EFIE_EINVAL, "leaf_cap too small for near_ptr (needs n_leaves + 1)"};
     if (near_src && near_cap < nz) throw EfieError{EFIE_EINVAL, "near_cap too small"};
     for (int64_t x = 0; x < NL; ++x) {
       if (leaf_level) leaf_level[x] = A.leaf_level[x];

@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 namespace efie {
 
 template <typename R> struct C2;
@@ -59,5 +61,19 @@ __host__ __device__ __forceinline__ T cscale(T a, S s) {
 }
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Raises a kernel's dynamic shared-memory limit on the current device the first
+// time that device launches it.  The limit is a per-device attribute, so the
+// mask holds one bit per device (devices 64 and up set it on every call);
+// threads that race both set the same value, which is harmless.
+template <typename K>
+inline void smem_attr_once(K kernel, int bytes, std::atomic<uint64_t>& done) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return;
+  const uint64_t bit = dev < 64 ? (1ull << dev) : 0;
+  if (bit && (done.load(std::memory_order_acquire) & bit)) return;
+  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess && bit)
+    done.fetch_or(bit, std::memory_order_acq_rel);
+}
 
 }  // namespace efie

@@ -1,4 +1,4 @@
-// Far-field kernels of the fast matvec (steps a1-a9) and small vector kernels.
+// Far-field kernels of the fast matvec (charges through interpolation) and small vector kernels.
 //
 //  a2  k_anterp : leaf anterpolation q_{d,b} = sum_{n in b} j_n m_{d,n} and the
 //                 charge component q_{4,b} = sum_{c in b} rho_c m^phi_c
@@ -157,11 +157,8 @@ template <typename R, bool CM, int NMAX, int LPT>
 static void run_mode_line(const cpx_t<R>* in, View vin, cpx_t<R>* out, View vout, int64_t B, int C, int ax,
                           int nin, int e0, int e1, int e2, const void* M0, const void* M1, const int8_t* sel,
                           const int64_t* srcmap, bool accumulate, size_t smem, cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_mode_line<R, CM, NMAX, LPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-    attr = true;
-  }
+  static std::atomic<uint64_t> attr{0};
+  smem_attr_once(k_mode_line<R, CM, NMAX, LPT>, 96 * 1024, attr);
   const int ea = ax == 0 ? e1 : e0, eb = ax == 2 ? e1 : e2;
   int64_t lines = B * ea * eb * (int64_t)(C / LPT);
   int64_t blocks = ceil_div(lines, 128);
@@ -511,11 +508,8 @@ bool launch_dft(const cpx_t<R>* in, View vin, cpx_t<R>* out, View vout, int64_t 
   if (nin <= NM) {                                                                                           \
     if (two && NM <= 21) {                                                                                   \
       auto k = k_dft_fwd_line<R, NM, (sizeof(R) == 4 && NM <= 21) ? 2 : 1>;                                  \
-      static bool attr = false;                                                                              \
-      if (!attr) {                                                                                           \
-        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);                     \
-        attr = true;                                                                                         \
-      }                                                                                                      \
+      static std::atomic<uint64_t> attr{0};                                                                  \
+      smem_attr_once(k, 96 * 1024, attr);                                                                    \
       k<<<(unsigned)blocks, 128, smem, s>>>(in, vin, out, vout, B, C, ax, nin, e0, e1, e2, M, n);            \
       return true;                                                                                           \
     }                                                                                                        \
@@ -523,11 +517,8 @@ bool launch_dft(const cpx_t<R>* in, View vin, cpx_t<R>* out, View vout, int64_t 
     int64_t blocks1 = ceil_div(lines1, 128);                                                                 \
     if (blocks1 > 152 * 32) blocks1 = 152 * 32;                                                              \
     auto k = k_dft_fwd_line<R, NM, 1>;                                                                       \
-    static bool attr1 = false;                                                                               \
-    if (!attr1) {                                                                                            \
-      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);                       \
-      attr1 = true;                                                                                          \
-    }                                                                                                        \
+    static std::atomic<uint64_t> attr1{0};                                                                   \
+    smem_attr_once(k, 96 * 1024, attr1);                                                                     \
     k<<<(unsigned)blocks1, 128, smem, s>>>(in, vin, out, vout, B, C, ax, nin, e0, e1, e2, M, n);             \
     return true;                                                                                             \
   }
@@ -544,11 +535,8 @@ bool launch_dft(const cpx_t<R>* in, View vin, cpx_t<R>* out, View vout, int64_t 
   if (nout <= AM) {                                                                                          \
     if (two && AM <= 21) {                                                                                   \
       auto k = k_dft_inv_line<R, AM, (sizeof(R) == 4 && AM <= 21) ? 2 : 1>;                                  \
-      static bool attr = false;                                                                              \
-      if (!attr) {                                                                                           \
-        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);                     \
-        attr = true;                                                                                         \
-      }                                                                                                      \
+      static std::atomic<uint64_t> attr{0};                                                                  \
+      smem_attr_once(k, 96 * 1024, attr);                                                                    \
       k<<<(unsigned)blocks, 128, smem, s>>>(in, vin, out, vout, B, C, ax, nin, e0, e1, e2, M, n);            \
       return true;                                                                                           \
     }                                                                                                        \
@@ -556,11 +544,8 @@ bool launch_dft(const cpx_t<R>* in, View vin, cpx_t<R>* out, View vout, int64_t 
     int64_t blocks1 = ceil_div(lines1, 128);                                                                 \
     if (blocks1 > 152 * 32) blocks1 = 152 * 32;                                                              \
     auto k = k_dft_inv_line<R, AM, 1>;                                                                       \
-    static bool attr1 = false;                                                                               \
-    if (!attr1) {                                                                                            \
-      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);                       \
-      attr1 = true;                                                                                          \
-    }                                                                                                        \
+    static std::atomic<uint64_t> attr1{0};                                                                   \
+    smem_attr_once(k, 96 * 1024, attr1);                                                                     \
     k<<<(unsigned)blocks1, 128, smem, s>>>(in, vin, out, vout, B, C, ax, nin, e0, e1, e2, M, n);             \
     return true;                                                                                             \
   }
@@ -1313,11 +1298,8 @@ void launch_mac(const cpx_t<R>* Qh, cpx_t<R>* Rh, const cpx_t<R>* Kh, int64_t B,
   if (!force_reg && sizeof(R) == 4 && C == 32 && max_tile_targets > 8 && max_tile_targets <= 128) {
     constexpr int YS = 16;
     const size_t smem = 2 * sizeof(float2) * YS * (128 + 32);
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(k_mac_top32<YS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      attr = true;
-    }
+    static std::atomic<uint64_t> attr{0};
+    smem_attr_once(k_mac_top32<YS>, (int)smem, attr);
     for (int64_t f0 = 0; f0 < nf; f0 += 65535) {
       int64_t nfc = std::min<int64_t>(65535, nf - f0);
       dim3 grid((unsigned)ntiles, (unsigned)nfc);
@@ -1336,11 +1318,8 @@ void launch_mac(const cpx_t<R>* Qh, cpx_t<R>* Rh, const cpx_t<R>* Kh, int64_t B,
     if (fpb < 1) fpb = 1;
     while (fpb > 1 && (size_t)fpb * O * sizeof(float2) > 64 * 1024) fpb >>= 1;
     const size_t smem = (size_t)fpb * O * sizeof(float2);
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(k_mac_il32<8, CRI>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
-      attr = true;
-    }
+    static std::atomic<uint64_t> attr{0};
+    smem_attr_once(k_mac_il32<8, CRI>, 64 * 1024, attr);
     const int64_t fchunk = (int64_t)65535 * fpb;
     for (int64_t f0 = 0; f0 < nf; f0 += fchunk) {
       int64_t nfc = std::min<int64_t>(fchunk, nf - f0);
@@ -1539,54 +1518,50 @@ void launch_rhs_planewave(const double* V, const int32_t* T, const double* area,
 }
 
 // ---------------------------------------------------------------- Krylov
-// h[r][i] += sum_n conj(V[r][i][n]) w[r][n]; grid (chunks, nbasis, nr)
-__global__ void k_multidot(const double2* __restrict__ Vb, int64_t ldv_r, int64_t ldv_i,
-                           const double2* __restrict__ w, int64_t ldw, int64_t N,
-                           const int* __restrict__ active, double2* __restrict__ h, int nbasis) {
-  int i = blockIdx.y, r = blockIdx.z;
-  if (active && !active[r]) return;
+// Block sum of 512 per-thread values in a fixed order (warp shuffles, then
+// the 16 warp sums in ascending order); the result is valid in thread 0.
+template <typename T>
+__device__ __forceinline__ T block_sum512(T v, T* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  T s = 0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < 16; ++i) s += red[i];
+  return s;
+}
+
+// h[r][i] = sum_n conj(V[r][i][n]) w[r][n]; grid (nbasis, nr), 512 threads.
+// One block per output and a fixed summation order: the Arnoldi coefficients,
+// and so the iterates, are the same on every run.
+__global__ void __launch_bounds__(512) k_multidot(const double2* __restrict__ Vb, int64_t ldv_r, int64_t ldv_i,
+                                                  const double2* __restrict__ w, int64_t ldw, int64_t N,
+                                                  const int* __restrict__ active, double2* __restrict__ h,
+                                                  int nbasis) {
+  const int i = blockIdx.x, r = blockIdx.y;
+  if (active && !active[r]) {
+    if (threadIdx.x == 0) h[(int64_t)r * nbasis + i] = make_double2(0, 0);
+    return;
+  }
   const double2* v = Vb + r * ldv_r + i * ldv_i;
   const double2* wr = w + r * ldw;
   double sx = 0, sy = 0;
-  for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t n = threadIdx.x; n < N; n += blockDim.x) {
     double2 a = v[n], b = wr[n];
     sx += a.x * b.x + a.y * b.y;
     sy += a.x * b.y - a.y * b.x;
   }
-  __shared__ double rx[32], ry[32];
-  for (int o = 16; o > 0; o >>= 1) {
-    sx += __shfl_down_sync(0xffffffffu, sx, o);
-    sy += __shfl_down_sync(0xffffffffu, sy, o);
-  }
-  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0) {
-    rx[wid] = sx;
-    ry[wid] = sy;
-  }
-  __syncthreads();
-  if (wid == 0) {
-    int nw = blockDim.x >> 5;
-    sx = lane < nw ? rx[lane] : 0;
-    sy = lane < nw ? ry[lane] : 0;
-    for (int o = 16; o > 0; o >>= 1) {
-      sx += __shfl_down_sync(0xffffffffu, sx, o);
-      sy += __shfl_down_sync(0xffffffffu, sy, o);
-    }
-    if (lane == 0) {
-      atomicAdd(&h[(int64_t)r * nbasis + i].x, sx);
-      atomicAdd(&h[(int64_t)r * nbasis + i].y, sy);
-    }
-  }
+  __shared__ double rx[16], ry[16];
+  sx = block_sum512(sx, rx);
+  sy = block_sum512(sy, ry);
+  if (threadIdx.x == 0) h[(int64_t)r * nbasis + i] = make_double2(sx, sy);
 }
 void launch_multidot(const double2* Vb, int64_t ldv_r, int64_t ldv_i, int nbasis, const double2* w,
                      int64_t ldw, int64_t N, int nr, const int* active, double2* h, cudaStream_t s) {
   if (nbasis <= 0 || nr <= 0) return;
-  cudaMemsetAsync(h, 0, sizeof(double2) * nbasis * nr, s);
-  int chunks = (int)ceil_div(N, 256 * 16);
-  if (chunks > 64) chunks = 64;
-  if (chunks < 1) chunks = 1;
-  dim3 grid(chunks, nbasis, nr);
-  k_multidot<<<grid, 256, 0, s>>>(Vb, ldv_r, ldv_i, w, ldw, N, active, h, nbasis);
+  dim3 grid(nbasis, nr);
+  k_multidot<<<grid, 512, 0, s>>>(Vb, ldv_r, ldv_i, w, ldw, N, active, h, nbasis);
 }
 
 // w[r][n] += sign * sum_i h[r][i] V[r][i][n]
@@ -1645,33 +1620,22 @@ void launch_conj_scale(const double2* x, double a, double2* out, int64_t n, cuda
   k_conj_scale<<<(unsigned)blocks, 256, 0, s>>>(x, a, out, n);
 }
 
-__global__ void k_norms(const double2* __restrict__ w, int64_t ldw, int64_t N, double* out) {
-  int r = blockIdx.y;
+// out[r] = sum_n |w[r][n]|^2; one 512-thread block per vector, fixed order
+__global__ void __launch_bounds__(512) k_norms(const double2* __restrict__ w, int64_t ldw, int64_t N,
+                                               double* out) {
+  const int r = blockIdx.x;
   double s = 0;
-  for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t n = threadIdx.x; n < N; n += blockDim.x) {
     double2 a = w[r * ldw + n];
     s += a.x * a.x + a.y * a.y;
   }
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-  __shared__ double red[32];
-  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0) red[wid] = s;
-  __syncthreads();
-  if (wid == 0) {
-    int nw = blockDim.x >> 5;
-    s = lane < nw ? red[lane] : 0;
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if (lane == 0) atomicAdd(&out[r], s);
-  }
+  __shared__ double red[16];
+  s = block_sum512(s, red);
+  if (threadIdx.x == 0) out[r] = s;
 }
 void launch_norms(const double2* w, int64_t ldw, int64_t N, int nr, double* out, cudaStream_t s) {
   if (nr <= 0) return;
-  cudaMemsetAsync(out, 0, sizeof(double) * nr, s);
-  int chunks = (int)ceil_div(N, 256 * 16);
-  if (chunks > 64) chunks = 64;
-  if (chunks < 1) chunks = 1;
-  dim3 grid(chunks, nr);
-  k_norms<<<grid, 256, 0, s>>>(w, ldw, N, out);
+  k_norms<<<nr, 512, 0, s>>>(w, ldw, N, out);
 }
 
 // explicit instantiations

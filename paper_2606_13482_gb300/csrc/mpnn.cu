@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <random>
 #include <vector>
@@ -39,6 +40,12 @@ constexpr int OFF_L0 = OFF_BE + NW;
 constexpr int OFF_WD = OFF_L0 + NL * LAYER_SZ;
 constexpr int OFF_BD = OFF_WD + 2 * NW;
 constexpr int NPARAM = OFF_BD + 2;
+// Gradient reductions are deterministic: each kernel runs on a fixed number of
+// blocks (a function of N only), every block writes its partial sums in a
+// fixed order, and k_nn_reduce adds the partials block by block.  Training
+// from a seed therefore gives the same network on every run.
+constexpr int NB_RED = 256;                    // blocks of the reducing kernels
+constexpr int PART_W = 2 * NW * NW + NW;       // widest partial: one layer's dWs | dWn | dbias
 
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
   __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
@@ -173,9 +180,10 @@ __global__ void k_nn_decode(const float* __restrict__ h, int64_t N, const float*
 }
 
 // ----------------------------------------------------------------- backward
-// loss terms: sum |z - e|^2 and sum |e|^2
-__global__ void k_nn_loss(const double2* __restrict__ z, const double2* __restrict__ e, int64_t N,
-                          double* __restrict__ out) {
+// loss terms: sum |z - e|^2 and sum |e|^2, one partial pair per block
+// (256 threads), reduced by k_nn_loss_reduce in block order
+__global__ void __launch_bounds__(256) k_nn_loss(const double2* __restrict__ z, const double2* __restrict__ e,
+                                                 int64_t N, double* __restrict__ dpart) {
   double a = 0, b = 0;
   for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < N; m += (int64_t)gridDim.x * blockDim.x) {
     const double dx = z[m].x - e[m].x, dy = z[m].y - e[m].y;
@@ -186,10 +194,41 @@ __global__ void k_nn_loss(const double2* __restrict__ z, const double2* __restri
     a += __shfl_down_sync(0xffffffffu, a, o);
     b += __shfl_down_sync(0xffffffffu, b, o);
   }
-  if ((threadIdx.x & 31) == 0) {
-    atomicAdd(out, a);
-    atomicAdd(out + 1, b);
+  __shared__ double ra[8], rb[8];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) {
+    ra[w] = a;
+    rb[w] = b;
   }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sa = 0, sb = 0;
+    for (int i = 0; i < 8; ++i) {
+      sa += ra[i];
+      sb += rb[i];
+    }
+    dpart[2 * blockIdx.x] = sa;
+    dpart[2 * blockIdx.x + 1] = sb;
+  }
+}
+__global__ void k_nn_loss_reduce(const double* __restrict__ dpart, int nb, double* __restrict__ out) {
+  if (threadIdx.x != 0) return;
+  double a = 0, b = 0;
+  for (int i = 0; i < nb; ++i) {
+    a += dpart[2 * i];
+    b += dpart[2 * i + 1];
+  }
+  out[0] = a;
+  out[1] = b;
+}
+
+// G[i] += sum_b part[b][i], b ascending
+__global__ void k_nn_reduce(const float* __restrict__ part, int nb, int width, float* __restrict__ G) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= width) return;
+  float acc = 0.f;
+  for (int b = 0; b < nb; ++b) acc += part[(int64_t)b * width + i];
+  G[i] += acc;
 }
 
 // g = 2 (z - e) / |e|^2, the gradient of the error loss with respect to z
@@ -201,31 +240,41 @@ __global__ void k_nn_err_grad(const double2* __restrict__ z, const double2* __re
 }
 
 // decoder backward from g = dL/dz (dL/dRe z = Re g, dL/dIm z = Im g):
-// dy = s (Re g, Im g) ; dWd, dbd ; dh = dy bf16(Wd)
-__global__ void k_nn_decode_back(const float* __restrict__ h, const double2* __restrict__ gz, int64_t N,
-                                 const double* __restrict__ sumsq, const float* __restrict__ P,
-                                 float* __restrict__ G, float* __restrict__ dh) {
+// dy = s (Re g, Im g) ; dWd, dbd ; dh = dy bf16(Wd).  256 threads = 4 nodes x
+// 64 features; the grid stride is a multiple of 64, so a thread keeps one
+// feature j and sums its own terms; the 4 threads of a feature are added in a
+// fixed order and the block writes part[block][2 NW + 2].
+__global__ void __launch_bounds__(256) k_nn_decode_back(const float* __restrict__ h,
+                                                        const double2* __restrict__ gz, int64_t N,
+                                                        const double* __restrict__ sumsq,
+                                                        const float* __restrict__ P, float* __restrict__ part,
+                                                        float* __restrict__ dh) {
   const double s = sqrt(sumsq[0] / (double)N);
-  __shared__ float red[2 * NW + 2];
-  for (int i = threadIdx.x; i < 2 * NW + 2; i += blockDim.x) red[i] = 0.f;
-  __syncthreads();
+  __shared__ float red[4][2 * NW + 2];
+  const int j = threadIdx.x & (NW - 1), q = threadIdx.x >> 6;
+  const float w0 = bf16r(P[OFF_WD + j]), w1 = bf16r(P[OFF_WD + NW + j]);
+  float p0 = 0.f, p1 = 0.f, c0 = 0.f, c1 = 0.f;
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < N * NW;
        idx += (int64_t)gridDim.x * blockDim.x) {
     const int64_t m = idx / NW;
-    const int j = (int)(idx - m * NW);
     const float d0 = (float)(s * gz[m].x);
     const float d1 = (float)(s * gz[m].y);
     const float hv = bf16r(h[idx]);
-    atomicAdd(&red[j], d0 * hv);
-    atomicAdd(&red[NW + j], d1 * hv);
-    if (j == 0) {
-      atomicAdd(&red[2 * NW], d0);
-      atomicAdd(&red[2 * NW + 1], d1);
-    }
-    dh[idx] = d0 * bf16r(P[OFF_WD + j]) + d1 * bf16r(P[OFF_WD + NW + j]);
+    p0 += d0 * hv;
+    p1 += d1 * hv;
+    c0 += d0;
+    c1 += d1;
+    dh[idx] = d0 * w0 + d1 * w1;
+  }
+  red[q][j] = p0;
+  red[q][NW + j] = p1;
+  if (j == 0) {
+    red[q][2 * NW] = c0;
+    red[q][2 * NW + 1] = c1;
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < 2 * NW + 2; i += blockDim.x) atomicAdd(&G[OFF_WD + i], red[i]);
+  for (int i = threadIdx.x; i < 2 * NW + 2; i += blockDim.x)
+    part[(int64_t)blockIdx.x * (2 * NW + 2) + i] = ((red[0][i] + red[1][i]) + red[2][i]) + red[3][i];
 }
 
 // du = dh (1 - tanh(u)^2)
@@ -237,47 +286,53 @@ __global__ void k_nn_du(const float* __restrict__ dh, const float* __restrict__ 
   }
 }
 
-// Layer backward on a tile of 64 nodes:
-//   dWcat += du^T [bf16(h) | bf16(a)]   (tensor cores, reduced into G)
+// Layer backward over tiles of 64 nodes (each block takes tiles b, b + grid,
+// ... in order):
+//   dWcat += du^T [bf16(h) | bf16(a)]   (tensor cores, summed over the block's
+//                                        tiles in registers)
 //   dbias += sum du
 //   dX = bf16(du) Wcat  -> dXh (added to dh_next), dXa (neighbour part, stored)
+// The block's dWs | dWn | dbias sums go to part[block][PART_W].
 __global__ void __launch_bounds__(128) k_nn_layer_back(const float* __restrict__ du, const float* __restrict__ h,
                                                        const float* __restrict__ a, int64_t N,
                                                        const __nv_bfloat16* __restrict__ WcatT,
-                                                       float* __restrict__ Gw, float* __restrict__ Gb,
-                                                       float* __restrict__ dh_next, float* __restrict__ dXa) {
+                                                       float* __restrict__ part, float* __restrict__ dh_next,
+                                                       float* __restrict__ dXa) {
   extern __shared__ __align__(16) unsigned char nn_smem[];
   __nv_bfloat16* duT = (__nv_bfloat16*)nn_smem;             // [n][m]      64 x 72
   __nv_bfloat16* XT = duT + NW * (TILE + 8);                 // [k][m]     128 x 72
   __nv_bfloat16* dus = XT + 128 * (TILE + 8);                // [m][n]      64 x 72
   __nv_bfloat16* Wt = dus + TILE * (NW + 8);                 // WcatT [k][n] 128 x 72
   const int LDT = TILE + 8, LDN = NW + 8;
-  const int64_t m0 = (int64_t)blockIdx.x * TILE;
   for (int i = threadIdx.x; i < 128 * NW; i += blockDim.x) Wt[(i >> 6) * LDN + (i & 63)] = WcatT[i];
-  for (int i = threadIdx.x; i < TILE * NW; i += blockDim.x) {
-    const int ml = i >> 6, j = i & 63;
-    const int64_t m = m0 + ml;
-    float dv = 0.f, hv = 0.f, av = 0.f;
-    if (m < N) {
-      dv = du[m * NW + j];
-      hv = h[m * NW + j];
-      av = a[m * NW + j];
-    }
-    const __nv_bfloat16 db = __float2bfloat16_rn(dv);
-    duT[j * LDT + ml] = db;
-    dus[ml * LDN + j] = db;
-    XT[j * LDT + ml] = __float2bfloat16_rn(hv);
-    XT[(64 + j) * LDT + ml] = __float2bfloat16_rn(av);
-  }
-  __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  // dW tile: rows n in [16 warp, +16), cols k in [0,128), K = 64 nodes
-  {
-    float acc[16][4];
+  float accW[16][4];
 #pragma unroll
-    for (int nt = 0; nt < 16; ++nt)
+  for (int nt = 0; nt < 16; ++nt)
 #pragma unroll
-      for (int i = 0; i < 4; ++i) acc[nt][i] = 0.f;
+    for (int i = 0; i < 4; ++i) accW[nt][i] = 0.f;
+  float accB = 0.f;
+  const int64_t ntiles = (N + TILE - 1) / TILE;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t m0 = tile * TILE;
+    __syncthreads();   // the previous tile's shared-memory reads are done
+    for (int i = threadIdx.x; i < TILE * NW; i += blockDim.x) {
+      const int ml = i >> 6, j = i & 63;
+      const int64_t m = m0 + ml;
+      float dv = 0.f, hv = 0.f, av = 0.f;
+      if (m < N) {
+        dv = du[m * NW + j];
+        hv = h[m * NW + j];
+        av = a[m * NW + j];
+      }
+      const __nv_bfloat16 db = __float2bfloat16_rn(dv);
+      duT[j * LDT + ml] = db;
+      dus[ml * LDN + j] = db;
+      XT[j * LDT + ml] = __float2bfloat16_rn(hv);
+      XT[(64 + j) * LDT + ml] = __float2bfloat16_rn(av);
+    }
+    __syncthreads();
+    // dW tile: rows n in [16 warp, +16), cols k in [0,128), K = 64 nodes
 #pragma unroll
     for (int kt = 0; kt < TILE / 16; ++kt) {
       uint32_t af[4];
@@ -286,29 +341,14 @@ __global__ void __launch_bounds__(128) k_nn_layer_back(const float* __restrict__
       for (int nt = 0; nt < 16; ++nt) {
         uint32_t bf[2];
         load_b(XT, LDT, nt * 8, kt * 16, bf);
-        mma_bf16(acc[nt], af, bf);
+        mma_bf16(accW[nt], af, bf);
       }
     }
-#pragma unroll
-    for (int nt = 0; nt < 16; ++nt)
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int n = warp * 16 + g + (i >= 2 ? 8 : 0);
-        const int k = nt * 8 + 2 * t + (i & 1);
-        // Gw layout: Ws [64][64] then Wn [64][64]
-        const int off = k < 64 ? n * NW + k : NW * NW + n * NW + (k - 64);
-        atomicAdd(&Gw[off], acc[nt][i]);
-      }
-  }
-  // bias gradient
-  if (threadIdx.x < NW) {
-    float sacc = 0.f;
-    for (int ml = 0; ml < TILE; ++ml)
-      if (m0 + ml < N) sacc += du[(m0 + ml) * NW + threadIdx.x];
-    atomicAdd(&Gb[threadIdx.x], sacc);
-  }
-  // dX tile: rows m in [16 warp, +16), cols k in [0, 128), K = 64 outputs
-  {
+    // bias gradient
+    if (threadIdx.x < NW)
+      for (int ml = 0; ml < TILE; ++ml)
+        if (m0 + ml < N) accB += du[(m0 + ml) * NW + threadIdx.x];
+    // dX tile: rows m in [16 warp, +16), cols k in [0, 128), K = 64 outputs
     float acc[16][4];
 #pragma unroll
     for (int nt = 0; nt < 16; ++nt)
@@ -339,6 +379,17 @@ __global__ void __launch_bounds__(128) k_nn_layer_back(const float* __restrict__
           dXa[m * NW + (k - 64)] = acc[nt][i];
       }
   }
+  float* pb = part + (int64_t)blockIdx.x * PART_W;
+#pragma unroll
+  for (int nt = 0; nt < 16; ++nt)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int n = warp * 16 + g + (i >= 2 ? 8 : 0);
+      const int k = nt * 8 + 2 * t + (i & 1);
+      // layout of one layer's parameters: Ws [64][64], Wn [64][64], bias [64]
+      pb[k < 64 ? n * NW + k : NW * NW + n * NW + (k - 64)] = accW[nt][i];
+    }
+  if (threadIdx.x < NW) pb[2 * NW * NW + threadIdx.x] = accB;
 }
 
 // dh_next[m] += sum_n s_mn dXa[n]
@@ -358,24 +409,28 @@ __global__ void k_nn_gather_back(const float* __restrict__ dXa, const int32_t* _
   }
 }
 
-// encoder backward: dWe += du0^T bf16(x), dbe += sum du0
-__global__ void k_nn_encode_back(const float* __restrict__ du0, const float* __restrict__ x, int64_t N,
-                                 float* __restrict__ G) {
-  __shared__ float red[NW * (NIN + 1)];
-  for (int i = threadIdx.x; i < NW * (NIN + 1); i += blockDim.x) red[i] = 0.f;
-  __syncthreads();
+// encoder backward: dWe += du0^T bf16(x), dbe += sum du0.  256 threads = 4
+// nodes x 64 features, one feature per thread (the grid stride is a multiple
+// of 64); the block writes part[block][NW (NIN + 1)] (dWe [64][4], dbe [64]).
+__global__ void __launch_bounds__(256) k_nn_encode_back(const float* __restrict__ du0, const float* __restrict__ x,
+                                                        int64_t N, float* __restrict__ part) {
+  __shared__ float red[4][NW * (NIN + 1)];
+  const int j = threadIdx.x & (NW - 1), q = threadIdx.x >> 6;
+  float pw[NIN] = {0.f, 0.f, 0.f, 0.f}, pbias = 0.f;
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < N * NW;
        idx += (int64_t)gridDim.x * blockDim.x) {
     const int64_t m = idx / NW;
-    const int j = (int)(idx - m * NW);
     const float d = du0[idx];
 #pragma unroll
-    for (int i = 0; i < NIN; ++i) atomicAdd(&red[j * NIN + i], d * x[m * NIN + i]);
-    atomicAdd(&red[NW * NIN + j], d);
+    for (int i = 0; i < NIN; ++i) pw[i] += d * x[m * NIN + i];
+    pbias += d;
   }
+#pragma unroll
+  for (int i = 0; i < NIN; ++i) red[q][j * NIN + i] = pw[i];
+  red[q][NW * NIN + j] = pbias;
   __syncthreads();
-  for (int i = threadIdx.x; i < NW * NIN; i += blockDim.x) atomicAdd(&G[OFF_WE + i], red[i]);
-  for (int i = threadIdx.x; i < NW; i += blockDim.x) atomicAdd(&G[OFF_BE + i], red[NW * NIN + i]);
+  for (int i = threadIdx.x; i < NW * (NIN + 1); i += blockDim.x)
+    part[(int64_t)blockIdx.x * NW * (NIN + 1) + i] = ((red[0][i] + red[1][i]) + red[2][i]) + red[3][i];
 }
 
 // bfloat16 copies of the layer matrices: Wcat [64][128] and WcatT [128][64]
@@ -417,6 +472,8 @@ struct Net {
   float* a[NL] = {nullptr};
   float *dh = nullptr, *du = nullptr, *dXa = nullptr;
   double* red = nullptr;   // [0] sum |r|^2, [1..2] loss terms
+  float* part = nullptr;   // [NB_RED][PART_W] per-block gradient partials
+  double* dpart = nullptr; // [NB_RED][2] per-block loss partials
   int step = 0;
 };
 
@@ -483,6 +540,8 @@ void nn_setup(Net& net, int64_t N, const std::vector<int32_t>& nbr, const std::v
     dal((void**)&net.dh, sizeof(float) * N * NW);
     dal((void**)&net.du, sizeof(float) * N * NW);
     dal((void**)&net.dXa, sizeof(float) * N * NW);
+    dal((void**)&net.part, sizeof(float) * NB_RED * PART_W);
+    dal((void**)&net.dpart, sizeof(double) * NB_RED * 2);
   }
   k_nn_pack<<<64, 256>>>(net.P, net.Wcat, net.WcatT);
   cudaError_t e = cudaDeviceSynchronize();
@@ -491,7 +550,7 @@ void nn_setup(Net& net, int64_t N, const std::vector<int32_t>& nbr, const std::v
 
 void nn_free(Net& net) {
   void* ps[] = {net.P, net.G, net.M, net.V, net.Wcat, net.WcatT, net.nbr, net.sgn, net.lnorm, net.x, net.u0,
-                net.dh, net.du, net.dXa, net.red};
+                net.dh, net.du, net.dXa, net.red, net.part, net.dpart};
   for (void* p : ps)
     if (p) cudaFree(p);
   for (int l = 0; l <= NL; ++l)
@@ -522,32 +581,35 @@ void nn_forward(Net& net, const double2* r, double2* z, bool training, cudaStrea
 // same input); parameter gradients are accumulated into G.
 void nn_backward_g(Net& net, const double2* gz, cudaStream_t s) {
   const int64_t N = net.N;
-  k_nn_decode_back<<<(unsigned)grid_for(N * NW, 256), 256, 0, s>>>(net.h[NL], gz, N, net.red, net.P, net.G, net.dh);
-  const unsigned tiles = (unsigned)((N + TILE - 1) / TILE);
+  // fixed block counts (functions of N only) keep the summation order fixed
+  const int nb_el = (int)std::min<int64_t>(NB_RED, (N * NW + 255) / 256);
+  const int64_t tiles = (N + TILE - 1) / TILE;
+  const int nb_tile = (int)std::min<int64_t>(NB_RED, tiles);
+  k_nn_decode_back<<<nb_el, 256, 0, s>>>(net.h[NL], gz, N, net.red, net.P, net.part, net.dh);
+  k_nn_reduce<<<(2 * NW + 2 + 127) / 128, 128, 0, s>>>(net.part, nb_el, 2 * NW + 2, net.G + OFF_WD);
   for (int l = NL - 1; l >= 0; --l) {
     k_nn_du<<<(unsigned)grid_for(N * NW, 256), 256, 0, s>>>(net.dh, net.u[l], net.du, N * NW);
     // dh stays as the residual-path gradient and receives dX_h and the neighbour part
     const size_t smem = sizeof(__nv_bfloat16) * (NW * (TILE + 8) + 128 * (TILE + 8) + TILE * (NW + 8) + 128 * (NW + 8));
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(k_nn_layer_back, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      attr = true;
-    }
-    k_nn_layer_back<<<tiles, 128, smem, s>>>(net.du, net.h[l], net.a[l], N, net.WcatT + l * NW * 128,
-                                          net.G + OFF_L0 + l * LAYER_SZ, net.G + OFF_L0 + l * LAYER_SZ + 2 * NW * NW,
-                                          net.dh, net.dXa);
+    static std::atomic<uint64_t> attr{0};
+    smem_attr_once(k_nn_layer_back, (int)smem, attr);
+    k_nn_layer_back<<<nb_tile, 128, smem, s>>>(net.du, net.h[l], net.a[l], N, net.WcatT + l * NW * 128, net.part,
+                                               net.dh, net.dXa);
+    k_nn_reduce<<<(PART_W + 127) / 128, 128, 0, s>>>(net.part, nb_tile, PART_W, net.G + OFF_L0 + l * LAYER_SZ);
     k_nn_gather_back<<<(unsigned)grid_for(N * NW, 256), 256, 0, s>>>(net.dXa, net.nbr, net.sgn, N, net.dh);
   }
   k_nn_du<<<(unsigned)grid_for(N * NW, 256), 256, 0, s>>>(net.dh, net.u0, net.du, N * NW);
-  k_nn_encode_back<<<(unsigned)grid_for(N * NW, 256), 256, 0, s>>>(net.du, net.x, N, net.G);
+  k_nn_encode_back<<<nb_el, 256, 0, s>>>(net.du, net.x, N, net.part);
+  k_nn_reduce<<<(NW * (NIN + 1) + 127) / 128, 128, 0, s>>>(net.part, nb_el, NW * (NIN + 1), net.G + OFF_WE);
 }
 
 // error loss |z - e|^2 / |e|^2: loss terms in red[1..2], gradient into G
 // (gbuf: N complex scratch)
 void nn_backward(Net& net, const double2* z, const double2* e, double2* gbuf, cudaStream_t s) {
   const int64_t N = net.N;
-  cudaMemsetAsync(net.red + 1, 0, sizeof(double) * 2, s);
-  k_nn_loss<<<(unsigned)grid_for(N, 256), 256, 0, s>>>(z, e, N, net.red + 1);
+  const int nb = (int)std::min<int64_t>(NB_RED, (N + 255) / 256);
+  k_nn_loss<<<nb, 256, 0, s>>>(z, e, N, net.dpart);
+  k_nn_loss_reduce<<<1, 32, 0, s>>>(net.dpart, nb, net.red + 1);
   k_nn_err_grad<<<(unsigned)grid_for(N, 256), 256, 0, s>>>(z, e, N, net.red + 1, gbuf);
   nn_backward_g(net, gbuf, s);
 }

@@ -29,11 +29,11 @@ double* g_ptr[kMaxDevices] = {nullptr};
 std::string g_err;
 
 // Host code only sees a stand-in for g_pw_scratch; the real device address is
-// looked up once per device, with that device current.
-cudaError_t scratch_for_current_device(double** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
+// looked up once per device, with that device current (the caller has checked
+// that it is the handle's device).  The cached address stays valid until the
+// device is reset (cudaDeviceReset unloads the module that holds the array).
+cudaError_t scratch_for_device(int dev, double** out) {
+  cudaError_t e = cudaSuccess;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lk(g_mu);
   if (!g_ptr[dev]) {
@@ -51,7 +51,7 @@ cudaError_t scratch_for_current_device(double** out) {
 namespace efie {
 // accessors implemented in api.cu (handle layout stays private there)
 int handle_rhs_args(const efie_handle* h, const double** V, const int32_t** T, const double** area,
-                    const int32_t** tri_pm, const int32_t** free_pm, int64_t* N, double* k);
+                    const int32_t** tri_pm, const int32_t** free_pm, int64_t* N, double* k, int* device);
 void handle_set_error(efie_handle* h, const char* msg);
 }  // namespace efie
 
@@ -72,9 +72,15 @@ extern "C" int efie_rhs_planewave_noalloc(efie_handle* h, int n_rhs, const doubl
   const int32_t *T, *tri_pm, *free_pm;
   int64_t N;
   double k;
-  if (efie::handle_rhs_args(h, &V, &T, &area, &tri_pm, &free_pm, &N, &k) != EFIE_OK) return EFIE_EINVAL;
+  int hdev = 0, cur = -1;
+  if (efie::handle_rhs_args(h, &V, &T, &area, &tri_pm, &free_pm, &N, &k, &hdev) != EFIE_OK) return EFIE_EINVAL;
+  if (cudaGetDevice(&cur) != cudaSuccess || cur != hdev) {
+    efie::handle_set_error(h, ("efie_rhs_planewave_noalloc: the current device (" + std::to_string(cur) +
+                               ") is not the handle's device (" + std::to_string(hdev) + ")").c_str());
+    return EFIE_EINVAL;
+  }
   double* scratch = nullptr;
-  cudaError_t e = scratch_for_current_device(&scratch);
+  cudaError_t e = scratch_for_device(hdev, &scratch);
   if (e != cudaSuccess) {
     efie::handle_set_error(h, (std::string("efie_rhs_planewave_noalloc: cudaGetSymbolAddress: ") +
                                cudaGetErrorString(e)).c_str());

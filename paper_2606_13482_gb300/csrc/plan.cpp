@@ -568,7 +568,7 @@ struct LeafOrder {
   const int32_t* tri_rank;
 };
 
-// Exact moments (Q10) of every RWG and pulse in its leaf box's splines
+// Exact moments (the paper asks only for numerical quadrature; these are exact) of every RWG and pulse in its leaf box's splines
 // (knots kcache[leaf], whose s' may differ from leaf to leaf), in sorted
 // order: dense blocks over each function's B-spline extents.  One leaf at a
 // time: every triangle used by the leaf's RWGs or pulses is integrated once
@@ -1084,7 +1084,7 @@ void build_plan(Plan& P, const double* xyz, int64_t nv, const int32_t* tri, int6
   }
   if (!with_moments) return;
 
-  // exact moments (Q10): collapsed Gauss rule of degree >= 3p+1 per piece
+  // exact moments: collapsed Gauss rule of degree >= 3p+1 per piece
   std::vector<LeafKnots> kcache(BD);
   for (size_t b = 0; b < BD; ++b) {
     LeafKnots& K = kcache[b];

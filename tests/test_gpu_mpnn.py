@@ -97,10 +97,10 @@ def test_training_reduces_loss(setup, tmp_path):
 def test_precond_gain_held_out(tmp_path):
     """Train on two ellipsoids with pairs from their own GMRES runs, then solve a
     held-out ellipsoid with FGMRES + network and with plain GMRES: both reach
-    the 1e-6 true residual, and the learned form stays within 1.5x of plain
-    GMRES's iterations.  The network's gradients are summed with atomics on
-    the GPU, so training, and with it the iteration count, varies from run to
-    run (measured: 454-515 against 526-534, and once 677 against 530)."""
+    the 1e-6 true residual (checked with the plain FP64 fast matvec), and the
+    learned form needs strictly fewer iterations than plain GMRES for every
+    right-hand side.  Training is deterministic (fixed-order gradient sums,
+    seeded shuffles), so this is one fixed outcome, not a lucky draw."""
     torch = _torch()
     import __graft_entry__ as g
     g.build()
@@ -133,8 +133,36 @@ def test_precond_gain_held_out(tmp_path):
     h.precond_load(path)
     _, learned, _ = h.solve(b, tol=1e-6)
     h.close()
-    for a, c in zip(plain, learned):
-        assert a["converged"] and c["converged"]
-        assert c["iterations"] <= 1.5 * a["iterations"] + 30
     print("held-out iterations plain", [a["iterations"] for a in plain],
           "learned", [c["iterations"] for c in learned])
+    for a, c in zip(plain, learned):
+        assert a["converged"] and c["converged"] and c["precond_fallback"] == 0
+        assert c["true_rel_residual"] <= 1e-6
+        assert c["iterations"] < a["iterations"]
+
+
+def test_training_is_deterministic():
+    """Two trainings from the same seed on the same harvested pairs give
+    bit-identical parameters, and so do two harvests of the same solves."""
+    torch = _torch()
+    import __graft_entry__ as g
+    g.build()
+    import paper_2606_13482_gb300 as G
+    V, T = E.ellipsoid(7, [0.4, 0.3, 0.35])
+    h = G.EFIE(V, T, 2 * np.pi, 3, 0.1, 1, precision=G.EFIE_MIXED, gmres_restart=30)
+    try:
+        b = h.rhs_planewave([[0, 0, -1.0], [1.0, 0, 0]], [[1.0, 0, 0], [0, 1.0, 0]])
+        R1, E1 = h.precond_harvest(b, restart=6, n_cycles=3)
+        R2, E2 = h.precond_harvest(b, restart=6, n_cycles=3)
+        assert torch.equal(R1, R2) and torch.equal(E1, E2)
+        p0 = (0.05 * np.random.default_rng(3).standard_normal(h.N_PARAMS)).astype(np.float32)
+        params = []
+        for objective in ("error", "residual"):
+            for _ in range(2):
+                h.precond_params(p0)                 # the same starting point each time
+                h.precond_train(R1, E1, epochs=3, lr=2e-3, seed=5, objective=objective)
+                params.append(h.precond_params())
+        assert np.array_equal(params[0], params[1]) and np.array_equal(params[2], params[3])
+        assert not np.array_equal(params[0], params[2])
+    finally:
+        h.close()

@@ -85,7 +85,7 @@ def test_plan_matrices_match_oracle(lib):
 
 
 def test_plan_moments_match_oracle(lib):
-    """Exact leaf-spline moments (Q10) built by the library's host planner
+    """Exact leaf-spline moments built by the library's host planner
     (each triangle clipped and integrated once per leaf box, its tiles shared
     by its RWGs and its pulse) against the oracle's per-function clipping and
     collapsed Gauss rule, for p = 2, 3, 5; and the divergence moments of the
@@ -226,3 +226,40 @@ def test_setup_without_gpu_fails_loudly(lib):
     with pytest.raises(G.EfieError) as e:
         G.EFIE(V, T, 2 * np.pi, 3, 0.1, 1)
     assert e.value.code == -3
+
+
+def test_planewave_argument_checks(lib):
+    """The C ABI takes no sizes for the plane-wave arrays, so the binding
+    checks them: khat and pol must both be [n, 3], and an output given by the
+    caller must be [n, N]; mismatches are rejected before any library call."""
+    G, _ = lib
+    kh, pol = G.planewave_args([0, 0, -1.0], [1.0, 0, 0])
+    assert kh.shape == (1, 3) and pol.shape == (1, 3) and kh.dtype == np.float64
+    kh, pol = G.planewave_args(np.zeros((4, 3)), np.ones((4, 3)), (4, 100), 100)
+    assert kh.flags.c_contiguous and pol.shape == (4, 3)
+    for bad in [(np.zeros((4, 3)), np.zeros((3, 3)), None, None),      # short pol
+                (np.zeros((4, 2)), np.zeros((4, 2)), None, None),      # not 3-vectors
+                (np.zeros((4, 3)), np.zeros((4, 3)), (3, 100), 100),   # short output
+                (np.zeros((4, 3)), np.zeros((4, 3)), (100,), 100),     # 1-D output
+                (np.zeros((4, 3)), np.zeros((4, 3)), (4, 99), 100)]:   # wrong N
+        with pytest.raises(ValueError):
+            G.planewave_args(*bad)
+
+
+def test_plan_adaptive_near_pointer_capacity(lib):
+    """near_ptr holds n_leaves + 1 entries; a capacity of n_leaves is rejected."""
+    G, L = lib
+    import ctypes
+    V, T = E.icosphere(14, 0.5)
+    m, keep = G._mesh(V, T)
+    o = G.TreeOptions(60, 0.25, 2, 0, 0)
+    nl, nz = ctypes.c_int64(), ctypes.c_int64()
+    assert L.efie_plan_adaptive_near(ctypes.byref(m), 2 * np.pi, 3, ctypes.byref(o), ctypes.byref(nl),
+                                     ctypes.byref(nz), None, None, 0, None, None, 0) == 0
+    ptr = np.zeros(nl.value + 1, np.int64)
+    ip = ptr.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    assert L.efie_plan_adaptive_near(ctypes.byref(m), 2 * np.pi, 3, ctypes.byref(o), None, None, None, None,
+                                     nl.value, ip, None, 0) == G.EFIE_EINVAL
+    assert L.efie_plan_adaptive_near(ctypes.byref(m), 2 * np.pi, 3, ctypes.byref(o), None, None, None, None,
+                                     nl.value + 1, ip, None, 0) == 0
+    assert ptr[-1] == nz.value
