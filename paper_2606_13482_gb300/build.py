@@ -20,7 +20,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc")
 CXX = os.environ.get("CXX", shutil.which("g++") or "g++")
 
-CU_SOURCES = ["near.cu", "far.cu", "api.cu", "noalloc.cu", "mpnn.cu"]
+CU_SOURCES = ["near.cu", "far.cu", "mac_tc.cu", "api.cu", "noalloc.cu", "mpnn.cu"]
 CXX_SOURCES = ["plan.cpp"]
 
 

@@ -138,11 +138,11 @@ namespace {
 // kernel classes for the profiling facility
 enum KClass {
   K_VEC = 0, K_ANTERP, K_UP, K_FWD, K_MAC, K_INV, K_DOWN, K_INTERP, K_NEAR_A, K_NEAR_V, K_KRYLOV, K_MAC_TOP,
-  K_PRECOND, K_NCLASS
+  K_PRECOND, K_MAC_TOP_TC, K_NCLASS
 };
 const char* kclass_name[K_NCLASS] = {"vector",   "anterpolation", "upward",  "forward_fft", "translation_mac",
                                      "inverse_fft", "downward",   "interpolation", "near_A", "near_V", "krylov",
-                                     "translation_mac_top", "precond"};
+                                     "translation_mac_top", "precond", "translation_mac_top_tc"};
 struct Prof {
   bool on = false;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev;
@@ -192,6 +192,7 @@ struct efie_handle {
   std::vector<float> g_sgn, g_len;
   ~efie_handle() {
     if (net) efie::nn_delete(net);
+    if (err_host) cudaFreeHost(err_host);
   }
   int64_t n_launches = 0;
   double setup_s[4] = {0, 0, 0, 0};  // efie_setup phases (efie_setup_times)
@@ -224,7 +225,10 @@ struct efie_handle {
   std::vector<LevDev> lev;
   FarSet<double> f64;
   FarSet<float> f32;
-  int mac_variant = 0;   // 0 auto (shared-memory staged), 1 register tiles (autotuner knob)
+  int mac_variant = 0;   // translation (autotuner knob): 0 auto (tensor cores on the top level when it
+                         // fits, else 2), 1 register tiles, 2 CUDA-core shared-memory staged
+  int* err_host = nullptr;  // host-mapped flag that device waits set when they run out
+  int* err_dev = nullptr;
   int near_variant = 0;  // mixed near field: 0 shared-memory staged x, 1 x through L1 (autotuner knob)
   // work vectors (FP64, sorted) and their double-float splits
   int Rw = 0;
@@ -389,7 +393,11 @@ std::vector<double2*> build_kernel_spectra64(efie_handle* h, cudaStream_t s) {
     std::vector<double2> fh((size_t)n * n);
     for (size_t i = 0; i < fh.size(); ++i) fh[i] = make_double2(L.Fn[i].real(), L.Fn[i].imag());
     cuda_check(cudaMemcpy(Fn, fh.data(), sizeof(double2) * fh.size(), cudaMemcpyHostToDevice), "Fn");
-    int64_t ob = std::max<int64_t>(1, std::min<int64_t>(O, (int64_t)(512LL << 20) / (n3 * 16)));
+    // offsets per pass: two work buffers of <= 512 MiB each, less when a
+    // device_mem_limit leaves less room
+    int64_t room = (int64_t)(512LL << 20);
+    if (h->mem.limit > 0) room = std::min(room, (h->mem.limit - h->mem.bytes - (int64_t)n * n * 16) / 2);
+    int64_t ob = std::max<int64_t>(1, std::min<int64_t>(O, room / (n3 * 16)));
     double2* a = h->mem.alloc<double2>(ob * n3);
     double2* b = h->mem.alloc<double2>(ob * n3);
     for (int64_t o0 = 0; o0 < O; o0 += ob) {
@@ -534,9 +542,17 @@ void far_chunk(efie_handle* h, FarSet<R>& F, int nr, cudaStream_t s) {
                        s);
     }
     {
-      KScope ks(h, ell == top ? K_MAC_TOP : K_MAC, s, 1);
-      launch_mac<R>(F.Qh, F.Rh, FL.Kh, B, C, LD.O, n3, LD.ntiles, h->mac_variant == 1 ? -LD.max_tile : LD.max_tile,
-                    LD.tile_tgt_ptr, LD.tile_tgt, LD.tile_src_ptr, LD.tile_src, LD.tile_kidx_off, LD.tile_kidx, s);
+      const bool tc = sizeof(R) == 4 && h->mac_variant == 0 && mac_top_tc_fits(C, LD.max_tile, LD.O);
+      KScope ks(h, tc ? K_MAC_TOP_TC : ell == top ? K_MAC_TOP : K_MAC, s, 1);
+      bool done = false;
+      if (tc)
+        done = launch_mac_top_tc((const float2*)F.Qh, (float2*)F.Rh, (const float2*)FL.Kh, B, C, LD.O, n3,
+                                 LD.ntiles, LD.max_tile, LD.tile_tgt_ptr, LD.tile_tgt, LD.tile_src_ptr, LD.tile_src,
+                                 LD.tile_kidx_off, LD.tile_kidx, h->err_dev, s);
+      if (!done)
+        launch_mac<R>(F.Qh, F.Rh, FL.Kh, B, C, LD.O, n3, LD.ntiles,
+                      h->mac_variant == 1 ? -LD.max_tile : LD.max_tile, LD.tile_tgt_ptr, LD.tile_tgt,
+                      LD.tile_src_ptr, LD.tile_src, LD.tile_kidx_off, LD.tile_kidx, s);
     }
     KScope ks(h, K_INV, s, 3);
     View b1{(int64_t)sp * n * n * C, (int64_t)n * n * C, (int64_t)n * C, C};
@@ -631,6 +647,11 @@ void matvec_chunk(efie_handle* h, FarSet<R>& F, const double2* x, int64_t ldx, i
 
 void do_matvec(efie_handle* h, const double2* x, int64_t ldx, double2* y, double2* yA, double2* yV,
                int64_t ldy, int n_rhs, bool force64, cudaStream_t s) {
+  // a device wait of an earlier product ran out (its outputs were set to NaN)
+  if (h->err_host && *reinterpret_cast<volatile int*>(h->err_host)) {
+    *reinterpret_cast<volatile int*>(h->err_host) = 0;
+    throw EfieError{EFIE_ETIMEOUT, "a bounded device wait of an earlier product expired"};
+  }
   // right-hand sides per far pass: at most 8; the FP64 pass of a mixed handle
   // (true residuals) runs one at a time to bound its buffers
   int Rc = h->opt.rhs_chunk > 0 ? std::min(h->opt.rhs_chunk, 8) : 8;
@@ -656,6 +677,11 @@ void setup_impl(efie_handle* h, const efie_mesh* mesh, double k, int p, double g
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0)
     throw EfieError{EFIE_ECUDA, "no CUDA device"};
   cuda_check(cudaGetDevice(&h->device), "cudaGetDevice");
+  // flag that bounded device waits set when they run out; host-mapped, so the
+  // host reads it without synchronising
+  cuda_check(cudaHostAlloc((void**)&h->err_host, sizeof(int), cudaHostAllocMapped), "cudaHostAlloc");
+  *h->err_host = 0;
+  cuda_check(cudaHostGetDevicePointer((void**)&h->err_dev, h->err_host, 0), "cudaHostGetDevicePointer");
   h->mem.limit = h->opt.device_mem_limit;
   Plan& P = h->plan;
   using clk = std::chrono::steady_clock;
@@ -892,7 +918,11 @@ void setup_impl(efie_handle* h, const efie_mesh* mesh, double k, int p, double g
       return (P.tset_ptr[x + 1] - P.tset_ptr[x]) * (P.tset_ptr[y + 1] - P.tset_ptr[y]);
     };
     for (int64_t j = 0; j < nblk; ++j) max_pairs = std::max(max_pairs, n_pairs(j));
-    int64_t cap = std::max(scr_cap, max_pairs);
+    // pairs per batch: ~1 GiB of scratch, less when a device_mem_limit leaves
+    // less room (never below the largest block)
+    int64_t cap = scr_cap;
+    if (M.limit > 0) cap = std::min(cap, (M.limit - M.bytes) / (10 * 16));
+    cap = std::max(cap, max_pairs);
     scratch = M.alloc<double2>(10 * cap);
     int64_t j0 = 0;
     std::vector<int64_t> scr_off;
@@ -1962,7 +1992,7 @@ int efie_precond_gradient(efie_handle* h, const void* r, const void* e, float* g
 }
 
 int efie_autotune_set(efie_handle* h, int rhs_chunk, int mac_variant, int near_variant) {
-  if (!h || rhs_chunk < 1 || rhs_chunk > 8 || mac_variant < 0 || mac_variant > 1 || near_variant < 0 ||
+  if (!h || rhs_chunk < 1 || rhs_chunk > 8 || mac_variant < 0 || mac_variant > 2 || near_variant < 0 ||
       near_variant > 1)
     return EFIE_EINVAL;
   h->opt.rhs_chunk = rhs_chunk;
@@ -1989,8 +2019,8 @@ int efie_autotune(efie_handle* h, int n_rhs, void* stream, int* best_chunk, int*
     int bc = 8, bm = 0, bn = 0;
     for (int chunk : {8, 4, 2, 1}) {
       if (chunk > n_rhs && chunk != 1) continue;
-      for (int cand = 0; cand < 4; ++cand) {
-        const int mv = cand & 1, nv = cand >> 1;
+      for (int cand = 0; cand < 6; ++cand) {
+        const int mv = cand % 3, nv = cand / 3;
         if (nv == 1 && !h->near_df) continue;  // the near variants differ in the mixed form only
         h->opt.rhs_chunk = chunk;
         h->mac_variant = mv;

@@ -102,13 +102,13 @@ template <typename R>
 bool launch_dft(const cpx_t<R>* in, View vin, cpx_t<R>* out, View vout, int64_t B, int C, int ax, int nin,
                 int e0, int e1, int e2, const cpx_t<R>* M, int n, bool inverse, cudaStream_t s);
 
-// top grid level: kernel spectra as a dense cube over box offsets (FP32)
-void launch_scatter_cube(const double2* K64, const int32_t* offsets, int64_t O, int64_t n3, int Dm, float2* Kd,
-                         cudaStream_t s);
-bool launch_mac_top_cube(const float2* Qh, float2* Rh, const float2* Kd, int64_t B, int C, int Dm, int64_t nf,
-                         int64_t ntiles, int max_tile_targets, int64_t max_tile_sources, const int64_t* tgt_ptr,
-                         const int32_t* tgt, const int64_t* src_ptr, const int32_t* src, const int4* ijk,
-                         cudaStream_t s);
+// top grid level on the tensor cores (tcgen05, kind::tf32 with a 3-term split,
+// FP32-class products); false when the configuration does not fit it
+bool mac_top_tc_fits(int C, int max_tile_targets, int64_t O);
+bool launch_mac_top_tc(const float2* Qh, float2* Rh, const float2* Kh, int64_t B, int C, int64_t O, int64_t nf,
+                       int64_t ntiles, int max_tile_targets, const int64_t* tgt_ptr, const int32_t* tgt,
+                       const int64_t* src_ptr, const int32_t* src, const int64_t* kidx_off, const int32_t* kidx,
+                       int* err, cudaStream_t s);
 
 template <typename R>
 void launch_gather_build(const R* mr, const int32_t* mr_base, const int32_t* mr_ext, const int64_t* mr_off,

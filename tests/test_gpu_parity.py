@@ -214,11 +214,11 @@ def test_top_level_mixed_batched(G, two_level_oracle):
         assert _rel(Y[r], ref_op.matvec(X[r])) < TOL32
 
 
-@pytest.mark.parametrize("mac_variant", [0, 1])
+@pytest.mark.parametrize("mac_variant", [0, 1, 2])
 def test_top_level_translation_variants(G, two_level_oracle, mac_variant):
-    """Both top-level translation kernels the autotuner can pick (0: shared-memory
-    staging through the pair index tile, 1: register tiles) against the oracle,
-    mixed form."""
+    """The three top-level translation kernels the autotuner can pick (0: tensor
+    cores, 3-term TF32 split; 1: register tiles; 2: CUDA cores with
+    shared-memory staging) against the oracle, mixed form."""
     torch = _torch()
     V, T, ref_op = two_level_oracle
     _, _, k, p, delta, levels = TWO_LEVEL
