@@ -321,16 +321,17 @@ int efie_precond_gradient(efie_handle *h, const void *r, const void *e, float *g
  * efie_autotune times one product of n_rhs vectors for each candidate
  * right-hand-side chunk (8, 4, 2, 1 vectors per far-field pass), each
  * top-level translation kernel (0: tensor cores, tcgen05 with a 3-term TF32
- * split of every FP32 operand, used where the top level fits it and the far
- * field is FP32, else as 2; 1: register tiles; 2: CUDA cores with
- * shared-memory staging through the pair index tile) and, for mixed handles,
- * each near-field
+ * split of every FP32 operand, in the persistent warp-specialised form where
+ * the top level fits it and the far field is FP32, else as 3, else as 2;
+ * 1: register tiles; 2: CUDA cores with shared-memory staging through the
+ * pair index tile; 3: tensor cores, one CTA per tile and frequency) and, for
+ * mixed handles, each near-field
  * kernel (0: source values staged in shared memory, 1: read through L1 with
  * no barriers), and keeps the fastest in the handle; the choices are
  * returned if the pointers are set. */
 int efie_autotune(efie_handle *h, int n_rhs, void *stream, int *best_chunk, int *best_mac, int *best_near);
 /* Sets the three choices efie_autotune makes: rhs_chunk in 1..8, mac_variant
- * in 0..2 and near_variant in 0..1 as above.  EFIE_EINVAL outside those
+ * in 0..3 and near_variant in 0..1 as above.  EFIE_EINVAL outside those
  * ranges. */
 int efie_autotune_set(efie_handle *h, int rhs_chunk, int mac_variant, int near_variant);
 

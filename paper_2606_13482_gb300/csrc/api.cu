@@ -117,6 +117,7 @@ struct LevDev {
   // translation tiles
   int64_t ntiles = 0;
   int max_tile = 0;
+  bool src_all = false;  // every tile's sources are all boxes of the level, in order
   int64_t *tile_tgt_ptr = nullptr, *tile_src_ptr = nullptr, *tile_kidx_off = nullptr;
   int32_t *tile_tgt = nullptr, *tile_src = nullptr, *tile_kidx = nullptr;
   // sibling-shared transfers between this (child) level and its parents:
@@ -225,8 +226,9 @@ struct efie_handle {
   std::vector<LevDev> lev;
   FarSet<double> f64;
   FarSet<float> f32;
-  int mac_variant = 0;   // translation (autotuner knob): 0 auto (tensor cores on the top level when it
-                         // fits, else 2), 1 register tiles, 2 CUDA-core shared-memory staged
+  int mac_variant = 0;   // translation (autotuner knob): 0 auto (tensor cores on the top level, persistent
+                         // form, else 3, else 2), 1 register tiles, 2 CUDA-core shared-memory staged,
+                         // 3 tensor cores with one CTA per (tile, frequency)
   int* err_host = nullptr;  // host-mapped flag that device waits set when they run out
   int* err_dev = nullptr;
   int near_variant = 0;  // mixed near field: 0 shared-memory staged x, 1 x through L1 (autotuner knob)
@@ -542,13 +544,22 @@ void far_chunk(efie_handle* h, FarSet<R>& F, int nr, cudaStream_t s) {
                        s);
     }
     {
-      const bool tc = sizeof(R) == 4 && h->mac_variant == 0 && mac_top_tc_fits(C, LD.max_tile, LD.O);
-      KScope ks(h, tc ? K_MAC_TOP_TC : ell == top ? K_MAC_TOP : K_MAC, s, 1);
+      const bool tc2 = sizeof(R) == 4 && h->mac_variant == 0 && LD.src_all &&
+                       mac_top_tc2_fits(C, LD.max_tile, LD.O, B, LD.ntiles);
+      const bool tc = sizeof(R) == 4 && (h->mac_variant == 0 || h->mac_variant == 3) &&
+                      mac_top_tc_fits(C, LD.max_tile, LD.O);
+      KScope ks(h, tc || tc2 ? K_MAC_TOP_TC : ell == top ? K_MAC_TOP : K_MAC, s, 1);
       bool done = false;
-      if (tc)
+      if (tc2)
+        done = launch_mac_top_tc2((const float2*)F.Qh, (float2*)F.Rh, (const float2*)FL.Kh, B, C, LD.O, n3,
+                                  LD.ntiles, LD.max_tile, LD.tile_tgt_ptr, LD.tile_tgt, LD.tile_src_ptr,
+                                  LD.tile_kidx_off, LD.tile_kidx, h->err_dev, s);
+      if (done) cuda_check(cudaPeekAtLastError(), "top-level translation (persistent tensor-core kernel)");
+      if (!done && tc)
         done = launch_mac_top_tc((const float2*)F.Qh, (float2*)F.Rh, (const float2*)FL.Kh, B, C, LD.O, n3,
                                  LD.ntiles, LD.max_tile, LD.tile_tgt_ptr, LD.tile_tgt, LD.tile_src_ptr, LD.tile_src,
                                  LD.tile_kidx_off, LD.tile_kidx, h->err_dev, s);
+      if (done) cuda_check(cudaPeekAtLastError(), "top-level translation (tensor-core kernel)");
       if (!done)
         launch_mac<R>(F.Qh, F.Rh, FL.Kh, B, C, LD.O, n3, LD.ntiles,
                       h->mac_variant == 1 ? -LD.max_tile : LD.max_tile, LD.tile_tgt_ptr, LD.tile_tgt,
@@ -838,6 +849,15 @@ void setup_impl(efie_handle* h, const efie_mesh* mesh, double k, int p, double g
       LD.dz_src = M.upload(dzs);
     }
     LD.ntiles = (int64_t)L.tile_tgt_ptr.size() - 1;
+    // every tile takes all boxes of the level as its sources, in box order
+    // (the top grid level), which the persistent tensor-core kernel assumes
+    LD.src_all = LD.ntiles > 0;
+    for (int64_t t = 0; t < LD.ntiles && LD.src_all; ++t) {
+      const int64_t a = L.tile_src_ptr[t], b = L.tile_src_ptr[t + 1];
+      if (b - a != (int64_t)L.code.size()) LD.src_all = false;
+      for (int64_t j = a; j < b && LD.src_all; ++j)
+        if (L.tile_src[j] != (int32_t)(j - a)) LD.src_all = false;
+    }
     for (int64_t t = 0; t < LD.ntiles; ++t)
       LD.max_tile = std::max<int>(LD.max_tile, (int)(L.tile_tgt_ptr[t + 1] - L.tile_tgt_ptr[t]));
     LD.tile_tgt_ptr = M.upload(L.tile_tgt_ptr);
@@ -1992,7 +2012,7 @@ int efie_precond_gradient(efie_handle* h, const void* r, const void* e, float* g
 }
 
 int efie_autotune_set(efie_handle* h, int rhs_chunk, int mac_variant, int near_variant) {
-  if (!h || rhs_chunk < 1 || rhs_chunk > 8 || mac_variant < 0 || mac_variant > 2 || near_variant < 0 ||
+  if (!h || rhs_chunk < 1 || rhs_chunk > 8 || mac_variant < 0 || mac_variant > 3 || near_variant < 0 ||
       near_variant > 1)
     return EFIE_EINVAL;
   h->opt.rhs_chunk = rhs_chunk;
@@ -2019,8 +2039,8 @@ int efie_autotune(efie_handle* h, int n_rhs, void* stream, int* best_chunk, int*
     int bc = 8, bm = 0, bn = 0;
     for (int chunk : {8, 4, 2, 1}) {
       if (chunk > n_rhs && chunk != 1) continue;
-      for (int cand = 0; cand < 6; ++cand) {
-        const int mv = cand % 3, nv = cand / 3;
+      for (int cand = 0; cand < 8; ++cand) {
+        const int mv = cand % 4, nv = cand / 4;
         if (nv == 1 && !h->near_df) continue;  // the near variants differ in the mixed form only
         h->opt.rhs_chunk = chunk;
         h->mac_variant = mv;

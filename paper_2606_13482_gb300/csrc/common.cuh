@@ -62,18 +62,28 @@ __host__ __device__ __forceinline__ T cscale(T a, S s) {
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
-// Raises a kernel's dynamic shared-memory limit on the current device the first
-// time that device launches it.  The limit is a per-device attribute, so the
-// mask holds one bit per device (devices 64 and up set it on every call);
-// threads that race both set the same value, which is harmless.
+// Raises a kernel's dynamic shared-memory limit on the current device when a
+// launch needs more than the limit set so far.  The limit is a per-device
+// attribute; `done` keeps, per device (64 at most; later devices set it on
+// every call), the largest value set.  Threads that race both set a value
+// that covers their launch.
 template <typename K>
-inline void smem_attr_once(K kernel, int bytes, std::atomic<uint64_t>& done) {
+inline void smem_attr_once(K kernel, int bytes, std::atomic<uint64_t>* done) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return;
-  const uint64_t bit = dev < 64 ? (1ull << dev) : 0;
-  if (bit && (done.load(std::memory_order_acquire) & bit)) return;
-  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess && bit)
-    done.fetch_or(bit, std::memory_order_acq_rel);
+  if (dev < 64 && done[dev].load(std::memory_order_acquire) >= (uint64_t)bytes) return;
+  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess && dev < 64) {
+    uint64_t cur = done[dev].load(std::memory_order_acquire);
+    while (cur < (uint64_t)bytes && !done[dev].compare_exchange_weak(cur, (uint64_t)bytes)) {
+    }
+  }
 }
+// per-kernel state of smem_attr_once
+struct SmemAttr {
+  std::atomic<uint64_t> v[64];
+  SmemAttr() {
+    for (auto& x : v) x.store(0);
+  }
+};
 
 }  // namespace efie

@@ -157,8 +157,8 @@ template <typename R, bool CM, int NMAX, int LPT>
 static void run_mode_line(const cpx_t<R>* in, View vin, cpx_t<R>* out, View vout, int64_t B, int C, int ax,
                           int nin, int e0, int e1, int e2, const void* M0, const void* M1, const int8_t* sel,
                           const int64_t* srcmap, bool accumulate, size_t smem, cudaStream_t s) {
-  static std::atomic<uint64_t> attr{0};
-  smem_attr_once(k_mode_line<R, CM, NMAX, LPT>, 96 * 1024, attr);
+  static SmemAttr attr;
+  smem_attr_once(k_mode_line<R, CM, NMAX, LPT>, 96 * 1024, attr.v);
   const int ea = ax == 0 ? e1 : e0, eb = ax == 2 ? e1 : e2;
   int64_t lines = B * ea * eb * (int64_t)(C / LPT);
   int64_t blocks = ceil_div(lines, 128);
@@ -508,8 +508,8 @@ bool launch_dft(const cpx_t<R>* in, View vin, cpx_t<R>* out, View vout, int64_t 
   if (nin <= NM) {                                                                                           \
     if (two && NM <= 21) {                                                                                   \
       auto k = k_dft_fwd_line<R, NM, (sizeof(R) == 4 && NM <= 21) ? 2 : 1>;                                  \
-      static std::atomic<uint64_t> attr{0};                                                                  \
-      smem_attr_once(k, 96 * 1024, attr);                                                                    \
+      static SmemAttr attr;                                                                  \
+      smem_attr_once(k, 96 * 1024, attr.v);                                                                    \
       k<<<(unsigned)blocks, 128, smem, s>>>(in, vin, out, vout, B, C, ax, nin, e0, e1, e2, M, n);            \
       return true;                                                                                           \
     }                                                                                                        \
@@ -517,8 +517,8 @@ bool launch_dft(const cpx_t<R>* in, View vin, cpx_t<R>* out, View vout, int64_t 
     int64_t blocks1 = ceil_div(lines1, 128);                                                                 \
     if (blocks1 > 152 * 32) blocks1 = 152 * 32;                                                              \
     auto k = k_dft_fwd_line<R, NM, 1>;                                                                       \
-    static std::atomic<uint64_t> attr1{0};                                                                   \
-    smem_attr_once(k, 96 * 1024, attr1);                                                                     \
+    static SmemAttr attr1;                                                                   \
+    smem_attr_once(k, 96 * 1024, attr1.v);                                                                     \
     k<<<(unsigned)blocks1, 128, smem, s>>>(in, vin, out, vout, B, C, ax, nin, e0, e1, e2, M, n);             \
     return true;                                                                                             \
   }
@@ -535,8 +535,8 @@ bool launch_dft(const cpx_t<R>* in, View vin, cpx_t<R>* out, View vout, int64_t 
   if (nout <= AM) {                                                                                          \
     if (two && AM <= 21) {                                                                                   \
       auto k = k_dft_inv_line<R, AM, (sizeof(R) == 4 && AM <= 21) ? 2 : 1>;                                  \
-      static std::atomic<uint64_t> attr{0};                                                                  \
-      smem_attr_once(k, 96 * 1024, attr);                                                                    \
+      static SmemAttr attr;                                                                  \
+      smem_attr_once(k, 96 * 1024, attr.v);                                                                    \
       k<<<(unsigned)blocks, 128, smem, s>>>(in, vin, out, vout, B, C, ax, nin, e0, e1, e2, M, n);            \
       return true;                                                                                           \
     }                                                                                                        \
@@ -544,8 +544,8 @@ bool launch_dft(const cpx_t<R>* in, View vin, cpx_t<R>* out, View vout, int64_t 
     int64_t blocks1 = ceil_div(lines1, 128);                                                                 \
     if (blocks1 > 152 * 32) blocks1 = 152 * 32;                                                              \
     auto k = k_dft_inv_line<R, AM, 1>;                                                                       \
-    static std::atomic<uint64_t> attr1{0};                                                                   \
-    smem_attr_once(k, 96 * 1024, attr1);                                                                     \
+    static SmemAttr attr1;                                                                   \
+    smem_attr_once(k, 96 * 1024, attr1.v);                                                                     \
     k<<<(unsigned)blocks1, 128, smem, s>>>(in, vin, out, vout, B, C, ax, nin, e0, e1, e2, M, n);             \
     return true;                                                                                             \
   }
@@ -1298,8 +1298,8 @@ void launch_mac(const cpx_t<R>* Qh, cpx_t<R>* Rh, const cpx_t<R>* Kh, int64_t B,
   if (!force_reg && sizeof(R) == 4 && C == 32 && max_tile_targets > 8 && max_tile_targets <= 128) {
     constexpr int YS = 16;
     const size_t smem = 2 * sizeof(float2) * YS * (128 + 32);
-    static std::atomic<uint64_t> attr{0};
-    smem_attr_once(k_mac_top32<YS>, (int)smem, attr);
+    static SmemAttr attr;
+    smem_attr_once(k_mac_top32<YS>, (int)smem, attr.v);
     for (int64_t f0 = 0; f0 < nf; f0 += 65535) {
       int64_t nfc = std::min<int64_t>(65535, nf - f0);
       dim3 grid((unsigned)ntiles, (unsigned)nfc);
@@ -1318,8 +1318,8 @@ void launch_mac(const cpx_t<R>* Qh, cpx_t<R>* Rh, const cpx_t<R>* Kh, int64_t B,
     if (fpb < 1) fpb = 1;
     while (fpb > 1 && (size_t)fpb * O * sizeof(float2) > 64 * 1024) fpb >>= 1;
     const size_t smem = (size_t)fpb * O * sizeof(float2);
-    static std::atomic<uint64_t> attr{0};
-    smem_attr_once(k_mac_il32<8, CRI>, 64 * 1024, attr);
+    static SmemAttr attr;
+    smem_attr_once(k_mac_il32<8, CRI>, 64 * 1024, attr.v);
     const int64_t fchunk = (int64_t)65535 * fpb;
     for (int64_t f0 = 0; f0 < nf; f0 += fchunk) {
       int64_t nfc = std::min<int64_t>(fchunk, nf - f0);

@@ -91,6 +91,11 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const float* v) {
       "f"(v[10]), "f"(v[11]), "f"(v[12]), "f"(v[13]), "f"(v[14]), "f"(v[15]));
 }
 
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const float* v) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};\n" ::"r"(taddr), "f"(v[0]),
+               "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7]));
+}
+
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%"
@@ -99,6 +104,14 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
         "=f"(v[9]), "=f"(v[10]), "=f"(v[11]), "=f"(v[12]), "=f"(v[13]), "=f"(v[14]), "=f"(v[15]), "=f"(v[16]),
         "=f"(v[17]), "=f"(v[18]), "=f"(v[19]), "=f"(v[20]), "=f"(v[21]), "=f"(v[22]), "=f"(v[23]), "=f"(v[24]),
         "=f"(v[25]), "=f"(v[26]), "=f"(v[27]), "=f"(v[28]), "=f"(v[29]), "=f"(v[30]), "=f"(v[31])
+      : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7]), "=f"(v[8]),
+        "=f"(v[9]), "=f"(v[10]), "=f"(v[11]), "=f"(v[12]), "=f"(v[13]), "=f"(v[14]), "=f"(v[15])
       : "r"(taddr));
 }
 
@@ -327,6 +340,374 @@ __global__ void __launch_bounds__(128, 2)
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tm), "r"(TC_COLS));
 }
 
+// ---------------------------------------------------------------------------
+// Persistent, warp-specialised form (one CTA per SM, all 512 TMEM columns).
+// The CTA owns frequencies f = blockIdx.x + k * gridDim.x and runs every tile
+// of each; the chunks of 16 sources of all tiles form one sequence g.  Roles:
+//   producers (2 warpgroups; chunk g goes to warpgroup g % 2): gather and
+//     split the kernel values of their target row into the A stage of chunk g
+//     (TMEM, tcgen05.st) and the source spectra into its B stage (shared
+//     memory), then arrive on full[g % 4];
+//   MMA warp (one lane): loads the kernel spectrum row of the next frequency
+//     by TMA bulk copies while the current one is in use, waits on full[],
+//     issues the 12 MMAs of a chunk (N = 64: B = [Q_r | Q_i] rows; the hi x hi,
+//     hi x lo and lo x hi products of K_r into D1 and of K_i into D2) and
+//     commits them to empty[g % 4], and after a tile's last chunk to dfull[];
+//   epilogue warpgroup: reads the tile's accumulators (double-buffered in
+//     TMEM), forms R_r = (K_r Q_r) - (K_i Q_i), R_i = (K_r Q_i) + (K_i Q_r),
+//     frees the buffer (dempty[]) and stores the complex rows.
+// Four chunk stages, two accumulator buffers, two kernel-row buffers; every
+// mbarrier wait is bounded and a timeout stops every role of the CTA.
+namespace {
+constexpr int T2_STAGES = 4;
+constexpr int T2_PROD = 256;                  // producer threads (2 warpgroups)
+constexpr int T2_MMA_WARP = T2_PROD / 32;     // warp 8
+constexpr int T2_EPI0 = T2_PROD + 32;         // first epilogue thread
+constexpr int T2_THREADS = T2_EPI0 + 128;     // 416 threads per CTA
+constexpr uint32_t T2_COLS = 512;
+constexpr uint32_t T2_DBUF = 128;             // one accumulator buffer: D1 (64) | D2 (64)
+constexpr uint32_t T2_A0 = 2 * T2_DBUF;       // A stages at 256 + 64 * stage
+constexpr int T2_BN = 64;                     // B rows: 32 channels real, then 32 imaginary
+constexpr int T2_BMAT = T2_BN * TC_KC * 4;    // 4 KB: one B matrix (hi or lo)
+constexpr int T2_BSTAGE = 2 * T2_BMAT;
+constexpr int T2_QMAX = 1024;                 // chunks per frequency (chunk table in shared memory)
+constexpr int T2_PIECE = 16384;               // bytes per bulk copy of a kernel row
+
+constexpr int T2_TMAX = 64;                   // tiles of the level
+struct T2Tile {
+  int64_t koff;        // start of the tile's index block
+  int32_t t0, nt, tpad, ns;
+};
+struct T2Bar {
+  uint64_t full[T2_STAGES], empty[T2_STAGES], dfull[2], dempty[2], rfull[2], rempty[2];
+  uint32_t tmem_base;
+  int abort;
+  int nq;
+  T2Tile tile[T2_TMAX];
+};
+
+// x = hi + lo with hi the TF32 part of x (sign, exponent and 10 mantissa bits
+// kept, the rest cleared) and lo = x - hi exactly; the tensor core truncates lo
+// to TF32 in turn, so x is carried to about 22 bits
+__device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(b)), "r"(count));
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(b)) : "memory");
+}
+// bounded wait that also gives up at once when another role of the CTA gave up
+__device__ __forceinline__ bool t2_wait(uint64_t* b, uint32_t parity, T2Bar* bar, int* err) {
+  const uint32_t a = smem_u32(b);
+  for (long long it = 0; it < TC_SPIN; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n.reg .pred q;\nmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\nselp.u32 %0, 1, 0, q;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if ((it & 63) == 63 && *reinterpret_cast<volatile int*>(&bar->abort)) return false;
+  }
+  *reinterpret_cast<volatile int*>(&bar->abort) = 1;
+  if (err) *reinterpret_cast<volatile int*>(err) = 1;
+  return false;
+}
+
+__device__ __forceinline__ uint64_t smem_desc_sbo(uint32_t saddr, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)((TC_LBO >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+// kind::tf32, FP32 accumulate, K-major A and B, M = 128, N = 64
+constexpr uint32_t T2_IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(T2_BN >> 3) << 17) | ((128u >> 4) << 24);
+}  // namespace
+
+// dynamic shared memory: [2 kernel rows of kbytes][4 B stages][chunk table]
+__global__ void __maxnreg__(128)
+    k_mac_top_tc2(const float2* __restrict__ Qh, float2* __restrict__ Rh, const float2* __restrict__ Kh, int64_t B,
+                  int64_t O, int64_t nf, int64_t ntiles, const int64_t* __restrict__ tgt_ptr,
+                  const int32_t* __restrict__ tgt, const int64_t* __restrict__ src_ptr,
+                  const int64_t* __restrict__ kidx_off, const int32_t* __restrict__ kidx, int kbytes, int* err) {
+  extern __shared__ __align__(1024) unsigned char t2_smem[];
+  __shared__ T2Bar bar;
+  unsigned char* rows = t2_smem;
+  unsigned char* Bs = t2_smem + 2 * kbytes;
+  int32_t* ctab = reinterpret_cast<int32_t*>(Bs + T2_STAGES * T2_BSTAGE);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t K = nf > blockIdx.x ? (nf - 1 - blockIdx.x) / gridDim.x + 1 : 0;   // frequencies of this CTA
+
+  if (tid == 0) {
+    for (int i = 0; i < T2_STAGES; ++i) {
+      mbar_init(&bar.full[i], 128);
+      mbar_init(&bar.empty[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&bar.dfull[i], 1);
+      mbar_init(&bar.dempty[i], 128);
+      mbar_init(&bar.rfull[i], 1);
+      mbar_init(&bar.rempty[i], T2_PROD);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    bar.abort = 0;
+    // tile table and chunk table ((tile << 16) | first source, tile by tile)
+    int q = 0;
+    for (int64_t t = 0; t < ntiles && t < T2_TMAX; ++t) {
+      const int64_t ns = src_ptr[t + 1] - src_ptr[t], nt = tgt_ptr[t + 1] - tgt_ptr[t];
+      bar.tile[t].koff = kidx_off[t];
+      bar.tile[t].t0 = (int32_t)tgt_ptr[t];
+      bar.tile[t].nt = (int32_t)nt;
+      bar.tile[t].tpad = (int32_t)(((nt + 7) / 8) * 8);
+      bar.tile[t].ns = (int32_t)ns;
+      for (int64_t j0 = 0; j0 < ns && q < T2_QMAX; j0 += TC_KC) ctab[q++] = (int32_t)((t << 16) | j0);
+    }
+    bar.nq = q;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&bar.tmem_base)),
+                 "r"(T2_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tm = bar.tmem_base;
+  const int64_t nq = bar.nq;
+  const int64_t TS = K * ntiles;      // tiles of this CTA
+
+  if (tid < T2_PROD) {
+    // ------------------------------------------------------------ producers
+    const int wg = tid >> 7, r = tid & 127;
+    const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+    // B operands: this thread stores source jB of the chunk, channels chB + 8u
+    const int jB = (warp & 3) * 4 + (lane >> 3), chB = lane & 7;
+    const int boff = (jB >> 2) * TC_LBO + (jB & 3) * 4 + chB * 16;   // + u SBO (real), + (4 + u) SBO (imaginary)
+    const int nq32 = (int)nq;
+    int32_t idn[TC_KC];
+    float2 qn[4];
+    // loads of chunk (k, q): the index rows of this thread's target, the source spectra
+    auto load = [&](int64_t k, int q) {
+#pragma unroll
+      for (int j = 0; j < TC_KC; ++j) idn[j] = -1;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) qn[u] = make_float2(0.f, 0.f);
+      if (k >= K) return;
+      const int32_t e = ctab[q];
+      const T2Tile& T = bar.tile[e >> 16];
+      const int j0 = e & 0xFFFF;
+      if (r < T.tpad) {
+        const int32_t* kb = kidx + T.koff + (int64_t)j0 * T.tpad + r;
+#pragma unroll
+        for (int j = 0; j < TC_KC; ++j)
+          if (j0 + j < T.ns) idn[j] = __ldg(kb + j * T.tpad);
+      }
+      // the top grid level translates every box: source j is box j
+      if (j0 + jB < T.ns) {
+        const float2* Qp = Qh + ((int64_t)(blockIdx.x + k * gridDim.x) * B + j0 + jB) * TC_C + chB;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) qn[u] = __ldg(Qp + 8 * u);
+      }
+    };
+    // this warpgroup's chunks g = wg, wg + 2, ... as (frequency k, chunk q)
+    int64_t kn = 0;
+    int qn_ = wg;
+    while (qn_ >= nq32 && nq32 > 0) {
+      qn_ -= nq32;
+      ++kn;
+    }
+    if (nq32 > 0) load(kn, qn_);
+    int64_t g = wg;
+    bool ok = true;
+    for (int64_t k = 0; k < K && ok; ++k) {
+      const int rb = (int)(k & 1);
+      ok = t2_wait(&bar.rfull[rb], (uint32_t)((k >> 1) & 1), &bar, err);
+      if (!ok) break;
+      const float2* Ks = reinterpret_cast<const float2*>(rows + rb * kbytes);
+      for (; g < (k + 1) * nq; g += 2) {
+        int32_t idc[TC_KC];
+        float2 qc[4];
+#pragma unroll
+        for (int j = 0; j < TC_KC; ++j) idc[j] = idn[j];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) qc[u] = qn[u];
+        qn_ += 2;
+        while (qn_ >= nq32) {
+          qn_ -= nq32;
+          ++kn;
+        }
+        load(kn, qn_);
+        const int slot = (int)(g & (T2_STAGES - 1));
+        if (g >= T2_STAGES) {
+          ok = t2_wait(&bar.empty[slot], (uint32_t)(((g >> 2) - 1) & 1), &bar, err);
+          if (!ok) break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        {
+          const uint32_t ta = tm + lane_base + T2_A0 + (uint32_t)slot * 4 * TC_KC;
+#pragma unroll
+          for (int hh = 0; hh < TC_KC; hh += 8) {
+            float arh[8], arl[8], aih[8], ail[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              const float2 kv = idc[hh + j] >= 0 ? Ks[idc[hh + j]] : make_float2(0.f, 0.f);
+              arh[j] = tf32_hi(kv.x);
+              arl[j] = kv.x - arh[j];
+              aih[j] = tf32_hi(kv.y);
+              ail[j] = kv.y - aih[j];
+            }
+            tmem_st8(ta + 0 * TC_KC + hh, arh);
+            tmem_st8(ta + 1 * TC_KC + hh, arl);
+            tmem_st8(ta + 2 * TC_KC + hh, aih);
+            tmem_st8(ta + 3 * TC_KC + hh, ail);
+          }
+        }
+        {
+          float* bb = reinterpret_cast<float*>(Bs + slot * T2_BSTAGE + boff);
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const float rh = tf32_hi(qc[u].x), ih = tf32_hi(qc[u].y);
+            bb[(u * TC_SBO) / 4] = rh;
+            bb[((4 + u) * TC_SBO) / 4] = ih;
+            bb[(T2_BMAT + u * TC_SBO) / 4] = qc[u].x - rh;
+            bb[(T2_BMAT + (4 + u) * TC_SBO) / 4] = qc[u].y - ih;
+          }
+        }
+        asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+        mbar_arrive(&bar.full[slot]);
+      }
+      if (!ok) break;
+      mbar_arrive(&bar.rempty[rb]);   // this thread is done with the row buffer
+    }
+  } else if (warp == T2_MMA_WARP) {
+    // ------------------------------------------------------------ MMA warp
+    if (lane == 0) {
+      auto load_row = [&](int64_t k) {
+        const int rb = (int)(k & 1);
+        const unsigned char* src = reinterpret_cast<const unsigned char*>(Kh + (blockIdx.x + k * gridDim.x) * O);
+        const uint32_t dst = smem_u32(rows + rb * kbytes);
+        const uint32_t bytes = (uint32_t)(O * 8);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(&bar.rfull[rb])),
+                     "r"(bytes)
+                     : "memory");
+        for (uint32_t off = 0; off < bytes; off += T2_PIECE) {
+          const uint32_t n = bytes - off < (uint32_t)T2_PIECE ? bytes - off : (uint32_t)T2_PIECE;
+          asm volatile(
+              "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst +
+                                                                                                                  off),
+              "l"(src + off), "r"(n), "r"(smem_u32(&bar.rfull[rb]))
+              : "memory");
+        }
+      };
+      bool ok = true;
+      if (K > 0) load_row(0);
+      if (K > 1) load_row(1);
+      int64_t g = 0, ts = 0;
+      for (int64_t k = 0; k < K && ok; ++k) {
+        if (k >= 1 && k + 1 < K) {
+          ok = t2_wait(&bar.rempty[(k + 1) & 1], (uint32_t)(((k - 1) >> 1) & 1), &bar, err);
+          if (!ok) break;
+          load_row(k + 1);
+        }
+        for (int64_t t = 0; t < ntiles && ok; ++t, ++ts) {
+          const int db = (int)(ts & 1);
+          if (ts >= 2) {
+            ok = t2_wait(&bar.dempty[db], (uint32_t)(((ts >> 1) - 1) & 1), &bar, err);
+            if (!ok) break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+          const int64_t nch = (bar.tile[t].ns + TC_KC - 1) / TC_KC;
+          const uint32_t d1 = tm + (uint32_t)db * T2_DBUF, d2 = d1 + 64;
+          for (int64_t c = 0; c < nch; ++c, ++g) {
+            const int slot = (int)(g & (T2_STAGES - 1));
+            ok = t2_wait(&bar.full[slot], (uint32_t)((g >> 2) & 1), &bar, err);
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            const uint32_t a0 = tm + T2_A0 + (uint32_t)slot * 4 * TC_KC;
+            const uint32_t bs = smem_u32(Bs + slot * T2_BSTAGE);
+#pragma unroll
+            for (int kk = 0; kk < TC_KC / 8; ++kk) {
+              const uint32_t arh = a0 + 0 * TC_KC + kk * 8, arl = a0 + 1 * TC_KC + kk * 8;
+              const uint32_t aih = a0 + 2 * TC_KC + kk * 8, ail = a0 + 3 * TC_KC + kk * 8;
+              const uint32_t ko = (uint32_t)kk * 2 * TC_LBO;
+              const uint64_t bh = smem_desc_sbo(bs + ko, TC_SBO), bl = smem_desc_sbo(bs + T2_BMAT + ko, TC_SBO);
+              const uint32_t acc0 = (c > 0 || kk > 0) ? 1u : 0u;
+              mma_tf32(d1, arh, bh, T2_IDESC, acc0);
+              mma_tf32(d1, arh, bl, T2_IDESC, 1u);
+              mma_tf32(d1, arl, bh, T2_IDESC, 1u);
+              mma_tf32(d2, aih, bh, T2_IDESC, acc0);
+              mma_tf32(d2, aih, bl, T2_IDESC, 1u);
+              mma_tf32(d2, ail, bh, T2_IDESC, 1u);
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                             smem_u32(&bar.empty[slot]))
+                         : "memory");
+          }
+          if (!ok) break;
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                           smem_u32(&bar.dfull[db]))
+                       : "memory");
+        }
+      }
+      // the last commits cover every MMA of this thread
+      if (ok && TS > 0) t2_wait(&bar.dfull[(TS - 1) & 1], (uint32_t)(((TS - 1) >> 1) & 1), &bar, err);
+    }
+    __syncwarp();
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int r = (warp & 3) * 32 + lane;
+    const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+    int64_t ts = 0;
+    bool ok = true;
+    for (int64_t k = 0; k < K && ok; ++k) {
+      const int64_t f = blockIdx.x + k * gridDim.x;
+      for (int64_t t = 0; t < ntiles; ++t, ++ts) {
+        const int db = (int)(ts & 1);
+        ok = t2_wait(&bar.dfull[db], (uint32_t)((ts >> 1) & 1), &bar, err);
+        if (!ok) break;
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        const uint32_t d1 = tm + lane_base + (uint32_t)db * T2_DBUF, d2 = d1 + 64;
+        const int64_t t0 = bar.tile[t].t0, nt = bar.tile[t].nt;
+        const bool any = bar.tile[t].ns > 0;
+        float2* out = r < nt ? Rh + f * B * TC_C + (int64_t)tgt[t0 + r] * TC_C : nullptr;
+#pragma unroll
+        for (int h = 0; h < TC_C; h += 16) {
+          float re[16], im[16], p[16];
+          tmem_ld16(d1 + h, re);         // K_r Q_r
+          tmem_ld16(d2 + 32 + h, p);     // K_i Q_i
+          asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+          for (int n = 0; n < 16; ++n) re[n] -= p[n];
+          tmem_ld16(d1 + 32 + h, im);    // K_r Q_i
+          tmem_ld16(d2 + h, p);          // K_i Q_r
+          asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+          for (int n = 0; n < 16; ++n) im[n] += p[n];
+          if (h + 16 == TC_C) {
+            // the accumulators of this buffer are read: the MMA warp may reuse it
+            asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+            mbar_arrive(&bar.dempty[db]);
+          }
+          if (out) {
+#pragma unroll
+            for (int n = 0; n < 16; n += 2)
+              *reinterpret_cast<float4*>(out + h + n) =
+                  any ? make_float4(re[n], im[n], re[n + 1], im[n + 1]) : make_float4(0.f, 0.f, 0.f, 0.f);
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tm), "r"(T2_COLS));
+}
+
 // Returns false when the configuration does not fit this kernel (the caller
 // then uses the CUDA-core kernels): 32 channels, tiles of 9..128 targets, and
 // a kernel spectrum row that fits in shared memory beside the B buffers with
@@ -349,14 +730,46 @@ bool launch_mac_top_tc(const float2* Qh, float2* Rh, const float2* Kh, int64_t B
   if (!mac_top_tc_fits(C, max_tile_targets, O)) return false;
   const int64_t kbytes = ((O * 8 + 1023) / 1024) * 1024;
   const int64_t smem = tc_smem_bytes(O);
-  static std::atomic<uint64_t> attr{0};
-  smem_attr_once(k_mac_top_tc, (int)smem, attr);
+  static SmemAttr attr;
+  smem_attr_once(k_mac_top_tc, (int)smem, attr.v);
   for (int64_t fs = 0; fs < nf; fs += 65535) {
     const int64_t nfc = nf - fs < 65535 ? nf - fs : 65535;
     dim3 grid((unsigned)ntiles, (unsigned)nfc);
     k_mac_top_tc<<<grid, 128, (size_t)smem, s>>>(Qh, Rh, Kh, B, O, nf, tgt_ptr, tgt, src_ptr, src, kidx_off, kidx,
                                                  fs, (int)kbytes, err);
   }
+  return true;
+}
+
+// The persistent kernel: the conditions of launch_mac_top_tc, plus an even
+// number of offsets (kernel rows are copied by TMA in 16-byte units) and
+// shared memory for two kernel rows; the top grid level's tiles take every
+// box as a source, in box order.  Returns false when it does not apply.
+static int64_t tc2_smem_bytes(int64_t O) {
+  const int64_t kbytes = ((O * 8 + 1023) / 1024) * 1024;
+  return 2 * kbytes + T2_STAGES * T2_BSTAGE + T2_QMAX * 4;
+}
+
+bool mac_top_tc2_fits(int C, int max_tile_targets, int64_t O, int64_t B, int64_t ntiles) {
+  return C == TC_C && max_tile_targets > 8 && max_tile_targets <= 128 && O > 0 && (O % 2) == 0 &&
+         tc2_smem_bytes(O) <= 220 * 1024 && ntiles * ((B + TC_KC - 1) / TC_KC) <= T2_QMAX && ntiles <= T2_TMAX;
+}
+
+bool launch_mac_top_tc2(const float2* Qh, float2* Rh, const float2* Kh, int64_t B, int C, int64_t O, int64_t nf,
+                        int64_t ntiles, int max_tile_targets, const int64_t* tgt_ptr, const int32_t* tgt,
+                        const int64_t* src_ptr, const int64_t* kidx_off, const int32_t* kidx, int* err,
+                        cudaStream_t s) {
+  if (!mac_top_tc2_fits(C, max_tile_targets, O, B, ntiles) || nf <= 0) return false;
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return false;
+  const int64_t kbytes = ((O * 8 + 1023) / 1024) * 1024;
+  const int64_t smem = tc2_smem_bytes(O);
+  static SmemAttr attr;
+  smem_attr_once(k_mac_top_tc2, (int)smem, attr.v);
+  const unsigned grid = (unsigned)std::min<int64_t>(nf, nsm);
+  k_mac_top_tc2<<<grid, T2_THREADS, (size_t)smem, s>>>(Qh, Rh, Kh, B, O, nf, ntiles, tgt_ptr, tgt, src_ptr, kidx_off,
+                                                        kidx, (int)kbytes, err);
   return true;
 }
 

@@ -591,8 +591,8 @@ void nn_backward_g(Net& net, const double2* gz, cudaStream_t s) {
     k_nn_du<<<(unsigned)grid_for(N * NW, 256), 256, 0, s>>>(net.dh, net.u[l], net.du, N * NW);
     // dh stays as the residual-path gradient and receives dX_h and the neighbour part
     const size_t smem = sizeof(__nv_bfloat16) * (NW * (TILE + 8) + 128 * (TILE + 8) + TILE * (NW + 8) + 128 * (NW + 8));
-    static std::atomic<uint64_t> attr{0};
-    smem_attr_once(k_nn_layer_back, (int)smem, attr);
+    static SmemAttr attr;
+    smem_attr_once(k_nn_layer_back, (int)smem, attr.v);
     k_nn_layer_back<<<nb_tile, 128, smem, s>>>(net.du, net.h[l], net.a[l], N, net.WcatT + l * NW * 128, net.part,
                                                net.dh, net.dXa);
     k_nn_reduce<<<(PART_W + 127) / 128, 128, 0, s>>>(net.part, nb_tile, PART_W, net.G + OFF_L0 + l * LAYER_SZ);

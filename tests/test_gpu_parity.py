@@ -214,11 +214,12 @@ def test_top_level_mixed_batched(G, two_level_oracle):
         assert _rel(Y[r], ref_op.matvec(X[r])) < TOL32
 
 
-@pytest.mark.parametrize("mac_variant", [0, 1, 2])
+@pytest.mark.parametrize("mac_variant", [0, 1, 2, 3])
 def test_top_level_translation_variants(G, two_level_oracle, mac_variant):
-    """The three top-level translation kernels the autotuner can pick (0: tensor
-    cores, 3-term TF32 split; 1: register tiles; 2: CUDA cores with
-    shared-memory staging) against the oracle, mixed form."""
+    """The four top-level translation kernels the autotuner can pick (0: tensor
+    cores, 3-term TF32 split, persistent warp-specialised; 1: register tiles;
+    2: CUDA cores with shared-memory staging; 3: tensor cores, one CTA per tile
+    and frequency) against the oracle, mixed form."""
     torch = _torch()
     V, T, ref_op = two_level_oracle
     _, _, k, p, delta, levels = TWO_LEVEL

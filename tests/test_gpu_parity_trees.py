@@ -122,11 +122,12 @@ def test_three_levels_two_doublings(G, two_doublings):
     _check(G, V, T, k, p, delta, levels, ref_op, 50, n_rhs=8, cols=(0, 7), tag="two doublings")
 
 
-@pytest.mark.parametrize("mac_variant", [0, 1, 2])
+@pytest.mark.parametrize("mac_variant", [0, 1, 2, 3])
 def test_two_doublings_translation_variants(G, two_doublings, mac_variant):
-    """The three top-level translation kernels the autotuner can pick (tensor
-    cores, register tiles, CUDA cores with shared-memory staging), mixed form,
-    8 vectors, against the oracle."""
+    """The four top-level translation kernels the autotuner can pick (tensor
+    cores persistent, register tiles, CUDA cores with shared-memory staging,
+    tensor cores per tile and frequency), mixed form, 8 vectors, against the
+    oracle."""
     torch = _torch()
     V, T, k, p, delta, levels, ref_op = two_doublings
     h = G.EFIE(V, T, k, p, delta, levels, precision=G.EFIE_MIXED)
