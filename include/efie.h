@@ -254,7 +254,8 @@ int efie_matvec(efie_handle *h, const void *x, void *y, int n_rhs, void *stream)
 
 /* y = T x with x and y in HOST memory (c128 [n_rhs][N]), the same product as
  * efie_matvec.  The right-hand sides go through the device in chunks of the
- * handle's chunk size, double-buffered: the copy-in of one chunk and the
+ * handle's chunk size (16 when two chunks of 8 share a top-level pass),
+ * double-buffered: the copy-in of one chunk and the
  * copy-out of the previous one overlap the product of the current one, on two
  * copy streams of the handle, ordered after the caller's earlier work on
  * `stream`.  The call returns once the work is queued; y is complete when

@@ -102,6 +102,11 @@ struct FarSet {
   int Rc = 0;
   std::vector<cpx_t<R>*> q, r;
   cpx_t<R>*tmp1 = nullptr, *tmp2 = nullptr, *Qh = nullptr, *Rh = nullptr;
+  // second chunk of a chunk pair (one top-level pass over 16 right-hand
+  // sides): its level grids r2[], and top-level spectra buffers for the first
+  // chunk's sources (Qt2) and the second chunk's results (Rt2)
+  std::vector<cpx_t<R>*> r2;
+  cpx_t<R>*Qt2 = nullptr, *Rt2 = nullptr;
 };
 
 struct LevDev {
@@ -457,6 +462,9 @@ void ensure_far_buffers(efie_handle* h, FarSet<R>& F, int Rc) {
 
 void ensure_work(efie_handle* h, int Rw) {
   if (h->Rw >= Rw) return;
+  for (void* p : {(void*)h->xs, (void*)h->yA, (void*)h->rho, (void*)h->w, (void*)h->xs4, (void*)h->rho4,
+                  (void*)h->xsf, (void*)h->rhof})
+    h->mem.release(p);
   const int64_t N = h->plan.g.N, Nt = h->plan.g.nt;
   h->xs = h->mem.alloc<double2>(N * Rw);
   h->yA = h->mem.alloc<double2>(N * Rw);
@@ -473,9 +481,40 @@ void ensure_work(efie_handle* h, int Rw) {
   h->Rw = Rw;
 }
 
+// buffers of the second chunk of a pair (FP32 far field, 8 right-hand sides)
+void ensure_pair_buffers(efie_handle* h, FarSet<float>& F) {
+  if (F.Qt2) return;
+  Plan& P = h->plan;
+  const int64_t C = 32;
+  F.r2.assign(P.lv.size(), nullptr);
+  for (int ell = P.D; ell >= P.top; --ell) {
+    const Level& L = P.L(ell);
+    const int64_t sp = L.sp;
+    F.r2[ell - P.top] = h->mem.alloc<float2>((int64_t)L.code.size() * sp * sp * sp * C);
+  }
+  const Level& T = P.L(P.top);
+  const int64_t n = T.nfft;
+  F.Qt2 = h->mem.alloc<float2>((int64_t)T.code.size() * n * n * n * C);
+  F.Rt2 = h->mem.alloc<float2>((int64_t)T.code.size() * n * n * n * C);
+}
+
 // ------------------------------------------------------------- far pipeline
+// The far pipeline of one chunk of nr <= 8 right-hand sides (work-vector
+// slots rhs0 .. rhs0 + nr - 1) is split in three phases so that two chunks can
+// share one top-level translation pass:
+//   far_up:   charges are in place; anterpolation, upward transfers, and on
+//             every level the stabilized forward transform, then (below the
+//             top grid level) translation and inverse transform into rr[];
+//             the top level's source spectra go to Qtop;
+//   run_mac:  the translation of one level (Qin -> Rout);
+//   far_down: top-level inverse transform from Rtop into rr[], downward
+//             transfers and interpolation.
 template <typename R>
-void far_chunk(efie_handle* h, FarSet<R>& F, int nr, cudaStream_t s) {
+void run_mac(efie_handle* h, FarSet<R>& F, int ell, int C, const cpx_t<R>* Qin, cpx_t<R>* Rout, cudaStream_t s);
+
+template <typename R>
+void far_up(efie_handle* h, FarSet<R>& F, int nr, int rhs0, std::vector<cpx_t<R>*>& rr, cpx_t<R>* Qtop,
+            cudaStream_t s) {
   Plan& P = h->plan;
   const int C = 4 * nr;
   const int D = P.D, top = P.top;
@@ -483,14 +522,14 @@ void far_chunk(efie_handle* h, FarSet<R>& F, int nr, cudaStream_t s) {
   // a2: anterpolation into the leaf grids
   {
     const Level& L = P.L(D);
-    const cpx_t<R>* xin = (const cpx_t<R>*)h->xs;
-    const cpx_t<R>* rin = (const cpx_t<R>*)h->rho;
+    const cpx_t<R>* xin = (const cpx_t<R>*)(h->xs + (int64_t)rhs0 * N);
+    const cpx_t<R>* rin = (const cpx_t<R>*)(h->rho + (int64_t)rhs0 * Nt);
     KScope ks(h, K_ANTERP, s, sizeof(R) == 4 ? 3 : 1);
     if (sizeof(R) == 4) {
-      launch_convert<R>(h->xs, (cpx_t<R>*)h->xsf, N * nr, s);
-      launch_convert<R>(h->rho, (cpx_t<R>*)h->rhof, Nt * nr, s);
-      xin = (const cpx_t<R>*)h->xsf;
-      rin = (const cpx_t<R>*)h->rhof;
+      launch_convert<R>(h->xs + (int64_t)rhs0 * N, (cpx_t<R>*)(h->xsf + (int64_t)rhs0 * N), N * nr, s);
+      launch_convert<R>(h->rho + (int64_t)rhs0 * Nt, (cpx_t<R>*)(h->rhof + (int64_t)rhs0 * Nt), Nt * nr, s);
+      xin = (const cpx_t<R>*)(h->xsf + (int64_t)rhs0 * N);
+      rin = (const cpx_t<R>*)(h->rhof + (int64_t)rhs0 * Nt);
     }
     launch_anterp<R>(F.gr, F.gt, h->gptr_r, h->gptr_t, h->mr_off, h->mt_off, h->d_box_rwg_ptr,
                      h->d_box_tri_ptr, (int64_t)L.code.size(), xin, N, rin, Nt, nr, F.q[D - top], L.sp, s);
@@ -524,7 +563,7 @@ void far_chunk(efie_handle* h, FarSet<R>& F, int nr, cudaStream_t s) {
     int sp = L.sp, n = L.nfft;
     int64_t n3 = (int64_t)n * n * n;
     if (LD.nfar == 0) {
-      cuda_check(cudaMemsetAsync(F.r[ell - top], 0, sizeof(cpx_t<R>) * B * sp * sp * sp * C, s), "memset r");
+      cuda_check(cudaMemsetAsync(rr[ell - top], 0, sizeof(cpx_t<R>) * B * sp * sp * sp * C, s), "memset r");
       continue;
     }
     View vq{(int64_t)sp * sp * sp * C, (int64_t)sp * sp * C, (int64_t)sp * C, C};
@@ -539,32 +578,13 @@ void far_chunk(efie_handle* h, FarSet<R>& F, int nr, cudaStream_t s) {
       if (!launch_dft<R>(F.tmp1, a1, F.tmp2, a2, B, C, 1, sp, n, n, sp, FL.Mf, n, false, s))
         launch_mode<R>(F.tmp1, a1, F.tmp2, a2, B, C, 1, sp, n, n, sp, FL.Mf, FL.Mf, true, nullptr, nullptr,
                        false, s);
-      if (!launch_dft<R>(F.tmp2, a2, F.Qh, vf, B, C, 2, sp, n, n, n, FL.Mf, n, false, s))
-        launch_mode<R>(F.tmp2, a2, F.Qh, vf, B, C, 2, sp, n, n, n, FL.Mf, FL.Mf, true, nullptr, nullptr, false,
+      cpx_t<R>* Qo = ell == top ? Qtop : F.Qh;
+      if (!launch_dft<R>(F.tmp2, a2, Qo, vf, B, C, 2, sp, n, n, n, FL.Mf, n, false, s))
+        launch_mode<R>(F.tmp2, a2, Qo, vf, B, C, 2, sp, n, n, n, FL.Mf, FL.Mf, true, nullptr, nullptr, false,
                        s);
     }
-    {
-      const bool tc2 = sizeof(R) == 4 && h->mac_variant == 0 && LD.src_all &&
-                       mac_top_tc2_fits(C, LD.max_tile, LD.O, B, LD.ntiles);
-      const bool tc = sizeof(R) == 4 && (h->mac_variant == 0 || h->mac_variant == 3) &&
-                      mac_top_tc_fits(C, LD.max_tile, LD.O);
-      KScope ks(h, tc || tc2 ? K_MAC_TOP_TC : ell == top ? K_MAC_TOP : K_MAC, s, 1);
-      bool done = false;
-      if (tc2)
-        done = launch_mac_top_tc2((const float2*)F.Qh, (float2*)F.Rh, (const float2*)FL.Kh, B, C, LD.O, n3,
-                                  LD.ntiles, LD.max_tile, LD.tile_tgt_ptr, LD.tile_tgt, LD.tile_src_ptr,
-                                  LD.tile_kidx_off, LD.tile_kidx, h->err_dev, s);
-      if (done) cuda_check(cudaPeekAtLastError(), "top-level translation (persistent tensor-core kernel)");
-      if (!done && tc)
-        done = launch_mac_top_tc((const float2*)F.Qh, (float2*)F.Rh, (const float2*)FL.Kh, B, C, LD.O, n3,
-                                 LD.ntiles, LD.max_tile, LD.tile_tgt_ptr, LD.tile_tgt, LD.tile_src_ptr, LD.tile_src,
-                                 LD.tile_kidx_off, LD.tile_kidx, h->err_dev, s);
-      if (done) cuda_check(cudaPeekAtLastError(), "top-level translation (tensor-core kernel)");
-      if (!done)
-        launch_mac<R>(F.Qh, F.Rh, FL.Kh, B, C, LD.O, n3, LD.ntiles,
-                      h->mac_variant == 1 ? -LD.max_tile : LD.max_tile, LD.tile_tgt_ptr, LD.tile_tgt,
-                      LD.tile_src_ptr, LD.tile_src, LD.tile_kidx_off, LD.tile_kidx, s);
-    }
+    if (ell == top) continue;   // the top level's translation and inverse come later
+    run_mac<R>(h, F, ell, C, F.Qh, F.Rh, s);
     KScope ks(h, K_INV, s, 3);
     View b1{(int64_t)sp * n * n * C, (int64_t)n * n * C, (int64_t)n * C, C};
     View b2{(int64_t)sp * sp * n * C, (int64_t)sp * n * C, (int64_t)n * C, C};
@@ -574,9 +594,80 @@ void far_chunk(efie_handle* h, FarSet<R>& F, int nr, cudaStream_t s) {
     if (!launch_dft<R>(F.tmp1, b1, F.tmp2, b2, B, C, 1, n, sp, sp, n, FL.Mb, n, true, s))
       launch_mode<R>(F.tmp1, b1, F.tmp2, b2, B, C, 1, n, sp, sp, n, FL.Mb, FL.Mb, true, nullptr, nullptr,
                      false, s);
-    if (!launch_dft<R>(F.tmp2, b2, F.r[ell - top], vq, B, C, 2, n, sp, sp, sp, FL.Mb, n, true, s))
-      launch_mode<R>(F.tmp2, b2, F.r[ell - top], vq, B, C, 2, n, sp, sp, sp, FL.Mb, FL.Mb, true, nullptr,
+    if (!launch_dft<R>(F.tmp2, b2, rr[ell - top], vq, B, C, 2, n, sp, sp, sp, FL.Mb, n, true, s))
+      launch_mode<R>(F.tmp2, b2, rr[ell - top], vq, B, C, 2, n, sp, sp, sp, FL.Mb, FL.Mb, true, nullptr,
                      nullptr, false, s);
+  }
+}
+
+template <typename R>
+void run_mac(efie_handle* h, FarSet<R>& F, int ell, int C, const cpx_t<R>* Qin, cpx_t<R>* Rout, cudaStream_t s) {
+  Plan& P = h->plan;
+  const int top = P.top;
+  const Level& L = P.L(ell);
+  const LevDev& LD = h->lev[ell - top];
+  auto& FL = F.lv[ell - top];
+  const int64_t B = (int64_t)L.code.size();
+  const int n = L.nfft;
+  const int64_t n3 = (int64_t)n * n * n;
+    {
+      const bool tc2 = sizeof(R) == 4 && h->mac_variant == 0 && LD.src_all &&
+                       mac_top_tc2_fits(C, LD.max_tile, LD.O, B, LD.ntiles, 1);
+      const bool tc = sizeof(R) == 4 && (h->mac_variant == 0 || h->mac_variant == 3) &&
+                      mac_top_tc_fits(C, LD.max_tile, LD.O);
+      KScope ks(h, tc || tc2 ? K_MAC_TOP_TC : ell == top ? K_MAC_TOP : K_MAC, s, 1);
+      bool done = false;
+      if (tc2)
+      {
+        const float2* qv[1] = {(const float2*)Qin};
+        float2* rv[1] = {(float2*)Rout};
+        done = launch_mac_top_tc2(qv, rv, 1, (const float2*)FL.Kh, B, C, LD.O, n3, LD.ntiles, LD.max_tile,
+                                  LD.tile_tgt_ptr, LD.tile_tgt, LD.tile_src_ptr, LD.tile_kidx_off, LD.tile_kidx,
+                                  h->err_dev, s);
+      }
+      if (done) cuda_check(cudaPeekAtLastError(), "top-level translation (persistent tensor-core kernel)");
+      if (!done && tc)
+        done = launch_mac_top_tc((const float2*)Qin, (float2*)Rout, (const float2*)FL.Kh, B, C, LD.O, n3,
+                                 LD.ntiles, LD.max_tile, LD.tile_tgt_ptr, LD.tile_tgt, LD.tile_src_ptr, LD.tile_src,
+                                 LD.tile_kidx_off, LD.tile_kidx, h->err_dev, s);
+      if (done) cuda_check(cudaPeekAtLastError(), "top-level translation (tensor-core kernel)");
+      if (!done)
+        launch_mac<R>(Qin, Rout, FL.Kh, B, C, LD.O, n3, LD.ntiles,
+                      h->mac_variant == 1 ? -LD.max_tile : LD.max_tile, LD.tile_tgt_ptr, LD.tile_tgt,
+                      LD.tile_src_ptr, LD.tile_src, LD.tile_kidx_off, LD.tile_kidx, s);
+    }
+}
+
+template <typename R>
+void far_down(efie_handle* h, FarSet<R>& F, int nr, int rhs0, std::vector<cpx_t<R>*>& rr, const cpx_t<R>* Rtop,
+              cudaStream_t s) {
+  Plan& P = h->plan;
+  const int C = 4 * nr;
+  const int D = P.D, top = P.top;
+  const int64_t N = P.g.N, Nt = P.g.nt;
+  {
+    const int ell = top;
+    const Level& L = P.L(ell);
+    const LevDev& LD = h->lev[ell - top];
+    auto& FL = F.lv[ell - top];
+    int64_t B = (int64_t)L.code.size();
+    int sp = L.sp, n = L.nfft;
+    if (LD.nfar > 0) {
+      View vq{(int64_t)sp * sp * sp * C, (int64_t)sp * sp * C, (int64_t)sp * C, C};
+      View vf{C, (int64_t)n * n * B * C, (int64_t)n * B * C, B * C};
+      KScope ks(h, K_INV, s, 3);
+      View b1{(int64_t)sp * n * n * C, (int64_t)n * n * C, (int64_t)n * C, C};
+      View b2{(int64_t)sp * sp * n * C, (int64_t)sp * n * C, (int64_t)n * C, C};
+      if (!launch_dft<R>(Rtop, vf, F.tmp1, b1, B, C, 0, n, sp, n, n, FL.Mb, n, true, s))
+        launch_mode<R>(Rtop, vf, F.tmp1, b1, B, C, 0, n, sp, n, n, FL.Mb, FL.Mb, true, nullptr, nullptr, false,
+                       s);
+      if (!launch_dft<R>(F.tmp1, b1, F.tmp2, b2, B, C, 1, n, sp, sp, n, FL.Mb, n, true, s))
+        launch_mode<R>(F.tmp1, b1, F.tmp2, b2, B, C, 1, n, sp, sp, n, FL.Mb, FL.Mb, true, nullptr, nullptr,
+                       false, s);
+      if (!launch_dft<R>(F.tmp2, b2, rr[ell - top], vq, B, C, 2, n, sp, sp, sp, FL.Mb, n, true, s))
+        launch_mode<R>(F.tmp2, b2, rr[ell - top], vq, B, C, 2, n, sp, sp, sp, FL.Mb, FL.Mb, true, nullptr,
+                       nullptr, false, s);
+    }
   }
   // a8: downward transfers r_c += C^T r_parent, shared among siblings one
   // axis at a time (x for (parent, b_x), y for (parent, b_x, b_y), z per child)
@@ -592,11 +683,11 @@ void far_chunk(efie_handle* h, FarSet<R>& F, int nr, cudaStream_t s) {
     View w1{(int64_t)sp * spp * spp * C, (int64_t)spp * spp * C, (int64_t)spp * C, C};
     View w2{(int64_t)sp * sp * spp * C, (int64_t)sp * spp * C, (int64_t)spp * C, C};
     View vq{(int64_t)sp * sp * sp * C, (int64_t)sp * sp * C, (int64_t)sp * C, C};
-    launch_mode<R>(F.r[ell - 1 - top], vp, F.tmp1, w1, LD.ng2, C, 0, spp, sp, spp, spp, FL.CLt, FL.CRt, false,
+    launch_mode<R>(rr[ell - 1 - top], vp, F.tmp1, w1, LD.ng2, C, 0, spp, sp, spp, spp, FL.CLt, FL.CRt, false,
                    LD.dx_sel, LD.dx_src, false, s);
     launch_mode<R>(F.tmp1, w1, F.tmp2, w2, LD.ng1, C, 1, spp, sp, sp, spp, FL.CLt, FL.CRt, false, LD.dy_sel,
                    LD.dy_src, false, s);
-    launch_mode<R>(F.tmp2, w2, F.r[ell - top], vq, B, C, 2, spp, sp, sp, sp, FL.CLt, FL.CRt, false, LD.bits,
+    launch_mode<R>(F.tmp2, w2, rr[ell - top], vq, B, C, 2, spp, sp, sp, sp, FL.CLt, FL.CRt, false, LD.bits,
                    LD.dz_src, true, s);
   }
   // a9: interpolation
@@ -604,25 +695,25 @@ void far_chunk(efie_handle* h, FarSet<R>& F, int nr, cudaStream_t s) {
     KScope ks(h, K_INTERP, s, 1);
     const Level& L = P.L(D);
     launch_interp<R>(F.mr, h->mr_base, h->mr_ext, h->mr_off, h->d_rwg_box, N, F.mt, h->mt_base, h->mt_ext,
-                     h->mt_off, h->d_tri_box, Nt, F.r[D - top], L.sp, nr, h->yA, N, h->w, Nt, s);
+                     h->mt_off, h->d_tri_box, Nt, rr[D - top], L.sp, nr, h->yA + (int64_t)rhs0 * N, N,
+                     h->w + (int64_t)rhs0 * Nt, Nt, s);
   }
 }
 
-// y = T x (or parts) for nr <= 8 right-hand sides; x, y canonical [nr][ldx]
+
 template <typename R>
-void matvec_chunk(efie_handle* h, FarSet<R>& F, const double2* x, int64_t ldx, int nr, double2* y,
-                  double2* yAo, double2* yVo, int64_t ldy, cudaStream_t s) {
+void far_chunk(efie_handle* h, FarSet<R>& F, int nr, cudaStream_t s) {
+  const int top = h->plan.top;
+  far_up<R>(h, F, nr, 0, F.r, F.Qh, s);
+  if (h->lev[0].nfar > 0) run_mac<R>(h, F, top, 4 * nr, F.Qh, F.Rh, s);
+  far_down<R>(h, F, nr, 0, F.r, F.Rh, s);
+}
+
+// a10 (near field, FP64 class) and the final combination for nr right-hand
+// sides whose far parts are in yA / w; y canonical [nr][ldy]
+void near_combine(efie_handle* h, int nr, double2* y, double2* yAo, double2* yVo, int64_t ldy, cudaStream_t s) {
   Plan& P = h->plan;
   const int64_t N = P.g.N, Nt = P.g.nt;
-  ensure_work(h, 8);
-  ensure_far_buffers(h, F, nr);
-  {
-    KScope ks(h, K_VEC, s, 2);
-    launch_permute_in(x, ldx, h->d_rwg_perm, N, nr, h->xs, s);
-    launch_charges(h->xs, N, h->d_tri_rwg, h->d_tri_sgn, Nt, nr, h->rho, Nt, s);  // a1
-  }
-  far_chunk<R>(h, F, nr, s);                                                       // a2-a9
-  // a10: near field, FP64
   int64_t BD = (int64_t)P.L(P.D).code.size();
   if (h->near_df) {
     {
@@ -656,6 +747,71 @@ void matvec_chunk(efie_handle* h, FarSet<R>& F, const double2* x, int64_t ldx, i
                  s);
 }
 
+
+// y = T x (or parts) for nr <= 8 right-hand sides; x, y canonical [nr][ldx]
+template <typename R>
+void matvec_chunk(efie_handle* h, FarSet<R>& F, const double2* x, int64_t ldx, int nr, double2* y,
+                  double2* yAo, double2* yVo, int64_t ldy, cudaStream_t s) {
+  Plan& P = h->plan;
+  const int64_t N = P.g.N, Nt = P.g.nt;
+  ensure_work(h, 8);
+  ensure_far_buffers(h, F, nr);
+  {
+    KScope ks(h, K_VEC, s, 2);
+    launch_permute_in(x, ldx, h->d_rwg_perm, N, nr, h->xs, s);
+    launch_charges(h->xs, N, h->d_tri_rwg, h->d_tri_sgn, Nt, nr, h->rho, Nt, s);  // a1
+  }
+  far_chunk<R>(h, F, nr, s);                                                       // a2-a9
+  near_combine(h, nr, y, yAo, yVo, ldy, s);
+}
+
+// Whether two full chunks (16 right-hand sides) can share one top-level pass:
+// FP32 far field, the automatic translation choice, and a top grid level that
+// the persistent tensor-core kernel takes with 128-row B operands.
+bool pair_fits(efie_handle* h) {
+  if (h->precision != EFIE_MIXED || h->mac_variant != 0) return false;
+  const Plan& P = h->plan;
+  const LevDev& LD = h->lev[0];
+  return LD.nfar > 0 && LD.src_all &&
+         mac_top_tc2_fits(32, LD.max_tile, LD.O, (int64_t)P.L(P.top).code.size(), LD.ntiles, 2);
+}
+
+// y = T x for 16 right-hand sides (two chunks of 8): each chunk's far
+// pipeline up to the top grid level, one top-level translation pass for both,
+// then each chunk's downward pipeline, and the near field for all 16.
+void matvec_pair(efie_handle* h, const double2* x, int64_t ldx, double2* y, double2* yAo, double2* yVo,
+                 int64_t ldy, cudaStream_t s) {
+  Plan& P = h->plan;
+  FarSet<float>& F = h->f32;
+  const int64_t N = P.g.N, Nt = P.g.nt;
+  ensure_work(h, 16);
+  ensure_far_buffers(h, F, 8);
+  ensure_pair_buffers(h, F);
+  {
+    KScope ks(h, K_VEC, s, 2);
+    launch_permute_in(x, ldx, h->d_rwg_perm, N, 16, h->xs, s);
+    launch_charges(h->xs, N, h->d_tri_rwg, h->d_tri_sgn, Nt, 16, h->rho, Nt, s);
+  }
+  far_up<float>(h, F, 8, 0, F.r, F.Qt2, s);
+  far_up<float>(h, F, 8, 8, F.r2, F.Qh, s);
+  {
+    const Level& L = P.L(P.top);
+    const LevDev& LD = h->lev[0];
+    const int64_t n = L.nfft;
+    KScope ks(h, K_MAC_TOP_TC, s, 1);
+    const float2* qv[2] = {F.Qt2, F.Qh};
+    float2* rv[2] = {F.Rh, F.Rt2};
+    if (!launch_mac_top_tc2(qv, rv, 2, F.lv[0].Kh, (int64_t)L.code.size(), 32, LD.O, n * n * n, LD.ntiles,
+                            LD.max_tile, LD.tile_tgt_ptr, LD.tile_tgt, LD.tile_src_ptr, LD.tile_kidx_off,
+                            LD.tile_kidx, h->err_dev, s))
+      throw EfieError{EFIE_ECUDA, "internal: chunk-pair translation does not apply"};
+    cuda_check(cudaPeekAtLastError(), "top-level translation (chunk pair)");
+  }
+  far_down<float>(h, F, 8, 0, F.r, F.Rh, s);
+  far_down<float>(h, F, 8, 8, F.r2, F.Rt2, s);
+  near_combine(h, 16, y, yAo, yVo, ldy, s);
+}
+
 void do_matvec(efie_handle* h, const double2* x, int64_t ldx, double2* y, double2* yA, double2* yV,
                int64_t ldy, int n_rhs, bool force64, cudaStream_t s) {
   // a device wait of an earlier product ran out (its outputs were set to NaN)
@@ -668,15 +824,23 @@ void do_matvec(efie_handle* h, const double2* x, int64_t ldx, double2* y, double
   int Rc = h->opt.rhs_chunk > 0 ? std::min(h->opt.rhs_chunk, 8) : 8;
   if (force64 && h->precision == EFIE_MIXED) Rc = 1;
   Rc = std::min(Rc, n_rhs);
-  for (int r0 = 0; r0 < n_rhs; r0 += Rc) {
-    int nr = std::min(Rc, n_rhs - r0);
+  // full chunk pairs share one top-level tensor-core pass
+  const bool pairs = Rc == 8 && !force64 && pair_fits(h);
+  for (int r0 = 0; r0 < n_rhs;) {
     double2* yy = y ? y + (int64_t)r0 * ldy : nullptr;
     double2* ya = yA ? yA + (int64_t)r0 * ldy : nullptr;
     double2* yv = yV ? yV + (int64_t)r0 * ldy : nullptr;
+    if (pairs && n_rhs - r0 >= 16) {
+      matvec_pair(h, x + (int64_t)r0 * ldx, ldx, yy, ya, yv, ldy, s);
+      r0 += 16;
+      continue;
+    }
+    int nr = std::min(Rc, n_rhs - r0);
+    r0 += nr;
     if (h->precision == EFIE_MIXED && !force64)
-      matvec_chunk<float>(h, h->f32, x + (int64_t)r0 * ldx, ldx, nr, yy, ya, yv, ldy, s);
+      matvec_chunk<float>(h, h->f32, x + (int64_t)(r0 - nr) * ldx, ldx, nr, yy, ya, yv, ldy, s);
     else
-      matvec_chunk<double>(h, h->f64, x + (int64_t)r0 * ldx, ldx, nr, yy, ya, yv, ldy, s);
+      matvec_chunk<double>(h, h->f64, x + (int64_t)(r0 - nr) * ldx, ldx, nr, yy, ya, yv, ldy, s);
   }
   cuda_check(cudaGetLastError(), "matvec launch");
 }
@@ -1692,7 +1856,9 @@ int efie_matvec_host(efie_handle* h, const void* x_host, void* y_host, int n_rhs
     if (n_rhs < 0 || ((!x_host || !y_host) && n_rhs > 0)) throw EfieError{EFIE_EINVAL, "bad arguments"};
     if (n_rhs == 0) return EFIE_OK;
     const int64_t N = h->plan.g.N;
-    const int Rc = h->opt.rhs_chunk > 0 ? std::min(h->opt.rhs_chunk, 8) : 8;
+    int Rc = h->opt.rhs_chunk > 0 ? std::min(h->opt.rhs_chunk, 8) : 8;
+    // a slot holds a chunk pair when the top-level pass takes two chunks
+    if (Rc == 8 && n_rhs >= 16 && pair_fits(h)) Rc = 16;
     HostPipe& hp = h->pipe;
     if (!hp.ready) {
       cuda_check(cudaStreamCreateWithFlags(&hp.s_in, cudaStreamNonBlocking), "host pipe stream");

@@ -105,12 +105,13 @@ bool launch_dft(const cpx_t<R>* in, View vin, cpx_t<R>* out, View vout, int64_t 
 // top grid level on the tensor cores (tcgen05, kind::tf32 with a 3-term split,
 // FP32-class products); false when the configuration does not fit it
 bool mac_top_tc_fits(int C, int max_tile_targets, int64_t O);
-// persistent warp-specialised form (tiles whose sources are all boxes in order)
-bool mac_top_tc2_fits(int C, int max_tile_targets, int64_t O, int64_t B, int64_t ntiles);
-bool launch_mac_top_tc2(const float2* Qh, float2* Rh, const float2* Kh, int64_t B, int C, int64_t O, int64_t nf,
-                        int64_t ntiles, int max_tile_targets, const int64_t* tgt_ptr, const int32_t* tgt,
-                        const int64_t* src_ptr, const int64_t* kidx_off, const int32_t* kidx, int* err,
-                        cudaStream_t s);
+// persistent warp-specialised form (tiles whose sources are all boxes in
+// order), on nch = 1 or 2 chunks of 8 right-hand sides per pass
+bool mac_top_tc2_fits(int C, int max_tile_targets, int64_t O, int64_t B, int64_t ntiles, int nch);
+bool launch_mac_top_tc2(const float2* const* Qh, float2* const* Rh, int nch, const float2* Kh, int64_t B, int C,
+                        int64_t O, int64_t nf, int64_t ntiles, int max_tile_targets, const int64_t* tgt_ptr,
+                        const int32_t* tgt, const int64_t* src_ptr, const int64_t* kidx_off, const int32_t* kidx,
+                        int* err, cudaStream_t s);
 bool launch_mac_top_tc(const float2* Qh, float2* Rh, const float2* Kh, int64_t B, int C, int64_t O, int64_t nf,
                        int64_t ntiles, int max_tile_targets, const int64_t* tgt_ptr, const int32_t* tgt,
                        const int64_t* src_ptr, const int32_t* src, const int64_t* kidx_off, const int32_t* kidx,

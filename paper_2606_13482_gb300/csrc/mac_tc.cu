@@ -359,19 +359,31 @@ __global__ void __launch_bounds__(128, 2)
 // Four chunk stages, two accumulator buffers, two kernel-row buffers; every
 // mbarrier wait is bounded and a timeout stops every role of the CTA.
 namespace {
-constexpr int T2_STAGES = 4;
 constexpr int T2_PROD = 256;                  // producer threads (2 warpgroups)
 constexpr int T2_MMA_WARP = T2_PROD / 32;     // warp 8
 constexpr int T2_EPI0 = T2_PROD + 32;         // first epilogue thread
 constexpr int T2_THREADS = T2_EPI0 + 128;     // 416 threads per CTA
 constexpr uint32_t T2_COLS = 512;
-constexpr uint32_t T2_DBUF = 128;             // one accumulator buffer: D1 (64) | D2 (64)
-constexpr uint32_t T2_A0 = 2 * T2_DBUF;       // A stages at 256 + 64 * stage
-constexpr int T2_BN = 64;                     // B rows: 32 channels real, then 32 imaginary
-constexpr int T2_BMAT = T2_BN * TC_KC * 4;    // 4 KB: one B matrix (hi or lo)
-constexpr int T2_BSTAGE = 2 * T2_BMAT;
+constexpr uint32_t T2_A0 = 256;               // A stages at 256 + 64 * stage
 constexpr int T2_QMAX = 1024;                 // chunks per frequency (chunk table in shared memory)
 constexpr int T2_PIECE = 16384;               // bytes per bulk copy of a kernel row
+// Per NCH (8-right-hand-side chunks per pass: 1 or 2):
+//   B rows: 32 NCH channels real, then 32 NCH imaginary (N = 64 NCH)
+//   accumulator buffer: D1 = K_r B (64 NCH columns) | D2 = K_i B; two buffers
+//   for NCH = 1, one for NCH = 2 (256 columns)
+//   chunk stages: 4 for NCH = 1, 3 for NCH = 2 (shared memory)
+template <int NCH>
+struct T2Cfg {
+  static constexpr int BN = 64 * NCH;
+  static constexpr int BMAT = BN * TC_KC * 4;
+  static constexpr int BSTAGE = 2 * BMAT;
+  static constexpr int STG = NCH == 1 ? 4 : 3;
+  static constexpr int DB = NCH == 1 ? 2 : 1;
+  static constexpr uint32_t DBUF = 128u * NCH;
+  static constexpr uint32_t IDESC =
+      (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) | ((128u >> 4) << 24);
+};
+constexpr int T2_STAGES = 4;                  // largest stage count (barrier arrays)
 
 constexpr int T2_TMAX = 64;                   // tiles of the level
 struct T2Tile {
@@ -423,13 +435,14 @@ __device__ __forceinline__ uint64_t smem_desc_sbo(uint32_t saddr, uint32_t sbo) 
   d |= (uint64_t)1 << 46;
   return d;
 }
-// kind::tf32, FP32 accumulate, K-major A and B, M = 128, N = 64
-constexpr uint32_t T2_IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(T2_BN >> 3) << 17) | ((128u >> 4) << 24);
 }  // namespace
 
-// dynamic shared memory: [2 kernel rows of kbytes][4 B stages][chunk table]
+// dynamic shared memory: [2 kernel rows of kbytes][STG B stages][chunk table].
+// Chunk c < NCH of the pass has its spectra at Qh[c] and writes Rh[c].
+template <int NCH>
 __global__ void __maxnreg__(128)
-    k_mac_top_tc2(const float2* __restrict__ Qh, float2* __restrict__ Rh, const float2* __restrict__ Kh, int64_t B,
+    k_mac_top_tc2(const float2* __restrict__ Qh0, const float2* __restrict__ Qh1, float2* __restrict__ Rh0,
+                  float2* __restrict__ Rh1, const float2* __restrict__ Kh, int64_t B,
                   int64_t O, int64_t nf, int64_t ntiles, const int64_t* __restrict__ tgt_ptr,
                   const int32_t* __restrict__ tgt, const int64_t* __restrict__ src_ptr,
                   const int64_t* __restrict__ kidx_off, const int32_t* __restrict__ kidx, int kbytes, int* err) {
@@ -437,12 +450,13 @@ __global__ void __maxnreg__(128)
   __shared__ T2Bar bar;
   unsigned char* rows = t2_smem;
   unsigned char* Bs = t2_smem + 2 * kbytes;
-  int32_t* ctab = reinterpret_cast<int32_t*>(Bs + T2_STAGES * T2_BSTAGE);
+  using Cfg = T2Cfg<NCH>;
+  int32_t* ctab = reinterpret_cast<int32_t*>(Bs + Cfg::STG * Cfg::BSTAGE);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t K = nf > blockIdx.x ? (nf - 1 - blockIdx.x) / gridDim.x + 1 : 0;   // frequencies of this CTA
 
   if (tid == 0) {
-    for (int i = 0; i < T2_STAGES; ++i) {
+    for (int i = 0; i < Cfg::STG; ++i) {
       mbar_init(&bar.full[i], 128);
       mbar_init(&bar.empty[i], 1);
     }
@@ -484,17 +498,19 @@ __global__ void __maxnreg__(128)
     const int wg = tid >> 7, r = tid & 127;
     const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
     // B operands: this thread stores source jB of the chunk, channels chB + 8u
+    // of pass chunk u / 4: row u * 8 + chB (real) and 32 NCH + u * 8 + chB
+    // (imaginary), i.e. core group u and 4 NCH + u
     const int jB = (warp & 3) * 4 + (lane >> 3), chB = lane & 7;
-    const int boff = (jB >> 2) * TC_LBO + (jB & 3) * 4 + chB * 16;   // + u SBO (real), + (4 + u) SBO (imaginary)
+    const int boff = (jB >> 2) * TC_LBO + (jB & 3) * 4 + chB * 16;
     const int nq32 = (int)nq;
     int32_t idn[TC_KC];
-    float2 qn[4];
+    float2 qn[4 * NCH];
     // loads of chunk (k, q): the index rows of this thread's target, the source spectra
     auto load = [&](int64_t k, int q) {
 #pragma unroll
       for (int j = 0; j < TC_KC; ++j) idn[j] = -1;
 #pragma unroll
-      for (int u = 0; u < 4; ++u) qn[u] = make_float2(0.f, 0.f);
+      for (int u = 0; u < 4 * NCH; ++u) qn[u] = make_float2(0.f, 0.f);
       if (k >= K) return;
       const int32_t e = ctab[q];
       const T2Tile& T = bar.tile[e >> 16];
@@ -507,9 +523,13 @@ __global__ void __maxnreg__(128)
       }
       // the top grid level translates every box: source j is box j
       if (j0 + jB < T.ns) {
-        const float2* Qp = Qh + ((int64_t)(blockIdx.x + k * gridDim.x) * B + j0 + jB) * TC_C + chB;
+        const int64_t o = ((int64_t)(blockIdx.x + k * gridDim.x) * B + j0 + jB) * TC_C + chB;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) qn[u] = __ldg(Qp + 8 * u);
+        for (int u = 0; u < 4; ++u) qn[u] = __ldg(Qh0 + o + 8 * u);
+        if (NCH == 2) {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) qn[4 + u] = __ldg(Qh1 + o + 8 * u);
+        }
       }
     };
     // this warpgroup's chunks g = wg, wg + 2, ... as (frequency k, chunk q)
@@ -529,20 +549,21 @@ __global__ void __maxnreg__(128)
       const float2* Ks = reinterpret_cast<const float2*>(rows + rb * kbytes);
       for (; g < (k + 1) * nq; g += 2) {
         int32_t idc[TC_KC];
-        float2 qc[4];
+        float2 qc[4 * NCH];
 #pragma unroll
         for (int j = 0; j < TC_KC; ++j) idc[j] = idn[j];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) qc[u] = qn[u];
+        for (int u = 0; u < 4 * NCH; ++u) qc[u] = qn[u];
         qn_ += 2;
         while (qn_ >= nq32) {
           qn_ -= nq32;
           ++kn;
         }
         load(kn, qn_);
-        const int slot = (int)(g & (T2_STAGES - 1));
-        if (g >= T2_STAGES) {
-          ok = t2_wait(&bar.empty[slot], (uint32_t)(((g >> 2) - 1) & 1), &bar, err);
+        const uint32_t gu = (uint32_t)g;
+        const int slot = (int)(gu % Cfg::STG);
+        if (gu >= (uint32_t)Cfg::STG) {
+          ok = t2_wait(&bar.empty[slot], ((gu / Cfg::STG) - 1) & 1, &bar, err);
           if (!ok) break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
@@ -566,14 +587,14 @@ __global__ void __maxnreg__(128)
           }
         }
         {
-          float* bb = reinterpret_cast<float*>(Bs + slot * T2_BSTAGE + boff);
+          float* bb = reinterpret_cast<float*>(Bs + slot * Cfg::BSTAGE + boff);
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
+          for (int u = 0; u < 4 * NCH; ++u) {
             const float rh = tf32_hi(qc[u].x), ih = tf32_hi(qc[u].y);
             bb[(u * TC_SBO) / 4] = rh;
-            bb[((4 + u) * TC_SBO) / 4] = ih;
-            bb[(T2_BMAT + u * TC_SBO) / 4] = qc[u].x - rh;
-            bb[(T2_BMAT + (4 + u) * TC_SBO) / 4] = qc[u].y - ih;
+            bb[((4 * NCH + u) * TC_SBO) / 4] = ih;
+            bb[(Cfg::BMAT + u * TC_SBO) / 4] = qc[u].x - rh;
+            bb[(Cfg::BMAT + (4 * NCH + u) * TC_SBO) / 4] = qc[u].y - ih;
           }
         }
         asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
@@ -615,34 +636,36 @@ __global__ void __maxnreg__(128)
           load_row(k + 1);
         }
         for (int64_t t = 0; t < ntiles && ok; ++t, ++ts) {
-          const int db = (int)(ts & 1);
-          if (ts >= 2) {
-            ok = t2_wait(&bar.dempty[db], (uint32_t)(((ts >> 1) - 1) & 1), &bar, err);
+          const uint32_t tsu = (uint32_t)ts;
+          const int db = (int)(tsu % Cfg::DB);
+          if (tsu >= (uint32_t)Cfg::DB) {
+            ok = t2_wait(&bar.dempty[db], ((tsu / Cfg::DB) - 1) & 1, &bar, err);
             if (!ok) break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
           const int64_t nch = (bar.tile[t].ns + TC_KC - 1) / TC_KC;
-          const uint32_t d1 = tm + (uint32_t)db * T2_DBUF, d2 = d1 + 64;
+          const uint32_t d1 = tm + (uint32_t)db * Cfg::DBUF, d2 = d1 + 64 * NCH;
           for (int64_t c = 0; c < nch; ++c, ++g) {
-            const int slot = (int)(g & (T2_STAGES - 1));
-            ok = t2_wait(&bar.full[slot], (uint32_t)((g >> 2) & 1), &bar, err);
+            const uint32_t gu = (uint32_t)g;
+            const int slot = (int)(gu % Cfg::STG);
+            ok = t2_wait(&bar.full[slot], (gu / Cfg::STG) & 1, &bar, err);
             if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
             const uint32_t a0 = tm + T2_A0 + (uint32_t)slot * 4 * TC_KC;
-            const uint32_t bs = smem_u32(Bs + slot * T2_BSTAGE);
+            const uint32_t bs = smem_u32(Bs + slot * Cfg::BSTAGE);
 #pragma unroll
             for (int kk = 0; kk < TC_KC / 8; ++kk) {
               const uint32_t arh = a0 + 0 * TC_KC + kk * 8, arl = a0 + 1 * TC_KC + kk * 8;
               const uint32_t aih = a0 + 2 * TC_KC + kk * 8, ail = a0 + 3 * TC_KC + kk * 8;
               const uint32_t ko = (uint32_t)kk * 2 * TC_LBO;
-              const uint64_t bh = smem_desc_sbo(bs + ko, TC_SBO), bl = smem_desc_sbo(bs + T2_BMAT + ko, TC_SBO);
+              const uint64_t bh = smem_desc_sbo(bs + ko, TC_SBO), bl = smem_desc_sbo(bs + Cfg::BMAT + ko, TC_SBO);
               const uint32_t acc0 = (c > 0 || kk > 0) ? 1u : 0u;
-              mma_tf32(d1, arh, bh, T2_IDESC, acc0);
-              mma_tf32(d1, arh, bl, T2_IDESC, 1u);
-              mma_tf32(d1, arl, bh, T2_IDESC, 1u);
-              mma_tf32(d2, aih, bh, T2_IDESC, acc0);
-              mma_tf32(d2, aih, bl, T2_IDESC, 1u);
-              mma_tf32(d2, ail, bh, T2_IDESC, 1u);
+              mma_tf32(d1, arh, bh, Cfg::IDESC, acc0);
+              mma_tf32(d1, arh, bl, Cfg::IDESC, 1u);
+              mma_tf32(d1, arl, bh, Cfg::IDESC, 1u);
+              mma_tf32(d2, aih, bh, Cfg::IDESC, acc0);
+              mma_tf32(d2, aih, bl, Cfg::IDESC, 1u);
+              mma_tf32(d2, ail, bh, Cfg::IDESC, 1u);
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
                              smem_u32(&bar.empty[slot]))
@@ -655,7 +678,8 @@ __global__ void __maxnreg__(128)
         }
       }
       // the last commits cover every MMA of this thread
-      if (ok && TS > 0) t2_wait(&bar.dfull[(TS - 1) & 1], (uint32_t)(((TS - 1) >> 1) & 1), &bar, err);
+      if (ok && TS > 0)
+        t2_wait(&bar.dfull[(uint32_t)(TS - 1) % Cfg::DB], ((uint32_t)(TS - 1) / Cfg::DB) & 1, &bar, err);
     }
     __syncwarp();
   } else {
@@ -667,36 +691,39 @@ __global__ void __maxnreg__(128)
     for (int64_t k = 0; k < K && ok; ++k) {
       const int64_t f = blockIdx.x + k * gridDim.x;
       for (int64_t t = 0; t < ntiles; ++t, ++ts) {
-        const int db = (int)(ts & 1);
-        ok = t2_wait(&bar.dfull[db], (uint32_t)((ts >> 1) & 1), &bar, err);
+        const uint32_t tsu = (uint32_t)ts;
+        const int db = (int)(tsu % Cfg::DB);
+        ok = t2_wait(&bar.dfull[db], (tsu / Cfg::DB) & 1, &bar, err);
         if (!ok) break;
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-        const uint32_t d1 = tm + lane_base + (uint32_t)db * T2_DBUF, d2 = d1 + 64;
+        const uint32_t d1 = tm + lane_base + (uint32_t)db * Cfg::DBUF, d2 = d1 + 64 * NCH;
         const int64_t t0 = bar.tile[t].t0, nt = bar.tile[t].nt;
         const bool any = bar.tile[t].ns > 0;
-        float2* out = r < nt ? Rh + f * B * TC_C + (int64_t)tgt[t0 + r] * TC_C : nullptr;
+        const int64_t ro = r < nt ? (f * B + tgt[t0 + r]) * TC_C : -1;
 #pragma unroll
-        for (int h = 0; h < TC_C; h += 16) {
+        for (int h = 0; h < TC_C * NCH; h += 16) {
+          // channels h .. h + 15 of the pass: chunk h / 32, its channels h % 32 + n
           float re[16], im[16], p[16];
-          tmem_ld16(d1 + h, re);         // K_r Q_r
-          tmem_ld16(d2 + 32 + h, p);     // K_i Q_i
+          tmem_ld16(d1 + h, re);                 // K_r Q_r
+          tmem_ld16(d2 + 32 * NCH + h, p);       // K_i Q_i
           asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
           for (int n = 0; n < 16; ++n) re[n] -= p[n];
-          tmem_ld16(d1 + 32 + h, im);    // K_r Q_i
-          tmem_ld16(d2 + h, p);          // K_i Q_r
+          tmem_ld16(d1 + 32 * NCH + h, im);      // K_r Q_i
+          tmem_ld16(d2 + h, p);                  // K_i Q_r
           asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
           for (int n = 0; n < 16; ++n) im[n] += p[n];
-          if (h + 16 == TC_C) {
+          if (h + 16 == TC_C * NCH) {
             // the accumulators of this buffer are read: the MMA warp may reuse it
             asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
             mbar_arrive(&bar.dempty[db]);
           }
-          if (out) {
+          if (ro >= 0) {
+            float2* out = (h < TC_C ? Rh0 : Rh1) + ro + (h % TC_C);
 #pragma unroll
             for (int n = 0; n < 16; n += 2)
-              *reinterpret_cast<float4*>(out + h + n) =
+              *reinterpret_cast<float4*>(out + n) =
                   any ? make_float4(re[n], im[n], re[n + 1], im[n + 1]) : make_float4(0.f, 0.f, 0.f, 0.f);
           }
         }
@@ -745,31 +772,41 @@ bool launch_mac_top_tc(const float2* Qh, float2* Rh, const float2* Kh, int64_t B
 // number of offsets (kernel rows are copied by TMA in 16-byte units) and
 // shared memory for two kernel rows; the top grid level's tiles take every
 // box as a source, in box order.  Returns false when it does not apply.
-static int64_t tc2_smem_bytes(int64_t O) {
+static int64_t tc2_smem_bytes(int64_t O, int nch) {
   const int64_t kbytes = ((O * 8 + 1023) / 1024) * 1024;
-  return 2 * kbytes + T2_STAGES * T2_BSTAGE + T2_QMAX * 4;
+  return 2 * kbytes + (nch == 1 ? 4 * T2Cfg<1>::BSTAGE : 3 * T2Cfg<2>::BSTAGE) + T2_QMAX * 4;
 }
 
-bool mac_top_tc2_fits(int C, int max_tile_targets, int64_t O, int64_t B, int64_t ntiles) {
-  return C == TC_C && max_tile_targets > 8 && max_tile_targets <= 128 && O > 0 && (O % 2) == 0 &&
-         tc2_smem_bytes(O) <= 220 * 1024 && ntiles * ((B + TC_KC - 1) / TC_KC) <= T2_QMAX && ntiles <= T2_TMAX;
+bool mac_top_tc2_fits(int C, int max_tile_targets, int64_t O, int64_t B, int64_t ntiles, int nch) {
+  return C == TC_C && (nch == 1 || nch == 2) && max_tile_targets > 8 && max_tile_targets <= 128 && O > 0 &&
+         (O % 2) == 0 && tc2_smem_bytes(O, nch) <= 220 * 1024 && ntiles * ((B + TC_KC - 1) / TC_KC) <= T2_QMAX &&
+         ntiles <= T2_TMAX;
 }
 
-bool launch_mac_top_tc2(const float2* Qh, float2* Rh, const float2* Kh, int64_t B, int C, int64_t O, int64_t nf,
-                        int64_t ntiles, int max_tile_targets, const int64_t* tgt_ptr, const int32_t* tgt,
-                        const int64_t* src_ptr, const int64_t* kidx_off, const int32_t* kidx, int* err,
-                        cudaStream_t s) {
-  if (!mac_top_tc2_fits(C, max_tile_targets, O, B, ntiles) || nf <= 0) return false;
+// nch = 2: two 8-right-hand-side chunks in one pass (Qh[1], Rh[1] used),
+// B operands of 128 rows and N = 128 MMAs.
+bool launch_mac_top_tc2(const float2* const* Qh, float2* const* Rh, int nch, const float2* Kh, int64_t B, int C,
+                        int64_t O, int64_t nf, int64_t ntiles, int max_tile_targets, const int64_t* tgt_ptr,
+                        const int32_t* tgt, const int64_t* src_ptr, const int64_t* kidx_off, const int32_t* kidx,
+                        int* err, cudaStream_t s) {
+  if (!mac_top_tc2_fits(C, max_tile_targets, O, B, ntiles, nch) || nf <= 0) return false;
   int dev = 0, nsm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return false;
   const int64_t kbytes = ((O * 8 + 1023) / 1024) * 1024;
-  const int64_t smem = tc2_smem_bytes(O);
-  static SmemAttr attr;
-  smem_attr_once(k_mac_top_tc2, (int)smem, attr.v);
+  const int64_t smem = tc2_smem_bytes(O, nch);
   const unsigned grid = (unsigned)std::min<int64_t>(nf, nsm);
-  k_mac_top_tc2<<<grid, T2_THREADS, (size_t)smem, s>>>(Qh, Rh, Kh, B, O, nf, ntiles, tgt_ptr, tgt, src_ptr, kidx_off,
-                                                        kidx, (int)kbytes, err);
+  if (nch == 1) {
+    static SmemAttr attr;
+    smem_attr_once(k_mac_top_tc2<1>, (int)smem, attr.v);
+    k_mac_top_tc2<1><<<grid, T2_THREADS, (size_t)smem, s>>>(Qh[0], nullptr, Rh[0], nullptr, Kh, B, O, nf, ntiles,
+                                                            tgt_ptr, tgt, src_ptr, kidx_off, kidx, (int)kbytes, err);
+  } else {
+    static SmemAttr attr;
+    smem_attr_once(k_mac_top_tc2<2>, (int)smem, attr.v);
+    k_mac_top_tc2<2><<<grid, T2_THREADS, (size_t)smem, s>>>(Qh[0], Qh[1], Rh[0], Rh[1], Kh, B, O, nf, ntiles,
+                                                            tgt_ptr, tgt, src_ptr, kidx_off, kidx, (int)kbytes, err);
+  }
   return true;
 }
 

@@ -140,3 +140,26 @@ def test_two_doublings_translation_variants(G, two_doublings, mac_variant):
     for r in (0, 5):
         rel, mx = _errs(Y[r], ref_op.matvec(X[r]))
         assert rel < TOL32 and mx < 10 * TOL32, (mac_variant, r, rel, mx)
+
+
+def test_two_doublings_chunk_pairs(G, two_doublings):
+    """19 vectors in the mixed form: the first 16 go through one top-level
+    tensor-core pass for two chunks of 8 (128-row B operands, N = 128 MMAs),
+    the last 3 through the single-chunk path; both against the oracle, and
+    against the CUDA-core translation (variant 2, one chunk at a time)."""
+    torch = _torch()
+    V, T, k, p, delta, levels, ref_op = two_doublings
+    X = E.complex_gaussian((19, ref_op.mesh.N), 70)
+    Xd = torch.from_numpy(X).cuda()
+    h = G.EFIE(V, T, k, p, delta, levels, precision=G.EFIE_MIXED)
+    try:
+        Y = h.matvec(Xd).cpu().numpy()
+        h.autotune_set(8, 2)
+        Y2 = h.matvec(Xd).cpu().numpy()
+    finally:
+        h.close()
+    for r in (0, 7, 8, 15, 16, 18):
+        rel, mx = _errs(Y[r], ref_op.matvec(X[r]))
+        print(f"chunk pair rhs {r}: rel l2 {rel:.3e}, max-abs {mx:.3e}")
+        assert rel < TOL32 and mx < 10 * TOL32, (r, rel, mx)
+    assert np.linalg.norm(Y - Y2) < 1e-5 * np.linalg.norm(Y2)
