@@ -102,10 +102,10 @@ struct FarSet {
   int Rc = 0;
   std::vector<cpx_t<R>*> q, r;
   cpx_t<R>*tmp1 = nullptr, *tmp2 = nullptr, *Qh = nullptr, *Rh = nullptr;
-  // second chunk of a chunk pair (one top-level pass over 16 right-hand
-  // sides): its level grids r2[], and top-level spectra buffers for the first
-  // chunk's sources (Qt2) and the second chunk's results (Rt2)
-  std::vector<cpx_t<R>*> r2;
+  // second chunk of a chunk pair (one translation pass per level over 16
+  // right-hand sides): its level grids q2[], r2[], and spectra buffers for its
+  // sources (Qt2) and results (Rt2)
+  std::vector<cpx_t<R>*> q2, r2;
   cpx_t<R>*Qt2 = nullptr, *Rt2 = nullptr;
 };
 
@@ -122,7 +122,12 @@ struct LevDev {
   // translation tiles
   int64_t ntiles = 0;
   int max_tile = 0;
-  bool src_all = false;  // every tile's sources are all boxes of the level, in order
+  int64_t nq = 0;        // chunks of 16 sources summed over the tiles
+  // tensor-core tiles of an interaction-list level (128 targets, union sources)
+  int64_t tct_ntiles = 0, tct_nq = 0;
+  int tct_max = 0;
+  int64_t *tct_tgt_ptr = nullptr, *tct_src_ptr = nullptr, *tct_kidx_off = nullptr;
+  int32_t *tct_tgt = nullptr, *tct_src = nullptr, *tct_kidx = nullptr;
   int64_t *tile_tgt_ptr = nullptr, *tile_src_ptr = nullptr, *tile_kidx_off = nullptr;
   int32_t *tile_tgt = nullptr, *tile_src = nullptr, *tile_kidx = nullptr;
   // sibling-shared transfers between this (child) level and its parents:
@@ -144,11 +149,12 @@ namespace {
 // kernel classes for the profiling facility
 enum KClass {
   K_VEC = 0, K_ANTERP, K_UP, K_FWD, K_MAC, K_INV, K_DOWN, K_INTERP, K_NEAR_A, K_NEAR_V, K_KRYLOV, K_MAC_TOP,
-  K_PRECOND, K_MAC_TOP_TC, K_NCLASS
+  K_PRECOND, K_MAC_TOP_TC, K_MAC_TC, K_NCLASS
 };
 const char* kclass_name[K_NCLASS] = {"vector",   "anterpolation", "upward",  "forward_fft", "translation_mac",
                                      "inverse_fft", "downward",   "interpolation", "near_A", "near_V", "krylov",
-                                     "translation_mac_top", "precond", "translation_mac_top_tc"};
+                                     "translation_mac_top", "precond", "translation_mac_top_tc",
+                                     "translation_mac_tc"};
 struct Prof {
   bool on = false;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev;
@@ -199,6 +205,11 @@ struct efie_handle {
   ~efie_handle() {
     if (net) efie::nn_delete(net);
     if (err_host) cudaFreeHost(err_host);
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_join) cudaEventDestroy(ev_join);
+    if (ev_far) cudaEventDestroy(ev_far);
+    if (s_near) cudaStreamDestroy(s_near);
+    if (s_far) cudaStreamDestroy(s_far);
   }
   int64_t n_launches = 0;
   double setup_s[4] = {0, 0, 0, 0};  // efie_setup phases (efie_setup_times)
@@ -232,14 +243,22 @@ struct efie_handle {
   FarSet<double> f64;
   FarSet<float> f32;
   int mac_variant = 0;   // translation (autotuner knob): 0 auto (tensor cores on the top level, persistent
-                         // form, else 3, else 2), 1 register tiles, 2 CUDA-core shared-memory staged,
-                         // 3 tensor cores with one CTA per (tile, frequency)
+                         // form, else 3, else 2; chunk pairs also take the interaction-list levels on
+                         // tensor cores), 1 register tiles, 2 CUDA-core shared-memory staged, 3 tensor
+                         // cores with one CTA per (tile, frequency), 4 as 0 but chunk pairs keep the
+                         // interaction-list levels on CUDA cores
   int* err_host = nullptr;  // host-mapped flag that device waits set when they run out
   int* err_dev = nullptr;
   int near_variant = 0;  // mixed near field: 0 shared-memory staged x, 1 x through L1 (autotuner knob)
   // work vectors (FP64, sorted) and their double-float splits
   int Rw = 0;
   double2 *xs = nullptr, *rho = nullptr, *yA = nullptr, *w = nullptr;
+  // near field on a second stream, overlapping the far field: its own outputs
+  // (added in the final combination), fork / join events
+  double2 *yAn = nullptr, *wn = nullptr;
+  cudaStream_t s_near = nullptr;
+  cudaStream_t s_far = nullptr;   // far field, highest priority, so its kernels go first
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_far = nullptr;
   float4 *xs4 = nullptr, *rho4 = nullptr;
   float2 *xsf = nullptr, *rhof = nullptr;   // FP32 copies for the far field
   bool near_df = false;   // near matrices stored as double-float pairs
@@ -463,13 +482,15 @@ void ensure_far_buffers(efie_handle* h, FarSet<R>& F, int Rc) {
 void ensure_work(efie_handle* h, int Rw) {
   if (h->Rw >= Rw) return;
   for (void* p : {(void*)h->xs, (void*)h->yA, (void*)h->rho, (void*)h->w, (void*)h->xs4, (void*)h->rho4,
-                  (void*)h->xsf, (void*)h->rhof})
+                  (void*)h->xsf, (void*)h->rhof, (void*)h->yAn, (void*)h->wn})
     h->mem.release(p);
   const int64_t N = h->plan.g.N, Nt = h->plan.g.nt;
   h->xs = h->mem.alloc<double2>(N * Rw);
   h->yA = h->mem.alloc<double2>(N * Rw);
   h->rho = h->mem.alloc<double2>(Nt * Rw);
   h->w = h->mem.alloc<double2>(Nt * Rw);
+  h->yAn = h->mem.alloc<double2>(N * Rw);
+  h->wn = h->mem.alloc<double2>(Nt * Rw);
   if (h->near_df) {
     h->xs4 = h->mem.alloc<float4>(N * Rw);
     h->rho4 = h->mem.alloc<float4>(Nt * Rw);
@@ -481,40 +502,47 @@ void ensure_work(efie_handle* h, int Rw) {
   h->Rw = Rw;
 }
 
-// buffers of the second chunk of a pair (FP32 far field, 8 right-hand sides)
+// buffers of the second chunk of a pair (FP32 far field, 8 right-hand sides):
+// its level grids q2[], r2[], and spectra buffers of the size of the largest
+// level (Qt2 for its sources, Rt2 for its results)
 void ensure_pair_buffers(efie_handle* h, FarSet<float>& F) {
   if (F.Qt2) return;
   Plan& P = h->plan;
   const int64_t C = 32;
+  F.q2.assign(P.lv.size(), nullptr);
   F.r2.assign(P.lv.size(), nullptr);
   for (int ell = P.D; ell >= P.top; --ell) {
     const Level& L = P.L(ell);
     const int64_t sp = L.sp;
+    F.q2[ell - P.top] = h->mem.alloc<float2>((int64_t)L.code.size() * sp * sp * sp * C);
     F.r2[ell - P.top] = h->mem.alloc<float2>((int64_t)L.code.size() * sp * sp * sp * C);
   }
-  const Level& T = P.L(P.top);
-  const int64_t n = T.nfft;
-  F.Qt2 = h->mem.alloc<float2>((int64_t)T.code.size() * n * n * n * C);
-  F.Rt2 = h->mem.alloc<float2>((int64_t)T.code.size() * n * n * n * C);
+  int64_t smax = 1;
+  for (int ell = P.D; ell >= P.top; --ell) {
+    const Level& L = P.L(ell);
+    const int64_t n = L.nfft;
+    smax = std::max(smax, (int64_t)L.code.size() * n * n * n * C);
+  }
+  F.Qt2 = h->mem.alloc<float2>(smax);
+  F.Rt2 = h->mem.alloc<float2>(smax);
 }
 
 // ------------------------------------------------------------- far pipeline
 // The far pipeline of one chunk of nr <= 8 right-hand sides (work-vector
-// slots rhs0 .. rhs0 + nr - 1) is split in three phases so that two chunks can
-// share one top-level translation pass:
-//   far_up:   charges are in place; anterpolation, upward transfers, and on
-//             every level the stabilized forward transform, then (below the
-//             top grid level) translation and inverse transform into rr[];
-//             the top level's source spectra go to Qtop;
-//   run_mac:  the translation of one level (Qin -> Rout);
-//   far_down: top-level inverse transform from Rtop into rr[], downward
-//             transfers and interpolation.
+// slots rhs0 .. rhs0 + nr - 1) in pieces, so that two chunks can share the
+// translation pass of every level:
+//   anterp_up:   anterpolation into the leaf grids and upward transfers (qq[]);
+//   fwd_level:   stabilized forward transform of one level (grids -> spectra);
+//   run_mac:     translation of one level (spectra -> spectra);
+//   inv_level:   inverse transform of one level (spectra -> grids rr[]);
+//   down_interp: downward transfers and interpolation.
 template <typename R>
 void run_mac(efie_handle* h, FarSet<R>& F, int ell, int C, const cpx_t<R>* Qin, cpx_t<R>* Rout, cudaStream_t s);
+template <typename R>
+void down_interp(efie_handle* h, FarSet<R>& F, int nr, int rhs0, std::vector<cpx_t<R>*>& rr, cudaStream_t s);
 
 template <typename R>
-void far_up(efie_handle* h, FarSet<R>& F, int nr, int rhs0, std::vector<cpx_t<R>*>& rr, cpx_t<R>* Qtop,
-            cudaStream_t s) {
+void anterp_up(efie_handle* h, FarSet<R>& F, int nr, int rhs0, std::vector<cpx_t<R>*>& qq, cudaStream_t s) {
   Plan& P = h->plan;
   const int C = 4 * nr;
   const int D = P.D, top = P.top;
@@ -532,7 +560,7 @@ void far_up(efie_handle* h, FarSet<R>& F, int nr, int rhs0, std::vector<cpx_t<R>
       rin = (const cpx_t<R>*)(h->rhof + (int64_t)rhs0 * Nt);
     }
     launch_anterp<R>(F.gr, F.gt, h->gptr_r, h->gptr_t, h->mr_off, h->mt_off, h->d_box_rwg_ptr,
-                     h->d_box_tri_ptr, (int64_t)L.code.size(), xin, N, rin, Nt, nr, F.q[D - top], L.sp, s);
+                     h->d_box_tri_ptr, (int64_t)L.code.size(), xin, N, rin, Nt, nr, qq[D - top], L.sp, s);
   }
   // a3: upward transfers, shared among siblings one axis at a time (z, y, x)
   for (int ell = D; ell > top; --ell) {
@@ -547,57 +575,73 @@ void far_up(efie_handle* h, FarSet<R>& F, int nr, int rhs0, std::vector<cpx_t<R>
     View t1{(int64_t)sp * sp * spp * C, (int64_t)sp * spp * C, (int64_t)spp * C, C};
     View t2{(int64_t)sp * spp * spp * C, (int64_t)spp * spp * C, (int64_t)spp * C, C};
     View vp{(int64_t)spp * spp * spp * C, (int64_t)spp * spp * C, (int64_t)spp * C, C};
-    launch_mode_pair<R>(F.q[ell - top], vq, F.tmp1, t1, LD.ng1, C, 2, sp, sp, sp, spp, FL.CL, FL.CR, LD.uz_s0,
+    launch_mode_pair<R>(qq[ell - top], vq, F.tmp1, t1, LD.ng1, C, 2, sp, sp, sp, spp, FL.CL, FL.CR, LD.uz_s0,
                         LD.uz_s1, LD.uz_b0, LD.uz_b1, s);
     launch_mode_pair<R>(F.tmp1, t1, F.tmp2, t2, LD.ng2, C, 1, sp, sp, spp, spp, FL.CL, FL.CR, LD.uy_s0,
                         LD.uy_s1, LD.uy_b0, LD.uy_b1, s);
-    launch_mode_pair<R>(F.tmp2, t2, F.q[ell - 1 - top], vp, Bp, C, 0, sp, spp, spp, spp, FL.CL, FL.CR, LD.ux_s0,
+    launch_mode_pair<R>(F.tmp2, t2, qq[ell - 1 - top], vp, Bp, C, 0, sp, spp, spp, spp, FL.CL, FL.CR, LD.ux_s0,
                         LD.ux_s1, LD.ux_b0, LD.ux_b1, s);
   }
-  // a4-a7: stabilized FFT translations per level
-  for (int ell = D; ell >= top; --ell) {
+}
+
+template <typename R>
+void fwd_level(efie_handle* h, FarSet<R>& F, int ell, int C, const cpx_t<R>* qin, cpx_t<R>* Qout, cudaStream_t s) {
+  Plan& P = h->plan;
+  const Level& L = P.L(ell);
+  auto& FL = F.lv[ell - P.top];
+  const int64_t B = (int64_t)L.code.size();
+  const int sp = L.sp, n = L.nfft;
+  View vq{(int64_t)sp * sp * sp * C, (int64_t)sp * sp * C, (int64_t)sp * C, C};
+  View a1{(int64_t)n * sp * sp * C, (int64_t)sp * sp * C, (int64_t)sp * C, C};
+  View a2{(int64_t)n * n * sp * C, (int64_t)n * sp * C, (int64_t)sp * C, C};
+  View vf{C, (int64_t)n * n * B * C, (int64_t)n * B * C, B * C};
+  KScope ks(h, K_FWD, s, 3);
+  if (!launch_dft<R>(qin, vq, F.tmp1, a1, B, C, 0, sp, n, sp, sp, FL.Mf, n, false, s))
+    launch_mode<R>(qin, vq, F.tmp1, a1, B, C, 0, sp, n, sp, sp, FL.Mf, FL.Mf, true, nullptr, nullptr, false, s);
+  if (!launch_dft<R>(F.tmp1, a1, F.tmp2, a2, B, C, 1, sp, n, n, sp, FL.Mf, n, false, s))
+    launch_mode<R>(F.tmp1, a1, F.tmp2, a2, B, C, 1, sp, n, n, sp, FL.Mf, FL.Mf, true, nullptr, nullptr, false, s);
+  if (!launch_dft<R>(F.tmp2, a2, Qout, vf, B, C, 2, sp, n, n, n, FL.Mf, n, false, s))
+    launch_mode<R>(F.tmp2, a2, Qout, vf, B, C, 2, sp, n, n, n, FL.Mf, FL.Mf, true, nullptr, nullptr, false, s);
+}
+
+template <typename R>
+void inv_level(efie_handle* h, FarSet<R>& F, int ell, int C, const cpx_t<R>* Rin, cpx_t<R>* rout, cudaStream_t s) {
+  Plan& P = h->plan;
+  const Level& L = P.L(ell);
+  auto& FL = F.lv[ell - P.top];
+  const int64_t B = (int64_t)L.code.size();
+  const int sp = L.sp, n = L.nfft;
+  View vq{(int64_t)sp * sp * sp * C, (int64_t)sp * sp * C, (int64_t)sp * C, C};
+  View vf{C, (int64_t)n * n * B * C, (int64_t)n * B * C, B * C};
+  View b1{(int64_t)sp * n * n * C, (int64_t)n * n * C, (int64_t)n * C, C};
+  View b2{(int64_t)sp * sp * n * C, (int64_t)sp * n * C, (int64_t)n * C, C};
+  KScope ks(h, K_INV, s, 3);
+  if (!launch_dft<R>(Rin, vf, F.tmp1, b1, B, C, 0, n, sp, n, n, FL.Mb, n, true, s))
+    launch_mode<R>(Rin, vf, F.tmp1, b1, B, C, 0, n, sp, n, n, FL.Mb, FL.Mb, true, nullptr, nullptr, false, s);
+  if (!launch_dft<R>(F.tmp1, b1, F.tmp2, b2, B, C, 1, n, sp, sp, n, FL.Mb, n, true, s))
+    launch_mode<R>(F.tmp1, b1, F.tmp2, b2, B, C, 1, n, sp, sp, n, FL.Mb, FL.Mb, true, nullptr, nullptr, false, s);
+  if (!launch_dft<R>(F.tmp2, b2, rout, vq, B, C, 2, n, sp, sp, sp, FL.Mb, n, true, s))
+    launch_mode<R>(F.tmp2, b2, rout, vq, B, C, 2, n, sp, sp, sp, FL.Mb, FL.Mb, true, nullptr, nullptr, false, s);
+}
+
+template <typename R>
+void far_chunk(efie_handle* h, FarSet<R>& F, int nr, cudaStream_t s) {
+  Plan& P = h->plan;
+  const int C = 4 * nr;
+  anterp_up<R>(h, F, nr, 0, F.q, s);
+  for (int ell = P.D; ell >= P.top; --ell) {
     const Level& L = P.L(ell);
-    const LevDev& LD = h->lev[ell - top];
-    auto& FL = F.lv[ell - top];
-    int64_t B = (int64_t)L.code.size();
-    int sp = L.sp, n = L.nfft;
-    int64_t n3 = (int64_t)n * n * n;
-    if (LD.nfar == 0) {
-      cuda_check(cudaMemsetAsync(rr[ell - top], 0, sizeof(cpx_t<R>) * B * sp * sp * sp * C, s), "memset r");
+    const int64_t sp = L.sp;
+    if (h->lev[ell - P.top].nfar == 0) {
+      cuda_check(cudaMemsetAsync(F.r[ell - P.top], 0, sizeof(cpx_t<R>) * (int64_t)L.code.size() * sp * sp * sp * C,
+                                 s), "memset r");
       continue;
     }
-    View vq{(int64_t)sp * sp * sp * C, (int64_t)sp * sp * C, (int64_t)sp * C, C};
-    View a1{(int64_t)n * sp * sp * C, (int64_t)sp * sp * C, (int64_t)sp * C, C};
-    View a2{(int64_t)n * n * sp * C, (int64_t)n * sp * C, (int64_t)sp * C, C};
-    View vf{C, (int64_t)n * n * B * C, (int64_t)n * B * C, B * C};
-    {
-      KScope ks(h, K_FWD, s, 3);
-      if (!launch_dft<R>(F.q[ell - top], vq, F.tmp1, a1, B, C, 0, sp, n, sp, sp, FL.Mf, n, false, s))
-        launch_mode<R>(F.q[ell - top], vq, F.tmp1, a1, B, C, 0, sp, n, sp, sp, FL.Mf, FL.Mf, true, nullptr,
-                       nullptr, false, s);
-      if (!launch_dft<R>(F.tmp1, a1, F.tmp2, a2, B, C, 1, sp, n, n, sp, FL.Mf, n, false, s))
-        launch_mode<R>(F.tmp1, a1, F.tmp2, a2, B, C, 1, sp, n, n, sp, FL.Mf, FL.Mf, true, nullptr, nullptr,
-                       false, s);
-      cpx_t<R>* Qo = ell == top ? Qtop : F.Qh;
-      if (!launch_dft<R>(F.tmp2, a2, Qo, vf, B, C, 2, sp, n, n, n, FL.Mf, n, false, s))
-        launch_mode<R>(F.tmp2, a2, Qo, vf, B, C, 2, sp, n, n, n, FL.Mf, FL.Mf, true, nullptr, nullptr, false,
-                       s);
-    }
-    if (ell == top) continue;   // the top level's translation and inverse come later
+    fwd_level<R>(h, F, ell, C, F.q[ell - P.top], F.Qh, s);
     run_mac<R>(h, F, ell, C, F.Qh, F.Rh, s);
-    KScope ks(h, K_INV, s, 3);
-    View b1{(int64_t)sp * n * n * C, (int64_t)n * n * C, (int64_t)n * C, C};
-    View b2{(int64_t)sp * sp * n * C, (int64_t)sp * n * C, (int64_t)n * C, C};
-    if (!launch_dft<R>(F.Rh, vf, F.tmp1, b1, B, C, 0, n, sp, n, n, FL.Mb, n, true, s))
-      launch_mode<R>(F.Rh, vf, F.tmp1, b1, B, C, 0, n, sp, n, n, FL.Mb, FL.Mb, true, nullptr, nullptr, false,
-                     s);
-    if (!launch_dft<R>(F.tmp1, b1, F.tmp2, b2, B, C, 1, n, sp, sp, n, FL.Mb, n, true, s))
-      launch_mode<R>(F.tmp1, b1, F.tmp2, b2, B, C, 1, n, sp, sp, n, FL.Mb, FL.Mb, true, nullptr, nullptr,
-                     false, s);
-    if (!launch_dft<R>(F.tmp2, b2, rr[ell - top], vq, B, C, 2, n, sp, sp, sp, FL.Mb, n, true, s))
-      launch_mode<R>(F.tmp2, b2, rr[ell - top], vq, B, C, 2, n, sp, sp, sp, FL.Mb, FL.Mb, true, nullptr,
-                     nullptr, false, s);
+    inv_level<R>(h, F, ell, C, F.Rh, F.r[ell - P.top], s);
   }
+  down_interp<R>(h, F, nr, 0, F.r, s);
 }
 
 template <typename R>
@@ -611,9 +655,9 @@ void run_mac(efie_handle* h, FarSet<R>& F, int ell, int C, const cpx_t<R>* Qin, 
   const int n = L.nfft;
   const int64_t n3 = (int64_t)n * n * n;
     {
-      const bool tc2 = sizeof(R) == 4 && h->mac_variant == 0 && LD.src_all &&
-                       mac_top_tc2_fits(C, LD.max_tile, LD.O, B, LD.ntiles, 1);
-      const bool tc = sizeof(R) == 4 && (h->mac_variant == 0 || h->mac_variant == 3) &&
+      const bool autov = h->mac_variant == 0 || h->mac_variant == 4;
+      const bool tc2 = sizeof(R) == 4 && autov && mac_top_tc2_fits(C, LD.max_tile, LD.O, LD.nq, LD.ntiles, 1);
+      const bool tc = sizeof(R) == 4 && (autov || h->mac_variant == 3) &&
                       mac_top_tc_fits(C, LD.max_tile, LD.O);
       KScope ks(h, tc || tc2 ? K_MAC_TOP_TC : ell == top ? K_MAC_TOP : K_MAC, s, 1);
       bool done = false;
@@ -622,8 +666,8 @@ void run_mac(efie_handle* h, FarSet<R>& F, int ell, int C, const cpx_t<R>* Qin, 
         const float2* qv[1] = {(const float2*)Qin};
         float2* rv[1] = {(float2*)Rout};
         done = launch_mac_top_tc2(qv, rv, 1, (const float2*)FL.Kh, B, C, LD.O, n3, LD.ntiles, LD.max_tile,
-                                  LD.tile_tgt_ptr, LD.tile_tgt, LD.tile_src_ptr, LD.tile_kidx_off, LD.tile_kidx,
-                                  h->err_dev, s);
+                                  LD.tile_tgt_ptr, LD.tile_tgt, LD.tile_src_ptr, LD.tile_src, LD.tile_kidx_off,
+                                  LD.tile_kidx, LD.nq, h->err_dev, s);
       }
       if (done) cuda_check(cudaPeekAtLastError(), "top-level translation (persistent tensor-core kernel)");
       if (!done && tc)
@@ -639,36 +683,11 @@ void run_mac(efie_handle* h, FarSet<R>& F, int ell, int C, const cpx_t<R>* Qin, 
 }
 
 template <typename R>
-void far_down(efie_handle* h, FarSet<R>& F, int nr, int rhs0, std::vector<cpx_t<R>*>& rr, const cpx_t<R>* Rtop,
-              cudaStream_t s) {
+void down_interp(efie_handle* h, FarSet<R>& F, int nr, int rhs0, std::vector<cpx_t<R>*>& rr, cudaStream_t s) {
   Plan& P = h->plan;
   const int C = 4 * nr;
   const int D = P.D, top = P.top;
   const int64_t N = P.g.N, Nt = P.g.nt;
-  {
-    const int ell = top;
-    const Level& L = P.L(ell);
-    const LevDev& LD = h->lev[ell - top];
-    auto& FL = F.lv[ell - top];
-    int64_t B = (int64_t)L.code.size();
-    int sp = L.sp, n = L.nfft;
-    if (LD.nfar > 0) {
-      View vq{(int64_t)sp * sp * sp * C, (int64_t)sp * sp * C, (int64_t)sp * C, C};
-      View vf{C, (int64_t)n * n * B * C, (int64_t)n * B * C, B * C};
-      KScope ks(h, K_INV, s, 3);
-      View b1{(int64_t)sp * n * n * C, (int64_t)n * n * C, (int64_t)n * C, C};
-      View b2{(int64_t)sp * sp * n * C, (int64_t)sp * n * C, (int64_t)n * C, C};
-      if (!launch_dft<R>(Rtop, vf, F.tmp1, b1, B, C, 0, n, sp, n, n, FL.Mb, n, true, s))
-        launch_mode<R>(Rtop, vf, F.tmp1, b1, B, C, 0, n, sp, n, n, FL.Mb, FL.Mb, true, nullptr, nullptr, false,
-                       s);
-      if (!launch_dft<R>(F.tmp1, b1, F.tmp2, b2, B, C, 1, n, sp, sp, n, FL.Mb, n, true, s))
-        launch_mode<R>(F.tmp1, b1, F.tmp2, b2, B, C, 1, n, sp, sp, n, FL.Mb, FL.Mb, true, nullptr, nullptr,
-                       false, s);
-      if (!launch_dft<R>(F.tmp2, b2, rr[ell - top], vq, B, C, 2, n, sp, sp, sp, FL.Mb, n, true, s))
-        launch_mode<R>(F.tmp2, b2, rr[ell - top], vq, B, C, 2, n, sp, sp, sp, FL.Mb, FL.Mb, true, nullptr,
-                       nullptr, false, s);
-    }
-  }
   // a8: downward transfers r_c += C^T r_parent, shared among siblings one
   // axis at a time (x for (parent, b_x), y for (parent, b_x, b_y), z per child)
   for (int ell = top + 1; ell <= D; ++ell) {
@@ -701,52 +720,61 @@ void far_down(efie_handle* h, FarSet<R>& F, int nr, int rhs0, std::vector<cpx_t<
 }
 
 
-template <typename R>
-void far_chunk(efie_handle* h, FarSet<R>& F, int nr, cudaStream_t s) {
-  const int top = h->plan.top;
-  far_up<R>(h, F, nr, 0, F.r, F.Qh, s);
-  if (h->lev[0].nfar > 0) run_mac<R>(h, F, top, 4 * nr, F.Qh, F.Rh, s);
-  far_down<R>(h, F, nr, 0, F.r, F.Rh, s);
-}
 
-// a10 (near field, FP64 class) and the final combination for nr right-hand
-// sides whose far parts are in yA / w; y canonical [nr][ldy]
-void near_combine(efie_handle* h, int nr, double2* y, double2* yAo, double2* yVo, int64_t ldy, cudaStream_t s) {
+// a10: the near field (FP64 class) of nr right-hand sides into yAn / wn, on
+// the handle's second stream, after the charges on `s` (fork); the far field
+// runs meanwhile on `s`.  near_join makes `s` wait for it, and combine adds
+// the near and far parts.
+void near_fork(efie_handle* h, int nr, cudaStream_t s) {
   Plan& P = h->plan;
   const int64_t N = P.g.N, Nt = P.g.nt;
-  int64_t BD = (int64_t)P.L(P.D).code.size();
+  const int64_t BD = (int64_t)P.L(P.D).code.size();
+  cudaStream_t sn = h->s_near;
+  cuda_check(cudaEventRecord(h->ev_fork, s), "near fork");
+  cuda_check(cudaStreamWaitEvent(sn, h->ev_fork, 0), "near fork");
+  cuda_check(cudaStreamWaitEvent(h->s_far, h->ev_fork, 0), "far fork");
+  cuda_check(cudaMemsetAsync(h->yAn, 0, sizeof(double2) * N * nr, sn), "near outputs");
+  cuda_check(cudaMemsetAsync(h->wn, 0, sizeof(double2) * Nt * nr, sn), "near outputs");
   if (h->near_df) {
     {
-      KScope ks(h, K_NEAR_A, s, 2);
-      launch_split_vec(h->xs, h->xs4, N * nr, s);
+      KScope ks(h, K_NEAR_A, sn, 2);
+      launch_split_vec(h->xs, h->xs4, N * nr, sn);
       launch_near_spmv_df((const float4*)h->nd.A, h->d_blkA_off, h->d_near_ptr, h->d_near_src, h->d_box_rwg_ptr,
-                          BD, h->xs4, h->yA, N, nr, h->near_variant, s);
+                          BD, h->xs4, h->yAn, N, nr, h->near_variant, sn);
     }
     {
-      KScope ks(h, K_NEAR_V, s, 2);
-      launch_split_vec(h->rho, h->rho4, Nt * nr, s);
+      KScope ks(h, K_NEAR_V, sn, 2);
+      launch_split_vec(h->rho, h->rho4, Nt * nr, sn);
       launch_near_spmv_df((const float4*)h->nd.Vn, h->d_blkV_off, h->d_near_ptr, h->d_near_src,
-                          h->d_box_tri_ptr, BD, h->rho4, h->w, Nt, nr, h->near_variant, s);
+                          h->d_box_tri_ptr, BD, h->rho4, h->wn, Nt, nr, h->near_variant, sn);
     }
   } else {
     {
-      KScope ks(h, K_NEAR_A, s, 1);
+      KScope ks(h, K_NEAR_A, sn, 1);
       launch_near_spmv(h->nd.A, h->d_blkA_off, h->d_near_ptr, h->d_near_src, h->d_box_rwg_ptr, BD, h->xs,
-                       h->yA, N, nr, s);
+                       h->yAn, N, nr, sn);
     }
     {
-      KScope ks(h, K_NEAR_V, s, 1);
+      KScope ks(h, K_NEAR_V, sn, 1);
       launch_near_spmv(h->nd.Vn, h->d_blkV_off, h->d_near_ptr, h->d_near_src, h->d_box_tri_ptr, BD, h->rho,
-                       h->w, Nt, nr, s);
+                       h->wn, Nt, nr, sn);
     }
   }
+  cuda_check(cudaEventRecord(h->ev_join, sn), "near join");
+}
+
+void near_join_combine(efie_handle* h, int nr, double2* y, double2* yAo, double2* yVo, int64_t ldy, cudaStream_t s) {
+  Plan& P = h->plan;
+  const int64_t N = P.g.N, Nt = P.g.nt;
+  cuda_check(cudaEventRecord(h->ev_far, h->s_far), "far join");
+  cuda_check(cudaStreamWaitEvent(s, h->ev_far, 0), "far join");
+  cuda_check(cudaStreamWaitEvent(s, h->ev_join, 0), "near join");
   std::complex<double> cA = jk_of(P.k), cV = 1.0 / jk_of(P.k);
   KScope ks(h, K_VEC, s, 1);
-  launch_combine(h->yA, N, h->w, Nt, h->d_rwg_perm, h->d_rwg_tri_sorted, N, nr,
+  launch_combine(h->yA, N, h->w, Nt, h->yAn, h->wn, h->d_rwg_perm, h->d_rwg_tri_sorted, N, nr,
                  make_double2(cA.real(), cA.imag()), make_double2(cV.real(), cV.imag()), y, ldy, yAo, yVo,
                  s);
 }
-
 
 // y = T x (or parts) for nr <= 8 right-hand sides; x, y canonical [nr][ldx]
 template <typename R>
@@ -761,55 +789,96 @@ void matvec_chunk(efie_handle* h, FarSet<R>& F, const double2* x, int64_t ldx, i
     launch_permute_in(x, ldx, h->d_rwg_perm, N, nr, h->xs, s);
     launch_charges(h->xs, N, h->d_tri_rwg, h->d_tri_sgn, Nt, nr, h->rho, Nt, s);  // a1
   }
-  far_chunk<R>(h, F, nr, s);                                                       // a2-a9
-  near_combine(h, nr, y, yAo, yVo, ldy, s);
+  near_fork(h, nr, s);                                                             // a10
+  far_chunk<R>(h, F, nr, h->s_far);                                                // a2-a9
+  near_join_combine(h, nr, y, yAo, yVo, ldy, s);
 }
 
-// Whether two full chunks (16 right-hand sides) can share one top-level pass:
-// FP32 far field, the automatic translation choice, and a top grid level that
-// the persistent tensor-core kernel takes with 128-row B operands.
+// Whether two full chunks (16 right-hand sides) can share the translation
+// passes: FP32 far field, the automatic translation choice, and a top grid
+// level that the persistent tensor-core kernel takes with 128-row B operands.
 bool pair_fits(efie_handle* h) {
-  if (h->precision != EFIE_MIXED || h->mac_variant != 0) return false;
-  const Plan& P = h->plan;
+  if (h->precision != EFIE_MIXED || (h->mac_variant != 0 && h->mac_variant != 4)) return false;
   const LevDev& LD = h->lev[0];
-  return LD.nfar > 0 && LD.src_all &&
-         mac_top_tc2_fits(32, LD.max_tile, LD.O, (int64_t)P.L(P.top).code.size(), LD.ntiles, 2);
+  return LD.nfar > 0 && mac_top_tc2_fits(32, LD.max_tile, LD.O, LD.nq, LD.ntiles, 2);
 }
 
-// y = T x for 16 right-hand sides (two chunks of 8): each chunk's far
-// pipeline up to the top grid level, one top-level translation pass for both,
-// then each chunk's downward pipeline, and the near field for all 16.
-void matvec_pair(efie_handle* h, const double2* x, int64_t ldx, double2* y, double2* yAo, double2* yVo,
-                 int64_t ldy, cudaStream_t s) {
+// The translation of level ell for both chunks of a pair (spectra Qa, Qb ->
+// Ra, Rb): one tensor-core pass over 64 channels with the level's 128-target
+// tiles (the top level's own tiles, or the interaction-list tiles below it),
+// or one pass per chunk on the single-chunk kernels when those do not fit.
+void run_mac_pair(efie_handle* h, int ell, const float2* Qa, const float2* Qb, float2* Ra, float2* Rb,
+                  cudaStream_t s) {
+  Plan& P = h->plan;
+  FarSet<float>& F = h->f32;
+  const Level& L = P.L(ell);
+  const LevDev& LD = h->lev[ell - P.top];
+  const int64_t n = L.nfft, B = (int64_t)L.code.size();
+  const bool top = ell == P.top;
+  const int64_t nt = top ? LD.ntiles : LD.tct_ntiles, nq = top ? LD.nq : LD.tct_nq;
+  const int mx = top ? LD.max_tile : LD.tct_max;
+  if (nt > 0 && (top || h->mac_variant == 0) && mac_top_tc2_fits(32, mx, LD.O, nq, nt, 2)) {
+    KScope ks(h, top ? K_MAC_TOP_TC : K_MAC_TC, s, 1);
+    const float2* qv[2] = {Qa, Qb};
+    float2* rv[2] = {Ra, Rb};
+    const bool ok = top ? launch_mac_top_tc2(qv, rv, 2, F.lv[ell - P.top].Kh, B, 32, LD.O, n * n * n, nt, mx,
+                                             LD.tile_tgt_ptr, LD.tile_tgt, LD.tile_src_ptr, LD.tile_src,
+                                             LD.tile_kidx_off, LD.tile_kidx, nq, h->err_dev, s)
+                        : launch_mac_top_tc2(qv, rv, 2, F.lv[ell - P.top].Kh, B, 32, LD.O, n * n * n, nt, mx,
+                                             LD.tct_tgt_ptr, LD.tct_tgt, LD.tct_src_ptr, LD.tct_src,
+                                             LD.tct_kidx_off, LD.tct_kidx, nq, h->err_dev, s);
+    if (!ok) throw EfieError{EFIE_ECUDA, "internal: chunk-pair translation does not apply"};
+    cuda_check(cudaPeekAtLastError(), "translation (chunk pair, tensor cores)");
+    return;
+  }
+  run_mac<float>(h, F, ell, 32, Qa, Ra, s);
+  run_mac<float>(h, F, ell, 32, Qb, Rb, s);
+}
+
+// y = T x for 16 np right-hand sides.  The near field takes all of them in
+// one pass over the near matrix on the second stream, while the far field
+// runs pair by pair (two chunks of 8): both chunks' upward pipelines, then
+// level by level both forward transforms, one translation pass for both,
+// both inverse transforms; then each chunk's downward pipeline.
+void matvec_pairs(efie_handle* h, const double2* x, int64_t ldx, double2* y, double2* yAo, double2* yVo,
+                  int64_t ldy, int np, cudaStream_t s) {
   Plan& P = h->plan;
   FarSet<float>& F = h->f32;
   const int64_t N = P.g.N, Nt = P.g.nt;
-  ensure_work(h, 16);
+  const int R = 16 * np;
+  ensure_work(h, R);
   ensure_far_buffers(h, F, 8);
   ensure_pair_buffers(h, F);
   {
     KScope ks(h, K_VEC, s, 2);
-    launch_permute_in(x, ldx, h->d_rwg_perm, N, 16, h->xs, s);
-    launch_charges(h->xs, N, h->d_tri_rwg, h->d_tri_sgn, Nt, 16, h->rho, Nt, s);
+    launch_permute_in(x, ldx, h->d_rwg_perm, N, R, h->xs, s);
+    launch_charges(h->xs, N, h->d_tri_rwg, h->d_tri_sgn, Nt, R, h->rho, Nt, s);
   }
-  far_up<float>(h, F, 8, 0, F.r, F.Qt2, s);
-  far_up<float>(h, F, 8, 8, F.r2, F.Qh, s);
-  {
-    const Level& L = P.L(P.top);
-    const LevDev& LD = h->lev[0];
-    const int64_t n = L.nfft;
-    KScope ks(h, K_MAC_TOP_TC, s, 1);
-    const float2* qv[2] = {F.Qt2, F.Qh};
-    float2* rv[2] = {F.Rh, F.Rt2};
-    if (!launch_mac_top_tc2(qv, rv, 2, F.lv[0].Kh, (int64_t)L.code.size(), 32, LD.O, n * n * n, LD.ntiles,
-                            LD.max_tile, LD.tile_tgt_ptr, LD.tile_tgt, LD.tile_src_ptr, LD.tile_kidx_off,
-                            LD.tile_kidx, h->err_dev, s))
-      throw EfieError{EFIE_ECUDA, "internal: chunk-pair translation does not apply"};
-    cuda_check(cudaPeekAtLastError(), "top-level translation (chunk pair)");
+  near_fork(h, R, s);
+  cudaStream_t sf = h->s_far;
+  for (int pi = 0; pi < np; ++pi) {
+    const int ra = 16 * pi, rb = ra + 8;
+    anterp_up<float>(h, F, 8, ra, F.q, sf);
+    anterp_up<float>(h, F, 8, rb, F.q2, sf);
+    for (int ell = P.D; ell >= P.top; --ell) {
+      const Level& L = P.L(ell);
+      const int64_t sp = L.sp;
+      if (h->lev[ell - P.top].nfar == 0) {
+        const size_t bytes = sizeof(float2) * (size_t)L.code.size() * sp * sp * sp * 32;
+        cuda_check(cudaMemsetAsync(F.r[ell - P.top], 0, bytes, sf), "memset r");
+        cuda_check(cudaMemsetAsync(F.r2[ell - P.top], 0, bytes, sf), "memset r");
+        continue;
+      }
+      fwd_level<float>(h, F, ell, 32, F.q[ell - P.top], F.Qh, sf);
+      fwd_level<float>(h, F, ell, 32, F.q2[ell - P.top], F.Qt2, sf);
+      run_mac_pair(h, ell, F.Qh, F.Qt2, F.Rh, F.Rt2, sf);
+      inv_level<float>(h, F, ell, 32, F.Rh, F.r[ell - P.top], sf);
+      inv_level<float>(h, F, ell, 32, F.Rt2, F.r2[ell - P.top], sf);
+    }
+    down_interp<float>(h, F, 8, ra, F.r, sf);
+    down_interp<float>(h, F, 8, rb, F.r2, sf);
   }
-  far_down<float>(h, F, 8, 0, F.r, F.Rh, s);
-  far_down<float>(h, F, 8, 8, F.r2, F.Rt2, s);
-  near_combine(h, 16, y, yAo, yVo, ldy, s);
+  near_join_combine(h, R, y, yAo, yVo, ldy, s);
 }
 
 void do_matvec(efie_handle* h, const double2* x, int64_t ldx, double2* y, double2* yA, double2* yV,
@@ -831,8 +900,9 @@ void do_matvec(efie_handle* h, const double2* x, int64_t ldx, double2* y, double
     double2* ya = yA ? yA + (int64_t)r0 * ldy : nullptr;
     double2* yv = yV ? yV + (int64_t)r0 * ldy : nullptr;
     if (pairs && n_rhs - r0 >= 16) {
-      matvec_pair(h, x + (int64_t)r0 * ldx, ldx, yy, ya, yv, ldy, s);
-      r0 += 16;
+      const int np = (n_rhs - r0) / 16;
+      matvec_pairs(h, x + (int64_t)r0 * ldx, ldx, yy, ya, yv, ldy, np, s);
+      r0 += 16 * np;
       continue;
     }
     int nr = std::min(Rc, n_rhs - r0);
@@ -857,6 +927,15 @@ void setup_impl(efie_handle* h, const efie_mesh* mesh, double k, int p, double g
   cuda_check(cudaHostAlloc((void**)&h->err_host, sizeof(int), cudaHostAllocMapped), "cudaHostAlloc");
   *h->err_host = 0;
   cuda_check(cudaHostGetDevicePointer((void**)&h->err_dev, h->err_host, 0), "cudaHostGetDevicePointer");
+  {
+    int least = 0, greatest = 0;
+    cuda_check(cudaDeviceGetStreamPriorityRange(&least, &greatest), "stream priorities");
+    cuda_check(cudaStreamCreateWithPriority(&h->s_near, cudaStreamNonBlocking, least), "near-field stream");
+    cuda_check(cudaStreamCreateWithPriority(&h->s_far, cudaStreamNonBlocking, greatest), "far-field stream");
+  }
+  cuda_check(cudaEventCreateWithFlags(&h->ev_far, cudaEventDisableTiming), "far-field event");
+  cuda_check(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming), "near-field event");
+  cuda_check(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming), "near-field event");
   h->mem.limit = h->opt.device_mem_limit;
   Plan& P = h->plan;
   using clk = std::chrono::steady_clock;
@@ -924,9 +1003,16 @@ void setup_impl(efie_handle* h, const efie_mesh* mesh, double k, int p, double g
     LD.il_ptr = M.upload(L.il_ptr);
     LD.il_src = M.upload(L.il_src);
     LD.il_off = M.upload(L.il_off);
-    LD.offsets = M.upload(L.offsets);
+    {
+      // an even number of kernel spectra per frequency (a copy of the last
+      // offset, referenced by no pair), so that every frequency's row of FP32
+      // spectra starts on a 16-byte boundary for the bulk copies
+      std::vector<int32_t> offs = L.offsets;
+      if ((offs.size() / 3) % 2 == 1) offs.insert(offs.end(), L.offsets.end() - 3, L.offsets.end());
+      LD.offsets = M.upload(offs);
+      LD.O = (int64_t)offs.size() / 3;
+    }
     LD.nfar = (int64_t)L.il_src.size();
-    LD.O = (int64_t)L.offsets.size() / 3;
     LD.parent = M.upload(L.parent);
     std::vector<int8_t> bits(3 * LD.B);
     for (int64_t b = 0; b < LD.B; ++b)
@@ -1013,14 +1099,26 @@ void setup_impl(efie_handle* h, const efie_mesh* mesh, double k, int p, double g
       LD.dz_src = M.upload(dzs);
     }
     LD.ntiles = (int64_t)L.tile_tgt_ptr.size() - 1;
-    // every tile takes all boxes of the level as its sources, in box order
-    // (the top grid level), which the persistent tensor-core kernel assumes
-    LD.src_all = LD.ntiles > 0;
-    for (int64_t t = 0; t < LD.ntiles && LD.src_all; ++t) {
-      const int64_t a = L.tile_src_ptr[t], b = L.tile_src_ptr[t + 1];
-      if (b - a != (int64_t)L.code.size()) LD.src_all = false;
-      for (int64_t j = a; j < b && LD.src_all; ++j)
-        if (L.tile_src[j] != (int32_t)(j - a)) LD.src_all = false;
+    // chunks of 16 sources over all tiles (the persistent tensor-core kernel's chunk table)
+    // (-1 when a tile has more sources than the table's 16-bit source field takes)
+    LD.nq = 0;
+    for (int64_t t = 0; t < LD.ntiles && LD.nq >= 0; ++t) {
+      const int64_t ns = L.tile_src_ptr[t + 1] - L.tile_src_ptr[t];
+      LD.nq = ns > 65536 ? -1 : LD.nq + (ns + 15) / 16;
+    }
+    if (!L.tct_tgt_ptr.empty()) {
+      LD.tct_ntiles = (int64_t)L.tct_tgt_ptr.size() - 1;
+      for (int64_t t = 0; t < LD.tct_ntiles; ++t) {
+        const int64_t ns = L.tct_src_ptr[t + 1] - L.tct_src_ptr[t];
+        LD.tct_max = std::max<int>(LD.tct_max, (int)(L.tct_tgt_ptr[t + 1] - L.tct_tgt_ptr[t]));
+        if (LD.tct_nq >= 0) LD.tct_nq = ns > 65536 ? -1 : LD.tct_nq + (ns + 15) / 16;
+      }
+      LD.tct_tgt_ptr = M.upload(L.tct_tgt_ptr);
+      LD.tct_src_ptr = M.upload(L.tct_src_ptr);
+      LD.tct_kidx_off = M.upload(L.tct_kidx_off);
+      LD.tct_tgt = M.upload(L.tct_tgt);
+      LD.tct_src = M.upload(L.tct_src);
+      LD.tct_kidx = M.upload(L.tct_kidx);
     }
     for (int64_t t = 0; t < LD.ntiles; ++t)
       LD.max_tile = std::max<int>(LD.max_tile, (int)(L.tile_tgt_ptr[t + 1] - L.tile_tgt_ptr[t]));
@@ -2178,7 +2276,7 @@ int efie_precond_gradient(efie_handle* h, const void* r, const void* e, float* g
 }
 
 int efie_autotune_set(efie_handle* h, int rhs_chunk, int mac_variant, int near_variant) {
-  if (!h || rhs_chunk < 1 || rhs_chunk > 8 || mac_variant < 0 || mac_variant > 3 || near_variant < 0 ||
+  if (!h || rhs_chunk < 1 || rhs_chunk > 8 || mac_variant < 0 || mac_variant > 4 || near_variant < 0 ||
       near_variant > 1)
     return EFIE_EINVAL;
   h->opt.rhs_chunk = rhs_chunk;
@@ -2205,9 +2303,10 @@ int efie_autotune(efie_handle* h, int n_rhs, void* stream, int* best_chunk, int*
     int bc = 8, bm = 0, bn = 0;
     for (int chunk : {8, 4, 2, 1}) {
       if (chunk > n_rhs && chunk != 1) continue;
-      for (int cand = 0; cand < 8; ++cand) {
-        const int mv = cand % 4, nv = cand / 4;
+      for (int cand = 0; cand < 10; ++cand) {
+        const int mv = cand % 5, nv = cand / 5;
         if (nv == 1 && !h->near_df) continue;  // the near variants differ in the mixed form only
+        if (mv == 4 && (chunk != 8 || n_rhs < 16)) continue;  // differs from 0 on chunk pairs only
         h->opt.rhs_chunk = chunk;
         h->mac_variant = mv;
         h->near_variant = nv;

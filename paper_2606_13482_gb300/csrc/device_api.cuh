@@ -105,13 +105,14 @@ bool launch_dft(const cpx_t<R>* in, View vin, cpx_t<R>* out, View vout, int64_t 
 // top grid level on the tensor cores (tcgen05, kind::tf32 with a 3-term split,
 // FP32-class products); false when the configuration does not fit it
 bool mac_top_tc_fits(int C, int max_tile_targets, int64_t O);
-// persistent warp-specialised form (tiles whose sources are all boxes in
-// order), on nch = 1 or 2 chunks of 8 right-hand sides per pass
-bool mac_top_tc2_fits(int C, int max_tile_targets, int64_t O, int64_t B, int64_t ntiles, int nch);
+// persistent warp-specialised form, on nch = 1 or 2 chunks of 8 right-hand
+// sides per pass; tiles of <= 128 targets with any source lists; nq = sum over
+// tiles of ceil(sources / 16)
+bool mac_top_tc2_fits(int C, int max_tile_targets, int64_t O, int64_t nq, int64_t ntiles, int nch);
 bool launch_mac_top_tc2(const float2* const* Qh, float2* const* Rh, int nch, const float2* Kh, int64_t B, int C,
                         int64_t O, int64_t nf, int64_t ntiles, int max_tile_targets, const int64_t* tgt_ptr,
-                        const int32_t* tgt, const int64_t* src_ptr, const int64_t* kidx_off, const int32_t* kidx,
-                        int* err, cudaStream_t s);
+                        const int32_t* tgt, const int64_t* src_ptr, const int32_t* src, const int64_t* kidx_off,
+                        const int32_t* kidx, int64_t nq, int* err, cudaStream_t s);
 bool launch_mac_top_tc(const float2* Qh, float2* Rh, const float2* Kh, int64_t B, int C, int64_t O, int64_t nf,
                        int64_t ntiles, int max_tile_targets, const int64_t* tgt_ptr, const int32_t* tgt,
                        const int64_t* src_ptr, const int32_t* src, const int64_t* kidx_off, const int32_t* kidx,
@@ -153,8 +154,8 @@ void launch_permute_in(const double2* x, int64_t ldx, const int32_t* perm, int64
                        double2* xs, cudaStream_t s);
 void launch_charges(const double2* xs, int64_t ldx, const int32_t* tri_rwg, const int8_t* tri_sgn,
                     int64_t Nt, int nr, double2* rho, int64_t ldr, cudaStream_t s);
-void launch_combine(const double2* yA, int64_t ldA, const double2* w, int64_t ldw,
-                    const int32_t* rwg_perm, const int32_t* rwg_tri_sorted, int64_t N, int nr,
+void launch_combine(const double2* yA, int64_t ldA, const double2* w, int64_t ldw, const double2* yAn,
+                    const double2* wn, const int32_t* rwg_perm, const int32_t* rwg_tri_sorted, int64_t N, int nr,
                     double2 cA, double2 cV, double2* y, int64_t ldy, double2* yAout,
                     double2* yVout, cudaStream_t s);
 void launch_rhs_planewave(const double* V, const int32_t* T, const double* area, const int32_t* tri_pm,

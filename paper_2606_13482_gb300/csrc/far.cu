@@ -1437,8 +1437,10 @@ void launch_charges(const double2* xs, int64_t ldx, const int32_t* tri_rwg, cons
 }
 
 // y[r][m] = cA * yA[r][i] + cV * (w[r][t+] - w[r][t-]), m = perm[i]
+// yAn, wn (optional): near-field parts kept apart from the far parts yA, w
 __global__ void k_combine(const double2* __restrict__ yA, int64_t ldA, const double2* __restrict__ w,
-                          int64_t ldw, const int32_t* __restrict__ perm, const int32_t* __restrict__ rts,
+                          int64_t ldw, const double2* __restrict__ yAn, const double2* __restrict__ wn,
+                          const int32_t* __restrict__ perm, const int32_t* __restrict__ rts,
                           int64_t N, int nr, double2 cA, double2 cV, double2* __restrict__ y, int64_t ldy,
                           double2* __restrict__ yAo, double2* __restrict__ yVo) {
   int64_t total = N * nr;
@@ -1447,6 +1449,11 @@ __global__ void k_combine(const double2* __restrict__ yA, int64_t ldA, const dou
     int64_t r = idx / N, i = idx - r * N;
     double2 a = yA[r * ldA + i];
     double2 wp = w[r * ldw + rts[2 * i]], wm = w[r * ldw + rts[2 * i + 1]];
+    if (yAn) {
+      a = cadd(a, yAn[r * ldA + i]);
+      wp = cadd(wp, wn[r * ldw + rts[2 * i]]);
+      wm = cadd(wm, wn[r * ldw + rts[2 * i + 1]]);
+    }
     double2 v = make_double2(wp.x - wm.x, wp.y - wm.y);
     int64_t m = perm[i];
     if (y) y[r * ldy + m] = cadd(cmul(cA, a), cmul(cV, v));
@@ -1454,15 +1461,15 @@ __global__ void k_combine(const double2* __restrict__ yA, int64_t ldA, const dou
     if (yVo) yVo[r * ldy + m] = v;
   }
 }
-void launch_combine(const double2* yA, int64_t ldA, const double2* w, int64_t ldw,
-                    const int32_t* rwg_perm, const int32_t* rwg_tri_sorted, int64_t N, int nr,
+void launch_combine(const double2* yA, int64_t ldA, const double2* w, int64_t ldw, const double2* yAn,
+                    const double2* wn, const int32_t* rwg_perm, const int32_t* rwg_tri_sorted, int64_t N, int nr,
                     double2 cA, double2 cV, double2* y, int64_t ldy, double2* yAout, double2* yVout,
                     cudaStream_t s) {
   int64_t total = N * nr;
   if (total <= 0) return;
   int64_t blocks = ceil_div(total, 256);
   if (blocks > 152 * 64) blocks = 152 * 64;
-  k_combine<<<(unsigned)blocks, 256, 0, s>>>(yA, ldA, w, ldw, rwg_perm, rwg_tri_sorted, N, nr, cA, cV,
+  k_combine<<<(unsigned)blocks, 256, 0, s>>>(yA, ldA, w, ldw, yAn, wn, rwg_perm, rwg_tri_sorted, N, nr, cA, cV,
                                              y, ldy, yAout, yVout);
 }
 

@@ -365,7 +365,6 @@ constexpr int T2_EPI0 = T2_PROD + 32;         // first epilogue thread
 constexpr int T2_THREADS = T2_EPI0 + 128;     // 416 threads per CTA
 constexpr uint32_t T2_COLS = 512;
 constexpr uint32_t T2_A0 = 256;               // A stages at 256 + 64 * stage
-constexpr int T2_QMAX = 1024;                 // chunks per frequency (chunk table in shared memory)
 constexpr int T2_PIECE = 16384;               // bytes per bulk copy of a kernel row
 // Per NCH (8-right-hand-side chunks per pass: 1 or 2):
 //   B rows: 32 NCH channels real, then 32 NCH imaginary (N = 64 NCH)
@@ -385,9 +384,9 @@ struct T2Cfg {
 };
 constexpr int T2_STAGES = 4;                  // largest stage count (barrier arrays)
 
-constexpr int T2_TMAX = 64;                   // tiles of the level
 struct T2Tile {
   int64_t koff;        // start of the tile's index block
+  int64_t s0;          // start of the tile's source list
   int32_t t0, nt, tpad, ns;
 };
 struct T2Bar {
@@ -395,7 +394,6 @@ struct T2Bar {
   uint32_t tmem_base;
   int abort;
   int nq;
-  T2Tile tile[T2_TMAX];
 };
 
 // x = hi + lo with hi the TF32 part of x (sign, exponent and 10 mantissa bits
@@ -437,21 +435,25 @@ __device__ __forceinline__ uint64_t smem_desc_sbo(uint32_t saddr, uint32_t sbo) 
 }
 }  // namespace
 
-// dynamic shared memory: [2 kernel rows of kbytes][STG B stages][chunk table].
-// Chunk c < NCH of the pass has its spectra at Qh[c] and writes Rh[c].
+// dynamic shared memory: [2 kernel rows of kbytes][STG B stages][tile table
+// (ntiles T2Tile)][chunk table (nq_cap entries)].  Chunk c < NCH of the pass
+// has its spectra at Qh[c] and writes Rh[c]; source j of tile t is box
+// src[src_ptr[t] + j].
 template <int NCH>
 __global__ void __maxnreg__(128)
     k_mac_top_tc2(const float2* __restrict__ Qh0, const float2* __restrict__ Qh1, float2* __restrict__ Rh0,
                   float2* __restrict__ Rh1, const float2* __restrict__ Kh, int64_t B,
                   int64_t O, int64_t nf, int64_t ntiles, const int64_t* __restrict__ tgt_ptr,
                   const int32_t* __restrict__ tgt, const int64_t* __restrict__ src_ptr,
-                  const int64_t* __restrict__ kidx_off, const int32_t* __restrict__ kidx, int kbytes, int* err) {
+                  const int32_t* __restrict__ src, const int64_t* __restrict__ kidx_off,
+                  const int32_t* __restrict__ kidx, int kbytes, int nq_cap, int* err) {
   extern __shared__ __align__(1024) unsigned char t2_smem[];
   __shared__ T2Bar bar;
   unsigned char* rows = t2_smem;
   unsigned char* Bs = t2_smem + 2 * kbytes;
   using Cfg = T2Cfg<NCH>;
-  int32_t* ctab = reinterpret_cast<int32_t*>(Bs + Cfg::STG * Cfg::BSTAGE);
+  T2Tile* tiles = reinterpret_cast<T2Tile*>(Bs + Cfg::STG * Cfg::BSTAGE);
+  uint32_t* ctab = reinterpret_cast<uint32_t*>(tiles + ntiles);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t K = nf > blockIdx.x ? (nf - 1 - blockIdx.x) / gridDim.x + 1 : 0;   // frequencies of this CTA
 
@@ -470,14 +472,15 @@ __global__ void __maxnreg__(128)
     bar.abort = 0;
     // tile table and chunk table ((tile << 16) | first source, tile by tile)
     int q = 0;
-    for (int64_t t = 0; t < ntiles && t < T2_TMAX; ++t) {
+    for (int64_t t = 0; t < ntiles; ++t) {
       const int64_t ns = src_ptr[t + 1] - src_ptr[t], nt = tgt_ptr[t + 1] - tgt_ptr[t];
-      bar.tile[t].koff = kidx_off[t];
-      bar.tile[t].t0 = (int32_t)tgt_ptr[t];
-      bar.tile[t].nt = (int32_t)nt;
-      bar.tile[t].tpad = (int32_t)(((nt + 7) / 8) * 8);
-      bar.tile[t].ns = (int32_t)ns;
-      for (int64_t j0 = 0; j0 < ns && q < T2_QMAX; j0 += TC_KC) ctab[q++] = (int32_t)((t << 16) | j0);
+      tiles[t].koff = kidx_off[t];
+      tiles[t].s0 = src_ptr[t];
+      tiles[t].t0 = (int32_t)tgt_ptr[t];
+      tiles[t].nt = (int32_t)nt;
+      tiles[t].tpad = (int32_t)(((nt + 7) / 8) * 8);
+      tiles[t].ns = (int32_t)ns;
+      for (int64_t j0 = 0; j0 < ns && q < nq_cap; j0 += TC_KC) ctab[q++] = (uint32_t)((t << 16) | j0);
     }
     bar.nq = q;
   }
@@ -512,18 +515,18 @@ __global__ void __maxnreg__(128)
 #pragma unroll
       for (int u = 0; u < 4 * NCH; ++u) qn[u] = make_float2(0.f, 0.f);
       if (k >= K) return;
-      const int32_t e = ctab[q];
-      const T2Tile& T = bar.tile[e >> 16];
-      const int j0 = e & 0xFFFF;
+      const uint32_t e = ctab[q];
+      const T2Tile& T = tiles[e >> 16];
+      const int j0 = (int)(e & 0xFFFFu);
       if (r < T.tpad) {
         const int32_t* kb = kidx + T.koff + (int64_t)j0 * T.tpad + r;
 #pragma unroll
         for (int j = 0; j < TC_KC; ++j)
           if (j0 + j < T.ns) idn[j] = __ldg(kb + j * T.tpad);
       }
-      // the top grid level translates every box: source j is box j
       if (j0 + jB < T.ns) {
-        const int64_t o = ((int64_t)(blockIdx.x + k * gridDim.x) * B + j0 + jB) * TC_C + chB;
+        const int64_t y = __ldg(src + T.s0 + j0 + jB);
+        const int64_t o = ((int64_t)(blockIdx.x + k * gridDim.x) * B + y) * TC_C + chB;
 #pragma unroll
         for (int u = 0; u < 4; ++u) qn[u] = __ldg(Qh0 + o + 8 * u);
         if (NCH == 2) {
@@ -643,7 +646,7 @@ __global__ void __maxnreg__(128)
             if (!ok) break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-          const int64_t nch = (bar.tile[t].ns + TC_KC - 1) / TC_KC;
+          const int64_t nch = (tiles[t].ns + TC_KC - 1) / TC_KC;
           const uint32_t d1 = tm + (uint32_t)db * Cfg::DBUF, d2 = d1 + 64 * NCH;
           for (int64_t c = 0; c < nch; ++c, ++g) {
             const uint32_t gu = (uint32_t)g;
@@ -697,8 +700,8 @@ __global__ void __maxnreg__(128)
         if (!ok) break;
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
         const uint32_t d1 = tm + lane_base + (uint32_t)db * Cfg::DBUF, d2 = d1 + 64 * NCH;
-        const int64_t t0 = bar.tile[t].t0, nt = bar.tile[t].nt;
-        const bool any = bar.tile[t].ns > 0;
+        const int64_t t0 = tiles[t].t0, nt = tiles[t].nt;
+        const bool any = tiles[t].ns > 0;
         const int64_t ro = r < nt ? (f * B + tgt[t0 + r]) * TC_C : -1;
 #pragma unroll
         for (int h = 0; h < TC_C * NCH; h += 16) {
@@ -768,44 +771,49 @@ bool launch_mac_top_tc(const float2* Qh, float2* Rh, const float2* Kh, int64_t B
   return true;
 }
 
-// The persistent kernel: the conditions of launch_mac_top_tc, plus an even
-// number of offsets (kernel rows are copied by TMA in 16-byte units) and
-// shared memory for two kernel rows; the top grid level's tiles take every
-// box as a source, in box order.  Returns false when it does not apply.
-static int64_t tc2_smem_bytes(int64_t O, int nch) {
+// The persistent kernel takes tiles of at most 128 targets with any source
+// lists, 32 channels per chunk, an even number of offsets (kernel rows are
+// copied by TMA in 16-byte units), and shared memory for two kernel rows, the
+// B stages and the tile and chunk tables (nq = sum over tiles of
+// ceil(sources / 16); at most 65,536 sources per tile, as a chunk-table entry
+// holds tile and first source in 16 bits each).  Returns false when it does
+// not apply.
+static int64_t tc2_smem_bytes(int64_t O, int nch, int64_t ntiles, int64_t nq) {
   const int64_t kbytes = ((O * 8 + 1023) / 1024) * 1024;
-  return 2 * kbytes + (nch == 1 ? 4 * T2Cfg<1>::BSTAGE : 3 * T2Cfg<2>::BSTAGE) + T2_QMAX * 4;
+  return 2 * kbytes + (nch == 1 ? 4 * T2Cfg<1>::BSTAGE : 3 * T2Cfg<2>::BSTAGE) + ntiles * (int64_t)sizeof(T2Tile) +
+         nq * 4;
 }
 
-bool mac_top_tc2_fits(int C, int max_tile_targets, int64_t O, int64_t B, int64_t ntiles, int nch) {
+bool mac_top_tc2_fits(int C, int max_tile_targets, int64_t O, int64_t nq, int64_t ntiles, int nch) {
   return C == TC_C && (nch == 1 || nch == 2) && max_tile_targets > 8 && max_tile_targets <= 128 && O > 0 &&
-         (O % 2) == 0 && tc2_smem_bytes(O, nch) <= 220 * 1024 && ntiles * ((B + TC_KC - 1) / TC_KC) <= T2_QMAX &&
-         ntiles <= T2_TMAX;
+         (O % 2) == 0 && ntiles > 0 && ntiles < 65536 && nq > 0 && tc2_smem_bytes(O, nch, ntiles, nq) <= 220 * 1024;
 }
 
 // nch = 2: two 8-right-hand-side chunks in one pass (Qh[1], Rh[1] used),
 // B operands of 128 rows and N = 128 MMAs.
 bool launch_mac_top_tc2(const float2* const* Qh, float2* const* Rh, int nch, const float2* Kh, int64_t B, int C,
                         int64_t O, int64_t nf, int64_t ntiles, int max_tile_targets, const int64_t* tgt_ptr,
-                        const int32_t* tgt, const int64_t* src_ptr, const int64_t* kidx_off, const int32_t* kidx,
-                        int* err, cudaStream_t s) {
-  if (!mac_top_tc2_fits(C, max_tile_targets, O, B, ntiles, nch) || nf <= 0) return false;
+                        const int32_t* tgt, const int64_t* src_ptr, const int32_t* src, const int64_t* kidx_off,
+                        const int32_t* kidx, int64_t nq, int* err, cudaStream_t s) {
+  if (!mac_top_tc2_fits(C, max_tile_targets, O, nq, ntiles, nch) || nf <= 0) return false;
   int dev = 0, nsm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return false;
   const int64_t kbytes = ((O * 8 + 1023) / 1024) * 1024;
-  const int64_t smem = tc2_smem_bytes(O, nch);
+  const int64_t smem = tc2_smem_bytes(O, nch, ntiles, nq);
   const unsigned grid = (unsigned)std::min<int64_t>(nf, nsm);
   if (nch == 1) {
     static SmemAttr attr;
     smem_attr_once(k_mac_top_tc2<1>, (int)smem, attr.v);
     k_mac_top_tc2<1><<<grid, T2_THREADS, (size_t)smem, s>>>(Qh[0], nullptr, Rh[0], nullptr, Kh, B, O, nf, ntiles,
-                                                            tgt_ptr, tgt, src_ptr, kidx_off, kidx, (int)kbytes, err);
+                                                            tgt_ptr, tgt, src_ptr, src, kidx_off, kidx, (int)kbytes,
+                                                            (int)nq, err);
   } else {
     static SmemAttr attr;
     smem_attr_once(k_mac_top_tc2<2>, (int)smem, attr.v);
     k_mac_top_tc2<2><<<grid, T2_THREADS, (size_t)smem, s>>>(Qh[0], Qh[1], Rh[0], Rh[1], Kh, B, O, nf, ntiles,
-                                                            tgt_ptr, tgt, src_ptr, kidx_off, kidx, (int)kbytes, err);
+                                                            tgt_ptr, tgt, src_ptr, src, kidx_off, kidx, (int)kbytes,
+                                                            (int)nq, err);
   }
   return true;
 }

@@ -574,9 +574,12 @@ __global__ void __launch_bounds__(NEAR_THREADS)
 k_near_rows_df(const float4* __restrict__ M, const int64_t* __restrict__ blk_off,
                const int64_t* __restrict__ near_ptr, const int32_t* __restrict__ near_src,
                const int64_t* __restrict__ box_ptr, const float4* __restrict__ x,
-               double2* __restrict__ y, int64_t ld, int nr) {
+               double2* __restrict__ y, int64_t ld, int nr, int nch) {
   __shared__ float4 xs[8][NEAR_CH];
-  const int xb = blockIdx.x, tid = threadIdx.x;
+  // block = (target box, chunk of 8 right-hand sides), chunks of one box adjacent
+  const int xb = blockIdx.x / nch, tid = threadIdx.x;
+  x += (int64_t)(blockIdx.x % nch) * 8 * ld;
+  y += (int64_t)(blockIdx.x % nch) * 8 * ld;
   const int64_t r0 = box_ptr[xb];
   const int nrow = (int)(box_ptr[xb + 1] - r0);
   const int ngrp = (nr + RPT - 1) / RPT, nunits = nrow * ngrp;
@@ -657,8 +660,10 @@ __global__ void __launch_bounds__(NEAR_THREADS)
 k_near_rows_df_g(const float4* __restrict__ M, const int64_t* __restrict__ blk_off,
                  const int64_t* __restrict__ near_ptr, const int32_t* __restrict__ near_src,
                  const int64_t* __restrict__ box_ptr, const float4* __restrict__ x,
-                 double2* __restrict__ y, int64_t ld, int nr) {
-  const int xb = blockIdx.x;
+                 double2* __restrict__ y, int64_t ld, int nr, int nch) {
+  const int xb = blockIdx.x / nch;
+  x += (int64_t)(blockIdx.x % nch) * 8 * ld;
+  y += (int64_t)(blockIdx.x % nch) * 8 * ld;
   const int64_t r0 = box_ptr[xb];
   const int nrow = (int)(box_ptr[xb + 1] - r0);
   const int ngrp = (nr + RPT - 1) / RPT, nunits = nrow * ngrp;
@@ -706,33 +711,42 @@ void launch_split_vec(const double2* x, float4* y, int64_t n, cudaStream_t s) {
   k_split_vec<<<(unsigned)blocks, 256, 0, s>>>(x, y, n);
 }
 // right-hand sides per unit: all of a 1-, 2- or 4-wide chunk; 4 for wider
-// chunks (two units per row, one unit per thread)
+// chunks (two units per row, one unit per thread).  Full chunks of 8 run in
+// one launch of (box, chunk) blocks with the chunks of a box adjacent, so
+// the blocks that read one block row of the matrix run together and the
+// matrix streams from DRAM about once for all right-hand sides; a last
+// partial chunk runs in a launch of its own.
 void launch_near_spmv_df(const float4* M, const int64_t* blk_off, const int64_t* near_ptr,
                          const int32_t* near_src, const int64_t* box_ptr, int64_t n_boxes, const float4* x,
                          double2* y, int64_t ld, int nr, int variant, cudaStream_t s) {
-  if (n_boxes <= 0) return;
-  for (int r0 = 0; r0 < nr; r0 += 8) {
-    int cnt = nr - r0 < 8 ? nr - r0 : 8;
+  if (n_boxes <= 0 || nr <= 0) return;
+  const int nfull = nr / 8;
+  for (int part = 0; part < 2; ++part) {
+    const int r0 = part == 0 ? 0 : nfull * 8;
+    const int cnt = part == 0 ? 8 : nr - r0;
+    const int nch = part == 0 ? nfull : 1;
+    if (nch == 0 || cnt == 0) continue;
     const float4* xr = x + (int64_t)r0 * ld;
     double2* yr = y + (int64_t)r0 * ld;
+    const unsigned grid = (unsigned)(n_boxes * nch);
     if (variant == 1) {
       if (cnt <= 2)
-        k_near_rows_df_g<2><<<(unsigned)n_boxes, NEAR_THREADS, 0, s>>>(M, blk_off, near_ptr, near_src, box_ptr, xr,
-                                                                       yr, ld, cnt);
+        k_near_rows_df_g<2><<<grid, NEAR_THREADS, 0, s>>>(M, blk_off, near_ptr, near_src, box_ptr, xr, yr, ld, cnt,
+                                                          nch);
       else
-        k_near_rows_df_g<4><<<(unsigned)n_boxes, NEAR_THREADS, 0, s>>>(M, blk_off, near_ptr, near_src, box_ptr, xr,
-                                                                       yr, ld, cnt);
+        k_near_rows_df_g<4><<<grid, NEAR_THREADS, 0, s>>>(M, blk_off, near_ptr, near_src, box_ptr, xr, yr, ld, cnt,
+                                                          nch);
       continue;
     }
     if (cnt == 1)
-      k_near_rows_df<1, 1><<<(unsigned)n_boxes, NEAR_THREADS, 0, s>>>(M, blk_off, near_ptr, near_src, box_ptr,
-                                                                       xr, yr, ld, cnt);
+      k_near_rows_df<1, 1><<<grid, NEAR_THREADS, 0, s>>>(M, blk_off, near_ptr, near_src, box_ptr, xr, yr, ld, cnt,
+                                                         nch);
     else if (cnt == 2)
-      k_near_rows_df<2, 1><<<(unsigned)n_boxes, NEAR_THREADS, 0, s>>>(M, blk_off, near_ptr, near_src, box_ptr,
-                                                                       xr, yr, ld, cnt);
+      k_near_rows_df<2, 1><<<grid, NEAR_THREADS, 0, s>>>(M, blk_off, near_ptr, near_src, box_ptr, xr, yr, ld, cnt,
+                                                         nch);
     else
-      k_near_rows_df<4, 1><<<(unsigned)n_boxes, NEAR_THREADS, 0, s>>>(M, blk_off, near_ptr, near_src, box_ptr,
-                                                                       xr, yr, ld, cnt);
+      k_near_rows_df<4, 1><<<grid, NEAR_THREADS, 0, s>>>(M, blk_off, near_ptr, near_src, box_ptr, xr, yr, ld, cnt,
+                                                         nch);
   }
 }
 

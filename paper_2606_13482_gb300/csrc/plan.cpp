@@ -942,6 +942,37 @@ void build_plan(Plan& P, const double* xyz, int64_t nv, const int32_t* tri, int6
     L.tile_tgt_ptr.push_back((int64_t)L.tile_tgt.size());
     L.tile_src_ptr.push_back((int64_t)L.tile_src.size());
     L.tile_kidx_off.push_back((int64_t)L.tile_kidx.size());
+    // tensor-core tiles below the top grid level (built from the interaction
+    // lists; the top level's own tiles already take every box)
+    if (ell != P.top && !L.il_src.empty()) {
+      std::vector<int32_t> pos(B, -1);
+      for (int64_t x0 = 0; x0 < B; x0 += TILE_TOP) {
+        const int64_t x1 = std::min<int64_t>(B, x0 + TILE_TOP);
+        std::vector<int32_t> sr;
+        for (int64_t x = x0; x < x1; ++x)
+          for (int64_t e = L.il_ptr[x]; e < L.il_ptr[x + 1]; ++e) sr.push_back(L.il_src[e]);
+        std::sort(sr.begin(), sr.end());
+        sr.erase(std::unique(sr.begin(), sr.end()), sr.end());
+        const int tpad = (int)(((x1 - x0) + TILE_X - 1) / TILE_X) * TILE_X;
+        L.tct_tgt_ptr.push_back((int64_t)L.tct_tgt.size());
+        L.tct_src_ptr.push_back((int64_t)L.tct_src.size());
+        L.tct_kidx_off.push_back((int64_t)L.tct_kidx.size());
+        for (int64_t x = x0; x < x1; ++x) L.tct_tgt.push_back((int32_t)x);
+        for (size_t j = 0; j < sr.size(); ++j) {
+          L.tct_src.push_back(sr[j]);
+          pos[sr[j]] = (int32_t)j;
+        }
+        const size_t k0 = L.tct_kidx.size();
+        L.tct_kidx.resize(k0 + sr.size() * (size_t)tpad, -1);
+        for (int64_t x = x0; x < x1; ++x)
+          for (int64_t e = L.il_ptr[x]; e < L.il_ptr[x + 1]; ++e)
+            L.tct_kidx[k0 + (size_t)pos[L.il_src[e]] * tpad + (size_t)(x - x0)] = L.il_off[e];
+        for (int32_t y : sr) pos[y] = -1;
+      }
+      L.tct_tgt_ptr.push_back((int64_t)L.tct_tgt.size());
+      L.tct_src_ptr.push_back((int64_t)L.tct_src.size());
+      L.tct_kidx_off.push_back((int64_t)L.tct_kidx.size());
+    }
   }
   // transfer matrices C^L, C^R (child level ell -> ell-1), lattice units of
   // the child knot spacing (Sec. IV-B)

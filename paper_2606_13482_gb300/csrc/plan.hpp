@@ -48,6 +48,11 @@ struct Level {
   // kidx[tile] is [n_src][TILE_T] offset ids (-1: pair not translated here)
   std::vector<int64_t> tile_tgt_ptr, tile_src_ptr, tile_kidx_off;
   std::vector<int32_t> tile_tgt, tile_src, tile_kidx;
+  // tensor-core tiles of an interaction-list level: TILE_TOP consecutive
+  // boxes as targets, the union of their interaction lists as sources (sorted),
+  // and the offset id of every (source, target) slot, -1 outside the lists
+  std::vector<int64_t> tct_tgt_ptr, tct_src_ptr, tct_kidx_off;
+  std::vector<int32_t> tct_tgt, tct_src, tct_kidx;
   // dense per-level matrices (row-major, FP64)
   std::vector<double> P;             // [shat][sp] = B_stab^-1 S
   std::vector<double> CL, CR;        // [sp_parent][sp_this] (child = this level)

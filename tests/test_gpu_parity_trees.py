@@ -143,10 +143,13 @@ def test_two_doublings_translation_variants(G, two_doublings, mac_variant):
 
 
 def test_two_doublings_chunk_pairs(G, two_doublings):
-    """19 vectors in the mixed form: the first 16 go through one top-level
-    tensor-core pass for two chunks of 8 (128-row B operands, N = 128 MMAs),
-    the last 3 through the single-chunk path; both against the oracle, and
-    against the CUDA-core translation (variant 2, one chunk at a time)."""
+    """19 vectors in the mixed form: the first 16 go through the chunk-pair
+    path (two chunks of 8 per tensor-core pass, 128-row B operands, N = 128
+    MMAs) on every level: the top level's all-pairs tiles and the
+    interaction-list tiles of the two levels below it (variant 0), or the top
+    level only with the lower levels on CUDA cores (variant 4); the last 3
+    through the single-chunk path.  Both against the oracle, and against the
+    CUDA-core translation (variant 2, one chunk at a time)."""
     torch = _torch()
     V, T, k, p, delta, levels, ref_op = two_doublings
     X = E.complex_gaussian((19, ref_op.mesh.N), 70)
@@ -154,12 +157,17 @@ def test_two_doublings_chunk_pairs(G, two_doublings):
     h = G.EFIE(V, T, k, p, delta, levels, precision=G.EFIE_MIXED)
     try:
         Y = h.matvec(Xd).cpu().numpy()
+        h.autotune_set(8, 4)
+        Y4 = h.matvec(Xd).cpu().numpy()
         h.autotune_set(8, 2)
         Y2 = h.matvec(Xd).cpu().numpy()
     finally:
         h.close()
     for r in (0, 7, 8, 15, 16, 18):
-        rel, mx = _errs(Y[r], ref_op.matvec(X[r]))
-        print(f"chunk pair rhs {r}: rel l2 {rel:.3e}, max-abs {mx:.3e}")
-        assert rel < TOL32 and mx < 10 * TOL32, (r, rel, mx)
+        ref = ref_op.matvec(X[r])
+        for tag, Yv in (("0", Y), ("4", Y4)):
+            rel, mx = _errs(Yv[r], ref)
+            print(f"chunk pair variant {tag} rhs {r}: rel l2 {rel:.3e}, max-abs {mx:.3e}")
+            assert rel < TOL32 and mx < 10 * TOL32, (tag, r, rel, mx)
     assert np.linalg.norm(Y - Y2) < 1e-5 * np.linalg.norm(Y2)
+    assert np.linalg.norm(Y4 - Y2) < 1e-5 * np.linalg.norm(Y2)
