@@ -321,20 +321,40 @@ int efie_precond_gradient(efie_handle *h, const void *r, const void *e, float *g
 /* ---- Batching over right-hand sides and meshes ----------------------------
  * efie_autotune times one product of n_rhs vectors for each candidate
  * right-hand-side chunk (8, 4, 2, 1 vectors per far-field pass), each
- * top-level translation kernel (0: tensor cores, tcgen05 with a 3-term TF32
+ * translation kernel choice (0: tensor cores, tcgen05 with a 3-term TF32
  * split of every FP32 operand, in the persistent warp-specialised form where
- * the top level fits it and the far field is FP32, else as 3, else as 2;
- * 1: register tiles; 2: CUDA cores with shared-memory staging through the
- * pair index tile; 3: tensor cores, one CTA per tile and frequency) and, for
+ * the level fits it and the far field is FP32, else as 3, else as 2; pairs
+ * of 8-vector chunks also run the interaction-list levels below the top on
+ * tensor cores; 1: register tiles; 2: CUDA cores with shared-memory staging
+ * through the pair index tile; 3: tensor cores, one CTA per tile and
+ * frequency; 4: as 0 with the interaction-list levels of chunk pairs on CUDA
+ * cores; 5: as 0 with a persistent form whose loader warp stages index
+ * blocks, source spectra and kernel rows in shared memory by asynchronous
+ * copies) and, for
  * mixed handles, each near-field
- * kernel (0: source values staged in shared memory, 1: read through L1 with
- * no barriers), and keeps the fastest in the handle; the choices are
- * returned if the pointers are set. */
+ * kernel (0: source values staged in shared memory by double-buffered
+ * asynchronous copies, one thread per row and 8 right-hand sides; 1: read
+ * through L1 with no barriers; 2: staged by the block between barriers, 4
+ * right-hand sides per thread), and keeps the fastest in the handle; the
+ * choices are returned if the pointers are set. */
 int efie_autotune(efie_handle *h, int n_rhs, void *stream, int *best_chunk, int *best_mac, int *best_near);
 /* Sets the three choices efie_autotune makes: rhs_chunk in 1..8, mac_variant
- * in 0..3 and near_variant in 0..1 as above.  EFIE_EINVAL outside those
+ * in 0..5 and near_variant in 0..2 as above.  EFIE_EINVAL outside those
  * ranges. */
 int efie_autotune_set(efie_handle *h, int rhs_chunk, int mac_variant, int near_variant);
+/* Transform schedule of the stabilized forward / inverse transforms
+ * (Sec. III-C, V-B: the per-axis products with F P and P^T F^-1 on every
+ * level).  0 (default): three line passes per transform; 1: for FP32 passes
+ * of 8 right-hand sides (32 channels) and 9, 13 or 21 splines per axis, the
+ * forward y and z passes run fused on (box, x-frequency) slabs in shared
+ * memory, so the intermediate of the second pass never goes to device
+ * memory; 2: the inverse z and y passes fused the same way as well.  All
+ * give the same operator up to rounding.
+ * efie_autotune times all three (after choosing the other knobs) for mixed
+ * handles whose best chunk is 8.  set: EFIE_EINVAL for a schedule outside
+ * 0..2; get writes the handle's. */
+int efie_transform_schedule_set(efie_handle *h, int schedule);
+int efie_transform_schedule_get(const efie_handle *h, int *schedule);
 
 /* A batch groups set-up handles (meshes of any size, same device).  Each
  * efie_batch_matvec runs y[i] = T_i x[i] (n_rhs[i] vectors, device c128) for
@@ -355,7 +375,10 @@ int efie_batch_destroy(efie_batch *b);
  * efie_profile(h, 0) stops.  efie_profile_read synchronizes the recorded
  * events and returns, for class index idx (0-based, EFIE_EINVAL past the last),
  * its name (NUL-terminated, truncated to name_len), total milliseconds and
- * number of kernel launches.  Either output pointer may be NULL. */
+ * number of kernel launches.  Either output pointer may be NULL.  While
+ * recording, a product runs its near field and its far field one after the
+ * other (they overlap on two streams otherwise), so that each class's time is
+ * its own kernels' time. */
 int efie_profile(efie_handle *h, int enable);
 int efie_profile_read(efie_handle *h, int idx, char *name, int name_len, double *ms,
                       int64_t *launches);

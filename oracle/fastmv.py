@@ -5,16 +5,16 @@ n = 2 s_hat - 1 (any n >= 2 s_hat - 1 gives the same result up to rounding,
 the paper does not fix n).
 
 Steps, in the paper's order:
-  a1  rho = Sigma^T j                                        (Sec. VI-A)
-  a2  leaf anterpolation q_{d,b} = sum_{n in b} j_n m_{d,n},
-      q_{4,b} = sum_{c in b} rho_c m^phi_c                   (Eq. TAfactor, Sec. VI-A)
-  a3  upward q_P += (C^{c1} x C^{c2} x C^{c3}) q_c           (Eq. interleveltransfer, Sec. IV-B)
-  a4  q~ = P^{x3} q, P = B_stab^{-1} S                       (Sec. III-C, Sec. V-B)
-  a5-a7 r~_x = sum_{y in IL(x)} G_xy q~_y, G_xy[a,b] = g(pt_x[a], pt_y[b])
-      (3-level Toeplitz, FFT-accelerated; Eq. TAfactorBspline), r_x = (P^T)^{x3} r~_x
-  a8  downward r_c += (C^{c1} x C^{c2} x C^{c3})^T r_P
-  a9  y_m = jk sum_d m_{d,m}.r_{d,b(m)} + (jk)^-1 sum_c Sigma[m,c] m^phi_c.r_{4,b(c)}
-  a10 y += jk A_near j + (jk)^-1 Sigma V_near Sigma^T j      (Sec. VI-A)
+  1. rho = Sigma^T j                                         (Sec. VI-A)
+  2. leaf anterpolation q_{d,b} = sum_{n in b} j_n m_{d,n},
+     q_{4,b} = sum_{c in b} rho_c m^phi_c                    (Eq. TAfactor, Sec. VI-A)
+  3. upward q_P += (C^{c1} x C^{c2} x C^{c3}) q_c            (Eq. interleveltransfer, Sec. IV-B)
+  4. q~ = P^{x3} q, P = B_stab^{-1} S                        (Sec. III-C, Sec. V-B)
+  5. r~_x = sum_{y in IL(x)} G_xy q~_y, G_xy[a,b] = g(pt_x[a], pt_y[b])
+     (3-level Toeplitz, FFT-accelerated; Eq. TAfactorBspline), r_x = (P^T)^{x3} r~_x
+  6. downward r_c += (C^{c1} x C^{c2} x C^{c3})^T r_P
+  7. y_m = jk sum_d m_{d,m}.r_{d,b(m)} + (jk)^-1 sum_c Sigma[m,c] m^phi_c.r_{4,b(c)}
+  8. y += jk A_near j + (jk)^-1 Sigma V_near Sigma^T j       (Sec. VI-A)
 """
 from __future__ import annotations
 

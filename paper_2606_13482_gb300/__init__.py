@@ -30,7 +30,8 @@ EXPORTED_SYMBOLS = [
     "efie_matvec_fp64",
     "efie_matvec_parts", "efie_solve", "efie_precond_harvest", "efie_precond_train", "efie_precond_save",
     "efie_precond_load", "efie_precond_enable", "efie_precond_params", "efie_precond_apply",
-    "efie_precond_gradient", "efie_autotune", "efie_autotune_set", "efie_batch_create", "efie_batch_matvec",
+    "efie_precond_gradient", "efie_autotune", "efie_autotune_set", "efie_transform_schedule_set",
+    "efie_transform_schedule_get", "efie_batch_create", "efie_batch_matvec",
     "efie_batch_destroy",
     "efie_profile", "efie_profile_read", "efie_launch_count", "efie_setup_times",
     "efie_destroy", "efie_last_error",
@@ -138,6 +139,8 @@ def load_library(path: str = LIB_PATH):
     lib.efie_precond_gradient.argtypes = [VP, VP, VP, P(F), P(D), VP]
     lib.efie_autotune.argtypes = [VP, ctypes.c_int, VP, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int)]
     lib.efie_autotune_set.argtypes = [VP, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    lib.efie_transform_schedule_set.argtypes = [VP, ctypes.c_int]
+    lib.efie_transform_schedule_get.argtypes = [VP, P(ctypes.c_int)]
     lib.efie_batch_create.argtypes = [P(VP), ctypes.c_int, P(VP)]
     lib.efie_batch_matvec.argtypes = [VP, P(VP), P(VP), P(ctypes.c_int), VP]
     lib.efie_batch_destroy.argtypes = [VP]
@@ -506,6 +509,16 @@ class EFIE:
 
     def autotune_set(self, rhs_chunk: int, mac_variant: int, near_variant: int = 0):
         _check(self.lib, self.lib.efie_autotune_set(self.h, rhs_chunk, mac_variant, near_variant), self.h)
+
+    def transform_schedule(self, schedule=None):
+        """Sets the transform schedule (0 line passes, 1 forward y-z passes
+        fused, 2 forward and inverse fused) when given; returns the handle's
+        schedule."""
+        if schedule is not None:
+            _check(self.lib, self.lib.efie_transform_schedule_set(self.h, int(schedule)), self.h)
+        v = ctypes.c_int()
+        _check(self.lib, self.lib.efie_transform_schedule_get(self.h, ctypes.byref(v)), self.h)
+        return v.value
 
     def profile(self, enable: bool):
         _check(self.lib, self.lib.efie_profile(self.h, 1 if enable else 0), self.h)

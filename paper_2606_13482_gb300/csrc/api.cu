@@ -246,10 +246,15 @@ struct efie_handle {
                          // form, else 3, else 2; chunk pairs also take the interaction-list levels on
                          // tensor cores), 1 register tiles, 2 CUDA-core shared-memory staged, 3 tensor
                          // cores with one CTA per (tile, frequency), 4 as 0 but chunk pairs keep the
-                         // interaction-list levels on CUDA cores
+                         // interaction-list levels on CUDA cores, 5 as 0 with the loader-fed persistent form
   int* err_host = nullptr;  // host-mapped flag that device waits set when they run out
   int* err_dev = nullptr;
-  int near_variant = 0;  // mixed near field: 0 shared-memory staged x, 1 x through L1 (autotuner knob)
+  int near_variant = 0;  // mixed near field (autotuner knob): 0 x staged in shared memory by
+                         // double-buffered asynchronous copies, one thread per row and 8 RHS; 1 x
+                         // through L1; 2 x staged by the block between barriers, 4 RHS per thread
+  int fft_variant = 0;   // transform schedule (autotuner knob): 0 line passes; 1 forward y and z passes
+                         // fused per slab where they apply (FP32, 32 channels); 2 forward and inverse
+                         // fused
   // work vectors (FP64, sorted) and their double-float splits
   int Rw = 0;
   double2 *xs = nullptr, *rho = nullptr, *yA = nullptr, *w = nullptr;
@@ -547,7 +552,7 @@ void anterp_up(efie_handle* h, FarSet<R>& F, int nr, int rhs0, std::vector<cpx_t
   const int C = 4 * nr;
   const int D = P.D, top = P.top;
   const int64_t N = P.g.N, Nt = P.g.nt;
-  // a2: anterpolation into the leaf grids
+  // anterpolation of the currents and charges into the leaf grids (Sec. VI-A)
   {
     const Level& L = P.L(D);
     const cpx_t<R>* xin = (const cpx_t<R>*)(h->xs + (int64_t)rhs0 * N);
@@ -562,7 +567,7 @@ void anterp_up(efie_handle* h, FarSet<R>& F, int nr, int rhs0, std::vector<cpx_t
     launch_anterp<R>(F.gr, F.gt, h->gptr_r, h->gptr_t, h->mr_off, h->mt_off, h->d_box_rwg_ptr,
                      h->d_box_tri_ptr, (int64_t)L.code.size(), xin, N, rin, Nt, nr, qq[D - top], L.sp, s);
   }
-  // a3: upward transfers, shared among siblings one axis at a time (z, y, x)
+  // upward transfers (Sec. IV-B), shared among siblings one axis at a time (z, y, x)
   for (int ell = D; ell > top; --ell) {
     KScope ks(h, K_UP, s, 3);
     const Level& L = P.L(ell);
@@ -598,6 +603,11 @@ void fwd_level(efie_handle* h, FarSet<R>& F, int ell, int C, const cpx_t<R>* qin
   KScope ks(h, K_FWD, s, 3);
   if (!launch_dft<R>(qin, vq, F.tmp1, a1, B, C, 0, sp, n, sp, sp, FL.Mf, n, false, s))
     launch_mode<R>(qin, vq, F.tmp1, a1, B, C, 0, sp, n, sp, sp, FL.Mf, FL.Mf, true, nullptr, nullptr, false, s);
+  // y and z passes fused per (box, x-frequency) slab, no y-pass intermediate in HBM
+  if (sizeof(R) == 4 && C == 32 && (h->fft_variant == 1 || h->fft_variant == 2) &&
+      launch_dft_yz(reinterpret_cast<const float2*>(F.tmp1), reinterpret_cast<float2*>(Qout), B, sp, n,
+                    reinterpret_cast<const float2*>(FL.Mf), false, s))
+    return;
   if (!launch_dft<R>(F.tmp1, a1, F.tmp2, a2, B, C, 1, sp, n, n, sp, FL.Mf, n, false, s))
     launch_mode<R>(F.tmp1, a1, F.tmp2, a2, B, C, 1, sp, n, n, sp, FL.Mf, FL.Mf, true, nullptr, nullptr, false, s);
   if (!launch_dft<R>(F.tmp2, a2, Qout, vf, B, C, 2, sp, n, n, n, FL.Mf, n, false, s))
@@ -616,6 +626,15 @@ void inv_level(efie_handle* h, FarSet<R>& F, int ell, int C, const cpx_t<R>* Rin
   View b1{(int64_t)sp * n * n * C, (int64_t)n * n * C, (int64_t)n * C, C};
   View b2{(int64_t)sp * sp * n * C, (int64_t)sp * n * C, (int64_t)n * C, C};
   KScope ks(h, K_INV, s, 3);
+  // z and y passes fused per (box, x-frequency) slab into t[b][fx][y][z][c], then the x pass
+  if (sizeof(R) == 4 && C == 32 && h->fft_variant == 2 &&
+      launch_dft_yz(reinterpret_cast<const float2*>(Rin), reinterpret_cast<float2*>(F.tmp1), B, sp, n,
+                    reinterpret_cast<const float2*>(FL.Mb), true, s)) {
+    View vt{(int64_t)n * sp * sp * C, (int64_t)sp * sp * C, (int64_t)sp * C, C};
+    if (!launch_dft<R>(F.tmp1, vt, rout, vq, B, C, 0, n, sp, sp, sp, FL.Mb, n, true, s))
+      launch_mode<R>(F.tmp1, vt, rout, vq, B, C, 0, n, sp, sp, sp, FL.Mb, FL.Mb, true, nullptr, nullptr, false, s);
+    return;
+  }
   if (!launch_dft<R>(Rin, vf, F.tmp1, b1, B, C, 0, n, sp, n, n, FL.Mb, n, true, s))
     launch_mode<R>(Rin, vf, F.tmp1, b1, B, C, 0, n, sp, n, n, FL.Mb, FL.Mb, true, nullptr, nullptr, false, s);
   if (!launch_dft<R>(F.tmp1, b1, F.tmp2, b2, B, C, 1, n, sp, sp, n, FL.Mb, n, true, s))
@@ -656,18 +675,23 @@ void run_mac(efie_handle* h, FarSet<R>& F, int ell, int C, const cpx_t<R>* Qin, 
   const int64_t n3 = (int64_t)n * n * n;
     {
       const bool autov = h->mac_variant == 0 || h->mac_variant == 4;
-      const bool tc2 = sizeof(R) == 4 && autov && mac_top_tc2_fits(C, LD.max_tile, LD.O, LD.nq, LD.ntiles, 1);
+      const bool tc3 = sizeof(R) == 4 && h->mac_variant == 5 &&
+                       mac_top_tc3_fits(C, LD.max_tile, LD.O, LD.nq, LD.ntiles, 1);
+      const bool tc2 = sizeof(R) == 4 && (autov || h->mac_variant == 5) && !tc3 &&
+                       mac_top_tc2_fits(C, LD.max_tile, LD.O, LD.nq, LD.ntiles, 1);
       const bool tc = sizeof(R) == 4 && (autov || h->mac_variant == 3) &&
                       mac_top_tc_fits(C, LD.max_tile, LD.O);
-      KScope ks(h, tc || tc2 ? K_MAC_TOP_TC : ell == top ? K_MAC_TOP : K_MAC, s, 1);
+      KScope ks(h, tc || tc2 || tc3 ? K_MAC_TOP_TC : ell == top ? K_MAC_TOP : K_MAC, s, 1);
       bool done = false;
-      if (tc2)
-      {
+      if (tc3 || tc2) {
         const float2* qv[1] = {(const float2*)Qin};
         float2* rv[1] = {(float2*)Rout};
-        done = launch_mac_top_tc2(qv, rv, 1, (const float2*)FL.Kh, B, C, LD.O, n3, LD.ntiles, LD.max_tile,
-                                  LD.tile_tgt_ptr, LD.tile_tgt, LD.tile_src_ptr, LD.tile_src, LD.tile_kidx_off,
-                                  LD.tile_kidx, LD.nq, h->err_dev, s);
+        done = tc3 ? launch_mac_top_tc3(qv, rv, 1, (const float2*)FL.Kh, B, C, LD.O, n3, LD.ntiles, LD.max_tile,
+                                        LD.tile_tgt_ptr, LD.tile_tgt, LD.tile_src_ptr, LD.tile_src,
+                                        LD.tile_kidx_off, LD.tile_kidx, LD.nq, h->err_dev, s)
+                   : launch_mac_top_tc2(qv, rv, 1, (const float2*)FL.Kh, B, C, LD.O, n3, LD.ntiles, LD.max_tile,
+                                        LD.tile_tgt_ptr, LD.tile_tgt, LD.tile_src_ptr, LD.tile_src,
+                                        LD.tile_kidx_off, LD.tile_kidx, LD.nq, h->err_dev, s);
       }
       if (done) cuda_check(cudaPeekAtLastError(), "top-level translation (persistent tensor-core kernel)");
       if (!done && tc)
@@ -688,7 +712,7 @@ void down_interp(efie_handle* h, FarSet<R>& F, int nr, int rhs0, std::vector<cpx
   const int C = 4 * nr;
   const int D = P.D, top = P.top;
   const int64_t N = P.g.N, Nt = P.g.nt;
-  // a8: downward transfers r_c += C^T r_parent, shared among siblings one
+  // downward transfers r_c += C^T r_parent (Sec. IV-B), shared among siblings one
   // axis at a time (x for (parent, b_x), y for (parent, b_x, b_y), z per child)
   for (int ell = top + 1; ell <= D; ++ell) {
     KScope ks(h, K_DOWN, s, 3);
@@ -709,7 +733,7 @@ void down_interp(efie_handle* h, FarSet<R>& F, int nr, int rhs0, std::vector<cpx
     launch_mode<R>(F.tmp2, w2, rr[ell - top], vq, B, C, 2, spp, sp, sp, sp, FL.CLt, FL.CRt, false, LD.bits,
                    LD.dz_src, true, s);
   }
-  // a9: interpolation
+  // interpolation onto the RWG test functions and the charges (Sec. VI-A)
   {
     KScope ks(h, K_INTERP, s, 1);
     const Level& L = P.L(D);
@@ -721,7 +745,7 @@ void down_interp(efie_handle* h, FarSet<R>& F, int nr, int rhs0, std::vector<cpx
 
 
 
-// a10: the near field (FP64 class) of nr right-hand sides into yAn / wn, on
+// the near field (Sec. VI-A; FP64 class) of nr right-hand sides into yAn / wn, on
 // the handle's second stream, after the charges on `s` (fork); the far field
 // runs meanwhile on `s`.  near_join makes `s` wait for it, and combine adds
 // the near and far parts.
@@ -761,6 +785,9 @@ void near_fork(efie_handle* h, int nr, cudaStream_t s) {
     }
   }
   cuda_check(cudaEventRecord(h->ev_join, sn), "near join");
+  // while kernel classes are being timed, the far field waits for the near
+  // field, so that no class's events include another class running beside it
+  if (h->prof.on) cuda_check(cudaStreamWaitEvent(h->s_far, h->ev_join, 0), "near join");
 }
 
 void near_join_combine(efie_handle* h, int nr, double2* y, double2* yAo, double2* yVo, int64_t ldy, cudaStream_t s) {
@@ -787,10 +814,10 @@ void matvec_chunk(efie_handle* h, FarSet<R>& F, const double2* x, int64_t ldx, i
   {
     KScope ks(h, K_VEC, s, 2);
     launch_permute_in(x, ldx, h->d_rwg_perm, N, nr, h->xs, s);
-    launch_charges(h->xs, N, h->d_tri_rwg, h->d_tri_sgn, Nt, nr, h->rho, Nt, s);  // a1
+    launch_charges(h->xs, N, h->d_tri_rwg, h->d_tri_sgn, Nt, nr, h->rho, Nt, s);  // rho = Sigma^T x
   }
-  near_fork(h, nr, s);                                                             // a10
-  far_chunk<R>(h, F, nr, h->s_far);                                                // a2-a9
+  near_fork(h, nr, s);                                                             // near field
+  far_chunk<R>(h, F, nr, h->s_far);                                                // far field
   near_join_combine(h, nr, y, yAo, yVo, ldy, s);
 }
 
@@ -798,9 +825,11 @@ void matvec_chunk(efie_handle* h, FarSet<R>& F, const double2* x, int64_t ldx, i
 // passes: FP32 far field, the automatic translation choice, and a top grid
 // level that the persistent tensor-core kernel takes with 128-row B operands.
 bool pair_fits(efie_handle* h) {
-  if (h->precision != EFIE_MIXED || (h->mac_variant != 0 && h->mac_variant != 4)) return false;
+  if (h->precision != EFIE_MIXED || (h->mac_variant != 0 && h->mac_variant != 4 && h->mac_variant != 5))
+    return false;
   const LevDev& LD = h->lev[0];
-  return LD.nfar > 0 && mac_top_tc2_fits(32, LD.max_tile, LD.O, LD.nq, LD.ntiles, 2);
+  return LD.nfar > 0 && (mac_top_tc3_fits(32, LD.max_tile, LD.O, LD.nq, LD.ntiles, 2) ||
+                         mac_top_tc2_fits(32, LD.max_tile, LD.O, LD.nq, LD.ntiles, 2));
 }
 
 // The translation of level ell for both chunks of a pair (spectra Qa, Qb ->
@@ -817,16 +846,20 @@ void run_mac_pair(efie_handle* h, int ell, const float2* Qa, const float2* Qb, f
   const bool top = ell == P.top;
   const int64_t nt = top ? LD.ntiles : LD.tct_ntiles, nq = top ? LD.nq : LD.tct_nq;
   const int mx = top ? LD.max_tile : LD.tct_max;
-  if (nt > 0 && (top || h->mac_variant == 0) && mac_top_tc2_fits(32, mx, LD.O, nq, nt, 2)) {
+  const bool il_tc = top || h->mac_variant == 0 || h->mac_variant == 5;
+  const bool use3 = h->mac_variant == 5 && nt > 0 && mac_top_tc3_fits(32, mx, LD.O, nq, nt, 2);
+  const bool use2 = !use3 && nt > 0 && mac_top_tc2_fits(32, mx, LD.O, nq, nt, 2);
+  if (il_tc && (use3 || use2)) {
     KScope ks(h, top ? K_MAC_TOP_TC : K_MAC_TC, s, 1);
     const float2* qv[2] = {Qa, Qb};
     float2* rv[2] = {Ra, Rb};
-    const bool ok = top ? launch_mac_top_tc2(qv, rv, 2, F.lv[ell - P.top].Kh, B, 32, LD.O, n * n * n, nt, mx,
-                                             LD.tile_tgt_ptr, LD.tile_tgt, LD.tile_src_ptr, LD.tile_src,
-                                             LD.tile_kidx_off, LD.tile_kidx, nq, h->err_dev, s)
-                        : launch_mac_top_tc2(qv, rv, 2, F.lv[ell - P.top].Kh, B, 32, LD.O, n * n * n, nt, mx,
-                                             LD.tct_tgt_ptr, LD.tct_tgt, LD.tct_src_ptr, LD.tct_src,
-                                             LD.tct_kidx_off, LD.tct_kidx, nq, h->err_dev, s);
+    auto launch = use3 ? launch_mac_top_tc3 : launch_mac_top_tc2;
+    const bool ok = top ? launch(qv, rv, 2, F.lv[ell - P.top].Kh, B, 32, LD.O, n * n * n, nt, mx, LD.tile_tgt_ptr,
+                                 LD.tile_tgt, LD.tile_src_ptr, LD.tile_src, LD.tile_kidx_off, LD.tile_kidx, nq,
+                                 h->err_dev, s)
+                        : launch(qv, rv, 2, F.lv[ell - P.top].Kh, B, 32, LD.O, n * n * n, nt, mx, LD.tct_tgt_ptr,
+                                 LD.tct_tgt, LD.tct_src_ptr, LD.tct_src, LD.tct_kidx_off, LD.tct_kidx, nq,
+                                 h->err_dev, s);
     if (!ok) throw EfieError{EFIE_ECUDA, "internal: chunk-pair translation does not apply"};
     cuda_check(cudaPeekAtLastError(), "translation (chunk pair, tensor cores)");
     return;
@@ -2276,12 +2309,24 @@ int efie_precond_gradient(efie_handle* h, const void* r, const void* e, float* g
 }
 
 int efie_autotune_set(efie_handle* h, int rhs_chunk, int mac_variant, int near_variant) {
-  if (!h || rhs_chunk < 1 || rhs_chunk > 8 || mac_variant < 0 || mac_variant > 4 || near_variant < 0 ||
-      near_variant > 1)
+  if (!h || rhs_chunk < 1 || rhs_chunk > 8 || mac_variant < 0 || mac_variant > 5 || near_variant < 0 ||
+      near_variant > 2)
     return EFIE_EINVAL;
   h->opt.rhs_chunk = rhs_chunk;
   h->mac_variant = mac_variant;
   h->near_variant = near_variant;
+  return EFIE_OK;
+}
+
+int efie_transform_schedule_set(efie_handle* h, int schedule) {
+  if (!h || schedule < 0 || schedule > 2) return EFIE_EINVAL;
+  h->fft_variant = schedule;
+  return EFIE_OK;
+}
+
+int efie_transform_schedule_get(const efie_handle* h, int* schedule) {
+  if (!h || !schedule) return EFIE_EINVAL;
+  *schedule = h->fft_variant;
   return EFIE_OK;
 }
 
@@ -2303,9 +2348,9 @@ int efie_autotune(efie_handle* h, int n_rhs, void* stream, int* best_chunk, int*
     int bc = 8, bm = 0, bn = 0;
     for (int chunk : {8, 4, 2, 1}) {
       if (chunk > n_rhs && chunk != 1) continue;
-      for (int cand = 0; cand < 10; ++cand) {
-        const int mv = cand % 5, nv = cand / 5;
-        if (nv == 1 && !h->near_df) continue;  // the near variants differ in the mixed form only
+      for (int cand = 0; cand < 18; ++cand) {
+        const int mv = cand % 6, nv = cand / 6;
+        if (nv > 0 && !h->near_df) continue;  // the near variants differ in the mixed form only
         if (mv == 4 && (chunk != 8 || n_rhs < 16)) continue;  // differs from 0 on chunk pairs only
         h->opt.rhs_chunk = chunk;
         h->mac_variant = mv;
@@ -2328,6 +2373,27 @@ int efie_autotune(efie_handle* h, int n_rhs, void* stream, int* best_chunk, int*
     h->opt.rhs_chunk = bc;
     h->mac_variant = bm;
     h->near_variant = bn;
+    // then the transform schedule with the chosen kernels (it differs only
+    // for FP32 passes of 8 right-hand sides)
+    if (h->precision == EFIE_MIXED && bc == 8) {
+      float best_f = 1e30f;
+      int bf = 0;
+      for (int fv = 0; fv < 3; ++fv) {
+        h->fft_variant = fv;
+        do_matvec(h, x, N, y, nullptr, nullptr, N, n_rhs, false, s);
+        cudaEventRecord(e0, s);
+        do_matvec(h, x, N, y, nullptr, nullptr, N, n_rhs, false, s);
+        cudaEventRecord(e1, s);
+        cuda_check(cudaEventSynchronize(e1), "autotune");
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_f) {
+          best_f = ms;
+          bf = fv;
+        }
+      }
+      h->fft_variant = bf;
+    }
     h->prof.on = prof;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

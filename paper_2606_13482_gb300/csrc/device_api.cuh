@@ -87,6 +87,10 @@ void launch_mode_pair(const cpx_t<R>* in, View vin, cpx_t<R>* out, View vout, in
 template <typename R>
 bool launch_dft(const cpx_t<R>* in, View vin, cpx_t<R>* out, View vout, int64_t B, int C, int ax, int nin,
                 int e0, int e1, int e2, const cpx_t<R>* M, int n, bool inverse, cudaStream_t s);
+// fused second and third transform passes, FP32, 32 channels, on (box,
+// x-frequency) slabs; false when they do not apply
+bool launch_dft_yz(const float2* in, float2* out, int64_t B, int sp, int n, const float2* M, bool inverse,
+                   cudaStream_t s);
 
 // one pass of the sibling-shared upward transfer: out[g] = M(bit0) in[src0] +
 // M(bit1) in[src1] along axis ax (src1 < 0: absent), M(0) = M0, M(1) = M1
@@ -110,6 +114,13 @@ bool mac_top_tc_fits(int C, int max_tile_targets, int64_t O);
 // tiles of ceil(sources / 16)
 bool mac_top_tc2_fits(int C, int max_tile_targets, int64_t O, int64_t nq, int64_t ntiles, int nch);
 bool launch_mac_top_tc2(const float2* const* Qh, float2* const* Rh, int nch, const float2* Kh, int64_t B, int C,
+                        int64_t O, int64_t nf, int64_t ntiles, int max_tile_targets, const int64_t* tgt_ptr,
+                        const int32_t* tgt, const int64_t* src_ptr, const int32_t* src, const int64_t* kidx_off,
+                        const int32_t* kidx, int64_t nq, int* err, cudaStream_t s);
+// the same contract, fed by a loader warp (TMA bulk copies of index blocks,
+// source spectra and kernel rows into shared-memory stages)
+bool mac_top_tc3_fits(int C, int max_tile_targets, int64_t O, int64_t nq, int64_t ntiles, int nch);
+bool launch_mac_top_tc3(const float2* const* Qh, float2* const* Rh, int nch, const float2* Kh, int64_t B, int C,
                         int64_t O, int64_t nf, int64_t ntiles, int max_tile_targets, const int64_t* tgt_ptr,
                         const int32_t* tgt, const int64_t* src_ptr, const int32_t* src, const int64_t* kidx_off,
                         const int32_t* kidx, int64_t nq, int* err, cudaStream_t s);

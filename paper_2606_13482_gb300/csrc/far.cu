@@ -1,19 +1,19 @@
 // Far-field kernels of the fast matvec (charges through interpolation) and small vector kernels.
 //
-//  a2  k_anterp : leaf anterpolation q_{d,b} = sum_{n in b} j_n m_{d,n} and the
-//                 charge component q_{4,b} = sum_{c in b} rho_c m^phi_c
-//                 (Eq. TAfactor, Sec. VI-A); one CTA per leaf box, one thread
-//                 per grid point gathering over the moments that cover it.
-//  a3/a8 k_mode : tensor mode products with the knot-insertion transfers
-//                 C^L / C^R and their transposes (Eq. interleveltransfer).
-//  a4-a7 k_mode : stabilize + zero-pad + DFT fused into one n x s' complex
-//                 matrix per axis (F P, P = B_stab^{-1} S), inverse likewise
-//                 (P^T F^{-1}); Sec. III-C, Sec. V-B.
-//  a6  k_mac    : frequency-domain translation R_x = sum_{y in IL(x)} K_{x-y} Q_y
-//                 (Eq. TAfactorBspline, Toeplitz structure), spectra stored
-//                 frequency-major so one frequency of all boxes is contiguous.
-//  a9  k_interp : interpolation (transpose of a2), one warp per basis function,
-//                 lanes over channels.
+//  k_anterp : leaf anterpolation q_{d,b} = sum_{n in b} j_n m_{d,n} and the
+//             charge component q_{4,b} = sum_{c in b} rho_c m^phi_c
+//             (Eq. TAfactor, Sec. VI-A); one CTA per leaf box, one thread
+//             per grid point gathering over the moments that cover it.
+//  k_mode   : tensor mode products with the knot-insertion transfers
+//             C^L / C^R and their transposes (Eq. interleveltransfer, Sec. IV-B).
+//  k_dft    : stabilize + zero-pad + DFT fused into one n x s' complex
+//             matrix per axis (F P, P = B_stab^{-1} S), inverse likewise
+//             (P^T F^{-1}); Sec. III-C, Sec. V-B.
+//  k_mac    : frequency-domain translation R_x = sum_{y in IL(x)} K_{x-y} Q_y
+//             (Eq. TAfactorBspline, Toeplitz structure), spectra stored
+//             frequency-major so one frequency of all boxes is contiguous.
+//  k_interp : interpolation (the transpose of anterpolation), one warp per
+//             basis function, lanes over channels.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -483,6 +483,201 @@ __global__ void k_dft_inv_line(const cpx_t<R>* __restrict__ in, View vin, cpx_t<
 #pragma unroll
         for (int l = 0; l < LPT; ++l) op[a * step_out + l] = acc[a][l];
   }
+}
+
+// Fused second and third passes (FP32, 32 channels), one block per
+// (box, x-frequency) slab.  Forward: the slab t[b][fx][y][z][c] (SP x SP x 32
+// values, the output of the x pass) is staged in shared memory; a warp takes
+// a pair of y-frequencies (fy, n - fy), lane = channel, forms the two rows
+// T[z] of the y pass in registers (the conjugate-row pairing of the line
+// kernels) and from each row the n z-frequencies, which it stores straight
+// into the spectrum layout Q[fx][fy][fz][b][c] (256 contiguous bytes per
+// warp store).  The y-pass intermediate never goes to HBM: per box the pass
+// pair reads n SP^2 and writes n^3 values instead of reading and writing
+// n SP^2 + n^2 SP.
+template <int SP>
+__global__ void __launch_bounds__(256, 2) k_dft_fwd_yz(const float2* __restrict__ in, float2* __restrict__ out,
+                                                    int64_t B, const float2* __restrict__ M, int n) {
+  extern __shared__ float4 fyz_smem[];
+  float2* slab = reinterpret_cast<float2*>(fyz_smem);  // [SP][SP][32]
+  float2* Ms = slab + SP * SP * 32;                    // rows 0 .. n/2 of M, [f][SP]
+  const int nh = n / 2 + 1;
+  const int64_t sl = blockIdx.x;
+  const int64_t b = sl / n;
+  const int fx = (int)(sl - b * n);
+  {
+    const float4* src = reinterpret_cast<const float4*>(in + sl * (SP * SP * 32));
+    float4* dst = reinterpret_cast<float4*>(slab);
+    for (int i = threadIdx.x; i < SP * SP * 16; i += blockDim.x) dst[i] = src[i];
+    for (int i = threadIdx.x; i < nh * SP; i += blockDim.x) Ms[i] = M[i];
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int64_t fstride = B * 32;  // between consecutive z-frequencies
+  for (int fy = warp; fy < nh; fy += nw) {
+    // y pass: a[z] = (S1, S3), c[z] = (S2, S4) over the slab's y lines
+    float2 t0[SP], t1[SP];
+#pragma unroll
+    for (int z = 0; z < SP; ++z) t0[z] = t1[z] = make_float2(0.f, 0.f);
+    const float2* Mr = Ms + fy * SP;
+#pragma unroll 1
+    for (int y = 0; y < SP; ++y) {
+      const float2 m = Mr[y];
+      const float2* sv = slab + y * SP * 32 + lane;
+#pragma unroll
+      for (int z = 0; z < SP; ++z) {
+        const float2 v = sv[z * 32];
+        t0[z].x = fmaf(m.x, v.x, t0[z].x);
+        t0[z].y = fmaf(m.x, v.y, t0[z].y);
+        t1[z].x = fmaf(m.y, v.y, t1[z].x);
+        t1[z].y = fmaf(m.y, v.x, t1[z].y);
+      }
+    }
+    // rows fy and n - fy: (S1 - S2) + i (S3 + S4) and (S1 + S2) + i (S3 - S4)
+#pragma unroll
+    for (int z = 0; z < SP; ++z) {
+      const float2 a = t0[z], c = t1[z];
+      t0[z] = make_float2(a.x - c.x, a.y + c.y);
+      t1[z] = make_float2(a.x + c.x, a.y - c.y);
+    }
+    const bool ypair = fy != 0 && 2 * fy != n;
+    for (int r = 0; r < (ypair ? 2 : 1); ++r) {
+      const int fyr = r == 0 ? fy : n - fy;
+      float2* op = out + (((int64_t)fx * n + fyr) * n * B + b) * 32 + lane;
+      for (int fz = 0; fz < nh; ++fz) {
+        const float2* Mz = Ms + fz * SP;
+        float s1 = 0.f, s2 = 0.f, s3 = 0.f, s4 = 0.f;
+#pragma unroll
+        for (int z = 0; z < SP; ++z) {
+          const float2 m = Mz[z];
+          const float2 v = r == 0 ? t0[z] : t1[z];
+          s1 = fmaf(m.x, v.x, s1);
+          s2 = fmaf(m.y, v.y, s2);
+          s3 = fmaf(m.x, v.y, s3);
+          s4 = fmaf(m.y, v.x, s4);
+        }
+        op[fz * fstride] = make_float2(s1 - s2, s3 + s4);
+        if (fz != 0 && 2 * fz != n) op[(int64_t)(n - fz) * fstride] = make_float2(s1 + s2, s3 - s4);
+      }
+    }
+  }
+}
+
+// Inverse counterpart: the z and y inverse passes of one (box, x-frequency)
+// slab.  Phase 1: a warp takes a y-frequency row, lane = channel, reads its n
+// spectrum values (256 bytes per warp load) and forms the SP outputs of the
+// z pass (conjugate input pairs folded as in k_dft_inv_line) into shared
+// memory U[fy][z][c].  Phase 2: a warp takes output points (y, z) and folds
+// the y-frequency pairs of U into t[b][fx][y][z][c], the input of the x pass.
+template <int SP>
+__global__ void __launch_bounds__(256) k_dft_inv_zy(const float2* __restrict__ in, float2* __restrict__ out,
+                                                    int64_t B, const float2* __restrict__ M, int n) {
+  extern __shared__ float4 izy_smem[];
+  float2* U = reinterpret_cast<float2*>(izy_smem);  // [n][SP][32]
+  float2* Ms = U + (int64_t)n * SP * 32;            // [f][a] = M[a][f], f = 0 .. n/2
+  const int nh = n / 2 + 1;
+  const int np = (n - 1) / 2;
+  const bool mid = (n % 2) == 0;
+  for (int i = threadIdx.x; i < nh * SP; i += blockDim.x) {
+    const int f = i / SP, a = i - f * SP;
+    Ms[i] = M[(int64_t)a * n + f];
+  }
+  __syncthreads();
+  const int64_t sl = blockIdx.x;
+  const int64_t b = sl / n;
+  const int fx = (int)(sl - b * n);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int64_t fstride = B * 32;
+  for (int fy = warp; fy < n; fy += nw) {
+    const float2* ip = in + (((int64_t)fx * n + fy) * n * B + b) * 32 + lane;
+    float2 acc[SP];
+    {
+      const float2 v0 = ip[0];
+#pragma unroll
+      for (int a = 0; a < SP; ++a) {
+        const float2 m = Ms[a];
+        acc[a] = make_float2(m.x * v0.x - m.y * v0.y, m.x * v0.y + m.y * v0.x);
+      }
+    }
+    for (int f = 1; f <= np; ++f) {
+      const float2 z1 = ip[f * fstride], z2 = ip[(int64_t)(n - f) * fstride];
+      const float2 u = make_float2(z1.x + z2.x, z1.y + z2.y), w = make_float2(z1.x - z2.x, z1.y - z2.y);
+      const float2* Mr = Ms + f * SP;
+#pragma unroll
+      for (int a = 0; a < SP; ++a) {
+        const float2 m = Mr[a];
+        acc[a].x = fmaf(m.x, u.x, acc[a].x);
+        acc[a].x = fmaf(-m.y, w.y, acc[a].x);
+        acc[a].y = fmaf(m.x, u.y, acc[a].y);
+        acc[a].y = fmaf(m.y, w.x, acc[a].y);
+      }
+    }
+    if (mid) {
+      const float2 vm = ip[(int64_t)(n / 2) * fstride];
+      const float2* Mr = Ms + (n / 2) * SP;
+#pragma unroll
+      for (int a = 0; a < SP; ++a) {
+        const float2 m = Mr[a];
+        acc[a].x = fmaf(m.x, vm.x, fmaf(-m.y, vm.y, acc[a].x));
+        acc[a].y = fmaf(m.x, vm.y, fmaf(m.y, vm.x, acc[a].y));
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < SP; ++a) U[(fy * SP + a) * 32 + lane] = acc[a];
+  }
+  __syncthreads();
+  float2* op = out + sl * (SP * SP * 32) + lane;
+  for (int o = warp; o < SP * SP; o += nw) {
+    const int y = o / SP, z = o - y * SP;
+    const float2 m0 = Ms[y], v0 = U[z * 32 + lane];
+    float ax = m0.x * v0.x - m0.y * v0.y, ay = m0.x * v0.y + m0.y * v0.x;
+    for (int f = 1; f <= np; ++f) {
+      const float2 z1 = U[(f * SP + z) * 32 + lane], z2 = U[((n - f) * SP + z) * 32 + lane];
+      const float2 m = Ms[f * SP + y];
+      ax = fmaf(m.x, z1.x + z2.x, ax);
+      ax = fmaf(-m.y, z1.y - z2.y, ax);
+      ay = fmaf(m.x, z1.y + z2.y, ay);
+      ay = fmaf(m.y, z1.x - z2.x, ay);
+    }
+    if (mid) {
+      const float2 m = Ms[(n / 2) * SP + y], vm = U[((n / 2) * SP + z) * 32 + lane];
+      ax = fmaf(m.x, vm.x, fmaf(-m.y, vm.y, ax));
+      ay = fmaf(m.x, vm.y, fmaf(m.y, vm.x, ay));
+    }
+    op[(int64_t)o * 32] = make_float2(ax, ay);
+  }
+}
+
+// Fused y-z forward (in: t[b][fx][y][z][32] -> out: Q[fx][fy][fz][b][32]) or
+// z-y inverse (in: Q layout -> out: t layout).  Returns false when they do not
+// apply (splines per axis other than 9, 13 or 21, or shared memory).
+bool launch_dft_yz(const float2* in, float2* out, int64_t B, int sp, int n, const float2* M, bool inverse,
+                   cudaStream_t s) {
+  const int nh = n / 2 + 1;
+  const int64_t slabs = B * (int64_t)n;
+  if (slabs <= 0) return true;
+  if (slabs > 0x7FFFFFFFLL) return false;
+  const size_t smem = inverse ? sizeof(float2) * ((size_t)n * sp * 32 + (size_t)nh * sp)
+                              : sizeof(float2) * ((size_t)sp * sp * 32 + (size_t)nh * sp);
+  if (smem > 200 * 1024) return false;
+#define EFIE_YZ(SPV)                                                                                 \
+  if (sp == SPV) {                                                                                   \
+    if (inverse) {                                                                                   \
+      static SmemAttr attr;                                                                          \
+      smem_attr_once(k_dft_inv_zy<SPV>, (int)smem, attr.v);                                          \
+      k_dft_inv_zy<SPV><<<(unsigned)slabs, 256, smem, s>>>(in, out, B, M, n);                        \
+    } else {                                                                                         \
+      static SmemAttr attr;                                                                          \
+      smem_attr_once(k_dft_fwd_yz<SPV>, (int)smem, attr.v);                                          \
+      k_dft_fwd_yz<SPV><<<(unsigned)slabs, 256, smem, s>>>(in, out, B, M, n);                        \
+    }                                                                                                \
+    return true;                                                                                     \
+  }
+  EFIE_YZ(9)
+  EFIE_YZ(13)
+  EFIE_YZ(21)
+#undef EFIE_YZ
+  return false;
 }
 
 // forward (inverse = false: M is n x nin, nin inputs -> n outputs along ax) or

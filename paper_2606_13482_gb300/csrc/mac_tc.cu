@@ -407,8 +407,9 @@ __device__ __forceinline__ void mbar_init(uint64_t* b, int count) {
 __device__ __forceinline__ void mbar_arrive(uint64_t* b) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(b)) : "memory");
 }
-// bounded wait that also gives up at once when another role of the CTA gave up
-__device__ __forceinline__ bool t2_wait(uint64_t* b, uint32_t parity, T2Bar* bar, int* err) {
+// bounded wait that also gives up at once when another role of the CTA gave
+// up (abort, a shared-memory flag of the CTA)
+__device__ __forceinline__ bool t2_wait(uint64_t* b, uint32_t parity, int* abort, int* err) {
   const uint32_t a = smem_u32(b);
   for (long long it = 0; it < TC_SPIN; ++it) {
     uint32_t done;
@@ -418,11 +419,14 @@ __device__ __forceinline__ bool t2_wait(uint64_t* b, uint32_t parity, T2Bar* bar
         : "r"(a), "r"(parity)
         : "memory");
     if (done) return true;
-    if ((it & 63) == 63 && *reinterpret_cast<volatile int*>(&bar->abort)) return false;
+    if ((it & 63) == 63 && *reinterpret_cast<volatile int*>(abort)) return false;
   }
-  *reinterpret_cast<volatile int*>(&bar->abort) = 1;
+  *reinterpret_cast<volatile int*>(abort) = 1;
   if (err) *reinterpret_cast<volatile int*>(err) = 1;
   return false;
+}
+__device__ __forceinline__ bool t2_wait(uint64_t* b, uint32_t parity, T2Bar* bar, int* err) {
+  return t2_wait(b, parity, &bar->abort, err);
 }
 
 __device__ __forceinline__ uint64_t smem_desc_sbo(uint32_t saddr, uint32_t sbo) {
@@ -738,6 +742,361 @@ __global__ void __maxnreg__(128)
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tm), "r"(T2_COLS));
 }
 
+// ---------------------------------------------------------------------------
+// Same pipeline, fed by a loader warp.  The producers of k_mac_top_tc2 wait on
+// their own global loads (index rows and source spectra, one chunk ahead);
+// here a loader warp copies, for every chunk, the tile's index block (16
+// sources x tpad targets, contiguous in the tile's index table) and the
+// chunk's source spectrum rows (256 bytes per source and 8-RHS chunk) into a
+// ring of shared-memory stages, LSTG chunks ahead, in 16-byte asynchronous
+// copies spread over its lanes, and the kernel spectrum rows (one buffer, or
+// two where they fit) by TMA bulk copies.  The
+// producers read everything from shared memory.  Roles: producers (warps
+// 0-7), MMA lane (warp 8), loader lane (warp 9), epilogue (warps 10-13).
+namespace {
+constexpr int T3_PROD = 256;
+constexpr int T3_MMA_WARP = 8;
+constexpr int T3_LOAD_WARP = 9;
+constexpr int T3_THREADS = 448;
+constexpr int T3_LSTG = 8;                 // most loader stages (barrier arrays)
+constexpr int T3_IBYTES = TC_KC * 128 * 4;   // index block of a chunk, at most 128 targets
+constexpr int T3_QBYTES = TC_KC * TC_C * 8;  // source spectra of a chunk, one 8-RHS chunk
+template <int NCH>
+struct T3Cfg {
+  static constexpr int LSTAGE = T3_IBYTES + NCH * T3_QBYTES;
+};
+struct T3Bar {
+  uint64_t full[T2_STAGES], empty[T2_STAGES], dfull[2], dempty[2], rfull[2], rempty[2], lfull[T3_LSTG],
+      lempty[T3_LSTG];
+  uint32_t tmem_base;
+  int abort;
+  int nq;
+};
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void arrive_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+}  // namespace
+
+// dynamic shared memory: [nrow kernel rows of kbytes][STG B stages][LSTG
+// loader stages][tile table][chunk table]
+template <int NCH>
+__global__ void __maxnreg__(128)
+    k_mac_top_tc3(const float2* __restrict__ Qh0, const float2* __restrict__ Qh1, float2* __restrict__ Rh0,
+                  float2* __restrict__ Rh1, const float2* __restrict__ Kh, int64_t B, int64_t O, int64_t nf,
+                  int64_t ntiles, const int64_t* __restrict__ tgt_ptr, const int32_t* __restrict__ tgt,
+                  const int64_t* __restrict__ src_ptr, const int32_t* __restrict__ src,
+                  const int64_t* __restrict__ kidx_off, const int32_t* __restrict__ kidx, int kbytes, int nrow,
+                  int lstg, int nq_cap, int* err) {
+  extern __shared__ __align__(1024) unsigned char t3_smem[];
+  __shared__ T3Bar bar;
+  using Cfg = T2Cfg<NCH>;
+  unsigned char* rows = t3_smem;
+  unsigned char* Bs = t3_smem + nrow * kbytes;
+  unsigned char* Ls = Bs + Cfg::STG * Cfg::BSTAGE;
+  T2Tile* tiles = reinterpret_cast<T2Tile*>(Ls + lstg * T3Cfg<NCH>::LSTAGE);
+  uint32_t* ctab = reinterpret_cast<uint32_t*>(tiles + ntiles);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t K = nf > blockIdx.x ? (nf - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+
+  if (tid == 0) {
+    for (int i = 0; i < Cfg::STG; ++i) {
+      mbar_init(&bar.full[i], 128);
+      mbar_init(&bar.empty[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&bar.dfull[i], 1);
+      mbar_init(&bar.dempty[i], 128);
+      mbar_init(&bar.rfull[i], 1);
+      mbar_init(&bar.rempty[i], T3_PROD);
+    }
+    for (int i = 0; i < lstg; ++i) {
+      mbar_init(&bar.lfull[i], 32);
+      mbar_init(&bar.lempty[i], 128);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    bar.abort = 0;
+    int q = 0;
+    for (int64_t t = 0; t < ntiles; ++t) {
+      const int64_t ns = src_ptr[t + 1] - src_ptr[t], nt = tgt_ptr[t + 1] - tgt_ptr[t];
+      tiles[t].koff = kidx_off[t];
+      tiles[t].s0 = src_ptr[t];
+      tiles[t].t0 = (int32_t)tgt_ptr[t];
+      tiles[t].nt = (int32_t)nt;
+      tiles[t].tpad = (int32_t)(((nt + 7) / 8) * 8);
+      tiles[t].ns = (int32_t)ns;
+      for (int64_t j0 = 0; j0 < ns && q < nq_cap; j0 += TC_KC) ctab[q++] = (uint32_t)((t << 16) | j0);
+    }
+    bar.nq = q;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&bar.tmem_base)),
+                 "r"(T2_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tm = bar.tmem_base;
+  const int64_t nq = bar.nq;
+  const int64_t TS = K * ntiles;
+  int* abar = &bar.abort;
+
+  if (tid < T3_PROD) {
+    // ------------------------------------------------------------ producers
+    const int wg = tid >> 7, r = tid & 127;
+    const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+    const int jB = (warp & 3) * 4 + (lane >> 3), chB = lane & 7;
+    const int boff = (jB >> 2) * TC_LBO + (jB & 3) * 4 + chB * 16;
+    int64_t g = wg;
+    bool ok = true;
+    for (int64_t k = 0; k < K && ok; ++k) {
+      const int rb = nrow == 2 ? (int)(k & 1) : 0;
+      const uint32_t rpar = (uint32_t)((nrow == 2 ? (k >> 1) : k) & 1);
+      ok = t2_wait(&bar.rfull[rb], rpar, abar, err);
+      if (!ok) break;
+      const float2* Ks = reinterpret_cast<const float2*>(rows + rb * kbytes);
+      for (; g < (k + 1) * nq; g += 2) {
+        const uint32_t gu = (uint32_t)g;
+        const int ls = (int)(gu % (uint32_t)lstg);
+        ok = t2_wait(&bar.lfull[ls], (gu / (uint32_t)lstg) & 1, abar, err);
+        if (!ok) break;
+        const uint32_t e = ctab[g - k * nq];
+        const T2Tile& T = tiles[e >> 16];
+        const int j0 = (int)(e & 0xFFFFu);
+        const unsigned char* st = Ls + ls * T3Cfg<NCH>::LSTAGE;
+        const int32_t* Is = reinterpret_cast<const int32_t*>(st);
+        const float2* Qs = reinterpret_cast<const float2*>(st + T3_IBYTES);
+        int32_t idc[TC_KC];
+        float2 qc[4 * NCH];
+#pragma unroll
+        for (int j = 0; j < TC_KC; ++j) idc[j] = (r < T.tpad && j0 + j < T.ns) ? Is[j * T.tpad + r] : -1;
+        const bool qv = j0 + jB < T.ns;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) qc[u] = qv ? Qs[jB * TC_C + chB + 8 * u] : make_float2(0.f, 0.f);
+        if (NCH == 2) {
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            qc[4 + u] = qv ? Qs[TC_KC * TC_C + jB * TC_C + chB + 8 * u] : make_float2(0.f, 0.f);
+        }
+        mbar_arrive(&bar.lempty[ls]);   // the stage is read
+        const int slot = (int)(gu % Cfg::STG);
+        if (gu >= (uint32_t)Cfg::STG) {
+          ok = t2_wait(&bar.empty[slot], ((gu / Cfg::STG) - 1) & 1, abar, err);
+          if (!ok) break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        {
+          const uint32_t ta = tm + lane_base + T2_A0 + (uint32_t)slot * 4 * TC_KC;
+#pragma unroll
+          for (int hh = 0; hh < TC_KC; hh += 8) {
+            float arh[8], arl[8], aih[8], ail[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              const float2 kv = idc[hh + j] >= 0 ? Ks[idc[hh + j]] : make_float2(0.f, 0.f);
+              arh[j] = tf32_hi(kv.x);
+              arl[j] = kv.x - arh[j];
+              aih[j] = tf32_hi(kv.y);
+              ail[j] = kv.y - aih[j];
+            }
+            tmem_st8(ta + 0 * TC_KC + hh, arh);
+            tmem_st8(ta + 1 * TC_KC + hh, arl);
+            tmem_st8(ta + 2 * TC_KC + hh, aih);
+            tmem_st8(ta + 3 * TC_KC + hh, ail);
+          }
+        }
+        {
+          float* bb = reinterpret_cast<float*>(Bs + slot * Cfg::BSTAGE + boff);
+#pragma unroll
+          for (int u = 0; u < 4 * NCH; ++u) {
+            const float rh = tf32_hi(qc[u].x), ih = tf32_hi(qc[u].y);
+            bb[(u * TC_SBO) / 4] = rh;
+            bb[((4 * NCH + u) * TC_SBO) / 4] = ih;
+            bb[(Cfg::BMAT + u * TC_SBO) / 4] = qc[u].x - rh;
+            bb[(Cfg::BMAT + (4 * NCH + u) * TC_SBO) / 4] = qc[u].y - ih;
+          }
+        }
+        asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+        mbar_arrive(&bar.full[slot]);
+      }
+      if (!ok) break;
+      mbar_arrive(&bar.rempty[rb]);   // this thread is done with the row buffer
+    }
+  } else if (warp == T3_MMA_WARP) {
+    // ------------------------------------------------------------ MMA warp
+    if (lane == 0) {
+      bool ok = true;
+      int64_t g = 0, ts = 0;
+      for (int64_t k = 0; k < K && ok; ++k) {
+        for (int64_t t = 0; t < ntiles && ok; ++t, ++ts) {
+          const uint32_t tsu = (uint32_t)ts;
+          const int db = (int)(tsu % Cfg::DB);
+          if (tsu >= (uint32_t)Cfg::DB) {
+            ok = t2_wait(&bar.dempty[db], ((tsu / Cfg::DB) - 1) & 1, abar, err);
+            if (!ok) break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+          const int64_t nch = (tiles[t].ns + TC_KC - 1) / TC_KC;
+          const uint32_t d1 = tm + (uint32_t)db * Cfg::DBUF, d2 = d1 + 64 * NCH;
+          for (int64_t c = 0; c < nch; ++c, ++g) {
+            const uint32_t gu = (uint32_t)g;
+            const int slot = (int)(gu % Cfg::STG);
+            ok = t2_wait(&bar.full[slot], (gu / Cfg::STG) & 1, abar, err);
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            const uint32_t a0 = tm + T2_A0 + (uint32_t)slot * 4 * TC_KC;
+            const uint32_t bs = smem_u32(Bs + slot * Cfg::BSTAGE);
+#pragma unroll
+            for (int kk = 0; kk < TC_KC / 8; ++kk) {
+              const uint32_t arh = a0 + 0 * TC_KC + kk * 8, arl = a0 + 1 * TC_KC + kk * 8;
+              const uint32_t aih = a0 + 2 * TC_KC + kk * 8, ail = a0 + 3 * TC_KC + kk * 8;
+              const uint32_t ko = (uint32_t)kk * 2 * TC_LBO;
+              const uint64_t bh = smem_desc_sbo(bs + ko, TC_SBO), bl = smem_desc_sbo(bs + Cfg::BMAT + ko, TC_SBO);
+              const uint32_t acc0 = (c > 0 || kk > 0) ? 1u : 0u;
+              mma_tf32(d1, arh, bh, Cfg::IDESC, acc0);
+              mma_tf32(d1, arh, bl, Cfg::IDESC, 1u);
+              mma_tf32(d1, arl, bh, Cfg::IDESC, 1u);
+              mma_tf32(d2, aih, bh, Cfg::IDESC, acc0);
+              mma_tf32(d2, aih, bl, Cfg::IDESC, 1u);
+              mma_tf32(d2, ail, bh, Cfg::IDESC, 1u);
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                             smem_u32(&bar.empty[slot]))
+                         : "memory");
+          }
+          if (!ok) break;
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                           smem_u32(&bar.dfull[db]))
+                       : "memory");
+        }
+      }
+      if (ok && TS > 0)
+        t2_wait(&bar.dfull[(uint32_t)(TS - 1) % Cfg::DB], ((uint32_t)(TS - 1) / Cfg::DB) & 1, abar, err);
+    }
+    __syncwarp();
+  } else if (warp == T3_LOAD_WARP) {
+    // ------------------------------------------------------------ loader
+    // lane 0 waits on the ring and copies the kernel rows (TMA bulk copies);
+    // the 32 lanes copy each chunk's index block and source spectra in
+    // 16-byte asynchronous copies and each signals lfull when its own
+    // copies have landed (lfull counts 32 arrivals)
+    bool ok = true;
+    int64_t g = 0;
+    const uint32_t rbytes = (uint32_t)(O * 8);
+    for (int64_t k = 0; k < K && ok; ++k) {
+      const int64_t f = blockIdx.x + k * gridDim.x;
+      const int rb = nrow == 2 ? (int)(k & 1) : 0;
+      if (k >= nrow) {
+        const uint32_t use = (uint32_t)(nrow == 2 ? (k >> 1) : k);   // earlier uses of this buffer
+        int w = 1;
+        if (lane == 0) w = t2_wait(&bar.rempty[rb], (use - 1) & 1, abar, err) ? 1 : 0;
+        ok = __shfl_sync(0xffffffffu, w, 0) != 0;
+        if (!ok) break;
+      }
+      if (lane == 0) {
+        const unsigned char* srow = reinterpret_cast<const unsigned char*>(Kh + f * O);
+        const uint32_t dst = smem_u32(rows + rb * kbytes);
+        arrive_tx(&bar.rfull[rb], rbytes);
+        for (uint32_t off = 0; off < rbytes; off += T2_PIECE) {
+          const uint32_t n = rbytes - off < (uint32_t)T2_PIECE ? rbytes - off : (uint32_t)T2_PIECE;
+          bulk_g2s(dst + off, srow + off, n, &bar.rfull[rb]);
+        }
+      }
+      for (int64_t q = 0; q < nq; ++q, ++g) {
+        const uint32_t gu = (uint32_t)g;
+        const int ls = (int)(gu % (uint32_t)lstg);
+        if (gu >= (uint32_t)lstg) {
+          int w = 1;
+          if (lane == 0) w = t2_wait(&bar.lempty[ls], ((gu / (uint32_t)lstg) - 1) & 1, abar, err) ? 1 : 0;
+          ok = __shfl_sync(0xffffffffu, w, 0) != 0;
+          if (!ok) break;
+        }
+        const uint32_t e = ctab[q];
+        const T2Tile& T = tiles[e >> 16];
+        const int j0 = (int)(e & 0xFFFFu);
+        const int nsrc = T.ns - j0 < TC_KC ? T.ns - j0 : TC_KC;
+        const int iseg = nsrc * T.tpad / 4;   // 16-byte pieces of the index block
+        const uint32_t st = smem_u32(Ls + ls * T3Cfg<NCH>::LSTAGE);
+        const int32_t yl = lane < nsrc ? __ldg(src + T.s0 + j0 + lane) : 0;
+        const unsigned char* ksrc = reinterpret_cast<const unsigned char*>(kidx + T.koff + (int64_t)j0 * T.tpad);
+        for (int sg = lane; sg < iseg; sg += 32) cp_async16(st + sg * 16, ksrc + sg * 16);
+        const int qseg = nsrc * 16;           // 16-byte pieces of the source rows of one 8-RHS chunk
+        for (int it = 0; it < 8; ++it) {
+          const int sg = it * 32 + lane, j = sg >> 4, part = sg & 15;
+          const int64_t yj = __shfl_sync(0xffffffffu, yl, j & 31);
+          if (sg < qseg) {
+            const int64_t o = (f * B + yj) * TC_C + part * 2;
+            cp_async16(st + T3_IBYTES + sg * 16, Qh0 + o);
+            if (NCH == 2) cp_async16(st + T3_IBYTES + T3_QBYTES + sg * 16, Qh1 + o);
+          }
+        }
+        asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];\n" ::"r"(smem_u32(&bar.lfull[ls]))
+                     : "memory");
+      }
+    }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    __syncwarp();
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int r = (warp & 3) * 32 + lane;
+    const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+    int64_t ts = 0;
+    bool ok = true;
+    for (int64_t k = 0; k < K && ok; ++k) {
+      const int64_t f = blockIdx.x + k * gridDim.x;
+      for (int64_t t = 0; t < ntiles; ++t, ++ts) {
+        const uint32_t tsu = (uint32_t)ts;
+        const int db = (int)(tsu % Cfg::DB);
+        ok = t2_wait(&bar.dfull[db], (tsu / Cfg::DB) & 1, abar, err);
+        if (!ok) break;
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        const uint32_t d1 = tm + lane_base + (uint32_t)db * Cfg::DBUF, d2 = d1 + 64 * NCH;
+        const int64_t t0 = tiles[t].t0, nt = tiles[t].nt;
+        const bool any = tiles[t].ns > 0;
+        const int64_t ro = r < nt ? (f * B + tgt[t0 + r]) * TC_C : -1;
+#pragma unroll
+        for (int h = 0; h < TC_C * NCH; h += 16) {
+          float re[16], im[16], p[16];
+          tmem_ld16(d1 + h, re);
+          tmem_ld16(d2 + 32 * NCH + h, p);
+          asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+          for (int n = 0; n < 16; ++n) re[n] -= p[n];
+          tmem_ld16(d1 + 32 * NCH + h, im);
+          tmem_ld16(d2 + h, p);
+          asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+          for (int n = 0; n < 16; ++n) im[n] += p[n];
+          if (h + 16 == TC_C * NCH) {
+            asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+            mbar_arrive(&bar.dempty[db]);
+          }
+          if (ro >= 0) {
+            float2* out = (h < TC_C ? Rh0 : Rh1) + ro + (h % TC_C);
+#pragma unroll
+            for (int n = 0; n < 16; n += 2)
+              *reinterpret_cast<float4*>(out + n) =
+                  any ? make_float4(re[n], im[n], re[n + 1], im[n + 1]) : make_float4(0.f, 0.f, 0.f, 0.f);
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tm), "r"(T2_COLS));
+}
+
 // Returns false when the configuration does not fit this kernel (the caller
 // then uses the CUDA-core kernels): 32 channels, tiles of 9..128 targets, and
 // a kernel spectrum row that fits in shared memory beside the B buffers with
@@ -780,8 +1139,10 @@ bool launch_mac_top_tc(const float2* Qh, float2* Rh, const float2* Kh, int64_t B
 // not apply.
 static int64_t tc2_smem_bytes(int64_t O, int nch, int64_t ntiles, int64_t nq) {
   const int64_t kbytes = ((O * 8 + 1023) / 1024) * 1024;
-  return 2 * kbytes + (nch == 1 ? 4 * T2Cfg<1>::BSTAGE : 3 * T2Cfg<2>::BSTAGE) + ntiles * (int64_t)sizeof(T2Tile) +
-         nq * 4;
+  // at least 120 KB: one CTA (one 512-column TMEM allocation) per SM
+  return std::max<int64_t>(2 * kbytes + (nch == 1 ? 4 * T2Cfg<1>::BSTAGE : 3 * T2Cfg<2>::BSTAGE) +
+                               ntiles * (int64_t)sizeof(T2Tile) + nq * 4,
+                           120 * 1024);
 }
 
 bool mac_top_tc2_fits(int C, int max_tile_targets, int64_t O, int64_t nq, int64_t ntiles, int nch) {
@@ -818,4 +1179,69 @@ bool launch_mac_top_tc2(const float2* const* Qh, float2* const* Rh, int nch, con
   return true;
 }
 
+
+// The loader-fed kernel: one or two kernel-row buffers (two where they fit
+// in 220 KB with the B stages, loader stages and tables), the same tile
+// limits as k_mac_top_tc2.
+static int64_t tc3_smem_bytes(int64_t O, int nch, int64_t ntiles, int64_t nq, int nrow, int lstg) {
+  const int64_t kbytes = ((O * 8 + 1023) / 1024) * 1024;
+  const int64_t b = nch == 1 ? T2Cfg<1>::STG * T2Cfg<1>::BSTAGE : T2Cfg<2>::STG * T2Cfg<2>::BSTAGE;
+  const int64_t l = lstg * (nch == 1 ? T3Cfg<1>::LSTAGE : T3Cfg<2>::LSTAGE);
+  // at least 120 KB, so that a second CTA (and a second 512-column TMEM
+  // allocation) never fits on an SM
+  return std::max<int64_t>(nrow * kbytes + b + l + ntiles * (int64_t)sizeof(T2Tile) + nq * 4, 120 * 1024);
+}
+
+// kernel-row buffers and loader stages: as many as fit in 220 KB, preferring
+// two row buffers, then up to 8 loader stages (at least 4)
+static void tc3_shape(int64_t O, int nch, int64_t ntiles, int64_t nq, int* nrow, int* lstg) {
+  *nrow = 0;
+  *lstg = 0;
+  for (int r = 2; r >= 1 && *nrow == 0; --r)
+    for (int l = T3_LSTG; l >= 4; --l)
+      if (tc3_smem_bytes(O, nch, ntiles, nq, r, l) <= 220 * 1024) {
+        *nrow = r;
+        *lstg = l;
+        break;
+      }
+}
+
+bool mac_top_tc3_fits(int C, int max_tile_targets, int64_t O, int64_t nq, int64_t ntiles, int nch) {
+  return C == TC_C && (nch == 1 || nch == 2) && max_tile_targets > 8 && max_tile_targets <= 128 && O > 0 &&
+         (O % 2) == 0 && O * 8 < (1 << 20) && ntiles > 0 && ntiles < 65536 && nq > 0 &&
+         [&] {
+           int r, l;
+           tc3_shape(O, nch, ntiles, nq, &r, &l);
+           return r > 0;
+         }();
+}
+
+bool launch_mac_top_tc3(const float2* const* Qh, float2* const* Rh, int nch, const float2* Kh, int64_t B, int C,
+                        int64_t O, int64_t nf, int64_t ntiles, int max_tile_targets, const int64_t* tgt_ptr,
+                        const int32_t* tgt, const int64_t* src_ptr, const int32_t* src, const int64_t* kidx_off,
+                        const int32_t* kidx, int64_t nq, int* err, cudaStream_t s) {
+  if (!mac_top_tc3_fits(C, max_tile_targets, O, nq, ntiles, nch) || nf <= 0) return false;
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return false;
+  int nrow = 0, lstg = 0;
+  tc3_shape(O, nch, ntiles, nq, &nrow, &lstg);
+  const int64_t kbytes = ((O * 8 + 1023) / 1024) * 1024;
+  const int64_t smem = tc3_smem_bytes(O, nch, ntiles, nq, nrow, lstg);
+  const unsigned grid = (unsigned)std::min<int64_t>(nf, nsm);
+  if (nch == 1) {
+    static SmemAttr attr;
+    smem_attr_once(k_mac_top_tc3<1>, (int)smem, attr.v);
+    k_mac_top_tc3<1><<<grid, T3_THREADS, (size_t)smem, s>>>(Qh[0], nullptr, Rh[0], nullptr, Kh, B, O, nf, ntiles,
+                                                            tgt_ptr, tgt, src_ptr, src, kidx_off, kidx, (int)kbytes,
+                                                            nrow, lstg, (int)nq, err);
+  } else {
+    static SmemAttr attr;
+    smem_attr_once(k_mac_top_tc3<2>, (int)smem, attr.v);
+    k_mac_top_tc3<2><<<grid, T3_THREADS, (size_t)smem, s>>>(Qh[0], Qh[1], Rh[0], Rh[1], Kh, B, O, nf, ntiles,
+                                                            tgt_ptr, tgt, src_ptr, src, kidx_off, kidx, (int)kbytes,
+                                                            nrow, lstg, (int)nq, err);
+  }
+  return true;
+}
 }  // namespace efie

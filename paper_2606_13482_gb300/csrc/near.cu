@@ -698,6 +698,102 @@ k_near_rows_df_g(const float4* __restrict__ M, const int64_t* __restrict__ blk_o
   }
 }
 
+// Full chunks of 8 right-hand sides: one thread per row with all 8 (the
+// matrix entry is loaded once for 8 double-float MACs), 128 threads per
+// (target box, chunk) block, and the source values staged in shared memory
+// 128 columns at a time with 16-byte asynchronous copies, double-buffered:
+// the next piece (source box, column block) is in flight while the current
+// one is multiplied, so a piece costs two barriers and no exposed load.
+constexpr int NDF_T = 128;
+constexpr int NDF_CH = 128;
+__device__ __forceinline__ void near_cp16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
+__global__ void __launch_bounds__(NDF_T)
+k_near_rows_df8(const float4* __restrict__ M, const int64_t* __restrict__ blk_off,
+                const int64_t* __restrict__ near_ptr, const int32_t* __restrict__ near_src,
+                const int64_t* __restrict__ box_ptr, const float4* __restrict__ x, double2* __restrict__ y,
+                int64_t ld, int nch) {
+  __shared__ __align__(16) float4 xs[2][8][NDF_CH];
+  const int xb = blockIdx.x / nch, tid = threadIdx.x;
+  x += (int64_t)(blockIdx.x % nch) * 8 * ld;
+  y += (int64_t)(blockIdx.x % nch) * 8 * ld;
+  const int64_t r0 = box_ptr[xb];
+  const int nrow = (int)(box_ptr[xb + 1] - r0);
+  const int64_t j0 = near_ptr[xb], j1 = near_ptr[xb + 1];
+  for (int ubase = 0; ubase < nrow; ubase += NDF_T) {
+    const int row = ubase + tid;
+    const bool ok = row < nrow;
+    DF re[8], im[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) re[q] = im[q] = DF{0.f, 0.f};
+    // pieces (source box j, first column cb) in near-list order; empty boxes skipped
+    int64_t ij = j0;
+    int icb = 0;
+    auto issue = [&](int buf) {
+      while (ij < j1 && box_ptr[near_src[ij] + 1] == box_ptr[near_src[ij]]) ++ij;
+      if (ij < j1) {
+        const int32_t yb = near_src[ij];
+        const int64_t c0 = box_ptr[yb];
+        const int ncol = (int)(box_ptr[yb + 1] - c0);
+        const int ncc = min(NDF_CH, ncol - icb);
+        for (int i = tid; i < 8 * ncc; i += NDF_T) {
+          const int r = i / ncc, cc = i - r * ncc;
+          near_cp16(&xs[buf][r][cc], x + r * ld + c0 + icb + cc);
+        }
+        icb += NDF_CH;
+        if (icb >= ncol) {
+          ++ij;
+          icb = 0;
+        }
+      }
+      asm volatile("cp.async.commit_group;\n" ::: "memory");
+    };
+    int64_t cj = j0;
+    int ccb = 0, buf = 0;
+    issue(0);
+    for (;;) {
+      while (cj < j1 && box_ptr[near_src[cj] + 1] == box_ptr[near_src[cj]]) ++cj;
+      if (cj >= j1) break;
+      issue(buf ^ 1);
+      asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+      __syncthreads();
+      const int32_t yb = near_src[cj];
+      const int ncol = (int)(box_ptr[yb + 1] - box_ptr[yb]);
+      const int ncc = min(NDF_CH, ncol - ccb);
+      if (ok) {
+        const float4* Mc = M + blk_off[cj] + (int64_t)ccb * nrow + row;
+        float4 a = Mc[0];
+        for (int cc = 0; cc < ncc; ++cc) {
+          const float4 an = Mc[(int64_t)(cc + 1 < ncc ? cc + 1 : cc) * nrow];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) df_cmac(re[q], im[q], a, xs[buf][q][cc]);
+          a = an;
+        }
+      }
+      __syncthreads();
+      ccb += NDF_CH;
+      if (ccb >= ncol) {
+        ++cj;
+        ccb = 0;
+      }
+      buf ^= 1;
+    }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    if (ok) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        double2* yp = y + q * ld + r0 + row;
+        double2 t = *yp;
+        *yp = make_double2(t.x + ((double)re[q].hi + (double)re[q].lo), t.y + ((double)im[q].hi + (double)im[q].lo));
+      }
+    }
+    __syncthreads();
+  }
+}
+
 void launch_split_df(double2* a, int64_t n, cudaStream_t s) {
   if (n <= 0) return;
   int64_t blocks = ceil_div(n, 256);
@@ -710,8 +806,11 @@ void launch_split_vec(const double2* x, float4* y, int64_t n, cudaStream_t s) {
   if (blocks > 152 * 64) blocks = 152 * 64;
   k_split_vec<<<(unsigned)blocks, 256, 0, s>>>(x, y, n);
 }
-// right-hand sides per unit: all of a 1-, 2- or 4-wide chunk; 4 for wider
-// chunks (two units per row, one unit per thread).  Full chunks of 8 run in
+// variant 0: full chunks of 8 through k_near_rows_df8, others through
+// k_near_rows_df; variant 1: k_near_rows_df_g; variant 2: k_near_rows_df
+// only.  k_near_rows_df: right-hand sides per unit: all of a 1-, 2- or
+// 4-wide chunk; 4 for wider chunks (two units per row, one unit per
+// thread).  Full chunks of 8 run in
 // one launch of (box, chunk) blocks with the chunks of a box adjacent, so
 // the blocks that read one block row of the matrix run together and the
 // matrix streams from DRAM about once for all right-hand sides; a last
@@ -729,6 +828,10 @@ void launch_near_spmv_df(const float4* M, const int64_t* blk_off, const int64_t*
     const float4* xr = x + (int64_t)r0 * ld;
     double2* yr = y + (int64_t)r0 * ld;
     const unsigned grid = (unsigned)(n_boxes * nch);
+    if (variant == 0 && cnt == 8) {
+      k_near_rows_df8<<<grid, NDF_T, 0, s>>>(M, blk_off, near_ptr, near_src, box_ptr, xr, yr, ld, nch);
+      continue;
+    }
     if (variant == 1) {
       if (cnt <= 2)
         k_near_rows_df_g<2><<<grid, NEAR_THREADS, 0, s>>>(M, blk_off, near_ptr, near_src, box_ptr, xr, yr, ld, cnt,

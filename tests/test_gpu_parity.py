@@ -214,12 +214,13 @@ def test_top_level_mixed_batched(G, two_level_oracle):
         assert _rel(Y[r], ref_op.matvec(X[r])) < TOL32
 
 
-@pytest.mark.parametrize("mac_variant", [0, 1, 2, 3])
+@pytest.mark.parametrize("mac_variant", [0, 1, 2, 3, 5])
 def test_top_level_translation_variants(G, two_level_oracle, mac_variant):
-    """The four top-level translation kernels the autotuner can pick (0: tensor
+    """The top-level translation kernels the autotuner can pick (0: tensor
     cores, 3-term TF32 split, persistent warp-specialised; 1: register tiles;
-    2: CUDA cores with shared-memory staging; 3: tensor cores, one CTA per tile
-    and frequency) against the oracle, mixed form."""
+    2: CUDA cores with shared-memory staging; 3: tensor cores, one CTA per
+    tile and frequency; 5: the persistent form fed by a loader warp) against
+    the oracle, mixed form."""
     torch = _torch()
     V, T, ref_op = two_level_oracle
     _, _, k, p, delta, levels = TWO_LEVEL
@@ -232,10 +233,12 @@ def test_top_level_translation_variants(G, two_level_oracle, mac_variant):
         assert _rel(Y[r], ref_op.matvec(X[r])) < TOL32
 
 
-@pytest.mark.parametrize("near_variant", [0, 1])
+@pytest.mark.parametrize("near_variant", [0, 1, 2])
 def test_near_field_variants_mixed(G, c1_gpu, c1_oracle, near_variant):
-    """Both double-float near-field kernels (x staged in shared memory; x read
-    through L1) against the FP64 oracle, with 8-, 3- and 1-vector chunks."""
+    """The double-float near-field kernels (x staged by double-buffered
+    asynchronous copies, 8 vectors per thread; x read through L1; x staged
+    between barriers, 4 vectors per thread) against the FP64 oracle, with
+    8-, 3- and 1-vector chunks."""
     torch = _torch()
     h64, h32 = c1_gpu
     X = E.complex_gaussian((12, h32.N), 8)

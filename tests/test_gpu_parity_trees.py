@@ -122,12 +122,12 @@ def test_three_levels_two_doublings(G, two_doublings):
     _check(G, V, T, k, p, delta, levels, ref_op, 50, n_rhs=8, cols=(0, 7), tag="two doublings")
 
 
-@pytest.mark.parametrize("mac_variant", [0, 1, 2, 3])
+@pytest.mark.parametrize("mac_variant", [0, 1, 2, 3, 5])
 def test_two_doublings_translation_variants(G, two_doublings, mac_variant):
-    """The four top-level translation kernels the autotuner can pick (tensor
-    cores persistent, register tiles, CUDA cores with shared-memory staging,
-    tensor cores per tile and frequency), mixed form, 8 vectors, against the
-    oracle."""
+    """The top-level translation kernels the autotuner can pick (tensor cores
+    persistent, register tiles, CUDA cores with shared-memory staging, tensor
+    cores per tile and frequency, tensor cores persistent and loader-fed),
+    mixed form, 8 vectors, against the oracle."""
     torch = _torch()
     V, T, k, p, delta, levels, ref_op = two_doublings
     h = G.EFIE(V, T, k, p, delta, levels, precision=G.EFIE_MIXED)
@@ -146,8 +146,9 @@ def test_two_doublings_chunk_pairs(G, two_doublings):
     """19 vectors in the mixed form: the first 16 go through the chunk-pair
     path (two chunks of 8 per tensor-core pass, 128-row B operands, N = 128
     MMAs) on every level: the top level's all-pairs tiles and the
-    interaction-list tiles of the two levels below it (variant 0), or the top
-    level only with the lower levels on CUDA cores (variant 4); the last 3
+    interaction-list tiles of the two levels below it (variant 0; variant 5,
+    the loader-fed kernel), or the top level
+    only with the lower levels on CUDA cores (variant 4); the last 3
     through the single-chunk path.  Both against the oracle, and against the
     CUDA-core translation (variant 2, one chunk at a time)."""
     torch = _torch()
@@ -159,15 +160,48 @@ def test_two_doublings_chunk_pairs(G, two_doublings):
         Y = h.matvec(Xd).cpu().numpy()
         h.autotune_set(8, 4)
         Y4 = h.matvec(Xd).cpu().numpy()
+        h.autotune_set(8, 5)
+        Y5 = h.matvec(Xd).cpu().numpy()
         h.autotune_set(8, 2)
         Y2 = h.matvec(Xd).cpu().numpy()
     finally:
         h.close()
     for r in (0, 7, 8, 15, 16, 18):
         ref = ref_op.matvec(X[r])
-        for tag, Yv in (("0", Y), ("4", Y4)):
+        for tag, Yv in (("0", Y), ("4", Y4), ("5", Y5)):
             rel, mx = _errs(Yv[r], ref)
             print(f"chunk pair variant {tag} rhs {r}: rel l2 {rel:.3e}, max-abs {mx:.3e}")
             assert rel < TOL32 and mx < 10 * TOL32, (tag, r, rel, mx)
     assert np.linalg.norm(Y - Y2) < 1e-5 * np.linalg.norm(Y2)
     assert np.linalg.norm(Y4 - Y2) < 1e-5 * np.linalg.norm(Y2)
+    assert np.linalg.norm(Y5 - Y2) < 1e-5 * np.linalg.norm(Y2)
+
+
+def test_two_doublings_transform_schedules(G, two_doublings):
+    """The three transform schedules (line passes; forward y and z passes
+    fused per (box, x-frequency) slab; forward and inverse fused) on all
+    three spline counts of the tree (s' = 9, 13, 21; FFT lengths 13, 21,
+    37), mixed form, 8 vectors: each against the oracle, and against the line
+    passes to FP32 rounding."""
+    torch = _torch()
+    V, T, k, p, delta, levels, ref_op = two_doublings
+    X = E.complex_gaussian((8, ref_op.mesh.N), 80)
+    Xd = torch.from_numpy(X).cuda()
+    h = G.EFIE(V, T, k, p, delta, levels, precision=G.EFIE_MIXED)
+    try:
+        assert h.transform_schedule() == 0
+        Y0 = h.matvec(Xd).cpu().numpy()
+        assert h.transform_schedule(1) == 1
+        Y1 = h.matvec(Xd).cpu().numpy()
+        assert h.transform_schedule(2) == 2
+        Y2 = h.matvec(Xd).cpu().numpy()
+    finally:
+        h.close()
+    for r in (0, 3, 7):
+        ref = ref_op.matvec(X[r])
+        for tag, Yv in (("lines", Y0), ("fused forward", Y1), ("fused both", Y2)):
+            rel, mx = _errs(Yv[r], ref)
+            print(f"transform schedule {tag} rhs {r}: rel l2 {rel:.3e}, max-abs {mx:.3e}")
+            assert rel < TOL32 and mx < 10 * TOL32, (tag, r, rel, mx)
+    assert np.linalg.norm(Y1 - Y0) < 1e-6 * np.linalg.norm(Y0)
+    assert np.linalg.norm(Y2 - Y0) < 1e-6 * np.linalg.norm(Y0)

@@ -215,6 +215,9 @@ def test_invalid_inputs(lib):
     assert L.efie_matvec_host(None, x, x, 1, None) == G.EFIE_EINVAL
     assert L.efie_setup_times(None, x, 4, None) == G.EFIE_EINVAL
     assert L.efie_launch_count(None, None) == G.EFIE_EINVAL
+    assert L.efie_transform_schedule_set(None, 0) == G.EFIE_EINVAL
+    sched = ctypes.c_int(-1)
+    assert L.efie_transform_schedule_get(None, ctypes.byref(sched)) == G.EFIE_EINVAL and sched.value == -1
 
 
 def test_setup_without_gpu_fails_loudly(lib):
