@@ -130,6 +130,11 @@ struct LevDev {
   int32_t *tct_tgt = nullptr, *tct_src = nullptr, *tct_kidx = nullptr;
   int64_t *tile_tgt_ptr = nullptr, *tile_src_ptr = nullptr, *tile_kidx_off = nullptr;
   int32_t *tile_tgt = nullptr, *tile_src = nullptr, *tile_kidx = nullptr;
+  // the same index tiles for the persistent tensor-core kernel: int16 ids in
+  // chunk-major blocks [chunk of 16 sources][tpad targets][16] per tile (null
+  // where an id does not fit in int16)
+  int64_t *tile_k16_off = nullptr, *tct_k16_off = nullptr;
+  int16_t *tile_k16 = nullptr, *tct_k16 = nullptr;
   // sibling-shared transfers between this (child) level and its parents:
   // g1 = (parent, b_x, b_y) groups of children, g2 = (parent, b_x) groups
   int64_t ng1 = 0, ng2 = 0;
@@ -677,7 +682,7 @@ void run_mac(efie_handle* h, FarSet<R>& F, int ell, int C, const cpx_t<R>* Qin, 
       const bool autov = h->mac_variant == 0 || h->mac_variant == 4;
       const bool tc3 = sizeof(R) == 4 && h->mac_variant == 5 &&
                        mac_top_tc3_fits(C, LD.max_tile, LD.O, LD.nq, LD.ntiles, 1);
-      const bool tc2 = sizeof(R) == 4 && (autov || h->mac_variant == 5) && !tc3 &&
+      const bool tc2 = sizeof(R) == 4 && (autov || h->mac_variant == 5) && !tc3 && LD.tile_k16 &&
                        mac_top_tc2_fits(C, LD.max_tile, LD.O, LD.nq, LD.ntiles, 1);
       const bool tc = sizeof(R) == 4 && (autov || h->mac_variant == 3) &&
                       mac_top_tc_fits(C, LD.max_tile, LD.O);
@@ -691,7 +696,7 @@ void run_mac(efie_handle* h, FarSet<R>& F, int ell, int C, const cpx_t<R>* Qin, 
                                         LD.tile_kidx_off, LD.tile_kidx, LD.nq, h->err_dev, s)
                    : launch_mac_top_tc2(qv, rv, 1, (const float2*)FL.Kh, B, C, LD.O, n3, LD.ntiles, LD.max_tile,
                                         LD.tile_tgt_ptr, LD.tile_tgt, LD.tile_src_ptr, LD.tile_src,
-                                        LD.tile_kidx_off, LD.tile_kidx, LD.nq, h->err_dev, s);
+                                        LD.tile_k16_off, LD.tile_k16, LD.nq, h->err_dev, s);
       }
       if (done) cuda_check(cudaPeekAtLastError(), "top-level translation (persistent tensor-core kernel)");
       if (!done && tc)
@@ -829,7 +834,7 @@ bool pair_fits(efie_handle* h) {
     return false;
   const LevDev& LD = h->lev[0];
   return LD.nfar > 0 && (mac_top_tc3_fits(32, LD.max_tile, LD.O, LD.nq, LD.ntiles, 2) ||
-                         mac_top_tc2_fits(32, LD.max_tile, LD.O, LD.nq, LD.ntiles, 2));
+                         (LD.tile_k16 && mac_top_tc2_fits(32, LD.max_tile, LD.O, LD.nq, LD.ntiles, 2)));
 }
 
 // The translation of level ell for both chunks of a pair (spectra Qa, Qb ->
@@ -848,18 +853,25 @@ void run_mac_pair(efie_handle* h, int ell, const float2* Qa, const float2* Qb, f
   const int mx = top ? LD.max_tile : LD.tct_max;
   const bool il_tc = top || h->mac_variant == 0 || h->mac_variant == 5;
   const bool use3 = h->mac_variant == 5 && nt > 0 && mac_top_tc3_fits(32, mx, LD.O, nq, nt, 2);
-  const bool use2 = !use3 && nt > 0 && mac_top_tc2_fits(32, mx, LD.O, nq, nt, 2);
+  const int16_t* k16 = top ? LD.tile_k16 : LD.tct_k16;
+  const bool use2 = !use3 && nt > 0 && k16 && mac_top_tc2_fits(32, mx, LD.O, nq, nt, 2);
   if (il_tc && (use3 || use2)) {
     KScope ks(h, top ? K_MAC_TOP_TC : K_MAC_TC, s, 1);
     const float2* qv[2] = {Qa, Qb};
     float2* rv[2] = {Ra, Rb};
-    auto launch = use3 ? launch_mac_top_tc3 : launch_mac_top_tc2;
-    const bool ok = top ? launch(qv, rv, 2, F.lv[ell - P.top].Kh, B, 32, LD.O, n * n * n, nt, mx, LD.tile_tgt_ptr,
-                                 LD.tile_tgt, LD.tile_src_ptr, LD.tile_src, LD.tile_kidx_off, LD.tile_kidx, nq,
-                                 h->err_dev, s)
-                        : launch(qv, rv, 2, F.lv[ell - P.top].Kh, B, 32, LD.O, n * n * n, nt, mx, LD.tct_tgt_ptr,
-                                 LD.tct_tgt, LD.tct_src_ptr, LD.tct_src, LD.tct_kidx_off, LD.tct_kidx, nq,
-                                 h->err_dev, s);
+    const float2* Kh = F.lv[ell - P.top].Kh;
+    const int64_t nf = n * n * n;
+    bool ok;
+    if (use3)
+      ok = top ? launch_mac_top_tc3(qv, rv, 2, Kh, B, 32, LD.O, nf, nt, mx, LD.tile_tgt_ptr, LD.tile_tgt,
+                                    LD.tile_src_ptr, LD.tile_src, LD.tile_kidx_off, LD.tile_kidx, nq, h->err_dev, s)
+               : launch_mac_top_tc3(qv, rv, 2, Kh, B, 32, LD.O, nf, nt, mx, LD.tct_tgt_ptr, LD.tct_tgt,
+                                    LD.tct_src_ptr, LD.tct_src, LD.tct_kidx_off, LD.tct_kidx, nq, h->err_dev, s);
+    else
+      ok = top ? launch_mac_top_tc2(qv, rv, 2, Kh, B, 32, LD.O, nf, nt, mx, LD.tile_tgt_ptr, LD.tile_tgt,
+                                    LD.tile_src_ptr, LD.tile_src, LD.tile_k16_off, LD.tile_k16, nq, h->err_dev, s)
+               : launch_mac_top_tc2(qv, rv, 2, Kh, B, 32, LD.O, nf, nt, mx, LD.tct_tgt_ptr, LD.tct_tgt,
+                                    LD.tct_src_ptr, LD.tct_src, LD.tct_k16_off, LD.tct_k16, nq, h->err_dev, s);
     if (!ok) throw EfieError{EFIE_ECUDA, "internal: chunk-pair translation does not apply"};
     cuda_check(cudaPeekAtLastError(), "translation (chunk pair, tensor cores)");
     return;
@@ -949,6 +961,35 @@ void do_matvec(efie_handle* h, const double2* x, int64_t ldx, double2* y, double
 }
 
 // ------------------------------------------------------------- setup
+// Index tiles (offset ids [source][tpad] per tile, -1 for excluded pairs)
+// re-laid out for the persistent tensor-core kernel: per tile, per chunk of
+// 16 sources, per target row the 16 ids as int16 (padded with -1), so that a
+// producer thread reads its row of a chunk as two 16-byte words.  off[t] is
+// the tile's first entry.  Returns false when an id exceeds int16.
+bool make_index16(const std::vector<int64_t>& tgt_ptr, const std::vector<int64_t>& src_ptr,
+                  const std::vector<int64_t>& kidx_off, const std::vector<int32_t>& kidx,
+                  std::vector<int16_t>& out, std::vector<int64_t>& off) {
+  const int64_t nt = (int64_t)tgt_ptr.size() - 1;
+  off.assign(nt + 1, 0);
+  for (int64_t t = 0; t < nt; ++t) {
+    const int64_t tpad = ((tgt_ptr[t + 1] - tgt_ptr[t] + 7) / 8) * 8;
+    const int64_t nch = (src_ptr[t + 1] - src_ptr[t] + 15) / 16;
+    off[t + 1] = off[t] + nch * tpad * 16;
+  }
+  out.assign(off[nt], (int16_t)-1);
+  for (int64_t t = 0; t < nt; ++t) {
+    const int64_t tpad = ((tgt_ptr[t + 1] - tgt_ptr[t] + 7) / 8) * 8;
+    const int64_t ns = src_ptr[t + 1] - src_ptr[t];
+    for (int64_t j = 0; j < ns; ++j)
+      for (int64_t r = 0; r < tpad; ++r) {
+        const int32_t id = kidx[kidx_off[t] + j * tpad + r];
+        if (id > 32767) return false;
+        out[off[t] + ((j / 16) * tpad + r) * 16 + (j % 16)] = (int16_t)id;
+      }
+  }
+  return true;
+}
+
 void setup_impl(efie_handle* h, const efie_mesh* mesh, double k, int p, double grid_spacing, int levels) {
   check_mesh(mesh);
   int ndev = 0;
@@ -1146,6 +1187,14 @@ void setup_impl(efie_handle* h, const efie_mesh* mesh, double k, int p, double g
         LD.tct_max = std::max<int>(LD.tct_max, (int)(L.tct_tgt_ptr[t + 1] - L.tct_tgt_ptr[t]));
         if (LD.tct_nq >= 0) LD.tct_nq = ns > 65536 ? -1 : LD.tct_nq + (ns + 15) / 16;
       }
+      {
+        std::vector<int16_t> k16;
+        std::vector<int64_t> k16_off;
+        if (make_index16(L.tct_tgt_ptr, L.tct_src_ptr, L.tct_kidx_off, L.tct_kidx, k16, k16_off)) {
+          LD.tct_k16 = M.upload(k16);
+          LD.tct_k16_off = M.upload(k16_off);
+        }
+      }
       LD.tct_tgt_ptr = M.upload(L.tct_tgt_ptr);
       LD.tct_src_ptr = M.upload(L.tct_src_ptr);
       LD.tct_kidx_off = M.upload(L.tct_kidx_off);
@@ -1155,6 +1204,14 @@ void setup_impl(efie_handle* h, const efie_mesh* mesh, double k, int p, double g
     }
     for (int64_t t = 0; t < LD.ntiles; ++t)
       LD.max_tile = std::max<int>(LD.max_tile, (int)(L.tile_tgt_ptr[t + 1] - L.tile_tgt_ptr[t]));
+    if (LD.ntiles > 0) {
+      std::vector<int16_t> k16;
+      std::vector<int64_t> k16_off;
+      if (make_index16(L.tile_tgt_ptr, L.tile_src_ptr, L.tile_kidx_off, L.tile_kidx, k16, k16_off)) {
+        LD.tile_k16 = M.upload(k16);
+        LD.tile_k16_off = M.upload(k16_off);
+      }
+    }
     LD.tile_tgt_ptr = M.upload(L.tile_tgt_ptr);
     LD.tile_src_ptr = M.upload(L.tile_src_ptr);
     LD.tile_kidx_off = M.upload(L.tile_kidx_off);

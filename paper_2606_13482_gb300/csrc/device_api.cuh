@@ -116,7 +116,7 @@ bool mac_top_tc2_fits(int C, int max_tile_targets, int64_t O, int64_t nq, int64_
 bool launch_mac_top_tc2(const float2* const* Qh, float2* const* Rh, int nch, const float2* Kh, int64_t B, int C,
                         int64_t O, int64_t nf, int64_t ntiles, int max_tile_targets, const int64_t* tgt_ptr,
                         const int32_t* tgt, const int64_t* src_ptr, const int32_t* src, const int64_t* kidx_off,
-                        const int32_t* kidx, int64_t nq, int* err, cudaStream_t s);
+                        const int16_t* kidx, int64_t nq, int* err, cudaStream_t s);
 // the same contract, fed by a loader warp (TMA bulk copies of index blocks,
 // source spectra and kernel rows into shared-memory stages)
 bool mac_top_tc3_fits(int C, int max_tile_targets, int64_t O, int64_t nq, int64_t ntiles, int nch);

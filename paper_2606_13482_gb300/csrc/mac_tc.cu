@@ -450,7 +450,7 @@ __global__ void __maxnreg__(128)
                   int64_t O, int64_t nf, int64_t ntiles, const int64_t* __restrict__ tgt_ptr,
                   const int32_t* __restrict__ tgt, const int64_t* __restrict__ src_ptr,
                   const int32_t* __restrict__ src, const int64_t* __restrict__ kidx_off,
-                  const int32_t* __restrict__ kidx, int kbytes, int nq_cap, int* err) {
+                  const int16_t* __restrict__ kidx, int kbytes, int nq_cap, int* err) {
   extern __shared__ __align__(1024) unsigned char t2_smem[];
   __shared__ T2Bar bar;
   unsigned char* rows = t2_smem;
@@ -510,43 +510,73 @@ __global__ void __maxnreg__(128)
     const int jB = (warp & 3) * 4 + (lane >> 3), chB = lane & 7;
     const int boff = (jB >> 2) * TC_LBO + (jB & 3) * 4 + chB * 16;
     const int nq32 = (int)nq;
-    int32_t idn[TC_KC];
     float2 qn[4 * NCH];
-    // loads of chunk (k, q): the index rows of this thread's target, the source spectra
-    auto load = [&](int64_t k, int q) {
+    // Loads run ahead of use: the index words of a chunk two chunks ahead,
+    // the source box of this thread's B row one chunk ahead of the spectra
+    // that depend on it, the spectra one chunk ahead.
+    // index words of chunk (k, q): its 16 sources of target row r, int16,
+    // packed two per word (the block [chunk][tpad][16] of the tile)
+    auto load_k = [&](int64_t k, int q, uint32_t (&w)[TC_KC / 2]) {
 #pragma unroll
-      for (int j = 0; j < TC_KC; ++j) idn[j] = -1;
-#pragma unroll
-      for (int u = 0; u < 4 * NCH; ++u) qn[u] = make_float2(0.f, 0.f);
+      for (int i = 0; i < TC_KC / 2; ++i) w[i] = 0xFFFFFFFFu;
       if (k >= K) return;
       const uint32_t e = ctab[q];
       const T2Tile& T = tiles[e >> 16];
       const int j0 = (int)(e & 0xFFFFu);
       if (r < T.tpad) {
-        const int32_t* kb = kidx + T.koff + (int64_t)j0 * T.tpad + r;
-#pragma unroll
-        for (int j = 0; j < TC_KC; ++j)
-          if (j0 + j < T.ns) idn[j] = __ldg(kb + j * T.tpad);
-      }
-      if (j0 + jB < T.ns) {
-        const int64_t y = __ldg(src + T.s0 + j0 + jB);
-        const int64_t o = ((int64_t)(blockIdx.x + k * gridDim.x) * B + y) * TC_C + chB;
-#pragma unroll
-        for (int u = 0; u < 4; ++u) qn[u] = __ldg(Qh0 + o + 8 * u);
-        if (NCH == 2) {
-#pragma unroll
-          for (int u = 0; u < 4; ++u) qn[4 + u] = __ldg(Qh1 + o + 8 * u);
-        }
+        const uint4* kb = reinterpret_cast<const uint4*>(kidx + T.koff + ((int64_t)(j0 / TC_KC) * T.tpad + r) * TC_KC);
+        const uint4 a = __ldg(kb), b = __ldg(kb + 1);
+        w[0] = a.x, w[1] = a.y, w[2] = a.z, w[3] = a.w, w[4] = b.x, w[5] = b.y, w[6] = b.z, w[7] = b.w;
       }
     };
-    // this warpgroup's chunks g = wg, wg + 2, ... as (frequency k, chunk q)
+    // source box of this thread's B row in chunk (k, q), or -1
+    auto load_src = [&](int64_t k, int q) -> int32_t {
+      if (k >= K) return -1;
+      const uint32_t e = ctab[q];
+      const T2Tile& T = tiles[e >> 16];
+      const int j0 = (int)(e & 0xFFFFu);
+      return j0 + jB < T.ns ? __ldg(src + T.s0 + j0 + jB) : -1;
+    };
+    auto load_q = [&](int64_t k, int32_t y) {
+#pragma unroll
+      for (int u = 0; u < 4 * NCH; ++u) qn[u] = make_float2(0.f, 0.f);
+      if (k >= K || y < 0) return;
+      const int64_t o = ((int64_t)(blockIdx.x + k * gridDim.x) * B + y) * TC_C + chB;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) qn[u] = __ldg(Qh0 + o + 8 * u);
+      if (NCH == 2) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) qn[4 + u] = __ldg(Qh1 + o + 8 * u);
+      }
+    };
+    // this warpgroup's chunks g = wg, wg + 2, ... as (frequency k, chunk q):
+    // (kn, qn_) the next one, (kn2, qn2) the one after it
+    auto advance = [&](int64_t& kk, int& qq) {
+      qq += 2;
+      while (qq >= nq32) {
+        qq -= nq32;
+        ++kk;
+      }
+    };
     int64_t kn = 0;
     int qn_ = wg;
     while (qn_ >= nq32 && nq32 > 0) {
       qn_ -= nq32;
       ++kn;
     }
-    if (nq32 > 0) load(kn, qn_);
+    int64_t kn2 = kn;
+    int qn2 = qn_;
+    uint32_t kwA[TC_KC / 2], kwB[TC_KC / 2];
+    int32_t yB = -1;
+#pragma unroll
+    for (int i = 0; i < TC_KC / 2; ++i) kwA[i] = kwB[i] = 0xFFFFFFFFu;
+    if (nq32 > 0) {
+      load_k(kn, qn_, kwA);
+      load_q(kn, load_src(kn, qn_));
+      advance(kn2, qn2);
+      load_k(kn2, qn2, kwB);
+      yB = load_src(kn2, qn2);
+    }
     int64_t g = wg;
     bool ok = true;
     for (int64_t k = 0; k < K && ok; ++k) {
@@ -558,15 +588,17 @@ __global__ void __maxnreg__(128)
         int32_t idc[TC_KC];
         float2 qc[4 * NCH];
 #pragma unroll
-        for (int j = 0; j < TC_KC; ++j) idc[j] = idn[j];
+        for (int j = 0; j < TC_KC; ++j) idc[j] = (int32_t)(int16_t)(kwA[j >> 1] >> ((j & 1) * 16));
 #pragma unroll
         for (int u = 0; u < 4 * NCH; ++u) qc[u] = qn[u];
-        qn_ += 2;
-        while (qn_ >= nq32) {
-          qn_ -= nq32;
-          ++kn;
-        }
-        load(kn, qn_);
+        // chunk after this one: index words already here, spectra now; the
+        // one after that: index words and source box now
+#pragma unroll
+        for (int i = 0; i < TC_KC / 2; ++i) kwA[i] = kwB[i];
+        load_q(kn2, yB);
+        advance(kn2, qn2);
+        load_k(kn2, qn2, kwB);
+        yB = load_src(kn2, qn2);
         const uint32_t gu = (uint32_t)g;
         const int slot = (int)(gu % Cfg::STG);
         if (gu >= (uint32_t)Cfg::STG) {
@@ -1132,7 +1164,9 @@ bool launch_mac_top_tc(const float2* Qh, float2* Rh, const float2* Kh, int64_t B
 
 // The persistent kernel takes tiles of at most 128 targets with any source
 // lists, 32 channels per chunk, an even number of offsets (kernel rows are
-// copied by TMA in 16-byte units), and shared memory for two kernel rows, the
+// copied by TMA in 16-byte units) below 32,768 (offset ids are read as int16
+// from the chunk-major index blocks [chunk][tpad][16] of make_index16), and
+// shared memory for two kernel rows, the
 // B stages and the tile and chunk tables (nq = sum over tiles of
 // ceil(sources / 16); at most 65,536 sources per tile, as a chunk-table entry
 // holds tile and first source in 16 bits each).  Returns false when it does
@@ -1147,6 +1181,7 @@ static int64_t tc2_smem_bytes(int64_t O, int nch, int64_t ntiles, int64_t nq) {
 
 bool mac_top_tc2_fits(int C, int max_tile_targets, int64_t O, int64_t nq, int64_t ntiles, int nch) {
   return C == TC_C && (nch == 1 || nch == 2) && max_tile_targets > 8 && max_tile_targets <= 128 && O > 0 &&
+         O <= 32767 &&
          (O % 2) == 0 && ntiles > 0 && ntiles < 65536 && nq > 0 && tc2_smem_bytes(O, nch, ntiles, nq) <= 220 * 1024;
 }
 
@@ -1155,7 +1190,7 @@ bool mac_top_tc2_fits(int C, int max_tile_targets, int64_t O, int64_t nq, int64_
 bool launch_mac_top_tc2(const float2* const* Qh, float2* const* Rh, int nch, const float2* Kh, int64_t B, int C,
                         int64_t O, int64_t nf, int64_t ntiles, int max_tile_targets, const int64_t* tgt_ptr,
                         const int32_t* tgt, const int64_t* src_ptr, const int32_t* src, const int64_t* kidx_off,
-                        const int32_t* kidx, int64_t nq, int* err, cudaStream_t s) {
+                        const int16_t* kidx, int64_t nq, int* err, cudaStream_t s) {
   if (!mac_top_tc2_fits(C, max_tile_targets, O, nq, ntiles, nch) || nf <= 0) return false;
   int dev = 0, nsm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
