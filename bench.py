@@ -58,6 +58,7 @@ FP32_LANES_PER_SM = 128
 FP64_TFLOPS_NOMINAL = 1.25
 TF32_PER_BF16 = 1.1 / 2.25
 TF32_SPLIT_TERMS = 3      # a_hi b_hi + a_hi b_lo + a_lo b_hi per FP32-accurate product
+DF_INSTR_PER_CMAC = 48     # FP32 instructions of one double-float complex multiply-add (near field)
 
 
 def fp32_peak_tflops(sm_max_mhz):
@@ -66,10 +67,16 @@ def fp32_peak_tflops(sm_max_mhz):
     return sms * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12, sms
 
 
-# DRAM bytes per launch of the dominant kernel from a one-pass ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum) of the same workload, keyed by
-# (workload, kernel class); an entry holds only while that kernel is unchanged.
-NCU_DRAM_BYTES_PER_LAUNCH = {}
+# DRAM bytes per launch of the class's main kernel from a one-pass ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum) of this bench command on the
+# same workload, keyed by (workload, kernel class); an entry holds only while
+# that kernel is unchanged.  near_A: the k_near_rows_df8 launch of the A part
+# (all 64 right-hand sides); translation_mac_top_tc: one top-level
+# k_mac_top_tc2<2> launch (one chunk pair).
+NCU_DRAM_BYTES_PER_LAUNCH = {
+    ("sphere20", "near_A"): 174.96e9 + 1.25e9,
+    ("sphere20", "translation_mac_top_tc"): 24.75e9 + 18.84e9,
+}
 
 
 class ClockSampler:
@@ -270,6 +277,11 @@ def run_ours(args, w, rank, world, local_rank):
         if name in ("translation_mac_top_tc", "translation_mac_tc"):
             return ("tensor", tf32_pk, f"{psrc} BF16 burst {peaks['bf16_tflops']:.1f} TFLOP/s x 1.1/2.25 "
                     f"(TF32/BF16 nominal) / {TF32_SPLIT_TERMS} split terms (FP32-accurate products)")
+        if mixed and name in ("near_A", "near_V"):
+            # double-float near field: 48 FP32 instructions per complex MAC (8 algorithmic flops)
+            return ("alu", fp32_pk / 2.0 * 8.0 / DF_INSTR_PER_CMAC,
+                    f"{n_sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_max:.0f} MHz instruction issue / "
+                    f"{DF_INSTR_PER_CMAC} FP32 instructions per double-float complex MAC x 8 flops")
         if mixed:
             return ("alu", fp32_pk, f"{n_sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flops x {sm_max:.0f} MHz")
         return ("alu", FP64_TFLOPS_NOMINAL, "NVIDIA nominal FP64 (non-tensor) rate of GB300")

@@ -47,6 +47,13 @@ extern "C" {
 #define EFIE_MIXED 1            /* far field in complex FP32; near field, projector
                                    construction, Arnoldi and true residual in FP64 */
 
+#define EFIE_FACT_STAR 0        /* star-based factorization (Sec. VI-A): RWG moments for the
+                                   vector part, pulse moments of the charges for the scalar
+                                   part, near A on RWG pairs and V on triangle pairs */
+#define EFIE_FACT_DIRECT 1      /* direct factorization (Sec. VI-B): RWG and RWG-divergence
+                                   moments in the RWG's leaf box, one near set of RWG pairs
+                                   holding A and Phi = Sigma V Sigma^T */
+
 #define EFIE_PRECOND_NONE 0
 #define EFIE_PRECOND_LEARNED 1  /* learned mesh-local FGMRES preconditioner (not in
                                    the paper); falls back to NONE when unusable */
@@ -72,6 +79,7 @@ typedef struct {
     const char *weights_path;/* learned preconditioner weights, or NULL */
     int64_t device_mem_limit;/* bytes; 0 -> no limit beyond the device */
     uint64_t seed;
+    int32_t factorization;   /* EFIE_FACT_STAR (default) or EFIE_FACT_DIRECT */
 } efie_options;
 
 /* Per-level summary filled by efie_plan / efie_level_info. */
@@ -89,10 +97,13 @@ typedef struct {
     int64_t n_unknowns, n_triangles;
     int32_t depth, top_level, n_levels, p;
     double root_lo[3], root_edge;
-    int64_t near_nnz_A, near_nnz_V;
+    int64_t near_nnz_A, near_nnz_V;  /* near entries of A and of the scalar part (V on triangle
+                                       pairs; Phi on A's RWG pairs for a direct-factorization
+                                       handle) */
     int64_t device_bytes;    /* estimated resident device bytes of the setup products */
     int64_t moment_entries_rwg;  /* leaf moment entries of all RWGs, per vector component */
-    int64_t moment_entries_tri;  /* leaf moment entries of all triangles (charge part) */
+    int64_t moment_entries_tri;  /* leaf moment entries of the scalar part: triangles (star),
+                                    RWG divergences (direct handle) */
 } efie_plan_info_t;
 
 typedef struct {
@@ -210,8 +221,14 @@ int efie_plan_moments(const efie_mesh *mesh, double wavenumber, int spline_degre
 /* Build every setup product on the current device: geometry, octree,
  * transfers, projectors, exact moments, kernel spectra per level and
  * offset, and the FP64 near field (Sec. VI-A: RWG pairs for A and triangle
- * pairs for V, each in adjacent leaf boxes).  opt may be NULL (defaults).
- * On success *out owns all device memory until efie_destroy. */
+ * pairs for V, each in adjacent leaf boxes).  With opt->factorization =
+ * EFIE_FACT_DIRECT (Sec. VI-B) the scalar part is anterpolated from the
+ * divergence moments of every RWG in its own leaf box and interpolated back
+ * onto them, and its near field Phi = Sigma V Sigma^T is assembled on the
+ * RWG pairs of A's blocks (from the same triangle-pair integrals); products,
+ * solves and the (A x, Phi x) split of efie_matvec_parts follow.  opt may be
+ * NULL (defaults).  EFIE_EINVAL for an unknown factorization.  On success
+ * *out owns all device memory until efie_destroy. */
 int efie_setup(const efie_mesh *mesh, double wavenumber, int spline_degree,
                double grid_spacing, int levels, const efie_options *opt,
                efie_handle **out);

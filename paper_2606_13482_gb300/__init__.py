@@ -14,12 +14,14 @@ import os
 import numpy as np
 
 __all__ = ["load_library", "Options", "EFIE", "Batch", "plan", "plan_matrix", "EfieError",
-           "EFIE_FP64", "EFIE_MIXED", "EFIE_PRECOND_NONE", "EFIE_PRECOND_LEARNED",
+           "EFIE_FP64", "EFIE_MIXED", "EFIE_PRECOND_NONE", "EFIE_PRECOND_LEARNED", "EFIE_FACT_STAR",
+           "EFIE_FACT_DIRECT",
            "EXPORTED_SYMBOLS"]
 
 EFIE_OK, EFIE_EINVAL, EFIE_ENOMEM, EFIE_ECUDA, EFIE_ETIMEOUT, EFIE_NOT_CONVERGED = 0, -1, -2, -3, -4, 1
 EFIE_FP64, EFIE_MIXED = 0, 1
 EFIE_PRECOND_NONE, EFIE_PRECOND_LEARNED = 0, 1
+EFIE_FACT_STAR, EFIE_FACT_DIRECT = 0, 1
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libefie_gb300.so")
@@ -54,7 +56,7 @@ class Options(ctypes.Structure):
                 ("gmres_restart", ctypes.c_int32), ("max_iters", ctypes.c_int32),
                 ("precond", ctypes.c_int32), ("rhs_chunk", ctypes.c_int32),
                 ("weights_path", ctypes.c_char_p), ("device_mem_limit", ctypes.c_int64),
-                ("seed", ctypes.c_uint64)]
+                ("seed", ctypes.c_uint64), ("factorization", ctypes.c_int32)]
 
 
 class LevelInfo(ctypes.Structure):

@@ -234,6 +234,13 @@ struct efie_handle {
   int32_t *d_rwg_perm = nullptr, *d_rwg_box = nullptr, *d_tri_box = nullptr, *d_rwg_tri_sorted = nullptr;
   int64_t *d_box_rwg_ptr = nullptr, *d_box_tri_ptr = nullptr;
   int32_t* d_tri_rwg = nullptr;
+  // scalar (charge) part of the factorization: star (Sec. VI-A) pulses on the
+  // triangles, or direct (Sec. VI-B) divergence moments of the RWGs
+  bool direct = false;
+  int64_t n_sc = 0;                  // scalar items: triangles (star) or RWGs (direct)
+  const int64_t* d_sc_box_ptr = nullptr;  // items of each leaf box
+  const int32_t* d_sc_box = nullptr;      // leaf box of each item
+  const int64_t* d_blkS_off = nullptr;    // near blocks of the scalar part (V, or Phi in A's layout)
   int8_t* d_tri_sgn = nullptr;
   // moments structure (shared by precisions)
   int32_t *mr_base = nullptr, *mr_ext = nullptr, *mt_base = nullptr, *mt_ext = nullptr;
@@ -351,7 +358,8 @@ void build_far(efie_handle* h, FarSet<R>& F, cudaStream_t s) {
         for (int d = 0; d < 3; ++d) mr[o + 3 * e + d] = (R)MB.data[o + d * ne + e];
     }
   }
-  std::vector<R> mt(P.mom_tri.data.begin(), P.mom_tri.data.end());
+  const MomentBlocks& MS = h->direct ? P.mom_div : P.mom_tri;   // scalar-part moments
+  std::vector<R> mt(MS.data.begin(), MS.data.end());
   F.mr = M.upload(mr);
   F.mt = M.upload(mt);
   {
@@ -364,7 +372,7 @@ void build_far(efie_handle* h, FarSet<R>& F, cudaStream_t s) {
     F.gr = M.alloc<R>((int64_t)mr.size() / 3 * 4);
     F.gt = M.alloc<R>((int64_t)mt.size() * 2);
     launch_gather_build<R>(F.mr, h->mr_base, h->mr_ext, h->mr_off, F.mt, h->mt_base, h->mt_ext, h->mt_off,
-                           h->d_box_rwg_ptr, h->d_box_tri_ptr, B, L.sp, h->gptr_r, h->gptr_t, F.gr, F.gt, s);
+                           h->d_box_rwg_ptr, h->d_sc_box_ptr, B, L.sp, h->gptr_r, h->gptr_t, F.gr, F.gt, s);
     cuda_check(cudaGetLastError(), "gather lists");
   }
   F.lv.assign(P.lv.size(), {});
@@ -498,9 +506,9 @@ void ensure_work(efie_handle* h, int Rw) {
   h->xs = h->mem.alloc<double2>(N * Rw);
   h->yA = h->mem.alloc<double2>(N * Rw);
   h->rho = h->mem.alloc<double2>(Nt * Rw);
-  h->w = h->mem.alloc<double2>(Nt * Rw);
+  h->w = h->mem.alloc<double2>(h->n_sc * Rw);
   h->yAn = h->mem.alloc<double2>(N * Rw);
-  h->wn = h->mem.alloc<double2>(Nt * Rw);
+  h->wn = h->mem.alloc<double2>(h->n_sc * Rw);
   if (h->near_df) {
     h->xs4 = h->mem.alloc<float4>(N * Rw);
     h->rho4 = h->mem.alloc<float4>(Nt * Rw);
@@ -561,16 +569,19 @@ void anterp_up(efie_handle* h, FarSet<R>& F, int nr, int rhs0, std::vector<cpx_t
   {
     const Level& L = P.L(D);
     const cpx_t<R>* xin = (const cpx_t<R>*)(h->xs + (int64_t)rhs0 * N);
-    const cpx_t<R>* rin = (const cpx_t<R>*)(h->rho + (int64_t)rhs0 * Nt);
-    KScope ks(h, K_ANTERP, s, sizeof(R) == 4 ? 3 : 1);
+    // scalar part: the charges (star) or the currents themselves (direct)
+    const cpx_t<R>* rin = h->direct ? xin : (const cpx_t<R>*)(h->rho + (int64_t)rhs0 * Nt);
+    KScope ks(h, K_ANTERP, s, sizeof(R) == 4 ? (h->direct ? 2 : 3) : 1);
     if (sizeof(R) == 4) {
       launch_convert<R>(h->xs + (int64_t)rhs0 * N, (cpx_t<R>*)(h->xsf + (int64_t)rhs0 * N), N * nr, s);
-      launch_convert<R>(h->rho + (int64_t)rhs0 * Nt, (cpx_t<R>*)(h->rhof + (int64_t)rhs0 * Nt), Nt * nr, s);
+      if (!h->direct)
+        launch_convert<R>(h->rho + (int64_t)rhs0 * Nt, (cpx_t<R>*)(h->rhof + (int64_t)rhs0 * Nt), Nt * nr, s);
       xin = (const cpx_t<R>*)(h->xsf + (int64_t)rhs0 * N);
-      rin = (const cpx_t<R>*)(h->rhof + (int64_t)rhs0 * Nt);
+      rin = h->direct ? xin : (const cpx_t<R>*)(h->rhof + (int64_t)rhs0 * Nt);
     }
     launch_anterp<R>(F.gr, F.gt, h->gptr_r, h->gptr_t, h->mr_off, h->mt_off, h->d_box_rwg_ptr,
-                     h->d_box_tri_ptr, (int64_t)L.code.size(), xin, N, rin, Nt, nr, qq[D - top], L.sp, s);
+                     h->d_sc_box_ptr, (int64_t)L.code.size(), xin, N, rin, h->direct ? N : Nt, nr, qq[D - top],
+                     L.sp, s);
   }
   // upward transfers (Sec. IV-B), shared among siblings one axis at a time (z, y, x)
   for (int ell = D; ell > top; --ell) {
@@ -743,8 +754,8 @@ void down_interp(efie_handle* h, FarSet<R>& F, int nr, int rhs0, std::vector<cpx
     KScope ks(h, K_INTERP, s, 1);
     const Level& L = P.L(D);
     launch_interp<R>(F.mr, h->mr_base, h->mr_ext, h->mr_off, h->d_rwg_box, N, F.mt, h->mt_base, h->mt_ext,
-                     h->mt_off, h->d_tri_box, Nt, rr[D - top], L.sp, nr, h->yA + (int64_t)rhs0 * N, N,
-                     h->w + (int64_t)rhs0 * Nt, Nt, s);
+                     h->mt_off, h->d_sc_box, h->n_sc, rr[D - top], L.sp, nr, h->yA + (int64_t)rhs0 * N, N,
+                     h->w + (int64_t)rhs0 * h->n_sc, h->n_sc, s);
   }
 }
 
@@ -763,7 +774,7 @@ void near_fork(efie_handle* h, int nr, cudaStream_t s) {
   cuda_check(cudaStreamWaitEvent(sn, h->ev_fork, 0), "near fork");
   cuda_check(cudaStreamWaitEvent(h->s_far, h->ev_fork, 0), "far fork");
   cuda_check(cudaMemsetAsync(h->yAn, 0, sizeof(double2) * N * nr, sn), "near outputs");
-  cuda_check(cudaMemsetAsync(h->wn, 0, sizeof(double2) * Nt * nr, sn), "near outputs");
+  cuda_check(cudaMemsetAsync(h->wn, 0, sizeof(double2) * h->n_sc * nr, sn), "near outputs");
   if (h->near_df) {
     {
       KScope ks(h, K_NEAR_A, sn, 2);
@@ -773,9 +784,10 @@ void near_fork(efie_handle* h, int nr, cudaStream_t s) {
     }
     {
       KScope ks(h, K_NEAR_V, sn, 2);
-      launch_split_vec(h->rho, h->rho4, Nt * nr, sn);
-      launch_near_spmv_df((const float4*)h->nd.Vn, h->d_blkV_off, h->d_near_ptr, h->d_near_src,
-                          h->d_box_tri_ptr, BD, h->rho4, h->wn, Nt, nr, h->near_variant, sn);
+      // scalar part: V on the charges (star), or Phi on the currents (direct)
+      if (!h->direct) launch_split_vec(h->rho, h->rho4, Nt * nr, sn);
+      launch_near_spmv_df((const float4*)h->nd.Vn, h->d_blkS_off, h->d_near_ptr, h->d_near_src, h->d_sc_box_ptr,
+                          BD, h->direct ? h->xs4 : h->rho4, h->wn, h->n_sc, nr, h->near_variant, sn);
     }
   } else {
     {
@@ -785,8 +797,8 @@ void near_fork(efie_handle* h, int nr, cudaStream_t s) {
     }
     {
       KScope ks(h, K_NEAR_V, sn, 1);
-      launch_near_spmv(h->nd.Vn, h->d_blkV_off, h->d_near_ptr, h->d_near_src, h->d_box_tri_ptr, BD, h->rho,
-                       h->wn, Nt, nr, sn);
+      launch_near_spmv(h->nd.Vn, h->d_blkS_off, h->d_near_ptr, h->d_near_src, h->d_sc_box_ptr, BD,
+                       h->direct ? h->xs : h->rho, h->wn, h->n_sc, nr, sn);
     }
   }
   cuda_check(cudaEventRecord(h->ev_join, sn), "near join");
@@ -803,7 +815,8 @@ void near_join_combine(efie_handle* h, int nr, double2* y, double2* yAo, double2
   cuda_check(cudaStreamWaitEvent(s, h->ev_join, 0), "near join");
   std::complex<double> cA = jk_of(P.k), cV = 1.0 / jk_of(P.k);
   KScope ks(h, K_VEC, s, 1);
-  launch_combine(h->yA, N, h->w, Nt, h->yAn, h->wn, h->d_rwg_perm, h->d_rwg_tri_sorted, N, nr,
+  launch_combine(h->yA, N, h->w, h->n_sc, h->yAn, h->wn, h->d_rwg_perm, h->direct ? nullptr : h->d_rwg_tri_sorted,
+                 N, nr,
                  make_double2(cA.real(), cA.imag()), make_double2(cV.real(), cV.imag()), y, ldy, yAo, yVo,
                  s);
 }
@@ -817,9 +830,9 @@ void matvec_chunk(efie_handle* h, FarSet<R>& F, const double2* x, int64_t ldx, i
   ensure_work(h, 8);
   ensure_far_buffers(h, F, nr);
   {
-    KScope ks(h, K_VEC, s, 2);
+    KScope ks(h, K_VEC, s, h->direct ? 1 : 2);
     launch_permute_in(x, ldx, h->d_rwg_perm, N, nr, h->xs, s);
-    launch_charges(h->xs, N, h->d_tri_rwg, h->d_tri_sgn, Nt, nr, h->rho, Nt, s);  // rho = Sigma^T x
+    if (!h->direct) launch_charges(h->xs, N, h->d_tri_rwg, h->d_tri_sgn, Nt, nr, h->rho, Nt, s);  // rho = Sigma^T x
   }
   near_fork(h, nr, s);                                                             // near field
   far_chunk<R>(h, F, nr, h->s_far);                                                // far field
@@ -895,9 +908,9 @@ void matvec_pairs(efie_handle* h, const double2* x, int64_t ldx, double2* y, dou
   ensure_far_buffers(h, F, 8);
   ensure_pair_buffers(h, F);
   {
-    KScope ks(h, K_VEC, s, 2);
+    KScope ks(h, K_VEC, s, h->direct ? 1 : 2);
     launch_permute_in(x, ldx, h->d_rwg_perm, N, R, h->xs, s);
-    launch_charges(h->xs, N, h->d_tri_rwg, h->d_tri_sgn, Nt, R, h->rho, Nt, s);
+    if (!h->direct) launch_charges(h->xs, N, h->d_tri_rwg, h->d_tri_sgn, Nt, R, h->rho, Nt, s);
   }
   near_fork(h, R, s);
   cudaStream_t sf = h->s_far;
@@ -992,6 +1005,8 @@ bool make_index16(const std::vector<int64_t>& tgt_ptr, const std::vector<int64_t
 
 void setup_impl(efie_handle* h, const efie_mesh* mesh, double k, int p, double grid_spacing, int levels) {
   check_mesh(mesh);
+  if (h->opt.factorization != EFIE_FACT_STAR && h->opt.factorization != EFIE_FACT_DIRECT)
+    throw EfieError{EFIE_EINVAL, "factorization must be EFIE_FACT_STAR or EFIE_FACT_DIRECT"};
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0)
     throw EfieError{EFIE_ECUDA, "no CUDA device"};
@@ -1019,8 +1034,9 @@ void setup_impl(efie_handle* h, const efie_mesh* mesh, double k, int p, double g
     h->setup_s[i] = std::chrono::duration<double>(now - t_mark).count();
     t_mark = now;
   };
+  h->direct = h->opt.factorization == EFIE_FACT_DIRECT;
   build_plan(P, mesh->xyz, mesh->n_vertices, mesh->tri, mesh->n_triangles, k, p, grid_spacing, levels,
-             h->opt.n_splines, true);
+             h->opt.n_splines, true, h->direct);
   phase_done(0);
   DevMem& M = h->mem;
   cudaStream_t s = 0;
@@ -1046,6 +1062,9 @@ void setup_impl(efie_handle* h, const efie_mesh* mesh, double k, int p, double g
   h->d_box_rwg_ptr = M.upload(P.box_rwg_ptr);
   h->d_box_tri_ptr = M.upload(P.box_tri_ptr);
   h->d_rwg_tri_sorted = M.upload(P.rwg_tri_sorted);
+  h->n_sc = h->direct ? N : Nt;
+  h->d_sc_box_ptr = h->direct ? h->d_box_rwg_ptr : h->d_box_tri_ptr;
+  h->d_sc_box = h->direct ? h->d_rwg_box : h->d_tri_box;
   {
     // per sorted triangle: its RWGs (sorted index) and signs
     std::vector<int32_t> tr(3 * Nt, -1);
@@ -1065,9 +1084,12 @@ void setup_impl(efie_handle* h, const efie_mesh* mesh, double k, int p, double g
   h->mr_base = M.upload(P.mom_rwg.base);
   h->mr_ext = M.upload(P.mom_rwg.ext);
   h->mr_off = M.upload(P.mom_rwg.off);
-  h->mt_base = M.upload(P.mom_tri.base);
-  h->mt_ext = M.upload(P.mom_tri.ext);
-  h->mt_off = M.upload(P.mom_tri.off);
+  {
+    const MomentBlocks& MS = h->direct ? P.mom_div : P.mom_tri;   // scalar-part moments
+    h->mt_base = M.upload(MS.base);
+    h->mt_ext = M.upload(MS.ext);
+    h->mt_off = M.upload(MS.off);
+  }
   // levels
   h->lev.assign(P.lv.size(), LevDev());
   for (int ell = P.D; ell >= P.top; --ell) {
@@ -1229,6 +1251,7 @@ void setup_impl(efie_handle* h, const efie_mesh* mesh, double k, int p, double g
     h->d_near_src = M.upload(P.near_src);
     h->d_blkA_off = M.upload(P.blkA_off);
     h->d_blkV_off = M.upload(P.blkV_off);
+    h->d_blkS_off = h->direct ? h->d_blkA_off : h->d_blkV_off;
     std::vector<int32_t> tgt(P.near_src.size());
     for (int64_t x = 0; x < BD; ++x)
       for (int64_t j = P.near_ptr[x]; j < P.near_ptr[x + 1]; ++j) tgt[j] = (int32_t)x;
@@ -1264,7 +1287,10 @@ void setup_impl(efie_handle* h, const efie_mesh* mesh, double k, int p, double g
       nd.tri_tl = M.upload(tl);
     }
     nd.A = M.alloc<double2>(P.nnzA);
-    nd.Vn = M.alloc<double2>(P.nnzV);
+    // direct factorization: the scalar part Phi lives on the A blocks
+    const int64_t nnzS = h->direct ? P.nnzA : P.nnzV;
+    nd.Vn = M.alloc<double2>(nnzS);
+    nd.Phi = h->direct ? nd.Vn : nullptr;
     // A: triangle-pair scratch per batch of blocks
     const int64_t nblk = nd.n_blocks;
     const int64_t scr_cap = (int64_t)(1LL << 30) / (10 * 16);  // pairs per batch (~1 GiB)
@@ -1312,7 +1338,9 @@ void setup_impl(efie_handle* h, const efie_mesh* mesh, double k, int p, double g
       launch_near_pairs_A(nd, j0, j1 - j0, d_scr_off, scratch, scr_off.back(), s);
       launch_near_combine_A(nd, j0, j1 - j0, d_scr_off, scratch, P.blkA_off[j0],
                             P.blkA_off[j1] - P.blkA_off[j0], s);
-      launch_near_V_pairs(nd, j0, j1 - j0, d_scr_off, scratch, P.blkV_off[j0], P.blkV_off[j1] - P.blkV_off[j0], s);
+      if (!h->direct)
+        launch_near_V_pairs(nd, j0, j1 - j0, d_scr_off, scratch, P.blkV_off[j0], P.blkV_off[j1] - P.blkV_off[j0],
+                            s);
       cuda_check(cudaStreamSynchronize(s), "near assembly");
       j0 = j1;
     }
@@ -1326,14 +1354,17 @@ void setup_impl(efie_handle* h, const efie_mesh* mesh, double k, int p, double g
                    "mirror list");
       }
       launch_near_mirror(nd.A, nd.blkA_off, nd.box_rwg_ptr, nd.blk_tgt, nd.near_src, d_mir, d_mir + nm, nm, s);
-      launch_near_mirror(nd.Vn, nd.blkV_off, nd.box_tri_ptr, nd.blk_tgt, nd.near_src, d_mir, d_mir + nm, nm, s);
+      if (h->direct)
+        launch_near_mirror(nd.Vn, nd.blkA_off, nd.box_rwg_ptr, nd.blk_tgt, nd.near_src, d_mir, d_mir + nm, nm, s);
+      else
+        launch_near_mirror(nd.Vn, nd.blkV_off, nd.box_tri_ptr, nd.blk_tgt, nd.near_src, d_mir, d_mir + nm, nm, s);
       cuda_check(cudaStreamSynchronize(s), "near mirror");
       M.release(d_mir);
     }
     if (h->precision == EFIE_MIXED) {
       // keep the FP64-assembled values as double-float pairs (in place)
       launch_split_df(nd.A, P.nnzA, s);
-      launch_split_df(nd.Vn, P.nnzV, s);
+      launch_split_df(nd.Vn, nnzS, s);
       cuda_check(cudaStreamSynchronize(s), "near split");
       h->near_df = true;
     }
@@ -1425,7 +1456,7 @@ int solve_impl(efie_handle* h, const double2* b, double2* x, int n_rhs, double t
     }
   }
   std::vector<std::vector<std::complex<double>>> H(n_rhs), cs(n_rhs), sn(n_rhs), gg(n_rhs);
-  std::vector<int> floor_hits(n_rhs, 0);
+  std::vector<int> floor_hits(n_rhs, 0), refine(n_rhs, 0);
   while (true) {
     bool any = false;
     for (int r = 0; r < n_rhs; ++r) {
@@ -1541,8 +1572,14 @@ int solve_impl(efie_handle* h, const double2* b, double2* x, int n_rhs, double t
       cuda_check(cudaMemcpyAsync(rec + (int64_t)cycle * n_rhs * N, x, sizeof(double2) * n_rhs * N,
                                  cudaMemcpyDeviceToDevice, s), "record");
     ++cycle;
-    // restart residual r = b - T x (working precision)
-    do_matvec(h, x, N, wv, nullptr, nullptr, N, n_rhs, false, s);
+    // restart residual r = b - T x: working precision, or the FP64 product
+    // once a right-hand side of a mixed handle has reached the working
+    // precision's accuracy floor (mixed-precision iterative refinement: the
+    // next cycles solve T_mixed d = b - T_fp64 x, whose fixed point is the
+    // FP64 solution)
+    bool use64 = false;
+    for (int r = 0; r < n_rhs; ++r) use64 |= act[r] && refine[r];
+    do_matvec(h, x, N, wv, nullptr, nullptr, N, n_rhs, use64, s);
     launch_lincomb(b, wv, 1.0, -1.0, rv, (int64_t)n_rhs * N, s);
     std::vector<double> beta_prev(beta);
     norms(rv, N, beta);
@@ -1551,17 +1588,29 @@ int solve_impl(efie_handle* h, const double2* b, double2* x, int n_rhs, double t
     if (use_pc)
       for (int r = 0; r < n_rhs; ++r)
         if (act[r] && !pc_fallback[r] && beta[r] > 0.99 * beta_prev[r]) pc_fallback[r] = 1;
-    // accuracy floor of the working precision: the cycle met the tolerance in
-    // its own arithmetic but the recomputed residual did not, twice in a row;
-    // further cycles cannot lower it, so stop and let the FP64 true residual
-    // below decide convergence
+    // accuracy floor: the cycle met the tolerance in its own arithmetic but
+    // the recomputed residual did not.  A mixed handle then switches that
+    // right-hand side to FP64 restart residuals (refinement, from this
+    // restart on); otherwise, twice in a row, further cycles cannot lower it,
+    // so stop and let the FP64 true residual below decide convergence
+    bool newly = false;
     for (int r = 0; r < n_rhs; ++r) {
       if (!act[r]) continue;
       if (est_conv[r] && beta[r] / bnorm[r] > tol_in) {
-        if (++floor_hits[r] >= 2) act[r] = 0;
+        if (h->precision == EFIE_MIXED && !refine[r]) {
+          refine[r] = 1;
+          newly = !use64 || newly;
+        } else if (++floor_hits[r] >= 2) {
+          act[r] = 0;
+        }
       } else {
         floor_hits[r] = 0;
       }
+    }
+    if (newly) {
+      do_matvec(h, x, N, wv, nullptr, nullptr, N, n_rhs, true, s);
+      launch_lincomb(b, wv, 1.0, -1.0, rv, (int64_t)n_rhs * N, s);
+      norms(rv, N, beta);
     }
   }
   // true residual with the FP64 fast matvec
@@ -1995,6 +2044,12 @@ int efie_plan_info(const efie_handle* h, efie_plan_info_t* info) {
   if (!h || !info) return EFIE_EINVAL;
   fill_plan_info(h->plan, info, nullptr, 0);
   info->device_bytes = h->mem.bytes;
+  if (h->direct) {
+    // the scalar part is Phi on the RWG pairs of the A blocks, its moments per RWG
+    info->near_nnz_V = info->near_nnz_A;
+    const MomentBlocks& MD = h->plan.mom_div;
+    info->moment_entries_tri = MD.off.empty() ? 0 : MD.off.back();
+  }
   return EFIE_OK;
 }
 

@@ -34,6 +34,9 @@ struct NearDev {
   double2* A;               // [nnzA]
   double2* Vn;              // [nnzV]
   const int32_t* tri_tl;    // [nt sorted] index of the triangle in the tset of its own box, -1 if absent
+  // direct factorization (Sec. VI-B): the scalar part on the RWG pairs of the
+  // A blocks, Phi[i][n] = int int div f_i div f_n g (same layout as A), or null
+  double2* Phi;
 };
 // Blocks (x, y) with x > y are not integrated: T is symmetric, so they are the
 // transposes of the (y, x) blocks, copied by launch_near_mirror.

@@ -1631,7 +1631,8 @@ void launch_charges(const double2* xs, int64_t ldx, const int32_t* tri_rwg, cons
   k_charges<<<(unsigned)blocks, 256, 0, s>>>(xs, ldx, tri_rwg, tri_sgn, Nt, nr, rho, ldr);
 }
 
-// y[r][m] = cA * yA[r][i] + cV * (w[r][t+] - w[r][t-]), m = perm[i]
+// y[r][m] = cA * yA[r][i] + cV * (w[r][t+] - w[r][t-]), m = perm[i]; with
+// rts null (direct factorization) the scalar part is w[r][i] itself.
 // yAn, wn (optional): near-field parts kept apart from the far parts yA, w
 __global__ void k_combine(const double2* __restrict__ yA, int64_t ldA, const double2* __restrict__ w,
                           int64_t ldw, const double2* __restrict__ yAn, const double2* __restrict__ wn,
@@ -1643,13 +1644,24 @@ __global__ void k_combine(const double2* __restrict__ yA, int64_t ldA, const dou
        idx += (int64_t)gridDim.x * blockDim.x) {
     int64_t r = idx / N, i = idx - r * N;
     double2 a = yA[r * ldA + i];
-    double2 wp = w[r * ldw + rts[2 * i]], wm = w[r * ldw + rts[2 * i + 1]];
-    if (yAn) {
-      a = cadd(a, yAn[r * ldA + i]);
-      wp = cadd(wp, wn[r * ldw + rts[2 * i]]);
-      wm = cadd(wm, wn[r * ldw + rts[2 * i + 1]]);
+    double2 v;
+    if (rts) {
+      // star factorization: the charge part of RWG i is w(c+) - w(c-)
+      double2 wp = w[r * ldw + rts[2 * i]], wm = w[r * ldw + rts[2 * i + 1]];
+      if (yAn) {
+        a = cadd(a, yAn[r * ldA + i]);
+        wp = cadd(wp, wn[r * ldw + rts[2 * i]]);
+        wm = cadd(wm, wn[r * ldw + rts[2 * i + 1]]);
+      }
+      v = make_double2(wp.x - wm.x, wp.y - wm.y);
+    } else {
+      // direct factorization: the scalar part is per RWG already
+      v = w[r * ldw + i];
+      if (yAn) {
+        a = cadd(a, yAn[r * ldA + i]);
+        v = cadd(v, wn[r * ldw + i]);
+      }
     }
-    double2 v = make_double2(wp.x - wm.x, wp.y - wm.y);
     int64_t m = perm[i];
     if (y) y[r * ldy + m] = cadd(cmul(cA, a), cmul(cV, v));
     if (yAo) yAo[r * ldy + m] = a;

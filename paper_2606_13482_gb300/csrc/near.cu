@@ -333,6 +333,9 @@ __global__ void k_near_pairs_A(NearDev nd, int64_t j0, int64_t nblk, const int64
 
 // A block entries from the pair scratch:
 // A[i][n] = sum_{s,t} coef_is coef_nt Ivv[(tl_is, tl_nt)][loc_is][loc_nt]
+// and, for the direct factorization, the scalar part of the same pair from
+// the I0 of the same triangle pairs (div f = sign / area on each side, and
+// coef = sign / (2 area)): Phi[i][n] = sum_{s,t} 4 coef_is coef_nt I0
 __global__ void k_near_combine_A(NearDev nd, int64_t j0, int64_t nblk, const int64_t* scr_off,
                                  const double2* scratch, int64_t e_begin, int64_t total) {
   int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -347,7 +350,7 @@ __global__ void k_near_combine_A(NearDev nd, int64_t j0, int64_t nblk, const int
   int64_t i = nd.box_rwg_ptr[x] + r, n = nd.box_rwg_ptr[y] + c;
   int64_t nty = nd.tset_ptr[y + 1] - nd.tset_ptr[y];
   const double2* scr = scratch + 10 * scr_off[j - j0];
-  double2 acc = make_double2(0, 0);
+  double2 acc = make_double2(0, 0), phi = make_double2(0, 0);
   for (int s = 0; s < 2; ++s)
     for (int t = 0; t < 2; ++t) {
       int64_t pe = (int64_t)nd.rwg_tl[2 * i + s] * nty + nd.rwg_tl[2 * n + t];
@@ -355,8 +358,12 @@ __global__ void k_near_combine_A(NearDev nd, int64_t j0, int64_t nblk, const int
       double2 v = scr[10 * pe + 1 + 3 * nd.rwg_loc[2 * i + s] + nd.rwg_loc[2 * n + t]];
       acc.x += cf * v.x;
       acc.y += cf * v.y;
+      const double2 i0 = scr[10 * pe];
+      phi.x += 4.0 * cf * i0.x;
+      phi.y += 4.0 * cf * i0.y;
     }
   nd.A[eg] = acc;
+  if (nd.Phi) nd.Phi[eg] = phi;
 }
 
 // Block (x, y) = transpose of block (y, x).  Block j is column-major

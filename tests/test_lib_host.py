@@ -229,6 +229,21 @@ def test_setup_without_gpu_fails_loudly(lib):
     with pytest.raises(G.EfieError) as e:
         G.EFIE(V, T, 2 * np.pi, 3, 0.1, 1)
     assert e.value.code == -3
+    with pytest.raises(G.EfieError) as e:
+        G.EFIE(V, T, 2 * np.pi, 3, 0.1, 1, factorization=G.EFIE_FACT_DIRECT)
+    assert e.value.code == -3
+
+
+def test_factorization_option_checked_first(lib):
+    # an unknown factorization is rejected before any device work (EINVAL,
+    # with or without a GPU); the option sits at the end of efie_options
+    import ctypes
+    G, _ = lib
+    V, T = E.icosphere(4, 0.5)
+    with pytest.raises(G.EfieError) as e:
+        G.EFIE(V, T, 2 * np.pi, 3, 0.1, 1, factorization=7)
+    assert e.value.code == -1 and "factorization" in str(e.value)
+    assert G.Options.factorization.offset == ctypes.sizeof(G.Options) - 8
 
 
 def test_planewave_argument_checks(lib):
