@@ -352,11 +352,13 @@ int efie_precond_gradient(efie_handle *h, const void *r, const void *e, float *g
  * kernel (0: source values staged in shared memory by double-buffered
  * asynchronous copies, one thread per row and 8 right-hand sides; 1: read
  * through L1 with no barriers; 2: staged by the block between barriers, 4
- * right-hand sides per thread), and keeps the fastest in the handle; the
+ * right-hand sides per thread; 3: as 0 with the staging in an mbarrier ring
+ * filled by a copy warp, so that row warps never wait on one another), and
+ * keeps the fastest in the handle; the
  * choices are returned if the pointers are set. */
 int efie_autotune(efie_handle *h, int n_rhs, void *stream, int *best_chunk, int *best_mac, int *best_near);
 /* Sets the three choices efie_autotune makes: rhs_chunk in 1..8, mac_variant
- * in 0..5 and near_variant in 0..2 as above.  EFIE_EINVAL outside those
+ * in 0..5 and near_variant in 0..3 as above.  EFIE_EINVAL outside those
  * ranges. */
 int efie_autotune_set(efie_handle *h, int rhs_chunk, int mac_variant, int near_variant);
 /* Transform schedule of the stabilized forward / inverse transforms

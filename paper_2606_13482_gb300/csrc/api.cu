@@ -263,7 +263,8 @@ struct efie_handle {
   int* err_dev = nullptr;
   int near_variant = 0;  // mixed near field (autotuner knob): 0 x staged in shared memory by
                          // double-buffered asynchronous copies, one thread per row and 8 RHS; 1 x
-                         // through L1; 2 x staged by the block between barriers, 4 RHS per thread
+                         // through L1; 2 x staged by the block between barriers, 4 RHS per thread;
+                         // 3 as 0 with an mbarrier ring filled by a copy warp
   int fft_variant = 0;   // transform schedule (autotuner knob): 0 line passes; 1 forward y and z passes
                          // fused per slab where they apply (FP32, 32 channels); 2 forward and inverse
                          // fused
@@ -780,14 +781,14 @@ void near_fork(efie_handle* h, int nr, cudaStream_t s) {
       KScope ks(h, K_NEAR_A, sn, 2);
       launch_split_vec(h->xs, h->xs4, N * nr, sn);
       launch_near_spmv_df((const float4*)h->nd.A, h->d_blkA_off, h->d_near_ptr, h->d_near_src, h->d_box_rwg_ptr,
-                          BD, h->xs4, h->yAn, N, nr, h->near_variant, sn);
+                          BD, h->xs4, h->yAn, N, nr, h->near_variant, h->err_dev, sn);
     }
     {
       KScope ks(h, K_NEAR_V, sn, 2);
       // scalar part: V on the charges (star), or Phi on the currents (direct)
       if (!h->direct) launch_split_vec(h->rho, h->rho4, Nt * nr, sn);
       launch_near_spmv_df((const float4*)h->nd.Vn, h->d_blkS_off, h->d_near_ptr, h->d_near_src, h->d_sc_box_ptr,
-                          BD, h->direct ? h->xs4 : h->rho4, h->wn, h->n_sc, nr, h->near_variant, sn);
+                          BD, h->direct ? h->xs4 : h->rho4, h->wn, h->n_sc, nr, h->near_variant, h->err_dev, sn);
     }
   } else {
     {
@@ -2422,7 +2423,7 @@ int efie_precond_gradient(efie_handle* h, const void* r, const void* e, float* g
 
 int efie_autotune_set(efie_handle* h, int rhs_chunk, int mac_variant, int near_variant) {
   if (!h || rhs_chunk < 1 || rhs_chunk > 8 || mac_variant < 0 || mac_variant > 5 || near_variant < 0 ||
-      near_variant > 2)
+      near_variant > 3)
     return EFIE_EINVAL;
   h->opt.rhs_chunk = rhs_chunk;
   h->mac_variant = mac_variant;
@@ -2460,7 +2461,7 @@ int efie_autotune(efie_handle* h, int n_rhs, void* stream, int* best_chunk, int*
     int bc = 8, bm = 0, bn = 0;
     for (int chunk : {8, 4, 2, 1}) {
       if (chunk > n_rhs && chunk != 1) continue;
-      for (int cand = 0; cand < 18; ++cand) {
+      for (int cand = 0; cand < 24; ++cand) {
         const int mv = cand % 6, nv = cand / 6;
         if (nv > 0 && !h->near_df) continue;  // the near variants differ in the mixed form only
         if (mv == 4 && (chunk != 8 || n_rhs < 16)) continue;  // differs from 0 on chunk pairs only

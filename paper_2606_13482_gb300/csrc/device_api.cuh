@@ -64,7 +64,7 @@ void launch_split_df(double2* a, int64_t n, cudaStream_t s);
 void launch_split_vec(const double2* x, float4* y, int64_t n, cudaStream_t s);
 void launch_near_spmv_df(const float4* M, const int64_t* blk_off, const int64_t* near_ptr,
                          const int32_t* near_src, const int64_t* box_ptr, int64_t n_boxes, const float4* x,
-                         double2* y, int64_t ld, int nr, int variant, cudaStream_t s);
+                         double2* y, int64_t ld, int nr, int variant, int* err, cudaStream_t s);
 
 // Strided tensor view of a box-batched 3D grid with channels innermost:
 // element (b, i0, i1, i2, c) at b*sb + i0*s0 + i1*s1 + i2*s2 + c.

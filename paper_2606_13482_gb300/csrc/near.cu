@@ -801,6 +801,147 @@ k_near_rows_df8(const float4* __restrict__ M, const int64_t* __restrict__ blk_of
   }
 }
 
+// The same product with the barriers taken out: a copy warp fills a ring of
+// NR_ST shared-memory stages (64 columns x 8 right-hand sides each) with
+// 16-byte asynchronous copies, and each of the four row warps waits only for
+// the stage it needs (mbarrier "full", 32 copy lanes) and frees it when done
+// (mbarrier "empty", one arrival per row warp).  A warp whose rows finish a
+// piece early goes on to the next one while the others are still working,
+// which a block barrier would not allow.  Every wait is bounded: on a timeout
+// the block sets *err, stops, and its outputs are left unwritten.
+constexpr int NR_ST = 5;
+constexpr int NR_CH = 64;
+constexpr long long NR_SPIN = 1LL << 22;
+struct NrBar {
+  uint64_t full[NR_ST], empty[NR_ST];
+  int abort;
+};
+__device__ __forceinline__ bool nr_wait(uint64_t* b, uint32_t parity, int* abort, int* err) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(b);
+  for (long long it = 0; it < NR_SPIN; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n.reg .pred q;\nmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\nselp.u32 %0, 1, 0, q;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if ((it & 63) == 63 && *reinterpret_cast<volatile int*>(abort)) return false;
+  }
+  *reinterpret_cast<volatile int*>(abort) = 1;
+  if (err) *reinterpret_cast<volatile int*>(err) = 1;
+  return false;
+}
+__global__ void __launch_bounds__(NDF_T + 32)
+k_near_rows_df8r(const float4* __restrict__ M, const int64_t* __restrict__ blk_off,
+                 const int64_t* __restrict__ near_ptr, const int32_t* __restrict__ near_src,
+                 const int64_t* __restrict__ box_ptr, const float4* __restrict__ x, double2* __restrict__ y,
+                 int64_t ld, int nch, int* err) {
+  __shared__ __align__(16) float4 xs[NR_ST][8][NR_CH];
+  __shared__ NrBar bar;
+  const int xb = blockIdx.x / nch, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  x += (int64_t)(blockIdx.x % nch) * 8 * ld;
+  y += (int64_t)(blockIdx.x % nch) * 8 * ld;
+  const int64_t r0 = box_ptr[xb];
+  const int nrow = (int)(box_ptr[xb + 1] - r0);
+  const int64_t j0 = near_ptr[xb], j1 = near_ptr[xb + 1];
+  if (tid == 0) {
+    for (int i = 0; i < NR_ST; ++i) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"((uint32_t)__cvta_generic_to_shared(&bar.full[i])),
+                   "r"(32));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"((uint32_t)__cvta_generic_to_shared(&bar.empty[i])),
+                   "r"(NDF_T / 32));
+    }
+    bar.abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+  // pieces in near-list order: (source box j, first column cb), empty boxes skipped
+  auto next_piece = [&](int64_t& j, int& cb) {
+    cb += NR_CH;
+    if (cb >= (int)(box_ptr[near_src[j] + 1] - box_ptr[near_src[j]])) {
+      ++j;
+      cb = 0;
+    }
+  };
+  auto skip_empty = [&](int64_t& j) {
+    while (j < j1 && box_ptr[near_src[j] + 1] == box_ptr[near_src[j]]) ++j;
+  };
+  if (warp == NDF_T / 32) {
+    // ------------------------------------------------ copy warp
+    uint32_t g = 0;
+    bool ok = true;
+    for (int ubase = 0; ubase < nrow && ok; ubase += NDF_T) {
+      int64_t j = j0;
+      int cb = 0;
+      for (skip_empty(j); j < j1 && ok; next_piece(j, cb), skip_empty(j), ++g) {
+        const int st = (int)(g % NR_ST);
+        if (g >= (uint32_t)NR_ST) {
+          int w = 1;
+          if (lane == 0) w = nr_wait(&bar.empty[st], ((g / NR_ST) - 1) & 1, &bar.abort, err) ? 1 : 0;
+          ok = __shfl_sync(0xffffffffu, w, 0) != 0;
+          if (!ok) break;
+        }
+        const int32_t yb = near_src[j];
+        const int64_t c0 = box_ptr[yb];
+        const int ncc = min(NR_CH, (int)(box_ptr[yb + 1] - c0) - cb);
+        for (int i = lane; i < 8 * ncc; i += 32) {
+          const int r = i / ncc, cc = i - r * ncc;
+          near_cp16(&xs[st][r][cc], x + r * ld + c0 + cb + cc);
+        }
+        asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];\n" ::"r"(
+                         (uint32_t)__cvta_generic_to_shared(&bar.full[st]))
+                     : "memory");
+      }
+    }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+  } else {
+    // ------------------------------------------------ row warps
+    uint32_t g = 0;
+    bool ok = true;
+    for (int ubase = 0; ubase < nrow && ok; ubase += NDF_T) {
+      const int row = ubase + tid;
+      const bool has = row < nrow;
+      DF re[8], im[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) re[q] = im[q] = DF{0.f, 0.f};
+      int64_t j = j0;
+      int cb = 0;
+      for (skip_empty(j); j < j1; next_piece(j, cb), skip_empty(j), ++g) {
+        const int st = (int)(g % NR_ST);
+        ok = nr_wait(&bar.full[st], (g / NR_ST) & 1, &bar.abort, err);
+        if (!ok) break;
+        const int32_t yb = near_src[j];
+        const int ncc = min(NR_CH, (int)(box_ptr[yb + 1] - box_ptr[yb]) - cb);
+        if (has) {
+          const float4* Mc = M + blk_off[j] + (int64_t)cb * nrow + row;
+          float4 a = Mc[0];
+          for (int cc = 0; cc < ncc; ++cc) {
+            const float4 an = Mc[(int64_t)(cc + 1 < ncc ? cc + 1 : cc) * nrow];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) df_cmac(re[q], im[q], a, xs[st][q][cc]);
+            a = an;
+          }
+        }
+        __syncwarp();
+        if (lane == 0)
+          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(
+                           (uint32_t)__cvta_generic_to_shared(&bar.empty[st]))
+                       : "memory");
+      }
+      if (ok && has) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          double2* yp = y + q * ld + r0 + row;
+          double2 t = *yp;
+          *yp = make_double2(t.x + ((double)re[q].hi + (double)re[q].lo), t.y + ((double)im[q].hi + (double)im[q].lo));
+        }
+      }
+    }
+  }
+  __syncthreads();
+}
+
 void launch_split_df(double2* a, int64_t n, cudaStream_t s) {
   if (n <= 0) return;
   int64_t blocks = ceil_div(n, 256);
@@ -815,7 +956,8 @@ void launch_split_vec(const double2* x, float4* y, int64_t n, cudaStream_t s) {
 }
 // variant 0: full chunks of 8 through k_near_rows_df8, others through
 // k_near_rows_df; variant 1: k_near_rows_df_g; variant 2: k_near_rows_df
-// only.  k_near_rows_df: right-hand sides per unit: all of a 1-, 2- or
+// only; variant 3: full chunks through k_near_rows_df8r (err: its timeout
+// flag).  k_near_rows_df: right-hand sides per unit: all of a 1-, 2- or
 // 4-wide chunk; 4 for wider chunks (two units per row, one unit per
 // thread).  Full chunks of 8 run in
 // one launch of (box, chunk) blocks with the chunks of a box adjacent, so
@@ -824,7 +966,7 @@ void launch_split_vec(const double2* x, float4* y, int64_t n, cudaStream_t s) {
 // partial chunk runs in a launch of its own.
 void launch_near_spmv_df(const float4* M, const int64_t* blk_off, const int64_t* near_ptr,
                          const int32_t* near_src, const int64_t* box_ptr, int64_t n_boxes, const float4* x,
-                         double2* y, int64_t ld, int nr, int variant, cudaStream_t s) {
+                         double2* y, int64_t ld, int nr, int variant, int* err, cudaStream_t s) {
   if (n_boxes <= 0 || nr <= 0) return;
   const int nfull = nr / 8;
   for (int part = 0; part < 2; ++part) {
@@ -837,6 +979,10 @@ void launch_near_spmv_df(const float4* M, const int64_t* blk_off, const int64_t*
     const unsigned grid = (unsigned)(n_boxes * nch);
     if (variant == 0 && cnt == 8) {
       k_near_rows_df8<<<grid, NDF_T, 0, s>>>(M, blk_off, near_ptr, near_src, box_ptr, xr, yr, ld, nch);
+      continue;
+    }
+    if (variant == 3 && cnt == 8) {
+      k_near_rows_df8r<<<grid, NDF_T + 32, 0, s>>>(M, blk_off, near_ptr, near_src, box_ptr, xr, yr, ld, nch, err);
       continue;
     }
     if (variant == 1) {

@@ -51,7 +51,7 @@ def test_all_near_equals_dense(freq, r, delta, levels):
     Td = _dense_T(freq, r)
     X = E.complex_gaussian((19, Td.shape[0]), 17)
     ref = X @ Td.T
-    for prec, nvs in ((G.EFIE_FP64, (0,)), (G.EFIE_MIXED, (0, 1, 2))):
+    for prec, nvs in ((G.EFIE_FP64, (0,)), (G.EFIE_MIXED, (0, 1, 2, 3))):
         h = G.EFIE(V, T, K, 3, delta, levels, precision=prec)
         try:
             for nv in nvs:

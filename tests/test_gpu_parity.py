@@ -233,12 +233,13 @@ def test_top_level_translation_variants(G, two_level_oracle, mac_variant):
         assert _rel(Y[r], ref_op.matvec(X[r])) < TOL32
 
 
-@pytest.mark.parametrize("near_variant", [0, 1, 2])
+@pytest.mark.parametrize("near_variant", [0, 1, 2, 3])
 def test_near_field_variants_mixed(G, c1_gpu, c1_oracle, near_variant):
     """The double-float near-field kernels (x staged by double-buffered
     asynchronous copies, 8 vectors per thread; x read through L1; x staged
-    between barriers, 4 vectors per thread) against the FP64 oracle, with
-    8-, 3- and 1-vector chunks."""
+    between barriers, 4 vectors per thread; x in an mbarrier ring filled by a
+    copy warp, no block barriers) against the FP64 oracle, with 8-, 3- and
+    1-vector chunks."""
     torch = _torch()
     h64, h32 = c1_gpu
     X = E.complex_gaussian((12, h32.N), 8)
