@@ -702,16 +702,17 @@ def reference_arm(args, w):
 
 def batch_meshes():
     """Ten PEC ellipsoids, semi-axes uniform in [0.5, 3] wavelengths (seed 3),
-    each a scaled geodesic sphere whose frequency keeps the edges along the
-    longest axis near 0.1 wavelength, clamped to 5,000 - 60,000 unknowns."""
+    each a scaled geodesic sphere (30 f^2 unknowns at frequency f).  The
+    unknown counts span 5,000 - 60,000: frequencies 13 ... 44 in ten even
+    steps, the finer meshes on the larger ellipsoids."""
     import efie_inputs as E
     rng = np.random.default_rng(3)
-    out = []
-    for _ in range(10):
-        axes = rng.uniform(0.5, 3.0, size=3)
-        freq = int(np.ceil(1.205 * axes.max() / 0.1))
-        freq = int(np.clip(freq, 13, 44))
-        out.append(E.ellipsoid(freq, tuple(axes)))
+    axes = [rng.uniform(0.5, 3.0, size=3) for _ in range(10)]
+    freqs = [int(round(13 + i * 31 / 9)) for i in range(10)]
+    order = np.argsort([a.max() for a in axes])
+    out = [None] * 10
+    for rank, i in enumerate(order):
+        out[i] = E.ellipsoid(freqs[rank], tuple(axes[i]))
     return out
 
 
