@@ -363,15 +363,16 @@ int efie_autotune(efie_handle *h, int n_rhs, void *stream, int *best_chunk, int 
 int efie_autotune_set(efie_handle *h, int rhs_chunk, int mac_variant, int near_variant);
 /* Transform schedule of the stabilized forward / inverse transforms
  * (Sec. III-C, V-B: the per-axis products with F P and P^T F^-1 on every
- * level).  0 (default): three line passes per transform; 1: for FP32 passes
- * of 8 right-hand sides (32 channels) and 9, 13 or 21 splines per axis, the
+ * level).  0: three line passes per transform; 1: for FP32 passes of 8
+ * right-hand sides (32 channels) and 9, 13 or 21 splines per axis, the
  * forward y and z passes run fused on (box, x-frequency) slabs in shared
  * memory, so the intermediate of the second pass never goes to device
- * memory; 2: the inverse z and y passes fused the same way as well.  All
- * give the same operator up to rounding.
- * efie_autotune times all three (after choosing the other knobs) for mixed
+ * memory; 2: the inverse z and y passes fused the same way as well; 3
+ * (default): forward and inverse fused on levels of 9 splines per axis only,
+ * line passes on the others.  All give the same operator up to rounding.
+ * efie_autotune times all four (after choosing the other knobs) for mixed
  * handles whose best chunk is 8.  set: EFIE_EINVAL for a schedule outside
- * 0..2; get writes the handle's. */
+ * 0..3; get writes the handle's. */
 int efie_transform_schedule_set(efie_handle *h, int schedule);
 int efie_transform_schedule_get(const efie_handle *h, int *schedule);
 

@@ -514,8 +514,8 @@ class EFIE:
 
     def transform_schedule(self, schedule=None):
         """Sets the transform schedule (0 line passes, 1 forward y-z passes
-        fused, 2 forward and inverse fused) when given; returns the handle's
-        schedule."""
+        fused, 2 forward and inverse fused, 3 both fused on 9-spline levels
+        only) when given; returns the handle's schedule."""
         if schedule is not None:
             _check(self.lib, self.lib.efie_transform_schedule_set(self.h, int(schedule)), self.h)
         v = ctypes.c_int()

@@ -265,9 +265,9 @@ struct efie_handle {
                          // double-buffered asynchronous copies, one thread per row and 8 RHS; 1 x
                          // through L1; 2 x staged by the block between barriers, 4 RHS per thread;
                          // 3 as 0 with an mbarrier ring filled by a copy warp
-  int fft_variant = 0;   // transform schedule (autotuner knob): 0 line passes; 1 forward y and z passes
+  int fft_variant = 3;   // transform schedule (autotuner knob): 0 line passes; 1 forward y and z passes
                          // fused per slab where they apply (FP32, 32 channels); 2 forward and inverse
-                         // fused
+                         // fused; 3 (default) both fused on levels of 9 splines per axis only
   // work vectors (FP64, sorted) and their double-float splits
   int Rw = 0;
   double2 *xs = nullptr, *rho = nullptr, *yA = nullptr, *w = nullptr;
@@ -617,11 +617,14 @@ void fwd_level(efie_handle* h, FarSet<R>& F, int ell, int C, const cpx_t<R>* qin
   View a1{(int64_t)n * sp * sp * C, (int64_t)sp * sp * C, (int64_t)sp * C, C};
   View a2{(int64_t)n * n * sp * C, (int64_t)n * sp * C, (int64_t)sp * C, C};
   View vf{C, (int64_t)n * n * B * C, (int64_t)n * B * C, B * C};
-  KScope ks(h, K_FWD, s, 3);
+  // y and z passes fused per (box, x-frequency) slab, no y-pass intermediate in HBM
+  const bool fuse = sizeof(R) == 4 && C == 32 &&
+                    (h->fft_variant == 1 || h->fft_variant == 2 || (h->fft_variant == 3 && sp == 9)) &&
+                    dft_yz_fits(sp, n);
+  KScope ks(h, K_FWD, s, fuse ? 2 : 3);
   if (!launch_dft<R>(qin, vq, F.tmp1, a1, B, C, 0, sp, n, sp, sp, FL.Mf, n, false, s))
     launch_mode<R>(qin, vq, F.tmp1, a1, B, C, 0, sp, n, sp, sp, FL.Mf, FL.Mf, true, nullptr, nullptr, false, s);
-  // y and z passes fused per (box, x-frequency) slab, no y-pass intermediate in HBM
-  if (sizeof(R) == 4 && C == 32 && (h->fft_variant == 1 || h->fft_variant == 2) &&
+  if (fuse &&
       launch_dft_yz(reinterpret_cast<const float2*>(F.tmp1), reinterpret_cast<float2*>(Qout), B, sp, n,
                     reinterpret_cast<const float2*>(FL.Mf), false, s))
     return;
@@ -642,9 +645,11 @@ void inv_level(efie_handle* h, FarSet<R>& F, int ell, int C, const cpx_t<R>* Rin
   View vf{C, (int64_t)n * n * B * C, (int64_t)n * B * C, B * C};
   View b1{(int64_t)sp * n * n * C, (int64_t)n * n * C, (int64_t)n * C, C};
   View b2{(int64_t)sp * sp * n * C, (int64_t)sp * n * C, (int64_t)n * C, C};
-  KScope ks(h, K_INV, s, 3);
   // z and y passes fused per (box, x-frequency) slab into t[b][fx][y][z][c], then the x pass
-  if (sizeof(R) == 4 && C == 32 && h->fft_variant == 2 &&
+  const bool fuse = sizeof(R) == 4 && C == 32 && (h->fft_variant == 2 || (h->fft_variant == 3 && sp == 9)) &&
+                    dft_zy_fits(sp, n);
+  KScope ks(h, K_INV, s, fuse ? 2 : 3);
+  if (fuse &&
       launch_dft_yz(reinterpret_cast<const float2*>(Rin), reinterpret_cast<float2*>(F.tmp1), B, sp, n,
                     reinterpret_cast<const float2*>(FL.Mb), true, s)) {
     View vt{(int64_t)n * sp * sp * C, (int64_t)sp * sp * C, (int64_t)sp * C, C};
@@ -2432,7 +2437,7 @@ int efie_autotune_set(efie_handle* h, int rhs_chunk, int mac_variant, int near_v
 }
 
 int efie_transform_schedule_set(efie_handle* h, int schedule) {
-  if (!h || schedule < 0 || schedule > 2) return EFIE_EINVAL;
+  if (!h || schedule < 0 || schedule > 3) return EFIE_EINVAL;
   h->fft_variant = schedule;
   return EFIE_OK;
 }
@@ -2491,7 +2496,7 @@ int efie_autotune(efie_handle* h, int n_rhs, void* stream, int* best_chunk, int*
     if (h->precision == EFIE_MIXED && bc == 8) {
       float best_f = 1e30f;
       int bf = 0;
-      for (int fv = 0; fv < 3; ++fv) {
+      for (int fv = 0; fv < 4; ++fv) {
         h->fft_variant = fv;
         do_matvec(h, x, N, y, nullptr, nullptr, N, n_rhs, false, s);
         cudaEventRecord(e0, s);

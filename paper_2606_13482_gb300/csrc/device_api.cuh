@@ -94,6 +94,8 @@ bool launch_dft(const cpx_t<R>* in, View vin, cpx_t<R>* out, View vout, int64_t 
 // x-frequency) slabs; false when they do not apply
 bool launch_dft_yz(const float2* in, float2* out, int64_t B, int sp, int n, const float2* M, bool inverse,
                    cudaStream_t s);
+bool dft_yz_fits(int sp, int n);   // the fused forward pass takes this level
+bool dft_zy_fits(int sp, int n);   // the fused inverse pass takes this level
 
 // one pass of the sibling-shared upward transfer: out[g] = M(bit0) in[src0] +
 // M(bit1) in[src1] along axis ax (src1 < 0: absent), M(0) = M0, M(1) = M1

@@ -648,17 +648,25 @@ __global__ void __launch_bounds__(256) k_dft_inv_zy(const float2* __restrict__ i
   }
 }
 
+// Whether the fused forward (y, z) / inverse (z, y) passes take a level of
+// sp splines per axis and FFT length n (9, 13 or 21 splines; shared memory).
+static size_t dft_yz_smem(int sp, int n, bool inverse) {
+  const int nh = n / 2 + 1;
+  return inverse ? sizeof(float2) * ((size_t)n * sp * 32 + (size_t)nh * sp)
+                 : sizeof(float2) * ((size_t)sp * sp * 32 + (size_t)nh * sp);
+}
+bool dft_yz_fits(int sp, int n) { return (sp == 9 || sp == 13 || sp == 21) && dft_yz_smem(sp, n, false) <= 200 * 1024; }
+bool dft_zy_fits(int sp, int n) { return (sp == 9 || sp == 13 || sp == 21) && dft_yz_smem(sp, n, true) <= 200 * 1024; }
+
 // Fused y-z forward (in: t[b][fx][y][z][32] -> out: Q[fx][fy][fz][b][32]) or
 // z-y inverse (in: Q layout -> out: t layout).  Returns false when they do not
 // apply (splines per axis other than 9, 13 or 21, or shared memory).
 bool launch_dft_yz(const float2* in, float2* out, int64_t B, int sp, int n, const float2* M, bool inverse,
                    cudaStream_t s) {
-  const int nh = n / 2 + 1;
   const int64_t slabs = B * (int64_t)n;
   if (slabs <= 0) return true;
   if (slabs > 0x7FFFFFFFLL) return false;
-  const size_t smem = inverse ? sizeof(float2) * ((size_t)n * sp * 32 + (size_t)nh * sp)
-                              : sizeof(float2) * ((size_t)sp * sp * 32 + (size_t)nh * sp);
+  const size_t smem = dft_yz_smem(sp, n, inverse);
   if (smem > 200 * 1024) return false;
 #define EFIE_YZ(SPV)                                                                                 \
   if (sp == SPV) {                                                                                   \

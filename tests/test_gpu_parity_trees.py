@@ -178,18 +178,21 @@ def test_two_doublings_chunk_pairs(G, two_doublings):
 
 
 def test_two_doublings_transform_schedules(G, two_doublings):
-    """The three transform schedules (line passes; forward y and z passes
-    fused per (box, x-frequency) slab; forward and inverse fused) on all
-    three spline counts of the tree (s' = 9, 13, 21; FFT lengths 13, 21,
-    37), mixed form, 8 vectors: each against the oracle, and against the line
-    passes to FP32 rounding."""
+    """The four transform schedules (line passes; forward y and z passes
+    fused per (box, x-frequency) slab; forward and inverse fused; both fused
+    on the 9-spline level only, the default) on all three spline counts of
+    the tree (s' = 9, 13, 21; FFT lengths 13, 21, 37), mixed form, 8
+    vectors: each against the oracle, and against the line passes to FP32
+    rounding."""
     torch = _torch()
     V, T, k, p, delta, levels, ref_op = two_doublings
     X = E.complex_gaussian((8, ref_op.mesh.N), 80)
     Xd = torch.from_numpy(X).cuda()
     h = G.EFIE(V, T, k, p, delta, levels, precision=G.EFIE_MIXED)
     try:
-        assert h.transform_schedule() == 0
+        assert h.transform_schedule() == 3
+        Y3 = h.matvec(Xd).cpu().numpy()
+        assert h.transform_schedule(0) == 0
         Y0 = h.matvec(Xd).cpu().numpy()
         assert h.transform_schedule(1) == 1
         Y1 = h.matvec(Xd).cpu().numpy()
@@ -199,9 +202,10 @@ def test_two_doublings_transform_schedules(G, two_doublings):
         h.close()
     for r in (0, 3, 7):
         ref = ref_op.matvec(X[r])
-        for tag, Yv in (("lines", Y0), ("fused forward", Y1), ("fused both", Y2)):
+        for tag, Yv in (("lines", Y0), ("fused forward", Y1), ("fused both", Y2), ("fused on 9", Y3)):
             rel, mx = _errs(Yv[r], ref)
             print(f"transform schedule {tag} rhs {r}: rel l2 {rel:.3e}, max-abs {mx:.3e}")
             assert rel < TOL32 and mx < 10 * TOL32, (tag, r, rel, mx)
     assert np.linalg.norm(Y1 - Y0) < 1e-6 * np.linalg.norm(Y0)
     assert np.linalg.norm(Y2 - Y0) < 1e-6 * np.linalg.norm(Y0)
+    assert np.linalg.norm(Y3 - Y0) < 1e-6 * np.linalg.norm(Y0)
