@@ -74,8 +74,8 @@ def fp32_peak_tflops(sm_max_mhz):
 # (all 64 right-hand sides); translation_mac_top_tc: one top-level
 # k_mac_top_tc2<2> launch (one chunk pair).
 NCU_DRAM_BYTES_PER_LAUNCH = {
-    ("sphere20", "near_A"): 174.96e9 + 1.25e9,
-    ("sphere20", "translation_mac_top_tc"): 24.75e9 + 18.84e9,
+    ("sphere20", "near_A"): 174.58e9 + 1.26e9,
+    ("sphere20", "translation_mac_top_tc"): 25.08e9 + 18.84e9,
 }
 
 

@@ -347,17 +347,21 @@ __global__ void __launch_bounds__(128, 2)
 //   producers (2 warpgroups; chunk g goes to warpgroup g % 2): gather and
 //     split the kernel values of their target row into the A stage of chunk g
 //     (TMEM, tcgen05.st) and the source spectra into its B stage (shared
-//     memory), then arrive on full[g % 4];
+//     memory), then arrive on full[g % STG]; their global loads run ahead
+//     (offset ids two chunks, spectra one chunk);
 //   MMA warp (one lane): loads the kernel spectrum row of the next frequency
 //     by TMA bulk copies while the current one is in use, waits on full[],
-//     issues the 12 MMAs of a chunk (N = 64: B = [Q_r | Q_i] rows; the hi x hi,
-//     hi x lo and lo x hi products of K_r into D1 and of K_i into D2) and
-//     commits them to empty[g % 4], and after a tile's last chunk to dfull[];
-//   epilogue warpgroup: reads the tile's accumulators (double-buffered in
-//     TMEM), forms R_r = (K_r Q_r) - (K_i Q_i), R_i = (K_r Q_i) + (K_i Q_r),
-//     frees the buffer (dempty[]) and stores the complex rows.
-// Four chunk stages, two accumulator buffers, two kernel-row buffers; every
-// mbarrier wait is bounded and a timeout stops every role of the CTA.
+//     issues the 12 MMAs of a chunk (N = 64 NCH: B = [Q_r | Q_i] rows; the
+//     hi x hi, hi x lo and lo x hi products of K_r into D1 and of K_i into
+//     D2) and commits them to empty[g % STG], and after a tile's last chunk
+//     to dfull[];
+//   epilogue warpgroup: reads the tile's accumulators, forms
+//     R_r = (K_r Q_r) - (K_i Q_i), R_i = (K_r Q_i) + (K_i Q_r), frees the
+//     buffer (dempty[]) and stores the complex rows.
+// One 8-RHS chunk per pass (NCH = 1): four chunk stages, two accumulator
+// buffers; two chunks (NCH = 2): three stages, one accumulator buffer of 256
+// columns.  Two kernel-row buffers; every mbarrier wait is bounded and a
+// timeout stops every role of the CTA.
 namespace {
 constexpr int T2_PROD = 256;                  // producer threads (2 warpgroups)
 constexpr int T2_MMA_WARP = T2_PROD / 32;     // warp 8
