@@ -964,7 +964,9 @@ void do_matvec(efie_handle* h, const double2* x, int64_t ldx, double2* y, double
     double2* ya = yA ? yA + (int64_t)r0 * ldy : nullptr;
     double2* yv = yV ? yV + (int64_t)r0 * ldy : nullptr;
     if (pairs && n_rhs - r0 >= 16) {
-      const int np = (n_rhs - r0) / 16;
+      // at most 4 pairs (64 right-hand sides) per near-field pass, which
+      // bounds the work vectors (they grow with the right-hand sides of a pass)
+      const int np = std::min((n_rhs - r0) / 16, 4);
       matvec_pairs(h, x + (int64_t)r0 * ldx, ldx, yy, ya, yv, ldy, np, s);
       r0 += 16 * np;
       continue;
