@@ -53,6 +53,10 @@ extern "C" {
 #define EFIE_FACT_DIRECT 1      /* direct factorization (Sec. VI-B): RWG and RWG-divergence
                                    moments in the RWG's leaf box, one near set of RWG pairs
                                    holding A and Phi = Sigma V Sigma^T */
+#define EFIE_FACT_DYADIC 2      /* dyadic factorization (Sec. VI-C): the three RWG moment
+                                   components translated with g and with the Hessian of g
+                                   (the scalar part is -int int f_m . grad grad g . f_n), near
+                                   field as in the direct form */
 
 #define EFIE_PRECOND_NONE 0
 #define EFIE_PRECOND_LEARNED 1  /* learned mesh-local FGMRES preconditioner (not in
@@ -79,7 +83,7 @@ typedef struct {
     const char *weights_path;/* learned preconditioner weights, or NULL */
     int64_t device_mem_limit;/* bytes; 0 -> no limit beyond the device */
     uint64_t seed;
-    int32_t factorization;   /* EFIE_FACT_STAR (default) or EFIE_FACT_DIRECT */
+    int32_t factorization;   /* EFIE_FACT_STAR (default), EFIE_FACT_DIRECT or EFIE_FACT_DYADIC */
 } efie_options;
 
 /* Per-level summary filled by efie_plan / efie_level_info. */
@@ -226,7 +230,14 @@ int efie_plan_moments(const efie_mesh *mesh, double wavenumber, int spline_degre
  * divergence moments of every RWG in its own leaf box and interpolated back
  * onto them, and its near field Phi = Sigma V Sigma^T is assembled on the
  * RWG pairs of A's blocks (from the same triangle-pair integrals); products,
- * solves and the (A x, Phi x) split of efie_matvec_parts follow.  opt may be
+ * solves and the (A x, Phi x) split of efie_matvec_parts follow.  With
+ * EFIE_FACT_DYADIC (Sec. VI-C) the near field and moments are the direct
+ * form's, and the far scalar part comes instead from the three RWG moment
+ * components translated with the six entries of the Hessian of g (one more
+ * set of kernel spectra per entry and offset, and a second output grid per
+ * level); efie_matvec_parts returns (A x, -H x) with H the Hessian product
+ * plus Phi on the near pairs.  Both precisions; the mixed form's far field
+ * runs one chunk of right-hand sides at a time on CUDA cores.  opt may be
  * NULL (defaults).  EFIE_EINVAL for an unknown factorization.  On success
  * *out owns all device memory until efie_destroy. */
 int efie_setup(const efie_mesh *mesh, double wavenumber, int spline_degree,

@@ -15,13 +15,13 @@ import numpy as np
 
 __all__ = ["load_library", "Options", "EFIE", "Batch", "plan", "plan_matrix", "EfieError",
            "EFIE_FP64", "EFIE_MIXED", "EFIE_PRECOND_NONE", "EFIE_PRECOND_LEARNED", "EFIE_FACT_STAR",
-           "EFIE_FACT_DIRECT",
+           "EFIE_FACT_DIRECT", "EFIE_FACT_DYADIC",
            "EXPORTED_SYMBOLS"]
 
 EFIE_OK, EFIE_EINVAL, EFIE_ENOMEM, EFIE_ECUDA, EFIE_ETIMEOUT, EFIE_NOT_CONVERGED = 0, -1, -2, -3, -4, 1
 EFIE_FP64, EFIE_MIXED = 0, 1
 EFIE_PRECOND_NONE, EFIE_PRECOND_LEARNED = 0, 1
-EFIE_FACT_STAR, EFIE_FACT_DIRECT = 0, 1
+EFIE_FACT_STAR, EFIE_FACT_DIRECT, EFIE_FACT_DYADIC = 0, 1, 2
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libefie_gb300.so")

@@ -97,6 +97,7 @@ struct FarSet {
     cpx_t<R>* Mb = nullptr;
     R *CL = nullptr, *CR = nullptr, *CLt = nullptr, *CRt = nullptr;
     cpx_t<R>* Kh = nullptr;
+    cpx_t<R>* KH[6] = {};  // dyadic factorization: Hessian spectra, ab = 00, 01, 02, 11, 12, 22
   };
   std::vector<Lev> lv;
   int Rc = 0;
@@ -107,6 +108,11 @@ struct FarSet {
   // sources (Qt2) and results (Rt2)
   std::vector<cpx_t<R>*> q2, r2;
   cpx_t<R>*Qt2 = nullptr, *Rt2 = nullptr;
+  // dyadic factorization: level grids and a spectrum buffer of the Hessian
+  // translation, for chunks of up to Rd right-hand sides
+  int Rd = 0;
+  std::vector<cpx_t<R>*> rd;
+  cpx_t<R>* Rdh = nullptr;
 };
 
 struct LevDev {
@@ -237,6 +243,9 @@ struct efie_handle {
   // scalar (charge) part of the factorization: star (Sec. VI-A) pulses on the
   // triangles, or direct (Sec. VI-B) divergence moments of the RWGs
   bool direct = false;
+  bool dyadic = false;   // dyadic factorization (Sec. VI-C): direct-form near field and moments, plus the
+                         // Hessian translation of the three vector components
+  double2* wd = nullptr; // dyadic: scratch for the scalar output of the Hessian grids' interpolation
   int64_t n_sc = 0;                  // scalar items: triangles (star) or RWGs (direct)
   const int64_t* d_sc_box_ptr = nullptr;  // items of each leaf box
   const int32_t* d_sc_box = nullptr;      // leaf box of each item
@@ -406,23 +415,25 @@ void build_far(efie_handle* h, FarSet<R>& F, cudaStream_t s) {
 
 // kernel spectra K^_o for every level (FP64), converted to R
 template <typename R>
-void build_spectra(efie_handle* h, FarSet<R>& F, const std::vector<double2*>& K64, cudaStream_t s) {
+void build_spectra(efie_handle* h, FarSet<R>& F, const std::vector<double2*>& K64, cudaStream_t s,
+                   int comp = -1) {
   Plan& P = h->plan;
   for (int ell = P.D; ell >= P.top; --ell) {
     const LevDev& LD = h->lev[ell - P.top];
     const Level& L = P.L(ell);
     int64_t n3 = (int64_t)L.nfft * L.nfft * L.nfft;
     int64_t tot = n3 * std::max<int64_t>(LD.O, 1);
+    cpx_t<R>*& dst = comp < 0 ? F.lv[ell - P.top].Kh : F.lv[ell - P.top].KH[comp];
     if (sizeof(R) == 8) {
-      F.lv[ell - P.top].Kh = (cpx_t<R>*)K64[ell - P.top];
+      dst = (cpx_t<R>*)K64[ell - P.top];
     } else {
-      F.lv[ell - P.top].Kh = h->mem.alloc<cpx_t<R>>(tot);
-      launch_convert<R>(K64[ell - P.top], F.lv[ell - P.top].Kh, LD.O * n3, s);
+      dst = h->mem.alloc<cpx_t<R>>(tot);
+      launch_convert<R>(K64[ell - P.top], dst, LD.O * n3, s);
     }
   }
 }
 
-std::vector<double2*> build_kernel_spectra64(efie_handle* h, cudaStream_t s) {
+std::vector<double2*> build_kernel_spectra64(efie_handle* h, cudaStream_t s, int comp = -1) {
   Plan& P = h->plan;
   std::vector<double2*> out(P.lv.size(), nullptr);
   for (int ell = P.D; ell >= P.top; --ell) {
@@ -447,7 +458,7 @@ std::vector<double2*> build_kernel_spectra64(efie_handle* h, cudaStream_t s) {
     double2* b = h->mem.alloc<double2>(ob * n3);
     for (int64_t o0 = 0; o0 < O; o0 += ob) {
       int64_t no = std::min(ob, O - o0);
-      launch_kernel_samples(a, LD.offsets, o0, no, n, L.shat, L.h, L.Delta, P.k, s);
+      launch_kernel_samples(a, LD.offsets, o0, no, n, L.shat, L.h, L.Delta, P.k, comp, s);
       // [o][i0][i1][i2] -> DFT along each axis; last pass writes frequency-major
       View v0{n3, (int64_t)n * n, n, 1};
       launch_mode<double>(a, v0, b, v0, no, 1, 0, n, n, n, n, Fn, Fn, true, nullptr, nullptr, false, s);
@@ -501,7 +512,7 @@ void ensure_far_buffers(efie_handle* h, FarSet<R>& F, int Rc) {
 void ensure_work(efie_handle* h, int Rw) {
   if (h->Rw >= Rw) return;
   for (void* p : {(void*)h->xs, (void*)h->yA, (void*)h->rho, (void*)h->w, (void*)h->xs4, (void*)h->rho4,
-                  (void*)h->xsf, (void*)h->rhof, (void*)h->yAn, (void*)h->wn})
+                  (void*)h->xsf, (void*)h->rhof, (void*)h->yAn, (void*)h->wn, (void*)h->wd})
     h->mem.release(p);
   const int64_t N = h->plan.g.N, Nt = h->plan.g.nt;
   h->xs = h->mem.alloc<double2>(N * Rw);
@@ -510,6 +521,7 @@ void ensure_work(efie_handle* h, int Rw) {
   h->w = h->mem.alloc<double2>(h->n_sc * Rw);
   h->yAn = h->mem.alloc<double2>(N * Rw);
   h->wn = h->mem.alloc<double2>(h->n_sc * Rw);
+  if (h->dyadic) h->wd = h->mem.alloc<double2>(h->n_sc * Rw);
   if (h->near_df) {
     h->xs4 = h->mem.alloc<float4>(N * Rw);
     h->rho4 = h->mem.alloc<float4>(Nt * Rw);
@@ -558,7 +570,8 @@ void ensure_pair_buffers(efie_handle* h, FarSet<float>& F) {
 template <typename R>
 void run_mac(efie_handle* h, FarSet<R>& F, int ell, int C, const cpx_t<R>* Qin, cpx_t<R>* Rout, cudaStream_t s);
 template <typename R>
-void down_interp(efie_handle* h, FarSet<R>& F, int nr, int rhs0, std::vector<cpx_t<R>*>& rr, cudaStream_t s);
+void down_interp(efie_handle* h, FarSet<R>& F, int nr, int rhs0, std::vector<cpx_t<R>*>& rr, cudaStream_t s,
+                 double2* yout = nullptr, double2* wout = nullptr);
 
 template <typename R>
 void anterp_up(efie_handle* h, FarSet<R>& F, int nr, int rhs0, std::vector<cpx_t<R>*>& qq, cudaStream_t s) {
@@ -665,24 +678,68 @@ void inv_level(efie_handle* h, FarSet<R>& F, int ell, int C, const cpx_t<R>* Rin
     launch_mode<R>(F.tmp2, b2, rout, vq, B, C, 2, n, sp, sp, sp, FL.Mb, FL.Mb, true, nullptr, nullptr, false, s);
 }
 
+// grids and spectra of the Hessian translation (dyadic factorization) for
+// chunks of up to Rc right-hand sides
+template <typename R>
+void ensure_dyad_buffers(efie_handle* h, FarSet<R>& F, int Rc) {
+  if (F.Rd >= Rc) return;
+  Plan& P = h->plan;
+  for (auto* p : F.rd) h->mem.release(p);
+  if (F.Rdh) h->mem.release(F.Rdh);
+  const int64_t C = 4 * Rc;
+  F.rd.assign(P.lv.size(), nullptr);
+  int64_t smax = 1;
+  for (int ell = P.D; ell >= P.top; --ell) {
+    const Level& L = P.L(ell);
+    const int64_t B = (int64_t)L.code.size(), sp = L.sp, n = L.nfft;
+    F.rd[ell - P.top] = h->mem.alloc<cpx_t<R>>(B * sp * sp * sp * C);
+    smax = std::max(smax, B * n * n * n * C);
+  }
+  F.Rdh = h->mem.alloc<cpx_t<R>>(smax);
+  F.Rd = Rc;
+}
+
 template <typename R>
 void far_chunk(efie_handle* h, FarSet<R>& F, int nr, cudaStream_t s) {
   Plan& P = h->plan;
   const int C = 4 * nr;
+  if (h->dyadic) ensure_dyad_buffers<R>(h, F, nr);
   anterp_up<R>(h, F, nr, 0, F.q, s);
   for (int ell = P.D; ell >= P.top; --ell) {
     const Level& L = P.L(ell);
     const int64_t sp = L.sp;
     if (h->lev[ell - P.top].nfar == 0) {
-      cuda_check(cudaMemsetAsync(F.r[ell - P.top], 0, sizeof(cpx_t<R>) * (int64_t)L.code.size() * sp * sp * sp * C,
-                                 s), "memset r");
+      const size_t bytes = sizeof(cpx_t<R>) * (int64_t)L.code.size() * sp * sp * sp * C;
+      cuda_check(cudaMemsetAsync(F.r[ell - P.top], 0, bytes, s), "memset r");
+      if (h->dyadic) cuda_check(cudaMemsetAsync(F.rd[ell - P.top], 0, bytes, s), "memset r");
       continue;
     }
     fwd_level<R>(h, F, ell, C, F.q[ell - P.top], F.Qh, s);
     run_mac<R>(h, F, ell, C, F.Qh, F.Rh, s);
     inv_level<R>(h, F, ell, C, F.Rh, F.r[ell - P.top], s);
+    if (h->dyadic) {
+      // Hessian translation of the same spectra (Sec. VI-C)
+      const Level& Lv = P.L(ell);
+      const LevDev& LD = h->lev[ell - P.top];
+      const auto& FL = F.lv[ell - P.top];
+      KH6<R> K;
+      for (int c = 0; c < 6; ++c) K.k[c] = FL.KH[c];
+      {
+        KScope ks(h, K_MAC, s, 1);
+        launch_mac_dyad<R>(F.Qh, F.Rdh, K, (int64_t)Lv.code.size(), nr, (int64_t)Lv.nfft * Lv.nfft * Lv.nfft, LD.O,
+                           LD.il_ptr, LD.il_src, LD.il_off, s);
+      }
+      inv_level<R>(h, F, ell, C, F.Rdh, F.rd[ell - P.top], s);
+    }
   }
   down_interp<R>(h, F, nr, 0, F.r, s);
+  if (h->dyadic) {
+    // the Hessian grids' vector part is the scalar part of the product, with
+    // the sign of int int f_m . grad grad g . f_n = -Phi_mn: w = -(m . r_H)
+    down_interp<R>(h, F, nr, 0, F.rd, s, h->w, h->wd);
+    KScope ks(h, K_VEC, s, 1);
+    launch_lincomb(h->w, h->w, 0.0, -1.0, h->w, h->n_sc * nr, s);
+  }
 }
 
 template <typename R>
@@ -728,8 +785,11 @@ void run_mac(efie_handle* h, FarSet<R>& F, int ell, int C, const cpx_t<R>* Qin, 
     }
 }
 
+// downward transfers and interpolation of the output grids rr into the
+// vector part yout (default h->yA) and the scalar part wout (default h->w)
 template <typename R>
-void down_interp(efie_handle* h, FarSet<R>& F, int nr, int rhs0, std::vector<cpx_t<R>*>& rr, cudaStream_t s) {
+void down_interp(efie_handle* h, FarSet<R>& F, int nr, int rhs0, std::vector<cpx_t<R>*>& rr, cudaStream_t s,
+                 double2* yout, double2* wout) {
   Plan& P = h->plan;
   const int C = 4 * nr;
   const int D = P.D, top = P.top;
@@ -760,8 +820,9 @@ void down_interp(efie_handle* h, FarSet<R>& F, int nr, int rhs0, std::vector<cpx
     KScope ks(h, K_INTERP, s, 1);
     const Level& L = P.L(D);
     launch_interp<R>(F.mr, h->mr_base, h->mr_ext, h->mr_off, h->d_rwg_box, N, F.mt, h->mt_base, h->mt_ext,
-                     h->mt_off, h->d_sc_box, h->n_sc, rr[D - top], L.sp, nr, h->yA + (int64_t)rhs0 * N, N,
-                     h->w + (int64_t)rhs0 * h->n_sc, h->n_sc, s);
+                     h->mt_off, h->d_sc_box, h->n_sc, rr[D - top], L.sp, nr,
+                     (yout ? yout : h->yA) + (int64_t)rhs0 * N, N, (wout ? wout : h->w) + (int64_t)rhs0 * h->n_sc,
+                     h->n_sc, s);
   }
 }
 
@@ -849,7 +910,8 @@ void matvec_chunk(efie_handle* h, FarSet<R>& F, const double2* x, int64_t ldx, i
 // passes: FP32 far field, the automatic translation choice, and a top grid
 // level that the persistent tensor-core kernel takes with 128-row B operands.
 bool pair_fits(efie_handle* h) {
-  if (h->precision != EFIE_MIXED || (h->mac_variant != 0 && h->mac_variant != 4 && h->mac_variant != 5))
+  if (h->precision != EFIE_MIXED || h->dyadic ||
+      (h->mac_variant != 0 && h->mac_variant != 4 && h->mac_variant != 5))
     return false;
   const LevDev& LD = h->lev[0];
   return LD.nfar > 0 && (mac_top_tc3_fits(32, LD.max_tile, LD.O, LD.nq, LD.ntiles, 2) ||
@@ -1013,8 +1075,9 @@ bool make_index16(const std::vector<int64_t>& tgt_ptr, const std::vector<int64_t
 
 void setup_impl(efie_handle* h, const efie_mesh* mesh, double k, int p, double grid_spacing, int levels) {
   check_mesh(mesh);
-  if (h->opt.factorization != EFIE_FACT_STAR && h->opt.factorization != EFIE_FACT_DIRECT)
-    throw EfieError{EFIE_EINVAL, "factorization must be EFIE_FACT_STAR or EFIE_FACT_DIRECT"};
+  if (h->opt.factorization != EFIE_FACT_STAR && h->opt.factorization != EFIE_FACT_DIRECT &&
+      h->opt.factorization != EFIE_FACT_DYADIC)
+    throw EfieError{EFIE_EINVAL, "factorization must be EFIE_FACT_STAR, EFIE_FACT_DIRECT or EFIE_FACT_DYADIC"};
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0)
     throw EfieError{EFIE_ECUDA, "no CUDA device"};
@@ -1042,7 +1105,8 @@ void setup_impl(efie_handle* h, const efie_mesh* mesh, double k, int p, double g
     h->setup_s[i] = std::chrono::duration<double>(now - t_mark).count();
     t_mark = now;
   };
-  h->direct = h->opt.factorization == EFIE_FACT_DIRECT;
+  h->dyadic = h->opt.factorization == EFIE_FACT_DYADIC;
+  h->direct = h->opt.factorization == EFIE_FACT_DIRECT || h->dyadic;
   build_plan(P, mesh->xyz, mesh->n_vertices, mesh->tri, mesh->n_triangles, k, p, grid_spacing, levels,
              h->opt.n_splines, true, h->direct);
   phase_done(0);
@@ -1391,6 +1455,12 @@ void setup_impl(efie_handle* h, const efie_mesh* mesh, double k, int p, double g
     build_far<float>(h, h->f32, s);
     build_spectra<float>(h, h->f32, K64, s);
   }
+  if (h->dyadic)
+    for (int c = 0; c < 6; ++c) {
+      std::vector<double2*> KH = build_kernel_spectra64(h, s, c);
+      build_spectra<double>(h, h->f64, KH, s, c);
+      if (h->precision == EFIE_MIXED) build_spectra<float>(h, h->f32, KH, s, c);
+    }
   cuda_check(cudaStreamSynchronize(s), "setup");
   phase_done(3);
 }

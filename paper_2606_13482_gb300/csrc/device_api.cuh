@@ -160,8 +160,19 @@ void launch_mac(const cpx_t<R>* Qh, cpx_t<R>* Rh, const cpx_t<R>* Kh, int64_t B,
                 cudaStream_t s);
 
 
+// the six Hessian kernel spectra of the dyadic factorization (ab = 00, 01,
+// 02, 11, 12, 22), [n^3][O] each
+template <typename R>
+struct KH6 {
+  const cpx_t<R>* k[6];
+};
+// R[x][a] = sum_{y in IL(x)} sum_b H_ab(x - y) Q[y][b] for the three vector
+// components (Sec. VI-C), fourth component zero; Q, R [n^3][B][4 nr]
+template <typename R>
+void launch_mac_dyad(const cpx_t<R>* Q, cpx_t<R>* Rout, KH6<R> K, int64_t B, int nr, int64_t nf, int64_t O,
+                     const int64_t* il_ptr, const int32_t* il_src, const int32_t* il_off, cudaStream_t s);
 void launch_kernel_samples(double2* Kc, const int32_t* offsets, int64_t o0, int64_t no, int n,
-                           int shat, double h, double Delta, double k, cudaStream_t s);
+                           int shat, double h, double Delta, double k, int comp, cudaStream_t s);
 template <typename R>
 void launch_convert(const double2* in, cpx_t<R>* out, int64_t n, cudaStream_t s);
 

@@ -1549,33 +1549,110 @@ void launch_mac(const cpx_t<R>* Qh, cpx_t<R>* Rh, const cpx_t<R>* Kh, int64_t B,
 
 // ---------------------------------------------------------------- kernel samples
 // Kc[o][i0][i1][i2] = g(o h + t Delta), t_d = i_d (i_d < shat) or i_d - n, FP64.
+// Samples of the Green's function g(D) = exp(-jkR) / (4 pi R) (comp < 0) or
+// of one entry of its Hessian d_a d_b g (comp 0..5: ab = 00, 01, 02, 11, 12,
+// 22; the dyadic factorization of Sec. VI-C) at D = o h + t Delta, with
+//   d_a d_b g = g2 r_a r_b + (g1 / R) (delta_ab - r_a r_b),
+//   g1 = dg/dR = -(jk + 1/R) g,  g2 = d2g/dR2 = ((jk + 1/R)^2 + 1/R^2) g,
+// r = D / R.
 __global__ void k_kernel_samples(double2* __restrict__ Kc, const int32_t* __restrict__ offsets,
                                  int64_t o0, int64_t no, int n, int shat, double h, double Delta,
-                                 double k) {
+                                 double k, int comp) {
   const int64_t n3 = (int64_t)n * n * n;
   const int64_t total = no * n3;
+  const int ca = comp < 0 ? 0 : (comp < 3 ? 0 : (comp < 5 ? 1 : 2));
+  const int cb = comp < 0 ? 0 : (comp < 3 ? comp : (comp < 5 ? comp - 2 : 2));
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
     int64_t o = idx / n3, e = idx - o * n3;
     int i0 = (int)(e / (n * n)), i1 = (int)((e / n) % n), i2 = (int)(e % n);
     int t0 = i0 < shat ? i0 : i0 - n, t1 = i1 < shat ? i1 : i1 - n, t2 = i2 < shat ? i2 : i2 - n;
     const int32_t* ov = offsets + 3 * (o0 + o);
-    double d0 = ov[0] * h + t0 * Delta, d1 = ov[1] * h + t1 * Delta, d2 = ov[2] * h + t2 * Delta;
-    double R = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+    double d[3] = {ov[0] * h + t0 * Delta, ov[1] * h + t1 * Delta, ov[2] * h + t2 * Delta};
+    double R = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
     double sn, cs;
     sincos(k * R, &sn, &cs);
     double fct = 1.0 / (12.566370614359172953850573533118 * R);
-    Kc[idx] = make_double2(cs * fct, -sn * fct);
+    const double2 g = make_double2(cs * fct, -sn * fct);
+    if (comp < 0) {
+      Kc[idx] = g;
+      continue;
+    }
+    // a = 1/R + jk; g1 = -a g; g2 = (a^2 + 1/R^2) g = (2/R^2 - k^2 + 2jk/R) g
+    const double iR = 1.0 / R;
+    const double2 a = make_double2(iR, k);
+    const double2 g1 = make_double2(-(a.x * g.x - a.y * g.y), -(a.x * g.y + a.y * g.x));
+    const double2 c2 = make_double2(2.0 * iR * iR - k * k, 2.0 * k * iR);
+    const double2 g2 = make_double2(c2.x * g.x - c2.y * g.y, c2.x * g.y + c2.y * g.x);
+    const double rr = d[ca] * d[cb] * iR * iR;
+    const double dl = (ca == cb ? 1.0 : 0.0) - rr;
+    Kc[idx] = make_double2(g2.x * rr + g1.x * iR * dl, g2.y * rr + g1.y * iR * dl);
   }
 }
 
+// Dyadic translation (Sec. VI-C): for every frequency, target box x and
+// right-hand side c, R[x][a] = sum_{y in IL(x)} sum_b H_ab(x - y) Q[y][b] over
+// the three vector components a, b (H symmetric: six spectra, ab = 00, 01,
+// 02, 11, 12, 22); the fourth component of R is set to zero.  Q and R are
+// [n^3][B][4 nr] (component-major channels), K[ab] are [n^3][O].  One thread
+// per (frequency, box, right-hand side), the interaction lists of the level.
+template <typename R>
+__global__ void k_mac_dyad(const cpx_t<R>* __restrict__ Q, cpx_t<R>* __restrict__ Rout, KH6<R> K, int64_t B,
+                           int nr, int64_t nf, int64_t O, const int64_t* __restrict__ il_ptr,
+                           const int32_t* __restrict__ il_src, const int32_t* __restrict__ il_off) {
+  using T = cpx_t<R>;
+  const int64_t C = 4 * nr;
+  const int64_t total = nf * B * nr;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(idx % nr);
+    const int64_t x = (idx / nr) % B, f = idx / (nr * B);
+    T acc[3] = {mk<R>(0, 0), mk<R>(0, 0), mk<R>(0, 0)};
+    for (int64_t e = il_ptr[x]; e < il_ptr[x + 1]; ++e) {
+      const T* q = Q + (f * B + il_src[e]) * C + c;
+      const T q0 = q[0], q1 = q[nr], q2 = q[2 * nr];
+      const int64_t ko = f * O + il_off[e];
+      const T h00 = K.k[0][ko], h01 = K.k[1][ko], h02 = K.k[2][ko];
+      const T h11 = K.k[3][ko], h12 = K.k[4][ko], h22 = K.k[5][ko];
+      cfma(acc[0], h00, q0);
+      cfma(acc[0], h01, q1);
+      cfma(acc[0], h02, q2);
+      cfma(acc[1], h01, q0);
+      cfma(acc[1], h11, q1);
+      cfma(acc[1], h12, q2);
+      cfma(acc[2], h02, q0);
+      cfma(acc[2], h12, q1);
+      cfma(acc[2], h22, q2);
+    }
+    T* r = Rout + (f * B + x) * C + c;
+    r[0] = acc[0];
+    r[nr] = acc[1];
+    r[2 * nr] = acc[2];
+    r[3 * nr] = mk<R>(0, 0);
+  }
+}
+
+template <typename R>
+void launch_mac_dyad(const cpx_t<R>* Q, cpx_t<R>* Rout, KH6<R> K, int64_t B, int nr, int64_t nf, int64_t O,
+                     const int64_t* il_ptr, const int32_t* il_src, const int32_t* il_off, cudaStream_t s) {
+  const int64_t total = nf * B * nr;
+  if (total <= 0) return;
+  int64_t blocks = ceil_div(total, 256);
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  k_mac_dyad<R><<<(unsigned)blocks, 256, 0, s>>>(Q, Rout, K, B, nr, nf, O, il_ptr, il_src, il_off);
+}
+template void launch_mac_dyad<float>(const float2*, float2*, KH6<float>, int64_t, int, int64_t, int64_t,
+                                     const int64_t*, const int32_t*, const int32_t*, cudaStream_t);
+template void launch_mac_dyad<double>(const double2*, double2*, KH6<double>, int64_t, int, int64_t, int64_t,
+                                      const int64_t*, const int32_t*, const int32_t*, cudaStream_t);
+
 void launch_kernel_samples(double2* Kc, const int32_t* offsets, int64_t o0, int64_t no, int n,
-                           int shat, double h, double Delta, double k, cudaStream_t s) {
+                           int shat, double h, double Delta, double k, int comp, cudaStream_t s) {
   int64_t total = no * (int64_t)n * n * n;
   if (total <= 0) return;
   int64_t blocks = ceil_div(total, 256);
   if (blocks > 152 * 64) blocks = 152 * 64;
-  k_kernel_samples<<<(unsigned)blocks, 256, 0, s>>>(Kc, offsets, o0, no, n, shat, h, Delta, k);
+  k_kernel_samples<<<(unsigned)blocks, 256, 0, s>>>(Kc, offsets, o0, no, n, shat, h, Delta, k, comp);
 }
 
 template <typename R>
