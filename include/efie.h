@@ -161,7 +161,8 @@ typedef struct {
  * pairs included).  Any output pointer may be NULL.  topt NULL -> the paper's
  * values (200, 0.25, top 2).  EFIE_EINVAL for a bad mesh or parameters, a
  * leaf above the top level, or buffer splines that close the gap between far
- * interpolation domains.  The device path does not take nonuniform trees yet. */
+ * interpolation domains.  efie_setup_adaptive sets up the device pipeline on
+ * the same tree. */
 int efie_plan_adaptive(const efie_mesh *mesh, double wavenumber, int spline_degree,
                        const efie_tree_options *topt, efie_adaptive_level_t *levels_out, int max_levels,
                        int32_t *n_levels, int64_t *near_pairs_rwg, int64_t *near_pairs_tri);
@@ -243,6 +244,21 @@ int efie_plan_moments(const efie_mesh *mesh, double wavenumber, int spline_degre
 int efie_setup(const efie_mesh *mesh, double wavenumber, int spline_degree,
                double grid_spacing, int levels, const efie_options *opt,
                efie_handle **out);
+
+/* efie_setup on the nonuniform octree of efie_plan_adaptive (Sec. VII tree
+ * rule, topt NULL -> the paper's values): every level's grids take the
+ * anterpolation of the functions whose leaves lie on it (each in its own
+ * leaf's splines) before the upward transfer to the parent level, the
+ * translations of the level's interaction lists, and after the downward
+ * transfer the interpolation onto those functions; the near field holds the
+ * RWG (A) and triangle (V) pairs of near leaves, leaves of different levels
+ * included.  Everything else (precisions, products, solves, batching of
+ * right-hand sides) as with efie_setup, in the star factorization (Sec. VI-A;
+ * EFIE_EINVAL for another opt->factorization); the spline count of the
+ * deepest level is topt->n_splines (opt->n_splines is not used).  Errors as
+ * efie_setup and efie_plan_adaptive. */
+int efie_setup_adaptive(const efie_mesh *mesh, double wavenumber, int spline_degree,
+                        const efie_tree_options *topt, const efie_options *opt, efie_handle **out);
 
 int efie_num_unknowns(const efie_handle *h, int64_t *n);
 int efie_plan_info(const efie_handle *h, efie_plan_info_t *info);

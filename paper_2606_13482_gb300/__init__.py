@@ -27,7 +27,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libefie_gb300.so")
 
 EXPORTED_SYMBOLS = [
-    "efie_plan", "efie_plan_adaptive", "efie_plan_adaptive_near", "efie_plan_adaptive_moments", "efie_plan_matrix", "efie_plan_moments", "efie_setup", "efie_num_unknowns", "efie_plan_info",
+    "efie_plan", "efie_plan_adaptive", "efie_plan_adaptive_near", "efie_plan_adaptive_moments", "efie_plan_matrix", "efie_plan_moments", "efie_setup", "efie_setup_adaptive", "efie_num_unknowns", "efie_plan_info",
     "efie_rwg_edges", "efie_rhs_planewave", "efie_rhs_planewave_noalloc", "efie_matvec", "efie_matvec_host",
     "efie_matvec_fp64",
     "efie_matvec_parts", "efie_solve", "efie_precond_harvest", "efie_precond_train", "efie_precond_save",
@@ -119,6 +119,7 @@ def load_library(path: str = LIB_PATH):
     lib.efie_plan_moments.argtypes = [P(_Mesh), D, ctypes.c_int, D, ctypes.c_int, P(Options), ctypes.c_int,
                                       P(I32), I64, P(D), I64, P(I32)]
     lib.efie_setup.argtypes = [P(_Mesh), D, ctypes.c_int, D, ctypes.c_int, P(Options), P(VP)]
+    lib.efie_setup_adaptive.argtypes = [P(_Mesh), D, ctypes.c_int, P(TreeOptions), P(Options), P(VP)]
     lib.efie_num_unknowns.argtypes = [VP, P(I64)]
     lib.efie_plan_info.argtypes = [VP, P(PlanInfo)]
     lib.efie_rwg_edges.argtypes = [VP, P(I32), P(I32)]
@@ -335,7 +336,11 @@ def plan_moments(V, T, k, p, grid_spacing, levels, kind, ids, options: Options |
 class EFIE:
     """Handle to a set-up problem on the current CUDA device."""
 
-    def __init__(self, V, T, k, p, grid_spacing, levels, precision=EFIE_FP64, **opts):
+    def __init__(self, V, T, k, p, grid_spacing, levels, precision=EFIE_FP64, tree=None, **opts):
+        """Uniform octree of (grid_spacing, levels) (efie_setup), or with
+        `tree` = dict(max_elems, max_prot, top, n_splines, max_depth) the
+        nonuniform octree of Sec. VII (efie_setup_adaptive; grid_spacing and
+        levels unused)."""
         import torch  # noqa: F401  (device memory and streams)
         self.lib = load_library()
         o = Options()
@@ -345,8 +350,15 @@ class EFIE:
         self.options = o
         m, keep = _mesh(V, T)
         h = ctypes.c_void_p()
-        _check(self.lib, self.lib.efie_setup(ctypes.byref(m), k, p, grid_spacing, levels, ctypes.byref(o),
-                                             ctypes.byref(h)))
+        if tree is None:
+            _check(self.lib, self.lib.efie_setup(ctypes.byref(m), k, p, grid_spacing, levels, ctypes.byref(o),
+                                                 ctypes.byref(h)))
+        else:
+            t = dict(max_elems=200, max_prot=0.25, top=2, n_splines=0, max_depth=0)
+            t.update(tree)
+            to = TreeOptions(t["max_elems"], t["max_prot"], t["top"], t["n_splines"], t["max_depth"])
+            _check(self.lib, self.lib.efie_setup_adaptive(ctypes.byref(m), k, p, ctypes.byref(to), ctypes.byref(o),
+                                                          ctypes.byref(h)))
         self.h = h
         n = ctypes.c_int64()
         self.lib.efie_num_unknowns(self.h, ctypes.byref(n))

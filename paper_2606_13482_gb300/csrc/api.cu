@@ -4,6 +4,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <functional>
 #include <cmath>
 #include <complex>
 #include <cstring>
@@ -150,6 +151,13 @@ struct LevDev {
          *ux_b1 = nullptr;
   int64_t *dx_src = nullptr, *dy_src = nullptr, *dz_src = nullptr;  // downward: g2 -> parent, g1 -> g2, child -> g1
   int8_t *dx_sel = nullptr, *dy_sel = nullptr;                      // [G][3]
+  // leaves of the tree on this level (all boxes of level D in a uniform tree;
+  // several levels in a nonuniform one): global leaf ids [leaf0, leaf0 + nleaf),
+  // their box indices (null when they are the level's boxes in order), and the
+  // gather-list offsets of their grid points
+  int64_t leaf0 = 0, nleaf = 0;
+  int32_t* leaf_box = nullptr;
+  int32_t *gptr_r = nullptr, *gptr_t = nullptr;
 };
 
 std::complex<double> jk_of(double k) { return std::complex<double>(0.0, k); }
@@ -247,14 +255,16 @@ struct efie_handle {
                          // Hessian translation of the three vector components
   double2* wd = nullptr; // dyadic: scratch for the scalar output of the Hessian grids' interpolation
   int64_t n_sc = 0;                  // scalar items: triangles (star) or RWGs (direct)
-  const int64_t* d_sc_box_ptr = nullptr;  // items of each leaf box
-  const int32_t* d_sc_box = nullptr;      // leaf box of each item
+  const int64_t* d_sc_box_ptr = nullptr;  // items of each leaf
+  const int32_t* d_sc_box = nullptr;      // leaf of each item
+  // box of each sorted function on its leaf's level (RWG, triangle, scalar item)
+  int32_t *d_rwg_lbox = nullptr, *d_tri_lbox = nullptr;
+  const int32_t* d_sc_lbox = nullptr;
   const int64_t* d_blkS_off = nullptr;    // near blocks of the scalar part (V, or Phi in A's layout)
   int8_t* d_tri_sgn = nullptr;
   // moments structure (shared by precisions)
   int32_t *mr_base = nullptr, *mr_ext = nullptr, *mt_base = nullptr, *mt_ext = nullptr;
   int64_t *mr_off = nullptr, *mt_off = nullptr;
-  int32_t *gptr_r = nullptr, *gptr_t = nullptr;  // gather-list offsets per leaf box and grid point
   // near
   NearDev nd{};
   int64_t *d_near_ptr = nullptr, *d_blkA_off = nullptr, *d_blkV_off = nullptr;
@@ -372,17 +382,22 @@ void build_far(efie_handle* h, FarSet<R>& F, cudaStream_t s) {
   std::vector<R> mt(MS.data.begin(), MS.data.end());
   F.mr = M.upload(mr);
   F.mt = M.upload(mt);
-  {
-    const Level& L = P.L(P.D);
-    const int64_t B = (int64_t)L.code.size(), npts = (int64_t)L.sp * L.sp * L.sp;
-    if (!h->gptr_r) {
-      h->gptr_r = M.alloc<int32_t>(B * (npts + 1));
-      h->gptr_t = M.alloc<int32_t>(B * (npts + 1));
+  F.gr = M.alloc<R>((int64_t)mr.size() / 3 * 4);
+  F.gt = M.alloc<R>((int64_t)mt.size() * 2);
+  for (int ell = P.D; ell >= P.top; --ell) {
+    // gather lists of the leaves of every level (the moment entries are the
+    // same in both precisions, so the offsets are built once)
+    LevDev& LD = h->lev[ell - P.top];
+    if (LD.nleaf == 0) continue;
+    const Level& L = P.L(ell);
+    const int64_t npts = (int64_t)L.sp * L.sp * L.sp;
+    if (!LD.gptr_r) {
+      LD.gptr_r = M.alloc<int32_t>(LD.nleaf * (npts + 1));
+      LD.gptr_t = M.alloc<int32_t>(LD.nleaf * (npts + 1));
     }
-    F.gr = M.alloc<R>((int64_t)mr.size() / 3 * 4);
-    F.gt = M.alloc<R>((int64_t)mt.size() * 2);
     launch_gather_build<R>(F.mr, h->mr_base, h->mr_ext, h->mr_off, F.mt, h->mt_base, h->mt_ext, h->mt_off,
-                           h->d_box_rwg_ptr, h->d_sc_box_ptr, B, L.sp, h->gptr_r, h->gptr_t, F.gr, F.gt, s);
+                           h->d_box_rwg_ptr + LD.leaf0, h->d_sc_box_ptr + LD.leaf0, LD.nleaf, L.sp, LD.gptr_r,
+                           LD.gptr_t, F.gr, F.gt, s);
     cuda_check(cudaGetLastError(), "gather lists");
   }
   F.lv.assign(P.lv.size(), {});
@@ -579,9 +594,12 @@ void anterp_up(efie_handle* h, FarSet<R>& F, int nr, int rhs0, std::vector<cpx_t
   const int C = 4 * nr;
   const int D = P.D, top = P.top;
   const int64_t N = P.g.N, Nt = P.g.nt;
-  // anterpolation of the currents and charges into the leaf grids (Sec. VI-A)
-  {
-    const Level& L = P.L(D);
+  // anterpolation of the currents and charges into the grids of the leaves
+  // of level ell (Sec. VI-A; every box of level D in a uniform tree)
+  auto anterp = [&](int ell) {
+    const Level& L = P.L(ell);
+    const LevDev& LV = h->lev[ell - top];
+    if (LV.nleaf == 0) return;
     const cpx_t<R>* xin = (const cpx_t<R>*)(h->xs + (int64_t)rhs0 * N);
     // scalar part: the charges (star) or the currents themselves (direct)
     const cpx_t<R>* rin = h->direct ? xin : (const cpx_t<R>*)(h->rho + (int64_t)rhs0 * Nt);
@@ -593,11 +611,14 @@ void anterp_up(efie_handle* h, FarSet<R>& F, int nr, int rhs0, std::vector<cpx_t
       xin = (const cpx_t<R>*)(h->xsf + (int64_t)rhs0 * N);
       rin = h->direct ? xin : (const cpx_t<R>*)(h->rhof + (int64_t)rhs0 * Nt);
     }
-    launch_anterp<R>(F.gr, F.gt, h->gptr_r, h->gptr_t, h->mr_off, h->mt_off, h->d_box_rwg_ptr,
-                     h->d_sc_box_ptr, (int64_t)L.code.size(), xin, N, rin, h->direct ? N : Nt, nr, qq[D - top],
-                     L.sp, s);
-  }
-  // upward transfers (Sec. IV-B), shared among siblings one axis at a time (z, y, x)
+    launch_anterp<R>(F.gr, F.gt, LV.gptr_r, LV.gptr_t, h->mr_off, h->mt_off, h->d_box_rwg_ptr + LV.leaf0,
+                     h->d_sc_box_ptr + LV.leaf0, LV.nleaf, LV.leaf_box, xin, N, rin, h->direct ? N : Nt, nr,
+                     qq[ell - top], L.sp, s);
+  };
+  anterp(D);
+  // upward transfers (Sec. IV-B), shared among siblings one axis at a time (z,
+  // y, x); a nonuniform tree's leaves on the parent level are anterpolated
+  // after the transfer into that level, over its zeros
   for (int ell = D; ell > top; --ell) {
     KScope ks(h, K_UP, s, 3);
     const Level& L = P.L(ell);
@@ -616,6 +637,7 @@ void anterp_up(efie_handle* h, FarSet<R>& F, int nr, int rhs0, std::vector<cpx_t
                         LD.uy_s1, LD.uy_b0, LD.uy_b1, s);
     launch_mode_pair<R>(F.tmp2, t2, qq[ell - 1 - top], vp, Bp, C, 0, sp, spp, spp, spp, FL.CL, FL.CR, LD.ux_s0,
                         LD.ux_s1, LD.ux_b0, LD.ux_b1, s);
+    anterp(ell - 1);
   }
 }
 
@@ -815,14 +837,21 @@ void down_interp(efie_handle* h, FarSet<R>& F, int nr, int rhs0, std::vector<cpx
     launch_mode<R>(F.tmp2, w2, rr[ell - top], vq, B, C, 2, spp, sp, sp, sp, FL.CLt, FL.CRt, false, LD.bits,
                    LD.dz_src, true, s);
   }
-  // interpolation onto the RWG test functions and the charges (Sec. VI-A)
-  {
+  // interpolation onto the RWG test functions and the charges (Sec. VI-A),
+  // level by level over the functions whose leaves lie there
+  double2* ya = (yout ? yout : h->yA) + (int64_t)rhs0 * N;
+  double2* wa = (wout ? wout : h->w) + (int64_t)rhs0 * h->n_sc;
+  const int64_t* sc_ptr = h->direct ? P.box_rwg_ptr.data() : P.box_tri_ptr.data();
+  for (int ell = top; ell <= D; ++ell) {
+    const LevDev& LV = h->lev[ell - top];
+    if (LV.nleaf == 0) continue;
     KScope ks(h, K_INTERP, s, 1);
-    const Level& L = P.L(D);
-    launch_interp<R>(F.mr, h->mr_base, h->mr_ext, h->mr_off, h->d_rwg_box, N, F.mt, h->mt_base, h->mt_ext,
-                     h->mt_off, h->d_sc_box, h->n_sc, rr[D - top], L.sp, nr,
-                     (yout ? yout : h->yA) + (int64_t)rhs0 * N, N, (wout ? wout : h->w) + (int64_t)rhs0 * h->n_sc,
-                     h->n_sc, s);
+    const Level& L = P.L(ell);
+    const int64_t i0 = P.box_rwg_ptr[LV.leaf0], i1 = P.box_rwg_ptr[LV.leaf0 + LV.nleaf];
+    const int64_t t0 = sc_ptr[LV.leaf0], t1 = sc_ptr[LV.leaf0 + LV.nleaf];
+    launch_interp<R>(F.mr, h->mr_base + 3 * i0, h->mr_ext + 3 * i0, h->mr_off + i0, h->d_rwg_lbox + i0, i1 - i0,
+                     F.mt, h->mt_base + 3 * t0, h->mt_ext + 3 * t0, h->mt_off + t0, h->d_sc_lbox + t0, t1 - t0,
+                     rr[ell - top], L.sp, nr, ya + i0, N, wa + t0, h->n_sc, s);
   }
 }
 
@@ -835,7 +864,7 @@ void down_interp(efie_handle* h, FarSet<R>& F, int nr, int rhs0, std::vector<cpx
 void near_fork(efie_handle* h, int nr, cudaStream_t s) {
   Plan& P = h->plan;
   const int64_t N = P.g.N, Nt = P.g.nt;
-  const int64_t BD = (int64_t)P.L(P.D).code.size();
+  const int64_t BD = P.n_leaves;
   cudaStream_t sn = h->s_near;
   cuda_check(cudaEventRecord(h->ev_fork, s), "near fork");
   cuda_check(cudaStreamWaitEvent(sn, h->ev_fork, 0), "near fork");
@@ -1073,7 +1102,11 @@ bool make_index16(const std::vector<int64_t>& tgt_ptr, const std::vector<int64_t
   return true;
 }
 
-void setup_impl(efie_handle* h, const efie_mesh* mesh, double k, int p, double grid_spacing, int levels) {
+// tree: null for the uniform octree of (grid_spacing, levels); else the
+// nonuniform octree of Sec. VII with these options (grid_spacing and levels
+// unused)
+void setup_impl(efie_handle* h, const efie_mesh* mesh, double k, int p, double grid_spacing, int levels,
+                const AdaptiveOptions* tree = nullptr) {
   check_mesh(mesh);
   if (h->opt.factorization != EFIE_FACT_STAR && h->opt.factorization != EFIE_FACT_DIRECT &&
       h->opt.factorization != EFIE_FACT_DYADIC)
@@ -1107,8 +1140,14 @@ void setup_impl(efie_handle* h, const efie_mesh* mesh, double k, int p, double g
   };
   h->dyadic = h->opt.factorization == EFIE_FACT_DYADIC;
   h->direct = h->opt.factorization == EFIE_FACT_DIRECT || h->dyadic;
-  build_plan(P, mesh->xyz, mesh->n_vertices, mesh->tri, mesh->n_triangles, k, p, grid_spacing, levels,
-             h->opt.n_splines, true, h->direct);
+  if (tree && h->opt.factorization != EFIE_FACT_STAR)
+    throw EfieError{EFIE_EINVAL, "the nonuniform tree takes the star factorization (EFIE_FACT_STAR)"};
+  if (tree)
+    build_plan_adaptive(P, mesh->xyz, mesh->n_vertices, mesh->tri, mesh->n_triangles, k, p, *tree, true,
+                        h->direct);
+  else
+    build_plan(P, mesh->xyz, mesh->n_vertices, mesh->tri, mesh->n_triangles, k, p, grid_spacing, levels,
+               h->opt.n_splines, true, h->direct);
   phase_done(0);
   DevMem& M = h->mem;
   cudaStream_t s = 0;
@@ -1137,6 +1176,9 @@ void setup_impl(efie_handle* h, const efie_mesh* mesh, double k, int p, double g
   h->n_sc = h->direct ? N : Nt;
   h->d_sc_box_ptr = h->direct ? h->d_box_rwg_ptr : h->d_box_tri_ptr;
   h->d_sc_box = h->direct ? h->d_rwg_box : h->d_tri_box;
+  h->d_rwg_lbox = P.adaptive ? M.upload(P.rwg_lbox) : h->d_rwg_box;
+  h->d_tri_lbox = P.adaptive ? M.upload(P.tri_lbox) : h->d_tri_box;
+  h->d_sc_lbox = h->direct ? h->d_rwg_lbox : h->d_tri_lbox;
   {
     // per sorted triangle: its RWGs (sorted index) and signs
     std::vector<int32_t> tr(3 * Nt, -1);
@@ -1168,6 +1210,13 @@ void setup_impl(efie_handle* h, const efie_mesh* mesh, double k, int p, double g
     const Level& L = P.L(ell);
     LevDev& LD = h->lev[ell - P.top];
     LD.B = (int64_t)L.code.size();
+    LD.leaf0 = P.level_leaf_ptr[ell - P.top];
+    LD.nleaf = P.level_leaf_ptr[ell - P.top + 1] - LD.leaf0;
+    if (LD.nleaf > 0 && LD.nleaf != LD.B) {
+      std::vector<int32_t> lb(LD.nleaf);
+      for (int64_t x = 0; x < LD.nleaf; ++x) lb[x] = (int32_t)P.leaf_box[LD.leaf0 + x];
+      LD.leaf_box = M.upload(lb);
+    }
     LD.il_ptr = M.upload(L.il_ptr);
     LD.il_src = M.upload(L.il_src);
     LD.il_off = M.upload(L.il_off);
@@ -1244,7 +1293,9 @@ void setup_impl(efie_handle* h, const efie_mesh* mesh, double k, int p, double g
             xb1[pb] = (int8_t)bx;
           }
         }
-        if (x0[pb] < 0) throw EfieError{EFIE_EINVAL, "internal: parent box without children"};
+        // a parent without children is a leaf (nonuniform tree): the upward
+        // pass writes zeros there, and the leaf's own anterpolation follows
+        if (x0[pb] < 0 && !U.leaf[pb]) throw EfieError{EFIE_EINVAL, "internal: parent box without children"};
       }
       LD.ng1 = (int64_t)z0.size();
       LD.ng2 = (int64_t)y0.size();
@@ -1317,8 +1368,7 @@ void setup_impl(efie_handle* h, const efie_mesh* mesh, double k, int p, double g
   phase_done(1);
   // near field (FP64)
   {
-    const Level& LD = P.L(P.D);
-    int64_t BD = (int64_t)LD.code.size();
+    const int64_t BD = P.n_leaves;
     h->d_near_ptr = M.upload(P.near_ptr);
     h->d_near_src = M.upload(P.near_src);
     h->d_blkA_off = M.upload(P.blkA_off);
@@ -1903,28 +1953,30 @@ int efie_plan_adaptive(const efie_mesh* mesh, double wavenumber, int spline_degr
   return guarded(nullptr, [&] {
     check_mesh(mesh);
     if (max_levels < 0) throw EfieError{EFIE_EINVAL, "max_levels < 0"};
-    AdaptivePlan A;
-    build_adaptive_plan(A, mesh->xyz, mesh->n_vertices, mesh->tri, mesh->n_triangles, wavenumber, spline_degree,
-                        adaptive_options(topt));
-    const int nl = (int)A.lv.size();
+    // the plan the device pipeline runs (efie_setup_adaptive): its
+    // interaction lists, leaves and near blocks are what is reported
+    Plan P;
+    build_plan_adaptive(P, mesh->xyz, mesh->n_vertices, mesh->tri, mesh->n_triangles, wavenumber, spline_degree,
+                        adaptive_options(topt), false);
+    const int nl = (int)P.lv.size();
     if (n_levels) *n_levels = nl;
-    if (near_pairs_rwg) *near_pairs_rwg = A.near_pairs_rwg;
-    if (near_pairs_tri) *near_pairs_tri = A.near_pairs_tri;
+    if (near_pairs_rwg) *near_pairs_rwg = P.nnzA;
+    if (near_pairs_tri) *near_pairs_tri = P.nnzV;
     if (levels_out)
       for (int i = 0; i < std::min(nl, max_levels); ++i) {
-        const AdaptiveLevel& L = A.lv[i];
+        const Level& L = P.lv[i];
         efie_adaptive_level_t& out = levels_out[i];
         out.level = L.level;
         out.s = L.s;
         out.sb = L.sb;
         out.sp = L.sp;
         out.shat = L.shat;
-        out.n_boxes = (int64_t)L.key.size();
-        out.n_leaves = 0;
-        for (uint8_t f : L.leaf) out.n_leaves += f;
-        out.n_far_pairs = L.n_far_pairs;
-        out.n_leaf_rwg = L.n_leaf_rwg;
-        out.n_leaf_tri = L.n_leaf_tri;
+        out.n_boxes = (int64_t)L.code.size();
+        const int64_t l0 = P.level_leaf_ptr[i], l1 = P.level_leaf_ptr[i + 1];
+        out.n_leaves = l1 - l0;
+        out.n_far_pairs = (int64_t)L.il_src.size();
+        out.n_leaf_rwg = P.box_rwg_ptr[l1] - P.box_rwg_ptr[l0];
+        out.n_leaf_tri = P.box_tri_ptr[l1] - P.box_tri_ptr[l0];
         out.h = L.h;
         out.delta = L.delta;
       }
@@ -2085,8 +2137,8 @@ int efie_plan_moments(const efie_mesh* mesh, double wavenumber, int spline_degre
   });
 }
 
-int efie_setup(const efie_mesh* mesh, double wavenumber, int spline_degree, double grid_spacing, int levels,
-               const efie_options* opt, efie_handle** out) {
+namespace {
+int setup_handle(const efie_options* opt, efie_handle** out, const std::function<void(efie_handle*)>& run) {
   if (!out) {
     g_last_error = "out is NULL";
     return EFIE_EINVAL;
@@ -2100,7 +2152,7 @@ int efie_setup(const efie_mesh* mesh, double wavenumber, int spline_degree, doub
   h->opt = defaults(opt);
   h->precision = h->opt.precision;
   int rc = guarded(h, [&] {
-    setup_impl(h, mesh, wavenumber, spline_degree, grid_spacing, levels);
+    run(h);
     return EFIE_OK;
   });
   if (rc != EFIE_OK) {
@@ -2110,6 +2162,22 @@ int efie_setup(const efie_mesh* mesh, double wavenumber, int spline_degree, doub
   }
   *out = h;
   return EFIE_OK;
+}
+}  // namespace
+
+int efie_setup(const efie_mesh* mesh, double wavenumber, int spline_degree, double grid_spacing, int levels,
+               const efie_options* opt, efie_handle** out) {
+  return setup_handle(opt, out, [&](efie_handle* h) {
+    setup_impl(h, mesh, wavenumber, spline_degree, grid_spacing, levels);
+  });
+}
+
+int efie_setup_adaptive(const efie_mesh* mesh, double wavenumber, int spline_degree, const efie_tree_options* topt,
+                        const efie_options* opt, efie_handle** out) {
+  return setup_handle(opt, out, [&](efie_handle* h) {
+    const AdaptiveOptions o = adaptive_options(topt);
+    setup_impl(h, mesh, wavenumber, spline_degree, 0.0, 0, &o);
+  });
 }
 
 int efie_num_unknowns(const efie_handle* h, int64_t* n) {

@@ -140,11 +140,12 @@ void launch_gather_build(const R* mr, const int32_t* mr_base, const int32_t* mr_
                          const int64_t* box_rwg_ptr, const int64_t* box_tri_ptr, int64_t B, int sp,
                          int32_t* gptr_r, int32_t* gptr_t, R* gr, R* gt, cudaStream_t s);
 
+// out_box: grid box of each of the B leaves (null: leaf b writes box b)
 template <typename R>
 void launch_anterp(const R* gr, const R* gt, const int32_t* gptr_r, const int32_t* gptr_t, const int64_t* mr_off,
                    const int64_t* mt_off, const int64_t* box_rwg_ptr, const int64_t* box_tri_ptr, int64_t B,
-                   const cpx_t<R>* xs, int64_t ldx, const cpx_t<R>* rho, int64_t ldr, int nr, cpx_t<R>* q,
-                   int sp, cudaStream_t s);
+                   const int32_t* out_box, const cpx_t<R>* xs, int64_t ldx, const cpx_t<R>* rho, int64_t ldr, int nr,
+                   cpx_t<R>* q, int sp, cudaStream_t s);
 
 template <typename R>
 void launch_interp(const R* mr, const int32_t* mr_base, const int32_t* mr_ext, const int64_t* mr_off,

@@ -235,16 +235,18 @@ __global__ void k_mode_pair(const cpx_t<R>* __restrict__ in, View vin, cpx_t<R>*
     t /= eb;
     const int ia = (int)(t % ea);
     const int64_t g = t / ea;
+    // g0 < 0: an output without inputs (a leaf on the parent level of a
+    // nonuniform tree), written as zeros
     const int64_t g0 = src0[g], g1 = src1[g];
-    const T* ip0 = in + g0 * vin.sb + ia * sa_in + ib * sb_in + c;
-    const T* ip1 = in + (g1 >= 0 ? g1 : g0) * vin.sb + ia * sa_in + ib * sb_in + c;
+    const T* ip0 = in + (g0 >= 0 ? g0 : 0) * vin.sb + ia * sa_in + ib * sb_in + c;
+    const T* ip1 = in + (g1 >= 0 ? g1 : (g0 >= 0 ? g0 : 0)) * vin.sb + ia * sa_in + ib * sb_in + c;
     T v0[NMAX][LPT], v1[NMAX][LPT];
 #pragma unroll
     for (int i = 0; i < NMAX; ++i)
       if (i < nin)
 #pragma unroll
         for (int l = 0; l < LPT; ++l) {
-          v0[i][l] = ip0[i * step_in + l];
+          v0[i][l] = g0 >= 0 ? ip0[i * step_in + l] : mk<R>(0, 0);
           v1[i][l] = g1 >= 0 ? ip1[i * step_in + l] : mk<R>(0, 0);
         }
     const R* Ma = Ms + (bit0[g] ? msz : 0);
@@ -896,6 +898,7 @@ __global__ void __launch_bounds__(256) k_anterp(const R* __restrict__ gr, const 
                                                 const int64_t* __restrict__ mt_off,
                                                 const int64_t* __restrict__ box_rwg_ptr,
                                                 const int64_t* __restrict__ box_tri_ptr,
+                                                const int32_t* __restrict__ out_box,
                                                 const cpx_t<R>* __restrict__ xs, int64_t ldx,
                                                 const cpx_t<R>* __restrict__ rho, int64_t ldr, int nr,
                                                 cpx_t<R>* __restrict__ q, int sp) {
@@ -1006,7 +1009,7 @@ __global__ void __launch_bounds__(256) k_anterp(const R* __restrict__ gr, const 
       }
     }
     if (okp && r < nr) {
-      T* qp = q + ((int64_t)b * npts + p) * C + r;
+      T* qp = q + ((int64_t)(out_box ? out_box[b] : b) * npts + p) * C + r;
       qp[0] = a0;
       qp[nr] = a1;
       qp[2 * nr] = a2;
@@ -1030,11 +1033,11 @@ void launch_gather_build(const R* mr, const int32_t* mr_base, const int32_t* mr_
 template <typename R>
 void launch_anterp(const R* gr, const R* gt, const int32_t* gptr_r, const int32_t* gptr_t, const int64_t* mr_off,
                    const int64_t* mt_off, const int64_t* box_rwg_ptr, const int64_t* box_tri_ptr, int64_t B,
-                   const cpx_t<R>* xs, int64_t ldx, const cpx_t<R>* rho, int64_t ldr, int nr, cpx_t<R>* q,
-                   int sp, cudaStream_t s) {
+                   const int32_t* out_box, const cpx_t<R>* xs, int64_t ldx, const cpx_t<R>* rho, int64_t ldr, int nr,
+                   cpx_t<R>* q, int sp, cudaStream_t s) {
   if (B <= 0 || nr <= 0) return;
-  k_anterp<R><<<(unsigned)B, 256, 0, s>>>(gr, gt, gptr_r, gptr_t, mr_off, mt_off, box_rwg_ptr, box_tri_ptr, xs,
-                                          ldx, rho, ldr, nr, q, sp);
+  k_anterp<R><<<(unsigned)B, 256, 0, s>>>(gr, gt, gptr_r, gptr_t, mr_off, mt_off, box_rwg_ptr, box_tri_ptr, out_box,
+                                          xs, ldx, rho, ldr, nr, q, sp);
 }
 
 // ---------------------------------------------------------------- interpolation
@@ -1963,11 +1966,12 @@ template void launch_gather_build<double>(const double*, const int32_t*, const i
                                           const int64_t*, const int64_t*, int64_t, int, int32_t*, int32_t*,
                                           double*, double*, cudaStream_t);
 template void launch_anterp<float>(const float*, const float*, const int32_t*, const int32_t*, const int64_t*,
-                                   const int64_t*, const int64_t*, const int64_t*, int64_t, const float2*, int64_t,
-                                   const float2*, int64_t, int, float2*, int, cudaStream_t);
+                                   const int64_t*, const int64_t*, const int64_t*, int64_t, const int32_t*,
+                                   const float2*, int64_t, const float2*, int64_t, int, float2*, int, cudaStream_t);
 template void launch_anterp<double>(const double*, const double*, const int32_t*, const int32_t*, const int64_t*,
-                                    const int64_t*, const int64_t*, const int64_t*, int64_t, const double2*,
-                                    int64_t, const double2*, int64_t, int, double2*, int, cudaStream_t);
+                                    const int64_t*, const int64_t*, const int64_t*, int64_t, const int32_t*,
+                                    const double2*, int64_t, const double2*, int64_t, int, double2*, int,
+                                    cudaStream_t);
 template void launch_interp<float>(const float*, const int32_t*, const int32_t*, const int64_t*, const int32_t*,
                                    int64_t, const float*, const int32_t*, const int32_t*, const int64_t*,
                                    const int32_t*, int64_t, const float2*, int, int, double2*, int64_t,

@@ -679,6 +679,307 @@ void leaf_moments(const Geometry& g, int p, const std::vector<LeafKnots>& kcache
 }
 }  // namespace
 
+// Interaction lists and translation tiles of every grid level (Sec. III-C):
+// pairs of non-adjacent boxes whose parents are adjacent, every non-adjacent
+// pair on the top grid level.  Needs the boxes, parents and children.
+static void build_translation_lists(Plan& P) {
+  const int D = P.D;
+  // interaction lists per grid level
+  for (int ell = D; ell >= P.top; --ell) {
+    Level& L = P.L(ell);
+    size_t B = L.code.size();
+    std::unordered_map<int64_t, int32_t> off_id;
+    std::vector<std::vector<std::pair<int32_t, int64_t>>> lists(B);
+    auto key_of = [](int64_t dx, int64_t dy, int64_t dz) {
+      return ((dx + (1LL << 20)) << 42) | ((dy + (1LL << 20)) << 21) | (dz + (1LL << 20));
+    };
+    for (size_t x = 0; x < B; ++x) {
+      const int64_t* xi = &L.ijk[3 * x];
+      auto consider = [&](int64_t y) {
+        const int64_t* yi = &L.ijk[3 * y];
+        int64_t dx = xi[0] - yi[0], dy = xi[1] - yi[1], dz = xi[2] - yi[2];
+        if (std::max(std::llabs(dx), std::max(std::llabs(dy), std::llabs(dz))) < 2) return;
+        lists[x].push_back({(int32_t)y, key_of(dx, dy, dz)});
+      };
+      if (ell == P.top) {
+        for (size_t y = 0; y < B; ++y) consider((int64_t)y);
+      } else {
+        const Level& U = P.L(ell - 1);
+        int64_t pb = L.parent[x];
+        const int64_t* pi = &U.ijk[3 * pb];
+        int64_t nb = 1LL << (ell - 1);
+        for (int a = -1; a <= 1; ++a)
+          for (int b = -1; b <= 1; ++b)
+            for (int c = -1; c <= 1; ++c) {
+              int64_t q[3] = {pi[0] + a, pi[1] + b, pi[2] + c};
+              if (q[0] < 0 || q[1] < 0 || q[2] < 0 || q[0] >= nb || q[1] >= nb || q[2] >= nb) continue;
+              int64_t qb = find_code(U.code, morton(q[0], q[1], q[2]));
+              if (qb < 0) continue;
+              for (int64_t y = U.child_ptr[qb]; y < U.child_ptr[qb + 1]; ++y) consider(y);
+            }
+      }
+      std::sort(lists[x].begin(), lists[x].end());
+    }
+    std::vector<int64_t> keys;
+    for (auto& l : lists)
+      for (auto& e : l) keys.push_back(e.second);
+    std::sort(keys.begin(), keys.end());
+    keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
+    L.offsets.resize(3 * keys.size());
+    for (size_t i = 0; i < keys.size(); ++i) {
+      off_id[keys[i]] = (int32_t)i;
+      L.offsets[3 * i] = (int32_t)((keys[i] >> 42) - (1LL << 20));
+      L.offsets[3 * i + 1] = (int32_t)(((keys[i] >> 21) & ((1LL << 21) - 1)) - (1LL << 20));
+      L.offsets[3 * i + 2] = (int32_t)((keys[i] & ((1LL << 21) - 1)) - (1LL << 20));
+    }
+    L.il_ptr.assign(B + 1, 0);
+    for (size_t x = 0; x < B; ++x) {
+      L.il_ptr[x + 1] = L.il_ptr[x] + (int64_t)lists[x].size();
+      for (auto& e : lists[x]) {
+        L.il_src.push_back(e.first);
+        L.il_off.push_back(off_id[e.second]);
+      }
+    }
+  }
+  // translation tiles.  Top grid level: chunks of TILE_TOP consecutive boxes,
+  // every box a source.  Lower levels: the children of one parent, whose
+  // interaction lists all lie in the children of the parent's neighbours.
+  for (int ell = D; ell >= P.top; --ell) {
+    Level& L = P.L(ell);
+    const int64_t B = (int64_t)L.code.size();
+    std::unordered_map<int64_t, int32_t> off_id;
+    for (size_t i = 0; i < L.offsets.size() / 3; ++i) {
+      int64_t key = (((int64_t)L.offsets[3 * i] + (1LL << 20)) << 42) |
+                    (((int64_t)L.offsets[3 * i + 1] + (1LL << 20)) << 21) | ((int64_t)L.offsets[3 * i + 2] + (1LL << 20));
+      off_id[key] = (int32_t)i;
+    }
+    auto add_tile = [&](const std::vector<int32_t>& tg, const std::vector<int32_t>& sr, int tpad) {
+      L.tile_tgt_ptr.push_back((int64_t)L.tile_tgt.size());
+      L.tile_src_ptr.push_back((int64_t)L.tile_src.size());
+      L.tile_kidx_off.push_back((int64_t)L.tile_kidx.size());
+      for (int32_t x : tg) L.tile_tgt.push_back(x);
+      for (int32_t y : sr) L.tile_src.push_back(y);
+      for (int32_t y : sr)
+        for (int a = 0; a < tpad; ++a) {
+          int32_t id = -1;
+          if (a < (int)tg.size()) {
+            const int64_t* xi = &L.ijk[3 * tg[a]];
+            const int64_t* yi = &L.ijk[3 * y];
+            int64_t dx = xi[0] - yi[0], dy = xi[1] - yi[1], dz = xi[2] - yi[2];
+            if (std::max(std::llabs(dx), std::max(std::llabs(dy), std::llabs(dz))) >= 2) {
+              int64_t key = ((dx + (1LL << 20)) << 42) | ((dy + (1LL << 20)) << 21) | (dz + (1LL << 20));
+              auto it = off_id.find(key);
+              if (it == off_id.end()) fail(-1, "internal: offset missing from the translation table");
+              id = it->second;
+            }
+          }
+          L.tile_kidx.push_back(id);
+        }
+    };
+    if (L.il_src.empty()) {
+      // no far pairs on this level
+    } else if (ell == P.top) {
+      std::vector<int32_t> all(B);
+      std::iota(all.begin(), all.end(), 0);
+      for (int64_t x0 = 0; x0 < B; x0 += TILE_TOP) {
+        std::vector<int32_t> tg;
+        for (int64_t x = x0; x < std::min<int64_t>(B, x0 + TILE_TOP); ++x) tg.push_back((int32_t)x);
+        int tpad = (int)((tg.size() + TILE_X - 1) / TILE_X) * TILE_X;
+        add_tile(tg, all, tpad);
+      }
+    } else {
+      const Level& U = P.L(ell - 1);
+      const int64_t nbp = 1LL << (ell - 1);
+      for (size_t pb = 0; pb < U.code.size(); ++pb) {
+        std::vector<int32_t> tg, sr;
+        for (int64_t c = U.child_ptr[pb]; c < U.child_ptr[pb + 1]; ++c) tg.push_back((int32_t)c);
+        if (tg.empty()) continue;  // a leaf of a nonuniform tree
+        const int64_t* pi = &U.ijk[3 * pb];
+        for (int a = -1; a <= 1; ++a)
+          for (int b = -1; b <= 1; ++b)
+            for (int c = -1; c <= 1; ++c) {
+              int64_t q[3] = {pi[0] + a, pi[1] + b, pi[2] + c};
+              if (q[0] < 0 || q[1] < 0 || q[2] < 0 || q[0] >= nbp || q[1] >= nbp || q[2] >= nbp) continue;
+              int64_t qb = find_code(U.code, morton(q[0], q[1], q[2]));
+              if (qb < 0) continue;
+              for (int64_t y = U.child_ptr[qb]; y < U.child_ptr[qb + 1]; ++y) sr.push_back((int32_t)y);
+            }
+        std::sort(sr.begin(), sr.end());
+        add_tile(tg, sr, TILE_X);
+      }
+    }
+    L.tile_tgt_ptr.push_back((int64_t)L.tile_tgt.size());
+    L.tile_src_ptr.push_back((int64_t)L.tile_src.size());
+    L.tile_kidx_off.push_back((int64_t)L.tile_kidx.size());
+    // tensor-core tiles below the top grid level (built from the interaction
+    // lists; the top level's own tiles already take every box)
+    if (ell != P.top && !L.il_src.empty()) {
+      std::vector<int32_t> pos(B, -1);
+      for (int64_t x0 = 0; x0 < B; x0 += TILE_TOP) {
+        const int64_t x1 = std::min<int64_t>(B, x0 + TILE_TOP);
+        std::vector<int32_t> sr;
+        for (int64_t x = x0; x < x1; ++x)
+          for (int64_t e = L.il_ptr[x]; e < L.il_ptr[x + 1]; ++e) sr.push_back(L.il_src[e]);
+        std::sort(sr.begin(), sr.end());
+        sr.erase(std::unique(sr.begin(), sr.end()), sr.end());
+        const int tpad = (int)(((x1 - x0) + TILE_X - 1) / TILE_X) * TILE_X;
+        L.tct_tgt_ptr.push_back((int64_t)L.tct_tgt.size());
+        L.tct_src_ptr.push_back((int64_t)L.tct_src.size());
+        L.tct_kidx_off.push_back((int64_t)L.tct_kidx.size());
+        for (int64_t x = x0; x < x1; ++x) L.tct_tgt.push_back((int32_t)x);
+        for (size_t j = 0; j < sr.size(); ++j) {
+          L.tct_src.push_back(sr[j]);
+          pos[sr[j]] = (int32_t)j;
+        }
+        const size_t k0 = L.tct_kidx.size();
+        L.tct_kidx.resize(k0 + sr.size() * (size_t)tpad, -1);
+        for (int64_t x = x0; x < x1; ++x)
+          for (int64_t e = L.il_ptr[x]; e < L.il_ptr[x + 1]; ++e)
+            L.tct_kidx[k0 + (size_t)pos[L.il_src[e]] * tpad + (size_t)(x - x0)] = L.il_off[e];
+        for (int32_t y : sr) pos[y] = -1;
+      }
+      L.tct_tgt_ptr.push_back((int64_t)L.tct_tgt.size());
+      L.tct_src_ptr.push_back((int64_t)L.tct_src.size());
+      L.tct_kidx_off.push_back((int64_t)L.tct_kidx.size());
+    }
+  }
+}
+
+// Transfer matrices (Sec. IV-B) and DFT-fused projectors of every level.
+static void build_level_matrices(Plan& P) {
+  const int D = P.D, p = P.p;
+  // transfer matrices C^L, C^R (child level ell -> ell-1), lattice units of
+  // the child knot spacing (Sec. IV-B)
+  for (int ell = D; ell > P.top; --ell) {
+    Level& c = P.L(ell);
+    const Level& pa = P.L(ell - 1);
+    int r = (int)std::lround(pa.delta / c.delta);
+    std::vector<double> Up = open_knots(-pa.sb * r, (pa.s - p + pa.sb) * r, pa.sp, p);
+    std::vector<double> UcL = open_knots(-c.sb, (c.s - p) + c.sb, c.sp, p);
+    std::vector<double> UcR = open_knots((c.s - p) - c.sb, 2 * (c.s - p) + c.sb, c.sp, p);
+    int rr, cc;
+    c.CL = restriction_matrix(Up, UcL, p, &rr, &cc);
+    c.CR = restriction_matrix(Up, UcR, p, &rr, &cc);
+  }
+  // DFT-fused projector matrices (n = 2 s_hat - 1)
+  const double twopi = 2.0 * 3.14159265358979323846;
+  for (int ell = D; ell >= P.top; --ell) {
+    Level& L = P.L(ell);
+    int n = L.nfft, ns = L.shat, sp = L.sp;
+    L.Fn.resize((size_t)n * n);
+    for (int f = 0; f < n; ++f)
+      for (int t = 0; t < n; ++t) {
+        long ft = ((long)f * t) % n;
+        double ang = -twopi * (double)ft / n;
+        L.Fn[(size_t)f * n + t] = cplx(std::cos(ang), std::sin(ang));
+      }
+    L.Mf.assign((size_t)n * sp, cplx(0, 0));
+    for (int f = 0; f < n; ++f)
+      for (int i = 0; i < sp; ++i) {
+        cplx acc(0, 0);
+        for (int t = 0; t < ns; ++t) acc += L.Fn[(size_t)f * n + t] * L.P[(size_t)t * sp + i];
+        L.Mf[(size_t)f * sp + i] = acc;
+      }
+    L.Mb.assign((size_t)sp * n, cplx(0, 0));
+    for (int i = 0; i < sp; ++i)
+      for (int f = 0; f < n; ++f) {
+        cplx acc(0, 0);
+        for (int t = 0; t < ns; ++t) acc += L.P[(size_t)t * sp + i] * std::conj(L.Fn[(size_t)f * n + t]);
+        L.Mb[(size_t)i * n + f] = acc / (double)n;
+      }
+  }
+}
+
+// Block offsets of the near field over the near lists of the leaves, and the
+// triangle sets, local indices and coefficients of the A assembly.
+static void build_near_blocks(Plan& P) {
+  const int64_t BD = P.n_leaves, N = P.g.N;
+  const Geometry& g = P.g;
+  const size_t nblk = P.near_src.size();
+  P.blkA_off.assign(nblk + 1, 0);
+  P.blkV_off.assign(nblk + 1, 0);
+  for (int64_t x = 0; x < BD; ++x)
+    for (int64_t j = P.near_ptr[x]; j < P.near_ptr[x + 1]; ++j) {
+      int32_t y = P.near_src[j];
+      int64_t na = (P.box_rwg_ptr[x + 1] - P.box_rwg_ptr[x]) * (P.box_rwg_ptr[y + 1] - P.box_rwg_ptr[y]);
+      int64_t nvv = (P.box_tri_ptr[x + 1] - P.box_tri_ptr[x]) * (P.box_tri_ptr[y + 1] - P.box_tri_ptr[y]);
+      P.blkA_off[j + 1] = P.blkA_off[j] + na;
+      P.blkV_off[j + 1] = P.blkV_off[j] + nvv;
+    }
+  P.nnzA = P.blkA_off[nblk];
+  P.nnzV = P.blkV_off[nblk];
+  // triangle sets of RWGs per box, local indices, coefficients sigma/(2a)
+  P.tset_ptr.assign(BD + 1, 0);
+  P.tset.clear();
+  P.rwg_tl.assign(2 * N, 0);
+  P.rwg_loc.assign(2 * N, 0);
+  P.rwg_coef.assign(2 * N, 0.0);
+  for (int64_t b = 0; b < BD; ++b) {
+    std::vector<int32_t> ts;
+    for (int64_t i = P.box_rwg_ptr[b]; i < P.box_rwg_ptr[b + 1]; ++i)
+      for (int s = 0; s < 2; ++s) ts.push_back(g.tri_pm[2 * P.rwg_perm[i] + s]);
+    std::sort(ts.begin(), ts.end());
+    ts.erase(std::unique(ts.begin(), ts.end()), ts.end());
+    for (int64_t i = P.box_rwg_ptr[b]; i < P.box_rwg_ptr[b + 1]; ++i) {
+      int32_t m = P.rwg_perm[i];
+      for (int s = 0; s < 2; ++s) {
+        int32_t t = g.tri_pm[2 * m + s];
+        P.rwg_tl[2 * i + s] = (int32_t)(std::lower_bound(ts.begin(), ts.end(), t) - ts.begin());
+        int32_t fv = g.free_pm[2 * m + s];
+        int loc = 0;
+        for (int a = 0; a < 3; ++a)
+          if (g.T[3 * t + a] == fv) loc = a;
+        P.rwg_loc[2 * i + s] = loc;
+        P.rwg_coef[2 * i + s] = (s == 0 ? 1.0 : -1.0) / (2.0 * g.area[t]);
+      }
+    }
+    for (int32_t t : ts) P.tset.push_back(t);
+    P.tset_ptr[b + 1] = (int64_t)P.tset.size();
+  }
+}
+
+// Exact moments of every function in its own leaf, with the splines of the
+// leaf's level.
+static void build_moments(Plan& P, bool with_div) {
+  const int p = P.p;
+  const int64_t BD = P.n_leaves;
+  // exact moments: collapsed Gauss rule of degree >= 3p+1 per piece
+  std::vector<LeafKnots> kcache(BD);
+  for (int64_t b = 0; b < BD; ++b) {
+    const Level& L = P.L(P.leaf_level[b]);
+    const int64_t box = P.leaf_box[b];
+    LeafKnots& K = kcache[b];
+    K.p = p;
+    K.sp = L.sp;
+    K.delta = L.delta;
+    for (int d = 0; d < 3; ++d) {
+      K.lo[d] = P.root_lo[d] + L.ijk[3 * box + d] * L.h - L.sb * L.delta;
+      K.U[d] = open_knots(K.lo[d], K.lo[d] + (L.sp - p) * L.delta, L.sp, p);
+    }
+  }
+  LeafOrder ord{P.rwg_perm.data(), P.rwg_box.data(), P.box_rwg_ptr.data(), P.tri_perm.data(), P.tri_box.data(),
+                P.box_tri_ptr.data(), P.tri_rank.data()};
+  leaf_moments(P.g, p, kcache, ord, with_div, P.mom_rwg, P.mom_tri, P.mom_div);
+}
+
+// Leaves of a uniform tree: the boxes of the deepest level, in order.
+static void set_uniform_leaves(Plan& P) {
+  const int D = P.D;
+  Level& LD = P.L(D);
+  const int64_t BD = (int64_t)LD.code.size();
+  P.adaptive = false;
+  P.n_leaves = BD;
+  P.leaf_level.assign(BD, D);
+  P.leaf_box.resize(BD);
+  std::iota(P.leaf_box.begin(), P.leaf_box.end(), (int64_t)0);
+  P.level_leaf_ptr.assign(P.lv.size() + 1, 0);
+  P.level_leaf_ptr[P.lv.size()] = BD;
+  for (auto& L : P.lv) L.leaf.assign(L.code.size(), 0);
+  LD.leaf.assign(BD, 1);
+  P.rwg_lbox = P.rwg_box;
+  P.tri_lbox = P.tri_box;
+}
+
 // ------------------------------------------------------------------ build
 void build_plan(Plan& P, const double* xyz, int64_t nv, const int32_t* tri, int64_t nt,
                 double k, int p, double grid_spacing, int levels, int n_splines,
@@ -816,204 +1117,8 @@ void build_plan(Plan& P, const double* xyz, int64_t nv, const int32_t* tri, int6
       }
     }
   }
-  // interaction lists per grid level
-  for (int ell = D; ell >= P.top; --ell) {
-    Level& L = P.L(ell);
-    size_t B = L.code.size();
-    std::unordered_map<int64_t, int32_t> off_id;
-    std::vector<std::vector<std::pair<int32_t, int64_t>>> lists(B);
-    auto key_of = [](int64_t dx, int64_t dy, int64_t dz) {
-      return ((dx + (1LL << 20)) << 42) | ((dy + (1LL << 20)) << 21) | (dz + (1LL << 20));
-    };
-    for (size_t x = 0; x < B; ++x) {
-      const int64_t* xi = &L.ijk[3 * x];
-      auto consider = [&](int64_t y) {
-        const int64_t* yi = &L.ijk[3 * y];
-        int64_t dx = xi[0] - yi[0], dy = xi[1] - yi[1], dz = xi[2] - yi[2];
-        if (std::max(std::llabs(dx), std::max(std::llabs(dy), std::llabs(dz))) < 2) return;
-        lists[x].push_back({(int32_t)y, key_of(dx, dy, dz)});
-      };
-      if (ell == P.top) {
-        for (size_t y = 0; y < B; ++y) consider((int64_t)y);
-      } else {
-        const Level& U = P.L(ell - 1);
-        int64_t pb = L.parent[x];
-        const int64_t* pi = &U.ijk[3 * pb];
-        int64_t nb = 1LL << (ell - 1);
-        for (int a = -1; a <= 1; ++a)
-          for (int b = -1; b <= 1; ++b)
-            for (int c = -1; c <= 1; ++c) {
-              int64_t q[3] = {pi[0] + a, pi[1] + b, pi[2] + c};
-              if (q[0] < 0 || q[1] < 0 || q[2] < 0 || q[0] >= nb || q[1] >= nb || q[2] >= nb) continue;
-              int64_t qb = find_code(U.code, morton(q[0], q[1], q[2]));
-              if (qb < 0) continue;
-              for (int64_t y = U.child_ptr[qb]; y < U.child_ptr[qb + 1]; ++y) consider(y);
-            }
-      }
-      std::sort(lists[x].begin(), lists[x].end());
-    }
-    std::vector<int64_t> keys;
-    for (auto& l : lists)
-      for (auto& e : l) keys.push_back(e.second);
-    std::sort(keys.begin(), keys.end());
-    keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
-    L.offsets.resize(3 * keys.size());
-    for (size_t i = 0; i < keys.size(); ++i) {
-      off_id[keys[i]] = (int32_t)i;
-      L.offsets[3 * i] = (int32_t)((keys[i] >> 42) - (1LL << 20));
-      L.offsets[3 * i + 1] = (int32_t)(((keys[i] >> 21) & ((1LL << 21) - 1)) - (1LL << 20));
-      L.offsets[3 * i + 2] = (int32_t)((keys[i] & ((1LL << 21) - 1)) - (1LL << 20));
-    }
-    L.il_ptr.assign(B + 1, 0);
-    for (size_t x = 0; x < B; ++x) {
-      L.il_ptr[x + 1] = L.il_ptr[x] + (int64_t)lists[x].size();
-      for (auto& e : lists[x]) {
-        L.il_src.push_back(e.first);
-        L.il_off.push_back(off_id[e.second]);
-      }
-    }
-  }
-  // translation tiles.  Top grid level: chunks of TILE_TOP consecutive boxes,
-  // every box a source.  Lower levels: the children of one parent, whose
-  // interaction lists all lie in the children of the parent's neighbours.
-  for (int ell = D; ell >= P.top; --ell) {
-    Level& L = P.L(ell);
-    const int64_t B = (int64_t)L.code.size();
-    std::unordered_map<int64_t, int32_t> off_id;
-    for (size_t i = 0; i < L.offsets.size() / 3; ++i) {
-      int64_t key = (((int64_t)L.offsets[3 * i] + (1LL << 20)) << 42) |
-                    (((int64_t)L.offsets[3 * i + 1] + (1LL << 20)) << 21) | ((int64_t)L.offsets[3 * i + 2] + (1LL << 20));
-      off_id[key] = (int32_t)i;
-    }
-    auto add_tile = [&](const std::vector<int32_t>& tg, const std::vector<int32_t>& sr, int tpad) {
-      L.tile_tgt_ptr.push_back((int64_t)L.tile_tgt.size());
-      L.tile_src_ptr.push_back((int64_t)L.tile_src.size());
-      L.tile_kidx_off.push_back((int64_t)L.tile_kidx.size());
-      for (int32_t x : tg) L.tile_tgt.push_back(x);
-      for (int32_t y : sr) L.tile_src.push_back(y);
-      for (int32_t y : sr)
-        for (int a = 0; a < tpad; ++a) {
-          int32_t id = -1;
-          if (a < (int)tg.size()) {
-            const int64_t* xi = &L.ijk[3 * tg[a]];
-            const int64_t* yi = &L.ijk[3 * y];
-            int64_t dx = xi[0] - yi[0], dy = xi[1] - yi[1], dz = xi[2] - yi[2];
-            if (std::max(std::llabs(dx), std::max(std::llabs(dy), std::llabs(dz))) >= 2) {
-              int64_t key = ((dx + (1LL << 20)) << 42) | ((dy + (1LL << 20)) << 21) | (dz + (1LL << 20));
-              auto it = off_id.find(key);
-              if (it == off_id.end()) fail(-1, "internal: offset missing from the translation table");
-              id = it->second;
-            }
-          }
-          L.tile_kidx.push_back(id);
-        }
-    };
-    if (L.il_src.empty()) {
-      // no far pairs on this level
-    } else if (ell == P.top) {
-      std::vector<int32_t> all(B);
-      std::iota(all.begin(), all.end(), 0);
-      for (int64_t x0 = 0; x0 < B; x0 += TILE_TOP) {
-        std::vector<int32_t> tg;
-        for (int64_t x = x0; x < std::min<int64_t>(B, x0 + TILE_TOP); ++x) tg.push_back((int32_t)x);
-        int tpad = (int)((tg.size() + TILE_X - 1) / TILE_X) * TILE_X;
-        add_tile(tg, all, tpad);
-      }
-    } else {
-      const Level& U = P.L(ell - 1);
-      const int64_t nbp = 1LL << (ell - 1);
-      for (size_t pb = 0; pb < U.code.size(); ++pb) {
-        std::vector<int32_t> tg, sr;
-        for (int64_t c = U.child_ptr[pb]; c < U.child_ptr[pb + 1]; ++c) tg.push_back((int32_t)c);
-        const int64_t* pi = &U.ijk[3 * pb];
-        for (int a = -1; a <= 1; ++a)
-          for (int b = -1; b <= 1; ++b)
-            for (int c = -1; c <= 1; ++c) {
-              int64_t q[3] = {pi[0] + a, pi[1] + b, pi[2] + c};
-              if (q[0] < 0 || q[1] < 0 || q[2] < 0 || q[0] >= nbp || q[1] >= nbp || q[2] >= nbp) continue;
-              int64_t qb = find_code(U.code, morton(q[0], q[1], q[2]));
-              if (qb < 0) continue;
-              for (int64_t y = U.child_ptr[qb]; y < U.child_ptr[qb + 1]; ++y) sr.push_back((int32_t)y);
-            }
-        std::sort(sr.begin(), sr.end());
-        add_tile(tg, sr, TILE_X);
-      }
-    }
-    L.tile_tgt_ptr.push_back((int64_t)L.tile_tgt.size());
-    L.tile_src_ptr.push_back((int64_t)L.tile_src.size());
-    L.tile_kidx_off.push_back((int64_t)L.tile_kidx.size());
-    // tensor-core tiles below the top grid level (built from the interaction
-    // lists; the top level's own tiles already take every box)
-    if (ell != P.top && !L.il_src.empty()) {
-      std::vector<int32_t> pos(B, -1);
-      for (int64_t x0 = 0; x0 < B; x0 += TILE_TOP) {
-        const int64_t x1 = std::min<int64_t>(B, x0 + TILE_TOP);
-        std::vector<int32_t> sr;
-        for (int64_t x = x0; x < x1; ++x)
-          for (int64_t e = L.il_ptr[x]; e < L.il_ptr[x + 1]; ++e) sr.push_back(L.il_src[e]);
-        std::sort(sr.begin(), sr.end());
-        sr.erase(std::unique(sr.begin(), sr.end()), sr.end());
-        const int tpad = (int)(((x1 - x0) + TILE_X - 1) / TILE_X) * TILE_X;
-        L.tct_tgt_ptr.push_back((int64_t)L.tct_tgt.size());
-        L.tct_src_ptr.push_back((int64_t)L.tct_src.size());
-        L.tct_kidx_off.push_back((int64_t)L.tct_kidx.size());
-        for (int64_t x = x0; x < x1; ++x) L.tct_tgt.push_back((int32_t)x);
-        for (size_t j = 0; j < sr.size(); ++j) {
-          L.tct_src.push_back(sr[j]);
-          pos[sr[j]] = (int32_t)j;
-        }
-        const size_t k0 = L.tct_kidx.size();
-        L.tct_kidx.resize(k0 + sr.size() * (size_t)tpad, -1);
-        for (int64_t x = x0; x < x1; ++x)
-          for (int64_t e = L.il_ptr[x]; e < L.il_ptr[x + 1]; ++e)
-            L.tct_kidx[k0 + (size_t)pos[L.il_src[e]] * tpad + (size_t)(x - x0)] = L.il_off[e];
-        for (int32_t y : sr) pos[y] = -1;
-      }
-      L.tct_tgt_ptr.push_back((int64_t)L.tct_tgt.size());
-      L.tct_src_ptr.push_back((int64_t)L.tct_src.size());
-      L.tct_kidx_off.push_back((int64_t)L.tct_kidx.size());
-    }
-  }
-  // transfer matrices C^L, C^R (child level ell -> ell-1), lattice units of
-  // the child knot spacing (Sec. IV-B)
-  for (int ell = D; ell > P.top; --ell) {
-    Level& c = P.L(ell);
-    const Level& pa = P.L(ell - 1);
-    int r = (int)std::lround(pa.delta / c.delta);
-    std::vector<double> Up = open_knots(-pa.sb * r, (pa.s - p + pa.sb) * r, pa.sp, p);
-    std::vector<double> UcL = open_knots(-c.sb, (c.s - p) + c.sb, c.sp, p);
-    std::vector<double> UcR = open_knots((c.s - p) - c.sb, 2 * (c.s - p) + c.sb, c.sp, p);
-    int rr, cc;
-    c.CL = restriction_matrix(Up, UcL, p, &rr, &cc);
-    c.CR = restriction_matrix(Up, UcR, p, &rr, &cc);
-  }
-  // DFT-fused projector matrices (n = 2 s_hat - 1)
-  const double twopi = 2.0 * 3.14159265358979323846;
-  for (int ell = D; ell >= P.top; --ell) {
-    Level& L = P.L(ell);
-    int n = L.nfft, ns = L.shat, sp = L.sp;
-    L.Fn.resize((size_t)n * n);
-    for (int f = 0; f < n; ++f)
-      for (int t = 0; t < n; ++t) {
-        long ft = ((long)f * t) % n;
-        double ang = -twopi * (double)ft / n;
-        L.Fn[(size_t)f * n + t] = cplx(std::cos(ang), std::sin(ang));
-      }
-    L.Mf.assign((size_t)n * sp, cplx(0, 0));
-    for (int f = 0; f < n; ++f)
-      for (int i = 0; i < sp; ++i) {
-        cplx acc(0, 0);
-        for (int t = 0; t < ns; ++t) acc += L.Fn[(size_t)f * n + t] * L.P[(size_t)t * sp + i];
-        L.Mf[(size_t)f * sp + i] = acc;
-      }
-    L.Mb.assign((size_t)sp * n, cplx(0, 0));
-    for (int i = 0; i < sp; ++i)
-      for (int f = 0; f < n; ++f) {
-        cplx acc(0, 0);
-        for (int t = 0; t < ns; ++t) acc += L.P[(size_t)t * sp + i] * std::conj(L.Fn[(size_t)f * n + t]);
-        L.Mb[(size_t)i * n + f] = acc / (double)n;
-      }
-  }
+  build_translation_lists(P);
+  build_level_matrices(P);
 
   // sorted basis-function order (by leaf box)
   const Level& LD = P.L(D);
@@ -1071,65 +1176,11 @@ void build_plan(Plan& P, const double* xyz, int64_t nv, const int32_t* tri, int6
       for (int32_t y : l) P.near_src.push_back(y);
       P.near_ptr[x + 1] = (int64_t)P.near_src.size();
     }
-    size_t nblk = P.near_src.size();
-    P.blkA_off.assign(nblk + 1, 0);
-    P.blkV_off.assign(nblk + 1, 0);
-    for (size_t x = 0; x < BD; ++x)
-      for (int64_t j = P.near_ptr[x]; j < P.near_ptr[x + 1]; ++j) {
-        int32_t y = P.near_src[j];
-        int64_t na = (P.box_rwg_ptr[x + 1] - P.box_rwg_ptr[x]) * (P.box_rwg_ptr[y + 1] - P.box_rwg_ptr[y]);
-        int64_t nvv = (P.box_tri_ptr[x + 1] - P.box_tri_ptr[x]) * (P.box_tri_ptr[y + 1] - P.box_tri_ptr[y]);
-        P.blkA_off[j + 1] = P.blkA_off[j] + na;
-        P.blkV_off[j + 1] = P.blkV_off[j] + nvv;
-      }
-    P.nnzA = P.blkA_off[nblk];
-    P.nnzV = P.blkV_off[nblk];
-    // triangle sets of RWGs per box, local indices, coefficients sigma/(2a)
-    P.tset_ptr.assign(BD + 1, 0);
-    P.tset.clear();
-    P.rwg_tl.assign(2 * N, 0);
-    P.rwg_loc.assign(2 * N, 0);
-    P.rwg_coef.assign(2 * N, 0.0);
-    for (size_t b = 0; b < BD; ++b) {
-      std::vector<int32_t> ts;
-      for (int64_t i = P.box_rwg_ptr[b]; i < P.box_rwg_ptr[b + 1]; ++i)
-        for (int s = 0; s < 2; ++s) ts.push_back(g.tri_pm[2 * P.rwg_perm[i] + s]);
-      std::sort(ts.begin(), ts.end());
-      ts.erase(std::unique(ts.begin(), ts.end()), ts.end());
-      for (int64_t i = P.box_rwg_ptr[b]; i < P.box_rwg_ptr[b + 1]; ++i) {
-        int32_t m = P.rwg_perm[i];
-        for (int s = 0; s < 2; ++s) {
-          int32_t t = g.tri_pm[2 * m + s];
-          P.rwg_tl[2 * i + s] = (int32_t)(std::lower_bound(ts.begin(), ts.end(), t) - ts.begin());
-          int32_t fv = g.free_pm[2 * m + s];
-          int loc = 0;
-          for (int a = 0; a < 3; ++a)
-            if (g.T[3 * t + a] == fv) loc = a;
-          P.rwg_loc[2 * i + s] = loc;
-          P.rwg_coef[2 * i + s] = (s == 0 ? 1.0 : -1.0) / (2.0 * g.area[t]);
-        }
-      }
-      for (int32_t t : ts) P.tset.push_back(t);
-      P.tset_ptr[b + 1] = (int64_t)P.tset.size();
-    }
   }
+  set_uniform_leaves(P);
+  build_near_blocks(P);
   if (!with_moments) return;
-
-  // exact moments: collapsed Gauss rule of degree >= 3p+1 per piece
-  std::vector<LeafKnots> kcache(BD);
-  for (size_t b = 0; b < BD; ++b) {
-    LeafKnots& K = kcache[b];
-    K.p = p;
-    K.sp = LD.sp;
-    K.delta = LD.delta;
-    for (int d = 0; d < 3; ++d) {
-      K.lo[d] = P.root_lo[d] + LD.ijk[3 * b + d] * LD.h - LD.sb * LD.delta;
-      K.U[d] = open_knots(K.lo[d], K.lo[d] + (LD.sp - p) * LD.delta, LD.sp, p);
-    }
-  }
-  LeafOrder ord{P.rwg_perm.data(), P.rwg_box.data(), P.box_rwg_ptr.data(), P.tri_perm.data(), P.tri_box.data(),
-                P.box_tri_ptr.data(), P.tri_rank.data()};
-  leaf_moments(g, p, kcache, ord, with_div, P.mom_rwg, P.mom_tri, P.mom_div);
+  build_moments(P, with_div);
 }
 
 // ------------------------------------------------------------ nonuniform tree
@@ -1472,5 +1523,147 @@ void build_adaptive_plan(AdaptivePlan& A, const double* xyz, int64_t nv, const i
                 A.tri_leaf.data(), A.leaf_tri_ptr.data(), A.tri_rank.data()};
   MomentBlocks unused;
   leaf_moments(g, p, kcache, ord, false, A.mom_rwg, A.mom_tri, unused);
+}
+
+// The nonuniform tree (Sec. VII) as a plan of the device pipeline: the
+// adaptive tree's boxes on every level in Morton order, its per-level spline
+// parameters, the translation lists, tiles and matrices of the uniform
+// builder, the leaves of all levels as the near field's boxes, and every
+// function's moments in its own leaf with that level's splines.
+void build_plan_adaptive(Plan& P, const double* xyz, int64_t nv, const int32_t* tri, int64_t nt, double k, int p,
+                         const AdaptiveOptions& o, bool with_moments, bool with_div) {
+  AdaptivePlan A;
+  build_adaptive_plan(A, xyz, nv, tri, nt, k, p, o, false);
+  P = Plan();
+  P.g = std::move(A.g);
+  P.k = k;
+  P.p = p;
+  P.D = A.D;
+  P.top = A.top;
+  P.n_levels = A.D - A.top + 1;
+  P.root_edge = A.root_edge;
+  for (int d = 0; d < 3; ++d) P.root_lo[d] = A.root_lo[d];
+  P.adaptive = true;
+  const int top = P.top, D = P.D, nlev = P.n_levels;
+  P.lv.assign(nlev, Level());
+  std::vector<std::vector<int64_t>> newidx(nlev);  // adaptive box index -> Morton position
+  for (int ell = top; ell <= D; ++ell) {
+    const AdaptiveLevel& AL = A.lv[ell - top];
+    Level& L = P.L(ell);
+    L.level = ell;
+    L.h = AL.h;
+    L.s = AL.s;
+    L.sb = AL.sb;
+    L.sp = AL.sp;
+    L.delta = AL.delta;
+    projector(L.sp, p, L.P, &L.shat);
+    if (L.shat != AL.shat) fail(-1, "internal: stabilized spline count differs from the tree's");
+    L.Delta = (L.sp - p) * L.delta / (L.shat - 1);
+    L.nfft = 2 * L.shat - 1;
+    const size_t B = AL.key.size();
+    std::vector<std::pair<uint64_t, int64_t>> cb(B);
+    for (size_t b = 0; b < B; ++b) cb[b] = {morton(AL.key[b][0], AL.key[b][1], AL.key[b][2]), (int64_t)b};
+    std::sort(cb.begin(), cb.end());
+    L.code.resize(B);
+    L.ijk.resize(3 * B);
+    L.leaf.resize(B);
+    newidx[ell - top].resize(B);
+    for (size_t b = 0; b < B; ++b) {
+      const int64_t a = cb[b].second;
+      L.code[b] = cb[b].first;
+      for (int d = 0; d < 3; ++d) L.ijk[3 * b + d] = AL.key[a][d];
+      L.leaf[b] = AL.leaf[a];
+      newidx[ell - top][a] = (int64_t)b;
+    }
+  }
+  for (int ell = D; ell >= top; --ell) {
+    Level& L = P.L(ell);
+    const size_t B = L.code.size();
+    L.parent.assign(B, -1);
+    if (ell > top) {
+      const Level& U = P.L(ell - 1);
+      for (size_t b = 0; b < B; ++b) {
+        L.parent[b] = find_code(U.code, L.code[b] >> 3);
+        if (L.parent[b] < 0 || U.leaf[L.parent[b]]) fail(-1, "internal: box without an inner parent");
+      }
+    }
+    if (ell < D) {
+      const Level& C = P.L(ell + 1);
+      L.child_ptr.assign(B + 1, 0);
+      for (size_t c = 0; c < C.code.size(); ++c) L.child_ptr[C.parent[c] + 1]++;
+      for (size_t b = 0; b < B; ++b) L.child_ptr[b + 1] += L.child_ptr[b];
+    }
+  }
+  // leaves, level by level from the top level
+  std::vector<std::vector<int64_t>> leaf_of(nlev);
+  P.level_leaf_ptr.assign(nlev + 1, 0);
+  for (int ell = top; ell <= D; ++ell) {
+    const Level& L = P.L(ell);
+    leaf_of[ell - top].assign(L.code.size(), -1);
+    for (size_t b = 0; b < L.code.size(); ++b)
+      if (L.leaf[b]) {
+        leaf_of[ell - top][b] = (int64_t)P.leaf_level.size();
+        P.leaf_level.push_back(ell);
+        P.leaf_box.push_back((int64_t)b);
+      }
+    P.level_leaf_ptr[ell - top + 1] = (int64_t)P.leaf_level.size();
+  }
+  const int64_t NL = (int64_t)P.leaf_level.size();
+  P.n_leaves = NL;
+  // functions sorted by leaf, then canonical id
+  auto sort_by_leaf = [&](const std::vector<int32_t>& lvl, const std::vector<int32_t>& box, int64_t n,
+                          std::vector<int32_t>& perm, std::vector<int32_t>& leaf, std::vector<int32_t>& lbox,
+                          std::vector<int64_t>& ptr) {
+    std::vector<std::pair<int64_t, int32_t>> kk(n);
+    for (int64_t i = 0; i < n; ++i) {
+      const int e = lvl[i] - top;
+      kk[i] = {leaf_of[e][newidx[e][box[i]]], (int32_t)i};
+      if (kk[i].first < 0) fail(-1, "internal: function outside a leaf");
+    }
+    std::sort(kk.begin(), kk.end());
+    perm.resize(n);
+    leaf.resize(n);
+    lbox.resize(n);
+    ptr.assign(NL + 1, 0);
+    for (int64_t i = 0; i < n; ++i) {
+      perm[i] = kk[i].second;
+      leaf[i] = (int32_t)kk[i].first;
+      lbox[i] = (int32_t)P.leaf_box[kk[i].first];
+      ptr[kk[i].first + 1]++;
+    }
+    for (int64_t x = 0; x < NL; ++x) ptr[x + 1] += ptr[x];
+  };
+  const int64_t N = P.g.N;
+  sort_by_leaf(A.rwg_level, A.rwg_box, N, P.rwg_perm, P.rwg_box, P.rwg_lbox, P.box_rwg_ptr);
+  sort_by_leaf(A.tri_level, A.tri_box, nt, P.tri_perm, P.tri_box, P.tri_lbox, P.box_tri_ptr);
+  P.tri_rank.assign(nt, 0);
+  for (int64_t i = 0; i < nt; ++i) P.tri_rank[P.tri_perm[i]] = (int32_t)i;
+  P.rwg_tri_sorted.resize(2 * N);
+  for (int64_t i = 0; i < N; ++i)
+    for (int s = 0; s < 2; ++s) P.rwg_tri_sorted[2 * i + s] = P.tri_rank[P.g.tri_pm[2 * P.rwg_perm[i] + s]];
+  // near leaves of the tree builder, renumbered
+  {
+    std::vector<int64_t> a2n(NL);
+    if ((int64_t)A.leaf_level.size() != NL) fail(-1, "internal: leaf count");
+    for (int64_t x = 0; x < NL; ++x) {
+      const int e = A.leaf_level[x] - top;
+      a2n[x] = leaf_of[e][newidx[e][A.leaf_box[x]]];
+    }
+    std::vector<std::vector<int32_t>> rows(NL);
+    for (int64_t x = 0; x < NL; ++x)
+      for (int64_t j = A.near_ptr[x]; j < A.near_ptr[x + 1]; ++j) rows[a2n[x]].push_back((int32_t)a2n[A.near_src[j]]);
+    P.near_ptr.assign(NL + 1, 0);
+    P.near_src.clear();
+    for (int64_t x = 0; x < NL; ++x) {
+      std::sort(rows[x].begin(), rows[x].end());
+      P.near_src.insert(P.near_src.end(), rows[x].begin(), rows[x].end());
+      P.near_ptr[x + 1] = (int64_t)P.near_src.size();
+    }
+  }
+  build_translation_lists(P);
+  build_level_matrices(P);
+  build_near_blocks(P);
+  if (!with_moments) return;
+  build_moments(P, with_div);
 }
 }  // namespace efie

@@ -44,6 +44,7 @@ struct Level {
   std::vector<int32_t> il_src;       // [nnz] source box
   std::vector<int32_t> il_off;       // [nnz] offset id
   std::vector<int32_t> offsets;      // [O][3] o = ijk_target - ijk_source
+  std::vector<uint8_t> leaf;         // [B] 1 for a leaf of the tree (its functions are anterpolated here)
   // translation tiles: groups of <= TILE_T targets sharing one source list;
   // kidx[tile] is [n_src][TILE_T] offset ids (-1: pair not translated here)
   std::vector<int64_t> tile_tgt_ptr, tile_src_ptr, tile_kidx_off;
@@ -82,24 +83,35 @@ struct Plan {
   Level& L(int ell) { return lv[ell - top]; }
   const Level& L(int ell) const { return lv[ell - top]; }
 
-  // leaf-level basis-function ordering (sorted by leaf box)
+  // leaves: the boxes of level D (uniform tree), or the leaves of every level
+  // (nonuniform tree, Sec. VII), numbered level by level from the top level,
+  // Morton order within a level.  The near field's boxes are these leaves.
+  bool adaptive = false;
+  int64_t n_leaves = 0;
+  std::vector<int32_t> leaf_level;      // [NL]
+  std::vector<int64_t> leaf_box;        // [NL] box index on its level
+  std::vector<int64_t> level_leaf_ptr;  // [n_levels+1]: leaves of level top+i are [ptr[i], ptr[i+1])
+
+  // basis-function ordering (sorted by leaf)
   std::vector<int32_t> rwg_perm;     // sorted k -> canonical m
-  std::vector<int32_t> rwg_box;      // sorted k -> leaf box
-  std::vector<int64_t> box_rwg_ptr;  // [B_D+1]
+  std::vector<int32_t> rwg_box;      // sorted k -> leaf
+  std::vector<int64_t> box_rwg_ptr;  // [NL+1]
   std::vector<int32_t> tri_perm;     // sorted t -> canonical triangle
-  std::vector<int32_t> tri_box;      // sorted t -> leaf box
-  std::vector<int64_t> box_tri_ptr;  // [B_D+1]
+  std::vector<int32_t> tri_box;      // sorted t -> leaf
+  std::vector<int64_t> box_tri_ptr;  // [NL+1]
+  std::vector<int32_t> rwg_lbox, tri_lbox;  // sorted function -> box index on its leaf's level
   std::vector<int32_t> tri_rank;     // canonical triangle -> sorted index
   std::vector<int32_t> rwg_tri_sorted;  // [N_sorted][2] sorted triangle index of c+, c-
 
-  // near field structure (leaf boxes with |d|_inf <= 1)
-  std::vector<int64_t> near_ptr;     // [B_D+1]
+  // near field structure over the leaves (uniform: leaf boxes with
+  // |d|_inf <= 1; nonuniform: ancestors on the coarser level adjacent or equal)
+  std::vector<int64_t> near_ptr;     // [NL+1]
   std::vector<int32_t> near_src;     // source box
   std::vector<int64_t> blkA_off;     // [nnz_blocks+1] offset of A block (entries)
   std::vector<int64_t> blkV_off;     // [nnz_blocks+1]
   int64_t nnzA = 0, nnzV = 0;
   // triangle set per leaf box for A assembly: triangles of RWGs in the box
-  std::vector<int64_t> tset_ptr;     // [B_D+1]
+  std::vector<int64_t> tset_ptr;     // [NL+1]
   std::vector<int32_t> tset;         // canonical triangle ids
   std::vector<int32_t> rwg_tl;       // [N_sorted][2] local index in tset of its box
   std::vector<int32_t> rwg_loc;      // [N_sorted][2] local vertex index of the free vertex
@@ -166,6 +178,12 @@ struct AdaptivePlan {
 
 void build_adaptive_plan(AdaptivePlan& A, const double* xyz, int64_t nv, const int32_t* tri, int64_t nt,
                          double k, int p, const AdaptiveOptions& o, bool with_moments = false);
+
+// The nonuniform tree as a plan of the device pipeline (boxes in Morton order,
+// leaves of every level as the near field's boxes, moments in each function's
+// own leaf); with_div as in build_plan.
+void build_plan_adaptive(Plan& P, const double* xyz, int64_t nv, const int32_t* tri, int64_t nt, double k, int p,
+                         const AdaptiveOptions& o, bool with_moments, bool with_div = false);
 
 // Spline helpers exposed for tests of the host code
 std::vector<double> open_knots(double lo, double hi, int ns, int p);

@@ -125,14 +125,19 @@ def test_plan_moments_match_oracle(lib):
 def test_plan_adaptive_matches_oracle(lib):
     """Nonuniform octree planned by the library's host code against the
     oracle's (`oracle.nonuniform`): per-level boxes, leaves, spline counts,
-    translated pairs, leaf functions, and the near RWG / triangle pairs."""
+    translated pairs, leaf functions, and the near RWG / triangle pairs.  The
+    library reports them from the plan its device pipeline runs
+    (efie_setup_adaptive): interaction lists, leaves in Morton order, and the
+    near blocks over the leaves."""
     G, _ = lib
     from oracle import nonuniform as NU
     from oracle.geometry import build_rwg
     from oracle.tree import interaction_lists
+    two = E.merge_meshes(E.icosphere(8, 0.3, center=(-1.0, 0, 0)), E.icosphere(5, 0.8, center=(1.0, 0.1, 0.05)))
     for (freq, r, k, me, top) in [(14, 0.5, 2 * np.pi, 60, 2), (14, 0.5, 2 * np.pi * 2.5, 60, 2),
-                                  (12, 0.5, 2 * np.pi, 40, 2)]:
-        V, T = E.icosphere(freq, r)
+                                  (12, 0.5, 2 * np.pi, 40, 2), (None, None, 2 * np.pi, 30, 2)]:
+        # the last case: a fine small sphere beside a coarse large one, leaves on levels 2, 3 and 4
+        V, T = E.icosphere(freq, r) if freq else two
         m = build_rwg(V, T)
         tr = NU.build_adaptive_tree(m, k, 3, max_elems=me, top=top)
         lv, nr, nt = G.plan_adaptive(V, T, k, 3, max_elems=me, top=top)
