@@ -182,7 +182,8 @@ int efie_plan_adaptive_near(const efie_mesh *mesh, double wavenumber, int spline
                             int64_t *near_ptr, int32_t *near_src, int64_t near_cap);
 
 /* Host-only: exact moments of the nonuniform tree, each function in its
- * own leaf's splines (that level's s', knots and buffers).  kind 0: RWGs
+ * own leaf's splines (that level's s', knots and buffers), as
+ * efie_setup_adaptive uploads them.  kind 0: RWGs
  * (canonical edge ids), [3][sp][sp][sp] per id; kind 1: triangles, pulse
  * 1/area, [sp][sp][sp] per id.  The blocks are packed one after the other in
  * out (out_len entries), each with its own sp; level_out and sp_out (n_ids

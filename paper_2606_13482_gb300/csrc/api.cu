@@ -2019,19 +2019,20 @@ int efie_plan_adaptive_moments(const efie_mesh* mesh, double wavenumber, int spl
     check_mesh(mesh);
     if (kind != 0 && kind != 1) throw EfieError{EFIE_EINVAL, "kind must be 0 (RWG) or 1 (triangle)"};
     if (n_ids < 0 || (n_ids > 0 && !ids)) throw EfieError{EFIE_EINVAL, "ids is NULL"};
-    AdaptivePlan A;
-    build_adaptive_plan(A, mesh->xyz, mesh->n_vertices, mesh->tri, mesh->n_triangles, wavenumber, spline_degree,
+    // the moments the device pipeline uploads (efie_setup_adaptive)
+    Plan A;
+    build_plan_adaptive(A, mesh->xyz, mesh->n_vertices, mesh->tri, mesh->n_triangles, wavenumber, spline_degree,
                         adaptive_options(topt), true);
     const int ncomp = kind == 0 ? 3 : 1;
     const std::vector<int32_t>& perm = kind == 0 ? A.rwg_perm : A.tri_perm;
-    const std::vector<int32_t>& leaf = kind == 0 ? A.rwg_leaf : A.tri_leaf;
+    const std::vector<int32_t>& leaf = kind == 0 ? A.rwg_box : A.tri_box;
     const MomentBlocks& MB = kind == 0 ? A.mom_rwg : A.mom_tri;
     std::vector<int64_t> rank(perm.size(), -1);
     for (size_t i = 0; i < perm.size(); ++i) rank[perm[i]] = (int64_t)i;
     int64_t need = 0;
     for (int64_t j = 0; j < n_ids; ++j) {
       if (ids[j] < 0 || ids[j] >= (int64_t)rank.size()) throw EfieError{EFIE_EINVAL, "index out of range"};
-      const AdaptiveLevel& L = A.lv[A.leaf_level[leaf[rank[ids[j]]]] - A.top];
+      const Level& L = A.L(A.leaf_level[leaf[rank[ids[j]]]]);
       need += (int64_t)ncomp * L.sp * L.sp * L.sp;
     }
     if (out_needed) *out_needed = need;
@@ -2040,7 +2041,7 @@ int efie_plan_adaptive_moments(const efie_mesh* mesh, double wavenumber, int spl
     for (int64_t j = 0; j < n_ids; ++j) {
       const int64_t i = rank[ids[j]];
       const int lvl = A.leaf_level[leaf[i]];
-      const int sp = A.lv[lvl - A.top].sp;
+      const int sp = A.L(lvl).sp;
       if (level_out) level_out[j] = lvl;
       if (sp_out) sp_out[j] = sp;
       if (out) {

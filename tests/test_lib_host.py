@@ -179,18 +179,26 @@ def test_plan_adaptive_near_and_moments_match_oracle(lib):
         assert np.all(np.diff(src[ptr[x]:ptr[x + 1]]) > 0)
     assert np.array_equal(nb, NU.near_leaf_pairs(tr))
     rng = np.random.default_rng(4)
-    for kind, n in ((0, m.N), (1, m.Nt)):
-        ids = rng.choice(n, 40, replace=False).astype(np.int32)
-        blocks, levels = G.plan_adaptive_moments(V, T, k, 3, kind, ids, max_elems=60, top=2)
-        flv = tr.rwg_level if kind == 0 else tr.tri_level
-        assert np.array_equal(levels, flv[ids]) and len(set(levels)) == 2
-        for ell in set(levels.tolist()):
-            sel = np.nonzero(levels == ell)[0]
-            view = NU._LevelView(tr, ell)
-            ref = (rwg_moments if kind == 0 else pulse_moments)(m, view, ids[sel])
-            got = np.stack([blocks[i] for i in sel])
-            assert got.shape == ref.shape
-            assert np.abs(got - ref).max() < 1e-13 * np.abs(ref).max()
+    # the moments efie_setup_adaptive uploads: the sphere above (leaves on two
+    # levels), and a fine small sphere beside a coarse large one (three levels)
+    two = E.merge_meshes(E.icosphere(8, 0.3, center=(-1.0, 0, 0)), E.icosphere(5, 0.8, center=(1.0, 0.1, 0.05)))
+    for (Vc, Tc, me, n_lv) in ((V, T, 60, 2), (two[0], two[1], 30, 3)):
+        mc = m if Vc is V else build_rwg(Vc, Tc)
+        trc = tr if Vc is V else NU.build_adaptive_tree(mc, k, 3, max_elems=me, top=2)
+        for kind, n in ((0, mc.N), (1, mc.Nt)):
+            flv = trc.rwg_level if kind == 0 else trc.tri_level
+            # up to 20 sampled functions from every level that holds leaves
+            ids = np.concatenate([rng.choice(np.nonzero(flv == ell)[0], min(20, int((flv == ell).sum())),
+                                             replace=False) for ell in np.unique(flv)]).astype(np.int32)
+            blocks, levels = G.plan_adaptive_moments(Vc, Tc, k, 3, kind, ids, max_elems=me, top=2)
+            assert np.array_equal(levels, flv[ids]) and len(set(levels)) == n_lv
+            for ell in set(levels.tolist()):
+                sel = np.nonzero(levels == ell)[0]
+                view = NU._LevelView(trc, ell)
+                ref = (rwg_moments if kind == 0 else pulse_moments)(mc, view, ids[sel])
+                got = np.stack([blocks[i] for i in sel])
+                assert got.shape == ref.shape
+                assert np.abs(got - ref).max() < 1e-13 * np.abs(ref).max()
 
 
 def test_invalid_inputs(lib):
