@@ -336,11 +336,13 @@ def plan_moments(V, T, k, p, grid_spacing, levels, kind, ids, options: Options |
 class EFIE:
     """Handle to a set-up problem on the current CUDA device."""
 
-    def __init__(self, V, T, k, p, grid_spacing, levels, precision=EFIE_FP64, tree=None, **opts):
+    def __init__(self, V, T, k, p, grid_spacing=None, levels=None, precision=EFIE_FP64, tree=None, **opts):
         """Uniform octree of (grid_spacing, levels) (efie_setup), or with
         `tree` = dict(max_elems, max_prot, top, n_splines, max_depth) the
         nonuniform octree of Sec. VII (efie_setup_adaptive; grid_spacing and
         levels unused)."""
+        if tree is None and (grid_spacing is None or levels is None):
+            raise ValueError("grid_spacing and levels are needed without a tree")
         import torch  # noqa: F401  (device memory and streams)
         self.lib = load_library()
         o = Options()

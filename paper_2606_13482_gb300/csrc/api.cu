@@ -1111,6 +1111,8 @@ void setup_impl(efie_handle* h, const efie_mesh* mesh, double k, int p, double g
   if (h->opt.factorization != EFIE_FACT_STAR && h->opt.factorization != EFIE_FACT_DIRECT &&
       h->opt.factorization != EFIE_FACT_DYADIC)
     throw EfieError{EFIE_EINVAL, "factorization must be EFIE_FACT_STAR, EFIE_FACT_DIRECT or EFIE_FACT_DYADIC"};
+  if (tree && h->opt.factorization != EFIE_FACT_STAR)
+    throw EfieError{EFIE_EINVAL, "the nonuniform tree takes the star factorization (EFIE_FACT_STAR)"};
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0)
     throw EfieError{EFIE_ECUDA, "no CUDA device"};
@@ -1140,8 +1142,6 @@ void setup_impl(efie_handle* h, const efie_mesh* mesh, double k, int p, double g
   };
   h->dyadic = h->opt.factorization == EFIE_FACT_DYADIC;
   h->direct = h->opt.factorization == EFIE_FACT_DIRECT || h->dyadic;
-  if (tree && h->opt.factorization != EFIE_FACT_STAR)
-    throw EfieError{EFIE_EINVAL, "the nonuniform tree takes the star factorization (EFIE_FACT_STAR)"};
   if (tree)
     build_plan_adaptive(P, mesh->xyz, mesh->n_vertices, mesh->tri, mesh->n_triangles, k, p, *tree, true,
                         h->direct);

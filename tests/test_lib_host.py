@@ -257,6 +257,18 @@ def test_factorization_option_checked_first(lib):
         G.EFIE(V, T, 2 * np.pi, 3, 0.1, 1, factorization=7)
     assert e.value.code == -1 and "factorization" in str(e.value)
     assert G.Options.factorization.offset == ctypes.sizeof(G.Options) - 8
+    # the nonuniform tree takes the star factorization only; bad tree options
+    # are rejected as well, both before any device work
+    tree = dict(max_elems=30, top=2)
+    for fact in (G.EFIE_FACT_DIRECT, G.EFIE_FACT_DYADIC):
+        with pytest.raises(G.EfieError) as e:
+            G.EFIE(V, T, 2 * np.pi, 3, tree=tree, factorization=fact)
+        assert e.value.code == -1 and "star" in str(e.value)
+    with pytest.raises(G.EfieError) as e:
+        G.EFIE(V, T, 2 * np.pi, 3, tree=dict(max_prot=-1.0))
+    assert e.value.code == -1
+    with pytest.raises(ValueError):
+        G.EFIE(V, T, 2 * np.pi, 3)
 
 
 def test_planewave_argument_checks(lib):
