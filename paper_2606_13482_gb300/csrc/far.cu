@@ -800,6 +800,11 @@ void launch_mode(const cpx_t<R>* in, View vin, cpx_t<R>* out, View vout, int64_t
 // (mr_off / 3, mt_off), since both orderings hold the same entries.  One CTA
 // per box, one thread per point; the covering test reads each basis
 // function's base and extents, so the lists are deterministic.
+// Points are taken GB_PTS at a time (the per-point counters live in shared
+// memory), so leaves of any spline count fit; thread 0 carries the running
+// list offsets from one group of points to the next.
+constexpr int GB_PTS = 8192;
+
 template <typename R>
 __global__ void k_gather_build(const R* __restrict__ mr, const int32_t* __restrict__ mr_base,
                                const int32_t* __restrict__ mr_ext, const int64_t* __restrict__ mr_off,
@@ -808,8 +813,9 @@ __global__ void k_gather_build(const R* __restrict__ mr, const int32_t* __restri
                                const int64_t* __restrict__ box_rwg_ptr, const int64_t* __restrict__ box_tri_ptr,
                                int sp, int32_t* __restrict__ gptr_r, int32_t* __restrict__ gptr_t,
                                R* __restrict__ gr, R* __restrict__ gt) {
-  extern __shared__ int32_t gcnt[];  // [2][npts]
+  extern __shared__ int32_t gcnt[];  // [2][min(npts, GB_PTS)]
   const int b = blockIdx.x, npts = sp * sp * sp;
+  const int gp = npts < GB_PTS ? npts : GB_PTS;
   const int64_t k0 = box_rwg_ptr[b], k1 = box_rwg_ptr[b + 1];
   const int64_t t0 = box_tri_ptr[b], t1 = box_tri_ptr[b + 1];
   auto covers = [&](const int32_t* base, const int32_t* ext, int64_t i, int p0, int p1, int p2, int& e) {
@@ -819,54 +825,60 @@ __global__ void k_gather_build(const R* __restrict__ mr, const int32_t* __restri
     e = (a0 * e1 + a1) * e2 + a2;
     return true;
   };
-  for (int pt = threadIdx.x; pt < npts; pt += blockDim.x) {
-    const int p0 = pt / (sp * sp), p1 = (pt / sp) % sp, p2 = pt % sp;
-    int cr = 0, ct = 0, e;
-    for (int64_t i = k0; i < k1; ++i) cr += covers(mr_base, mr_ext, i, p0, p1, p2, e);
-    for (int64_t i = t0; i < t1; ++i) ct += covers(mt_base, mt_ext, i, p0, p1, p2, e);
-    gcnt[pt] = cr;
-    gcnt[npts + pt] = ct;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int32_t* pr = gptr_r + (int64_t)b * (npts + 1);
-    int32_t* pt_ = gptr_t + (int64_t)b * (npts + 1);
-    int32_t rr = 0, rt = 0;
-    for (int pt = 0; pt < npts; ++pt) {
-      const int32_t vr = gcnt[pt], vt = gcnt[npts + pt];
-      gcnt[pt] = rr;
-      gcnt[npts + pt] = rt;
-      pr[pt] = rr;
-      pt_[pt] = rt;
-      rr += vr;
-      rt += vt;
-    }
-    pr[npts] = rr;
-    pt_[npts] = rt;
-  }
-  __syncthreads();
+  int32_t* pr = gptr_r + (int64_t)b * (npts + 1);
+  int32_t* pt_ = gptr_t + (int64_t)b * (npts + 1);
   R* outr = gr + 4 * (k0 < k1 ? mr_off[k0] / 3 : 0);
   R* outt = gt + 2 * (t0 < t1 ? mt_off[t0] : 0);
-  for (int pt = threadIdx.x; pt < npts; pt += blockDim.x) {
-    const int p0 = pt / (sp * sp), p1 = (pt / sp) % sp, p2 = pt % sp;
-    int64_t pos = gcnt[pt];
-    int e;
-    for (int64_t i = k0; i < k1; ++i)
-      if (covers(mr_base, mr_ext, i, p0, p1, p2, e)) {
-        const R* m = mr + mr_off[i] + 3 * e;
-        R* o = outr + 4 * pos++;
-        o[0] = (R)(i - k0);
-        o[1] = m[0];
-        o[2] = m[1];
-        o[3] = m[2];
+  int32_t rr = 0, rt = 0;  // running offsets (thread 0)
+  for (int q0 = 0; q0 < npts; q0 += gp) {
+    const int q1 = q0 + gp < npts ? q0 + gp : npts;
+    for (int pt = q0 + threadIdx.x; pt < q1; pt += blockDim.x) {
+      const int p0 = pt / (sp * sp), p1 = (pt / sp) % sp, p2 = pt % sp;
+      int cr = 0, ct = 0, e;
+      for (int64_t i = k0; i < k1; ++i) cr += covers(mr_base, mr_ext, i, p0, p1, p2, e);
+      for (int64_t i = t0; i < t1; ++i) ct += covers(mt_base, mt_ext, i, p0, p1, p2, e);
+      gcnt[pt - q0] = cr;
+      gcnt[gp + pt - q0] = ct;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int pt = q0; pt < q1; ++pt) {
+        const int32_t vr = gcnt[pt - q0], vt = gcnt[gp + pt - q0];
+        gcnt[pt - q0] = rr;
+        gcnt[gp + pt - q0] = rt;
+        pr[pt] = rr;
+        pt_[pt] = rt;
+        rr += vr;
+        rt += vt;
       }
-    pos = gcnt[npts + pt];
-    for (int64_t i = t0; i < t1; ++i)
-      if (covers(mt_base, mt_ext, i, p0, p1, p2, e)) {
-        R* o = outt + 2 * pos++;
-        o[0] = (R)(i - t0);
-        o[1] = mt[mt_off[i] + e];
+      if (q1 == npts) {
+        pr[npts] = rr;
+        pt_[npts] = rt;
       }
+    }
+    __syncthreads();
+    for (int pt = q0 + threadIdx.x; pt < q1; pt += blockDim.x) {
+      const int p0 = pt / (sp * sp), p1 = (pt / sp) % sp, p2 = pt % sp;
+      int64_t pos = gcnt[pt - q0];
+      int e;
+      for (int64_t i = k0; i < k1; ++i)
+        if (covers(mr_base, mr_ext, i, p0, p1, p2, e)) {
+          const R* m = mr + mr_off[i] + 3 * e;
+          R* o = outr + 4 * pos++;
+          o[0] = (R)(i - k0);
+          o[1] = m[0];
+          o[2] = m[1];
+          o[3] = m[2];
+        }
+      pos = gcnt[gp + pt - q0];
+      for (int64_t i = t0; i < t1; ++i)
+        if (covers(mt_base, mt_ext, i, p0, p1, p2, e)) {
+          R* o = outt + 2 * pos++;
+          o[0] = (R)(i - t0);
+          o[1] = mt[mt_off[i] + e];
+        }
+    }
+    __syncthreads();  // gcnt is reused by the next group of points
   }
 }
 
@@ -1024,7 +1036,8 @@ void launch_gather_build(const R* mr, const int32_t* mr_base, const int32_t* mr_
                          const int64_t* box_rwg_ptr, const int64_t* box_tri_ptr, int64_t B, int sp,
                          int32_t* gptr_r, int32_t* gptr_t, R* gr, R* gt, cudaStream_t s) {
   if (B <= 0) return;
-  const size_t smem = sizeof(int32_t) * 2 * (size_t)sp * sp * sp;
+  const int64_t npts = (int64_t)sp * sp * sp;
+  const size_t smem = sizeof(int32_t) * 2 * (size_t)(npts < GB_PTS ? npts : GB_PTS);
   if (smem > 48 * 1024) cudaFuncSetAttribute(k_gather_build<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_gather_build<R><<<(unsigned)B, 256, smem, s>>>(mr, mr_base, mr_ext, mr_off, mt, mt_base, mt_ext, mt_off,
                                                    box_rwg_ptr, box_tri_ptr, sp, gptr_r, gptr_t, gr, gt);
