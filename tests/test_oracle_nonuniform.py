@@ -35,20 +35,22 @@ def nu_op(nu_mesh):
     return NU.AdaptiveBsplineEFIE(nu_mesh, 2 * np.pi, P, max_elems=60, top=2, near=None)
 
 
-def _split_rows(mesh, op, k, rows, x, kernel, want_far):
+def _split_rows(mesh, op, k, rows, x, kernel, want_far, **quad):
     """Exact (far or near) part of (T x)[rows] for the op's block partition:
     (yA, yV) with the A part summed over the far (near) RWG columns of each row
-    and the V part over the far (near) triangles of each test triangle."""
+    and the V part over the far (near) triangles of each test triangle.  quad:
+    the dense reference's quadrature orders (n_reg high enough that a
+    polynomial kernel is integrated exactly)."""
     nb, rl, tl = op.near_masks()
     Xm = np.stack([x * (nb[rl[m], rl] != want_far) for m in rows])
-    yA = np.diagonal(dense.rows_dense(mesh, k, rows, Xm, kernel=kernel)[0]).copy()
+    yA = np.diagonal(dense.rows_dense(mesh, k, rows, Xm, kernel=kernel, **quad)[0]).copy()
     tri, _, _ = dense.rwg_sides(mesh)
     rho = mesh.sigmaT_apply(x)
     yV = np.zeros(len(rows), dtype=np.complex128)
     for i, m in enumerate(rows):
         for s, sgn in ((0, 1.0), (1, -1.0)):
             c = tri[m, s]
-            I0, _ = dense.pair_integrals(mesh, np.full(mesh.Nt, c), np.arange(mesh.Nt), k, kernel=kernel)
+            I0, _ = dense.pair_integrals(mesh, np.full(mesh.Nt, c), np.arange(mesh.Nt), k, kernel=kernel, **quad)
             keep = nb[tl[c], tl] != want_far
             yV[i] += sgn * np.sum(np.where(keep, I0 / (mesh.area[c] * mesh.area) * rho, 0.0))
     return yA, yV
@@ -112,3 +114,24 @@ def test_fast_vs_dense_rows(nu_mesh, nu_op):
     dA, dV = dense.rows_dense(m, k, rows, x)
     y_dense = 1j * k * dA[0] + dV[0] / (1j * k)
     assert np.linalg.norm(y_fast - y_dense) / np.linalg.norm(y_dense) < 1e-3
+
+
+@pytest.mark.parametrize("p", [1, 5])
+def test_polynomial_kernel_exact_other_degrees(nu_mesh, p):
+    """The same exactness for p = 1 (Table I: no knots removed) and p = 5 (two
+    removed per side), with a kernel of degree p, on the nonuniform tree with
+    leaves on two levels."""
+    m, k = nu_mesh, 2 * np.pi
+
+    def kern(D):
+        return (D[..., 0] + 2.0 * D[..., 1] - D[..., 2] + 0.3) ** p + 0j
+
+    op = NU.AdaptiveBsplineEFIE(m, k, p, max_elems=60, top=2, kernel=kern, near=None, allow_overlap=True)
+    assert sum(op.tree.is_leaf[ell].any() for ell in op.grid_levels) >= 2
+    x = E.complex_gaussian(m.N, 16 + p)
+    rows = np.random.default_rng(30 + p).choice(m.N, 8, replace=False)
+    yA, yV = op.far_parts(x)
+    # a regular rule exact for the degree-p kernel times the linear basis functions
+    rA, rV = _split_rows(m, op, k, rows, x, kern, want_far=True, n_reg=(p + 4) // 2 + 1)
+    assert np.linalg.norm(yA[rows] - rA) / np.linalg.norm(rA) < 1e-11
+    assert np.linalg.norm(yV[rows] - rV) / np.linalg.norm(rV) < 1e-11
