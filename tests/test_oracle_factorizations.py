@@ -47,6 +47,35 @@ def test_polynomial_kernel_exact(k):
         assert np.linalg.norm(yV - rV) / np.linalg.norm(rV) < 1e-12, cls.__name__
 
 
+@pytest.mark.parametrize("p", [2, 5])
+def test_polynomial_kernel_exact_other_degrees(p):
+    """The same exactness for p = 2 (Table I: no knots removed) and p = 5 (two
+    removed per side), with a kernel of degree p and its Hessian; the dense
+    reference on a regular rule exact for the degree-p kernel."""
+    def kern(D):
+        return (D[..., 0] + 2.0 * D[..., 1] - D[..., 2] + 0.3) ** p + 0j
+
+    def hess(D):
+        u = D[..., 0] + 2.0 * D[..., 1] - D[..., 2] + 0.3
+        return (p * (p - 1) * u ** (p - 2))[..., None, None] * np.outer(A_VEC, A_VEC) + 0j
+
+    V, T = E.icosphere(3, 0.5)
+    m = build_rwg(V, T)
+    A, Vm = dense.assemble_dense(m, 2 * np.pi, kernel=kern, n_reg=(p + 4) // 2 + 1)
+    S = m.sigma_dense()
+    Phi = S @ Vm @ S.T
+    x = E.complex_gaussian(m.N, 20 + p)
+    for cls, extra in ((F.DirectBsplineEFIE, {}), (F.DyadicBsplineEFIE, {"kernel_hessian": hess})):
+        op = cls(m, 2 * np.pi, p, 0.06, 2, kernel=kern, near=None, allow_overlap=True, **extra)
+        assert len(op.IL[op.tree.D][0]) > 0
+        nb, rb, _ = op.near_masks()
+        mask = nb[rb[:, None], rb[None, :]]
+        yA, yV = op.far_parts(x)
+        rA, rV = np.where(mask, 0, A) @ x, np.where(mask, 0, Phi) @ x
+        assert np.linalg.norm(yA - rA) / np.linalg.norm(rA) < 1e-11, (cls.__name__, p)
+        assert np.linalg.norm(yV - rV) / np.linalg.norm(rV) < 1e-11, (cls.__name__, p)
+
+
 def test_green_hessian_finite_difference():
     k = 2 * np.pi
     rng = np.random.default_rng(1)

@@ -117,19 +117,21 @@ def test_fast_vs_dense_rows(nu_mesh, nu_op):
 
 
 @pytest.mark.parametrize("p", [1, 5])
-def test_polynomial_kernel_exact_other_degrees(nu_mesh, p):
+def test_polynomial_kernel_exact_other_degrees(p):
     """The same exactness for p = 1 (Table I: no knots removed) and p = 5 (two
-    removed per side), with a kernel of degree p, on the nonuniform tree with
-    leaves on two levels."""
-    m, k = nu_mesh, 2 * np.pi
+    removed per side), with a kernel of degree p, on a tree with leaves on three
+    levels (a fine small sphere beside a coarse large one)."""
+    k = 2 * np.pi
+    m = build_rwg(*E.merge_meshes(E.icosphere(8, 0.3, center=(-1.0, 0.0, 0.0)),
+                                  E.icosphere(5, 0.8, center=(1.0, 0.1, 0.05))))
 
     def kern(D):
         return (D[..., 0] + 2.0 * D[..., 1] - D[..., 2] + 0.3) ** p + 0j
 
-    op = NU.AdaptiveBsplineEFIE(m, k, p, max_elems=60, top=2, kernel=kern, near=None, allow_overlap=True)
+    op = NU.AdaptiveBsplineEFIE(m, k, p, max_elems=30, top=2, kernel=kern, near=None, allow_overlap=True)
     assert sum(op.tree.is_leaf[ell].any() for ell in op.grid_levels) >= 2
     x = E.complex_gaussian(m.N, 16 + p)
-    rows = np.random.default_rng(30 + p).choice(m.N, 8, replace=False)
+    rows = np.random.default_rng(30 + p).choice(m.N, 6, replace=False)
     yA, yV = op.far_parts(x)
     # a regular rule exact for the degree-p kernel times the linear basis functions
     rA, rV = _split_rows(m, op, k, rows, x, kern, want_far=True, n_reg=(p + 4) // 2 + 1)
