@@ -357,6 +357,9 @@ class EFIE:
                                                  ctypes.byref(h)))
         else:
             t = dict(max_elems=200, max_prot=0.25, top=2, n_splines=0, max_depth=0)
+            unknown = set(tree) - set(t)
+            if unknown:
+                raise ValueError(f"unknown tree options: {sorted(unknown)}")
             t.update(tree)
             to = TreeOptions(t["max_elems"], t["max_prot"], t["top"], t["n_splines"], t["max_depth"])
             _check(self.lib, self.lib.efie_setup_adaptive(ctypes.byref(m), k, p, ctypes.byref(to), ctypes.byref(o),

@@ -269,6 +269,8 @@ def test_factorization_option_checked_first(lib):
     assert e.value.code == -1
     with pytest.raises(ValueError):
         G.EFIE(V, T, 2 * np.pi, 3)
+    with pytest.raises(ValueError):
+        G.EFIE(V, T, 2 * np.pi, 3, tree=dict(max_elem=30))
 
 
 def test_planewave_argument_checks(lib):
