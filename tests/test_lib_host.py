@@ -245,6 +245,13 @@ def test_setup_without_gpu_fails_loudly(lib):
     with pytest.raises(G.EfieError) as e:
         G.EFIE(V, T, 2 * np.pi, 3, 0.1, 1, factorization=G.EFIE_FACT_DIRECT)
     assert e.value.code == -3
+    for fact in (G.EFIE_FACT_DYADIC,):
+        with pytest.raises(G.EfieError) as e:
+            G.EFIE(V, T, 2 * np.pi, 3, 0.1, 1, factorization=fact)
+        assert e.value.code == -3
+    with pytest.raises(G.EfieError) as e:
+        G.EFIE(V, T, 2 * np.pi, 3, tree=dict(max_elems=30, top=2))
+    assert e.value.code == -3
 
 
 def test_factorization_option_checked_first(lib):
