@@ -225,3 +225,126 @@ class DyadicBsplineEFIE(DirectBsplineEFIE):
                 R[x, :3] += Kg[None] * Q[y]
                 R[x, 3:] += np.einsum("abxyz,bxyz->axyz", Kh, Q[y])
         return np.fft.ifftn(R, axes=(-3, -2, -1))[..., :ns, :ns, :ns]
+
+
+# ------------------------------------------------------------ nonuniform tree
+# The direct and dyadic factorizations on the nonuniform octree of Sec. VII
+# (`oracle.nonuniform`): every RWG's moments (and, for the direct form, its
+# divergence moments) in its own leaf with that level's splines; the leaves of
+# every level anterpolated into, and interpolated from, their own level's grids;
+# the near field on the RWG pairs of near leaves (ancestors on the coarser of
+# the two levels adjacent or equal).
+
+from . import nonuniform as _nu  # noqa: E402  (the nonuniform tree does not import this module)
+
+
+class AdaptiveDirectBsplineEFIE(_RwgNearMixin, _nu.AdaptiveBsplineEFIE):
+    """Direct factorization (Sec. VI-B) on the nonuniform octree."""
+
+    n_comp = 4
+
+    def __init__(self, mesh: RWGMesh, k, p, max_elems=200, max_prot=0.25, top=2, n_splines=None, kernel=None,
+                 near="auto", dense_AV=None, translation="fft", root=None, max_depth=30, allow_overlap=False):
+        super().__init__(mesh, k, p, max_elems, max_prot, top, n_splines, kernel, near=None, dense_AV=None,
+                         translation=translation, root=root, max_depth=max_depth, allow_overlap=allow_overlap)
+        self.m_div_l = {ell: divergence_moments(mesh, _nu._LevelView(self.tree, ell), self.rwg_at[ell])
+                        for ell in self.grid_levels}
+        if near is None:
+            self.A_near = sp.csr_matrix((mesh.N, mesh.N), dtype=np.complex128)
+            self.Phi_near = sp.csr_matrix((mesh.N, mesh.N), dtype=np.complex128)
+        else:
+            self.A_near, self.Phi_near = self._near_rwg(dense_AV)
+
+    def _leaf_grids(self, j):
+        """Grids of every level with the anterpolated moments of the RWGs whose
+        leaves lie there: components 0..2 the RWG moments, 3 (direct form) the
+        divergence moments."""
+        tree = self.tree
+        q = {}
+        for ell in self.grid_levels:
+            L = tree.levels[ell]
+            q[ell] = np.zeros((len(L.boxes), self.n_comp, L.sp, L.sp, L.sp), dtype=np.complex128)
+            ra = self.rwg_at[ell]
+            np.add.at(q[ell], (tree.rwg_box[ra], slice(0, 3)), j[ra][:, None, None, None, None] * self.m_rwg_l[ell])
+            if self.n_comp == 4:
+                np.add.at(q[ell], (tree.rwg_box[ra], 3), j[ra][:, None, None, None] * self.m_div_l[ell])
+        return q
+
+    def _far_pass_levels(self, q):
+        """Upward transfers (children added into their parents), stabilized
+        translations of every level, downward transfers; the output grids of
+        every level."""
+        tree = self.tree
+        for ell in range(tree.D, tree.top, -1):
+            ijk = tree.levels[ell].ijk
+            for b in range(len(ijk)):
+                M = [self.CR[ell] if bb else self.CL[ell] for bb in ijk[b] % 2]
+                q[ell - 1][tree.parent[ell][b]] += fastmv.mode3(M[0], M[1], M[2], q[ell][b])
+        r = {}
+        for ell in self.grid_levels:
+            P = self.P[ell]
+            r[ell] = fastmv.mode3(P.T, P.T, P.T, self._translate(ell, fastmv.mode3(P, P, P, q[ell])))
+        for ell in range(tree.top + 1, tree.D + 1):
+            ijk = tree.levels[ell].ijk
+            for b in range(len(ijk)):
+                M = [self.CR[ell] if bb else self.CL[ell] for bb in ijk[b] % 2]
+                r[ell][b] += fastmv.mode3(M[0].T, M[1].T, M[2].T, r[ell - 1][tree.parent[ell][b]])
+        return r
+
+    def _translate(self, ell, qt):
+        return self._translate_level(ell, qt)
+
+    def far_parts(self, j):
+        j = np.asarray(j, dtype=np.complex128)
+        tree = self.tree
+        r = self._far_pass_levels(self._leaf_grids(j))
+        yA = np.zeros(self.mesh.N, dtype=np.complex128)
+        yV = np.zeros(self.mesh.N, dtype=np.complex128)
+        for ell in self.grid_levels:
+            ra = self.rwg_at[ell]
+            rb = r[ell][tree.rwg_box[ra]]
+            yA[ra] = np.einsum("ndabc,ndabc->n", self.m_rwg_l[ell], rb[:, :3])
+            yV[ra] = np.einsum("nabc,nabc->n", self.m_div_l[ell], rb[:, 3])
+        return yA, yV
+
+    def matvec_parts(self, j):
+        return _RwgNearMixin.matvec_parts(self, j)
+
+
+class AdaptiveDyadicBsplineEFIE(AdaptiveDirectBsplineEFIE):
+    """Dyadic factorization (Sec. VI-C) on the nonuniform octree: three RWG
+    moment components, translated with g and with the Hessian of g; the
+    scalar part is returned as -(H x).  kernel_hessian(D) -> [..., 3, 3] must
+    accompany a custom kernel."""
+
+    n_comp = 3
+
+    def __init__(self, mesh: RWGMesh, k, p, max_elems=200, max_prot=0.25, top=2, n_splines=None, kernel=None,
+                 kernel_hessian=None, near="auto", dense_AV=None, translation="fft", root=None, max_depth=30,
+                 allow_overlap=False):
+        if (kernel is None) != (kernel_hessian is None):
+            raise ValueError("a custom kernel needs its Hessian")
+        self.kernel_hessian = kernel_hessian
+        super().__init__(mesh, k, p, max_elems, max_prot, top, n_splines, kernel, near, dense_AV, translation,
+                         root, max_depth, allow_overlap)
+
+    def _hess(self, D):
+        if self.kernel_hessian is not None:
+            return self.kernel_hessian(D)
+        return green_hessian(D, self.k)
+
+    def _translate(self, ell, qt):
+        return DyadicBsplineEFIE._translate_dyad(self, ell, qt)
+
+    def far_parts(self, j):
+        j = np.asarray(j, dtype=np.complex128)
+        tree = self.tree
+        r = self._far_pass_levels(self._leaf_grids(j))    # [B, 6, ...]: g q_d, then sum_e H_de q_e
+        yA = np.zeros(self.mesh.N, dtype=np.complex128)
+        yH = np.zeros(self.mesh.N, dtype=np.complex128)
+        for ell in self.grid_levels:
+            ra = self.rwg_at[ell]
+            rb = r[ell][tree.rwg_box[ra]]
+            yA[ra] = np.einsum("ndabc,ndabc->n", self.m_rwg_l[ell], rb[:, :3])
+            yH[ra] = np.einsum("ndabc,ndabc->n", self.m_rwg_l[ell], rb[:, 3:])
+        return yA, -yH

@@ -117,3 +117,58 @@ def test_symmetric(c1_mesh, c1_forms):
     for op in c1_forms:
         a, b = x2 @ op.matvec(x1), x1 @ op.matvec(x2)
         assert abs(a - b) / abs(a) < 1e-12, type(op).__name__
+
+
+def test_adaptive_forms_uniform_limit(c1_mesh, c1_oracle):
+    """The direct and dyadic forms on the nonuniform octree, with every box
+    subdivided down to the uniform tree's depth (same root), reproduce the
+    uniform-tree forms to rounding (far parts; near parts share the code)."""
+    _, _, m = c1_mesh
+    tr = c1_oracle.tree
+    x = E.complex_gaussian(m.N, 40)
+    lim = dict(max_elems=-1, max_prot=np.inf, top=tr.top, root=(tr.root_lo, tr.root_edge), max_depth=tr.D,
+               near=None)
+    for uni, ada in ((F.DirectBsplineEFIE, F.AdaptiveDirectBsplineEFIE),
+                     (F.DyadicBsplineEFIE, F.AdaptiveDyadicBsplineEFIE)):
+        u = uni(m, 2 * np.pi, P, 0.1, 2, near=None)
+        a = ada(m, 2 * np.pi, P, **lim)
+        assert a.tree.D == tr.D and all(a.tree.is_leaf[tr.D])
+        for yu, ya in zip(u.far_parts(x), a.far_parts(x)):
+            assert np.linalg.norm(ya - yu) / np.linalg.norm(yu) < 1e-12, ada.__name__
+
+
+def test_adaptive_forms_polynomial_kernel_exact():
+    """Far exactness of the direct and dyadic forms on a nonuniform tree with
+    leaves on three levels (a fine small sphere beside a coarse large one):
+    with a degree-p polynomial kernel (and its Hessian) the far parts equal
+    the dense far rows, A masked and Phi = Sigma V Sigma^T masked by the RWG
+    pairs of non-near leaves (the dyadic scalar part -H x equals Phi x by
+    integration by parts)."""
+    from oracle.geometry import build_rwg
+    k = 2 * np.pi
+    m = build_rwg(*E.merge_meshes(E.icosphere(8, 0.3, center=(-1.0, 0.0, 0.0)),
+                                  E.icosphere(5, 0.8, center=(1.0, 0.1, 0.05))))
+    x = E.complex_gaussian(m.N, 41)
+    rows = np.random.default_rng(42).choice(m.N, 6, replace=False)
+    quad = dict(n_reg=(P + 4) // 2 + 1)
+    S = m.sigma_dense()
+    tri, _, _ = dense.rwg_sides(m)
+    for cls, extra in ((F.AdaptiveDirectBsplineEFIE, {}), (F.AdaptiveDyadicBsplineEFIE, {"kernel_hessian": _hess})):
+        op = cls(m, k, P, max_elems=30, top=2, kernel=_kern, near=None, allow_overlap=True, **extra)
+        assert sum(op.tree.is_leaf[ell].any() for ell in op.grid_levels) == 3
+        nb, rl, _ = op.near_masks()
+        yA, yV = op.far_parts(x)
+        far = [~nb[rl[mm], rl] for mm in rows]
+        Xm = np.stack([x * f for f in far])
+        rA = np.diagonal(dense.rows_dense(m, k, rows, Xm, kernel=_kern, **quad)[0])
+        rV = np.zeros(len(rows), dtype=np.complex128)
+        for i, mm in enumerate(rows):
+            # row mm of Sigma V Sigma^T: its two triangles' rows of V, then Sigma^T
+            vrow = np.zeros(m.Nt, dtype=np.complex128)
+            for s in range(2):
+                c = tri[mm, s]
+                I0, _ = dense.pair_integrals(m, np.full(m.Nt, c), np.arange(m.Nt), k, kernel=_kern, **quad)
+                vrow += S[mm, c] * I0 / (m.area[c] * m.area)
+            rV[i] = (vrow @ S.T) @ (x * far[i])
+        assert np.linalg.norm(yA[rows] - rA) / np.linalg.norm(rA) < 1e-11, cls.__name__
+        assert np.linalg.norm(yV[rows] - rV) / np.linalg.norm(rV) < 1e-11, cls.__name__
