@@ -980,6 +980,113 @@ static void set_uniform_leaves(Plan& P) {
   P.tri_lbox = P.tri_box;
 }
 
+// Index checks of everything the device kernels index with: every box,
+// leaf, function, list and tile index in range, every CSR pointer array
+// monotone and closed, every moment block inside its leaf's grid.  A planner
+// error becomes EfieError here, before any kernel runs.
+static void validate_plan(const Plan& P, bool with_moments) {
+  auto check = [](bool ok, const char* what) {
+    if (!ok) fail(-1, std::string("internal: plan check failed: ") + what);
+  };
+  auto csr = [&](const std::vector<int64_t>& ptr, size_t rows, size_t nnz, const char* what) {
+    check(ptr.size() == rows + 1 && ptr[0] == 0 && (size_t)ptr[rows] == nnz, what);
+    for (size_t i = 0; i < rows; ++i) check(ptr[i] <= ptr[i + 1], what);
+  };
+  const int nlev = (int)P.lv.size();
+  check(nlev == P.D - P.top + 1, "level count");
+  for (int ell = P.top; ell <= P.D; ++ell) {
+    const Level& L = P.L(ell);
+    const size_t B = L.code.size();
+    check(L.ijk.size() == 3 * B && L.leaf.size() == B && L.parent.size() == B, "box arrays");
+    const size_t O = L.offsets.size() / 3;
+    check(L.offsets.size() == 3 * O, "offsets");
+    if (ell > P.top) {
+      const Level& U = P.L(ell - 1);
+      for (size_t b = 0; b < B; ++b) check(L.parent[b] >= 0 && (size_t)L.parent[b] < U.code.size(), "parent");
+    }
+    if (ell < P.D) {
+      csr(L.child_ptr, B, P.L(ell + 1).code.size(), "children");
+      const Level& C = P.L(ell + 1);
+      for (size_t b = 0; b < B; ++b)
+        for (int64_t c = L.child_ptr[b]; c < L.child_ptr[b + 1]; ++c) check(C.parent[c] == (int64_t)b, "children");
+    }
+    csr(L.il_ptr, B, L.il_src.size(), "interaction list");
+    check(L.il_off.size() == L.il_src.size(), "interaction list");
+    for (size_t e = 0; e < L.il_src.size(); ++e)
+      check(L.il_src[e] >= 0 && (size_t)L.il_src[e] < B && L.il_off[e] >= 0 && (size_t)L.il_off[e] < O,
+            "interaction list");
+    auto tiles = [&](const std::vector<int64_t>& tp, const std::vector<int64_t>& sp_, const std::vector<int64_t>& kp,
+                     const std::vector<int32_t>& tg, const std::vector<int32_t>& sr,
+                     const std::vector<int32_t>& kx, const char* what) {
+      if (tp.empty()) return;
+      const size_t nt = tp.size() - 1;
+      csr(tp, nt, tg.size(), what);
+      csr(sp_, nt, sr.size(), what);
+      csr(kp, nt, kx.size(), what);
+      for (int32_t x : tg) check(x >= 0 && (size_t)x < B, what);
+      for (int32_t y : sr) check(y >= 0 && (size_t)y < B, what);
+      for (int32_t o : kx) check(o >= -1 && o < (int64_t)O, what);
+      for (size_t t = 0; t < nt; ++t) {
+        const int64_t ntg = tp[t + 1] - tp[t], nsr = sp_[t + 1] - sp_[t];
+        check(kp[t + 1] - kp[t] >= ntg * nsr, what);
+      }
+    };
+    tiles(L.tile_tgt_ptr, L.tile_src_ptr, L.tile_kidx_off, L.tile_tgt, L.tile_src, L.tile_kidx, "tiles");
+    tiles(L.tct_tgt_ptr, L.tct_src_ptr, L.tct_kidx_off, L.tct_tgt, L.tct_src, L.tct_kidx, "tensor-core tiles");
+  }
+  // leaves
+  const int64_t NL = P.n_leaves;
+  check((int64_t)P.leaf_level.size() == NL && (int64_t)P.leaf_box.size() == NL, "leaves");
+  csr(P.level_leaf_ptr, (size_t)nlev, (size_t)NL, "leaves per level");
+  for (int i = 0; i < nlev; ++i) {
+    const Level& L = P.lv[i];
+    for (int64_t x = P.level_leaf_ptr[i]; x < P.level_leaf_ptr[i + 1]; ++x)
+      check(P.leaf_level[x] == P.top + i && P.leaf_box[x] >= 0 && (size_t)P.leaf_box[x] < L.code.size() &&
+                L.leaf[P.leaf_box[x]],
+            "leaf box");
+  }
+  // functions sorted by leaf
+  auto functions = [&](const std::vector<int32_t>& perm, const std::vector<int32_t>& leaf,
+                       const std::vector<int32_t>& lbox, const std::vector<int64_t>& ptr, int64_t n, const char* what) {
+    check((int64_t)perm.size() == n && (int64_t)leaf.size() == n && (int64_t)lbox.size() == n, what);
+    csr(ptr, (size_t)NL, (size_t)n, what);
+    for (int64_t x = 0; x < NL; ++x)
+      for (int64_t i = ptr[x]; i < ptr[x + 1]; ++i) check(leaf[i] == x && lbox[i] == P.leaf_box[x], what);
+    std::vector<uint8_t> seen(n, 0);
+    for (int32_t c : perm) {
+      check(c >= 0 && c < n && !seen[c], what);
+      seen[c] = 1;
+    }
+  };
+  functions(P.rwg_perm, P.rwg_box, P.rwg_lbox, P.box_rwg_ptr, P.g.N, "RWG order");
+  functions(P.tri_perm, P.tri_box, P.tri_lbox, P.box_tri_ptr, P.g.nt, "triangle order");
+  // near blocks over the leaves
+  csr(P.near_ptr, (size_t)NL, P.near_src.size(), "near lists");
+  for (int32_t y : P.near_src) check(y >= 0 && y < NL, "near lists");
+  check(P.blkA_off.size() == P.near_src.size() + 1 && P.blkV_off.size() == P.near_src.size() + 1, "near blocks");
+  csr(P.tset_ptr, (size_t)NL, P.tset.size(), "triangle sets");
+  if (!with_moments) return;
+  // moment blocks inside the grid of each function's leaf
+  auto blocks = [&](const MomentBlocks& MB, const std::vector<int32_t>& leaf, int ncomp, const char* what) {
+    const size_t n = leaf.size();
+    check(MB.base.size() == 3 * n && MB.ext.size() == 3 * n && MB.off.size() == n + 1 && MB.off[0] == 0, what);
+    for (size_t i = 0; i < n; ++i) {
+      const int sp = P.L(P.leaf_level[leaf[i]]).sp;
+      int64_t ne = ncomp;
+      for (int d = 0; d < 3; ++d) {
+        const int b = MB.base[3 * i + d], e = MB.ext[3 * i + d];
+        check(b >= 0 && e >= 0 && b + e <= sp, what);
+        ne *= e;
+      }
+      check(MB.off[i + 1] - MB.off[i] == ne, what);
+    }
+    check((size_t)MB.off[n] == MB.data.size(), what);
+  };
+  blocks(P.mom_rwg, P.rwg_box, 3, "RWG moments");
+  blocks(P.mom_tri, P.tri_box, 1, "pulse moments");
+  if (!P.mom_div.off.empty()) blocks(P.mom_div, P.rwg_box, 1, "divergence moments");
+}
+
 // ------------------------------------------------------------------ build
 void build_plan(Plan& P, const double* xyz, int64_t nv, const int32_t* tri, int64_t nt,
                 double k, int p, double grid_spacing, int levels, int n_splines,
@@ -1179,8 +1286,8 @@ void build_plan(Plan& P, const double* xyz, int64_t nv, const int32_t* tri, int6
   }
   set_uniform_leaves(P);
   build_near_blocks(P);
-  if (!with_moments) return;
-  build_moments(P, with_div);
+  if (with_moments) build_moments(P, with_div);
+  validate_plan(P, with_moments);
 }
 
 // ------------------------------------------------------------ nonuniform tree
@@ -1663,7 +1770,7 @@ void build_plan_adaptive(Plan& P, const double* xyz, int64_t nv, const int32_t* 
   build_translation_lists(P);
   build_level_matrices(P);
   build_near_blocks(P);
-  if (!with_moments) return;
-  build_moments(P, with_div);
+  if (with_moments) build_moments(P, with_div);
+  validate_plan(P, with_moments);
 }
 }  // namespace efie
