@@ -33,7 +33,8 @@ Contents (all FP64 unless a function says otherwise):
                    rule, Sec. IV-C/D buffer rule for leaves on the parent
                    level, level-consistent near blocks).
 * ``factorizations`` - the direct (RWG + divergence moments) and dyadic
-                   (3 x 3 Hessian translations) factorizations (Sec. VI).
+                   (3 x 3 Hessian translations) factorizations (Sec. VI), on
+                   the uniform and on the nonuniform octree.
 * ``krylov``     - plain GMRES / FGMRES.
 * ``mpnn``       - FP64 NumPy forward/backward of the learned preconditioner
                    network (not part of the paper).
