@@ -1148,6 +1148,14 @@ void setup_impl(efie_handle* h, const efie_mesh* mesh, double k, int p, double g
   else
     build_plan(P, mesh->xyz, mesh->n_vertices, mesh->tri, mesh->n_triangles, k, p, grid_spacing, levels,
                h->opt.n_splines, true, h->direct);
+  // the upward transfer takes at most TRANSFER_MAX_SPLINES splines per axis
+  // on every level below the top one: refuse other plans before any device
+  // memory is allocated (not at the first product)
+  for (int ell = P.top + 1; ell <= P.D; ++ell)
+    if (P.L(ell).sp > TRANSFER_MAX_SPLINES)
+      throw EfieError{EFIE_EINVAL, "level " + std::to_string(ell) + " has " + std::to_string(P.L(ell).sp) +
+                                       " splines per axis; the transfers take at most " +
+                                       std::to_string(TRANSFER_MAX_SPLINES) + " below the top level"};
   phase_done(0);
   DevMem& M = h->mem;
   cudaStream_t s = 0;

@@ -78,7 +78,10 @@ void launch_mode(const cpx_t<R>* in, View vin, cpx_t<R>* out, View vout, int64_t
                  const int8_t* sel, const int64_t* srcmap, bool accumulate, cudaStream_t s);
 
 // one pass of the sibling-shared upward transfer: out[g] = M(bit0) in[src0] +
-// M(bit1) in[src1] along axis ax (src1 < 0: absent), M(0) = M0, M(1) = M1
+// M(bit1) in[src1] along axis ax (src1 < 0: absent; src0 < 0: an output
+// without inputs, written as zeros), M(0) = M0, M(1) = M1; nin (the child
+// level's splines per axis) at most TRANSFER_MAX_SPLINES
+constexpr int TRANSFER_MAX_SPLINES = 40;
 template <typename R>
 void launch_mode_pair(const cpx_t<R>* in, View vin, cpx_t<R>* out, View vout, int64_t G, int C, int ax, int nin,
                       int e0, int e1, int e2, const R* M0, const R* M1, const int64_t* src0, const int64_t* src1,
@@ -97,12 +100,6 @@ bool launch_dft_yz(const float2* in, float2* out, int64_t B, int sp, int n, cons
 bool dft_yz_fits(int sp, int n);   // the fused forward pass takes this level
 bool dft_zy_fits(int sp, int n);   // the fused inverse pass takes this level
 
-// one pass of the sibling-shared upward transfer: out[g] = M(bit0) in[src0] +
-// M(bit1) in[src1] along axis ax (src1 < 0: absent), M(0) = M0, M(1) = M1
-template <typename R>
-void launch_mode_pair(const cpx_t<R>* in, View vin, cpx_t<R>* out, View vout, int64_t G, int C, int ax, int nin,
-                      int e0, int e1, int e2, const R* M0, const R* M1, const int64_t* src0, const int64_t* src1,
-                      const int8_t* bit0, const int8_t* bit1, cudaStream_t s);
 
 // DFT passes of the stabilized transforms using the conjugate symmetry of
 // M = F P (forward, n x nin) / P^T F^{-1} (inverse, nout x n); false when no

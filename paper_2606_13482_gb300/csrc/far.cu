@@ -306,7 +306,7 @@ void launch_mode_pair(const cpx_t<R>* in, View vin, cpx_t<R>* out, View vout, in
   EFIE_MP(9)
   EFIE_MP(13)
   EFIE_MP(21)
-  EFIE_MP(40)
+  EFIE_MP(TRANSFER_MAX_SPLINES)
 #undef EFIE_MP
   throw EfieError{EFIE_EINVAL, "transfer: more than 40 splines per axis below the top level"};
 }
