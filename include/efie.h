@@ -232,7 +232,9 @@ int efie_plan_moments(const efie_mesh *mesh, double wavenumber, int spline_degre
  * divergence moments of every RWG in its own leaf box and interpolated back
  * onto them, and its near field Phi = Sigma V Sigma^T is assembled on the
  * RWG pairs of A's blocks (from the same triangle-pair integrals); products,
- * solves and the (A x, Phi x) split of efie_matvec_parts follow.  With
+ * solves and the (A x, Phi x) split of efie_matvec_parts follow.  EFIE_EINVAL
+ * also for a plan with more than 40 splines per axis on a level below the top
+ * grid level (the interlevel transfer kernels take at most that).  With
  * EFIE_FACT_DYADIC (Sec. VI-C) the near field and moments are the direct
  * form's, and the far scalar part comes instead from the three RWG moment
  * components translated with the six entries of the Hessian of g (one more
