@@ -197,8 +197,17 @@ class Batch:
         self.b = b
 
     def matvec(self, xs, ys):
+        """ys[i] = T_i xs[i]; xs[i] and ys[i] are contiguous complex128 CUDA
+        tensors [n_i, N_i] of the same shape (N_i: member i's unknowns)."""
         import torch
         n = len(self.handles)
+        if len(xs) != n or len(ys) != n:
+            raise ValueError(f"expected {n} inputs and {n} outputs (got {len(xs)} and {len(ys)})")
+        for i, (h, x, y) in enumerate(zip(self.handles, xs, ys)):
+            if x.dim() != 2:
+                raise ValueError(f"xs[{i}] must be [n, N] (got {list(x.shape)})")
+            h._vec(x)
+            h._vec(EFIE._same_rows(x, y, f"ys[{i}]"))
         X = (ctypes.c_void_p * n)(*[x.data_ptr() for x in xs])
         Y = (ctypes.c_void_p * n)(*[y.data_ptr() for y in ys])
         R = (ctypes.c_int * n)(*[x.shape[0] for x in xs])
@@ -382,6 +391,23 @@ class EFIE:
             raise ValueError("last dimension must equal the number of unknowns")
         return ctypes.c_void_p(x.data_ptr())
 
+    @staticmethod
+    def _rows(x, what):
+        """x as [n, N]: a vector [N] becomes one row."""
+        if x.dim() not in (1, 2):
+            raise ValueError(f"{what} must be [N] or [n, N] (got {list(x.shape)})")
+        return x if x.dim() == 2 else x.unsqueeze(0)
+
+    @classmethod
+    def _same_rows(cls, x2, y, what):
+        """The caller's second array as [n, N], holding exactly the rows of x2.
+        The C ABI takes one count for both arrays and no sizes, so this check
+        is the only guard against reading or writing past the shorter one."""
+        y2 = cls._rows(y, what)
+        if tuple(y2.shape) != tuple(x2.shape):
+            raise ValueError(f"{what} must have the shape of the input, {list(x2.shape)} (got {list(y.shape)})")
+        return y2
+
     def info(self):
         i = PlanInfo()
         _check(self.lib, self.lib.efie_plan_info(self.h, ctypes.byref(i)), self.h)
@@ -415,12 +441,15 @@ class EFIE:
 
     def matvec(self, x, y=None, fp64=False):
         import torch
-        x2 = x if x.dim() == 2 else x.unsqueeze(0)
+        x2 = self._rows(x, "x")
         if y is None:
-            y = torch.empty_like(x2)
+            y2 = torch.empty_like(x2)
+            out = y2 if x.dim() == 2 else y2[0]
+        else:
+            y2, out = self._same_rows(x2, y, "y"), y
         fn = self.lib.efie_matvec_fp64 if fp64 else self.lib.efie_matvec
-        _check(self.lib, fn(self.h, self._vec(x2), self._vec(y), x2.shape[0], self._stream()), self.h)
-        return y if x.dim() == 2 else y[0]
+        _check(self.lib, fn(self.h, self._vec(x2), self._vec(y2), x2.shape[0], self._stream()), self.h)
+        return out
 
     def matvec_host(self, x, y=None):
         """y = T x with x, y complex128 CPU tensors [n_rhs, N] (pin them for the
@@ -444,7 +473,7 @@ class EFIE:
 
     def matvec_parts(self, x):
         import torch
-        x2 = x if x.dim() == 2 else x.unsqueeze(0)
+        x2 = self._rows(x, "x")
         yA = torch.empty_like(x2)
         yV = torch.empty_like(x2)
         _check(self.lib, self.lib.efie_matvec_parts(self.h, self._vec(x2), self._vec(yA), self._vec(yV),
@@ -453,14 +482,17 @@ class EFIE:
 
     def solve(self, rhs, tol=1e-6, x=None):
         import torch
-        r2 = rhs if rhs.dim() == 2 else rhs.unsqueeze(0)
+        r2 = self._rows(rhs, "rhs")
         if x is None:
-            x = torch.empty_like(r2)
+            x2 = torch.empty_like(r2)
+            sol = x2 if rhs.dim() == 2 else x2[0]
+        else:
+            x2, sol = self._same_rows(r2, x, "x"), x
         infos = (SolveInfo * r2.shape[0])()
-        rc = _check(self.lib, self.lib.efie_solve(self.h, self._vec(r2), self._vec(x), r2.shape[0], tol, infos,
+        rc = _check(self.lib, self.lib.efie_solve(self.h, self._vec(r2), self._vec(x2), r2.shape[0], tol, infos,
                                                   self._stream()), self.h)
         out = [{f: getattr(i, f) for f, _ in SolveInfo._fields_} for i in infos]
-        return (x if rhs.dim() == 2 else x[0]), out, rc
+        return sol, out, rc
 
     # ---- learned preconditioner (not part of the paper)
     N_PARAMS = 25218
@@ -468,7 +500,7 @@ class EFIE:
     def precond_harvest(self, rhs, restart=10, n_cycles=4):
         """Residual/error pairs from the plain solver's restarted GMRES iterates."""
         import torch
-        r2 = rhs if rhs.dim() == 2 else rhs.unsqueeze(0)
+        r2 = self._rows(rhs, "rhs")
         n = r2.shape[0] * n_cycles
         R = torch.empty((n, self.N), dtype=torch.complex128, device="cuda")
         Ee = torch.empty_like(R)
@@ -478,7 +510,10 @@ class EFIE:
         return R, Ee
 
     def precond_train(self, r, e, epochs=10, lr=1e-3, seed=0, objective="residual"):
-        losses = (ctypes.c_double * epochs)()
+        if r.dim() != 2:
+            raise ValueError(f"r must be [n_pairs, N] (got {list(r.shape)})")
+        e = self._same_rows(r, e, "e")
+        losses = (ctypes.c_double * max(epochs, 0))()
         obj = {"error": 0, "residual": 1}[objective]
         _check(self.lib, self.lib.efie_precond_train(self.h, self._vec(r), self._vec(e), r.shape[0], epochs, lr,
                                                      seed, obj, losses, self._stream()), self.h)
@@ -497,7 +532,9 @@ class EFIE:
         out = np.zeros(self.N_PARAMS, dtype=np.float32)
         pin = None
         if new is not None:
-            new = np.ascontiguousarray(new, dtype=np.float32)
+            new = np.ascontiguousarray(new, dtype=np.float32).ravel()
+            if new.size != self.N_PARAMS:
+                raise ValueError(f"expected {self.N_PARAMS} parameters (got {new.size})")
             pin = new.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
         _check(self.lib, self.lib.efie_precond_params(self.h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
                                                       pin, self.N_PARAMS), self.h)
@@ -505,7 +542,7 @@ class EFIE:
 
     def precond_apply(self, r):
         import torch
-        r2 = r if r.dim() == 2 else r.unsqueeze(0)
+        r2 = self._rows(r, "r")
         z = torch.empty_like(r2)
         _check(self.lib, self.lib.efie_precond_apply(self.h, self._vec(r2), self._vec(z), r2.shape[0],
                                                      self._stream()), self.h)

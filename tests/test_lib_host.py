@@ -315,3 +315,90 @@ def test_plan_adaptive_near_pointer_capacity(lib):
     assert L.efie_plan_adaptive_near(ctypes.byref(m), 2 * np.pi, 3, ctypes.byref(o), None, None, None, None,
                                      nl.value + 1, ip, None, 0) == 0
     assert ptr[-1] == nz.value
+
+
+class _DeviceArray:
+    """Stands in for a contiguous complex128 CUDA tensor of a given shape
+    (shape checks only: nothing reads its memory)."""
+
+    def __init__(self, *shape):
+        import torch
+        self.shape = tuple(shape)
+        self.dtype = torch.complex128
+        self.is_cuda = True
+
+    def dim(self):
+        return len(self.shape)
+
+    def is_contiguous(self):
+        return True
+
+    def unsqueeze(self, d):
+        assert d == 0
+        return _DeviceArray(1, *self.shape)
+
+    def data_ptr(self):
+        return 0
+
+
+class _NoCalls:
+    """A library whose every entry point fails the test: the binding must
+    reject the arguments before it calls one."""
+
+    def __getattr__(self, name):
+        raise AssertionError(f"{name} was called with arguments the binding should reject")
+
+
+def test_vector_argument_checks(lib):
+    """The C ABI's products, solves and training calls take one count for an
+    input and an output array and no sizes, so the binding checks that a
+    caller-given output (or second input) holds exactly the input's rows and
+    that every array is [N] or [n, N]; a parameter vector must hold the
+    network's parameter count.  Mismatches are ValueErrors before any
+    library call."""
+    G, _ = lib
+    N = 100
+    h = G.EFIE.__new__(G.EFIE)
+    h.lib, h.h, h.N = _NoCalls(), None, N
+    D = _DeviceArray
+    bad_products = [(D(4, N), D(3, N)),      # short output
+                    (D(4, N), D(N)),         # one row for four
+                    (D(N), D(2, N)),         # two rows for one
+                    (D(4, N), D(4, N - 1)),  # wrong N
+                    (D(2, 2, N), D(2, 2, N))]  # not [n, N]
+    for x, y in bad_products:
+        with pytest.raises(ValueError):
+            h.matvec(x, y)
+        with pytest.raises(ValueError):
+            h.solve(x, 1e-6, y)
+    with pytest.raises(ValueError):
+        h.precond_train(D(8, N), D(7, N))
+    with pytest.raises(ValueError):
+        h.precond_train(D(N), D(N))
+    with pytest.raises(ValueError):
+        h.precond_params(np.zeros(h.N_PARAMS - 1, np.float32))
+    with pytest.raises(ValueError):
+        h.matvec_parts(D(1, 1, N))
+    # matching shapes get through to the library
+    for x, y in [(D(4, N), D(4, N)), (D(N), D(N)), (D(N), D(1, N))]:
+        with pytest.raises(AssertionError):
+            h.matvec(x, y)
+        with pytest.raises(AssertionError):
+            h.solve(x, 1e-6, y)
+    with pytest.raises(AssertionError):
+        h.precond_train(D(8, N), D(8, N))
+    with pytest.raises(AssertionError):
+        h.precond_params(np.zeros(h.N_PARAMS, np.float32))
+    # a batch: one input and one output per member, of the member's shape
+    h2 = G.EFIE.__new__(G.EFIE)
+    h2.lib, h2.h, h2.N = _NoCalls(), None, 2 * N
+    b = G.Batch.__new__(G.Batch)
+    b.lib, b.handles, b.b = _NoCalls(), [h, h2], None
+    for xs, ys in [([D(2, N)], [D(2, N)]),                                  # one member missing
+                   ([D(2, N), D(3, 2 * N)], [D(2, N), D(2, 2 * N)]),        # short output
+                   ([D(2, N), D(3, N)], [D(2, N), D(3, N)]),                # wrong N for member 1
+                   ([D(N), D(3, 2 * N)], [D(N), D(3, 2 * N)])]:             # not [n, N]
+        with pytest.raises(ValueError):
+            b.matvec(xs, ys)
+    with pytest.raises(AssertionError):
+        b.matvec([D(2, N), D(3, 2 * N)], [D(2, N), D(3, 2 * N)])
