@@ -326,7 +326,8 @@ int efie_matvec_parts(efie_handle *h, const void *x, void *yA, void *yV, int n_r
  * FP64 CGS2 Arnoldi; success when the true relative residual, recomputed with
  * the FP64 fast matvec, is <= tol.  rhs, x: device c128 [n_rhs][N]; info: host
  * array of n_rhs entries or NULL.  Returns EFIE_NOT_CONVERGED if any rhs did not
- * reach tol within max_iters (x then holds the best iterate). */
+ * reach tol within max_iters (x then holds the best iterate).  EFIE_EINVAL for
+ * tol <= 0 or for x aliasing rhs (x0 = 0 would overwrite it). */
 int efie_solve(efie_handle *h, const void *rhs, void *x, int n_rhs, double tol,
                efie_solve_info *info, void *stream);
 
@@ -359,7 +360,8 @@ int efie_precond_enable(efie_handle *h, int enable);
 /* Copy the parameters out (out != NULL) and/or replace them (in != NULL); n must
  * equal the network's parameter count. */
 int efie_precond_params(efie_handle *h, float *out, const float *in, int n);
-/* z_i = net(r_i) for n_vec device c128 vectors [n_vec][N]. */
+/* z_i = net(r_i) for n_vec device c128 vectors [n_vec][N]; z must not alias r
+ * (EFIE_EINVAL). */
 int efie_precond_apply(efie_handle *h, const void *r, void *z, int n_vec, void *stream);
 /* Loss and parameter gradient (host float[n]) of one pair at the current weights. */
 int efie_precond_gradient(efie_handle *h, const void *r, const void *e, float *grad, double *loss,

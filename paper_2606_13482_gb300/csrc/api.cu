@@ -2342,6 +2342,7 @@ int efie_solve(efie_handle* h, const void* rhs, void* x, int n_rhs, double tol, 
   if (!h) return EFIE_EINVAL;
   return guarded(h, [&] {
     if (n_rhs < 0 || ((!rhs || !x) && n_rhs > 0)) throw EfieError{EFIE_EINVAL, "bad arguments"};
+    if (rhs == x && n_rhs > 0) throw EfieError{EFIE_EINVAL, "rhs and x must not alias"};
     if (n_rhs == 0) return EFIE_OK;
     return solve_impl(h, (const double2*)rhs, (double2*)x, n_rhs, tol, info, (cudaStream_t)stream);
   });
@@ -2539,6 +2540,8 @@ int efie_precond_params(efie_handle* h, float* out, const float* in, int n) {
 int efie_precond_apply(efie_handle* h, const void* r, void* z, int n_vec, void* stream) {
   if (!h) return EFIE_EINVAL;
   return guarded(h, [&] {
+    if (n_vec < 0 || ((!r || !z) && n_vec > 0)) throw EfieError{EFIE_EINVAL, "bad arguments"};
+    if (r == z && n_vec > 0) throw EfieError{EFIE_EINVAL, "r and z must not alias"};
     if (!h->net) throw EfieError{EFIE_EINVAL, "no network loaded"};
     const int64_t N = h->plan.g.N;
     KScope ks(h, K_PRECOND, (cudaStream_t)stream, 6 * n_vec);
@@ -2552,6 +2555,7 @@ int efie_precond_apply(efie_handle* h, const void* r, void* z, int n_vec, void* 
 int efie_precond_gradient(efie_handle* h, const void* r, const void* e, float* grad, double* loss, void* stream) {
   if (!h) return EFIE_EINVAL;
   return guarded(h, [&] {
+    if (!r || !e) throw EfieError{EFIE_EINVAL, "bad arguments"};
     if (h->net_params.empty()) throw EfieError{EFIE_EINVAL, "no network parameters"};
     cudaStream_t s = (cudaStream_t)stream;
     std::vector<float> p = h->net_params;
