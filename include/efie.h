@@ -318,7 +318,8 @@ int efie_matvec_host(efie_handle *h, const void *x_host, void *y_host, int n_rhs
 int efie_matvec_fp64(efie_handle *h, const void *x, void *y, int n_rhs, void *stream);
 
 /* Separate parts, y_A = A x and y_V = Sigma V Sigma^T x (far + near), so that
- * T x = jk y_A + (jk)^-1 y_V.  Either output may be NULL. */
+ * T x = jk y_A + (jk)^-1 y_V.  Either output may be NULL; neither may alias x
+ * or the other (EFIE_EINVAL). */
 int efie_matvec_parts(efie_handle *h, const void *x, void *yA, void *yV, int n_rhs,
                       void *stream);
 
@@ -414,7 +415,9 @@ int efie_transform_schedule_get(const efie_handle *h, int *schedule);
  * default one included: capture uses an internal stream), each member on its
  * own branch of the graph.  The graph is captured on the first call and re-captured
  * whenever the pointers or counts change (that call also runs the products
- * once uncaptured to allocate the members' work buffers). */
+ * once uncaptured to allocate the members' work buffers).  EFIE_EINVAL,
+ * before any member's work, for a negative count, or for a member with vectors
+ * whose x is NULL, y is NULL or y aliases x. */
 typedef struct efie_batch efie_batch;
 int efie_batch_create(efie_handle *const *hs, int n, efie_batch **out);
 int efie_batch_matvec(efie_batch *b, const void *const *x, void *const *y, const int *n_rhs, void *stream);

@@ -2330,6 +2330,8 @@ int efie_matvec_parts(efie_handle* h, const void* x, void* yA, void* yV, int n_r
   if (!h) return EFIE_EINVAL;
   return guarded(h, [&] {
     if (n_rhs < 0 || (!x && n_rhs > 0)) throw EfieError{EFIE_EINVAL, "bad arguments"};
+    if (n_rhs > 0 && (yA == x || yV == x || (yA && yA == yV)))
+      throw EfieError{EFIE_EINVAL, "yA, yV and x must not alias"};
     if (n_rhs == 0) return EFIE_OK;
     do_matvec(h, (const double2*)x, h->plan.g.N, nullptr, (double2*)yA, (double2*)yV, h->plan.g.N, n_rhs,
               false, (cudaStream_t)stream);
@@ -2750,11 +2752,14 @@ int efie_batch_matvec(efie_batch* b, const void* const* x, void* const* y, const
   std::vector<void*> ky(y, y + n);
   std::vector<int> kn(n_rhs, n_rhs + n);
   try {
+    // every member's arguments before any member's work
+    for (size_t i = 0; i < n; ++i)
+      if (kn[i] < 0 || (kn[i] > 0 && (!x[i] || !y[i] || x[i] == y[i])))
+        throw EfieError{EFIE_EINVAL, "bad batch arguments (member " + std::to_string(i) + ")"};
     if (!b->exec || kx != b->key_x || ky != b->key_y || kn != b->key_n) {
       // allocate every member's buffers outside the capture
       for (size_t i = 0; i < n; ++i) {
         efie_handle* h = b->hs[i];
-        if (kn[i] < 0 || (kn[i] > 0 && (!x[i] || !y[i]))) throw EfieError{EFIE_EINVAL, "bad batch arguments"};
         if (kn[i] > 0)
           do_matvec(h, (const double2*)x[i], h->plan.g.N, (double2*)y[i], nullptr, nullptr, h->plan.g.N, kn[i],
                     false, s);
